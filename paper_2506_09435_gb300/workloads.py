@@ -1,0 +1,140 @@
+"""Seeded synthetic wave-tank workloads shaped like the paper's cases.
+
+This module only produces inputs (mesh descriptors, bathymetry, initial
+surface fields); it holds none of the method's arithmetic, so the CPU oracle
+and the CUDA path both consume exactly the same arrays.  Fields are evaluated
+at surface-node coordinates that the caller passes in.
+
+Physics used for inputs (not the method):
+  * linear dispersion relation omega^2 = g k tanh(k h) (used by the paper for
+    linear initial conditions, Sec. 3.3),
+  * linear (Airy) wave potential  phi = (g a / omega) cosh(k (z + h)) / cosh(k h) sin(k.x + theta)
+    evaluated at z = eta for the free-surface potential,
+  * the manufactured harmonic potential phi = cosh(kappa (z + h)) cos(kx x) cos(ky y),
+    kappa = |(kx, ky)|, with exact vertical velocity d phi/dz.
+Random numbers come from splitmix64 (Steele, Lea, Flood 2014), a counter-based
+64-bit generator, so that any implementation can reproduce them.
+"""
+import math
+
+import numpy as np
+
+G_DEFAULT = 9.81
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state):
+    """One splitmix64 step: returns (new_state, output)."""
+    state = (state + 0x9E3779B97F4A7C15) & MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return state, z ^ (z >> 31)
+
+
+def uniform01(seed, n):
+    """n doubles in [0, 1) from the top 53 bits of successive splitmix64 outputs."""
+    out = np.empty(n)
+    s = seed & MASK64
+    for i in range(n):
+        s, z = splitmix64(s)
+        out[i] = (z >> 11) * (1.0 / (1 << 53))
+    return out
+
+
+def omega(k, h, g=G_DEFAULT):
+    return math.sqrt(g * k * math.tanh(k * h))
+
+
+def period(k, h, g=G_DEFAULT):
+    return 2 * math.pi / omega(k, h, g)
+
+
+# ----------------------------------------------------------------------------
+# mesh descriptors (plain dicts; both sides build their own mesh from them)
+
+def standing_wave_2d(nx=8, nz=2, p=4, kh=1.0, h=1.0, g=G_DEFAULT):
+    """2D (x, z) periodic linear standing-wave tank: L = 2 pi / k."""
+    k = kh / h
+    return dict(dim=2, nx=nx, ny=1, nz=nz, p=p, periodic_x=True, periodic_y=False,
+                Lx=2 * math.pi / k, Ly=1.0, h0=h, k=k, g=g)
+
+
+def periodic_box_3d(nx=32, ny=32, nz=2, p=6, kh=2.0, L=1.0, g=G_DEFAULT):
+    """3D periodic box L x L, flat bottom, one wavelength k0 = 2 pi / L along x."""
+    k0 = 2 * math.pi / L
+    return dict(dim=3, nx=nx, ny=ny, nz=nz, p=p, periodic_x=True, periodic_y=True,
+                Lx=L, Ly=L, h0=kh / k0, k=k0, g=g)
+
+
+def dof_counts(desc):
+    """Global volume and surface node counts of a structured extruded mesh."""
+    p = desc["p"]
+    ncx = p * desc["nx"] + (0 if desc["periodic_x"] else 1)
+    if desc["dim"] == 3:
+        ncy = p * desc["ny"] + (0 if desc["periodic_y"] else 1)
+    else:
+        ncy = 1
+    ns = ncx * ncy
+    return (p * desc["nz"] + 1) * ns, ns
+
+
+# ----------------------------------------------------------------------------
+# initial surface states at given surface coordinates
+
+def standing_wave_state(desc, x, amp_over_h=1e-4):
+    """eta = a cos(k x) with a = amp_over_h * h, phi_eta = 0."""
+    a = amp_over_h * desc["h0"]
+    return a * np.cos(desc["k"] * x), np.zeros_like(x)
+
+
+def airy_potential(x, y, eta, a, kvec, theta, h, g):
+    kx, ky = kvec
+    k = math.hypot(kx, ky)
+    w = omega(k, h, g)
+    return (g * a / w) * np.cosh(k * (eta + h)) / math.cosh(k * h) * np.sin(kx * x + ky * y + theta)
+
+
+def airy_plus_spectrum_state(desc, x, y, seed=2, steepness=0.05, pert_rel=1e-3):
+    """Airy wave of height H = steepness * L along x plus a seeded Gaussian
+    spectrum of small perturbations in both directions.
+
+    Perturbation modes: k_m = 2 pi (mx / Lx, my / Ly) over the half-plane
+    (my > 0, or my == 0 and mx > 0) with 1 <= |k_m| / k0 <= 3; amplitude
+    proportional to exp(-(|k_m| - k0)^2 / (2 (0.25 k0)^2)); phases uniform in
+    [0, 2 pi) from splitmix64(seed); the sum is scaled so that its maximum
+    magnitude over the given nodes is pert_rel * H.  Each component's potential
+    follows linear theory and is evaluated at z = eta (total elevation)."""
+    g, h, k0 = desc["g"], desc["h0"], desc["k"]
+    Lx, Ly = desc["Lx"], desc["Ly"]
+    H = steepness * Lx
+    a0 = H / 2
+    modes = []
+    mmax = int(math.ceil(3 * k0 * max(Lx, Ly) / (2 * math.pi))) + 1
+    for my in range(0, mmax + 1):
+        for mx in range(-mmax, mmax + 1):
+            if my == 0 and mx <= 0:
+                continue
+            kv = (2 * math.pi * mx / Lx, 2 * math.pi * my / Ly)
+            kk = math.hypot(*kv)
+            if k0 <= kk <= 3 * k0 + 1e-12:
+                modes.append((kv, math.exp(-((kk - k0) ** 2) / (2 * (0.25 * k0) ** 2))))
+    phases = 2 * math.pi * uniform01(seed, len(modes))
+    pert = np.zeros_like(x)
+    for (kv, amp), th in zip(modes, phases):
+        pert += amp * np.cos(kv[0] * x + kv[1] * y + th)
+    scale = pert_rel * H / max(np.max(np.abs(pert)), 1e-300)
+    eta = a0 * np.cos(k0 * x) + scale * pert
+    # eta = a cos(k.x + theta) travels along +k with potential (g a / omega) ... sin(k.x + theta)
+    phis = airy_potential(x, y, eta, a0, (k0, 0.0), 0.0, h, g)
+    for (kv, amp), th in zip(modes, phases):
+        phis = phis + airy_potential(x, y, eta, scale * amp, kv, th, h, g)
+    return eta, phis
+
+
+def manufactured_potential(x, y, z, h, kx, ky):
+    """Harmonic phi = cosh(kappa (z + h)) cos(kx x) cos(ky y) and its d/dz."""
+    kap = math.hypot(kx, ky)
+    phi = np.cosh(kap * (z + h)) * np.cos(kx * x) * np.cos(ky * y)
+    dphidz = kap * np.sinh(kap * (z + h)) * np.cos(kx * x) * np.cos(ky * y)
+    return phi, dphidz
