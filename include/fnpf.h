@@ -1,0 +1,171 @@
+/*
+ * fnpf.h -- C ABI of the GB300 (sm_103a) FNPF-SEM hot path.
+ *
+ * Method: fully nonlinear potential flow on a free-surface-following mesh,
+ * arXiv 2506.09435.  Per explicit RK4 stage (paper Sec. 3.2, Sec. 3.4 Steps
+ * 4.1-4.6): move the mesh with eta, solve the Laplace problem for the velocity
+ * potential phi with phi = phi_eta on the free surface (Sec. 2, Eq.
+ * Laplace_strong; weak form Sec. 3.1.1, Eq. Laplace_weak), recover the
+ * vertical surface velocity w, and evaluate the Zakharov free-surface
+ * conditions (Sec. 2, Eqs. kinematic/dynamic_free_surface_strong).
+ *
+ * Discretisation (readings of the paper, which uses P_p prisms):
+ *   Q_p GLL tensor-product hexahedra (2D: quadrilaterals in the (x, z) slice)
+ *   on an Nx x Ny surface grid extruded into Nz layers; z = -h + sigma (eta + h)
+ *   with uniform layers; GLL quadrature at the nodes; lumped GLL surface mass.
+ *
+ * Data layout ("plane-major"): a volume field has N = Nv * Ns entries,
+ * index = k * Ns + col, k = 0 (bottom) .. Nv - 1 = p Nz (free surface),
+ * col = iy * ncx + ix (ix fastest), ncx = p Nx (+1 if walled in x),
+ * ncy = p Ny (+1 if walled in y; 1 in 2D), Ns = ncx * ncy.  The surface plane is
+ * the last Ns entries; the first N_I = (Nv - 1) Ns entries are the unknowns of
+ * the Laplace solve.  A surface field has Ns entries in column order.
+ *
+ * Conventions for every call below:
+ *   - double / float pointers to field data are DEVICE pointers owned by the
+ *     caller; the library never frees or retains them beyond the call;
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream); work is
+ *     enqueued on it.  A solve keeps its convergence test on the device and
+ *     the host reads the flag every check_every iterations, so solve, DtN and
+ *     RK4 calls wait for the stream at those points; apply, diagonal and
+ *     right-hand-side calls only enqueue;
+ *   - no exception crosses the ABI; failures return a status and leave a
+ *     message for fnpf_last_error(); FNPF_EINVAL is returned before any
+ *     work is enqueued.
+ */
+#ifndef FNPF_H
+#define FNPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FNPF_OK = 0,
+  FNPF_EINVAL = 1,        /* bad argument: NULL pointer, size, order, depth   */
+  FNPF_ENOMEM = 2,        /* device allocation failed                         */
+  FNPF_ECUDA = 3,         /* a CUDA runtime call failed                       */
+  FNPF_ENOCONV = 4,       /* iteration cap reached before the tolerance       */
+  FNPF_EBREAKDOWN = 5,    /* CG breakdown: p^T A p <= 0 or not finite         */
+  FNPF_EDIVERGED = 6,     /* non-finite state, or eta + h <= 0 (mesh folded)  */
+  FNPF_EUNSUPPORTED = 7   /* valid but not implemented combination            */
+} fnpf_status;
+
+enum { FNPF_BOX = 0, FNPF_ISOPARAMETRIC = 1 };
+enum { FNPF_FP64 = 0, FNPF_MIXED = 1 };
+enum { FNPF_JACOBI = 0, FNPF_PMG = 1 };
+
+/* Mesh descriptor.  All arrays are HOST pointers, copied at creation. */
+typedef struct {
+  int dim;                 /* 2: (x, z) vertical slice; 3: (x, y, z)              */
+  int nx, ny, nz;          /* elements per direction (ny ignored in 2D), >= 1      */
+  int p;                   /* GLL order, 1..8                                      */
+  int periodic_x, periodic_y; /* 1: periodic (>= 2 elements that way); 0: walls     */
+  int horiz_kind;          /* FNPF_BOX (Lx, Ly) or FNPF_ISOPARAMETRIC (X, Y)        */
+  double Lx, Ly;           /* box lengths (FNPF_BOX)                               */
+  const double* X;         /* [Ns] surface-node x (FNPF_ISOPARAMETRIC), else NULL  */
+  const double* Y;         /* [Ns] surface-node y (FNPF_ISOPARAMETRIC), else NULL  */
+  const double* h;         /* [Ns] still-water depth at surface nodes, all > 0     */
+  double g;                /* gravitational acceleration (> 0)                     */
+} fnpf_mesh_desc;
+
+/* Solver options (fnpf_default_opts fills every field). */
+typedef struct {
+  int precision;           /* FNPF_FP64 or FNPF_MIXED (FP32 inner, FP64 outer)     */
+  int precond;             /* FNPF_JACOBI or FNPF_PMG                              */
+  double rtol;             /* stop when ||r||_2 <= max(rtol ||b||_2, atol)         */
+  double atol;
+  int max_iter;            /* CG iteration cap per solve (ENOCONV beyond)          */
+  int check_every;         /* host reads the convergence flag every k iterations  */
+  int cheb_degree;         /* Chebyshev smoother degree (FNPF_PMG)                 */
+  int coarse_iters;        /* fixed coarse-level iterations (FNPF_PMG)             */
+  double inner_rtol;       /* inner FP32 solve tolerance (FNPF_MIXED)              */
+  int max_outer;           /* defect-correction cap (FNPF_MIXED)                   */
+} fnpf_opts;
+
+typedef struct {
+  int iters;               /* CG iterations (inner iterations for FNPF_MIXED)     */
+  int outer_iters;         /* defect-correction steps (0 for FNPF_FP64)            */
+  double rel_res;          /* final ||r|| / ||b|| (FP64 residual)                  */
+  int status;              /* fnpf_status of this solve                            */
+  float ms;                /* device time of the solve                             */
+} fnpf_solve_info;
+
+typedef struct fnpf_mesh fnpf_mesh;
+
+/* Node counts of a descriptor without creating anything (host arithmetic only):
+ * n_vol = (p Nz + 1) Ns, n_surf = Ns.  Returns FNPF_EINVAL on a bad descriptor. */
+fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t* n_surf);
+
+/* Fills *opts with the defaults: FP64, Jacobi, rtol 1e-10, atol 0,
+ * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 30,
+ * inner_rtol 1e-5, max_outer 20. */
+void fnpf_default_opts(fnpf_opts* opts);
+
+/* Creates a mesh on the current CUDA device: GLL tables, horizontal metric,
+ * lumped surface mass, depth, and all solver workspaces (device memory, owned
+ * by the mesh).  opts may be NULL (defaults).  Sec. 3.1.2, Sec. 3.4 Step 1.
+ * Errors: EINVAL (descriptor), ENOMEM, ECUDA. */
+fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, fnpf_mesh** out);
+void fnpf_destroy_mesh(fnpf_mesh* mesh);
+fnpf_status fnpf_set_opts(fnpf_mesh* mesh, const fnpf_opts* opts);
+fnpf_status fnpf_mesh_sizes(const fnpf_mesh* mesh, int64_t* n_vol, int64_t* n_surf);
+
+/* Physical (x, y) of every surface column into HOST arrays [Ns] (y = 0 in 2D;
+ * a periodic seam column reports its first copy, x = 0 / y = 0). */
+fnpf_status fnpf_surface_coords(const fnpf_mesh* mesh, double* x, double* y);
+
+/* y = A(eta) x: the assembled stiffness matrix of the weak Laplace form
+ * (Eq. Laplace_weak, all N rows, no Dirichlet masking) applied to x [N];
+ * eta [Ns].  Matrix-free, sum-factorised, geometric factors rebuilt from eta.
+ * x and y must not overlap. */
+fnpf_status fnpf_apply(fnpf_mesh* mesh, const double* eta, const double* x, double* y, void* stream);
+
+/* d = diag(A(eta)) [N] (Jacobi preconditioner of the Laplace solve). */
+fnpf_status fnpf_diagonal(fnpf_mesh* mesh, const double* eta, double* d, void* stream);
+
+/* Laplace solve (Sec. 3.4 Steps 4.1-4.3): A_II phi_I = -A_IS phi_eta.
+ * eta, phis [Ns]; phi [N]: on entry its first N_I entries are the initial
+ * guess, on return phi holds the solution with phi = phis on the surface
+ * plane.  info may be NULL.  The failure statuses ENOCONV, EBREAKDOWN and
+ * EDIVERGED are returned by the call itself. */
+fnpf_status fnpf_laplace_solve(fnpf_mesh* mesh, const double* eta, const double* phis, double* phi,
+                               fnpf_solve_info* info, void* stream);
+
+/* Dirichlet-to-Neumann map (Steps 4.1-4.5): w = d phi / dz on the surface,
+ * w [Ns].  The volume potential is kept inside the mesh and warm-starts the
+ * next solve. */
+fnpf_status fnpf_dtn(fnpf_mesh* mesh, const double* eta, const double* phis, double* w,
+                     fnpf_solve_info* info, void* stream);
+
+/* Zakharov right-hand side (Step 4.6, lumped GLL mass): given eta, phis, w [Ns]
+ * returns d eta/dt and d phi_eta/dt [Ns]. */
+fnpf_status fnpf_zakharov_rhs(fnpf_mesh* mesh, const double* eta, const double* phis, const double* w,
+                              double* deta, double* dphis, void* stream);
+
+/* One classical RK4 step (Sec. 3.2) of the state (eta, phis) [Ns], in place:
+ * four DtN solves and right-hand sides.  info may be NULL or point to 4
+ * structs (one per stage; then the call waits for the stream). */
+fnpf_status fnpf_rk4_step(fnpf_mesh* mesh, double* eta, double* phis, double t, double dt,
+                          fnpf_solve_info* info, void* stream);
+
+/* Instrumentation (tracing): when enabled, every operator application issued
+ * by a solve is bracketed by CUDA events on the solve's stream, and the
+ * elapsed device time and count are accumulated.  The launch counter counts
+ * every kernel the library enqueues for this mesh, enabled or not.
+ * fnpf_profile_read returns the totals and, if reset != 0, clears them. */
+fnpf_status fnpf_profile_enable(fnpf_mesh* mesh, int on);
+fnpf_status fnpf_profile_read(fnpf_mesh* mesh, double* apply_ms, int64_t* apply_count, int64_t* kernel_launches,
+                              int reset);
+
+/* Message of the last failure on this mesh (or of the last create failure
+ * when mesh is NULL).  Valid until the next call on the same mesh. */
+const char* fnpf_last_error(const fnpf_mesh* mesh);
+const char* fnpf_status_string(fnpf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FNPF_H */

@@ -1,0 +1,144 @@
+// C entry points of the compute path (operator, solve, DtN, right-hand side,
+// RK4 step).  See include/fnpf.h for the contract of each call.
+#include <math.h>
+
+#include <algorithm>
+
+#include "mesh.cuh"
+
+using fnpf::Geom;
+
+namespace {
+
+fnpf_status cuda_fail(fnpf_mesh* m, cudaError_t e, const char* what) {
+  m->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return FNPF_ECUDA;
+}
+
+// Laplace solve into the mesh-owned potential (or the caller's) and copy the
+// Dirichlet data into its surface plane.
+fnpf_status solve_into(fnpf_mesh* m, const double* eta, const double* phis, double* phi, fnpf_solve_info* info,
+                       cudaStream_t s) {
+  const Geom& g = m->g;
+  fnpf_status st = fnpf::cg_solve(m, eta, phis, phi, info, s);
+  cudaError_t e = cudaMemcpyAsync(phi + g.NI, phis, g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(m, e, "copy surface plane");
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+fnpf_status fnpf_apply(fnpf_mesh* m, const double* eta, const double* x, double* y, void* stream) {
+  if (!m || !eta || !x || !y) return FNPF_EINVAL;
+  const Geom& g = m->g;
+  cudaError_t e = fnpf::launch_apply<double>(g, m->tables(), eta, x, x + g.NI, y, y + g.NI, m->ring, m->variant,
+                                             (cudaStream_t)stream);
+  return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "apply");
+}
+
+fnpf_status fnpf_diagonal(fnpf_mesh* m, const double* eta, double* d, void* stream) {
+  if (!m || !eta || !d) return FNPF_EINVAL;
+  const Geom& g = m->g;
+  cudaError_t e = fnpf::launch_diag<double>(g, m->tables(), eta, d, d + g.NI, m->ring, (cudaStream_t)stream);
+  return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "diagonal");
+}
+
+fnpf_status fnpf_laplace_solve(fnpf_mesh* m, const double* eta, const double* phis, double* phi,
+                               fnpf_solve_info* info, void* stream) {
+  if (!m || !eta || !phis || !phi) return FNPF_EINVAL;
+  return solve_into(m, eta, phis, phi, info, (cudaStream_t)stream);
+}
+
+fnpf_status fnpf_dtn(fnpf_mesh* m, const double* eta, const double* phis, double* w, fnpf_solve_info* info,
+                     void* stream) {
+  if (!m || !eta || !phis || !w) return FNPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  fnpf_status st = solve_into(m, eta, phis, m->phi, info, s);
+  if (st != FNPF_OK) return st;
+  cudaError_t e = fnpf::launch_w(m->g, m->tables(), eta, phis, m->phi, w, s);
+  m->launches += 1;
+  return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "w recovery");
+}
+
+fnpf_status fnpf_zakharov_rhs(fnpf_mesh* m, const double* eta, const double* phis, const double* w, double* deta,
+                              double* dphis, void* stream) {
+  if (!m || !eta || !phis || !w || !deta || !dphis) return FNPF_EINVAL;
+  fnpf::StageArgs a{};
+  a.eta = eta;
+  a.phis = phis;
+  a.w_in = w;
+  a.deta = deta;
+  a.dphis = dphis;
+  cudaError_t e = fnpf::launch_stage(m->g, m->tables(), a, (cudaStream_t)stream);
+  return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "rhs");
+}
+
+fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, double dt, fnpf_solve_info* info,
+                          void* stream) {
+  (void)t;
+  if (!m || !eta || !phis || !(dt > 0) || !isfinite(dt)) return FNPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  static const double bw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const double cn[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+  const double* ce = eta;
+  const double* cp = phis;
+  for (int st = 0; st < 4; ++st) {
+    fnpf_status r = fnpf::cg_solve(m, ce, cp, m->phi, info ? info + st : nullptr, s);
+    if (r != FNPF_OK) return r;
+    fnpf::StageArgs a{};
+    a.eta = ce;
+    a.phis = cp;
+    a.phi = m->phi;
+    a.y0_eta = eta;
+    a.y0_phi = phis;
+    a.acc_eta = m->acc_eta;
+    a.acc_phi = m->acc_phi;
+    a.out_eta = st < 3 ? m->s_eta[st & 1] : eta;
+    a.out_phi = st < 3 ? m->s_phi[st & 1] : phis;
+    a.bw = bw[st];
+    a.cn = cn[st];
+    a.dt = dt;
+    a.first = st == 0;
+    a.last = st == 3;
+    a.status = &m->sc->status;
+    cudaError_t e = fnpf::launch_stage(m->g, m->tables(), a, s);
+    m->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(m, e, "stage");
+    ce = a.out_eta;
+    cp = a.out_phi;
+  }
+  return FNPF_OK;
+}
+
+fnpf_status fnpf_profile_enable(fnpf_mesh* m, int on) {
+  if (!m) return FNPF_EINVAL;
+  if (on && m->prof_ev.empty()) {
+    const int pairs = std::max(64, m->opts.check_every + 8);
+    m->prof_ev.resize(2 * pairs);
+    m->prof_it.assign(pairs, -1);
+    for (auto& e : m->prof_ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return cuda_fail(m, r, "profile events");
+    }
+  }
+  m->prof_on = on != 0;
+  return FNPF_OK;
+}
+
+fnpf_status fnpf_profile_read(fnpf_mesh* m, double* apply_ms, int64_t* apply_count, int64_t* kernel_launches,
+                              int reset) {
+  if (!m) return FNPF_EINVAL;
+  if (apply_ms) *apply_ms = m->prof_ms;
+  if (apply_count) *apply_count = m->prof_count;
+  if (kernel_launches) *kernel_launches = m->launches;
+  if (reset) {
+    m->prof_ms = 0;
+    m->prof_count = 0;
+    m->launches = 0;
+  }
+  return FNPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,9 @@
+// Instantiations of the operator kernels for GLL order p = 2.
+#include "ax_impl.cuh"
+
+namespace fnpf {
+template cudaError_t launch_ax_n<double, 3>(const Geom&, const Tables<double>&, const AxPtrs<double>&, bool, int,
+                                            cudaStream_t);
+template cudaError_t launch_ax_n<float, 3>(const Geom&, const Tables<float>&, const AxPtrs<float>&, bool, int,
+                                           cudaStream_t);
+}  // namespace fnpf

@@ -1,0 +1,158 @@
+// Internal declarations of the FNPF-SEM CUDA library (not part of the ABI).
+//
+// Layout reminder (see include/fnpf.h): volume index = k * ns + col,
+// col = iy * ncx + ix; the surface plane is k = nv - 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fnpf.h"
+
+namespace fnpf {
+
+constexpr int kMaxP = 8;
+constexpr int kMaxN = kMaxP + 1;
+constexpr int kVecBlocks = 608;      // 4 x 152 SMs: grid of the vector kernels
+constexpr int kVecThreads = 256;
+
+// Mesh sizes, passed by value to every kernel.
+struct Geom {
+  int dim, nx, ny, nz, p, n;
+  int px, py;                // periodic flags
+  int ncx, ncy;              // node columns per direction
+  int ns, nv;                // surface columns, nodes per column
+  int n_ecol;                // element columns nx * ny
+  int lines;                 // vertical lines per element column: n*n (3D) or n (2D)
+  int ring;                  // ring lines per element column: 4p (3D) or 2 (2D)
+  int64_t N, NI;             // volume DOF, interior (unknown) DOF
+  double g;
+};
+
+// Device-resident tables of one mesh in precision T.
+template <typename T>
+struct Tables {
+  const T* D;      // [n*n], D[i*n + a] = l_a'(xi_i)
+  const T* xi;     // [n]
+  const T* w;      // [n]
+  const T* hm;     // [5][n_ecol * lines]: r_x, r_y, s_x, s_y, w_i w_j |J2|
+  const T* h;      // [ns] depth
+  const T* minv;   // [ns] inverse lumped surface mass
+};
+
+// Scalars of one CG solve, device-resident.  rz is double-buffered by the
+// host-known iteration parity so that no kernel reads a scalar another block
+// of the same kernel writes.
+struct CgScalars {
+  double rz[2];
+  double rr;
+  double bb;
+  double tol2;
+  double pq;
+  int done;
+  int iters;
+  int status;
+  int pad;
+};
+
+// Shared device helpers -------------------------------------------------------
+
+// Global column of local horizontal node (i, j) of element column (ex, ey).
+__host__ __device__ inline int node_col(const Geom& g, int ex, int ey, int i, int j) {
+  int ix = ex * g.p + i;
+  if (g.px && ix >= g.ncx) ix -= g.ncx;
+  int iy = 0;
+  if (g.dim == 3) {
+    iy = ey * g.p + j;
+    if (g.py && iy >= g.ncy) iy -= g.ncy;
+  }
+  return iy * g.ncx + ix;
+}
+
+// Ring slot of boundary line (i, j) of an element column, -1 for interior lines.
+__host__ __device__ inline int ring_slot(int dim, int p, int i, int j) {
+  if (dim == 2) return i == 0 ? 0 : (i == p ? 1 : -1);
+  const int n = p + 1;
+  if (j == 0) return i;
+  if (j == p) return n + i;
+  if (i == 0) return 2 * n + (j - 1);
+  if (i == p) return 2 * n + (p - 1) + (j - 1);
+  return -1;
+}
+
+// Owners of a node index along one direction: up to two (element, local index)
+// pairs, in a fixed order.
+__host__ __device__ inline int line_owners(int idx, int p, int ne, int periodic, int* e, int* loc) {
+  if (idx % p != 0) {
+    e[0] = idx / p;
+    loc[0] = idx % p;
+    return 1;
+  }
+  int L = idx / p, cnt = 0;
+  if (L < ne) { e[cnt] = L; loc[cnt] = 0; ++cnt; }
+  if (L >= 1) { e[cnt] = L - 1; loc[cnt] = p; ++cnt; }
+  else if (periodic) { e[cnt] = ne - 1; loc[cnt] = p; ++cnt; }
+  return cnt;
+}
+
+// Host-side helpers ------------------------------------------------------------
+fnpf_status validate_desc(const fnpf_mesh_desc* d, std::string* why);
+Geom make_geom(const fnpf_mesh_desc* d);
+void gll_tables(int p, double* xi, double* w, double* D);   // host, long-double Newton
+
+// Pointers of one operator application.
+template <typename T>
+struct AxPtrs {
+  const T* eta;
+  const T* xI;
+  const T* xs;
+  T* yI;
+  T* ys;
+  T* ring;
+  const int* skip;   // if non-null and *skip != 0 the launch does nothing (converged solve)
+};
+
+// Per-order operator launcher, explicitly instantiated in ax_n<N>.cu.
+template <typename T, int N>
+cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, bool diag, int variant,
+                        cudaStream_t s);
+
+// Operator launches (ax_dispatch.cu).  xI == nullptr means zero interior;
+// xs == nullptr means zero surface plane; ys == nullptr: surface rows not
+// written.  `ring` is scratch of size nv * n_ecol * g.ring.
+template <typename T>
+cudaError_t launch_apply(const Geom& g, const Tables<T>& t, const T* eta, const T* xI, const T* xs, T* yI,
+                         T* ys, T* ring, int variant, cudaStream_t s, const int* skip = nullptr);
+template <typename T>
+cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, T* ds, T* ring, cudaStream_t s);
+int apply_variants(int n, int dim);   // number of elements-per-CTA variants for order n-1
+
+// Surface kernels (surface.cu).
+struct StageArgs {
+  const double* eta;     // stage state (read, neighbours)
+  const double* phis;
+  const double* phi;     // volume potential of this stage (top planes)
+  const double* y0_eta;  // y_n (pointwise)
+  const double* y0_phi;
+  double* acc_eta;       // RK4 accumulator (pointwise)
+  double* acc_phi;
+  double* out_eta;       // next stage state, or y_{n+1} on the last stage
+  double* out_phi;
+  double bw;             // weight of this stage's k in the final combination
+  double cn;             // c_{s+1} dt for the next stage state
+  double dt;
+  int first, last;
+  double* deta;          // plain right-hand-side output (may be null)
+  double* dphis;
+  const double* w_in;    // if non-null, use this w instead of recovering it from phi
+  int* status;           // set to FNPF_EDIVERGED on a non-finite or folded state
+};
+cudaError_t launch_stage(const Geom& g, const Tables<double>& t, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_w(const Geom& g, const Tables<double>& t, const double* eta, const double* phis,
+                     const double* phi, double* w, cudaStream_t s);
+cudaError_t launch_check_state(const Geom& g, const double* eta, const double* phis, const double* h, int* status,
+                               int* done, cudaStream_t s);
+
+}  // namespace fnpf

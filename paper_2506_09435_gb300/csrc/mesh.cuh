@@ -1,0 +1,65 @@
+// The opaque fnpf_mesh of the C ABI: sizes, tables, workspaces.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "fnpf_internal.cuh"
+
+struct fnpf_mesh {
+  fnpf::Geom g{};
+  fnpf_opts opts{};
+  std::string err;
+  int device = 0;
+  int variant = 1;                  // elements-per-CTA shape of the apply kernel
+
+  // host copies
+  std::vector<double> xi, w, D;     // GLL tables
+  std::vector<double> hm;           // horizontal metric [5][n_ecol * lines]
+  std::vector<double> h, minv;      // depth, inverse lumped mass [ns]
+  std::vector<double> xs, ys;       // surface coordinates [ns]
+
+  // device tables (double)
+  double* dD = nullptr;
+  double* dxi = nullptr;
+  double* dw = nullptr;
+  double* dhm = nullptr;
+  double* dh = nullptr;
+  double* dminv = nullptr;
+
+  // workspaces (double)
+  double* ring = nullptr;           // nv * n_ecol * ring
+  double* r = nullptr;              // NI each
+  double* z = nullptr;
+  double* p = nullptr;
+  double* q = nullptr;
+  double* dinv = nullptr;
+  double* phi = nullptr;            // N: potential kept between solves (warm start)
+  double* partials = nullptr;       // 4 * kVecBlocks
+  fnpf::CgScalars* sc = nullptr;    // device scalars
+  fnpf::CgScalars* sc_host = nullptr;  // pinned mirror
+  double* s_eta[2] = {nullptr, nullptr};  // RK4 stage states
+  double* s_phi[2] = {nullptr, nullptr};
+  double* acc_eta = nullptr;
+  double* acc_phi = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // instrumentation
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop) of operator applications
+  std::vector<int> prof_it;          // CG iteration of each recorded pair
+  int prof_used = 0;                 // pairs recorded since the last host sync
+  double prof_ms = 0.0;
+  int64_t prof_count = 0;
+  int64_t launches = 0;
+
+  fnpf::Tables<double> tables() const { return fnpf::Tables<double>{dD, dxi, dw, dhm, dh, dminv}; }
+};
+
+namespace fnpf {
+// Accumulates the recorded event pairs (call after a host sync of the stream).
+void prof_collect(fnpf_mesh* m, int iters_done);
+// CG solve of A_II x = -A_IS phis for the interior part x [NI] (in: initial guess).
+fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,
+                     cudaStream_t s);
+}  // namespace fnpf

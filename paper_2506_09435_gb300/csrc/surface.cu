@@ -1,0 +1,141 @@
+// Surface kernels: vertical-velocity recovery, Zakharov right-hand side with
+// lumped GLL mass, and the fused RK4 stage update (arXiv 2506.09435, Sec. 2
+// Eqs. kinematic/dynamic_free_surface_strong; Sec. 3.1.1 Eq. free_surface_weak;
+// Sec. 3.2 ERK4; Sec. 3.4 Steps 4.4-4.6).
+//
+// One thread per surface node column.  w = d phi/dz = phi_t / z_t with
+// z_t = (eta + h) / (2 Nz) and phi_t the GLL derivative along the top
+// element's vertical line (unique across the elements sharing the node, since
+// the mesh is extruded vertically).  The right-hand side is evaluated in every
+// element sharing the node with the element-local horizontal gradients and
+// combined with the lumped-mass weights w_i w_j |det H|:
+//     d eta/dt = sum_e W_e f_eta,e / sum_e W_e  (likewise for phi).
+// The 1/2 |grad phi|^2 term carries the sign of the strong (Bernoulli) form.
+#include <math.h>
+
+#include "fnpf_internal.cuh"
+
+namespace fnpf {
+namespace {
+
+__device__ inline double top_w(const Geom& g, const double* D, const double* phi, const double* phis,
+                               const double* h, const double* eta, int col) {
+  const int P = g.p;
+  double s = 0;
+  for (int j = 0; j < P; ++j) s += D[P * g.n + j] * phi[(int64_t)(g.nv - 1 - P + j) * g.ns + col];
+  s += D[P * g.n + P] * phis[col];
+  return s * (2.0 * g.nz) / (eta[col] + h[col]);
+}
+
+__global__ void stage_kernel(Geom g, Tables<double> t, StageArgs a) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= g.ns) return;
+  const int P = g.p, n = g.n;
+  const int ix = col % g.ncx, iy = col / g.ncx;
+  const double e0 = a.eta[col];
+  const double hh = t.h[col];
+  if (!(e0 + hh > 0.0) || !isfinite(e0) || !isfinite(a.phis[col])) {
+    if (a.status) atomicExch(a.status, (int)FNPF_EDIVERGED);
+  }
+  const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.eta, col);
+  int exo[2], io[2], eyo[2] = {0, 0}, jo[2] = {0, 0};
+  const int cx = line_owners(ix, P, g.nx, g.px, exo, io);
+  const int cy = g.dim == 3 ? line_owners(iy, P, g.ny, g.py, eyo, jo) : 1;
+  const int64_t hstride = (int64_t)g.n_ecol * g.lines;
+  double se = 0, sp = 0, sw = 0;
+  for (int u = 0; u < cx; ++u) {
+    for (int v = 0; v < cy; ++v) {
+      const int ex = exo[u], ey = eyo[v], i = io[u], j = jo[v];
+      const int ecol = ey * g.nx + ex;
+      const int line = j * n + i;
+      double er = 0, pr = 0, es = 0, ps = 0;
+      for (int m = 0; m < n; ++m) {
+        const double d = t.D[i * n + m];
+        const int c2 = node_col(g, ex, ey, m, j);
+        er += d * a.eta[c2];
+        pr += d * a.phis[c2];
+      }
+      if (g.dim == 3) {
+        for (int m = 0; m < n; ++m) {
+          const double d = t.D[j * n + m];
+          const int c2 = node_col(g, ex, ey, i, m);
+          es += d * a.eta[c2];
+          ps += d * a.phis[c2];
+        }
+      }
+      const int64_t hidx = (int64_t)ecol * g.lines + line;
+      const double rx = t.hm[hidx], ry = t.hm[hstride + hidx], sx = t.hm[2 * hstride + hidx],
+                   sy = t.hm[3 * hstride + hidx], cw = t.hm[4 * hstride + hidx];
+      const double ex_ = er * rx + es * sx, ey_ = er * ry + es * sy;   // grad eta
+      const double px_ = pr * rx + ps * sx, py_ = pr * ry + ps * sy;   // grad phi
+      const double ge2 = 1.0 + ex_ * ex_ + ey_ * ey_;
+      const double fe = -(ex_ * px_ + ey_ * py_) + w * ge2;
+      const double fp = -g.g * e0 - 0.5 * (px_ * px_ + py_ * py_) + 0.5 * w * w * ge2;
+      se += cw * fe;
+      sp += cw * fp;
+      sw += cw;
+    }
+  }
+  (void)sw;
+  const double ke = se * t.minv[col], kp = sp * t.minv[col];
+  if (a.deta) {
+    a.deta[col] = ke;
+    a.dphis[col] = kp;
+  }
+  if (a.out_eta) {
+    const double acc_e = (a.first ? 0.0 : a.acc_eta[col]) + a.bw * ke;
+    const double acc_p = (a.first ? 0.0 : a.acc_phi[col]) + a.bw * kp;
+    const double y0e = a.y0_eta[col], y0p = a.y0_phi[col];
+    if (a.last) {
+      a.out_eta[col] = y0e + a.dt * acc_e;
+      a.out_phi[col] = y0p + a.dt * acc_p;
+    } else {
+      a.acc_eta[col] = acc_e;
+      a.acc_phi[col] = acc_p;
+      a.out_eta[col] = y0e + a.cn * ke;
+      a.out_phi[col] = y0p + a.cn * kp;
+    }
+  }
+}
+
+__global__ void w_kernel(Geom g, Tables<double> t, const double* eta, const double* phis, const double* phi,
+                         double* w) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= g.ns) return;
+  w[col] = top_w(g, t.D, phi, phis, t.h, eta, col);
+}
+
+__global__ void check_state_kernel(Geom g, const double* eta, const double* phis, const double* h, int* status,
+                                   int* done) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= g.ns) return;
+  const double e = eta[col];
+  if (!(e + h[col] > 0.0) || !isfinite(e) || !isfinite(phis[col])) {
+    atomicExch(status, (int)FNPF_EDIVERGED);
+    atomicExch(done, 1);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stage(const Geom& g, const Tables<double>& t, const StageArgs& a, cudaStream_t s) {
+  const int threads = 128;
+  stage_kernel<<<(g.ns + threads - 1) / threads, threads, 0, s>>>(g, t, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_w(const Geom& g, const Tables<double>& t, const double* eta, const double* phis,
+                     const double* phi, double* w, cudaStream_t s) {
+  const int threads = 128;
+  w_kernel<<<(g.ns + threads - 1) / threads, threads, 0, s>>>(g, t, eta, phis, phi, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_state(const Geom& g, const double* eta, const double* phis, const double* h, int* status,
+                               int* done, cudaStream_t s) {
+  const int threads = 128;
+  check_state_kernel<<<(g.ns + threads - 1) / threads, threads, 0, s>>>(g, eta, phis, h, status, done);
+  return cudaGetLastError();
+}
+
+}  // namespace fnpf

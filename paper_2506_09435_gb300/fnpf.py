@@ -1,0 +1,227 @@
+"""Python binding of the C ABI in include/fnpf.h (argument marshalling only).
+
+Every computation runs in libfnpf.so's CUDA kernels; this module only turns
+torch tensors into device pointers and streams into cudaStream_t handles.
+Importing it fails loudly when the shared library is missing: there is no
+CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfnpf.so")
+
+FNPF_OK, FNPF_EINVAL, FNPF_ENOMEM, FNPF_ECUDA, FNPF_ENOCONV, FNPF_EBREAKDOWN, FNPF_EDIVERGED, \
+    FNPF_EUNSUPPORTED = range(8)
+FNPF_BOX, FNPF_ISOPARAMETRIC = 0, 1
+FNPF_FP64, FNPF_MIXED = 0, 1
+FNPF_JACOBI, FNPF_PMG = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("p", ctypes.c_int), ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int),
+                ("horiz_kind", ctypes.c_int), ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+                ("X", _dp), ("Y", _dp), ("h", _dp), ("g", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("max_outer", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("status", ctypes.c_int), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, outer_iters=self.outer_iters, rel_res=self.rel_res, status=self.status,
+                    ms=self.ms)
+
+
+def load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfnpf.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_2506_09435_gb300.build); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "fnpf_count_dofs": [ctypes.POINTER(MeshDesc), i64p, i64p],
+        "fnpf_create_mesh": [ctypes.POINTER(MeshDesc), ctypes.POINTER(Opts), ctypes.POINTER(vp)],
+        "fnpf_set_opts": [vp, ctypes.POINTER(Opts)],
+        "fnpf_mesh_sizes": [vp, i64p, i64p],
+        "fnpf_surface_coords": [vp, _dp, _dp],
+        "fnpf_apply": [vp, vp, vp, vp, vp],
+        "fnpf_diagonal": [vp, vp, vp, vp],
+        "fnpf_laplace_solve": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
+        "fnpf_dtn": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
+        "fnpf_zakharov_rhs": [vp, vp, vp, vp, vp, vp, vp],
+        "fnpf_rk4_step": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(SolveInfo), vp],
+        "fnpf_profile_enable": [vp, ctypes.c_int],
+        "fnpf_profile_read": [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p, ctypes.c_int],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.fnpf_destroy_mesh.argtypes = [vp]
+    lib.fnpf_destroy_mesh.restype = None
+    lib.fnpf_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.fnpf_default_opts.restype = None
+    lib.fnpf_last_error.argtypes = [vp]
+    lib.fnpf_last_error.restype = ctypes.c_char_p
+    lib.fnpf_status_string.argtypes = [ctypes.c_int]
+    lib.fnpf_status_string.restype = ctypes.c_char_p
+    return lib
+
+
+_LIB = load()
+
+
+class FnpfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("fnpf status %d (%s): %s" % (status, _LIB.fnpf_status_string(status).decode(), msg))
+        self.status = status
+
+
+def lib():
+    return _LIB
+
+
+def default_opts(**kw):
+    o = Opts()
+    _LIB.fnpf_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    """Device pointer of a contiguous CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_desc(dim, nx, ny, nz, p, periodic_x, periodic_y, h, Lx=1.0, Ly=1.0, X=None, Y=None, g=9.81):
+    """Builds a MeshDesc; returns (desc, keepalive) -- the arrays must outlive the call."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    keep = [h]
+    d = MeshDesc(dim=dim, nx=nx, ny=ny, nz=nz, p=p, periodic_x=int(periodic_x), periodic_y=int(periodic_y),
+                 horiz_kind=FNPF_BOX if X is None else FNPF_ISOPARAMETRIC, Lx=Lx, Ly=Ly, g=g)
+    d.h = h.ctypes.data_as(_dp)
+    if X is not None:
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.ascontiguousarray(Y if Y is not None else np.zeros_like(X), dtype=np.float64)
+        keep += [X, Y]
+        d.X = X.ctypes.data_as(_dp)
+        d.Y = Y.ctypes.data_as(_dp)
+    return d, keep
+
+
+def count_dofs(dim, nx, ny, nz, p, periodic_x=True, periodic_y=True):
+    d = MeshDesc(dim=dim, nx=nx, ny=ny, nz=nz, p=p, periodic_x=int(periodic_x), periodic_y=int(periodic_y),
+                 horiz_kind=FNPF_BOX, Lx=1.0, Ly=1.0, g=9.81)
+    nv, ns = ctypes.c_int64(), ctypes.c_int64()
+    st = _LIB.fnpf_count_dofs(ctypes.byref(d), ctypes.byref(nv), ctypes.byref(ns))
+    if st != FNPF_OK:
+        raise FnpfError(st, "bad descriptor")
+    return nv.value, ns.value
+
+
+class Mesh:
+    """Owns one fnpf_mesh (device workspaces on the current CUDA device)."""
+
+    def __init__(self, dim, nx, ny, nz, p, periodic_x=True, periodic_y=True, h=None, Lx=1.0, Ly=1.0, X=None,
+                 Y=None, g=9.81, opts=None):
+        if h is None:
+            raise ValueError("h (depth at surface nodes) is required")
+        d, keep = make_desc(dim, nx, ny, nz, p, periodic_x, periodic_y, h, Lx, Ly, X, Y, g)
+        o = opts if opts is not None else default_opts()
+        handle = ctypes.c_void_p()
+        st = _LIB.fnpf_create_mesh(ctypes.byref(d), ctypes.byref(o), ctypes.byref(handle))
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_last_error(None).decode())
+        self._h = handle
+        self.g = g
+        nv, ns = ctypes.c_int64(), ctypes.c_int64()
+        _LIB.fnpf_mesh_sizes(self._h, ctypes.byref(nv), ctypes.byref(ns))
+        self.N, self.ns = nv.value, ns.value
+        self.n_interior = self.N - self.ns
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _LIB.fnpf_destroy_mesh(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, st):
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_last_error(self._h).decode())
+
+    def set_opts(self, opts):
+        self._check(_LIB.fnpf_set_opts(self._h, ctypes.byref(opts)))
+
+    def surface_coords(self):
+        x = np.zeros(self.ns)
+        y = np.zeros(self.ns)
+        self._check(_LIB.fnpf_surface_coords(self._h, x.ctypes.data_as(_dp), y.ctypes.data_as(_dp)))
+        return x, y
+
+    def apply(self, eta, x, y, stream=None):
+        self._check(_LIB.fnpf_apply(self._h, _ptr(eta), _ptr(x), _ptr(y), _stream(stream)))
+
+    def diagonal(self, eta, d, stream=None):
+        self._check(_LIB.fnpf_diagonal(self._h, _ptr(eta), _ptr(d), _stream(stream)))
+
+    def laplace_solve(self, eta, phis, phi, stream=None, info=True, check=True):
+        inf = SolveInfo() if info else None
+        st = _LIB.fnpf_laplace_solve(self._h, _ptr(eta), _ptr(phis), _ptr(phi),
+                                     ctypes.byref(inf) if inf is not None else None, _stream(stream))
+        if check:
+            self._check(st)
+        return inf.as_dict() if inf is not None else st
+
+    def dtn(self, eta, phis, w, stream=None, info=True, check=True):
+        inf = SolveInfo() if info else None
+        st = _LIB.fnpf_dtn(self._h, _ptr(eta), _ptr(phis), _ptr(w),
+                           ctypes.byref(inf) if inf is not None else None, _stream(stream))
+        if check:
+            self._check(st)
+        return inf.as_dict() if inf is not None else st
+
+    def zakharov_rhs(self, eta, phis, w, deta, dphis, stream=None):
+        self._check(_LIB.fnpf_zakharov_rhs(self._h, _ptr(eta), _ptr(phis), _ptr(w), _ptr(deta), _ptr(dphis),
+                                           _stream(stream)))
+
+    def profile_enable(self, on=True):
+        self._check(_LIB.fnpf_profile_enable(self._h, int(on)))
+
+    def profile_read(self, reset=False):
+        ms, cnt, launches = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(_LIB.fnpf_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(launches),
+                                           int(reset)))
+        return dict(apply_ms=ms.value, apply_count=cnt.value, launches=launches.value)
+
+    def rk4_step(self, eta, phis, t, dt, stream=None, info=False, check=True):
+        infos = (SolveInfo * 4)() if info else None
+        st = _LIB.fnpf_rk4_step(self._h, _ptr(eta), _ptr(phis), float(t), float(dt), infos, _stream(stream))
+        if check:
+            self._check(st)
+        return [i.as_dict() for i in infos] if infos is not None else st

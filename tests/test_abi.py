@@ -1,0 +1,51 @@
+"""The C ABI library loads and exports every entry point declared in
+include/fnpf.h; host-only calls work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fnpf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fnpf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(fnpf):
+    names = declared_functions()
+    assert "fnpf_rk4_step" in names and "fnpf_create_mesh" in names
+    lib = ctypes.CDLL(fnpf.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_count_dofs_matches_paper_tables(fnpf):
+    from tests.test_oracle_operator import read_dof_table
+    for nx, ny, nz, p, nvol, nsurf, _ in read_dof_table():
+        nv, ns = fnpf.count_dofs(3, nx, ny, nz, p, True, True)
+        assert nv == nvol
+        if nsurf >= 0:
+            assert ns == nsurf
+
+
+def test_count_dofs_walled_and_2d(fnpf):
+    assert fnpf.count_dofs(3, 3, 2, 2, 4, False, False) == ((4 * 2 + 1) * 13 * 9, 13 * 9)
+    assert fnpf.count_dofs(2, 8, 1, 2, 4, True, False) == (9 * 32, 32)
+
+
+@pytest.mark.parametrize("bad", [dict(p=0), dict(p=9), dict(nx=0), dict(nz=0), dict(dim=4)])
+def test_count_dofs_rejects_bad_descriptors(fnpf, bad):
+    args = dict(dim=3, nx=2, ny=2, nz=1, p=3)
+    args.update(bad)
+    with pytest.raises(fnpf.FnpfError) as e:
+        fnpf.count_dofs(args["dim"], args["nx"], args["ny"], args["nz"], args["p"])
+    assert e.value.status == fnpf.FNPF_EINVAL
+
+
+def test_default_opts(fnpf):
+    o = fnpf.default_opts()
+    assert o.precision == fnpf.FNPF_FP64 and o.rtol == 1e-10 and o.max_iter > 0 and o.check_every > 0
