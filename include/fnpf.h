@@ -151,6 +151,29 @@ fnpf_status fnpf_zakharov_rhs(fnpf_mesh* mesh, const double* eta, const double* 
 fnpf_status fnpf_rk4_step(fnpf_mesh* mesh, double* eta, double* phis, double t, double dt,
                           fnpf_solve_info* info, void* stream);
 
+/* Operator application without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, such as a
+ * plug-in inside a host application that owns all device memory through its
+ * own pool, or a loop with a fixed, pre-reserved memory budget where an
+ * allocation could fail or stall.  Computes y = A(eta) x exactly as
+ * fnpf_apply does, for an FNPF_BOX mesh described by desc (host struct; its
+ * h, X, Y pointers are ignored) with the depth h [Ns], eta [Ns], x [N] and
+ * y [N] given as caller-owned DEVICE arrays.
+ * The GLL tables, the box metric and the operator's scratch live in one
+ * file-scope device array of 16 MiB (2,097,152 doubles) that every GPU
+ * loading the library holds until exit; a mesh needs
+ * n^2 + 2n + 5 n_ecol L + Nv n_ecol R doubles of it (L = (p+1)^2, R = 4p in
+ * 3D; L = p+1, R = 2 in 2D; n_ecol = Nx Ny; each part rounded up to 32), and
+ * a larger mesh is rejected with FNPF_EINVAL before any work is enqueued.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (each call rewrites what it reads); calls that overlap on
+ * the GPU race on it.  Errors: EINVAL, EUNSUPPORTED (not FNPF_BOX), ECUDA;
+ * the message is available from fnpf_last_error(NULL). */
+fnpf_status fnpf_apply_noalloc(const fnpf_mesh_desc* desc, const double* h, const double* eta, const double* x,
+                               double* y, void* stream);
+
 /* Instrumentation (tracing): when enabled, every operator application issued
  * by a solve is bracketed by CUDA events on the solve's stream, and the
  * elapsed device time and count are accumulated.  The launch counter counts

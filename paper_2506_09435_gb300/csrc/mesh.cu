@@ -141,6 +141,10 @@ void free_mesh(fnpf_mesh* m) {
 }
 }  // namespace
 
+namespace fnpf {
+void set_create_error(const char* msg) { g_create_error = msg; }
+}  // namespace fnpf
+
 extern "C" {
 
 fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t* n_surf) {

@@ -63,6 +63,7 @@ def load():
         "fnpf_dtn": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_zakharov_rhs": [vp, vp, vp, vp, vp, vp, vp],
         "fnpf_rk4_step": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(SolveInfo), vp],
+        "fnpf_apply_noalloc": [ctypes.POINTER(MeshDesc), vp, vp, vp, vp, vp],
         "fnpf_profile_enable": [vp, ctypes.c_int],
         "fnpf_profile_read": [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p, ctypes.c_int],
     }
@@ -141,6 +142,16 @@ def count_dofs(dim, nx, ny, nz, p, periodic_x=True, periodic_y=True):
     if st != FNPF_OK:
         raise FnpfError(st, "bad descriptor")
     return nv.value, ns.value
+
+
+def apply_noalloc(dim, nx, ny, nz, p, periodic_x, periodic_y, Lx, Ly, h, eta, x, y, stream=None):
+    """y = A(eta) x for a box mesh without any device allocation (fnpf_apply_noalloc);
+    h, eta, x, y are CUDA tensors."""
+    d = MeshDesc(dim=dim, nx=nx, ny=ny, nz=nz, p=p, periodic_x=int(periodic_x), periodic_y=int(periodic_y),
+                 horiz_kind=FNPF_BOX, Lx=Lx, Ly=Ly, g=9.81)
+    st = _LIB.fnpf_apply_noalloc(ctypes.byref(d), _ptr(h), _ptr(eta), _ptr(x), _ptr(y), _stream(stream))
+    if st != FNPF_OK:
+        raise FnpfError(st, _LIB.fnpf_last_error(None).decode())
 
 
 class Mesh:
