@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=32)
+    ap.add_argument("--mode", default="step", choices=["step", "apply"],
+                    help="step: RK4 steps (the benchmark); apply: operator applications only")
+    ap.add_argument("--p", type=int, default=6)
+    ap.add_argument("--nz", type=int, default=2)
     return ap.parse_args()
 
 
@@ -320,10 +324,57 @@ def main_gb300(args):
     return 0
 
 
+def main_apply(args):
+    """Laplacian applications per second on an nx x nx x nz periodic box of
+    order p (FP64 operator, fnpf_apply), L2 flushed before every timed
+    application; used for the operator roofline and its ncu captures."""
+    import numpy as np
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    from paper_2506_09435_gb300 import workloads as W
+
+    d = W.periodic_box_3d(nx=args.nx, ny=args.nx, nz=args.nz, p=args.p, kh=2.0)
+    ncx = d["p"] * d["nx"]
+    mesh = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, np.full(ncx * ncx, d["h0"]),
+                     Lx=d["Lx"], Ly=d["Ly"], g=d["g"])
+    x, y = mesh.surface_coords()
+    eta0, _ = W.airy_plus_spectrum_state(d, x, y, seed=2)
+    dev = torch.device("cuda", 0)
+    eta = torch.tensor(eta0, dtype=torch.float64, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    xv = torch.randn(mesh.N, dtype=torch.float64, device=dev, generator=gen)
+    yv = torch.empty_like(xv)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        mesh.apply(eta, xv, yv)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stream = torch.cuda.current_stream()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        mesh.apply(eta, xv, yv)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    n = d["p"] + 1
+    E = d["nx"] * d["ny"] * d["nz"]
+    flops = (12 * n ** 4 + 45 * n ** 3) * E
+    print(json.dumps({"mode": "apply", "dof": mesh.N, "p": d["p"], "nx": d["nx"], "nz": d["nz"],
+                      "ms_per_apply": ms, "applies_per_s": 1e3 / ms, "tflops_alg": flops / (ms * 1e-3) / 1e12,
+                      "frac_fp64_peak": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                      "gbs_alg": (2 * 8 * mesh.N + 16 * mesh.ns) / (ms * 1e-3) / 1e9}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return main_reference(args)
+    if args.mode == "apply":
+        return main_apply(args)
     return main_gb300(args)
 
 
