@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--nx", type=int, default=32)
     ap.add_argument("--mode", default="step", choices=["step", "apply"],
                     help="step: RK4 steps (the benchmark); apply: operator applications only")
@@ -231,6 +232,7 @@ def main_gb300(args):
         barrier()
         wall = time.perf_counter() - wall0
     launches = mesh.profile_read(reset=True)["launches"]
+    eta64_end, phi64_end = eta.clone(), phis.clone()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if dist is not None:
@@ -242,6 +244,60 @@ def main_gb300(args):
     rel_res = max(i["rel_res"] for inf in infos for i in inf)
     assert all(i["status"] == 0 for inf in infos for i in inf)
     assert torch.isfinite(eta).all() and torch.isfinite(phis).all()
+
+    # --- mixed precision on the same workload from the same initial state: FP32 operator and
+    #     inner Jacobi-PCG, FP64 defect correction to the same rtol; error vs the FP64 path
+    mixed = None
+    if not args.no_mixed:
+        mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000)
+        mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
+                       opts=mopts)
+        em = torch.tensor(eta0, dtype=torch.float64, device=dev)
+        pm = torch.tensor(phi0, dtype=torch.float64, device=dev)
+        tm = 0.0
+        for _ in range(args.warmup):
+            mm.rk4_step(em, pm, tm, dt)
+            tm += dt
+        torch.cuda.synchronize()
+        mm.profile_read(reset=True)
+        mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        minfos = []
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            mev[k][0].record(stream)
+            minfos.append(mm.rk4_step(em, pm, tm, dt, info=True))
+            mev[k][1].record(stream)
+            tm += dt
+        torch.cuda.synchronize()
+        barrier()
+        mlaunch = mm.profile_read(reset=True)["launches"]
+        m_ms = sum(a.elapsed_time(b) for a, b in mev)
+        if dist is not None:
+            tt = torch.tensor([m_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            m_ms = float(tt.item())
+        err_e = float(torch.linalg.norm(em - eta64_end) / torch.linalg.norm(eta64_end))
+        err_p = float(torch.linalg.norm(pm - phi64_end) / torch.linalg.norm(phi64_end))
+        mm.profile_enable(True)
+        for _ in range(2):
+            flush.zero_()
+            mm.rk4_step(em, pm, tm, dt)
+            tm += dt
+        torch.cuda.synchronize()
+        mprof = mm.profile_read(reset=True)
+        mixed = {"value": world * mesh.N * args.steps / (m_ms * 1e-3), "unit": UNIT,
+                 "ms_per_step": m_ms / args.steps, "dtype": "f32 inner / f64 outer",
+                 "rel_l2_vs_fp64_path": {"eta": err_e, "phis": err_p},
+                 "inner_iters_per_solve_mean": statistics.mean(i["iters"] for inf in minfos for i in inf),
+                 "outer_iters_per_solve_mean": statistics.mean(i["outer_iters"] for inf in minfos for i in inf),
+                 "max_rel_res": max(i["rel_res"] for inf in minfos for i in inf),
+                 "fp32_apply_ms": mprof["apply32_ms"] / max(1, mprof["apply32_count"]),
+                 "gpu_launches": mlaunch}
+        assert all(i["status"] == 0 for inf in minfos for i in inf)
+        del mm
 
     # --- dominant kernel: the operator application inside the solves, timed live with
     #     CUDA events on the solve's stream over a further 3 RK4 steps
@@ -313,6 +369,7 @@ def main_gb300(args):
                        "cg_iters_per_solve_mean": statistics.mean(iters), "max_rel_res": rel_res,
                        "wall_s": wall},
             "roofline": roofline,
+            "mixed": mixed,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

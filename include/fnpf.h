@@ -123,6 +123,10 @@ fnpf_status fnpf_surface_coords(const fnpf_mesh* mesh, double* x, double* y);
  * x and y must not overlap. */
 fnpf_status fnpf_apply(fnpf_mesh* mesh, const double* eta, const double* x, double* y, void* stream);
 
+/* The FP32 operator of the FNPF_MIXED inner solves (FP32 tables, geometry and
+ * contractions): y = A32(eta) x with eta [Ns], x, y [N] float. */
+fnpf_status fnpf_apply_f32(fnpf_mesh* mesh, const float* eta, const float* x, float* y, void* stream);
+
 /* d = diag(A(eta)) [N] (Jacobi preconditioner of the Laplace solve). */
 fnpf_status fnpf_diagonal(fnpf_mesh* mesh, const double* eta, double* d, void* stream);
 
@@ -182,6 +186,9 @@ fnpf_status fnpf_apply_noalloc(const fnpf_mesh_desc* desc, const double* h, cons
 fnpf_status fnpf_profile_enable(fnpf_mesh* mesh, int on);
 fnpf_status fnpf_profile_read(fnpf_mesh* mesh, double* apply_ms, int64_t* apply_count, int64_t* kernel_launches,
                               int reset);
+/* The same totals for the FP32 operator applications of FNPF_MIXED solves
+ * (fnpf_profile_read above reports the FP64 ones; its reset clears both). */
+fnpf_status fnpf_profile_read_fp32(fnpf_mesh* mesh, double* apply_ms, int64_t* apply_count);
 
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */

@@ -38,6 +38,14 @@ fnpf_status fnpf_apply(fnpf_mesh* m, const double* eta, const double* x, double*
   return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "apply");
 }
 
+fnpf_status fnpf_apply_f32(fnpf_mesh* m, const float* eta, const float* x, float* y, void* stream) {
+  if (!m || !eta || !x || !y) return FNPF_EINVAL;
+  const Geom& g = m->g;
+  cudaError_t e = fnpf::launch_apply<float>(g, m->tables32(), eta, x, x + g.NI, y, y + g.NI,
+                                            reinterpret_cast<float*>(m->ring), m->variant, (cudaStream_t)stream);
+  return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "apply_f32");
+}
+
 fnpf_status fnpf_diagonal(fnpf_mesh* m, const double* eta, double* d, void* stream) {
   if (!m || !eta || !d) return FNPF_EINVAL;
   const Geom& g = m->g;
@@ -118,6 +126,7 @@ fnpf_status fnpf_profile_enable(fnpf_mesh* m, int on) {
     const int pairs = std::max(64, m->opts.check_every + 8);
     m->prof_ev.resize(2 * pairs);
     m->prof_it.assign(pairs, -1);
+    m->prof_fp32.assign(pairs, 0);
     for (auto& e : m->prof_ev) {
       cudaError_t r = cudaEventCreate(&e);
       if (r != cudaSuccess) return cuda_fail(m, r, "profile events");
@@ -136,8 +145,17 @@ fnpf_status fnpf_profile_read(fnpf_mesh* m, double* apply_ms, int64_t* apply_cou
   if (reset) {
     m->prof_ms = 0;
     m->prof_count = 0;
+    m->prof_ms32 = 0;
+    m->prof_count32 = 0;
     m->launches = 0;
   }
+  return FNPF_OK;
+}
+
+fnpf_status fnpf_profile_read_fp32(fnpf_mesh* m, double* apply_ms, int64_t* apply_count) {
+  if (!m) return FNPF_EINVAL;
+  if (apply_ms) *apply_ms = m->prof_ms32;
+  if (apply_count) *apply_count = m->prof_count32;
   return FNPF_OK;
 }
 

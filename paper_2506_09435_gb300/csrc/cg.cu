@@ -1,6 +1,13 @@
-// Jacobi-preconditioned conjugate gradients for the Dirichlet-Neumann Laplace
-// problem A_II phi_I = -A_IS phi_eta (arXiv 2506.09435, Sec. 3.4 Steps 4.2-4.3;
-// the paper uses CG with algebraic multigrid, Sec. 4 solver settings).
+// Preconditioned conjugate gradients for the Dirichlet-Neumann Laplace problem
+// A_II phi_I = -A_IS phi_eta (arXiv 2506.09435, Sec. 3.4 Steps 4.2-4.3; the
+// paper uses CG with algebraic multigrid, Sec. 4 solver settings), in two forms:
+//
+//  * FNPF_FP64: CG on the FP64 operator with Jacobi preconditioning;
+//  * FNPF_MIXED: FP64 defect correction around FP32 inner solves -- the outer
+//    residual r = b - A64 x is formed with the FP64 operator, the correction
+//    e ~ A32^-1 r comes from Jacobi-PCG on the FP32 operator (FP32 geometry
+//    and vectors, FP64 dot products), x += e in FP64, until
+//    ||b - A64 x|| <= rtol ||b||.
 //
 // Reductions are deterministic: each block of a vector kernel writes one FP64
 // partial sum; every consumer block re-reduces all partials in the same fixed
@@ -36,24 +43,31 @@ __device__ double reduce_partials(const double* part, int nb, double* sh) {
   return block_sum(v, sh);
 }
 
-__global__ void __launch_bounds__(NT) invert_kernel(int64_t n, double* d) {
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) d[i] = 1.0 / d[i];
+#define GRID_LOOP(i, n) for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < (n); i += (int64_t)gridDim.x * NT)
+
+template <typename T>
+__global__ void __launch_bounds__(NT) invert_kernel(int64_t n, T* d) {
+  GRID_LOOP(i, n) d[i] = T(1) / d[i];
 }
 
+// b = -y (y = A [0; phis]_I), r = b - q (q = A x), z = dinv r, p = z; partials bb, rz, rr.
 __global__ void __launch_bounds__(NT) cg_init_kernel(int64_t n, double* r, const double* q, const double* dinv,
-                                                     double* z, double* p, double* part, int nb) {
+                                                     double* z, double* p, double* b_out, double* part, int nb) {
   __shared__ double sh[NT / 32];
   double sbb = 0, srz = 0, srr = 0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+  GRID_LOOP(i, n) {
     const double b = -r[i];
     const double rn = b - q[i];
-    const double zz = dinv[i] * rn;
+    if (b_out) b_out[i] = b;
     r[i] = rn;
-    z[i] = zz;
-    p[i] = zz;
     sbb += b * b;
-    srz += rn * zz;
     srr += rn * rn;
+    if (dinv) {
+      const double zz = dinv[i] * rn;
+      z[i] = zz;
+      p[i] = zz;
+      srz += rn * zz;
+    }
   }
   sbb = block_sum(sbb, sh);
   srz = block_sum(srz, sh);
@@ -65,6 +79,7 @@ __global__ void __launch_bounds__(NT) cg_init_kernel(int64_t n, double* r, const
   }
 }
 
+// Sets bb, rz[0], rr, tol2 from the partials; done if already converged.
 __global__ void __launch_bounds__(NT) cg_init_finish_kernel(CgScalars* sc, const double* part, int nb, double rtol2,
                                                             double atol2) {
   __shared__ double sh[NT / 32];
@@ -88,19 +103,60 @@ __global__ void __launch_bounds__(NT) cg_init_finish_kernel(CgScalars* sc, const
   }
 }
 
-__global__ void __launch_bounds__(NT) cg_dot_kernel(const CgScalars* sc, int64_t n, const double* p, const double* q,
+// Inner (FP32) solve start from the FP64 residual: r32 = r64, e = 0, z = dinv r,
+// p = z; partials rz, rr (FP64).
+__global__ void __launch_bounds__(NT) inner_init_kernel(int64_t n, const double* r64, float* r, float* e, float* z,
+                                                        float* p, const float* dinv, double* part, int nb) {
+  __shared__ double sh[NT / 32];
+  double srz = 0, srr = 0;
+  GRID_LOOP(i, n) {
+    const float rn = (float)r64[i];
+    const float zz = dinv[i] * rn;
+    r[i] = rn;
+    e[i] = 0.0f;
+    z[i] = zz;
+    p[i] = zz;
+    srz += (double)rn * (double)zz;
+    srr += (double)rn * (double)rn;
+  }
+  srz = block_sum(srz, sh);
+  srr = block_sum(srr, sh);
+  if (threadIdx.x == 0) {
+    part[1 * nb + blockIdx.x] = srz;
+    part[2 * nb + blockIdx.x] = srr;
+  }
+}
+
+__global__ void __launch_bounds__(NT) inner_init_finish_kernel(CgScalars* sc, const double* part, int nb,
+                                                               double rtol2) {
+  __shared__ double sh[NT / 32];
+  const double rz = reduce_partials(part + nb, nb, sh);
+  const double rr = reduce_partials(part + 2 * nb, nb, sh);
+  if (threadIdx.x == 0) {
+    sc->bb = rr;
+    sc->rz[0] = rz;
+    sc->rr = rr;
+    sc->iters = 0;
+    sc->tol2 = rtol2 * rr;
+    sc->done = (rr == 0.0 || !isfinite(rr)) ? 1 : 0;
+    if (!isfinite(rr)) sc->status = FNPF_EDIVERGED;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) cg_dot_kernel(const CgScalars* sc, int64_t n, const T* p, const T* q,
                                                     double* part) {
   if (sc->done) return;
   __shared__ double sh[NT / 32];
   double s = 0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) s += p[i] * q[i];
+  GRID_LOOP(i, n) s += (double)p[i] * (double)q[i];
   s = block_sum(s, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(NT) cg_update_kernel(CgScalars* sc, int it, int64_t n, double* x, double* r,
-                                                       double* z, const double* p, const double* q,
-                                                       const double* dinv, double* part, int nb) {
+template <typename T>
+__global__ void __launch_bounds__(NT) cg_update_kernel(CgScalars* sc, int it, int64_t n, T* x, T* r, T* z,
+                                                       const T* p, const T* q, const T* dinv, double* part, int nb) {
   if (sc->done) return;
   __shared__ double sh[NT / 32];
   const double pq = reduce_partials(part + 3 * nb, nb, sh);
@@ -112,16 +168,16 @@ __global__ void __launch_bounds__(NT) cg_update_kernel(CgScalars* sc, int it, in
     }
     return;
   }
-  const double alpha = rz / pq;
+  const T alpha = (T)(rz / pq);
   double srz = 0, srr = 0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+  GRID_LOOP(i, n) {
     x[i] += alpha * p[i];
-    const double rn = r[i] - alpha * q[i];
-    const double zz = dinv[i] * rn;
+    const T rn = r[i] - alpha * q[i];
+    const T zz = dinv[i] * rn;
     r[i] = rn;
     z[i] = zz;
-    srz += rn * zz;
-    srr += rn * rn;
+    srz += (double)rn * (double)zz;
+    srr += (double)rn * (double)rn;
   }
   srz = block_sum(srz, sh);
   srr = block_sum(srr, sh);
@@ -131,15 +187,15 @@ __global__ void __launch_bounds__(NT) cg_update_kernel(CgScalars* sc, int it, in
   }
 }
 
-__global__ void __launch_bounds__(NT) cg_pupdate_kernel(CgScalars* sc, int it, int64_t n, const double* z, double* p,
+template <typename T>
+__global__ void __launch_bounds__(NT) cg_pupdate_kernel(CgScalars* sc, int it, int64_t n, const T* z, T* p,
                                                         const double* part, int nb) {
   if (sc->done) return;
   __shared__ double sh[NT / 32];
   const double rz_new = reduce_partials(part + nb, nb, sh);
   const double rr = reduce_partials(part + 2 * nb, nb, sh);
-  const double beta = rz_new / sc->rz[it & 1];
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
-    p[i] = z[i] + beta * p[i];
+  const T beta = (T)(rz_new / sc->rz[it & 1]);
+  GRID_LOOP(i, n) p[i] = z[i] + beta * p[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     sc->rz[(it + 1) & 1] = rz_new;
     sc->rr = rr;
@@ -153,25 +209,64 @@ __global__ void __launch_bounds__(NT) cg_pupdate_kernel(CgScalars* sc, int it, i
   }
 }
 
-// Operator application bracketed by profiling events when enabled.
-// `it` is the CG iteration the application belongs to (-1: set-up); applications
+// x += e (FP64 += FP32); the outer residual r = b - q follows q = A64 x.
+__global__ void __launch_bounds__(NT) add_correction_kernel(int64_t n, double* x, const float* e) {
+  GRID_LOOP(i, n) x[i] += (double)e[i];
+}
+
+__global__ void __launch_bounds__(NT) outer_residual_kernel(int64_t n, const double* b, const double* q, double* r,
+                                                            double* part, int nb) {
+  __shared__ double sh[NT / 32];
+  double srr = 0;
+  GRID_LOOP(i, n) {
+    const double rn = b[i] - q[i];
+    r[i] = rn;
+    srr += rn * rn;
+  }
+  srr = block_sum(srr, sh);
+  if (threadIdx.x == 0) part[2 * nb + blockIdx.x] = srr;
+}
+
+__global__ void __launch_bounds__(NT) outer_finish_kernel(CgScalars* sc, const double* part, int nb) {
+  __shared__ double sh[NT / 32];
+  const double rr = reduce_partials(part + 2 * nb, nb, sh);
+  if (threadIdx.x == 0) {
+    sc->rr = rr;
+    if (!isfinite(rr)) {
+      sc->status = FNPF_EDIVERGED;
+      sc->done = 1;
+    } else if (rr <= sc->tol2) {
+      sc->done = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT) to_float_kernel(int64_t n, const double* a, float* b) {
+  GRID_LOOP(i, n) b[i] = (float)a[i];
+}
+
+inline int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kVecBlocks, (n + NT - 1) / NT)); }
+
+// Operator application bracketed by profiling events when enabled.  `it` is the
+// CG iteration the application belongs to (-1: outside the loop); applications
 // of iterations that turn out to follow convergence exit at once and are not
 // counted.
-cudaError_t timed_apply(fnpf_mesh* m, const double* eta, const double* xI, const double* xs, double* yI,
+template <typename T>
+cudaError_t timed_apply(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T* xI, const T* xs, T* yI,
                         cudaStream_t s, const int* skip, int it) {
   const bool rec = m->prof_on && m->prof_used * 2 + 1 < (int)m->prof_ev.size();
   if (rec) cudaEventRecord(m->prof_ev[2 * m->prof_used], s);
-  cudaError_t e = launch_apply<double>(m->g, m->tables(), eta, xI, xs, yI, nullptr, m->ring, m->variant, s, skip);
+  cudaError_t e = launch_apply<T>(m->g, t, eta, xI, xs, yI, nullptr, reinterpret_cast<T*>(m->ring), m->variant, s,
+                                  skip);
   if (rec) {
     cudaEventRecord(m->prof_ev[2 * m->prof_used + 1], s);
     m->prof_it[m->prof_used] = it;
+    m->prof_fp32[m->prof_used] = sizeof(T) == 4 ? 1 : 0;
     ++m->prof_used;
   }
   m->launches += 2;
   return e;
 }
-
-inline int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kVecBlocks, (n + NT - 1) / NT)); }
 
 }  // namespace
 
@@ -180,63 +275,75 @@ void prof_collect(fnpf_mesh* m, int iters_done) {
     if (m->prof_it[k] >= iters_done) continue;
     float ms = 0;
     if (cudaEventElapsedTime(&ms, m->prof_ev[2 * k], m->prof_ev[2 * k + 1]) == cudaSuccess) {
-      m->prof_ms += ms;
-      ++m->prof_count;
+      if (m->prof_fp32[k]) {
+        m->prof_ms32 += ms;
+        ++m->prof_count32;
+      } else {
+        m->prof_ms += ms;
+        ++m->prof_count;
+      }
     }
   }
   m->prof_used = 0;
 }
 
-#define FNPF_CK(call)                                  \
-  do {                                                 \
-    cudaError_t e_ = (call);                           \
-    if (e_ != cudaSuccess) {                           \
+#define FNPF_CK(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
       m->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
-      return FNPF_ECUDA;                               \
-    }                                                  \
+      return FNPF_ECUDA;                                           \
+    }                                                              \
   } while (0)
 
-fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,
-                     cudaStream_t s) {
-  const Geom& g = m->g;
-  const Tables<double> t = m->tables();
-  const int64_t NI = g.NI;
+namespace {
+
+// Buffers of one PCG iteration loop in precision T.
+template <typename T>
+struct PcgBufs {
+  const T* eta;
+  T* x;
+  T* r;
+  T* z;
+  T* p;
+  T* q;
+  const T* dinv;
+  CgScalars* sc;
+};
+
+// Runs Jacobi-PCG iterations until the device flag is set or max_iter is reached;
+// the scalars must have been initialised.  Returns the host copy of the scalars
+// in *out and whether the loop converged.
+template <typename T>
+fnpf_status pcg_loop(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>& B, int max_iter, cudaStream_t s,
+                     CgScalars* out, bool* done) {
+  const int64_t NI = m->g.NI;
   const int nb = vec_blocks(NI);
-  CgScalars* sc = m->sc;
-  if (info) FNPF_CK(cudaEventRecord(m->ev0, s));
-  FNPF_CK(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
-  FNPF_CK(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
-  FNPF_CK(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
-  invert_kernel<<<nb, NT, 0, s>>>(NI, m->dinv);
-  FNPF_CK(cudaGetLastError());
-  FNPF_CK(timed_apply(m, eta, nullptr, phis, m->r, s, nullptr, -1));
-  FNPF_CK(timed_apply(m, eta, x, nullptr, m->q, s, nullptr, -1));
-  cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, m->dinv, m->z, m->p, m->partials, nb);
-  cg_init_finish_kernel<<<1, NT, 0, s>>>(sc, m->partials, nb, m->opts.rtol * m->opts.rtol,
-                                         m->opts.atol * m->opts.atol);
-  FNPF_CK(cudaGetLastError());
-  m->launches += 6;   // check, diagonal + gather, invert, init, init-finish
-  const int max_iter = std::max(0, m->opts.max_iter);
   const int every = std::max(1, m->opts.check_every);
   int it = 0;
-  bool done = false;
+  *done = false;
   while (true) {
-    FNPF_CK(cudaMemcpyAsync(m->sc_host, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    FNPF_CK(cudaMemcpyAsync(m->sc_host, B.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     FNPF_CK(cudaStreamSynchronize(s));
     prof_collect(m, m->sc_host->done ? m->sc_host->iters : it);
-    done = m->sc_host->done != 0;
-    if (done || it >= max_iter) break;
+    *done = m->sc_host->done != 0;
+    if (*done || it >= max_iter) break;
     const int chunk = std::min(every, max_iter - it);
     for (int k = 0; k < chunk; ++k, ++it) {
-      FNPF_CK(timed_apply(m, eta, m->p, nullptr, m->q, s, &sc->done, it));
+      FNPF_CK(timed_apply<T>(m, t, B.eta, B.p, nullptr, B.q, s, &B.sc->done, it));
+      cg_dot_kernel<T><<<nb, NT, 0, s>>>(B.sc, NI, B.p, B.q, m->partials + 3 * nb);
+      cg_update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, B.dinv, m->partials, nb);
+      cg_pupdate_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.z, B.p, m->partials, nb);
       m->launches += 3;
-      cg_dot_kernel<<<nb, NT, 0, s>>>(sc, NI, m->p, m->q, m->partials + 3 * nb);
-      cg_update_kernel<<<nb, NT, 0, s>>>(sc, it, NI, x, m->r, m->z, m->p, m->q, m->dinv, m->partials, nb);
-      cg_pupdate_kernel<<<nb, NT, 0, s>>>(sc, it, NI, m->z, m->p, m->partials, nb);
     }
     FNPF_CK(cudaGetLastError());
   }
-  const CgScalars& h = *m->sc_host;
+  *out = *m->sc_host;
+  return FNPF_OK;
+}
+
+fnpf_status finish(fnpf_mesh* m, const CgScalars& h, bool done, int iters, int outer, fnpf_solve_info* info,
+                   cudaStream_t s) {
   fnpf_status st = FNPF_OK;
   if (h.status != 0) st = (fnpf_status)h.status;
   else if (!done) st = FNPF_ENOCONV;
@@ -245,16 +352,99 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double
     FNPF_CK(cudaEventSynchronize(m->ev1));
     float ms = 0;
     cudaEventElapsedTime(&ms, m->ev0, m->ev1);
-    info->iters = h.iters;
-    info->outer_iters = 0;
+    info->iters = iters;
+    info->outer_iters = outer;
     info->rel_res = h.bb > 0 ? sqrt(h.rr / h.bb) : 0.0;
     info->status = st;
     info->ms = ms;
   }
-  if (st == FNPF_ENOCONV) m->err = "CG reached max_iter before the tolerance";
+  if (st == FNPF_ENOCONV) m->err = "solver reached its iteration cap before the tolerance";
   else if (st == FNPF_EBREAKDOWN) m->err = "CG breakdown (p^T A p <= 0 or non-finite)";
   else if (st == FNPF_EDIVERGED) m->err = "non-finite state or eta + h <= 0";
   return st;
+}
+
+}  // namespace
+
+fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,
+                     cudaStream_t s) {
+  const Geom& g = m->g;
+  const Tables<double> t = m->tables();
+  const int64_t NI = g.NI;
+  const int nb = vec_blocks(NI);
+  CgScalars* sc = m->sc;
+  const bool mixed = m->opts.precision == FNPF_MIXED;
+  if (info) FNPF_CK(cudaEventRecord(m->ev0, s));
+  FNPF_CK(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
+  FNPF_CK(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
+  if (!mixed) {
+    FNPF_CK(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
+    invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
+  }
+  FNPF_CK(cudaGetLastError());
+  // lift: r = A [0; phis]_I = -b; q = A [x; 0]_I; then b, r = b - q (, z, p)
+  FNPF_CK(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
+  FNPF_CK(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
+  cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, mixed ? nullptr : m->dinv, m->z, m->p, mixed ? m->b : nullptr,
+                                   m->partials, nb);
+  cg_init_finish_kernel<<<1, NT, 0, s>>>(sc, m->partials, nb, m->opts.rtol * m->opts.rtol,
+                                         m->opts.atol * m->opts.atol);
+  FNPF_CK(cudaGetLastError());
+  m->launches += 4 + (mixed ? 0 : 3);
+  const int max_iter = std::max(0, m->opts.max_iter);
+  CgScalars h{};
+  bool done = false;
+  if (!mixed) {
+    PcgBufs<double> B{eta, x, m->r, m->z, m->p, m->q, m->dinv, sc};
+    fnpf_status st = pcg_loop<double>(m, t, B, max_iter, s, &h, &done);
+    if (st != FNPF_OK) return st;
+    return finish(m, h, done, h.iters, 0, info, s);
+  }
+
+  // ---- mixed precision: FP64 defect correction around FP32 Jacobi-PCG
+  const Tables<float> t32 = m->tables32();
+  to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+  FNPF_CK(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
+  invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+  FNPF_CK(cudaGetLastError());
+  m->launches += 4;
+  int inner_total = 0, outer = 0;
+  const int max_outer = std::max(1, m->opts.max_outer);
+  const double in_rtol2 = m->opts.inner_rtol * m->opts.inner_rtol;
+  while (true) {
+    FNPF_CK(cudaMemcpyAsync(m->sc_host, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    FNPF_CK(cudaStreamSynchronize(s));
+    prof_collect(m, 1 << 30);
+    h = *m->sc_host;
+    done = h.done != 0;
+    if (done || outer >= max_outer || inner_total >= max_iter) break;
+    // inner solve A32 e = r (FP32, Jacobi-PCG, relative tolerance inner_rtol)
+    CgScalars* si = m->sc_in;
+    FNPF_CK(cudaMemsetAsync(si, 0, sizeof(CgScalars), s));
+    inner_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->r32, m->e32, m->z32, m->p32, m->dinv32, m->partials, nb);
+    inner_init_finish_kernel<<<1, NT, 0, s>>>(si, m->partials, nb, in_rtol2);
+    FNPF_CK(cudaGetLastError());
+    m->launches += 2;
+    PcgBufs<float> B{m->eta32, m->e32, m->r32, m->z32, m->p32, m->q32, m->dinv32, si};
+    CgScalars hi{};
+    bool idone = false;
+    fnpf_status st = pcg_loop<float>(m, t32, B, max_iter - inner_total, s, &hi, &idone);
+    if (st != FNPF_OK) return st;
+    inner_total += hi.iters;
+    if (hi.status == FNPF_EBREAKDOWN || hi.status == FNPF_EDIVERGED) {
+      h.status = hi.status;
+      break;
+    }
+    // x += e; r = b - A64 x
+    add_correction_kernel<<<nb, NT, 0, s>>>(NI, x, m->e32);
+    FNPF_CK(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
+    outer_residual_kernel<<<nb, NT, 0, s>>>(NI, m->b, m->q, m->r, m->partials, nb);
+    outer_finish_kernel<<<1, NT, 0, s>>>(sc, m->partials, nb);
+    FNPF_CK(cudaGetLastError());
+    m->launches += 3;
+    ++outer;
+  }
+  return finish(m, h, done, inner_total, outer, info, s);
 }
 
 }  // namespace fnpf

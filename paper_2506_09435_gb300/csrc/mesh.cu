@@ -131,6 +131,12 @@ void free_mesh(fnpf_mesh* m) {
                     m->acc_phi};
   for (double* p : ptrs)
     if (p) cudaFree(p);
+  float* fptrs[] = {m->fD, m->fxi, m->fw, m->fhm, m->fh, m->eta32, m->r32, m->z32, m->p32, m->q32, m->e32,
+                    m->dinv32};
+  for (float* p : fptrs)
+    if (p) cudaFree(p);
+  if (m->b) cudaFree(m->b);
+  if (m->sc_in) cudaFree(m->sc_in);
   if (m->sc) cudaFree(m->sc);
   if (m->sc_host) cudaFreeHost(m->sc_host);
   if (m->ev0) cudaEventDestroy(m->ev0);
@@ -305,6 +311,23 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   }
   A(&m->acc_eta, g.ns);
   A(&m->acc_phi, g.ns);
+  A(&m->b, g.NI);
+  auto AF = [&](float** ptr, size_t cnt) {
+    if (e == cudaSuccess) e = dalloc(ptr, cnt);
+  };
+  AF(&m->fD, n * n);
+  AF(&m->fxi, n);
+  AF(&m->fw, n);
+  AF(&m->fhm, 5 * HS);
+  AF(&m->fh, g.ns);
+  AF(&m->eta32, g.ns);
+  AF(&m->r32, g.NI);
+  AF(&m->z32, g.NI);
+  AF(&m->p32, g.NI);
+  AF(&m->q32, g.NI);
+  AF(&m->e32, g.NI);
+  AF(&m->dinv32, g.NI);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->sc_in, sizeof(fnpf::CgScalars));
   if (e == cudaSuccess) e = cudaMalloc((void**)&m->sc, sizeof(fnpf::CgScalars));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->sc_host, sizeof(fnpf::CgScalars));
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
@@ -316,6 +339,17 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   if (e == cudaSuccess) e = cudaMemcpy(m->dh, m->h.data(), g.ns * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->dminv, m->minv.data(), g.ns * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->phi, 0, g.N * sizeof(double));
+  {
+    auto up32 = [&](float* dst, const std::vector<double>& src) {
+      std::vector<float> f(src.begin(), src.end());
+      if (e == cudaSuccess) e = cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+    };
+    up32(m->fD, m->D);
+    up32(m->fxi, m->xi);
+    up32(m->fw, m->w);
+    up32(m->fhm, m->hm);
+    up32(m->fh, m->h);
+  }
   if (e != cudaSuccess) {
     g_create_error = std::string("device set-up failed: ") + cudaGetErrorString(e);
     const fnpf_status ret = (e == cudaErrorMemoryAllocation) ? FNPF_ENOMEM : FNPF_ECUDA;

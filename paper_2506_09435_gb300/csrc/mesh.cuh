@@ -42,18 +42,38 @@ struct fnpf_mesh {
   double* s_phi[2] = {nullptr, nullptr};
   double* acc_eta = nullptr;
   double* acc_phi = nullptr;
+
+  // mixed precision: FP32 tables and inner-solve vectors, FP64 right-hand side
+  float* fD = nullptr;
+  float* fxi = nullptr;
+  float* fw = nullptr;
+  float* fhm = nullptr;
+  float* fh = nullptr;
+  float* eta32 = nullptr;           // ns
+  float* r32 = nullptr;             // NI each
+  float* z32 = nullptr;
+  float* p32 = nullptr;
+  float* q32 = nullptr;
+  float* e32 = nullptr;
+  float* dinv32 = nullptr;
+  double* b = nullptr;              // NI: lifted right-hand side
+  fnpf::CgScalars* sc_in = nullptr; // inner-solve scalars
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   // instrumentation
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop) of operator applications
   std::vector<int> prof_it;          // CG iteration of each recorded pair
+  std::vector<char> prof_fp32;       // pair timed an FP32 application
+  double prof_ms32 = 0.0;
+  int64_t prof_count32 = 0;
   int prof_used = 0;                 // pairs recorded since the last host sync
   double prof_ms = 0.0;
   int64_t prof_count = 0;
   int64_t launches = 0;
 
   fnpf::Tables<double> tables() const { return fnpf::Tables<double>{dD, dxi, dw, dhm, dh, dminv}; }
+  fnpf::Tables<float> tables32() const { return fnpf::Tables<float>{fD, fxi, fw, fhm, fh, nullptr}; }
 };
 
 namespace fnpf {

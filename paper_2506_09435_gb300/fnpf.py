@@ -59,6 +59,7 @@ def load():
         "fnpf_surface_coords": [vp, _dp, _dp],
         "fnpf_apply": [vp, vp, vp, vp, vp],
         "fnpf_diagonal": [vp, vp, vp, vp],
+        "fnpf_apply_f32": [vp, vp, vp, vp, vp],
         "fnpf_laplace_solve": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_dtn": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_zakharov_rhs": [vp, vp, vp, vp, vp, vp, vp],
@@ -66,6 +67,7 @@ def load():
         "fnpf_apply_noalloc": [ctypes.POINTER(MeshDesc), vp, vp, vp, vp, vp],
         "fnpf_profile_enable": [vp, ctypes.c_int],
         "fnpf_profile_read": [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p, ctypes.c_int],
+        "fnpf_profile_read_fp32": [vp, ctypes.POINTER(ctypes.c_double), i64p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -198,6 +200,9 @@ class Mesh:
     def apply(self, eta, x, y, stream=None):
         self._check(_LIB.fnpf_apply(self._h, _ptr(eta), _ptr(x), _ptr(y), _stream(stream)))
 
+    def apply_f32(self, eta, x, y, stream=None):
+        self._check(_LIB.fnpf_apply_f32(self._h, _ptr(eta), _ptr(x), _ptr(y), _stream(stream)))
+
     def diagonal(self, eta, d, stream=None):
         self._check(_LIB.fnpf_diagonal(self._h, _ptr(eta), _ptr(d), _stream(stream)))
 
@@ -226,9 +231,12 @@ class Mesh:
 
     def profile_read(self, reset=False):
         ms, cnt, launches = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        ms32, cnt32 = ctypes.c_double(), ctypes.c_int64()
+        self._check(_LIB.fnpf_profile_read_fp32(self._h, ctypes.byref(ms32), ctypes.byref(cnt32)))
         self._check(_LIB.fnpf_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(launches),
                                            int(reset)))
-        return dict(apply_ms=ms.value, apply_count=cnt.value, launches=launches.value)
+        return dict(apply_ms=ms.value, apply_count=cnt.value, launches=launches.value, apply32_ms=ms32.value,
+                    apply32_count=cnt32.value)
 
     def rk4_step(self, eta, phis, t, dt, stream=None, info=False, check=True):
         infos = (SolveInfo * 4)() if info else None
