@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--precond", default="pmg", choices=["pmg", "jacobi"])
+    ap.add_argument("--cheb-degree", type=int, default=3)
+    ap.add_argument("--coarse-degree", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--nx", type=int, default=32)
@@ -195,7 +198,9 @@ def main_gb300(args):
 
     d = workload(args.nx)
     h = None
-    opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000)
+    pre = fnpf.FNPF_PMG if args.precond == "pmg" else fnpf.FNPF_JACOBI
+    opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000, precond=pre, cheb_degree=args.cheb_degree,
+                             coarse_iters=args.coarse_degree)
     ncx = d["p"] * d["nx"]
     h = np.full(ncx * ncx, d["h0"])
     mesh = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
@@ -249,7 +254,8 @@ def main_gb300(args):
     #     inner Jacobi-PCG, FP64 defect correction to the same rtol; error vs the FP64 path
     mixed = None
     if not args.no_mixed:
-        mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000)
+        mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
+                                  precond=pre, cheb_degree=args.cheb_degree, coarse_iters=args.coarse_degree)
         mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
                        opts=mopts)
         em = torch.tensor(eta0, dtype=torch.float64, device=dev)
@@ -364,7 +370,7 @@ def main_gb300(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": mesh.N, "surface_dof": mesh.ns, "precision": "fp64",
-                       "precond": "jacobi", "l2": "flushed before every timed step (256 MB write, untimed)",
+                       "precond": args.precond, "l2": "flushed before every timed step (256 MB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "cg_iters_per_solve_mean": statistics.mean(iters), "max_rel_res": rel_res,
                        "wall_s": wall},

@@ -2,11 +2,12 @@
 // A_II phi_I = -A_IS phi_eta (arXiv 2506.09435, Sec. 3.4 Steps 4.2-4.3; the
 // paper uses CG with algebraic multigrid, Sec. 4 solver settings), in two forms:
 //
-//  * FNPF_FP64: CG on the FP64 operator with Jacobi preconditioning;
+//  * FNPF_FP64: CG on the FP64 operator, preconditioned by Jacobi or by the
+//    p-multigrid V-cycle of mg.cu;
 //  * FNPF_MIXED: FP64 defect correction around FP32 inner solves -- the outer
 //    residual r = b - A64 x is formed with the FP64 operator, the correction
-//    e ~ A32^-1 r comes from Jacobi-PCG on the FP32 operator (FP32 geometry
-//    and vectors, FP64 dot products), x += e in FP64, until
+//    e ~ A32^-1 r comes from PCG on the FP32 operator (FP32 geometry, vectors
+//    and preconditioner, FP64 dot products), x += e in FP64, until
 //    ||b - A64 x|| <= rtol ||b||.
 //
 // Reductions are deterministic: each block of a vector kernel writes one FP64
@@ -20,35 +21,16 @@
 #include <algorithm>
 
 #include "mesh.cuh"
+#include "mg.cuh"
+#include "vec.cuh"
 
 namespace fnpf {
 namespace {
 
 constexpr int NT = kVecThreads;
-
-__device__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double s = 0;
-  for (int k = 0; k < NT / 32; ++k) s += sh[k];
-  return s;
-}
-
-__device__ double reduce_partials(const double* part, int nb, double* sh) {
-  double v = 0;
-  for (int k = threadIdx.x; k < nb; k += NT) v += part[k];
-  return block_sum(v, sh);
-}
-
-#define GRID_LOOP(i, n) for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < (n); i += (int64_t)gridDim.x * NT)
-
-template <typename T>
-__global__ void __launch_bounds__(NT) invert_kernel(int64_t n, T* d) {
-  GRID_LOOP(i, n) d[i] = T(1) / d[i];
-}
+using vec::block_sum;
+using vec::reduce_partials;
+#define GRID_LOOP(i, n) FNPF_GRID_LOOP(i, n)
 
 // b = -y (y = A [0; phis]_I), r = b - q (q = A x), z = dinv r, p = z; partials bb, rz, rr.
 __global__ void __launch_bounds__(NT) cg_init_kernel(int64_t n, double* r, const double* q, const double* dinv,
@@ -111,18 +93,20 @@ __global__ void __launch_bounds__(NT) inner_init_kernel(int64_t n, const double*
   double srz = 0, srr = 0;
   GRID_LOOP(i, n) {
     const float rn = (float)r64[i];
-    const float zz = dinv[i] * rn;
     r[i] = rn;
     e[i] = 0.0f;
-    z[i] = zz;
-    p[i] = zz;
-    srz += (double)rn * (double)zz;
     srr += (double)rn * (double)rn;
+    if (dinv) {
+      const float zz = dinv[i] * rn;
+      z[i] = zz;
+      p[i] = zz;
+      srz += (double)rn * (double)zz;
+    }
   }
   srz = block_sum(srz, sh);
   srr = block_sum(srr, sh);
   if (threadIdx.x == 0) {
-    part[1 * nb + blockIdx.x] = srz;
+    if (dinv) part[1 * nb + blockIdx.x] = srz;
     part[2 * nb + blockIdx.x] = srr;
   }
 }
@@ -140,72 +124,6 @@ __global__ void __launch_bounds__(NT) inner_init_finish_kernel(CgScalars* sc, co
     sc->tol2 = rtol2 * rr;
     sc->done = (rr == 0.0 || !isfinite(rr)) ? 1 : 0;
     if (!isfinite(rr)) sc->status = FNPF_EDIVERGED;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT) cg_dot_kernel(const CgScalars* sc, int64_t n, const T* p, const T* q,
-                                                    double* part) {
-  if (sc->done) return;
-  __shared__ double sh[NT / 32];
-  double s = 0;
-  GRID_LOOP(i, n) s += (double)p[i] * (double)q[i];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT) cg_update_kernel(CgScalars* sc, int it, int64_t n, T* x, T* r, T* z,
-                                                       const T* p, const T* q, const T* dinv, double* part, int nb) {
-  if (sc->done) return;
-  __shared__ double sh[NT / 32];
-  const double pq = reduce_partials(part + 3 * nb, nb, sh);
-  const double rz = sc->rz[it & 1];
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      sc->status = FNPF_EBREAKDOWN;
-      sc->done = 1;
-    }
-    return;
-  }
-  const T alpha = (T)(rz / pq);
-  double srz = 0, srr = 0;
-  GRID_LOOP(i, n) {
-    x[i] += alpha * p[i];
-    const T rn = r[i] - alpha * q[i];
-    const T zz = dinv[i] * rn;
-    r[i] = rn;
-    z[i] = zz;
-    srz += (double)rn * (double)zz;
-    srr += (double)rn * (double)rn;
-  }
-  srz = block_sum(srz, sh);
-  srr = block_sum(srr, sh);
-  if (threadIdx.x == 0) {
-    part[1 * nb + blockIdx.x] = srz;
-    part[2 * nb + blockIdx.x] = srr;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(NT) cg_pupdate_kernel(CgScalars* sc, int it, int64_t n, const T* z, T* p,
-                                                        const double* part, int nb) {
-  if (sc->done) return;
-  __shared__ double sh[NT / 32];
-  const double rz_new = reduce_partials(part + nb, nb, sh);
-  const double rr = reduce_partials(part + 2 * nb, nb, sh);
-  const T beta = (T)(rz_new / sc->rz[it & 1]);
-  GRID_LOOP(i, n) p[i] = z[i] + beta * p[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    sc->rz[(it + 1) & 1] = rz_new;
-    sc->rr = rr;
-    sc->iters = it + 1;
-    if (!isfinite(rr)) {
-      sc->status = FNPF_EBREAKDOWN;
-      sc->done = 1;
-    } else if (rr <= sc->tol2) {
-      sc->done = 1;
-    }
   }
 }
 
@@ -245,7 +163,7 @@ __global__ void __launch_bounds__(NT) to_float_kernel(int64_t n, const double* a
   GRID_LOOP(i, n) b[i] = (float)a[i];
 }
 
-inline int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kVecBlocks, (n + NT - 1) / NT)); }
+inline int vec_blocks(int64_t n) { return vec::blocks_for(n); }
 
 // Operator application bracketed by profiling events when enabled.  `it` is the
 // CG iteration the application belongs to (-1: outside the loop); applications
@@ -320,6 +238,7 @@ fnpf_status pcg_loop(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>& B, int 
   const int64_t NI = m->g.NI;
   const int nb = vec_blocks(NI);
   const int every = std::max(1, m->opts.check_every);
+  const bool pmg = m->opts.precond == FNPF_PMG;
   int it = 0;
   *done = false;
   while (true) {
@@ -330,15 +249,37 @@ fnpf_status pcg_loop(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>& B, int 
     if (*done || it >= max_iter) break;
     const int chunk = std::min(every, max_iter - it);
     for (int k = 0; k < chunk; ++k, ++it) {
-      FNPF_CK(timed_apply<T>(m, t, B.eta, B.p, nullptr, B.q, s, &B.sc->done, it));
-      cg_dot_kernel<T><<<nb, NT, 0, s>>>(B.sc, NI, B.p, B.q, m->partials + 3 * nb);
-      cg_update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, B.dinv, m->partials, nb);
-      cg_pupdate_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.z, B.p, m->partials, nb);
+      const int* skip = &B.sc->done;
+      FNPF_CK(timed_apply<T>(m, t, B.eta, B.p, nullptr, B.q, s, skip, it));
+      vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.p, B.q, m->partials + 3 * nb);
+      vec::update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, pmg ? nullptr : B.dinv,
+                                              m->partials, nb, nullptr);
+      if (pmg) {
+        FNPF_CK(mg_apply<T>(m->mg, t, B.eta, B.r, B.z, reinterpret_cast<T*>(m->ring), m->variant,
+                            m->opts.cheb_degree, m->opts.coarse_iters, skip, s, &m->launches));
+        vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.r, B.z, m->partials + 1 * nb);
+        m->launches += 1;
+      }
+      vec::pupdate_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.z, B.p, m->partials, nb, nullptr);
       m->launches += 3;
     }
     FNPF_CK(cudaGetLastError());
   }
   *out = *m->sc_host;
+  return FNPF_OK;
+}
+
+// With the p-multigrid preconditioner: z = M r, p = z, partial rz (slot 1).
+template <typename T>
+fnpf_status pmg_start(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T* r, T* z, T* p, cudaStream_t s) {
+  const int64_t NI = m->g.NI;
+  const int nb = vec_blocks(NI);
+  FNPF_CK(mg_apply<T>(m->mg, t, eta, r, z, reinterpret_cast<T*>(m->ring), m->variant, m->opts.cheb_degree,
+                      m->opts.coarse_iters, nullptr, s, &m->launches));
+  vec::copy_kernel<T><<<nb, NT, 0, s>>>(NI, z, p, nullptr);
+  vec::dot_kernel<T><<<nb, NT, 0, s>>>(nullptr, NI, r, z, m->partials + 1 * nb);
+  m->launches += 2;
+  FNPF_CK(cudaGetLastError());
   return FNPF_OK;
 }
 
@@ -374,19 +315,35 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double
   const int nb = vec_blocks(NI);
   CgScalars* sc = m->sc;
   const bool mixed = m->opts.precision == FNPF_MIXED;
+  const bool pmg = m->opts.precond == FNPF_PMG;
+  if (pmg && !m->mg) {
+    std::string why;
+    m->mg = mg_create(g, m->h, m->Xs, m->Ys, m->iso, m->Lx, m->Ly, &why);
+    if (!m->mg) {
+      m->err = why;
+      return FNPF_ENOMEM;
+    }
+  }
   if (info) FNPF_CK(cudaEventRecord(m->ev0, s));
   FNPF_CK(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
   FNPF_CK(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
-  if (!mixed) {
+  if (!mixed && !pmg) {
     FNPF_CK(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
-    invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
+    vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
+  }
+  if (!mixed && pmg) {
+    FNPF_CK(mg_prepare<double>(m->mg, t, eta, m->ring, m->variant, m->opts.cheb_degree, m->opts.coarse_iters, s));
   }
   FNPF_CK(cudaGetLastError());
   // lift: r = A [0; phis]_I = -b; q = A [x; 0]_I; then b, r = b - q (, z, p)
   FNPF_CK(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
   FNPF_CK(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
-  cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, mixed ? nullptr : m->dinv, m->z, m->p, mixed ? m->b : nullptr,
-                                   m->partials, nb);
+  cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
+                                   mixed ? m->b : nullptr, m->partials, nb);
+  if (!mixed && pmg) {
+    fnpf_status st = pmg_start<double>(m, t, eta, m->r, m->z, m->p, s);
+    if (st != FNPF_OK) return st;
+  }
   cg_init_finish_kernel<<<1, NT, 0, s>>>(sc, m->partials, nb, m->opts.rtol * m->opts.rtol,
                                          m->opts.atol * m->opts.atol);
   FNPF_CK(cudaGetLastError());
@@ -404,8 +361,13 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double
   // ---- mixed precision: FP64 defect correction around FP32 Jacobi-PCG
   const Tables<float> t32 = m->tables32();
   to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
-  FNPF_CK(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
-  invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+  if (pmg) {
+    FNPF_CK(mg_prepare<float>(m->mg, t32, m->eta32, reinterpret_cast<float*>(m->ring), m->variant,
+                              m->opts.cheb_degree, m->opts.coarse_iters, s));
+  } else {
+    FNPF_CK(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
+    vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+  }
   FNPF_CK(cudaGetLastError());
   m->launches += 4;
   int inner_total = 0, outer = 0;
@@ -421,7 +383,12 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double
     // inner solve A32 e = r (FP32, Jacobi-PCG, relative tolerance inner_rtol)
     CgScalars* si = m->sc_in;
     FNPF_CK(cudaMemsetAsync(si, 0, sizeof(CgScalars), s));
-    inner_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->r32, m->e32, m->z32, m->p32, m->dinv32, m->partials, nb);
+    inner_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->r32, m->e32, m->z32, m->p32, pmg ? nullptr : m->dinv32,
+                                        m->partials, nb);
+    if (pmg) {
+      fnpf_status st = pmg_start<float>(m, t32, m->eta32, m->r32, m->z32, m->p32, s);
+      if (st != FNPF_OK) return st;
+    }
     inner_init_finish_kernel<<<1, NT, 0, s>>>(si, m->partials, nb, in_rtol2);
     FNPF_CK(cudaGetLastError());
     m->launches += 2;

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "fnpf.h"
 
@@ -101,6 +102,11 @@ __host__ __device__ inline int line_owners(int idx, int p, int ne, int periodic,
 fnpf_status validate_desc(const fnpf_mesh_desc* d, std::string* why);
 Geom make_geom(const fnpf_mesh_desc* d);
 void gll_tables(int p, double* xi, double* w, double* D);   // host, long-double Newton
+// Horizontal metric (r_x, r_y, s_x, s_y, w_i w_j |J2|) of every element-column
+// line, lumped surface mass and surface coordinates; false on a degenerate map.
+bool build_hmetric(const Geom& g, const double* xi, const double* w, const double* D, bool iso, double Lx, double Ly,
+                   const double* Xs, const double* Ys, std::vector<double>* hm, std::vector<double>* mass,
+                   std::vector<double>* xs, std::vector<double>* ys);
 
 // Pointers of one operator application.
 template <typename T>

@@ -58,6 +58,74 @@ void gll_tables(int p, double* xi, double* w, double* D) {
   D[p * n + p] = (double)p * (p + 1) / 4.0;
 }
 
+bool build_hmetric(const Geom& g, const double* xi, const double* w, const double* D, bool iso, double Lx, double Ly,
+                   const double* Xs, const double* Ys, std::vector<double>* hm, std::vector<double>* mass,
+                   std::vector<double>* xs, std::vector<double>* ys) {
+  const int n = g.n;
+  const int64_t L = g.lines, HS = (int64_t)g.n_ecol * L;
+  hm->assign(5 * HS, 0.0);
+  mass->assign(g.ns, 0.0);
+  xs->assign(g.ns, 0.0);
+  ys->assign(g.ns, 0.0);
+  const double dx = iso ? 0.0 : Lx / g.nx;
+  const double dy = (iso || g.dim == 2) ? 0.0 : Ly / g.ny;
+  bool bad_jac = false;
+  for (int ecol = g.n_ecol - 1; ecol >= 0; --ecol) {   // reverse: the lowest element writes coords last
+    const int ex = ecol % g.nx, ey = ecol / g.nx;
+    for (int line = (int)L - 1; line >= 0; --line) {
+      const int i = line % n, j = line / n;
+      const int col = node_col(g, ex, ey, i, j);
+      double xr, xs_, yr, ys_;
+      double X, Y;
+      if (!iso) {
+        xr = dx / 2;
+        xs_ = 0;
+        yr = 0;
+        ys_ = dy / 2;
+        X = ex * dx + (1 + xi[i]) * dx / 2;
+        Y = g.dim == 3 ? ey * dy + (1 + xi[j]) * dy / 2 : 0.0;
+      } else {
+        xr = xs_ = yr = ys_ = 0;
+        for (int a = 0; a < n; ++a) {
+          xr += D[i * n + a] * Xs[node_col(g, ex, ey, a, j)];
+          if (g.dim == 3) {
+            yr += D[i * n + a] * Ys[node_col(g, ex, ey, a, j)];
+            xs_ += D[j * n + a] * Xs[node_col(g, ex, ey, i, a)];
+            ys_ += D[j * n + a] * Ys[node_col(g, ex, ey, i, a)];
+          }
+        }
+        X = Xs[col];
+        Y = g.dim == 3 ? Ys[col] : 0.0;
+      }
+      double rx, ry, sx, sy, cw;
+      if (g.dim == 3) {
+        const double J2 = xr * ys_ - xs_ * yr;
+        if (!(fabs(J2) > 0)) bad_jac = true;
+        rx = ys_ / J2;
+        ry = -xs_ / J2;
+        sx = -yr / J2;
+        sy = xr / J2;
+        cw = w[i] * w[j] * fabs(J2);
+      } else {
+        if (!(fabs(xr) > 0)) bad_jac = true;
+        rx = 1.0 / xr;
+        ry = sx = sy = 0.0;
+        cw = w[i] * fabs(xr);
+      }
+      const int64_t hidx = (int64_t)ecol * L + line;
+      (*hm)[hidx] = rx;
+      (*hm)[HS + hidx] = ry;
+      (*hm)[2 * HS + hidx] = sx;
+      (*hm)[3 * HS + hidx] = sy;
+      (*hm)[4 * HS + hidx] = cw;
+      (*mass)[col] += cw;
+      (*xs)[col] = X;
+      (*ys)[col] = Y;
+    }
+  }
+  return !bad_jac;
+}
+
 fnpf_status validate_desc(const fnpf_mesh_desc* d, std::string* why) {
   if (!d) { *why = "descriptor is NULL"; return FNPF_EINVAL; }
   if (d->dim != 2 && d->dim != 3) { *why = "dim must be 2 or 3"; return FNPF_EINVAL; }
@@ -137,6 +205,7 @@ void free_mesh(fnpf_mesh* m) {
     if (p) cudaFree(p);
   if (m->b) cudaFree(m->b);
   if (m->sc_in) cudaFree(m->sc_in);
+  fnpf::mg_destroy(m->mg);
   if (m->sc) cudaFree(m->sc);
   if (m->sc_host) cudaFreeHost(m->sc_host);
   if (m->ev0) cudaEventDestroy(m->ev0);
@@ -214,71 +283,20 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   m->D.resize(n * n);
   fnpf::gll_tables(p, m->xi.data(), m->w.data(), m->D.data());
   m->h.assign(desc->h, desc->h + g.ns);
+  m->iso = desc->horiz_kind == FNPF_ISOPARAMETRIC;
+  m->Lx = desc->Lx;
+  m->Ly = desc->Ly;
+  if (m->iso) {
+    m->Xs.assign(desc->X, desc->X + g.ns);
+    m->Ys = g.dim == 3 ? std::vector<double>(desc->Y, desc->Y + g.ns) : std::vector<double>(g.ns, 0.0);
+  }
 
   // horizontal metric of every element-column node and lumped surface mass
-  const int64_t L = g.lines, HS = (int64_t)g.n_ecol * L;
-  m->hm.assign(5 * HS, 0.0);
-  std::vector<double> mass(g.ns, 0.0);
-  m->xs.assign(g.ns, 0.0);
-  m->ys.assign(g.ns, 0.0);
+  const int64_t HS = (int64_t)g.n_ecol * g.lines;
+  std::vector<double> mass;
   const bool iso = desc->horiz_kind == FNPF_ISOPARAMETRIC;
-  const double dx = iso ? 0.0 : desc->Lx / g.nx;
-  const double dy = (iso || g.dim == 2) ? 0.0 : desc->Ly / g.ny;
-  bool bad_jac = false;
-  for (int ecol = g.n_ecol - 1; ecol >= 0; --ecol) {   // reverse: the lowest element writes coords last
-    const int ex = ecol % g.nx, ey = ecol / g.nx;
-    for (int line = (int)L - 1; line >= 0; --line) {
-      const int i = line % n, j = line / n;
-      const int col = fnpf::node_col(g, ex, ey, i, j);
-      double xr, xs_, yr, ys_;
-      double X, Y;
-      if (!iso) {
-        xr = dx / 2;
-        xs_ = 0;
-        yr = 0;
-        ys_ = dy / 2;
-        X = ex * dx + (1 + m->xi[i]) * dx / 2;
-        Y = g.dim == 3 ? ey * dy + (1 + m->xi[j]) * dy / 2 : 0.0;
-      } else {
-        xr = xs_ = yr = ys_ = 0;
-        for (int a = 0; a < n; ++a) {
-          xr += m->D[i * n + a] * desc->X[fnpf::node_col(g, ex, ey, a, j)];
-          if (g.dim == 3) {
-            yr += m->D[i * n + a] * desc->Y[fnpf::node_col(g, ex, ey, a, j)];
-            xs_ += m->D[j * n + a] * desc->X[fnpf::node_col(g, ex, ey, i, a)];
-            ys_ += m->D[j * n + a] * desc->Y[fnpf::node_col(g, ex, ey, i, a)];
-          }
-        }
-        X = desc->X[col];
-        Y = g.dim == 3 ? desc->Y[col] : 0.0;
-      }
-      double rx, ry, sx, sy, cw;
-      if (g.dim == 3) {
-        const double J2 = xr * ys_ - xs_ * yr;
-        if (!(fabs(J2) > 0)) bad_jac = true;
-        rx = ys_ / J2;
-        ry = -xs_ / J2;
-        sx = -yr / J2;
-        sy = xr / J2;
-        cw = m->w[i] * m->w[j] * fabs(J2);
-      } else {
-        if (!(fabs(xr) > 0)) bad_jac = true;
-        rx = 1.0 / xr;
-        ry = sx = sy = 0.0;
-        cw = m->w[i] * fabs(xr);
-      }
-      const int64_t hidx = (int64_t)ecol * L + line;
-      m->hm[hidx] = rx;
-      m->hm[HS + hidx] = ry;
-      m->hm[2 * HS + hidx] = sx;
-      m->hm[3 * HS + hidx] = sy;
-      m->hm[4 * HS + hidx] = cw;
-      mass[col] += cw;
-      m->xs[col] = X;
-      m->ys[col] = Y;
-    }
-  }
-  if (bad_jac) {
+  if (!fnpf::build_hmetric(g, m->xi.data(), m->w.data(), m->D.data(), iso, desc->Lx, desc->Ly, desc->X, desc->Y,
+                           &m->hm, &mass, &m->xs, &m->ys)) {
     g_create_error = "degenerate horizontal Jacobian";
     delete m;
     return FNPF_EINVAL;

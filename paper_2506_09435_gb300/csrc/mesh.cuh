@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "fnpf_internal.cuh"
+#include "mg.cuh"
 
 struct fnpf_mesh {
   fnpf::Geom g{};
@@ -58,6 +59,12 @@ struct fnpf_mesh {
   float* dinv32 = nullptr;
   double* b = nullptr;              // NI: lifted right-hand side
   fnpf::CgScalars* sc_in = nullptr; // inner-solve scalars
+
+  // p-multigrid hierarchy (created at the first FNPF_PMG solve)
+  fnpf::Mg* mg = nullptr;
+  bool iso = false;
+  double Lx = 0, Ly = 0;
+  std::vector<double> Xs, Ys;       // surface-node coordinates of an isoparametric mesh
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   // instrumentation

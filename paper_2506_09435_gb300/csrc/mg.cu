@@ -1,0 +1,561 @@
+// p-multigrid preconditioner with Chebyshev-Jacobi smoothing for the Laplace
+// solve (the paper preconditions CG with algebraic multigrid, Sec. 4 solver
+// settings; this is the spectral-element counterpart).
+//
+// Levels p_0 = p > p_1 = p_0/2 > ... > p_L = 1 on the same element columns.
+// Each level is a rediscretisation of the weak Laplace form (Eq. Laplace_weak)
+// on the same eta-following geometry: eta and h are interpolated to the
+// level's surface nodes and the level's operator rebuilds its geometric
+// factors exactly like the fine one.  Transfers: see mg_impl.cuh.
+//
+// Smoother: Chebyshev iteration on D^-1 A over [lmax / range, lmax] (Saad,
+// Iterative Methods, Algorithm 12.1, with the Jacobi diagonal), degree d pre-
+// and post-smoothing; the coarsest level gets one Chebyshev sweep of degree
+// d_c over a wider interval.  Every sweep is a fixed polynomial in D^-1 A, so
+// the V-cycle is a fixed symmetric operator and plain PCG applies.
+// lmax per level comes from a 10-step Jacobi-CG Lanczos run on a fixed
+// pseudo-random right-hand side; the largest eigenvalue of the Lanczos
+// tridiagonal matrix is found by bisection on the device and multiplied by a
+// safety factor, so the set-up needs no host synchronisation.
+#include <math.h>
+
+#include <string>
+#include <vector>
+
+#include "mg.cuh"
+#include "vec.cuh"
+
+namespace fnpf {
+
+cudaError_t launch_transfer_double(const Geom& gf, const Geom& gc, const double* J, const double* in, double* out,
+                                   double* ring, int mode, const int* skip, cudaStream_t s);
+cudaError_t launch_transfer_float(const Geom& gf, const Geom& gc, const float* J, const float* in, float* out,
+                                  float* ring, int mode, const int* skip, cudaStream_t s);
+
+namespace {
+
+constexpr int kMaxLevels = 5;
+constexpr int kLanczos = 10;
+constexpr double kSafety = 1.1;
+constexpr double kSmoothRange = 20.0;
+
+inline cudaError_t launch_transfer(const Geom& gf, const Geom& gc, const double* J, const double* in, double* out,
+                                   double* ring, int mode, const int* skip, cudaStream_t s) {
+  return launch_transfer_double(gf, gc, J, in, out, ring, mode, skip, s);
+}
+inline cudaError_t launch_transfer(const Geom& gf, const Geom& gc, const float* J, const float* in, float* out,
+                                   float* ring, int mode, const int* skip, cudaStream_t s) {
+  return launch_transfer_float(gf, gc, J, in, out, ring, mode, skip, s);
+}
+
+// ---------------------------------------------------------------------------- kernels
+
+// eta at the level's surface nodes: evaluation of the fine element polynomial.
+template <typename T>
+__global__ void surface_interp_kernel(Geom g0, Geom gl, const T* Js, const T* eta0, T* etal) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= gl.ns) return;
+  const int ix = col % gl.ncx, iy = col / gl.ncx;
+  int ex[2], io[2], ey[2] = {0, 0}, jo[2] = {0, 0};
+  line_owners(ix, gl.p, gl.nx, gl.px, ex, io);
+  if (gl.dim == 3) line_owners(iy, gl.p, gl.ny, gl.py, ey, jo);
+  const int n0 = g0.n;
+  T s = 0;
+  if (gl.dim == 3) {
+    for (int b = 0; b < n0; ++b) {
+      T sb = 0;
+      for (int a = 0; a < n0; ++a) sb += Js[io[0] * n0 + a] * eta0[node_col(g0, ex[0], ey[0], a, b)];
+      s += Js[jo[0] * n0 + b] * sb;
+    }
+  } else {
+    for (int a = 0; a < n0; ++a) s += Js[io[0] * n0 + a] * eta0[node_col(g0, ex[0], 0, a, 0)];
+  }
+  etal[col] = s;
+}
+
+// Deterministic pseudo-random right-hand side in [-0.5, 0.5) (splitmix64 of the index).
+template <typename T>
+__global__ void random_kernel(int64_t n, T* r) {
+  FNPF_GRID_LOOP(i, n) {
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    r[i] = (T)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+  }
+}
+
+// Lanczos start: x = 0, z = dinv r, p = z; partials rz, rr.
+template <typename T>
+__global__ void __launch_bounds__(vec::NT) lz_init_kernel(int64_t n, const T* r, const T* dinv, T* x, T* z, T* p,
+                                                          double* part, int nb) {
+  __shared__ double sh[vec::NT / 32];
+  double srz = 0, srr = 0;
+  FNPF_GRID_LOOP(i, n) {
+    const T zz = dinv[i] * r[i];
+    x[i] = T(0);
+    z[i] = zz;
+    p[i] = zz;
+    srz += (double)r[i] * (double)zz;
+    srr += (double)r[i] * (double)r[i];
+  }
+  srz = vec::block_sum(srz, sh);
+  srr = vec::block_sum(srr, sh);
+  if (threadIdx.x == 0) {
+    part[1 * nb + blockIdx.x] = srz;
+    part[2 * nb + blockIdx.x] = srr;
+  }
+}
+
+__global__ void __launch_bounds__(vec::NT) lz_init_finish_kernel(CgScalars* sc, const double* part, int nb) {
+  __shared__ double sh[vec::NT / 32];
+  const double rz = vec::reduce_partials(part + nb, nb, sh);
+  const double rr = vec::reduce_partials(part + 2 * nb, nb, sh);
+  if (threadIdx.x == 0) {
+    sc->rz[0] = rz;
+    sc->rr = rr;
+    sc->bb = rr;
+    sc->iters = 0;
+    sc->tol2 = 1e-28 * rr;
+    sc->status = 0;
+    sc->done = (rr > 0.0 && isfinite(rr)) ? 0 : 1;
+  }
+}
+
+// Largest eigenvalue of the Lanczos tridiagonal matrix from the CG coefficients
+// (T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_j,j+1 = sqrt(b_j)/a_j), by Sturm-count
+// bisection; writes the Chebyshev interval.
+__global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, int kmax, double safety, double range,
+                              ChebParams* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int k = sc->iters < kmax ? sc->iters : kmax;
+  double a[32], b[32];
+  if (k > 32) k = 32;
+  for (int j = 0; j < k; ++j) {
+    const double al = hist[2 * j];
+    a[j] = 1.0 / al + (j > 0 ? hist[2 * (j - 1) + 1] / hist[2 * (j - 1)] : 0.0);
+    b[j] = j + 1 < k ? sqrt(fmax(hist[2 * j + 1], 0.0)) / al : 0.0;
+  }
+  double lmax;
+  if (k == 0) {
+    lmax = out->lmax > 0 ? out->lmax : 2.0;
+  } else {
+    double hi = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double r = a[j] + fabs(b[j]) + (j > 0 ? fabs(b[j - 1]) : 0.0);
+      hi = fmax(hi, r);
+    }
+    double lo = 0.0;
+    for (int it = 0; it < 80; ++it) {
+      const double x = 0.5 * (lo + hi);
+      int below = 0;
+      double d = 1.0;
+      for (int j = 0; j < k; ++j) {
+        d = a[j] - x - (j > 0 ? b[j - 1] * b[j - 1] / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0) ++below;
+      }
+      if (below == k) hi = x;   // every eigenvalue lies below x
+      else lo = x;
+    }
+    lmax = hi;
+  }
+  out->lmax = safety * lmax;
+  out->range = range;
+}
+
+__device__ inline void cheb_coeffs(const ChebParams* cp, double* theta, double* delta, double* sigma) {
+  const double lmax = cp->lmax, lmin = lmax / cp->range;
+  *theta = 0.5 * (lmax + lmin);
+  *delta = 0.5 * (lmax - lmin);
+  *sigma = *theta / *delta;
+}
+
+// Step 0 of a Chebyshev sweep: (r = b if b given); d = dinv r / theta; x = d or x += d.
+template <typename T>
+__global__ void __launch_bounds__(vec::NT) cheb_start_kernel(int64_t n, const T* b, T* r, const T* dinv, T* d, T* x,
+                                                             const ChebParams* cp, int x_zero, const int* skip) {
+  if (skip && *skip) return;
+  double theta, delta, sigma;
+  cheb_coeffs(cp, &theta, &delta, &sigma);
+  const T it = (T)(1.0 / theta);
+  FNPF_GRID_LOOP(i, n) {
+    T rr;
+    if (b) {
+      rr = b[i];
+      r[i] = rr;
+    } else {
+      rr = r[i];
+    }
+    const T dd = it * dinv[i] * rr;
+    d[i] = dd;
+    x[i] = x_zero ? dd : x[i] + dd;
+  }
+}
+
+// Step k >= 1: r -= w (w = A d_{k-1}); d = rho_k rho_{k-1} d + (2 rho_k / delta) dinv r; x += d.
+template <typename T>
+__global__ void __launch_bounds__(vec::NT) cheb_step_kernel(int64_t n, const T* w, T* r, const T* dinv, T* d, T* x,
+                                                            const ChebParams* cp, int k, const int* skip) {
+  if (skip && *skip) return;
+  double theta, delta, sigma;
+  cheb_coeffs(cp, &theta, &delta, &sigma);
+  double rho_old = 1.0 / sigma, rho = rho_old;
+  for (int j = 1; j <= k; ++j) {
+    rho = 1.0 / (2.0 * sigma - rho_old);
+    if (j < k) rho_old = rho;
+  }
+  const T c1 = (T)(rho * rho_old), c2 = (T)(2.0 * rho / delta);
+  FNPF_GRID_LOOP(i, n) {
+    const T rn = r[i] - w[i];
+    r[i] = rn;
+    const T dd = c1 * d[i] + c2 * dinv[i] * rn;
+    d[i] = dd;
+    x[i] += dd;
+  }
+}
+
+// r = b - w, or r -= w when b is null.
+template <typename T>
+__global__ void __launch_bounds__(vec::NT) residual_kernel(int64_t n, const T* b, const T* w, T* r, const int* skip) {
+  if (skip && *skip) return;
+  FNPF_GRID_LOOP(i, n) r[i] = (b ? b[i] : r[i]) - w[i];
+}
+
+// ---------------------------------------------------------------------------- host helpers
+
+int next_p(int p) { return p / 2 > 1 ? p / 2 : 1; }
+
+std::vector<double> interp_matrix(const std::vector<double>& xf, const std::vector<double>& xc) {
+  const int nf = (int)xf.size(), nc = (int)xc.size();
+  std::vector<double> J(nf * nc);
+  for (int i = 0; i < nf; ++i)
+    for (int c = 0; c < nc; ++c) {
+      double v = 1.0;
+      for (int m = 0; m < nc; ++m)
+        if (m != c) v *= (xf[i] - xc[m]) / (xc[c] - xc[m]);
+      J[i * nc + c] = v;
+    }
+  return J;
+}
+
+Geom level_geom(const Geom& g0, int p) {
+  Geom g = g0;
+  g.p = p;
+  g.n = p + 1;
+  g.ncx = p * g.nx + (g.px ? 0 : 1);
+  g.ncy = g.dim == 3 ? p * g.ny + (g.py ? 0 : 1) : 1;
+  g.ns = g.ncx * g.ncy;
+  g.nv = p * g.nz + 1;
+  g.lines = g.dim == 3 ? g.n * g.n : g.n;
+  g.ring = g.dim == 3 ? 4 * p : 2;
+  g.N = (int64_t)g.nv * g.ns;
+  g.NI = (int64_t)(g.nv - 1) * g.ns;
+  return g;
+}
+
+// Values of a surface field of level 0 at the surface nodes of level l (host).
+std::vector<double> host_surface_interp(const Geom& g0, const Geom& gl, const std::vector<double>& Js,
+                                        const double* f0) {
+  std::vector<double> out(gl.ns);
+  const int n0 = g0.n;
+  for (int col = 0; col < gl.ns; ++col) {
+    const int ix = col % gl.ncx, iy = col / gl.ncx;
+    int ex[2], io[2], ey[2] = {0, 0}, jo[2] = {0, 0};
+    line_owners(ix, gl.p, gl.nx, gl.px, ex, io);
+    if (gl.dim == 3) line_owners(iy, gl.p, gl.ny, gl.py, ey, jo);
+    double s = 0;
+    if (gl.dim == 3) {
+      for (int b = 0; b < n0; ++b) {
+        double sb = 0;
+        for (int a = 0; a < n0; ++a) sb += Js[io[0] * n0 + a] * f0[node_col(g0, ex[0], ey[0], a, b)];
+        s += Js[jo[0] * n0 + b] * sb;
+      }
+    } else {
+      for (int a = 0; a < n0; ++a) s += Js[io[0] * n0 + a] * f0[node_col(g0, ex[0], 0, a, 0)];
+    }
+    out[col] = s;
+  }
+  return out;
+}
+
+}  // namespace
+
+struct Mg {
+  int L = 0;
+  Geom g[kMaxLevels];
+  MgLevelBufs<double> b64[kMaxLevels];
+  MgLevelBufs<float> b32[kMaxLevels];
+  ChebParams* cheb64 = nullptr;   // [L]
+  ChebParams* cheb32 = nullptr;
+  double* hist = nullptr;         // [L][2 * kLanczos]
+  CgScalars* sc = nullptr;        // [L] Lanczos scalars
+  double* part = nullptr;         // [4 * kVecBlocks]
+  std::vector<void*> allocs;
+
+  template <typename T>
+  MgLevelBufs<T>* bufs();
+  template <typename T>
+  ChebParams* cheb();
+};
+template <>
+MgLevelBufs<double>* Mg::bufs<double>() { return b64; }
+template <>
+MgLevelBufs<float>* Mg::bufs<float>() { return b32; }
+template <>
+ChebParams* Mg::cheb<double>() { return cheb64; }
+template <>
+ChebParams* Mg::cheb<float>() { return cheb32; }
+
+void mg_destroy(Mg* mg) {
+  if (!mg) return;
+  for (void* p : mg->allocs) cudaFree(p);
+  delete mg;
+}
+
+int mg_levels(const Mg* mg) { return mg ? mg->L : 0; }
+
+Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<double>& X0,
+              const std::vector<double>& Y0, bool iso, double Lx, double Ly, std::string* err) {
+  Mg* mg = new Mg();
+  int p = g0.p;
+  mg->g[0] = g0;
+  mg->L = 1;
+  while (p > 1 && mg->L < kMaxLevels) {
+    p = next_p(p);
+    mg->g[mg->L] = level_geom(g0, p);
+    ++mg->L;
+  }
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(ptr, bytes < 8 ? 8 : bytes);
+    if (e == cudaSuccess) mg->allocs.push_back(*ptr);
+  };
+  auto upload = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  std::vector<double> xi0(g0.n), w0(g0.n), D0(g0.n * g0.n);
+  gll_tables(g0.p, xi0.data(), w0.data(), D0.data());
+  std::vector<double> xprev = xi0;
+  for (int l = 0; l < mg->L; ++l) {
+    const Geom& g = mg->g[l];
+    MgLevelBufs<double>& B = mg->b64[l];
+    MgLevelBufs<float>& F = mg->b32[l];
+    double** dv[] = {&B.dinv, &B.X, &B.B, &B.R, &B.Dd, &B.W, &B.P};
+    for (double** v : dv) alloc((void**)v, g.NI * sizeof(double));
+    float** fv[] = {&F.dinv, &F.X, &F.B, &F.R, &F.Dd, &F.W, &F.P};
+    for (float** v : fv) alloc((void**)v, g.NI * sizeof(float));
+    if (l == 0) continue;
+    std::vector<double> xi(g.n), w(g.n), D(g.n * g.n);
+    gll_tables(g.p, xi.data(), w.data(), D.data());
+    const std::vector<double> J = interp_matrix(xprev, xi);     // level l-1 nodes x level l
+    const std::vector<double> Js = interp_matrix(xi, xi0);      // level l nodes x level-0 nodes
+    xprev = xi;
+    std::vector<double> hl = host_surface_interp(g0, g, Js, h0.data());
+    std::vector<double> Xl, Yl;
+    if (iso) {
+      Xl = host_surface_interp(g0, g, Js, X0.data());
+      Yl = g.dim == 3 ? host_surface_interp(g0, g, Js, Y0.data()) : std::vector<double>(g.ns, 0.0);
+    }
+    std::vector<double> hm, mass, xs, ys;
+    if (!build_hmetric(g, xi.data(), w.data(), D.data(), iso, Lx, Ly, iso ? Xl.data() : nullptr,
+                       iso ? Yl.data() : nullptr, &hm, &mass, &xs, &ys)) {
+      *err = "degenerate horizontal Jacobian on a multigrid level";
+      mg_destroy(mg);
+      return nullptr;
+    }
+    for (double hv : hl)
+      if (!(hv > 0)) {
+        *err = "interpolated depth not positive on a multigrid level";
+        mg_destroy(mg);
+        return nullptr;
+      }
+    // double tables
+    double *dD, *dxi, *dw, *dhm, *dh, *dJ, *dJs, *deta;
+    alloc((void**)&dD, D.size() * 8);
+    alloc((void**)&dxi, xi.size() * 8);
+    alloc((void**)&dw, w.size() * 8);
+    alloc((void**)&dhm, hm.size() * 8);
+    alloc((void**)&dh, hl.size() * 8);
+    alloc((void**)&dJ, J.size() * 8);
+    alloc((void**)&dJs, Js.size() * 8);
+    alloc((void**)&deta, g.ns * 8);
+    upload(dD, D.data(), D.size() * 8);
+    upload(dxi, xi.data(), xi.size() * 8);
+    upload(dw, w.data(), w.size() * 8);
+    upload(dhm, hm.data(), hm.size() * 8);
+    upload(dh, hl.data(), hl.size() * 8);
+    upload(dJ, J.data(), J.size() * 8);
+    upload(dJs, Js.data(), Js.size() * 8);
+    B.t = Tables<double>{dD, dxi, dw, dhm, dh, nullptr};
+    B.J = dJ;
+    B.Js = dJs;
+    B.eta = deta;
+    // float tables
+    auto f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    const std::vector<float> fD = f32(D), fxi = f32(xi), fw = f32(w), fhm = f32(hm), fh = f32(hl), fJ = f32(J),
+                             fJs = f32(Js);
+    float *sD, *sxi, *sw, *shm, *sh, *sJ, *sJs, *seta;
+    alloc((void**)&sD, fD.size() * 4);
+    alloc((void**)&sxi, fxi.size() * 4);
+    alloc((void**)&sw, fw.size() * 4);
+    alloc((void**)&shm, fhm.size() * 4);
+    alloc((void**)&sh, fh.size() * 4);
+    alloc((void**)&sJ, fJ.size() * 4);
+    alloc((void**)&sJs, fJs.size() * 4);
+    alloc((void**)&seta, g.ns * 4);
+    upload(sD, fD.data(), fD.size() * 4);
+    upload(sxi, fxi.data(), fxi.size() * 4);
+    upload(sw, fw.data(), fw.size() * 4);
+    upload(shm, fhm.data(), fhm.size() * 4);
+    upload(sh, fh.data(), fh.size() * 4);
+    upload(sJ, fJ.data(), fJ.size() * 4);
+    upload(sJs, fJs.data(), fJs.size() * 4);
+    F.t = Tables<float>{sD, sxi, sw, shm, sh, nullptr};
+    F.J = sJ;
+    F.Js = sJs;
+    F.eta = seta;
+  }
+  alloc((void**)&mg->cheb64, mg->L * sizeof(ChebParams));
+  alloc((void**)&mg->cheb32, mg->L * sizeof(ChebParams));
+  alloc((void**)&mg->hist, mg->L * 2 * kLanczos * sizeof(double));
+  alloc((void**)&mg->sc, mg->L * sizeof(CgScalars));
+  alloc((void**)&mg->part, 4 * kVecBlocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(mg->cheb64, 0, mg->L * sizeof(ChebParams));
+  if (e == cudaSuccess) e = cudaMemset(mg->cheb32, 0, mg->L * sizeof(ChebParams));
+  if (e != cudaSuccess) {
+    *err = std::string("multigrid set-up failed: ") + cudaGetErrorString(e);
+    mg_destroy(mg);
+    return nullptr;
+  }
+  return mg;
+}
+
+namespace {
+
+template <typename T>
+Tables<T> level_tables(Mg* mg, int l, const Tables<T>& t0) {
+  return l == 0 ? t0 : mg->bufs<T>()[l].t;
+}
+
+template <typename T>
+const T* level_eta(Mg* mg, int l, const T* eta0) {
+  return l == 0 ? eta0 : mg->bufs<T>()[l].eta;
+}
+
+// One Chebyshev sweep of `degree` steps on level l solving A x = b.
+// x_zero: start from x = 0 (r = b, no operator application needed);
+// otherwise r = b - A x first.  With `final_residual` the residual of the
+// result is left in R.
+template <typename T>
+cudaError_t cheb_sweep(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* b, T* x, int degree, bool x_zero,
+                       bool final_residual, T* ring, int variant, const int* skip, cudaStream_t s, int64_t* nl) {
+  const Geom& g = mg->g[l];
+  MgLevelBufs<T>& L = mg->bufs<T>()[l];
+  const Tables<T> t = level_tables(mg, l, t0);
+  const T* eta = level_eta(mg, l, eta0);
+  const ChebParams* cp = mg->cheb<T>() + l;
+  const int nb = vec::blocks_for(g.NI);
+  cudaError_t e;
+  if (x_zero) {
+    cheb_start_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, b, L.R, L.dinv, L.Dd, x, cp, 1, skip);
+    *nl += 1;
+  } else {
+    if ((e = launch_apply<T>(g, t, eta, x, nullptr, L.W, nullptr, ring, variant, s, skip)) != cudaSuccess) return e;
+    residual_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, b, L.W, L.R, skip);
+    cheb_start_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, nullptr, L.R, L.dinv, L.Dd, x, cp, 0, skip);
+    *nl += 4;
+  }
+  for (int k = 1; k < degree; ++k) {
+    if ((e = launch_apply<T>(g, t, eta, L.Dd, nullptr, L.W, nullptr, ring, variant, s, skip)) != cudaSuccess)
+      return e;
+    cheb_step_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.W, L.R, L.dinv, L.Dd, x, cp, k, skip);
+    *nl += 3;
+  }
+  if (final_residual) {
+    if ((e = launch_apply<T>(g, t, eta, L.Dd, nullptr, L.W, nullptr, ring, variant, s, skip)) != cudaSuccess)
+      return e;
+    residual_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, nullptr, L.W, L.R, skip);
+    *nl += 3;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vcycle(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* b, T* x, T* ring, int variant,
+                   int degree, int coarse_degree, const int* skip, cudaStream_t s, int64_t* nl) {
+  cudaError_t e;
+  if (l == mg->L - 1) return cheb_sweep<T>(mg, l, t0, eta0, b, x, coarse_degree, true, false, ring, variant, skip, s, nl);
+  MgLevelBufs<T>* Lv = mg->bufs<T>();
+  if ((e = cheb_sweep<T>(mg, l, t0, eta0, b, x, degree, true, true, ring, variant, skip, s, nl)) != cudaSuccess)
+    return e;
+  // restrict the residual, solve on the next level, prolong and add
+  if ((e = launch_transfer(mg->g[l], mg->g[l + 1], Lv[l + 1].J, Lv[l].R, Lv[l + 1].B, ring, 0, skip, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = vcycle<T>(mg, l + 1, t0, eta0, Lv[l + 1].B, Lv[l + 1].X, ring, variant, degree, coarse_degree, skip, s,
+                     nl)) != cudaSuccess)
+    return e;
+  if ((e = launch_transfer(mg->g[l], mg->g[l + 1], Lv[l + 1].J, Lv[l + 1].X, x, ring, 2, skip, s)) != cudaSuccess)
+    return e;
+  *nl += 3;
+  return cheb_sweep<T>(mg, l, t0, eta0, b, x, degree, false, false, ring, variant, skip, s, nl);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, T* ring, int variant, int cheb_degree,
+                       int coarse_degree, cudaStream_t s) {
+  (void)cheb_degree;
+  cudaError_t e;
+  MgLevelBufs<T>* Lv = mg->bufs<T>();
+  for (int l = 1; l < mg->L; ++l) {
+    const Geom& gl = mg->g[l];
+    surface_interp_kernel<T><<<(gl.ns + 127) / 128, 128, 0, s>>>(mg->g[0], gl, Lv[l].Js, eta0, Lv[l].eta);
+  }
+  for (int l = 0; l < mg->L; ++l) {
+    const Geom& g = mg->g[l];
+    const Tables<T> t = level_tables(mg, l, t0);
+    const T* eta = level_eta(mg, l, eta0);
+    MgLevelBufs<T>& L = Lv[l];
+    const int nb = vec::blocks_for(g.NI);
+    if ((e = launch_diag<T>(g, t, eta, L.dinv, nullptr, ring, s)) != cudaSuccess) return e;
+    vec::invert_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.dinv);
+    // Lanczos through Jacobi-CG: x = X, r = R, z = Dd, p = P, q = W
+    random_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.R);
+    CgScalars* sc = mg->sc + l;
+    double* hist = mg->hist + 2 * kLanczos * l;
+    lz_init_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.R, L.dinv, L.X, L.Dd, L.P, mg->part, nb);
+    lz_init_finish_kernel<<<1, vec::NT, 0, s>>>(sc, mg->part, nb);
+    for (int it = 0; it < kLanczos; ++it) {
+      if ((e = launch_apply<T>(g, t, eta, L.P, nullptr, L.W, nullptr, ring, variant, s, &sc->done)) != cudaSuccess)
+        return e;
+      vec::dot_kernel<T><<<nb, vec::NT, 0, s>>>(&sc->done, g.NI, L.P, L.W, mg->part + 3 * nb);
+      vec::update_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.X, L.R, L.Dd, L.P, L.W, L.dinv, mg->part, nb,
+                                                   hist);
+      vec::pupdate_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.Dd, L.P, mg->part, nb, hist);
+    }
+    const double range = l == mg->L - 1 ? fmax(kSmoothRange, 0.25 * coarse_degree * coarse_degree) : kSmoothRange;
+    lz_eig_kernel<<<1, 1, 0, s>>>(sc, hist, kLanczos, kSafety, range, mg->cheb<T>() + l);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t mg_apply(Mg* mg, const Tables<T>& t0, const T* eta0, const T* r, T* z, T* ring, int variant,
+                     int cheb_degree, int coarse_degree, const int* skip, cudaStream_t s, int64_t* launches) {
+  return vcycle<T>(mg, 0, t0, eta0, r, z, ring, variant, cheb_degree, coarse_degree, skip, s, launches);
+}
+
+template cudaError_t mg_prepare<double>(Mg*, const Tables<double>&, const double*, double*, int, int, int,
+                                        cudaStream_t);
+template cudaError_t mg_prepare<float>(Mg*, const Tables<float>&, const float*, float*, int, int, int, cudaStream_t);
+template cudaError_t mg_apply<double>(Mg*, const Tables<double>&, const double*, const double*, double*, double*, int,
+                                      int, int, const int*, cudaStream_t, int64_t*);
+template cudaError_t mg_apply<float>(Mg*, const Tables<float>&, const float*, const float*, float*, float*, int, int,
+                                     int, const int*, cudaStream_t, int64_t*);
+
+}  // namespace fnpf

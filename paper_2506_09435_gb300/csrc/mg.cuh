@@ -1,0 +1,56 @@
+// p-multigrid preconditioner: declarations shared by mg.cu and cg.cu.
+#pragma once
+
+#include <vector>
+
+#include "fnpf_internal.cuh"
+
+namespace fnpf {
+
+// Chebyshev interval of one level, written on the device by the Lanczos
+// eigenvalue kernel: smoothing targets [lmax / range, lmax].
+struct ChebParams {
+  double lmax;
+  double range;
+};
+
+// Device buffers of one level in precision T.  Level 0 is the mesh itself: its
+// X and B are supplied by the caller (the CG vectors z and r).
+template <typename T>
+struct MgLevelBufs {
+  Tables<T> t;          // GLL tables, horizontal metric, depth of this level
+  T* eta = nullptr;     // [ns] eta interpolated to this level's surface nodes
+  T* dinv = nullptr;    // [NI] inverse Jacobi diagonal
+  T* X = nullptr;       // [NI] correction (levels >= 1)
+  T* B = nullptr;       // [NI] right-hand side (levels >= 1)
+  T* R = nullptr;       // [NI] residual
+  T* Dd = nullptr;      // [NI] Chebyshev direction
+  T* W = nullptr;       // [NI] operator output
+  T* P = nullptr;       // [NI] CG direction of the Lanczos estimate
+  const T* J = nullptr;   // [n_{l-1} x n_l] prolongation from this level to level l-1 (levels >= 1)
+  const T* Js = nullptr;  // [n_l x n_0] surface interpolation from level 0 (levels >= 1)
+};
+
+struct Mg;   // opaque; owned by the mesh
+
+// Builds the hierarchy p -> p/2 -> ... -> 1 for the mesh sizes g0 (host work and
+// device allocations).  Returns nullptr and sets *err on failure.
+Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<double>& X0,
+              const std::vector<double>& Y0, bool iso, double Lx, double Ly, std::string* err);
+void mg_destroy(Mg* mg);
+int mg_levels(const Mg* mg);
+
+// Per-solve set-up in precision T: eta at every level, Jacobi diagonals, and
+// the Chebyshev intervals from a short Lanczos run per level (all on the
+// device, no host synchronisation).  eta0 is the fine eta in precision T,
+// t0 the fine tables, dinv0/R0.. fine scratch supplied by the mesh.
+template <typename T>
+cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, T* ring, int variant, int cheb_degree,
+                       int coarse_degree, cudaStream_t s);
+
+// z = M r (one symmetric V-cycle); kernels exit at once when *skip != 0.
+template <typename T>
+cudaError_t mg_apply(Mg* mg, const Tables<T>& t0, const T* eta0, const T* r, T* z, T* ring, int variant,
+                     int cheb_degree, int coarse_degree, const int* skip, cudaStream_t s, int64_t* launches);
+
+}  // namespace fnpf

@@ -1,0 +1,132 @@
+// Vector kernels shared by the CG solves and the Lanczos eigenvalue estimates of
+// the p-multigrid smoothers.  Reductions are deterministic: each block writes
+// one FP64 partial; consumers re-reduce all partials in a fixed order, so every
+// block obtains the same bits.
+#pragma once
+
+#include <math.h>
+
+#include "fnpf_internal.cuh"
+
+namespace fnpf {
+namespace vec {
+
+constexpr int NT = kVecThreads;
+
+#define FNPF_GRID_LOOP(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)vec::NT + threadIdx.x; i < (n); i += (int64_t)gridDim.x * vec::NT)
+
+__device__ inline double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0;
+  for (int k = 0; k < NT / 32; ++k) s += sh[k];
+  return s;
+}
+
+__device__ inline double reduce_partials(const double* part, int nb, double* sh) {
+  double v = 0;
+  for (int k = threadIdx.x; k < nb; k += NT) v += part[k];
+  return block_sum(v, sh);
+}
+
+inline int blocks_for(int64_t n) {
+  int64_t b = (n + NT - 1) / NT;
+  if (b < 1) b = 1;
+  if (b > kVecBlocks) b = kVecBlocks;
+  return (int)b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) invert_kernel(int64_t n, T* d) {
+  FNPF_GRID_LOOP(i, n) d[i] = T(1) / d[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) copy_kernel(int64_t n, const T* a, T* b, const int* skip) {
+  if (skip && *skip) return;
+  FNPF_GRID_LOOP(i, n) b[i] = a[i];
+}
+
+// part[blockIdx] = sum p q (FP64 accumulation)
+template <typename T>
+__global__ void __launch_bounds__(NT) dot_kernel(const int* skip, int64_t n, const T* p, const T* q, double* part) {
+  if (skip && *skip) return;
+  __shared__ double sh[NT / 32];
+  double s = 0;
+  FNPF_GRID_LOOP(i, n) s += (double)p[i] * (double)q[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; with dinv: z = dinv r and
+// partials rz (slot 1), rr (slot 2); without dinv only rr.  hist (optional)
+// records alpha at hist[2 it].
+template <typename T>
+__global__ void __launch_bounds__(NT) update_kernel(CgScalars* sc, int it, int64_t n, T* x, T* r, T* z, const T* p,
+                                                    const T* q, const T* dinv, double* part, int nb, double* hist) {
+  if (sc->done) return;
+  __shared__ double sh[NT / 32];
+  const double pq = reduce_partials(part + 3 * nb, nb, sh);
+  const double rz = sc->rz[it & 1];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc->status = FNPF_EBREAKDOWN;
+      sc->done = 1;
+    }
+    return;
+  }
+  const double alpha_d = rz / pq;
+  if (hist && blockIdx.x == 0 && threadIdx.x == 0) hist[2 * it] = alpha_d;
+  const T alpha = (T)alpha_d;
+  double srz = 0, srr = 0;
+  FNPF_GRID_LOOP(i, n) {
+    x[i] += alpha * p[i];
+    const T rn = r[i] - alpha * q[i];
+    r[i] = rn;
+    srr += (double)rn * (double)rn;
+    if (dinv) {
+      const T zz = dinv[i] * rn;
+      z[i] = zz;
+      srz += (double)rn * (double)zz;
+    }
+  }
+  srz = block_sum(srz, sh);
+  srr = block_sum(srr, sh);
+  if (threadIdx.x == 0) {
+    if (dinv) part[1 * nb + blockIdx.x] = srz;
+    part[2 * nb + blockIdx.x] = srr;
+  }
+}
+
+// beta = rz_new / rz; p = z + beta p; block 0 advances the scalars and tests
+// convergence.  hist (optional) records beta at hist[2 it + 1].
+template <typename T>
+__global__ void __launch_bounds__(NT) pupdate_kernel(CgScalars* sc, int it, int64_t n, const T* z, T* p,
+                                                     const double* part, int nb, double* hist) {
+  if (sc->done) return;
+  __shared__ double sh[NT / 32];
+  const double rz_new = reduce_partials(part + nb, nb, sh);
+  const double rr = reduce_partials(part + 2 * nb, nb, sh);
+  const double beta_d = rz_new / sc->rz[it & 1];
+  const T beta = (T)beta_d;
+  FNPF_GRID_LOOP(i, n) p[i] = z[i] + beta * p[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (hist) hist[2 * it + 1] = beta_d;
+    sc->rz[(it + 1) & 1] = rz_new;
+    sc->rr = rr;
+    sc->iters = it + 1;
+    if (!isfinite(rr) || !isfinite(rz_new)) {
+      sc->status = FNPF_EBREAKDOWN;
+      sc->done = 1;
+    } else if (rr <= sc->tol2) {
+      sc->done = 1;
+    }
+  }
+}
+
+}  // namespace vec
+}  // namespace fnpf
