@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--precond", default="pmg", choices=["pmg", "jacobi"])
     ap.add_argument("--cheb-degree", type=int, default=3)
-    ap.add_argument("--coarse-degree", type=int, default=30)
+    ap.add_argument("--coarse-degree", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--nx", type=int, default=32)

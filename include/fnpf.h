@@ -83,6 +83,8 @@ typedef struct {
   int coarse_iters;        /* fixed coarse-level iterations (FNPF_PMG)             */
   double inner_rtol;       /* inner FP32 solve tolerance (FNPF_MIXED)              */
   int max_outer;           /* defect-correction cap (FNPF_MIXED)                   */
+  int use_graphs;          /* 1: replay CG iterations as CUDA graphs (not while
+                              instrumentation is enabled); 0: plain launches      */
 } fnpf_opts;
 
 typedef struct {
@@ -100,8 +102,8 @@ typedef struct fnpf_mesh fnpf_mesh;
 fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t* n_surf);
 
 /* Fills *opts with the defaults: FP64, Jacobi, rtol 1e-10, atol 0,
- * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 30,
- * inner_rtol 1e-5, max_outer 20. */
+ * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 10,
+ * inner_rtol 1e-5, max_outer 20, use_graphs 1. */
 void fnpf_default_opts(fnpf_opts* opts);
 
 /* Creates a mesh on the current CUDA device: GLL tables, horizontal metric,

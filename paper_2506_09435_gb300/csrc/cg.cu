@@ -188,6 +188,13 @@ cudaError_t timed_apply(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T*
 
 }  // namespace
 
+void graph_reset(GraphSlot* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->exec = nullptr;
+  g->kernels = 0;
+  g->key[0] = g->key[1] = nullptr;
+}
+
 void prof_collect(fnpf_mesh* m, int iters_done) {
   for (int k = 0; k < m->prof_used; ++k) {
     if (m->prof_it[k] >= iters_done) continue;
@@ -229,16 +236,42 @@ struct PcgBufs {
   CgScalars* sc;
 };
 
-// Runs Jacobi-PCG iterations until the device flag is set or max_iter is reached;
-// the scalars must have been initialised.  Returns the host copy of the scalars
-// in *out and whether the loop converged.
+// One PCG iteration (iteration parity it & 1), enqueued on s.
+template <typename T>
+cudaError_t enqueue_iteration(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>& B, int it, cudaStream_t s) {
+  const int64_t NI = m->g.NI;
+  const int nb = vec_blocks(NI);
+  const bool pmg = m->opts.precond == FNPF_PMG;
+  const int* skip = &B.sc->done;
+  cudaError_t e = timed_apply<T>(m, t, B.eta, B.p, nullptr, B.q, s, skip, it);
+  if (e != cudaSuccess) return e;
+  vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.p, B.q, m->partials + 3 * nb);
+  vec::update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, pmg ? nullptr : B.dinv,
+                                          m->partials, nb, nullptr);
+  if (pmg) {
+    e = mg_apply<T>(m->mg, t, B.eta, B.r, B.z, reinterpret_cast<T*>(m->ring), m->variant, m->opts.cheb_degree,
+                    m->opts.coarse_iters, skip, s, &m->launches);
+    if (e != cudaSuccess) return e;
+    vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.r, B.z, m->partials + 1 * nb);
+    m->launches += 1;
+  }
+  vec::pupdate_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.z, B.p, m->partials, nb, nullptr);
+  m->launches += 3;
+  return cudaGetLastError();
+}
+
+// Runs PCG iterations until the device flag is set or max_iter is reached; the
+// scalars must have been initialised.  After the first chunk (which also does
+// any lazy kernel set-up) the iterations run as replays of a CUDA graph that
+// holds two iterations (parities 0 and 1), captured once per mesh and
+// precision on the mesh's capture stream and launched on s.  Returns the host
+// copy of the scalars in *out and whether the loop converged.
 template <typename T>
 fnpf_status pcg_loop(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>& B, int max_iter, cudaStream_t s,
                      CgScalars* out, bool* done) {
-  const int64_t NI = m->g.NI;
-  const int nb = vec_blocks(NI);
-  const int every = std::max(1, m->opts.check_every);
-  const bool pmg = m->opts.precond == FNPF_PMG;
+  const int every = std::max(2, m->opts.check_every & ~1);
+  const bool graphs = m->opts.use_graphs && !m->prof_on;
+  GraphSlot& slot = m->g_iter[sizeof(T) == 4 ? 1 : 0];
   int it = 0;
   *done = false;
   while (true) {
@@ -247,23 +280,33 @@ fnpf_status pcg_loop(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>& B, int 
     prof_collect(m, m->sc_host->done ? m->sc_host->iters : it);
     *done = m->sc_host->done != 0;
     if (*done || it >= max_iter) break;
-    const int chunk = std::min(every, max_iter - it);
-    for (int k = 0; k < chunk; ++k, ++it) {
-      const int* skip = &B.sc->done;
-      FNPF_CK(timed_apply<T>(m, t, B.eta, B.p, nullptr, B.q, s, skip, it));
-      vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.p, B.q, m->partials + 3 * nb);
-      vec::update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, pmg ? nullptr : B.dinv,
-                                              m->partials, nb, nullptr);
-      if (pmg) {
-        FNPF_CK(mg_apply<T>(m->mg, t, B.eta, B.r, B.z, reinterpret_cast<T*>(m->ring), m->variant,
-                            m->opts.cheb_degree, m->opts.coarse_iters, skip, s, &m->launches));
-        vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.r, B.z, m->partials + 1 * nb);
-        m->launches += 1;
+    int chunk = std::min(every, max_iter - it);
+    if (graphs && it > 0 && (it & 1) == 0 && chunk >= 2) {
+      if (!slot.exec || slot.key[0] != B.x || slot.key[1] != B.eta) {
+        graph_reset(&slot);
+        FNPF_CK(cudaStreamBeginCapture(m->gstream, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = m->launches;
+        cudaError_t e = enqueue_iteration<T>(m, t, B, 0, m->gstream);
+        if (e == cudaSuccess) e = enqueue_iteration<T>(m, t, B, 1, m->gstream);
+        slot.kernels = m->launches - l0;
+        m->launches = l0;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(m->gstream, &graph);
+        FNPF_CK(e);
+        FNPF_CK(e2);
+        const cudaError_t e3 = cudaGraphInstantiate(&slot.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        FNPF_CK(e3);
+        slot.key[0] = B.x;
+        slot.key[1] = B.eta;
       }
-      vec::pupdate_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.z, B.p, m->partials, nb, nullptr);
-      m->launches += 3;
+      const int pairs = chunk / 2;
+      for (int k = 0; k < pairs; ++k) FNPF_CK(cudaGraphLaunch(slot.exec, s));
+      m->launches += pairs * slot.kernels;
+      it += 2 * pairs;
+      chunk -= 2 * pairs;
     }
-    FNPF_CK(cudaGetLastError());
+    for (int k = 0; k < chunk; ++k, ++it) FNPF_CK(enqueue_iteration<T>(m, t, B, it, s));
   }
   *out = *m->sc_host;
   return FNPF_OK;
@@ -307,7 +350,7 @@ fnpf_status finish(fnpf_mesh* m, const CgScalars& h, bool done, int iters, int o
 
 }  // namespace
 
-fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,
+fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, double* x, fnpf_solve_info* info,
                      cudaStream_t s) {
   const Geom& g = m->g;
   const Tables<double> t = m->tables();
@@ -325,6 +368,9 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double
     }
   }
   if (info) FNPF_CK(cudaEventRecord(m->ev0, s));
+  // the solve reads eta from a mesh-owned copy, so captured graphs keep valid pointers
+  FNPF_CK(cudaMemcpyAsync(m->eta64, eta_in, g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  const double* eta = m->eta64;
   FNPF_CK(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
   FNPF_CK(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
   if (!mixed && !pmg) {

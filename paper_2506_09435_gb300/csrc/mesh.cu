@@ -204,8 +204,11 @@ void free_mesh(fnpf_mesh* m) {
   for (float* p : fptrs)
     if (p) cudaFree(p);
   if (m->b) cudaFree(m->b);
+  if (m->eta64) cudaFree(m->eta64);
   if (m->sc_in) cudaFree(m->sc_in);
   fnpf::mg_destroy(m->mg);
+  for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);
+  if (m->gstream) cudaStreamDestroy(m->gstream);
   if (m->sc) cudaFree(m->sc);
   if (m->sc_host) cudaFreeHost(m->sc_host);
   if (m->ev0) cudaEventDestroy(m->ev0);
@@ -251,9 +254,10 @@ void fnpf_default_opts(fnpf_opts* o) {
   o->max_iter = 20000;
   o->check_every = 16;
   o->cheb_degree = 3;
-  o->coarse_iters = 30;
+  o->coarse_iters = 10;
   o->inner_rtol = 1e-5;
   o->max_outer = 20;
+  o->use_graphs = 1;
 }
 
 fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, fnpf_mesh** out) {
@@ -330,6 +334,7 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   A(&m->acc_eta, g.ns);
   A(&m->acc_phi, g.ns);
   A(&m->b, g.NI);
+  A(&m->eta64, g.ns);
   auto AF = [&](float** ptr, size_t cnt) {
     if (e == cudaSuccess) e = dalloc(ptr, cnt);
   };
@@ -348,6 +353,7 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   if (e == cudaSuccess) e = cudaMalloc((void**)&m->sc_in, sizeof(fnpf::CgScalars));
   if (e == cudaSuccess) e = cudaMalloc((void**)&m->sc, sizeof(fnpf::CgScalars));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->sc_host, sizeof(fnpf::CgScalars));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
   if (e == cudaSuccess) e = cudaMemcpy(m->dD, m->D.data(), n * n * sizeof(double), cudaMemcpyHostToDevice);
@@ -383,6 +389,7 @@ void fnpf_destroy_mesh(fnpf_mesh* m) { free_mesh(m); }
 fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   if (!m || !o) return FNPF_EINVAL;
   m->opts = *o;
+  for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);   // captured arguments depend on the options
   return FNPF_OK;
 }
 

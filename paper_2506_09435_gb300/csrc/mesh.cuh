@@ -7,6 +7,13 @@
 #include "fnpf_internal.cuh"
 #include "mg.cuh"
 
+// One captured CUDA graph and the pointers it was captured with.
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+  const void* key[2] = {nullptr, nullptr};
+};
+
 struct fnpf_mesh {
   fnpf::Geom g{};
   fnpf_opts opts{};
@@ -58,6 +65,7 @@ struct fnpf_mesh {
   float* e32 = nullptr;
   float* dinv32 = nullptr;
   double* b = nullptr;              // NI: lifted right-hand side
+  double* eta64 = nullptr;          // ns: copy of the solve's eta
   fnpf::CgScalars* sc_in = nullptr; // inner-solve scalars
 
   // p-multigrid hierarchy (created at the first FNPF_PMG solve)
@@ -66,6 +74,10 @@ struct fnpf_mesh {
   double Lx = 0, Ly = 0;
   std::vector<double> Xs, Ys;       // surface-node coordinates of an isoparametric mesh
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // CUDA graphs of the CG iteration (0: FP64, 1: FP32), captured on gstream
+  cudaStream_t gstream = nullptr;
+  GraphSlot g_iter[2];
 
   // instrumentation
   bool prof_on = false;
@@ -86,6 +98,7 @@ struct fnpf_mesh {
 namespace fnpf {
 // Accumulates the recorded event pairs (call after a host sync of the stream).
 void prof_collect(fnpf_mesh* m, int iters_done);
+void graph_reset(GraphSlot* g);
 // CG solve of A_II x = -A_IS phis for the interior part x [NI] (in: initial guess).
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,
                      cudaStream_t s);

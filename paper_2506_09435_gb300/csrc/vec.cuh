@@ -103,7 +103,9 @@ __global__ void __launch_bounds__(NT) update_kernel(CgScalars* sc, int it, int64
 }
 
 // beta = rz_new / rz; p = z + beta p; block 0 advances the scalars and tests
-// convergence.  hist (optional) records beta at hist[2 it + 1].
+// convergence.  `it` only selects the parity of the rz double buffer (and the
+// hist slot), so a captured pair of iterations with it = 0, 1 can be replayed.
+// hist (optional) records beta at hist[2 it + 1].
 template <typename T>
 __global__ void __launch_bounds__(NT) pupdate_kernel(CgScalars* sc, int it, int64_t n, const T* z, T* p,
                                                      const double* part, int nb, double* hist) {
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(NT) pupdate_kernel(CgScalars* sc, int it, int6
     if (hist) hist[2 * it + 1] = beta_d;
     sc->rz[(it + 1) & 1] = rz_new;
     sc->rr = rr;
-    sc->iters = it + 1;
+    sc->iters += 1;
     if (!isfinite(rr) || !isfinite(rz_new)) {
       sc->status = FNPF_EBREAKDOWN;
       sc->done = 1;

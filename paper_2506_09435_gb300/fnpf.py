@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("max_outer", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

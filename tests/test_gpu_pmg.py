@@ -61,3 +61,20 @@ def test_pmg_rk4_matches_oracle(fnpf):
     torch.cuda.synchronize()
     assert rel_l2(eta.cpu().numpy(), eta_r) < 1e-10
     assert rel_l2(phis.cpu().numpy(), phi_r) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_is_bitwise_identical_to_plain_launches(fnpf, precision):
+    """CUDA-graph replay of the CG iterations runs the same kernels with the
+    same arguments: results match plain launches bit for bit."""
+    prec = fnpf.FNPF_MIXED if precision == "mixed" else fnpf.FNPF_FP64
+    shape = (3, 6, 5, 2, 5, True, False)
+    out = []
+    for graphs in (0, 1):
+        c = Case(fnpf, *shape, opts=pmg(fnpf, rtol=1e-12, precision=prec, use_graphs=graphs, check_every=4))
+        eta, phis = c.t(c.eta), c.t(c.phis)
+        for _ in range(2):
+            c.gm.rk4_step(eta, phis, 0.0, 0.01)
+        torch.cuda.synchronize()
+        out.append((eta.cpu().numpy(), phis.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
