@@ -85,6 +85,10 @@ typedef struct {
   int max_outer;           /* defect-correction cap (FNPF_MIXED)                   */
   int use_graphs;          /* 1: replay CG iterations as CUDA graphs (not while
                               instrumentation is enabled); 0: plain launches      */
+  int store_metric;        /* FNPF_FP64 solves: 1 = rebuild the metric G from eta
+                              once per solve into device memory (6 doubles per
+                              point, allocated at the first solve) and read it in
+                              every application; 0 = rebuild it per application */
 } fnpf_opts;
 
 typedef struct {
@@ -103,7 +107,7 @@ fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t*
 
 /* Fills *opts with the defaults: FP64, Jacobi, rtol 1e-10, atol 0,
  * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 10,
- * inner_rtol 1e-5, max_outer 20, use_graphs 1. */
+ * inner_rtol 1e-5, max_outer 20, use_graphs 1, store_metric 1. */
 void fnpf_default_opts(fnpf_opts* opts);
 
 /* Creates a mesh on the current CUDA device: GLL tables, horizontal metric,
@@ -179,6 +183,12 @@ fnpf_status fnpf_rk4_step(fnpf_mesh* mesh, double* eta, double* phis, double t, 
  * the message is available from fnpf_last_error(NULL). */
 fnpf_status fnpf_apply_noalloc(const fnpf_mesh_desc* desc, const double* h, const double* eta, const double* x,
                                double* y, void* stream);
+
+/* Autotuner: times every elements-per-CTA shape of the FP64 and of the FP32
+ * operator kernel on this mesh (eta [Ns]) and keeps the fastest of each; the
+ * chosen shape indices are returned when the pointers are non-NULL.  Runs
+ * automatically before the first solve of a mesh; waits for the stream. */
+fnpf_status fnpf_autotune(fnpf_mesh* mesh, const double* eta, int* variant64, int* variant32, void* stream);
 
 /* Instrumentation (tracing): when enabled, every operator application issued
  * by a solve is bracketed by CUDA events on the solve's stream, and the

@@ -33,7 +33,7 @@ extern "C" {
 fnpf_status fnpf_apply(fnpf_mesh* m, const double* eta, const double* x, double* y, void* stream) {
   if (!m || !eta || !x || !y) return FNPF_EINVAL;
   const Geom& g = m->g;
-  cudaError_t e = fnpf::launch_apply<double>(g, m->tables(), eta, x, x + g.NI, y, y + g.NI, m->ring, m->variant,
+  cudaError_t e = fnpf::launch_apply<double>(g, m->tables(), eta, x, x + g.NI, y, y + g.NI, m->ring, m->variant64,
                                              (cudaStream_t)stream);
   return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "apply");
 }
@@ -42,7 +42,7 @@ fnpf_status fnpf_apply_f32(fnpf_mesh* m, const float* eta, const float* x, float
   if (!m || !eta || !x || !y) return FNPF_EINVAL;
   const Geom& g = m->g;
   cudaError_t e = fnpf::launch_apply<float>(g, m->tables32(), eta, x, x + g.NI, y, y + g.NI,
-                                            reinterpret_cast<float*>(m->ring), m->variant, (cudaStream_t)stream);
+                                            reinterpret_cast<float*>(m->ring), m->variant32, (cudaStream_t)stream);
   return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "apply_f32");
 }
 
@@ -118,6 +118,14 @@ fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, dou
     cp = a.out_phi;
   }
   return FNPF_OK;
+}
+
+fnpf_status fnpf_autotune(fnpf_mesh* m, const double* eta, int* variant64, int* variant32, void* stream) {
+  if (!m || !eta) return FNPF_EINVAL;
+  fnpf_status st = fnpf::autotune(m, eta, nullptr, (cudaStream_t)stream);
+  if (variant64) *variant64 = m->variant64;
+  if (variant32) *variant32 = m->variant32;
+  return st;
 }
 
 fnpf_status fnpf_profile_enable(fnpf_mesh* m, int on) {

@@ -4,17 +4,17 @@
 namespace fnpf {
 
 template <typename T>
-static cudaError_t dispatch(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, bool diag, int variant,
+static cudaError_t dispatch(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, int variant,
                             cudaStream_t s) {
   switch (g.n) {
-    case 2: return launch_ax_n<T, 2>(g, t, a, diag, variant, s);
-    case 3: return launch_ax_n<T, 3>(g, t, a, diag, variant, s);
-    case 4: return launch_ax_n<T, 4>(g, t, a, diag, variant, s);
-    case 5: return launch_ax_n<T, 5>(g, t, a, diag, variant, s);
-    case 6: return launch_ax_n<T, 6>(g, t, a, diag, variant, s);
-    case 7: return launch_ax_n<T, 7>(g, t, a, diag, variant, s);
-    case 8: return launch_ax_n<T, 8>(g, t, a, diag, variant, s);
-    case 9: return launch_ax_n<T, 9>(g, t, a, diag, variant, s);
+    case 2: return launch_ax_n<T, 2>(g, t, a, mode, variant, s);
+    case 3: return launch_ax_n<T, 3>(g, t, a, mode, variant, s);
+    case 4: return launch_ax_n<T, 4>(g, t, a, mode, variant, s);
+    case 5: return launch_ax_n<T, 5>(g, t, a, mode, variant, s);
+    case 6: return launch_ax_n<T, 6>(g, t, a, mode, variant, s);
+    case 7: return launch_ax_n<T, 7>(g, t, a, mode, variant, s);
+    case 8: return launch_ax_n<T, 8>(g, t, a, mode, variant, s);
+    case 9: return launch_ax_n<T, 9>(g, t, a, mode, variant, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -22,17 +22,39 @@ static cudaError_t dispatch(const Geom& g, const Tables<T>& t, const AxPtrs<T>& 
 template <typename T>
 cudaError_t launch_apply(const Geom& g, const Tables<T>& t, const T* eta, const T* xI, const T* xs, T* yI, T* ys,
                          T* ring, int variant, cudaStream_t s, const int* skip) {
-  AxPtrs<T> a{eta, xI, xs, yI, ys, ring, skip};
-  return dispatch<T>(g, t, a, false, variant, s);
+  AxPtrs<T> a{eta, xI, xs, yI, ys, ring, skip, nullptr};
+  return dispatch<T>(g, t, a, AX_APPLY, variant, s);
 }
 
 template <typename T>
 cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, T* ds, T* ring, cudaStream_t s) {
-  AxPtrs<T> a{eta, nullptr, nullptr, dI, ds, ring, nullptr};
-  return dispatch<T>(g, t, a, true, 1, s);
+  AxPtrs<T> a{eta, nullptr, nullptr, dI, ds, ring, nullptr, nullptr};
+  return dispatch<T>(g, t, a, AX_DIAG, 1, s);
 }
 
 int apply_variants(int n, int dim) { return dim == 2 ? 1 : 3; }
+
+int64_t geom_points(const Geom& g) { return (int64_t)g.nz * g.n_ecol * g.n * g.lines; }
+
+template <typename T>
+cudaError_t launch_geom(const Geom& g, const Tables<T>& t, const T* eta, T* G, cudaStream_t s) {
+  AxPtrs<T> a{eta, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, G};
+  return dispatch<T>(g, t, a, AX_GEOM, 1, s);
+}
+
+template <typename T>
+cudaError_t launch_apply_g(const Geom& g, const Tables<T>& t, const T* G, const T* xI, const T* xs, T* yI, T* ys,
+                           T* ring, int variant, cudaStream_t s, const int* skip) {
+  AxPtrs<T> a{nullptr, xI, xs, yI, ys, ring, skip, const_cast<T*>(G)};
+  return dispatch<T>(g, t, a, AX_APPLY_G, variant, s);
+}
+
+template cudaError_t launch_geom<double>(const Geom&, const Tables<double>&, const double*, double*, cudaStream_t);
+template cudaError_t launch_geom<float>(const Geom&, const Tables<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_apply_g<double>(const Geom&, const Tables<double>&, const double*, const double*,
+                                            const double*, double*, double*, double*, int, cudaStream_t, const int*);
+template cudaError_t launch_apply_g<float>(const Geom&, const Tables<float>&, const float*, const float*,
+                                           const float*, float*, float*, float*, int, cudaStream_t, const int*);
 
 template cudaError_t launch_apply<double>(const Geom&, const Tables<double>&, const double*, const double*,
                                           const double*, double*, double*, double*, int, cudaStream_t,

@@ -300,6 +300,161 @@ __global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
   if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
 }
 
+// Number of stored metric entries per point: (rr, rs, ss, rt, st, tt) in 3D,
+// (rr, rt, tt) in 2D.  Layout G[e][pt], pt = ((l n_ecol + ecol) N + k) L + line,
+// so the threads of a CTA read consecutive addresses.
+template <int DIM>
+struct NGeo {
+  static constexpr int value = DIM == 3 ? 6 : 3;
+};
+
+// G of every element point, from eta, h and the horizontal metric (the same
+// formulas as the on-the-fly operator); run once per solve.
+template <typename T, int N, int DIM, int C>
+__global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
+    geom_kernel(Geom g, Tables<T> t, AxPtrs<T> a) {
+  using S = AxShape<T, N, DIM, C>;
+  constexpr int L = S::L;
+  extern __shared__ __align__(16) unsigned char ax_smem[];
+  T* sD = reinterpret_cast<T*>(ax_smem) + 3 * S::BUF;
+  T* sXi = sD + N * N;
+  T* sW = sXi + N;
+  T* sE = sW + N;
+  T* sH = sE + C * L;
+  const int c = threadIdx.x / L, line = threadIdx.x - c * L;
+  const int i = line % N, j = line / N;
+  const int ecol = blockIdx.x * C + c;
+  const bool active = ecol < g.n_ecol;
+  int col;
+  LineGeom<T> lg;
+  ax_prologue<T, N, DIM, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, i, j, ecol, active, col, lg);
+  if (!active) return;
+  const T inv_nz = T(1) / T(g.nz);
+  const int64_t P = (int64_t)g.nz * g.n_ecol * N * L;
+  T* G = a.G;
+  for (int l = 0; l < g.nz; ++l) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
+      const T wk = sW[k];
+      const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
+      const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
+      const T wc = wk * lg.cw;
+      const int64_t pt = (((int64_t)l * g.n_ecol + ecol) * N + k) * L + line;
+      if (DIM == 3) {
+        G[pt] = wk * lg.grr;
+        G[P + pt] = wk * lg.grs;
+        G[2 * P + pt] = wk * lg.gss;
+        G[3 * P + pt] = -wc * (lg.rx * ax + lg.ry * ay);
+        G[4 * P + pt] = -wc * (lg.sx * ax + lg.sy * ay);
+        G[5 * P + pt] = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
+      } else {
+        G[pt] = wk * lg.grr;
+        G[P + pt] = -wc * (lg.rx * ax);
+        G[2 * P + pt] = wc * (ax * ax + T(1)) * lg.Ainv;
+      }
+    }
+  }
+}
+
+// The operator with G read from memory instead of rebuilt: fewer FP64
+// instructions per point, for the FP64 solves where the FP64 pipe is the bound.
+template <typename T, int N, int DIM, int C>
+__global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
+    axg_kernel(Geom g, Tables<T> t, AxPtrs<T> a) {
+  using S = AxShape<T, N, DIM, C>;
+  constexpr int P = N - 1, L = S::L;
+  extern __shared__ __align__(16) unsigned char ax_smem[];
+  T* sU = reinterpret_cast<T*>(ax_smem);
+  T* sR = sU + S::BUF;
+  T* sS = sR + S::BUF;
+  T* sD = sS + S::BUF;
+  if (a.skip && *a.skip) return;
+  const int c = threadIdx.x / L, line = threadIdx.x - c * L;
+  const int i = line % N, j = line / N;
+  const int ecol = blockIdx.x * C + c;
+  const bool active = ecol < g.n_ecol;
+  for (int q = threadIdx.x; q < N * N; q += S::THREADS) sD[q] = t.D[q];
+  int col = 0;
+  if (active) col = node_col(g, ecol % g.nx, ecol / g.nx, i, j);
+  const int slot = ring_slot(DIM, P, i, j);
+  const int64_t PT = (int64_t)g.nz * g.n_ecol * N * L;
+  const T* G = a.G;
+  __syncthreads();
+  T carry = 0;
+  for (int l = 0; l < g.nz; ++l) {
+    T u[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int plane = l * P + k;
+      T v = 0;
+      if (active) {
+        if (plane < g.nv - 1) {
+          if (a.xI) v = a.xI[(int64_t)plane * g.ns + col];
+        } else if (a.xs) {
+          v = a.xs[col];
+        }
+      }
+      u[k] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) sU[(c * N + k) * L + line] = u[k];
+    __syncthreads();
+    T ft[N];
+    const int64_t pt0 = (((int64_t)l * g.n_ecol + (active ? ecol : 0)) * N) * L + line;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const T* uk = sU + (c * N + k) * L;
+      T ur = 0, us = 0, ut = 0;
+#pragma unroll
+      for (int m = 0; m < N; ++m) ur += sD[i * N + m] * uk[j * N + m];
+      if (DIM == 3) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) us += sD[j * N + m] * uk[m * N + i];
+      }
+#pragma unroll
+      for (int m = 0; m < N; ++m) ut += sD[k * N + m] * u[m];
+      const int64_t pt = pt0 + (int64_t)k * L;
+      if (DIM == 3) {
+        const T grr = G[pt], grs = G[PT + pt], gss = G[2 * PT + pt];
+        const T grt = G[3 * PT + pt], gst = G[4 * PT + pt], gtt = G[5 * PT + pt];
+        sR[(c * N + k) * L + line] = grr * ur + grs * us + grt * ut;
+        sS[(c * N + k) * L + line] = grs * ur + gss * us + gst * ut;
+        ft[k] = grt * ur + gst * us + gtt * ut;
+      } else {
+        const T grr = G[pt], grt = G[PT + pt], gtt = G[2 * PT + pt];
+        sR[(c * N + k) * L + line] = grr * ur + grt * ut;
+        ft[k] = grt * ur + gtt * ut;
+      }
+    }
+    __syncthreads();
+    T y[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const T* rk = sR + (c * N + k) * L;
+      const T* sk = sS + (c * N + k) * L;
+      T s = 0;
+#pragma unroll
+      for (int m = 0; m < N; ++m) s += sD[m * N + i] * rk[j * N + m];
+      if (DIM == 3) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) s += sD[m * N + j] * sk[m * N + i];
+      }
+#pragma unroll
+      for (int m = 0; m < N; ++m) s += sD[m * N + k] * ft[m];
+      y[k] = s;
+    }
+    y[0] += carry;
+    carry = y[P];
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
+    }
+  }
+  if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
+}
+
 // Sums the ring contributions of every element-boundary node column, in a
 // fixed order (x owners outer, y owners inner), and writes the output field.
 template <typename T, int DIM>
@@ -365,23 +520,37 @@ cudaError_t launch_gather(const Geom& g, const T* ring, T* yI, T* ys, const int*
   return cudaGetLastError();
 }
 
+template <typename T, int N, int DIM, int C, typename K>
+void set_smem_attr(K kernel, bool* done) {
+  using S = AxShape<T, N, DIM, C>;
+  if (!*done && S::SMEM > 48 * 1024) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    *done = true;
+  }
+}
+
+// mode: AX_APPLY (on-the-fly geometry), AX_DIAG, AX_GEOM (store G), AX_APPLY_G (stored G)
 template <typename T, int N, int DIM, int C>
-cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, bool diag, cudaStream_t s) {
+cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, cudaStream_t s) {
   using S = AxShape<T, N, DIM, C>;
   const unsigned blocks = (unsigned)((g.n_ecol + C - 1) / C);
-  if (diag) {
+  if (mode == AX_GEOM) {
     static bool attr = false;
-    if (!attr && S::SMEM > 48 * 1024) {
-      cudaFuncSetAttribute(diag_kernel<T, N, DIM, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-      attr = true;
-    }
+    set_smem_attr<T, N, DIM, C>(geom_kernel<T, N, DIM, C>, &attr);
+    geom_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    return cudaGetLastError();
+  }
+  if (mode == AX_APPLY_G) {
+    static bool attr = false;
+    set_smem_attr<T, N, DIM, C>(axg_kernel<T, N, DIM, C>, &attr);
+    axg_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+  } else if (mode == AX_DIAG) {
+    static bool attr = false;
+    set_smem_attr<T, N, DIM, C>(diag_kernel<T, N, DIM, C>, &attr);
     diag_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
   } else {
     static bool attr = false;
-    if (!attr && S::SMEM > 48 * 1024) {
-      cudaFuncSetAttribute(ax_kernel<T, N, DIM, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-      attr = true;
-    }
+    set_smem_attr<T, N, DIM, C>(ax_kernel<T, N, DIM, C>, &attr);
     ax_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
   }
   cudaError_t e = cudaGetLastError();
@@ -402,13 +571,13 @@ template <> struct CtaChoices<8> { static constexpr int c[3] = {1, 2, 4}; };
 template <> struct CtaChoices<9> { static constexpr int c[3] = {1, 2, 3}; };
 
 template <typename T, int N>
-cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, bool diag, int variant,
+cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, int variant,
                         cudaStream_t s) {
-  if (g.dim == 2) return launch_ax_shape<T, N, 2, (128 + N - 1) / N>(g, t, a, diag, s);
+  if (g.dim == 2) return launch_ax_shape<T, N, 2, (128 + N - 1) / N>(g, t, a, mode, s);
   constexpr int C0 = CtaChoices<N>::c[0], C1 = CtaChoices<N>::c[1], C2 = CtaChoices<N>::c[2];
-  if (diag || variant == 1) return launch_ax_shape<T, N, 3, C1>(g, t, a, diag, s);
-  if (variant == 0) return launch_ax_shape<T, N, 3, C0>(g, t, a, diag, s);
-  return launch_ax_shape<T, N, 3, C2>(g, t, a, diag, s);
+  if (mode == AX_DIAG || mode == AX_GEOM || variant == 1) return launch_ax_shape<T, N, 3, C1>(g, t, a, mode, s);
+  if (variant == 0) return launch_ax_shape<T, N, 3, C0>(g, t, a, mode, s);
+  return launch_ax_shape<T, N, 3, C2>(g, t, a, mode, s);
 }
 
 }  // namespace fnpf

@@ -2,8 +2,8 @@
 #include "ax_impl.cuh"
 
 namespace fnpf {
-template cudaError_t launch_ax_n<double, 9>(const Geom&, const Tables<double>&, const AxPtrs<double>&, bool, int,
+template cudaError_t launch_ax_n<double, 9>(const Geom&, const Tables<double>&, const AxPtrs<double>&, int, int,
                                             cudaStream_t);
-template cudaError_t launch_ax_n<float, 9>(const Geom&, const Tables<float>&, const AxPtrs<float>&, bool, int,
+template cudaError_t launch_ax_n<float, 9>(const Geom&, const Tables<float>&, const AxPtrs<float>&, int, int,
                                            cudaStream_t);
 }  // namespace fnpf

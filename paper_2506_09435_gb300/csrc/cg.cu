@@ -24,6 +24,15 @@
 #include "mg.cuh"
 #include "vec.cuh"
 
+#define FNPF_CK(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      m->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return FNPF_ECUDA;                                           \
+    }                                                              \
+  } while (0)
+
 namespace fnpf {
 namespace {
 
@@ -165,6 +174,12 @@ __global__ void __launch_bounds__(NT) to_float_kernel(int64_t n, const double* a
 
 inline int vec_blocks(int64_t n) { return vec::blocks_for(n); }
 
+// The stored metric of the finest level while an FP64 solve uses it.
+template <typename T>
+const T* level0_G(const fnpf_mesh* m) {
+  return sizeof(T) == 8 && m->g64_active ? reinterpret_cast<const T*>(m->G64) : nullptr;
+}
+
 // Operator application bracketed by profiling events when enabled.  `it` is the
 // CG iteration the application belongs to (-1: outside the loop); applications
 // of iterations that turn out to follow convergence exit at once and are not
@@ -174,8 +189,11 @@ cudaError_t timed_apply(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T*
                         cudaStream_t s, const int* skip, int it) {
   const bool rec = m->prof_on && m->prof_used * 2 + 1 < (int)m->prof_ev.size();
   if (rec) cudaEventRecord(m->prof_ev[2 * m->prof_used], s);
-  cudaError_t e = launch_apply<T>(m->g, t, eta, xI, xs, yI, nullptr, reinterpret_cast<T*>(m->ring), m->variant, s,
-                                  skip);
+  const T* G = sizeof(T) == 8 && m->g64_active ? reinterpret_cast<const T*>(m->G64) : nullptr;
+  cudaError_t e = G ? launch_apply_g<T>(m->g, t, G, xI, xs, yI, nullptr, reinterpret_cast<T*>(m->ring),
+                                        m->variant<T>(), s, skip)
+                    : launch_apply<T>(m->g, t, eta, xI, xs, yI, nullptr, reinterpret_cast<T*>(m->ring),
+                                      m->variant<T>(), s, skip);
   if (rec) {
     cudaEventRecord(m->prof_ev[2 * m->prof_used + 1], s);
     m->prof_it[m->prof_used] = it;
@@ -186,7 +204,47 @@ cudaError_t timed_apply(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T*
   return e;
 }
 
+template <typename T>
+fnpf_status tune_one(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T* G, T* x, T* y, cudaStream_t s,
+                     int* best) {
+  const Geom& g = m->g;
+  const int nv = apply_variants(g.n, g.dim);
+  float best_ms = 1e30f;
+  *best = 1;
+  T* ring = reinterpret_cast<T*>(m->ring);
+  auto run = [&](int v) {
+    return G ? launch_apply_g<T>(g, t, G, x, nullptr, y, nullptr, ring, v, s, nullptr)
+             : launch_apply<T>(g, t, eta, x, nullptr, y, nullptr, ring, v, s, nullptr);
+  };
+  for (int v = 0; v < nv; ++v) {
+    FNPF_CK(run(v));
+    FNPF_CK(cudaEventRecord(m->ev0, s));
+    for (int r = 0; r < 3; ++r) FNPF_CK(run(v));
+    FNPF_CK(cudaEventRecord(m->ev1, s));
+    FNPF_CK(cudaEventSynchronize(m->ev1));
+    float ms = 0;
+    FNPF_CK(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = v;
+    }
+  }
+  return FNPF_OK;
+}
+
 }  // namespace
+
+fnpf_status autotune(fnpf_mesh* m, const double* eta, const double* G, cudaStream_t s) {
+  const Geom& g = m->g;
+  FNPF_CK(cudaMemsetAsync(m->p, 0, g.NI * sizeof(double), s));
+  FNPF_CK(cudaMemsetAsync(m->p32, 0, g.NI * sizeof(float), s));
+  to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+  FNPF_CK(cudaGetLastError());
+  fnpf_status st = tune_one<double>(m, m->tables(), eta, G, m->p, m->q, s, &m->variant64);
+  if (st == FNPF_OK) st = tune_one<float>(m, m->tables32(), m->eta32, nullptr, m->p32, m->q32, s, &m->variant32);
+  m->tuned = true;
+  return st;
+}
 
 void graph_reset(GraphSlot* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
@@ -212,14 +270,6 @@ void prof_collect(fnpf_mesh* m, int iters_done) {
   m->prof_used = 0;
 }
 
-#define FNPF_CK(call)                                              \
-  do {                                                             \
-    cudaError_t e_ = (call);                                       \
-    if (e_ != cudaSuccess) {                                       \
-      m->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
-      return FNPF_ECUDA;                                           \
-    }                                                              \
-  } while (0)
 
 namespace {
 
@@ -249,8 +299,8 @@ cudaError_t enqueue_iteration(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>
   vec::update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, pmg ? nullptr : B.dinv,
                                           m->partials, nb, nullptr);
   if (pmg) {
-    e = mg_apply<T>(m->mg, t, B.eta, B.r, B.z, reinterpret_cast<T*>(m->ring), m->variant, m->opts.cheb_degree,
-                    m->opts.coarse_iters, skip, s, &m->launches);
+    e = mg_apply<T>(m->mg, t, B.eta, level0_G<T>(m), B.r, B.z, reinterpret_cast<T*>(m->ring), m->variant<T>(),
+                    m->opts.cheb_degree, m->opts.coarse_iters, skip, s, &m->launches);
     if (e != cudaSuccess) return e;
     vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.r, B.z, m->partials + 1 * nb);
     m->launches += 1;
@@ -317,8 +367,8 @@ template <typename T>
 fnpf_status pmg_start(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T* r, T* z, T* p, cudaStream_t s) {
   const int64_t NI = m->g.NI;
   const int nb = vec_blocks(NI);
-  FNPF_CK(mg_apply<T>(m->mg, t, eta, r, z, reinterpret_cast<T*>(m->ring), m->variant, m->opts.cheb_degree,
-                      m->opts.coarse_iters, nullptr, s, &m->launches));
+  FNPF_CK(mg_apply<T>(m->mg, t, eta, level0_G<T>(m), r, z, reinterpret_cast<T*>(m->ring), m->variant<T>(),
+                      m->opts.cheb_degree, m->opts.coarse_iters, nullptr, s, &m->launches));
   vec::copy_kernel<T><<<nb, NT, 0, s>>>(NI, z, p, nullptr);
   vec::dot_kernel<T><<<nb, NT, 0, s>>>(nullptr, NI, r, z, m->partials + 1 * nb);
   m->launches += 2;
@@ -328,6 +378,7 @@ fnpf_status pmg_start(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T* r
 
 fnpf_status finish(fnpf_mesh* m, const CgScalars& h, bool done, int iters, int outer, fnpf_solve_info* info,
                    cudaStream_t s) {
+  m->g64_active = false;
   fnpf_status st = FNPF_OK;
   if (h.status != 0) st = (fnpf_status)h.status;
   else if (!done) st = FNPF_ENOCONV;
@@ -359,6 +410,11 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   CgScalars* sc = m->sc;
   const bool mixed = m->opts.precision == FNPF_MIXED;
   const bool pmg = m->opts.precond == FNPF_PMG;
+  if (pmg && (m->opts.cheb_degree < 1 || m->opts.cheb_degree >= kMaxChebDegree || m->opts.coarse_iters < 1 ||
+              m->opts.coarse_iters >= kMaxChebDegree)) {
+    m->err = "Chebyshev degrees must be in 1..63";
+    return FNPF_EINVAL;
+  }
   if (pmg && !m->mg) {
     std::string why;
     m->mg = mg_create(g, m->h, m->Xs, m->Ys, m->iso, m->Lx, m->Ly, &why);
@@ -373,12 +429,33 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   const double* eta = m->eta64;
   FNPF_CK(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
   FNPF_CK(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
+  // FP64 solves: the metric is rebuilt from this eta once and read by every
+  // operator application of the solve (fewer FP64 instructions per point)
+  m->g64_active = false;
+  if (!mixed && m->opts.store_metric) {
+    if (!m->G64) {
+      const int64_t ng = (g.dim == 3 ? 6 : 3) * geom_points(g);
+      if (cudaMalloc((void**)&m->G64, ng * sizeof(double)) != cudaSuccess) {
+        m->G64 = nullptr;
+        m->err = "cannot allocate the stored metric";
+        return FNPF_ENOMEM;
+      }
+    }
+    FNPF_CK(launch_geom<double>(g, t, eta, m->G64, s));
+    m->g64_active = true;
+    m->launches += 1;
+  }
+  if (!m->tuned) {
+    const fnpf_status st = autotune(m, eta, m->g64_active ? m->G64 : nullptr, s);
+    if (st != FNPF_OK) return st;
+  }
   if (!mixed && !pmg) {
     FNPF_CK(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
     vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
   }
   if (!mixed && pmg) {
-    FNPF_CK(mg_prepare<double>(m->mg, t, eta, m->ring, m->variant, m->opts.cheb_degree, m->opts.coarse_iters, s));
+    FNPF_CK(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
+                               m->opts.coarse_iters, s));
   }
   FNPF_CK(cudaGetLastError());
   // lift: r = A [0; phis]_I = -b; q = A [x; 0]_I; then b, r = b - q (, z, p)
@@ -408,7 +485,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   const Tables<float> t32 = m->tables32();
   to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
   if (pmg) {
-    FNPF_CK(mg_prepare<float>(m->mg, t32, m->eta32, reinterpret_cast<float*>(m->ring), m->variant,
+    FNPF_CK(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
                               m->opts.cheb_degree, m->opts.coarse_iters, s));
   } else {
     FNPF_CK(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));

@@ -118,11 +118,14 @@ struct AxPtrs {
   T* ys;
   T* ring;
   const int* skip;   // if non-null and *skip != 0 the launch does nothing (converged solve)
+  T* G = nullptr;    // stored metric (AX_GEOM output, AX_APPLY_G input)
 };
+
+enum { AX_APPLY = 0, AX_DIAG = 1, AX_GEOM = 2, AX_APPLY_G = 3 };
 
 // Per-order operator launcher, explicitly instantiated in ax_n<N>.cu.
 template <typename T, int N>
-cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, bool diag, int variant,
+cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, int variant,
                         cudaStream_t s);
 
 // Operator launches (ax_dispatch.cu).  xI == nullptr means zero interior;
@@ -134,6 +137,14 @@ cudaError_t launch_apply(const Geom& g, const Tables<T>& t, const T* eta, const 
 template <typename T>
 cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, T* ds, T* ring, cudaStream_t s);
 int apply_variants(int n, int dim);   // number of elements-per-CTA variants for order n-1
+// Stored metric: G (6 entries per point in 3D, 3 in 2D; geom_points(g) points)
+// computed from eta once, and the operator reading it.
+int64_t geom_points(const Geom& g);
+template <typename T>
+cudaError_t launch_geom(const Geom& g, const Tables<T>& t, const T* eta, T* G, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply_g(const Geom& g, const Tables<T>& t, const T* G, const T* xI, const T* xs, T* yI, T* ys,
+                           T* ring, int variant, cudaStream_t s, const int* skip = nullptr);
 
 // Surface kernels (surface.cu).
 struct StageArgs {

@@ -205,6 +205,7 @@ void free_mesh(fnpf_mesh* m) {
     if (p) cudaFree(p);
   if (m->b) cudaFree(m->b);
   if (m->eta64) cudaFree(m->eta64);
+  if (m->G64) cudaFree(m->G64);
   if (m->sc_in) cudaFree(m->sc_in);
   fnpf::mg_destroy(m->mg);
   for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);
@@ -258,6 +259,7 @@ void fnpf_default_opts(fnpf_opts* o) {
   o->inner_rtol = 1e-5;
   o->max_outer = 20;
   o->use_graphs = 1;
+  o->store_metric = 1;
 }
 
 fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, fnpf_mesh** out) {

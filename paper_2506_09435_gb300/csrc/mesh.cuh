@@ -19,7 +19,11 @@ struct fnpf_mesh {
   fnpf_opts opts{};
   std::string err;
   int device = 0;
-  int variant = 1;                  // elements-per-CTA shape of the apply kernel
+  int variant64 = 1;                // elements-per-CTA shape of the FP64 operator kernel
+  int variant32 = 1;                // ... of the FP32 operator kernel
+  bool tuned = false;               // shapes chosen by the autotuner
+  template <typename T>
+  int variant() const { return sizeof(T) == 4 ? variant32 : variant64; }
 
   // host copies
   std::vector<double> xi, w, D;     // GLL tables
@@ -66,6 +70,8 @@ struct fnpf_mesh {
   float* dinv32 = nullptr;
   double* b = nullptr;              // NI: lifted right-hand side
   double* eta64 = nullptr;          // ns: copy of the solve's eta
+  double* G64 = nullptr;            // stored metric of FP64 solves (allocated at the first one)
+  bool g64_active = false;          // the current FP64 solve reads G64
   fnpf::CgScalars* sc_in = nullptr; // inner-solve scalars
 
   // p-multigrid hierarchy (created at the first FNPF_PMG solve)
@@ -96,6 +102,10 @@ struct fnpf_mesh {
 };
 
 namespace fnpf {
+// Times every elements-per-CTA shape of the FP64 and FP32 operator on this mesh
+// (eta given in FP64; the FP64 timing uses the stored metric G when given) and
+// keeps the fastest of each; synchronises the stream.
+fnpf_status autotune(fnpf_mesh* m, const double* eta, const double* G, cudaStream_t s);
 // Accumulates the recorded event pairs (call after a host sync of the stream).
 void prof_collect(fnpf_mesh* m, int iters_done);
 void graph_reset(GraphSlot* g);

@@ -162,13 +162,20 @@ __global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, int kmax,
   }
   out->lmax = safety * lmax;
   out->range = range;
-}
-
-__device__ inline void cheb_coeffs(const ChebParams* cp, double* theta, double* delta, double* sigma) {
-  const double lmax = cp->lmax, lmin = lmax / cp->range;
-  *theta = 0.5 * (lmax + lmin);
-  *delta = 0.5 * (lmax - lmin);
-  *sigma = *theta / *delta;
+  // Chebyshev recurrence on [lmax / range, lmax]: theta = centre, delta = half
+  // width, sigma = theta / delta, rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1})
+  const double lm = out->lmax, lmin = lm / range;
+  const double theta = 0.5 * (lm + lmin), delta = 0.5 * (lm - lmin), sigma = theta / delta;
+  out->inv_theta = 1.0 / theta;
+  double rho_old = 1.0 / sigma;
+  out->c1[0] = 0.0;
+  out->c2[0] = 0.0;
+  for (int k = 1; k < kMaxChebDegree; ++k) {
+    const double rho = 1.0 / (2.0 * sigma - rho_old);
+    out->c1[k] = rho * rho_old;
+    out->c2[k] = 2.0 * rho / delta;
+    rho_old = rho;
+  }
 }
 
 // Step 0 of a Chebyshev sweep: (r = b if b given); d = dinv r / theta; x = d or x += d.
@@ -176,9 +183,7 @@ template <typename T>
 __global__ void __launch_bounds__(vec::NT) cheb_start_kernel(int64_t n, const T* b, T* r, const T* dinv, T* d, T* x,
                                                              const ChebParams* cp, int x_zero, const int* skip) {
   if (skip && *skip) return;
-  double theta, delta, sigma;
-  cheb_coeffs(cp, &theta, &delta, &sigma);
-  const T it = (T)(1.0 / theta);
+  const T it = (T)cp->inv_theta;
   FNPF_GRID_LOOP(i, n) {
     T rr;
     if (b) {
@@ -198,14 +203,7 @@ template <typename T>
 __global__ void __launch_bounds__(vec::NT) cheb_step_kernel(int64_t n, const T* w, T* r, const T* dinv, T* d, T* x,
                                                             const ChebParams* cp, int k, const int* skip) {
   if (skip && *skip) return;
-  double theta, delta, sigma;
-  cheb_coeffs(cp, &theta, &delta, &sigma);
-  double rho_old = 1.0 / sigma, rho = rho_old;
-  for (int j = 1; j <= k; ++j) {
-    rho = 1.0 / (2.0 * sigma - rho_old);
-    if (j < k) rho_old = rho;
-  }
-  const T c1 = (T)(rho * rho_old), c2 = (T)(2.0 * rho / delta);
+  const T c1 = (T)cp->c1[k], c2 = (T)cp->c2[k];
   FNPF_GRID_LOOP(i, n) {
     const T rn = r[i] - w[i];
     r[i] = rn;
@@ -444,38 +442,47 @@ const T* level_eta(Mg* mg, int l, const T* eta0) {
   return l == 0 ? eta0 : mg->bufs<T>()[l].eta;
 }
 
+// Operator of level l (level 0 reads the stored metric when given).
+template <typename T>
+cudaError_t level_apply(const Geom& g, const Tables<T>& t, const T* eta, const T* G, const T* x, T* y, T* ring,
+                        int variant, const int* skip, cudaStream_t s) {
+  if (G) return launch_apply_g<T>(g, t, G, x, nullptr, y, nullptr, ring, variant, s, skip);
+  return launch_apply<T>(g, t, eta, x, nullptr, y, nullptr, ring, variant, s, skip);
+}
+
 // One Chebyshev sweep of `degree` steps on level l solving A x = b.
 // x_zero: start from x = 0 (r = b, no operator application needed);
 // otherwise r = b - A x first.  With `final_residual` the residual of the
 // result is left in R.
 template <typename T>
-cudaError_t cheb_sweep(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* b, T* x, int degree, bool x_zero,
-                       bool final_residual, T* ring, int variant, const int* skip, cudaStream_t s, int64_t* nl) {
+cudaError_t cheb_sweep(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* G0, const T* b, T* x, int degree,
+                       bool x_zero, bool final_residual, T* ring, int variant, const int* skip, cudaStream_t s,
+                       int64_t* nl) {
+  const T* G = l == 0 ? G0 : nullptr;
   const Geom& g = mg->g[l];
   MgLevelBufs<T>& L = mg->bufs<T>()[l];
   const Tables<T> t = level_tables(mg, l, t0);
   const T* eta = level_eta(mg, l, eta0);
   const ChebParams* cp = mg->cheb<T>() + l;
+  variant = l == 0 ? variant : 1;   // the autotuned shape is for the finest order
   const int nb = vec::blocks_for(g.NI);
   cudaError_t e;
   if (x_zero) {
     cheb_start_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, b, L.R, L.dinv, L.Dd, x, cp, 1, skip);
     *nl += 1;
   } else {
-    if ((e = launch_apply<T>(g, t, eta, x, nullptr, L.W, nullptr, ring, variant, s, skip)) != cudaSuccess) return e;
+    if ((e = level_apply<T>(g, t, eta, G, x, L.W, ring, variant, skip, s)) != cudaSuccess) return e;
     residual_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, b, L.W, L.R, skip);
     cheb_start_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, nullptr, L.R, L.dinv, L.Dd, x, cp, 0, skip);
     *nl += 4;
   }
   for (int k = 1; k < degree; ++k) {
-    if ((e = launch_apply<T>(g, t, eta, L.Dd, nullptr, L.W, nullptr, ring, variant, s, skip)) != cudaSuccess)
-      return e;
+    if ((e = level_apply<T>(g, t, eta, G, L.Dd, L.W, ring, variant, skip, s)) != cudaSuccess) return e;
     cheb_step_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.W, L.R, L.dinv, L.Dd, x, cp, k, skip);
     *nl += 3;
   }
   if (final_residual) {
-    if ((e = launch_apply<T>(g, t, eta, L.Dd, nullptr, L.W, nullptr, ring, variant, s, skip)) != cudaSuccess)
-      return e;
+    if ((e = level_apply<T>(g, t, eta, G, L.Dd, L.W, ring, variant, skip, s)) != cudaSuccess) return e;
     residual_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, nullptr, L.W, L.R, skip);
     *nl += 3;
   }
@@ -483,31 +490,32 @@ cudaError_t cheb_sweep(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const 
 }
 
 template <typename T>
-cudaError_t vcycle(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* b, T* x, T* ring, int variant,
-                   int degree, int coarse_degree, const int* skip, cudaStream_t s, int64_t* nl) {
+cudaError_t vcycle(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* G0, const T* b, T* x, T* ring,
+                   int variant, int degree, int coarse_degree, const int* skip, cudaStream_t s, int64_t* nl) {
   cudaError_t e;
-  if (l == mg->L - 1) return cheb_sweep<T>(mg, l, t0, eta0, b, x, coarse_degree, true, false, ring, variant, skip, s, nl);
+  if (l == mg->L - 1)
+    return cheb_sweep<T>(mg, l, t0, eta0, G0, b, x, coarse_degree, true, false, ring, variant, skip, s, nl);
   MgLevelBufs<T>* Lv = mg->bufs<T>();
-  if ((e = cheb_sweep<T>(mg, l, t0, eta0, b, x, degree, true, true, ring, variant, skip, s, nl)) != cudaSuccess)
+  if ((e = cheb_sweep<T>(mg, l, t0, eta0, G0, b, x, degree, true, true, ring, variant, skip, s, nl)) != cudaSuccess)
     return e;
   // restrict the residual, solve on the next level, prolong and add
   if ((e = launch_transfer(mg->g[l], mg->g[l + 1], Lv[l + 1].J, Lv[l].R, Lv[l + 1].B, ring, 0, skip, s)) !=
       cudaSuccess)
     return e;
-  if ((e = vcycle<T>(mg, l + 1, t0, eta0, Lv[l + 1].B, Lv[l + 1].X, ring, variant, degree, coarse_degree, skip, s,
-                     nl)) != cudaSuccess)
+  if ((e = vcycle<T>(mg, l + 1, t0, eta0, G0, Lv[l + 1].B, Lv[l + 1].X, ring, variant, degree, coarse_degree, skip,
+                     s, nl)) != cudaSuccess)
     return e;
   if ((e = launch_transfer(mg->g[l], mg->g[l + 1], Lv[l + 1].J, Lv[l + 1].X, x, ring, 2, skip, s)) != cudaSuccess)
     return e;
   *nl += 3;
-  return cheb_sweep<T>(mg, l, t0, eta0, b, x, degree, false, false, ring, variant, skip, s, nl);
+  return cheb_sweep<T>(mg, l, t0, eta0, G0, b, x, degree, false, false, ring, variant, skip, s, nl);
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, T* ring, int variant, int cheb_degree,
-                       int coarse_degree, cudaStream_t s) {
+cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, T* ring, int variant,
+                       int cheb_degree, int coarse_degree, cudaStream_t s) {
   (void)cheb_degree;
   cudaError_t e;
   MgLevelBufs<T>* Lv = mg->bufs<T>();
@@ -521,6 +529,7 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, T* ring, int 
     const T* eta = level_eta(mg, l, eta0);
     MgLevelBufs<T>& L = Lv[l];
     const int nb = vec::blocks_for(g.NI);
+    const int lv = l == 0 ? variant : 1;
     if ((e = launch_diag<T>(g, t, eta, L.dinv, nullptr, ring, s)) != cudaSuccess) return e;
     vec::invert_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.dinv);
     // Lanczos through Jacobi-CG: x = X, r = R, z = Dd, p = P, q = W
@@ -530,7 +539,7 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, T* ring, int 
     lz_init_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.R, L.dinv, L.X, L.Dd, L.P, mg->part, nb);
     lz_init_finish_kernel<<<1, vec::NT, 0, s>>>(sc, mg->part, nb);
     for (int it = 0; it < kLanczos; ++it) {
-      if ((e = launch_apply<T>(g, t, eta, L.P, nullptr, L.W, nullptr, ring, variant, s, &sc->done)) != cudaSuccess)
+      if ((e = level_apply<T>(g, t, eta, l == 0 ? G0 : nullptr, L.P, L.W, ring, lv, &sc->done, s)) != cudaSuccess)
         return e;
       vec::dot_kernel<T><<<nb, vec::NT, 0, s>>>(&sc->done, g.NI, L.P, L.W, mg->part + 3 * nb);
       vec::update_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.X, L.R, L.Dd, L.P, L.W, L.dinv, mg->part, nb,
@@ -545,17 +554,19 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, T* ring, int 
 }
 
 template <typename T>
-cudaError_t mg_apply(Mg* mg, const Tables<T>& t0, const T* eta0, const T* r, T* z, T* ring, int variant,
-                     int cheb_degree, int coarse_degree, const int* skip, cudaStream_t s, int64_t* launches) {
-  return vcycle<T>(mg, 0, t0, eta0, r, z, ring, variant, cheb_degree, coarse_degree, skip, s, launches);
+cudaError_t mg_apply(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, const T* r, T* z, T* ring,
+                     int variant, int cheb_degree, int coarse_degree, const int* skip, cudaStream_t s,
+                     int64_t* launches) {
+  return vcycle<T>(mg, 0, t0, eta0, G0, r, z, ring, variant, cheb_degree, coarse_degree, skip, s, launches);
 }
 
-template cudaError_t mg_prepare<double>(Mg*, const Tables<double>&, const double*, double*, int, int, int,
-                                        cudaStream_t);
-template cudaError_t mg_prepare<float>(Mg*, const Tables<float>&, const float*, float*, int, int, int, cudaStream_t);
-template cudaError_t mg_apply<double>(Mg*, const Tables<double>&, const double*, const double*, double*, double*, int,
-                                      int, int, const int*, cudaStream_t, int64_t*);
-template cudaError_t mg_apply<float>(Mg*, const Tables<float>&, const float*, const float*, float*, float*, int, int,
-                                     int, const int*, cudaStream_t, int64_t*);
+template cudaError_t mg_prepare<double>(Mg*, const Tables<double>&, const double*, const double*, double*, int, int,
+                                        int, cudaStream_t);
+template cudaError_t mg_prepare<float>(Mg*, const Tables<float>&, const float*, const float*, float*, int, int, int,
+                                       cudaStream_t);
+template cudaError_t mg_apply<double>(Mg*, const Tables<double>&, const double*, const double*, const double*,
+                                      double*, double*, int, int, int, const int*, cudaStream_t, int64_t*);
+template cudaError_t mg_apply<float>(Mg*, const Tables<float>&, const float*, const float*, const float*, float*,
+                                     float*, int, int, int, const int*, cudaStream_t, int64_t*);
 
 }  // namespace fnpf

@@ -7,11 +7,18 @@
 
 namespace fnpf {
 
+constexpr int kMaxChebDegree = 64;
+
 // Chebyshev interval of one level, written on the device by the Lanczos
 // eigenvalue kernel: smoothing targets [lmax / range, lmax].
 struct ChebParams {
   double lmax;
   double range;
+  // step coefficients precomputed by one thread: step 0 uses d = inv_theta dinv r,
+  // step k >= 1 uses d = c1[k] d + c2[k] dinv r
+  double inv_theta;
+  double c1[kMaxChebDegree];
+  double c2[kMaxChebDegree];
 };
 
 // Device buffers of one level in precision T.  Level 0 is the mesh itself: its
@@ -44,13 +51,15 @@ int mg_levels(const Mg* mg);
 // the Chebyshev intervals from a short Lanczos run per level (all on the
 // device, no host synchronisation).  eta0 is the fine eta in precision T,
 // t0 the fine tables, dinv0/R0.. fine scratch supplied by the mesh.
+// G0, if non-null, is the stored metric of level 0 (the operator there reads it).
 template <typename T>
-cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, T* ring, int variant, int cheb_degree,
-                       int coarse_degree, cudaStream_t s);
+cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, T* ring, int variant,
+                       int cheb_degree, int coarse_degree, cudaStream_t s);
 
 // z = M r (one symmetric V-cycle); kernels exit at once when *skip != 0.
 template <typename T>
-cudaError_t mg_apply(Mg* mg, const Tables<T>& t0, const T* eta0, const T* r, T* z, T* ring, int variant,
-                     int cheb_degree, int coarse_degree, const int* skip, cudaStream_t s, int64_t* launches);
+cudaError_t mg_apply(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, const T* r, T* z, T* ring,
+                     int variant, int cheb_degree, int coarse_degree, const int* skip, cudaStream_t s,
+                     int64_t* launches);
 
 }  // namespace fnpf

@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(NT) update_kernel(CgScalars* sc, int it, int64
                                                     const T* q, const T* dinv, double* part, int nb, double* hist) {
   if (sc->done) return;
   __shared__ double sh[NT / 32];
+  __shared__ double s_alpha;
   const double pq = reduce_partials(part + 3 * nb, nb, sh);
-  const double rz = sc->rz[it & 1];
   if (!(pq > 0.0) || !isfinite(pq)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       sc->status = FNPF_EBREAKDOWN;
@@ -79,9 +79,13 @@ __global__ void __launch_bounds__(NT) update_kernel(CgScalars* sc, int it, int64
     }
     return;
   }
-  const double alpha_d = rz / pq;
-  if (hist && blockIdx.x == 0 && threadIdx.x == 0) hist[2 * it] = alpha_d;
-  const T alpha = (T)alpha_d;
+  // one FP64 division per block (FP64 is the slow pipe on this GPU)
+  if (threadIdx.x == 0) {
+    s_alpha = sc->rz[it & 1] / pq;
+    if (hist && blockIdx.x == 0) hist[2 * it] = s_alpha;
+  }
+  __syncthreads();
+  const T alpha = (T)s_alpha;
   double srz = 0, srr = 0;
   FNPF_GRID_LOOP(i, n) {
     x[i] += alpha * p[i];
@@ -111,9 +115,12 @@ __global__ void __launch_bounds__(NT) pupdate_kernel(CgScalars* sc, int it, int6
                                                      const double* part, int nb, double* hist) {
   if (sc->done) return;
   __shared__ double sh[NT / 32];
+  __shared__ double s_beta;
   const double rz_new = reduce_partials(part + nb, nb, sh);
   const double rr = reduce_partials(part + 2 * nb, nb, sh);
-  const double beta_d = rz_new / sc->rz[it & 1];
+  if (threadIdx.x == 0) s_beta = rz_new / sc->rz[it & 1];
+  __syncthreads();
+  const double beta_d = s_beta;
   const T beta = (T)beta_d;
   FNPF_GRID_LOOP(i, n) p[i] = z[i] + beta * p[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) {

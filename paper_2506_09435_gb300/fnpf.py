@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int), ("store_metric", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -65,6 +65,7 @@ def load():
         "fnpf_zakharov_rhs": [vp, vp, vp, vp, vp, vp, vp],
         "fnpf_rk4_step": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(SolveInfo), vp],
         "fnpf_apply_noalloc": [ctypes.POINTER(MeshDesc), vp, vp, vp, vp, vp],
+        "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
         "fnpf_profile_enable": [vp, ctypes.c_int],
         "fnpf_profile_read": [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p, ctypes.c_int],
         "fnpf_profile_read_fp32": [vp, ctypes.POINTER(ctypes.c_double), i64p],
@@ -225,6 +226,11 @@ class Mesh:
     def zakharov_rhs(self, eta, phis, w, deta, dphis, stream=None):
         self._check(_LIB.fnpf_zakharov_rhs(self._h, _ptr(eta), _ptr(phis), _ptr(w), _ptr(deta), _ptr(dphis),
                                            _stream(stream)))
+
+    def autotune(self, eta, stream=None):
+        v64, v32 = ctypes.c_int(), ctypes.c_int()
+        self._check(_LIB.fnpf_autotune(self._h, _ptr(eta), ctypes.byref(v64), ctypes.byref(v32), _stream(stream)))
+        return v64.value, v32.value
 
     def profile_enable(self, on=True):
         self._check(_LIB.fnpf_profile_enable(self._h, int(on)))

@@ -78,3 +78,20 @@ def test_graph_replay_is_bitwise_identical_to_plain_launches(fnpf, precision):
         torch.cuda.synchronize()
         out.append((eta.cpu().numpy(), phis.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "pmg"])
+def test_stored_metric_matches_on_the_fly_metric(fnpf, precond):
+    """FP64 solves reading the metric stored once per solve give the solution
+    of the solves that rebuild it per application (and of the oracle)."""
+    pre = fnpf.FNPF_PMG if precond == "pmg" else fnpf.FNPF_JACOBI
+    shape = (3, 5, 4, 2, 5, True, False)
+    sol = []
+    for store in (0, 1):
+        c = Case(fnpf, *shape, opts=fnpf.default_opts(rtol=1e-13, precond=pre, store_metric=store, max_iter=20000))
+        phi = torch.zeros(c.om.N, dtype=torch.float64, device=c.dev)
+        assert c.gm.laplace_solve(c.t(c.eta), c.t(c.phis), phi)["status"] == 0
+        sol.append(phi.cpu().numpy())
+    assert rel_l2(sol[1], sol[0]) < 1e-12
+    phi_ref = osolve.laplace_solve(c.om, c.eta, c.h, c.phis)
+    assert rel_l2(sol[1], phi_ref) < 1e-10
