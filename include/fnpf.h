@@ -156,8 +156,9 @@ fnpf_status fnpf_zakharov_rhs(fnpf_mesh* mesh, const double* eta, const double* 
                               double* deta, double* dphis, void* stream);
 
 /* One classical RK4 step (Sec. 3.2) of the state (eta, phis) [Ns], in place:
- * four DtN solves and right-hand sides.  info may be NULL or point to 4
- * structs (one per stage; then the call waits for the stream). */
+ * four DtN solves and right-hand sides, then the relaxation zones (if set)
+ * with the targets at time t + dt.  info may be NULL or point to 4 structs
+ * (one per stage; then the call waits for the stream). */
 fnpf_status fnpf_rk4_step(fnpf_mesh* mesh, double* eta, double* phis, double t, double dt,
                           fnpf_solve_info* info, void* stream);
 
@@ -201,6 +202,23 @@ fnpf_status fnpf_profile_read(fnpf_mesh* mesh, double* apply_ms, int64_t* apply_
 /* The same totals for the FP32 operator applications of FNPF_MIXED solves
  * (fnpf_profile_read above reports the FP64 ones; its reset clears both). */
 fnpf_status fnpf_profile_read_fp32(fnpf_mesh* mesh, double* apply_ms, int64_t* apply_count);
+
+/* Relaxation zones (Sec. 3.3; Step 4.7 of Sec. 3.4): after every RK4 step,
+ * f <- (1 - C_r) f + C_r f_true for f in {eta, phi_eta}.  In generation nodes
+ * (gen = 1) the target is the linear incident wave
+ *   eta_I = a cos(kx x + ky y - omega t + phase),
+ *   phi_I = (g a / omega) cosh(k (eta_I + h)) / cosh(k h) sin(kx x + ky y - omega t + phase),
+ * k = |(kx, ky)|, h the node's depth, multiplied by the ramp min(1, t / ramp_time)
+ * (the paper activates generation over five wave periods); in absorption nodes
+ * (gen = 0) the target is 0.  C_r = 0 leaves a node untouched.  cr and gen
+ * are HOST arrays [Ns], copied; a NULL cr removes the relaxation. */
+typedef struct {
+  const double* cr;        /* [Ns] relaxation weight in [0, 1]                  */
+  const double* gen;       /* [Ns] 1: generation target, 0: absorption target   */
+  double amp, kx, ky, omega, phase;
+  double ramp_time;        /* > 0 */
+} fnpf_relaxation;
+fnpf_status fnpf_set_relaxation(fnpf_mesh* mesh, const fnpf_relaxation* relax);
 
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */

@@ -93,6 +93,30 @@ def relax(f, f_true, cr):
     return (1 - cr) * f + cr * f_true
 
 
+def incident_wave(x, y, h, t, amp, kx, ky, omega, phase, g, ramp_time):
+    """Linear incident wave of Sec. 3.3's generation zone at time t, multiplied by
+    the generation ramp min(1, t / ramp_time) (the paper ramps generation over five
+    wave periods; reading: a linear ramp applied to the target).  The potential
+    is the linear one evaluated at the (ramped) target elevation."""
+    r = min(1.0, t / ramp_time)
+    th = kx * x + ky * y - omega * t + phase
+    k = np.hypot(kx, ky)
+    eta = r * amp * np.cos(th)
+    phi = r * (g * amp / omega) * np.cosh(k * (eta + h)) / np.cosh(k * h) * np.sin(th)
+    return eta, phi
+
+
+def relaxation_step(mesh, h, eta, phis, t, dt, g, cr, gen, wave, linear=False, method="direct"):
+    """One RK4 step followed by the relaxation-zone blend with targets at t + dt:
+    the incident wave where gen = 1, zero where gen = 0 (Sec. 3.3, Step 4.7)."""
+    eta, phis = rk4_step(mesh, h, eta, phis, dt, g, linear=linear, method=method)
+    x, y = mesh.surface_coords()
+    te, tp = incident_wave(x, y, h, t + dt, g=g, **wave)
+    te = np.where(gen != 0, te, 0.0)
+    tp = np.where(gen != 0, tp, 0.0)
+    return relax(eta, te, cr), relax(phis, tp, cr)
+
+
 def mass(mesh, eta):
     return float(lumped_mass(mesh) @ eta)
 

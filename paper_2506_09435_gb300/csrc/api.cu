@@ -111,12 +111,64 @@ fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, dou
     a.first = st == 0;
     a.last = st == 3;
     a.status = &m->sc->status;
+    if (st == 3 && m->relax_on) {
+      a.cr = m->rx_cr;
+      a.gen = m->rx_gen;
+      a.xs = m->dxs;
+      a.ys = m->dys;
+      a.amp = m->relax.amp;
+      a.kx = m->relax.kx;
+      a.ky = m->relax.ky;
+      a.omega = m->relax.omega;
+      a.phase = m->relax.phase;
+      a.ramp_time = m->relax.ramp_time;
+      a.t_end = t + dt;
+    }
     cudaError_t e = fnpf::launch_stage(m->g, m->tables(), a, s);
     m->launches += 1;
     if (e != cudaSuccess) return cuda_fail(m, e, "stage");
     ce = a.out_eta;
     cp = a.out_phi;
   }
+  return FNPF_OK;
+}
+
+fnpf_status fnpf_set_relaxation(fnpf_mesh* m, const fnpf_relaxation* r) {
+  if (!m || !r) return FNPF_EINVAL;
+  if (!r->cr) {
+    m->relax_on = false;
+    return FNPF_OK;
+  }
+  if (!r->gen || !(r->ramp_time > 0) || !(r->omega > 0)) {
+    m->err = "relaxation needs gen, omega > 0 and ramp_time > 0";
+    return FNPF_EINVAL;
+  }
+  const Geom& g = m->g;
+  for (int c = 0; c < g.ns; ++c)
+    if (!(r->cr[c] >= 0.0 && r->cr[c] <= 1.0)) {
+      m->err = "relaxation weights must lie in [0, 1]";
+      return FNPF_EINVAL;
+    }
+  const size_t bytes = g.ns * sizeof(double);
+  double** bufs[] = {&m->rx_cr, &m->rx_gen, &m->dxs, &m->dys};
+  for (double** b : bufs)
+    if (!*b) {
+      cudaError_t e = cudaMalloc((void**)b, bytes);
+      if (e != cudaSuccess) {
+        *b = nullptr;
+        m->err = "cannot allocate relaxation arrays";
+        return FNPF_ENOMEM;
+      }
+    }
+  cudaError_t e = cudaMemcpy(m->rx_cr, r->cr, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->rx_gen, r->gen, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->dxs, m->xs.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->dys, m->ys.data(), bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(m, e, "relaxation upload");
+  m->relax = *r;
+  m->relax.cr = nullptr;
+  m->relax.gen = nullptr;
+  m->relax_on = true;
   return FNPF_OK;
 }
 

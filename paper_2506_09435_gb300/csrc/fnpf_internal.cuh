@@ -165,6 +165,12 @@ struct StageArgs {
   double* dphis;
   const double* w_in;    // if non-null, use this w instead of recovering it from phi
   int* status;           // set to FNPF_EDIVERGED on a non-finite or folded state
+  // relaxation after the last stage (cr null: none)
+  const double* cr;
+  const double* gen;
+  const double* xs;      // surface-node coordinates
+  const double* ys;
+  double amp, kx, ky, omega, phase, ramp_time, t_end;
 };
 cudaError_t launch_stage(const Geom& g, const Tables<double>& t, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_w(const Geom& g, const Tables<double>& t, const double* eta, const double* phis,

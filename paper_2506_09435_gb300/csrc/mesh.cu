@@ -206,6 +206,9 @@ void free_mesh(fnpf_mesh* m) {
   if (m->b) cudaFree(m->b);
   if (m->eta64) cudaFree(m->eta64);
   if (m->G64) cudaFree(m->G64);
+  double* rptrs[] = {m->rx_cr, m->rx_gen, m->dxs, m->dys};
+  for (double* p : rptrs)
+    if (p) cudaFree(p);
   if (m->sc_in) cudaFree(m->sc_in);
   fnpf::mg_destroy(m->mg);
   for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);

@@ -74,6 +74,14 @@ struct fnpf_mesh {
   bool g64_active = false;          // the current FP64 solve reads G64
   fnpf::CgScalars* sc_in = nullptr; // inner-solve scalars
 
+  // relaxation zones (fnpf_set_relaxation)
+  double* rx_cr = nullptr;          // ns
+  double* rx_gen = nullptr;         // ns
+  double* dxs = nullptr;            // ns surface coordinates on the device
+  double* dys = nullptr;
+  fnpf_relaxation relax{};          // scalar parameters (array pointers unused)
+  bool relax_on = false;
+
   // p-multigrid hierarchy (created at the first FNPF_PMG solve)
   fnpf::Mg* mg = nullptr;
   bool iso = false;

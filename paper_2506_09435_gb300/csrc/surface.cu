@@ -87,8 +87,25 @@ __global__ void stage_kernel(Geom g, Tables<double> t, StageArgs a) {
     const double acc_p = (a.first ? 0.0 : a.acc_phi[col]) + a.bw * kp;
     const double y0e = a.y0_eta[col], y0p = a.y0_phi[col];
     if (a.last) {
-      a.out_eta[col] = y0e + a.dt * acc_e;
-      a.out_phi[col] = y0p + a.dt * acc_p;
+      double ye = y0e + a.dt * acc_e, yp = y0p + a.dt * acc_p;
+      if (a.cr) {
+        // relaxation zones: f <- (1 - C_r) f + C_r f_true at t + dt
+        const double c = a.cr[col];
+        if (c != 0.0) {
+          double te = 0.0, tp = 0.0;
+          if (a.gen[col] != 0.0) {
+            const double ramp = fmin(1.0, a.t_end / a.ramp_time);
+            const double th = a.kx * a.xs[col] + a.ky * a.ys[col] - a.omega * a.t_end + a.phase;
+            const double k = hypot(a.kx, a.ky);
+            te = ramp * a.amp * cos(th);
+            tp = ramp * (g.g * a.amp / a.omega) * cosh(k * (te + hh)) / cosh(k * hh) * sin(th);
+          }
+          ye = (1.0 - c) * ye + c * te;
+          yp = (1.0 - c) * yp + c * tp;
+        }
+      }
+      a.out_eta[col] = ye;
+      a.out_phi[col] = yp;
     } else {
       a.acc_eta[col] = acc_e;
       a.acc_phi[col] = acc_p;

@@ -45,6 +45,12 @@ class SolveInfo(ctypes.Structure):
                     ms=self.ms)
 
 
+class Relaxation(ctypes.Structure):
+    _fields_ = [("cr", _dp), ("gen", _dp), ("amp", ctypes.c_double), ("kx", ctypes.c_double),
+                ("ky", ctypes.c_double), ("omega", ctypes.c_double), ("phase", ctypes.c_double),
+                ("ramp_time", ctypes.c_double)]
+
+
 def load():
     if not os.path.exists(LIB_PATH):
         raise RuntimeError("libfnpf.so is not built (run __graft_entry__.build() or "
@@ -65,6 +71,7 @@ def load():
         "fnpf_zakharov_rhs": [vp, vp, vp, vp, vp, vp, vp],
         "fnpf_rk4_step": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(SolveInfo), vp],
         "fnpf_apply_noalloc": [ctypes.POINTER(MeshDesc), vp, vp, vp, vp, vp],
+        "fnpf_set_relaxation": [vp, ctypes.POINTER(Relaxation)],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
         "fnpf_profile_enable": [vp, ctypes.c_int],
         "fnpf_profile_read": [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p, ctypes.c_int],
@@ -226,6 +233,19 @@ class Mesh:
     def zakharov_rhs(self, eta, phis, w, deta, dphis, stream=None):
         self._check(_LIB.fnpf_zakharov_rhs(self._h, _ptr(eta), _ptr(phis), _ptr(w), _ptr(deta), _ptr(dphis),
                                            _stream(stream)))
+
+    def set_relaxation(self, cr, gen, amp=0.0, kx=0.0, ky=0.0, omega=1.0, phase=0.0, ramp_time=1.0):
+        """Relaxation zones applied after every RK4 step (cr=None removes them)."""
+        if cr is None:
+            r = Relaxation(omega=1.0, ramp_time=1.0)
+            self._check(_LIB.fnpf_set_relaxation(self._h, ctypes.byref(r)))
+            return
+        cr = np.ascontiguousarray(cr, dtype=np.float64)
+        gen = np.ascontiguousarray(gen, dtype=np.float64)
+        r = Relaxation(amp=amp, kx=kx, ky=ky, omega=omega, phase=phase, ramp_time=ramp_time)
+        r.cr = cr.ctypes.data_as(_dp)
+        r.gen = gen.ctypes.data_as(_dp)
+        self._check(_LIB.fnpf_set_relaxation(self._h, ctypes.byref(r)))
 
     def autotune(self, eta, stream=None):
         v64, v32 = ctypes.c_int(), ctypes.c_int()

@@ -67,6 +67,68 @@ def periodic_box_3d(nx=32, ny=32, nz=2, p=6, kh=2.0, L=1.0, g=G_DEFAULT):
                 Lx=L, Ly=L, h0=kh / k0, k=k0, g=g)
 
 
+def wavenumber(omega_, h, g=G_DEFAULT):
+    """k with omega^2 = g k tanh(k h) (Newton on the dispersion relation)."""
+    k = omega_ * omega_ / g
+    for _ in range(100):
+        f = g * k * math.tanh(k * h) - omega_ * omega_
+        df = g * math.tanh(k * h) + g * k * h / math.cosh(k * h) ** 2
+        dk = f / df
+        k -= dk
+        if abs(dk) < 1e-15 * k:
+            break
+    return k
+
+
+def bar_flume(nx=256, ny=16, nz=3, p=5, Lx=38.0, Ly=1.0, g=G_DEFAULT):
+    """Walled wave flume over a submerged trapezoidal bar (the shape of the
+    paper's Beji-Battjes case): depth 0.4 m, a 1:20 slope from x = 14 m up to
+    0.1 m at x = 20 m, crest to x = 22 m, a 1:10 slope back to 0.4 m at x = 25 m.
+    Incident wave T = 2.02 s, H = 0.02 m; generation zone over the first 8 m,
+    absorption zone over the last 8 m."""
+    T = 2.02
+    om = 2 * math.pi / T
+    return dict(dim=3, nx=nx, ny=ny, nz=nz, p=p, periodic_x=False, periodic_y=False, Lx=Lx, Ly=Ly, h0=0.4,
+                g=g, T=T, omega=om, k=wavenumber(om, 0.4, g), amp=0.01, zone=8.0)
+
+
+def bar_depth(x):
+    x = np.asarray(x, dtype=np.float64)
+    h = np.full_like(x, 0.4)
+    up = (x >= 14.0) & (x < 20.0)
+    h[up] = 0.4 - (x[up] - 14.0) / 20.0
+    h[(x >= 20.0) & (x <= 22.0)] = 0.1
+    dn = (x > 22.0) & (x < 25.0)
+    h[dn] = 0.1 + (x[dn] - 22.0) / 10.0
+    return h
+
+
+def relaxation_weight(xi):
+    """C_r on a zone coordinate xi in [0, 1] (0 at the domain edge, 1 at the
+    target side): 1 - (exp(xi^3.5) - 1) / (e - 1)."""
+    xi = np.clip(np.asarray(xi, dtype=np.float64), 0.0, 1.0)
+    return 1.0 - (np.exp(xi ** 3.5) - 1.0) / (math.e - 1.0)
+
+
+def flume_zones(desc, x):
+    """(C_r, gen) at surface nodes x: generation zone [0, zone], absorption zone
+    [Lx - zone, Lx]."""
+    zone, Lx = desc["zone"], desc["Lx"]
+    cr = np.zeros_like(x)
+    gen = np.zeros_like(x)
+    g_ = x <= zone
+    cr[g_] = relaxation_weight(x[g_] / zone)
+    gen[g_] = 1.0
+    a_ = x >= Lx - zone
+    cr[a_] = relaxation_weight((Lx - x[a_]) / zone)
+    return cr, gen
+
+
+def flume_wave(desc):
+    """Incident-wave parameters of the relaxation (linear wave along +x)."""
+    return dict(amp=desc["amp"], kx=desc["k"], ky=0.0, omega=desc["omega"], phase=0.0, ramp_time=5 * desc["T"])
+
+
 def dof_counts(desc):
     """Global volume and surface node counts of a structured extruded mesh."""
     p = desc["p"]

@@ -110,3 +110,36 @@ def test_energy_nearly_conserved_nonlinear_3d():
     E1 = surface.energy(m, h, eta, phis, g)
     assert abs(E1 / E0 - 1) < 1e-4
     assert abs(surface.mass(m, eta) - M0) < 1e-5 * np.max(np.abs(eta)) * d["Lx"] * d["Ly"]
+
+
+def test_relaxation_blend_and_target():
+    """Pins of the relaxation step: C_r = 1 replaces the state by the target,
+    C_r = 0 leaves it; the generation target at the ramp's end is the linear
+    Airy wave (eta = a cos(kx - wt), phi_eta = (g a / w) sin(...) at z = 0 for
+    deep ramps); the weight function is 1 at the edge and 0 at the target side."""
+    assert abs(workloads.relaxation_weight(0.0) - 1) < 1e-15
+    assert abs(workloads.relaxation_weight(1.0)) < 1e-15
+    xi = np.linspace(0, 1, 11)
+    assert np.all(np.diff(workloads.relaxation_weight(xi)) < 0)
+    f = np.array([1.0, 2.0, 3.0])
+    ft = np.array([5.0, 5.0, 5.0])
+    assert np.array_equal(surface.relax(f, ft, np.array([0.0, 1.0, 0.5])), np.array([1.0, 5.0, 4.0]))
+    x = np.linspace(0, 3, 7)
+    h = np.full_like(x, 0.4)
+    g = 9.81
+    k = workloads.wavenumber(2 * math.pi / 2.02, 0.4, g)
+    om = 2 * math.pi / 2.02
+    assert abs(om ** 2 - g * k * math.tanh(k * 0.4)) < 1e-12
+    e, p = surface.incident_wave(x, 0 * x, h, 20.0, 1e-9, k, 0.0, om, 0.0, g, 10.0)
+    th = k * x - om * 20.0
+    assert np.max(np.abs(e - 1e-9 * np.cos(th))) < 1e-24
+    assert np.max(np.abs(p - g * 1e-9 / om * np.sin(th))) < 1e-7 * g * 1e-9 / om
+    e2, _ = surface.incident_wave(x, 0 * x, h, 5.0, 1e-3, k, 0.0, om, 0.0, g, 10.0)
+    assert np.max(np.abs(e2 - 0.5e-3 * np.cos(k * x - om * 5.0))) < 1e-15
+
+
+def test_bar_depth_profile():
+    x = np.array([0.0, 14.0, 17.0, 20.0, 21.0, 22.0, 23.5, 25.0, 30.0])
+    assert np.allclose(workloads.bar_depth(x), [0.4, 0.4, 0.25, 0.1, 0.1, 0.1, 0.25, 0.4, 0.4])
+    d = workloads.bar_flume()
+    assert workloads.dof_counts(d) == (1660176, 103761)
