@@ -158,7 +158,10 @@ fnpf_status fnpf_zakharov_rhs(fnpf_mesh* mesh, const double* eta, const double* 
 /* One classical RK4 step (Sec. 3.2) of the state (eta, phis) [Ns], in place:
  * four DtN solves and right-hand sides, then the relaxation zones (if set)
  * with the targets at time t + dt.  info may be NULL or point to 4 structs
- * (one per stage; then the call waits for the stream). */
+ * (one per stage).  The first call runs host-driven solves; later calls (with
+ * use_graphs and instrumentation off) replay one captured CUDA graph per step
+ * whose CG loops are conditional WHILE nodes evaluated on the device, and wait
+ * for the stream once (re-captured when eta, phis or dt change). */
 fnpf_status fnpf_rk4_step(fnpf_mesh* mesh, double* eta, double* phis, double t, double dt,
                           fnpf_solve_info* info, void* stream);
 
@@ -219,6 +222,23 @@ typedef struct {
   double ramp_time;        /* > 0 */
 } fnpf_relaxation;
 fnpf_status fnpf_set_relaxation(fnpf_mesh* mesh, const fnpf_relaxation* relax);
+
+/* Ensembles of independent tanks (batched form).  An ensemble groups existing
+ * meshes (not owned; they must outlive it).  fnpf_ensemble_rk4_step advances
+ * tank i by one RK4 step of size dts[i] from time ts[i], state etas[i],
+ * phiss[i] (device arrays, in place), exactly as fnpf_rk4_step would: from the
+ * second call on, all tanks' steps run as one launch of a captured CUDA graph
+ * (fork/join branches, device-side CG loops), with one host synchronisation per
+ * ensemble step; the first call steps each tank on its own (set-up, autotuning).
+ * The graph is re-captured when a state pointer or step size changes.  info may
+ * be NULL or point to 4 n structs (tank-major).  Returns the first failing
+ * tank's status; fnpf_ensemble_last_error names it. */
+typedef struct fnpf_ensemble fnpf_ensemble;
+fnpf_status fnpf_ensemble_create(fnpf_mesh* const* meshes, int n, fnpf_ensemble** out);
+void fnpf_ensemble_destroy(fnpf_ensemble* ens);
+fnpf_status fnpf_ensemble_rk4_step(fnpf_ensemble* ens, double* const* etas, double* const* phiss, const double* ts,
+                                   const double* dts, fnpf_solve_info* info, void* stream);
+const char* fnpf_ensemble_last_error(const fnpf_ensemble* ens);
 
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */

@@ -83,53 +83,155 @@ fnpf_status fnpf_zakharov_rhs(fnpf_mesh* m, const double* eta, const double* phi
   return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "rhs");
 }
 
-fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, double dt, fnpf_solve_info* info,
-                          void* stream) {
-  (void)t;
-  if (!m || !eta || !phis || !(dt > 0) || !isfinite(dt)) return FNPF_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace fnpf {
+
+// Stage arguments of RK4 stage st (0..3) reading the stage state (ce, cp).
+StageArgs stage_args(fnpf_mesh* m, double* eta, double* phis, const double* ce, const double* cp, int st, double t,
+                     double dt, const double* t_dev) {
   static const double bw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const double cn[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+  StageArgs a{};
+  a.eta = ce;
+  a.phis = cp;
+  a.phi = m->phi;
+  a.y0_eta = eta;
+  a.y0_phi = phis;
+  a.acc_eta = m->acc_eta;
+  a.acc_phi = m->acc_phi;
+  a.out_eta = st < 3 ? m->s_eta[st & 1] : eta;
+  a.out_phi = st < 3 ? m->s_phi[st & 1] : phis;
+  a.bw = bw[st];
+  a.cn = cn[st];
+  a.dt = dt;
+  a.first = st == 0;
+  a.last = st == 3;
+  a.status = &m->sc->status;
+  if (st == 3 && m->relax_on) {
+    a.cr = m->rx_cr;
+    a.gen = m->rx_gen;
+    a.xs = m->dxs;
+    a.ys = m->dys;
+    a.amp = m->relax.amp;
+    a.kx = m->relax.kx;
+    a.ky = m->relax.ky;
+    a.omega = m->relax.omega;
+    a.phase = m->relax.phase;
+    a.ramp_time = m->relax.ramp_time;
+    a.t_end = t + dt;
+    a.t_dev = t_dev;
+  }
+  return a;
+}
+
+// Captures one RK4 step of mesh m (state arrays eta, phis, step dt; the time is
+// read from m->t_dev) on the capturing stream s: four device-driven solves and
+// stage kernels, then the per-stage summaries copied to pinned host memory.
+cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cudaStream_t s) {
+  const double* ce = eta;
+  const double* cp = phis;
+  for (int st = 0; st < 4; ++st) {
+    cudaError_t e = enqueue_solve_device(m, ce, cp, m->phi, m->stage_info + st, s);
+    if (e != cudaSuccess) return e;
+    const StageArgs a = stage_args(m, eta, phis, ce, cp, st, 0.0, dt, m->t_dev);
+    if ((e = launch_stage(m->g, m->tables(), a, s)) != cudaSuccess) return e;
+    ce = a.out_eta;
+    cp = a.out_phi;
+  }
+  return cudaMemcpyAsync(m->stage_info_host, m->stage_info, 4 * sizeof(StageInfo), cudaMemcpyDeviceToHost, s);
+}
+
+// Reads the per-stage summaries after a replayed step (stream synchronised) and
+// adds the kernels the replay executed to the launch counter: the top-level
+// kernel nodes plus the loop bodies once per body execution (a CG body holds
+// two iterations).
+fnpf_status read_step_info(fnpf_mesh* m, fnpf_solve_info* info, float ms) {
+  fnpf_status st = FNPF_OK;
+  const bool mixed = m->opts.precision == FNPF_MIXED;
+  m->launches += m->step_kernels;
+  for (int k = 0; k < 4; ++k) {
+    const StageInfo& si = m->stage_info_host[k];
+    if (mixed) m->launches += si.outer * m->body_kernels[0] + (si.iters + 1) / 2 * m->body_kernels[1];
+    else m->launches += (si.iters + 1) / 2 * m->body_kernels[0];
+    if (si.status != 0 && st == FNPF_OK) st = (fnpf_status)si.status;
+    if (info) {
+      info[k].iters = si.iters;
+      info[k].outer_iters = si.outer;
+      info[k].rel_res = si.bb > 0 ? sqrt(si.rr / si.bb) : 0.0;
+      info[k].status = si.status;
+      info[k].ms = ms / 4;
+    }
+  }
+  if (st == FNPF_ENOCONV) m->err = "solver reached its iteration cap before the tolerance";
+  else if (st == FNPF_EBREAKDOWN) m->err = "CG breakdown (p^T A p <= 0 or non-finite)";
+  else if (st == FNPF_EDIVERGED) m->err = "non-finite state or eta + h <= 0";
+  return st;
+}
+
+cudaError_t build_step_graph(fnpf_mesh* m, double* eta, double* phis, double dt) {
+  if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
+  m->step_exec = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(m->gstream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t e1 = enqueue_step(m, eta, phis, dt, m->gstream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(m->gstream, &graph);
+  if (e1 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return e1;
+  }
+  if (e2 != cudaSuccess) return e2;
+  m->step_kernels = graph_kernel_nodes(graph);
+  e = cudaGraphInstantiate(&m->step_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return e;
+  m->step_key[0] = eta;
+  m->step_key[1] = phis;
+  m->step_dt = dt;
+  return cudaSuccess;
+}
+
+bool graph_mode(const fnpf_mesh* m) { return m->opts.use_graphs && !m->prof_on && m->warm; }
+
+}  // namespace fnpf
+
+extern "C" {
+
+fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, double dt, fnpf_solve_info* info,
+                          void* stream) {
+  if (!m || !eta || !phis || !(dt > 0) || !isfinite(dt)) return FNPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (fnpf::graph_mode(m)) {
+    // one replay of the captured step: no host work between the kernels
+    if (!m->step_exec || m->step_key[0] != eta || m->step_key[1] != phis || m->step_dt != dt) {
+      cudaError_t e = fnpf::build_step_graph(m, eta, phis, dt);
+      if (e != cudaSuccess) return cuda_fail(m, e, "step graph capture");
+    }
+    *m->t_host = t;
+    cudaError_t e = cudaMemcpyAsync(m->t_dev, m->t_host, sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && info) e = cudaEventRecord(m->ev0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(m->step_exec, s);
+    if (e == cudaSuccess && info) e = cudaEventRecord(m->ev1, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(m, e, "step graph");
+    float ms = 0;
+    if (info) cudaEventElapsedTime(&ms, m->ev0, m->ev1);
+    return fnpf::read_step_info(m, info, ms);
+  }
   const double* ce = eta;
   const double* cp = phis;
   for (int st = 0; st < 4; ++st) {
     fnpf_status r = fnpf::cg_solve(m, ce, cp, m->phi, info ? info + st : nullptr, s);
     if (r != FNPF_OK) return r;
-    fnpf::StageArgs a{};
-    a.eta = ce;
-    a.phis = cp;
-    a.phi = m->phi;
-    a.y0_eta = eta;
-    a.y0_phi = phis;
-    a.acc_eta = m->acc_eta;
-    a.acc_phi = m->acc_phi;
-    a.out_eta = st < 3 ? m->s_eta[st & 1] : eta;
-    a.out_phi = st < 3 ? m->s_phi[st & 1] : phis;
-    a.bw = bw[st];
-    a.cn = cn[st];
-    a.dt = dt;
-    a.first = st == 0;
-    a.last = st == 3;
-    a.status = &m->sc->status;
-    if (st == 3 && m->relax_on) {
-      a.cr = m->rx_cr;
-      a.gen = m->rx_gen;
-      a.xs = m->dxs;
-      a.ys = m->dys;
-      a.amp = m->relax.amp;
-      a.kx = m->relax.kx;
-      a.ky = m->relax.ky;
-      a.omega = m->relax.omega;
-      a.phase = m->relax.phase;
-      a.ramp_time = m->relax.ramp_time;
-      a.t_end = t + dt;
-    }
+    const fnpf::StageArgs a = fnpf::stage_args(m, eta, phis, ce, cp, st, t, dt, nullptr);
     cudaError_t e = fnpf::launch_stage(m->g, m->tables(), a, s);
     m->launches += 1;
     if (e != cudaSuccess) return cuda_fail(m, e, "stage");
     ce = a.out_eta;
     cp = a.out_phi;
   }
+  m->warm = true;
   return FNPF_OK;
 }
 

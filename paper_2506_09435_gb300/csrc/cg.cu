@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "mesh.cuh"
 #include "mg.cuh"
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(NT) outer_finish_kernel(CgScalars* sc, const d
   const double rr = reduce_partials(part + 2 * nb, nb, sh);
   if (threadIdx.x == 0) {
     sc->rr = rr;
+    sc->outer += 1;
     if (!isfinite(rr)) {
       sc->status = FNPF_EDIVERGED;
       sc->done = 1;
@@ -535,6 +537,215 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     ++outer;
   }
   return finish(m, h, done, inner_total, outer, info, s);
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven solves for captured RK4-step graphs: every loop is a CUDA
+// conditional WHILE node whose body ends with a kernel that sets the loop
+// condition from the device scalars, so a whole RK4 step runs without the host.
+
+namespace {
+
+__global__ void set_cond_kernel(const CgScalars* sc, cudaGraphConditionalHandle h, int cap, int use_outer) {
+  const int cnt = use_outer ? sc->outer : sc->iters;
+  cudaGraphSetConditional(h, (!sc->done && cnt < cap) ? 1u : 0u);
+}
+
+// inner solve finished: propagate a breakdown to the outer scalars
+__global__ void inner_done_kernel(const CgScalars* si, CgScalars* so, int* inner_total) {
+  *inner_total += si->iters;
+  if (si->status == FNPF_EBREAKDOWN || si->status == FNPF_EDIVERGED) {
+    so->status = si->status;
+    so->done = 1;
+  }
+}
+
+__global__ void stage_info_kernel(const CgScalars* sc, const int* inner_total, int mixed, StageInfo* out) {
+  out->rr = sc->rr;
+  out->bb = sc->bb;
+  out->iters = mixed ? *inner_total : sc->iters;
+  out->outer = mixed ? sc->outer : 0;
+  int st = sc->status;
+  if (st == 0 && !sc->done) st = FNPF_ENOCONV;
+  out->status = st;
+}
+
+cudaError_t new_handle(cudaStream_t s, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  return cudaGraphConditionalHandleCreate(h, g, 0, 0);
+}
+
+// Kernel nodes directly in graph g (not inside nested conditional bodies).
+int64_t kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  int64_t k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+// Appends a WHILE node controlled by h to the graph captured on s and captures
+// body(bs) into its body graph on stream bs; *body_kernels receives the number
+// of kernel nodes of the body.
+template <typename F>
+cudaError_t capture_while(cudaStream_t s, cudaStream_t bs, cudaGraphConditionalHandle h, int64_t* body_kernels,
+                          F&& body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &ed, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, ed, nd, &p)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return e;
+  cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess)
+    return e;
+  cudaError_t eb = body(bs);
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(bs, &out);
+  if (e == cudaSuccess && out) *body_kernels = kernel_nodes(out);
+  return eb != cudaSuccess ? eb : e;
+}
+
+}  // namespace
+
+int64_t graph_kernel_nodes(cudaGraph_t g) { return kernel_nodes(g); }
+
+// Enqueues (on a capturing stream s) one Laplace solve of the mesh's current
+// options and its summary into *info_dev.  The mesh must have run a host-driven
+// solve before (multigrid hierarchy, autotuned shapes, lazy kernel set-up).
+cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const double* phis, double* x,
+                                 StageInfo* info_dev, cudaStream_t s) {
+  const Geom& g = m->g;
+  const Tables<double> t = m->tables();
+  const int64_t NI = g.NI;
+  const int nb = vec_blocks(NI);
+  CgScalars* sc = m->sc;
+  const bool mixed = m->opts.precision == FNPF_MIXED;
+  const bool pmg = m->opts.precond == FNPF_PMG;
+  const int max_iter = std::max(1, m->opts.max_iter);
+  cudaError_t e;
+#define ENQ(call)                      \
+  do {                                 \
+    if ((e = (call)) != cudaSuccess) { \
+      m->g64_active = false;           \
+      return e;                        \
+    }                                  \
+  } while (0)
+  ENQ(cudaMemcpyAsync(m->eta64, eta_in, g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  const double* eta = m->eta64;
+  ENQ(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
+  ENQ(cudaMemsetAsync(m->inner_total, 0, sizeof(int), s));
+  ENQ(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
+  m->g64_active = false;
+  if (!mixed && m->opts.store_metric && m->G64) {
+    ENQ(launch_geom<double>(g, t, eta, m->G64, s));
+    m->g64_active = true;
+  }
+  if (!mixed && !pmg) {
+    ENQ(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
+    vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
+  }
+  if (!mixed && pmg)
+    ENQ(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
+                           m->opts.coarse_iters, s));
+  ENQ(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
+  ENQ(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
+  cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
+                                   mixed ? m->b : nullptr, m->partials, nb);
+  if (!mixed && pmg) {
+    ENQ(mg_apply<double>(m->mg, t, eta, level0_G<double>(m), m->r, m->z, m->ring, m->variant64,
+                         m->opts.cheb_degree, m->opts.coarse_iters, nullptr, s, &m->launches));
+    vec::copy_kernel<double><<<nb, NT, 0, s>>>(NI, m->z, m->p, nullptr);
+    vec::dot_kernel<double><<<nb, NT, 0, s>>>(nullptr, NI, m->r, m->z, m->partials + 1 * nb);
+  }
+  cg_init_finish_kernel<<<1, NT, 0, s>>>(sc, m->partials, nb, m->opts.rtol * m->opts.rtol,
+                                         m->opts.atol * m->opts.atol);
+  ENQ(cudaGetLastError());
+  if (!mixed) {
+    cudaGraphConditionalHandle h;
+    ENQ(new_handle(s, &h));
+    set_cond_kernel<<<1, 1, 0, s>>>(sc, h, max_iter, 0);
+    PcgBufs<double> B{eta, x, m->r, m->z, m->p, m->q, m->dinv, sc};
+    ENQ(capture_while(s, m->bstream[0], h, &m->body_kernels[0], [&](cudaStream_t bs) -> cudaError_t {
+      cudaError_t eb = enqueue_iteration<double>(m, t, B, 0, bs);
+      if (eb == cudaSuccess) eb = enqueue_iteration<double>(m, t, B, 1, bs);
+      set_cond_kernel<<<1, 1, 0, bs>>>(sc, h, max_iter, 0);
+      return eb == cudaSuccess ? cudaGetLastError() : eb;
+    }));
+  } else {
+    const Tables<float> t32 = m->tables32();
+    to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+    if (pmg) {
+      ENQ(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
+                            m->opts.cheb_degree, m->opts.coarse_iters, s));
+    } else {
+      ENQ(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
+      vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+    }
+    const int max_outer = std::max(1, m->opts.max_outer);
+    const double in_rtol2 = m->opts.inner_rtol * m->opts.inner_rtol;
+    cudaGraphConditionalHandle ho;
+    ENQ(new_handle(s, &ho));
+    set_cond_kernel<<<1, 1, 0, s>>>(sc, ho, max_outer, 1);
+    ENQ(capture_while(s, m->bstream[0], ho, &m->body_kernels[0], [&](cudaStream_t bs) -> cudaError_t {
+      CgScalars* si = m->sc_in;
+      cudaError_t eb = cudaMemsetAsync(si, 0, sizeof(CgScalars), bs);
+      if (eb != cudaSuccess) return eb;
+      inner_init_kernel<<<nb, NT, 0, bs>>>(NI, m->r, m->r32, m->e32, m->z32, m->p32, pmg ? nullptr : m->dinv32,
+                                           m->partials, nb);
+      if (pmg) {
+        if ((eb = mg_apply<float>(m->mg, t32, m->eta32, nullptr, m->r32, m->z32, reinterpret_cast<float*>(m->ring),
+                                  m->variant32, m->opts.cheb_degree, m->opts.coarse_iters, nullptr, bs,
+                                  &m->launches)) != cudaSuccess)
+          return eb;
+        vec::copy_kernel<float><<<nb, NT, 0, bs>>>(NI, m->z32, m->p32, nullptr);
+        vec::dot_kernel<float><<<nb, NT, 0, bs>>>(nullptr, NI, m->r32, m->z32, m->partials + 1 * nb);
+      }
+      inner_init_finish_kernel<<<1, NT, 0, bs>>>(si, m->partials, nb, in_rtol2);
+      cudaGraphConditionalHandle hi;
+      if ((eb = new_handle(bs, &hi)) != cudaSuccess) return eb;
+      set_cond_kernel<<<1, 1, 0, bs>>>(si, hi, max_iter, 0);
+      PcgBufs<float> B{m->eta32, m->e32, m->r32, m->z32, m->p32, m->q32, m->dinv32, si};
+      eb = capture_while(bs, m->bstream[1], hi, &m->body_kernels[1], [&](cudaStream_t bs2) -> cudaError_t {
+        cudaError_t e2 = enqueue_iteration<float>(m, t32, B, 0, bs2);
+        if (e2 == cudaSuccess) e2 = enqueue_iteration<float>(m, t32, B, 1, bs2);
+        set_cond_kernel<<<1, 1, 0, bs2>>>(si, hi, max_iter, 0);
+        return e2 == cudaSuccess ? cudaGetLastError() : e2;
+      });
+      if (eb != cudaSuccess) return eb;
+      inner_done_kernel<<<1, 1, 0, bs>>>(si, sc, m->inner_total);
+      add_correction_kernel<<<nb, NT, 0, bs>>>(NI, x, m->e32);
+      if ((eb = timed_apply<double>(m, t, eta, x, nullptr, m->q, bs, nullptr, -1)) != cudaSuccess) return eb;
+      outer_residual_kernel<<<nb, NT, 0, bs>>>(NI, m->b, m->q, m->r, m->partials, nb);
+      outer_finish_kernel<<<1, NT, 0, bs>>>(sc, m->partials, nb);
+      set_cond_kernel<<<1, 1, 0, bs>>>(sc, ho, max_outer, 1);
+      return cudaGetLastError();
+    }));
+  }
+  stage_info_kernel<<<1, 1, 0, s>>>(sc, m->inner_total, mixed ? 1 : 0, info_dev);
+  m->g64_active = false;
+  return cudaGetLastError();
+#undef ENQ
 }
 
 }  // namespace fnpf

@@ -55,7 +55,13 @@ struct CgScalars {
   int done;
   int iters;
   int status;
-  int pad;
+  int outer;     // defect-correction steps of a mixed-precision solve
+};
+
+// Per-stage summary of a solve run inside a captured RK4-step graph.
+struct StageInfo {
+  double rr, bb;
+  int iters, outer, status, pad;
 };
 
 // Shared device helpers -------------------------------------------------------
@@ -171,6 +177,7 @@ struct StageArgs {
   const double* xs;      // surface-node coordinates
   const double* ys;
   double amp, kx, ky, omega, phase, ramp_time, t_end;
+  const double* t_dev;   // if non-null: t_end = *t_dev + dt (graph replays)
 };
 cudaError_t launch_stage(const Geom& g, const Tables<double>& t, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_w(const Geom& g, const Tables<double>& t, const double* eta, const double* phis,

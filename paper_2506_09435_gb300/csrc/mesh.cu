@@ -212,7 +212,15 @@ void free_mesh(fnpf_mesh* m) {
   if (m->sc_in) cudaFree(m->sc_in);
   fnpf::mg_destroy(m->mg);
   for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);
+  if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
   if (m->gstream) cudaStreamDestroy(m->gstream);
+  for (cudaStream_t b : m->bstream)
+    if (b) cudaStreamDestroy(b);
+  if (m->inner_total) cudaFree(m->inner_total);
+  if (m->stage_info) cudaFree(m->stage_info);
+  if (m->t_dev) cudaFree(m->t_dev);
+  if (m->stage_info_host) cudaFreeHost(m->stage_info_host);
+  if (m->t_host) cudaFreeHost(m->t_host);
   if (m->sc) cudaFree(m->sc);
   if (m->sc_host) cudaFreeHost(m->sc_host);
   if (m->ev0) cudaEventDestroy(m->ev0);
@@ -359,6 +367,12 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   if (e == cudaSuccess) e = cudaMalloc((void**)&m->sc, sizeof(fnpf::CgScalars));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->sc_host, sizeof(fnpf::CgScalars));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&m->bstream[k], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->inner_total, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->stage_info, 4 * sizeof(fnpf::StageInfo));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&m->t_dev, sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&m->stage_info_host, 4 * sizeof(fnpf::StageInfo));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&m->t_host, sizeof(double));
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
   if (e == cudaSuccess) e = cudaMemcpy(m->dD, m->D.data(), n * n * sizeof(double), cudaMemcpyHostToDevice);
@@ -395,6 +409,8 @@ fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   if (!m || !o) return FNPF_EINVAL;
   m->opts = *o;
   for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);   // captured arguments depend on the options
+  if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
+  m->step_exec = nullptr;
   return FNPF_OK;
 }
 

@@ -92,6 +92,18 @@ struct fnpf_mesh {
   // CUDA graphs of the CG iteration (0: FP64, 1: FP32), captured on gstream
   cudaStream_t gstream = nullptr;
   GraphSlot g_iter[2];
+  cudaStream_t bstream[2] = {nullptr, nullptr};   // capture streams of nested loop bodies
+  int* inner_total = nullptr;                     // device: inner iterations of a mixed solve
+  fnpf::StageInfo* stage_info = nullptr;          // device [4]
+  fnpf::StageInfo* stage_info_host = nullptr;     // pinned [4]
+  double* t_dev = nullptr;                        // device time of the step graph
+  double* t_host = nullptr;                       // pinned
+  cudaGraphExec_t step_exec = nullptr;            // captured RK4 step
+  const void* step_key[2] = {nullptr, nullptr};
+  double step_dt = 0.0;
+  bool warm = false;                              // a host-driven step has run
+  int64_t step_kernels = 0;                       // top-level kernel nodes of the step graph
+  int64_t body_kernels[2] = {0, 0};               // kernel nodes of a loop body (outer / inner)
 
   // instrumentation
   bool prof_on = false;
@@ -117,6 +129,14 @@ fnpf_status autotune(fnpf_mesh* m, const double* eta, const double* G, cudaStrea
 // Accumulates the recorded event pairs (call after a host sync of the stream).
 void prof_collect(fnpf_mesh* m, int iters_done);
 void graph_reset(GraphSlot* g);
+// Captured RK4 steps (api.cu).
+cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cudaStream_t s);
+fnpf_status read_step_info(fnpf_mesh* m, fnpf_solve_info* info, float ms);
+bool graph_mode(const fnpf_mesh* m);
+int64_t graph_kernel_nodes(cudaGraph_t g);
+// Device-driven solve for graph capture (see cg.cu).
+cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const double* phis, double* x,
+                                 StageInfo* info_dev, cudaStream_t s);
 // CG solve of A_II x = -A_IS phis for the interior part x [NI] (in: initial guess).
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,
                      cudaStream_t s);

@@ -94,8 +94,9 @@ __global__ void stage_kernel(Geom g, Tables<double> t, StageArgs a) {
         if (c != 0.0) {
           double te = 0.0, tp = 0.0;
           if (a.gen[col] != 0.0) {
-            const double ramp = fmin(1.0, a.t_end / a.ramp_time);
-            const double th = a.kx * a.xs[col] + a.ky * a.ys[col] - a.omega * a.t_end + a.phase;
+            const double t_end = a.t_dev ? *a.t_dev + a.dt : a.t_end;
+            const double ramp = fmin(1.0, t_end / a.ramp_time);
+            const double th = a.kx * a.xs[col] + a.ky * a.ys[col] - a.omega * t_end + a.phase;
             const double k = hypot(a.kx, a.ky);
             te = ramp * a.amp * cos(th);
             tp = ramp * (g.g * a.amp / a.omega) * cosh(k * (te + hh)) / cosh(k * hh) * sin(th);

@@ -72,6 +72,9 @@ def load():
         "fnpf_rk4_step": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(SolveInfo), vp],
         "fnpf_apply_noalloc": [ctypes.POINTER(MeshDesc), vp, vp, vp, vp, vp],
         "fnpf_set_relaxation": [vp, ctypes.POINTER(Relaxation)],
+        "fnpf_ensemble_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
+        "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
         "fnpf_profile_enable": [vp, ctypes.c_int],
         "fnpf_profile_read": [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p, ctypes.c_int],
@@ -87,6 +90,10 @@ def load():
     lib.fnpf_default_opts.restype = None
     lib.fnpf_last_error.argtypes = [vp]
     lib.fnpf_last_error.restype = ctypes.c_char_p
+    lib.fnpf_ensemble_destroy.argtypes = [vp]
+    lib.fnpf_ensemble_destroy.restype = None
+    lib.fnpf_ensemble_last_error.argtypes = [vp]
+    lib.fnpf_ensemble_last_error.restype = ctypes.c_char_p
     lib.fnpf_status_string.argtypes = [ctypes.c_int]
     lib.fnpf_status_string.restype = ctypes.c_char_p
     return lib
@@ -270,3 +277,37 @@ class Mesh:
         if check:
             self._check(st)
         return [i.as_dict() for i in infos] if infos is not None else st
+
+
+class Ensemble:
+    """Independent tanks advanced together, one CUDA graph launch per RK4 step
+    (fnpf_ensemble_*).  The meshes must stay alive while the ensemble exists."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        h = ctypes.c_void_p()
+        st = _LIB.fnpf_ensemble_create(arr, len(self.meshes), ctypes.byref(h))
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_ensemble_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _LIB.fnpf_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def rk4_step(self, etas, phiss, ts, dts, stream=None, info=False):
+        n = len(self.meshes)
+        e = (ctypes.c_void_p * n)(*[t.data_ptr() for t in etas])
+        p = (ctypes.c_void_p * n)(*[t.data_ptr() for t in phiss])
+        tt = (ctypes.c_double * n)(*[float(v) for v in ts])
+        dd = (ctypes.c_double * n)(*[float(v) for v in dts])
+        infos = (SolveInfo * (4 * n))() if info else None
+        st = _LIB.fnpf_ensemble_rk4_step(self._h, e, p, tt, dd, infos, _stream(stream))
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_ensemble_last_error(self._h).decode())
+        return [i.as_dict() for i in infos] if infos is not None else None

@@ -194,6 +194,25 @@ def airy_plus_spectrum_state(desc, x, y, seed=2, steepness=0.05, pert_rel=1e-3):
     return eta, phis
 
 
+def ensemble_tanks(n=64, seed=5, nmin=8, nmax=96, pmin=3, pmax=7):
+    """Seeded ensemble of independent periodic tanks (L = 1 m boxes, 2 vertical
+    elements): per tank nx, ny ~ U{nmin..nmax}, p ~ U{pmin..pmax}, kh ~ U[0.5, 3],
+    steepness H/L ~ U[0.01, 0.06], perturbation seed; from splitmix64(seed)."""
+    u = uniform01(seed, 6 * n)
+    tanks = []
+    for i in range(n):
+        a = u[6 * i:6 * i + 6]
+        nx = nmin + int(a[0] * (nmax - nmin + 1))
+        ny = nmin + int(a[1] * (nmax - nmin + 1))
+        p = pmin + int(a[2] * (pmax - pmin + 1))
+        kh = 0.5 + 2.5 * a[3]
+        steep = 0.01 + 0.05 * a[4]
+        d = periodic_box_3d(nx=nx, ny=ny, nz=2, p=p, kh=kh)
+        d.update(steepness=steep, seed=1000 + i)
+        tanks.append(d)
+    return tanks
+
+
 def manufactured_potential(x, y, z, h, kx, ky):
     """Harmonic phi = cosh(kappa (z + h)) cos(kx x) cos(ky y) and its d/dz."""
     kap = math.hypot(kx, ky)
