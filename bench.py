@@ -50,8 +50,10 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
-    ap.add_argument("--mode", default="step", choices=["step", "apply"],
-                    help="step: RK4 steps (the benchmark); apply: operator applications only")
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "ensemble"],
+                    help="step: RK4 steps (the benchmark); apply: operator applications only; "
+                         "ensemble: 64 seeded tanks in one launch per step vs one tank at a time")
+    ap.add_argument("--tanks", type=int, default=64)
     ap.add_argument("--p", type=int, default=6)
     ap.add_argument("--nz", type=int, default=2)
     return ap.parse_args()
@@ -445,8 +447,83 @@ def main_apply(args):
     return 0
 
 
+def main_ensemble(args):
+    """Batched ensemble form: seeded independent periodic tanks (nx, ny in 8..96, 2
+    layers, p in 3..7, kh in 0.5..3, steepness 0.01..0.06), FP32 operator and
+    p-multigrid inside FP64 defect correction, each ensemble RK4 step one launch of
+    a captured graph; the same tanks stepped one launch at a time for comparison.
+    The working set (tens of millions of DOF) is far larger than L2, so no flush."""
+    import numpy as np
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    from paper_2506_09435_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    tanks = W.ensemble_tanks(n=args.tanks, seed=5)
+    opts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=1e-5,
+                             cheb_degree=args.cheb_degree, coarse_iters=args.coarse_degree, max_iter=50000)
+    meshes, etas, phiss, dts = [], [], [], []
+    for d in tanks:
+        ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"]
+        m = fnpf.Mesh(3, d["nx"], d["ny"], 2, d["p"], True, True, np.full(ncx * ncy, d["h0"]), Lx=d["Lx"],
+                      Ly=d["Ly"], g=d["g"], opts=opts)
+        x, y = m.surface_coords()
+        e0, p0 = W.airy_plus_spectrum_state(d, x, y, seed=d["seed"], steepness=d["steepness"])
+        meshes.append(m)
+        etas.append(torch.tensor(e0, dtype=torch.float64, device=dev))
+        phiss.append(torch.tensor(p0, dtype=torch.float64, device=dev))
+        dts.append(W.period(d["k"], d["h0"], d["g"]) / 100)
+    ndof = sum(m.N for m in meshes)
+    ens = fnpf.Ensemble(meshes)
+    stream = torch.cuda.current_stream()
+    steps = [0] * len(meshes)
+    for _ in range(max(2, args.warmup)):
+        ens.rk4_step(etas, phiss, [k * dt for k, dt in zip(steps, dts)], dts)
+        steps = [k + 1 for k in steps]
+    torch.cuda.synchronize()
+    for m in meshes:
+        m.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            ens.rk4_step(etas, phiss, [s_ * dt for s_, dt in zip(steps, dts)], dts)
+            ev[k][1].record(stream)
+            steps = [s_ + 1 for s_ in steps]
+        torch.cuda.synchronize()
+    ens_ms = sum(a.elapsed_time(b) for a, b in ev)
+    launches = sum(m.profile_read(reset=True)["launches"] for m in meshes)
+    # the same tanks, one launch (captured step graph) at a time
+    for m, e, p, dt, s_ in zip(meshes, etas, phiss, dts, steps):
+        m.rk4_step(e, p, s_ * dt, dt)           # warm the single-tank graphs
+    steps = [s_ + 1 for s_ in steps]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        for i, (m, e, p, dt) in enumerate(zip(meshes, etas, phiss, dts)):
+            m.rk4_step(e, p, steps[i] * dt, dt)
+        steps = [s_ + 1 for s_ in steps]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    one_ms = e0.elapsed_time(e1)
+    ok = all(bool(torch.isfinite(e).all()) for e in etas)
+    print(json.dumps({
+        "mode": "ensemble", "metric": "aggregate DOF·RK4-steps/s (batched ensemble)", "unit": UNIT,
+        "value": ndof * args.steps / (ens_ms * 1e-3), "one_at_a_time": ndof * args.steps / (one_ms * 1e-3),
+        "speedup_vs_one_at_a_time": one_ms / ens_ms, "tanks": len(meshes), "total_dof": ndof,
+        "ms_per_ensemble_step": ens_ms / args.steps, "steps": args.steps, "dtype": "f32 inner / f64 outer",
+        "orders": sorted(set(d["p"] for d in tanks)), "finite": ok, "gpu_launches": launches,
+        "clocks": clk.summary(), "data": "synthetic"}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "ensemble":
+        return main_ensemble(args)
     if args.impl == "reference":
         return main_reference(args)
     if args.mode == "apply":

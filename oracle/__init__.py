@@ -15,5 +15,6 @@ Modules
   operator -- stiffness operator by its quadrature definition, sparse assembly
   solve    -- Dirichlet-Neumann Laplace solve, vertical velocity recovery
   surface  -- Zakharov right-hand side, ERK4, relaxation, diagnostics
+  tlm      -- exact tangent-linear model of one RK4 step (complex step)
 """
-from . import gll, mesh, operator, solve, surface  # noqa: F401
+from . import gll, mesh, operator, solve, surface, tlm  # noqa: F401

@@ -127,8 +127,9 @@ class Mesh:
     def element_coords(self, eta, h):
         """Nodal (x, y, z) of every volume element, shape (E, n^dim) each.
         z = -h + sigma (eta + h) with uniform layers (Step 4.1, Sec. 3.1.2)."""
-        eta = np.asarray(eta, dtype=np.float64)
-        h = np.asarray(h, dtype=np.float64)
+        dt_ = np.result_type(np.asarray(eta), np.asarray(h), np.float64)   # complex for the complex-step TLM
+        eta = np.asarray(eta, dtype=dt_)
+        h = np.asarray(h, dtype=dt_)
         xi = self.rule.xi
         xs, ys, zs = [], [], []
         for ez in range(self.nz):

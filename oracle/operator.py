@@ -60,7 +60,7 @@ def jacobians(mesh, eta, h):
     coords = [x, z] if mesh.dim == 2 else [x, y, z]
     dim = mesh.dim
     E, nl = x.shape
-    J = np.empty((E, nl, dim, dim))
+    J = np.empty((E, nl, dim, dim), dtype=np.result_type(x, y, z))
     for m, c in enumerate(coords):
         for a, Da in enumerate(Dl):
             J[:, :, m, a] = c @ Da.T
@@ -74,7 +74,10 @@ def metric(mesh, eta, h):
     detJ = np.linalg.det(J)
     Jinv = np.linalg.inv(J)                   # Jinv[..., a, m] = d r_a / d x_m
     wq = quadrature_weights(mesh)
-    G = np.einsum("eqam,eqbm->eqab", Jinv, Jinv) * (wq[None, :] * np.abs(detJ))[..., None, None]
+    # |det J| written as det J times its (real) orientation sign, which is the
+    # same for real data and stays analytic for the complex-step derivative
+    absdet = detJ * np.sign(detJ.real)
+    G = np.einsum("eqam,eqbm->eqab", Jinv, Jinv) * (wq[None, :] * absdet)[..., None, None]
     return G, detJ
 
 
@@ -100,7 +103,7 @@ class Operator:
         """y = A x without forming A (same definition, used on large meshes)."""
         dim = self.mesh.dim
         g = [Pb @ x for Pb in self.P]
-        y = np.zeros(self.mesh.N)
+        y = np.zeros(self.mesh.N, dtype=np.result_type(x, self.G))
         for a in range(dim):
             f = sum(self.Gflat[a][b] * g[b] for b in range(dim))
             y += self.P[a].T @ f

@@ -59,15 +59,15 @@ def cg(apply, b, x0=None, rtol=1e-14, max_iter=100000, minv=None):
 def laplace_solve(mesh, eta, h, phis, op=None, method="direct", rtol=1e-14):
     """Full-volume potential phi (length N, plane-major) with phi = phis on the
     surface plane."""
-    phis = np.asarray(phis, dtype=np.float64)
+    phis = np.asarray(phis, dtype=np.result_type(np.asarray(phis), np.float64))
     if op is None:
         op = Operator(mesh, eta, h, assemble=(method != "cg_free"))
     nI = mesh.n_interior
     if method == "cg_free":
         def apply_II(v):
-            full = np.concatenate([v, np.zeros(mesh.ns)])
+            full = np.concatenate([v, np.zeros(mesh.ns, dtype=v.dtype)])
             return op.apply(full)[:nI]
-        b = -op.apply(np.concatenate([np.zeros(nI), phis]))[:nI]
+        b = -op.apply(np.concatenate([np.zeros(nI, dtype=phis.dtype), phis]))[:nI]
         phiI, _ = cg(apply_II, b, rtol=rtol)
     else:
         AII, AIS = dirichlet_split(mesh, op.A)
@@ -75,7 +75,10 @@ def laplace_solve(mesh, eta, h, phis, op=None, method="direct", rtol=1e-14):
         if method == "direct":
             lu = spla.splu(AII.tocsc(), permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
                            options=dict(SymmetricMode=True))
-            phiI = lu.solve(b)
+            if np.iscomplexobj(b) and not np.iscomplexobj(AII.data):
+                phiI = lu.solve(np.ascontiguousarray(b.real)) + 1j * lu.solve(np.ascontiguousarray(b.imag))
+            else:
+                phiI = lu.solve(b)
         elif method == "dense":
             c = sla.cho_factor(AII.toarray())
             phiI = sla.cho_solve(c, b)
@@ -138,7 +141,7 @@ def vertical_velocity(mesh, eta, h, phi):
         dz = dz.reshape(C, n, n)[..., n - 1]
     W = surface_weights(mesh)
     cols = surface_cols(mesh)
-    num = np.zeros(mesh.ns)
+    num = np.zeros(mesh.ns, dtype=dz.dtype)
     den = np.zeros(mesh.ns)
     np.add.at(num, cols.ravel(), (W * dz).ravel())
     np.add.at(den, cols.ravel(), W.ravel())

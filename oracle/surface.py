@@ -55,8 +55,8 @@ def zakharov_rhs(mesh, eta, phis, w, g):
     f_phi = -g * el - 0.5 * gp2 + 0.5 * wl * wl * (1 + ge2)
     W = surface_weights(mesh)
     M = lumped_mass(mesh)
-    d_eta = np.zeros(mesh.ns)
-    d_phi = np.zeros(mesh.ns)
+    d_eta = np.zeros(mesh.ns, dtype=f_eta.dtype)
+    d_phi = np.zeros(mesh.ns, dtype=f_phi.dtype)
     np.add.at(d_eta, cols.ravel(), (W * f_eta).ravel())
     np.add.at(d_phi, cols.ravel(), (W * f_phi).ravel())
     return d_eta / M, d_phi / M

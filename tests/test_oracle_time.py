@@ -143,3 +143,28 @@ def test_bar_depth_profile():
     assert np.allclose(workloads.bar_depth(x), [0.4, 0.4, 0.25, 0.1, 0.1, 0.1, 0.25, 0.4, 0.4])
     d = workloads.bar_flume()
     assert workloads.dof_counts(d) == (1660176, 103761)
+
+
+def test_complex_step_tlm_matches_central_differences():
+    """The oracle's tangent-linear model (complex step) against central finite
+    differences of the real oracle, for perturbations of eta, phi and h."""
+    from oracle import tlm
+    m = mesh.Mesh(3, 3, 2, 2, 3, periodic_x=True, periodic_y=False)
+    x, y = m.surface_coords()
+    h = 0.4 + 0.05 * np.cos(2 * np.pi * x)
+    eta = 0.02 * np.cos(2 * np.pi * x + 0.3) * (1 + 0.3 * y)
+    phis = 0.05 * np.sin(2 * np.pi * x) + 0.01 * y
+    rng = np.random.default_rng(3)
+    de, dp, dh = (rng.standard_normal(m.ns) for _ in range(3))
+    dt, g = 0.02, 9.81
+    te, tp = tlm.step_tlm(m, h, eta, phis, dt, g, de, dp, dh)
+    s = 1e-6
+    ep, pp = surface.rk4_step(m, h + s * dh, eta + s * de, phis + s * dp, dt, g)
+    em, pm = surface.rk4_step(m, h - s * dh, eta - s * de, phis - s * dp, dt, g)
+    fe, fp = (ep - em) / (2 * s), (pp - pm) / (2 * s)
+    assert np.linalg.norm(te - fe) / np.linalg.norm(fe) < 1e-6
+    assert np.linalg.norm(tp - fp) / np.linalg.norm(fp) < 1e-6
+    # and the real part of the complex evaluation is the plain step
+    e0, p0 = surface.rk4_step(m, h, eta, phis, dt, g)
+    ec, pc = surface.rk4_step(m, h + 0j, eta + 1e-30j * de, phis + 0j, dt, g)
+    assert np.max(np.abs(ec.real - e0)) < 1e-15 and np.max(np.abs(pc.real - p0)) < 1e-15
