@@ -240,6 +240,24 @@ fnpf_status fnpf_ensemble_rk4_step(fnpf_ensemble* ens, double* const* etas, doub
                                    const double* dts, fnpf_solve_info* info, void* stream);
 const char* fnpf_ensemble_last_error(const fnpf_ensemble* ens);
 
+/* Adjoint of one RK4 step (reverse mode; the differentiation form built around
+ * the paper's method, Sec. 3.2 and Sec. 3.4 Steps 4.1-4.7).  Given the step's
+ * input state eta_n, phis_n [Ns] and lam = dJ/d(eta, phis) at the step's output
+ * (lam_eta, lam_phis [Ns]), writes dJ/d(eta, phis) at its input into
+ * lam_eta_out, lam_phis_out (may alias the inputs) and ADDS dJ/dh into lam_h
+ * [Ns] when it is not NULL.  The step is recomputed (four forward solves,
+ * storing the stage states and potentials), then each stage costs one adjoint
+ * Laplace solve with the same PCG (the operator is symmetric), the
+ * vector-Jacobian products of the Zakharov right-hand side and of the
+ * vertical-velocity recovery, and the product with the eta- and h-derivative
+ * of the operator.  Relaxation zones enter through (1 - C_r).  FP64 only
+ * (the mesh's precond, rtol and max_iter apply to every solve).  Waits for the
+ * stream at every solve.  Workspace (4 N_I + ~30 Ns doubles) is allocated at
+ * the first call. */
+fnpf_status fnpf_step_adjoint(fnpf_mesh* mesh, const double* eta_n, const double* phis_n, const double* lam_eta,
+                              const double* lam_phis, double* lam_eta_out, double* lam_phis_out, double* lam_h,
+                              double t, double dt, void* stream);
+
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */
 const char* fnpf_last_error(const fnpf_mesh* mesh);

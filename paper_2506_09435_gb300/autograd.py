@@ -1,0 +1,52 @@
+"""Differentiable RK4 time loop (torch.autograd.Function) with checkpointing.
+
+Forward: `nsteps` calls of fnpf_rk4_step on one work buffer, storing (eta,
+phi_eta) every `every` steps.  Backward: for each segment, newest first, the
+segment is recomputed from its checkpoint (keeping each step's input state) and
+fnpf_step_adjoint runs over its steps in reverse, accumulating dJ/dh.  Every
+computation runs in libfnpf's kernels; this module only orders the calls.
+"""
+import torch
+
+
+class RK4Run(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, eta0, phis0, h, mesh, t0, dt, nsteps, every):
+        work_e = eta0.detach().clone().contiguous()
+        work_p = phis0.detach().clone().contiguous()
+        ckpts = []
+        for n in range(nsteps):
+            if n % every == 0:
+                ckpts.append((n, work_e.clone(), work_p.clone()))
+            mesh.rk4_step(work_e, work_p, t0 + n * dt, dt)
+        ctx.mesh, ctx.t0, ctx.dt, ctx.nsteps, ctx.every = mesh, t0, dt, nsteps, every
+        ctx.ckpts, ctx.work = ckpts, (work_e, work_p)
+        ctx.h_shape = h.shape
+        return work_e.clone(), work_p.clone()
+
+    @staticmethod
+    def backward(ctx, g_eta, g_phis):
+        mesh, t0, dt, nsteps, every = ctx.mesh, ctx.t0, ctx.dt, ctx.nsteps, ctx.every
+        work_e, work_p = ctx.work
+        lam_e = (g_eta if g_eta is not None else torch.zeros_like(work_e)).detach().clone().contiguous()
+        lam_p = (g_phis if g_phis is not None else torch.zeros_like(work_p)).detach().clone().contiguous()
+        lam_h = torch.zeros(ctx.h_shape, dtype=lam_e.dtype, device=lam_e.device)
+        for n0, e0, p0 in reversed(ctx.ckpts):
+            n1 = min(n0 + every, nsteps)
+            work_e.copy_(e0)
+            work_p.copy_(p0)
+            states = []
+            for n in range(n0, n1):
+                states.append((work_e.clone(), work_p.clone()))
+                if n + 1 < n1:
+                    mesh.rk4_step(work_e, work_p, t0 + n * dt, dt)
+            for n in reversed(range(n0, n1)):
+                es, ps = states[n - n0]
+                mesh.step_adjoint(es, ps, lam_e, lam_p, lam_e, lam_p, lam_h, t0 + n * dt, dt)
+        return lam_e, lam_p, lam_h, None, None, None, None, None
+
+
+def rk4_run(mesh, eta0, phis0, h, t0, dt, nsteps, every=16):
+    """(eta_N, phi_N) after nsteps RK4 steps; differentiable in eta0, phis0 and h
+    (the gradient for h is dJ/dh at the surface nodes; the mesh keeps its own h)."""
+    return RK4Run.apply(eta0, phis0, h, mesh, t0, dt, nsteps, every)

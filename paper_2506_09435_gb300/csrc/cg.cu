@@ -403,8 +403,12 @@ fnpf_status finish(fnpf_mesh* m, const CgScalars& h, bool done, int iters, int o
 
 }  // namespace
 
+__global__ void __launch_bounds__(NT) negate_kernel(int64_t n, const double* a, double* b) {
+  GRID_LOOP(i, n) b[i] = -a[i];
+}
+
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, double* x, fnpf_solve_info* info,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* rhs) {
   const Geom& g = m->g;
   const Tables<double> t = m->tables();
   const int64_t NI = g.NI;
@@ -430,7 +434,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   FNPF_CK(cudaMemcpyAsync(m->eta64, eta_in, g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
   const double* eta = m->eta64;
   FNPF_CK(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
-  FNPF_CK(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
+  FNPF_CK(launch_check_state(g, eta, rhs ? eta : phis, m->dh, &sc->status, &sc->done, s));
   // FP64 solves: the metric is rebuilt from this eta once and read by every
   // operator application of the solve (fewer FP64 instructions per point)
   m->g64_active = false;
@@ -460,8 +464,13 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
                                m->opts.coarse_iters, s));
   }
   FNPF_CK(cudaGetLastError());
-  // lift: r = A [0; phis]_I = -b; q = A [x; 0]_I; then b, r = b - q (, z, p)
-  FNPF_CK(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
+  // lift: r = A [0; phis]_I = -b (or r = -rhs); q = A [x; 0]_I; then b, r = b - q (, z, p)
+  if (rhs) {
+    negate_kernel<<<nb, NT, 0, s>>>(NI, rhs, m->r);
+    FNPF_CK(cudaGetLastError());
+  } else {
+    FNPF_CK(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
+  }
   FNPF_CK(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
   cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
                                    mixed ? m->b : nullptr, m->partials, nb);

@@ -82,6 +82,10 @@ struct fnpf_mesh {
   fnpf_relaxation relax{};          // scalar parameters (array pointers unused)
   bool relax_on = false;
 
+  // adjoint step workspaces (allocated at the first fnpf_step_adjoint)
+  double* adj = nullptr;            // one block holding all of them
+  size_t adj_bytes = 0;
+
   // p-multigrid hierarchy (created at the first FNPF_PMG solve)
   fnpf::Mg* mg = nullptr;
   bool iso = false;
@@ -137,7 +141,8 @@ int64_t graph_kernel_nodes(cudaGraph_t g);
 // Device-driven solve for graph capture (see cg.cu).
 cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const double* phis, double* x,
                                  StageInfo* info_dev, cudaStream_t s);
-// CG solve of A_II x = -A_IS phis for the interior part x [NI] (in: initial guess).
+// CG solve of A_II x = -A_IS phis for the interior part x [NI] (in: initial guess),
+// or of A_II x = rhs when rhs [NI] is given (phis is then unused).
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,
-                     cudaStream_t s);
+                     cudaStream_t s, const double* rhs = nullptr);
 }  // namespace fnpf

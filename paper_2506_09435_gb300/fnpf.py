@@ -72,6 +72,7 @@ def load():
         "fnpf_rk4_step": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(SolveInfo), vp],
         "fnpf_apply_noalloc": [ctypes.POINTER(MeshDesc), vp, vp, vp, vp, vp],
         "fnpf_set_relaxation": [vp, ctypes.POINTER(Relaxation)],
+        "fnpf_step_adjoint": [vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp],
         "fnpf_ensemble_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
@@ -253,6 +254,13 @@ class Mesh:
         r.cr = cr.ctypes.data_as(_dp)
         r.gen = gen.ctypes.data_as(_dp)
         self._check(_LIB.fnpf_set_relaxation(self._h, ctypes.byref(r)))
+
+    def step_adjoint(self, eta, phis, lam_eta, lam_phis, lam_eta_out, lam_phis_out, lam_h=None, t=0.0, dt=0.01,
+                     stream=None):
+        """dJ/dy_n from dJ/dy_{n+1} for one RK4 step from (eta, phis); adds dJ/dh into lam_h."""
+        self._check(_LIB.fnpf_step_adjoint(self._h, _ptr(eta), _ptr(phis), _ptr(lam_eta), _ptr(lam_phis),
+                                           _ptr(lam_eta_out), _ptr(lam_phis_out), _ptr(lam_h), float(t),
+                                           float(dt), _stream(stream)))
 
     def autotune(self, eta, stream=None):
         v64, v32 = ctypes.c_int(), ctypes.c_int()
