@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--coarse-degree", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
@@ -337,6 +338,28 @@ def main_gb300(args):
                 "bytes_per_application": 2 * 8 * mesh.N + 6 * 8 * E * n ** 3,
                 "hbm_frac_of_measured": (2 * 8 * mesh.N + 6 * 8 * E * n ** 3) / (apply_ms * 1e-3) / 1e9 / 6785.2}
 
+    # --- adjoint step (reverse mode, FP64, same mesh and state) against the forward step
+    adjoint = None
+    if not args.no_adjoint:
+        le = torch.ones(mesh.ns, dtype=torch.float64, device=dev) / mesh.ns
+        lp = torch.zeros_like(le)
+        oe, op_ = torch.empty_like(le), torch.empty_like(le)
+        lh = torch.zeros_like(le)
+        mesh.step_adjoint(eta, phis, le, lp, oe, op_, lh, t, dt)      # workspace allocation, warm
+        torch.cuda.synchronize()
+        aev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(max(1, args.steps // 2))]
+        for a_, b_ in aev:
+            flush.zero_()
+            a_.record(stream)
+            mesh.step_adjoint(eta, phis, le, lp, oe, op_, lh, t, dt)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        adj_ms = statistics.mean(a_.elapsed_time(b_) for a_, b_ in aev)
+        adjoint = {"ms_per_step": adj_ms, "ratio_to_forward": adj_ms / (total_ms / args.steps),
+                   "note": "recomputes the step's four forward solves (host-driven) and runs four adjoint "
+                           "solves plus the vector-Jacobian products; forward = the timed graph-replayed step"}
+
     # --- end to end through the public API: pinned host state in, step, state out
     eta_h = torch.empty(mesh.ns, dtype=torch.float64, pin_memory=True)
     phi_h = torch.empty(mesh.ns, dtype=torch.float64, pin_memory=True)
@@ -385,6 +408,7 @@ def main_gb300(args):
                        "wall_s": wall},
             "roofline": roofline,
             "mixed": mixed,
+            "adjoint": adjoint,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

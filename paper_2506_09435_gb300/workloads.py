@@ -213,6 +213,25 @@ def ensemble_tanks(n=64, seed=5, nmin=8, nmax=96, pmin=3, pmax=7):
     return tanks
 
 
+def ogrid_map(theta, s, a=1.0, R=10.0, stretch=2.0):
+    """Annulus around a vertical cylinder of radius a out to R: logical
+    coordinates (theta in [0, 2 pi), s in [0, 1]) -> (x, y), with radial
+    clustering r = a + (R - a) (exp(stretch s) - 1) / (exp(stretch) - 1); theta
+    runs clockwise so that the map (theta, s) -> (x, y) keeps a positive
+    orientation."""
+    r = a + (R - a) * (np.exp(stretch * s) - 1.0) / (math.exp(stretch) - 1.0)
+    return r * np.cos(theta), -r * np.sin(theta)
+
+
+def cylinder_case(nth=64, nr=24, nz=3, p=4, ka=1.0, kh=1.0, a=1.0, Rout=10.0, g=G_DEFAULT):
+    """Wave interaction with a bottom-mounted vertical cylinder (O-grid,
+    periodic in theta, walls at the cylinder and at R): k a = 1, k h = 1,
+    sponge ring 0.8 R .. R."""
+    k = ka / a
+    return dict(dim=3, nx=nth, ny=nr, nz=nz, p=p, periodic_x=True, periodic_y=False, Lx=2 * math.pi, Ly=1.0,
+                a=a, R=Rout, h0=kh / k, k=k, g=g, T=period(k, kh / k, g))
+
+
 def manufactured_potential(x, y, z, h, kx, ky):
     """Harmonic phi = cosh(kappa (z + h)) cos(kx x) cos(ky y) and its d/dz."""
     kap = math.hypot(kx, ky)
