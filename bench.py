@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--precond", default="pmg", choices=["pmg", "jacobi"])
-    ap.add_argument("--cheb-degree", type=int, default=3)
-    ap.add_argument("--coarse-degree", type=int, default=10)
+    ap.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev degree of the FP64 path's smoothers")
+    ap.add_argument("--mixed-cheb-degree", type=int, default=3, help="... of the mixed path's FP32 smoothers")
+    ap.add_argument("--coarse-degree", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -205,7 +206,8 @@ def main_gb300(args):
     h = None
     pre = fnpf.FNPF_PMG if args.precond == "pmg" else fnpf.FNPF_JACOBI
     prec = fnpf.FNPF_MIXED if args.precision == "mixed" else fnpf.FNPF_FP64
-    opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000, precond=pre, cheb_degree=args.cheb_degree,
+    cdeg = args.mixed_cheb_degree if args.precision == "mixed" else args.cheb_degree
+    opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000, precond=pre, cheb_degree=cdeg,
                              coarse_iters=args.coarse_degree, precision=prec)
     ncx = d["p"] * d["nx"]
     h = np.full(ncx * ncx, d["h0"])
@@ -261,7 +263,7 @@ def main_gb300(args):
     mixed = None
     if not args.no_mixed:
         mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
-                                  precond=pre, cheb_degree=args.cheb_degree, coarse_iters=args.coarse_degree)
+                                  precond=pre, cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree)
         mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
                        opts=mopts)
         em = torch.tensor(eta0, dtype=torch.float64, device=dev)
@@ -402,7 +404,8 @@ def main_gb300(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": mesh.N, "surface_dof": mesh.ns, "precision": "fp64",
-                       "precond": args.precond, "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
+                       "precond": args.precond, "cheb_degree": cdeg, "coarse_degree": args.coarse_degree,
+                       "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "cg_iters_per_solve_mean": statistics.mean(iters), "max_rel_res": rel_res,
                        "wall_s": wall},
@@ -486,7 +489,7 @@ def main_ensemble(args):
     dev = torch.device("cuda", 0)
     tanks = W.ensemble_tanks(n=args.tanks, seed=5)
     opts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=1e-5,
-                             cheb_degree=args.cheb_degree, coarse_iters=args.coarse_degree, max_iter=50000)
+                             cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree, max_iter=50000)
     meshes, etas, phiss, dts = [], [], [], []
     for d in tanks:
         ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"]

@@ -106,7 +106,7 @@ typedef struct fnpf_mesh fnpf_mesh;
 fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t* n_surf);
 
 /* Fills *opts with the defaults: FP64, Jacobi, rtol 1e-10, atol 0,
- * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 10,
+ * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 6,
  * inner_rtol 1e-5, max_outer 20, use_graphs 1, store_metric 1. */
 void fnpf_default_opts(fnpf_opts* opts);
 

@@ -132,7 +132,7 @@ cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cud
   const double* ce = eta;
   const double* cp = phis;
   for (int st = 0; st < 4; ++st) {
-    cudaError_t e = enqueue_solve_device(m, ce, cp, m->phi, m->stage_info + st, s);
+    cudaError_t e = enqueue_solve_device(m, ce, cp, m->phi, m->stage_info + st, s, st == 0);
     if (e != cudaSuccess) return e;
     const StageArgs a = stage_args(m, eta, phis, ce, cp, st, 0.0, dt, m->t_dev);
     if ((e = launch_stage(m->g, m->tables(), a, s)) != cudaSuccess) return e;

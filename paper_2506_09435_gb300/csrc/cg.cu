@@ -176,6 +176,16 @@ __global__ void __launch_bounds__(NT) to_float_kernel(int64_t n, const double* a
 
 inline int vec_blocks(int64_t n) { return vec::blocks_for(n); }
 
+// Host-driven solves re-estimate the Chebyshev intervals on the first solve of
+// a precision and then every fourth solve (once per RK4 step); the 1.1 safety
+// factor on lmax covers the change of the geometry between stages.
+bool want_estimate(fnpf_mesh* m, int prec) {
+  const bool e = !m->cheb_valid[prec] || m->solve_count[prec] % 4 == 0;
+  ++m->solve_count[prec];
+  m->cheb_valid[prec] = true;
+  return e;
+}
+
 // The stored metric of the finest level while an FP64 solve uses it.
 template <typename T>
 const T* level0_G(const fnpf_mesh* m) {
@@ -461,7 +471,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   }
   if (!mixed && pmg) {
     FNPF_CK(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
-                               m->opts.coarse_iters, s));
+                               m->opts.coarse_iters, want_estimate(m, 0), s));
   }
   FNPF_CK(cudaGetLastError());
   // lift: r = A [0; phis]_I = -b (or r = -rhs); q = A [x; 0]_I; then b, r = b - q (, z, p)
@@ -497,7 +507,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
   if (pmg) {
     FNPF_CK(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
-                              m->opts.cheb_degree, m->opts.coarse_iters, s));
+                              m->opts.cheb_degree, m->opts.coarse_iters, want_estimate(m, 1), s));
   } else {
     FNPF_CK(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
     vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
@@ -643,7 +653,7 @@ int64_t graph_kernel_nodes(cudaGraph_t g) { return kernel_nodes(g); }
 // options and its summary into *info_dev.  The mesh must have run a host-driven
 // solve before (multigrid hierarchy, autotuned shapes, lazy kernel set-up).
 cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const double* phis, double* x,
-                                 StageInfo* info_dev, cudaStream_t s) {
+                                 StageInfo* info_dev, cudaStream_t s, bool estimate) {
   const Geom& g = m->g;
   const Tables<double> t = m->tables();
   const int64_t NI = g.NI;
@@ -676,7 +686,7 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
   }
   if (!mixed && pmg)
     ENQ(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
-                           m->opts.coarse_iters, s));
+                           m->opts.coarse_iters, estimate, s));
   ENQ(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
   ENQ(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
   cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
@@ -706,7 +716,7 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
     to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
     if (pmg) {
       ENQ(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
-                            m->opts.cheb_degree, m->opts.coarse_iters, s));
+                            m->opts.cheb_degree, m->opts.coarse_iters, estimate, s));
     } else {
       ENQ(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
       vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);

@@ -267,7 +267,7 @@ void fnpf_default_opts(fnpf_opts* o) {
   o->max_iter = 20000;
   o->check_every = 16;
   o->cheb_degree = 3;
-  o->coarse_iters = 10;
+  o->coarse_iters = 6;
   o->inner_rtol = 1e-5;
   o->max_outer = 20;
   o->use_graphs = 1;
@@ -412,6 +412,7 @@ fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);   // captured arguments depend on the options
   if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
   m->step_exec = nullptr;
+  m->cheb_valid[0] = m->cheb_valid[1] = false;
   return FNPF_OK;
 }
 

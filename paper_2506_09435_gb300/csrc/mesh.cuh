@@ -88,6 +88,8 @@ struct fnpf_mesh {
 
   // p-multigrid hierarchy (created at the first FNPF_PMG solve)
   fnpf::Mg* mg = nullptr;
+  bool cheb_valid[2] = {false, false};   // Chebyshev intervals estimated (FP64, FP32)
+  int64_t solve_count[2] = {0, 0};
   bool iso = false;
   double Lx = 0, Ly = 0;
   std::vector<double> Xs, Ys;       // surface-node coordinates of an isoparametric mesh
@@ -140,7 +142,7 @@ bool graph_mode(const fnpf_mesh* m);
 int64_t graph_kernel_nodes(cudaGraph_t g);
 // Device-driven solve for graph capture (see cg.cu).
 cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const double* phis, double* x,
-                                 StageInfo* info_dev, cudaStream_t s);
+                                 StageInfo* info_dev, cudaStream_t s, bool estimate);
 // CG solve of A_II x = -A_IS phis for the interior part x [NI] (in: initial guess),
 // or of A_II x = rhs when rhs [NI] is given (phis is then unused).
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,

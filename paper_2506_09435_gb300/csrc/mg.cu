@@ -387,6 +387,7 @@ Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<d
     upload(dJ, J.data(), J.size() * 8);
     upload(dJs, Js.data(), Js.size() * 8);
     B.t = Tables<double>{dD, dxi, dw, dhm, dh, nullptr};
+    alloc((void**)&B.G, (size_t)(g.dim == 3 ? 6 : 3) * geom_points(g) * sizeof(double));
     B.J = dJ;
     B.Js = dJs;
     B.eta = deta;
@@ -458,9 +459,9 @@ template <typename T>
 cudaError_t cheb_sweep(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* G0, const T* b, T* x, int degree,
                        bool x_zero, bool final_residual, T* ring, int variant, const int* skip, cudaStream_t s,
                        int64_t* nl) {
-  const T* G = l == 0 ? G0 : nullptr;
   const Geom& g = mg->g[l];
   MgLevelBufs<T>& L = mg->bufs<T>()[l];
+  const T* G = l == 0 ? G0 : (G0 ? L.G : nullptr);
   const Tables<T> t = level_tables(mg, l, t0);
   const T* eta = level_eta(mg, l, eta0);
   const ChebParams* cp = mg->cheb<T>() + l;
@@ -515,7 +516,7 @@ cudaError_t vcycle(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* G
 
 template <typename T>
 cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, T* ring, int variant,
-                       int cheb_degree, int coarse_degree, cudaStream_t s) {
+                       int cheb_degree, int coarse_degree, bool estimate, cudaStream_t s) {
   (void)cheb_degree;
   cudaError_t e;
   MgLevelBufs<T>* Lv = mg->bufs<T>();
@@ -532,6 +533,10 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
     const int lv = l == 0 ? variant : 1;
     if ((e = launch_diag<T>(g, t, eta, L.dinv, nullptr, ring, s)) != cudaSuccess) return e;
     vec::invert_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.dinv);
+    if (l > 0 && G0 && L.G)
+      if ((e = launch_geom<T>(g, t, eta, L.G, s)) != cudaSuccess) return e;
+    if (!estimate) continue;
+    const T* Gl = l == 0 ? G0 : (G0 ? L.G : nullptr);
     // Lanczos through Jacobi-CG: x = X, r = R, z = Dd, p = P, q = W
     random_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.R);
     CgScalars* sc = mg->sc + l;
@@ -539,8 +544,7 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
     lz_init_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.R, L.dinv, L.X, L.Dd, L.P, mg->part, nb);
     lz_init_finish_kernel<<<1, vec::NT, 0, s>>>(sc, mg->part, nb);
     for (int it = 0; it < kLanczos; ++it) {
-      if ((e = level_apply<T>(g, t, eta, l == 0 ? G0 : nullptr, L.P, L.W, ring, lv, &sc->done, s)) != cudaSuccess)
-        return e;
+      if ((e = level_apply<T>(g, t, eta, Gl, L.P, L.W, ring, lv, &sc->done, s)) != cudaSuccess) return e;
       vec::dot_kernel<T><<<nb, vec::NT, 0, s>>>(&sc->done, g.NI, L.P, L.W, mg->part + 3 * nb);
       vec::update_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.X, L.R, L.Dd, L.P, L.W, L.dinv, mg->part, nb,
                                                    hist);
@@ -561,9 +565,9 @@ cudaError_t mg_apply(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, co
 }
 
 template cudaError_t mg_prepare<double>(Mg*, const Tables<double>&, const double*, const double*, double*, int, int,
-                                        int, cudaStream_t);
+                                        int, bool, cudaStream_t);
 template cudaError_t mg_prepare<float>(Mg*, const Tables<float>&, const float*, const float*, float*, int, int, int,
-                                       cudaStream_t);
+                                       bool, cudaStream_t);
 template cudaError_t mg_apply<double>(Mg*, const Tables<double>&, const double*, const double*, const double*,
                                       double*, double*, int, int, int, const int*, cudaStream_t, int64_t*);
 template cudaError_t mg_apply<float>(Mg*, const Tables<float>&, const float*, const float*, const float*, float*,

@@ -34,6 +34,7 @@ struct MgLevelBufs {
   T* Dd = nullptr;      // [NI] Chebyshev direction
   T* W = nullptr;       // [NI] operator output
   T* P = nullptr;       // [NI] CG direction of the Lanczos estimate
+  T* G = nullptr;         // stored metric of this level (FP64 solves, levels >= 1)
   const T* J = nullptr;   // [n_{l-1} x n_l] prolongation from this level to level l-1 (levels >= 1)
   const T* Js = nullptr;  // [n_l x n_0] surface interpolation from level 0 (levels >= 1)
 };
@@ -47,14 +48,15 @@ Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<d
 void mg_destroy(Mg* mg);
 int mg_levels(const Mg* mg);
 
-// Per-solve set-up in precision T: eta at every level, Jacobi diagonals, and
+// Per-solve set-up in precision T: eta at every level, Jacobi diagonals, the
+// stored metric of the coarser levels when G0 is given, and (when `estimate`)
 // the Chebyshev intervals from a short Lanczos run per level (all on the
-// device, no host synchronisation).  eta0 is the fine eta in precision T,
-// t0 the fine tables, dinv0/R0.. fine scratch supplied by the mesh.
-// G0, if non-null, is the stored metric of level 0 (the operator there reads it).
+// device, no host synchronisation).  eta0 is the fine eta in precision T, t0
+// the fine tables; G0, if non-null, is the stored metric of level 0 (the
+// operator there reads it, and the coarser levels then store theirs too).
 template <typename T>
 cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, T* ring, int variant,
-                       int cheb_degree, int coarse_degree, cudaStream_t s);
+                       int cheb_degree, int coarse_degree, bool estimate, cudaStream_t s);
 
 // z = M r (one symmetric V-cycle); kernels exit at once when *skip != 0.
 template <typename T>
