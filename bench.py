@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev degree of the FP64 path's smoothers")
     ap.add_argument("--mixed-cheb-degree", type=int, default=3, help="... of the mixed path's FP32 smoothers")
     ap.add_argument("--coarse-degree", type=int, default=6)
+    ap.add_argument("--shape", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="elements-per-CTA shape of the operator kernels (-1: autotuned)")
+    ap.add_argument("--cheb-kind", type=int, default=1, choices=[1, 4],
+                    help="Chebyshev smoother: 1 = first kind on [lmax/20, lmax], 4 = fourth kind on [0, lmax]")
+    ap.add_argument("--coarse-solver", default="cluster", choices=["cluster", "launches"],
+                    help="coarsest multigrid level on one thread-block cluster, or one launch per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -208,11 +214,14 @@ def main_gb300(args):
     prec = fnpf.FNPF_MIXED if args.precision == "mixed" else fnpf.FNPF_FP64
     cdeg = args.mixed_cheb_degree if args.precision == "mixed" else args.cheb_degree
     opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000, precond=pre, cheb_degree=cdeg,
-                             coarse_iters=args.coarse_degree, precision=prec)
+                             coarse_iters=args.coarse_degree, coarse_solver=coarse_mode(args),
+                             cheb_kind=args.cheb_kind, precision=prec)
     ncx = d["p"] * d["nx"]
     h = np.full(ncx * ncx, d["h0"])
     mesh = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
                      opts=opts)
+    if args.shape >= 0:
+        mesh.set_shapes(args.shape, args.shape)
     x, y = mesh.surface_coords()
     eta0, phi0 = W.airy_plus_spectrum_state(d, x, y, seed=2)
     dt = W.period(d["k"], d["h0"], d["g"]) / 100
@@ -263,7 +272,8 @@ def main_gb300(args):
     mixed = None
     if not args.no_mixed:
         mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
-                                  precond=pre, cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree)
+                                  precond=pre, cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
+                                  coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind)
         mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
                        opts=mopts)
         em = torch.tensor(eta0, dtype=torch.float64, device=dev)
@@ -405,6 +415,8 @@ def main_gb300(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": mesh.N, "surface_dof": mesh.ns, "precision": "fp64",
                        "precond": args.precond, "cheb_degree": cdeg, "coarse_degree": args.coarse_degree,
+                       "coarse_solver": args.coarse_solver, "cheb_kind": args.cheb_kind,
+                       "cta_shape": "autotuned" if args.shape < 0 else args.shape,
                        "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "cg_iters_per_solve_mean": statistics.mean(iters), "max_rel_res": rel_res,
@@ -437,6 +449,8 @@ def main_apply(args):
     ncx = d["p"] * d["nx"]
     mesh = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, np.full(ncx * ncx, d["h0"]),
                      Lx=d["Lx"], Ly=d["Ly"], g=d["g"])
+    if args.shape >= 0:
+        mesh.set_shapes(args.shape, args.shape)
     x, y = mesh.surface_coords()
     eta0, _ = W.airy_plus_spectrum_state(d, x, y, seed=2)
     dev = torch.device("cuda", 0)
@@ -489,7 +503,8 @@ def main_ensemble(args):
     dev = torch.device("cuda", 0)
     tanks = W.ensemble_tanks(n=args.tanks, seed=5)
     opts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=1e-5,
-                             cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree, max_iter=50000)
+                             cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
+                             coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind, max_iter=50000)
     meshes, etas, phiss, dts = [], [], [], []
     for d in tanks:
         ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"]
@@ -545,6 +560,11 @@ def main_ensemble(args):
         "orders": sorted(set(d["p"] for d in tanks)), "finite": ok, "gpu_launches": launches,
         "clocks": clk.summary(), "data": "synthetic"}))
     return 0
+
+
+def coarse_mode(args):
+    from paper_2506_09435_gb300 import fnpf
+    return fnpf.FNPF_COARSE_CLUSTER if args.coarse_solver == "cluster" else fnpf.FNPF_COARSE_LAUNCHES
 
 
 def main():

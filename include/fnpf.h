@@ -56,6 +56,18 @@ typedef enum {
 enum { FNPF_BOX = 0, FNPF_ISOPARAMETRIC = 1 };
 enum { FNPF_FP64 = 0, FNPF_MIXED = 1 };
 enum { FNPF_JACOBI = 0, FNPF_PMG = 1 };
+/* Coarsest multigrid level (p = 1): FNPF_COARSE_CLUSTER assembles its 27-point
+ * (9-point in 2D) stencil once per solve and runs the whole coarse Chebyshev
+ * sweep in one kernel on one thread-block cluster of 8 CTAs (levels of at most
+ * 32768 unknowns; larger ones fall back to FNPF_COARSE_LAUNCHES, one operator
+ * launch per Chebyshev step).  Both apply the same polynomial. */
+enum { FNPF_COARSE_LAUNCHES = 0, FNPF_COARSE_CLUSTER = 1 };
+/* Chebyshev smoothers of FNPF_PMG: FNPF_CHEB_FIRST = first-kind Chebyshev
+ * acceleration of Jacobi on [lmax/20, lmax] (Saad, Iterative Methods, Alg.
+ * 12.1); FNPF_CHEB_FOURTH = fourth-kind Chebyshev smoother on [0, lmax]
+ * (Lottes, Numer. Linear Algebra Appl. 2023).  lmax of D^-1 A is estimated per
+ * level on the device. */
+enum { FNPF_CHEB_FIRST = 1, FNPF_CHEB_FOURTH = 4 };
 
 /* Mesh descriptor.  All arrays are HOST pointers, copied at creation. */
 typedef struct {
@@ -89,6 +101,8 @@ typedef struct {
                               once per solve into device memory (6 doubles per
                               point, allocated at the first solve) and read it in
                               every application; 0 = rebuild it per application */
+  int coarse_solver;       /* FNPF_COARSE_CLUSTER or FNPF_COARSE_LAUNCHES (FNPF_PMG) */
+  int cheb_kind;           /* FNPF_CHEB_FIRST or FNPF_CHEB_FOURTH (FNPF_PMG)        */
 } fnpf_opts;
 
 typedef struct {
@@ -107,7 +121,8 @@ fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t*
 
 /* Fills *opts with the defaults: FP64, Jacobi, rtol 1e-10, atol 0,
  * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 6,
- * inner_rtol 1e-5, max_outer 20, use_graphs 1, store_metric 1. */
+ * inner_rtol 1e-5, max_outer 20, use_graphs 1, store_metric 1,
+ * coarse_solver FNPF_COARSE_CLUSTER, cheb_kind FNPF_CHEB_FIRST. */
 void fnpf_default_opts(fnpf_opts* opts);
 
 /* Creates a mesh on the current CUDA device: GLL tables, horizontal metric,
@@ -135,6 +150,18 @@ fnpf_status fnpf_apply_f32(fnpf_mesh* mesh, const float* eta, const float* x, fl
 
 /* d = diag(A(eta)) [N] (Jacobi preconditioner of the Laplace solve). */
 fnpf_status fnpf_diagonal(fnpf_mesh* mesh, const double* eta, double* d, void* stream);
+
+/* z = M r: one application of the FP64 preconditioner of the Laplace solve
+ * (the paper preconditions its CG with algebraic multigrid, Sec. 4 solver
+ * settings; this is the p-multigrid V-cycle of FNPF_PMG, or the Jacobi
+ * preconditioner z = diag(A_II)^-1 r of FNPF_JACOBI) for the geometry of eta
+ * [Ns]: the set-up (level geometry, diagonals, Chebyshev intervals from a
+ * deterministic Lanczos run) is done from eta on every call.  r, z [N_I] device
+ * doubles in the interior layout of the unknowns (planes 0 .. nv-2), not
+ * overlapping.  M is a fixed symmetric positive definite operator for a given
+ * eta and options.  Ignores opts.precision (always FP64).  Synchronous on
+ * `stream` only through stream order.  Errors: EINVAL (NULL), ENOMEM, ECUDA. */
+fnpf_status fnpf_precond_apply(fnpf_mesh* mesh, const double* eta, const double* r, double* z, void* stream);
 
 /* Laplace solve (Sec. 3.4 Steps 4.1-4.3): A_II phi_I = -A_IS phi_eta.
  * eta, phis [Ns]; phi [N]: on entry its first N_I entries are the initial
@@ -193,6 +220,12 @@ fnpf_status fnpf_apply_noalloc(const fnpf_mesh_desc* desc, const double* h, cons
  * chosen shape indices are returned when the pointers are non-NULL.  Runs
  * automatically before the first solve of a mesh; waits for the stream. */
 fnpf_status fnpf_autotune(fnpf_mesh* mesh, const double* eta, int* variant64, int* variant32, void* stream);
+
+/* Sets the elements-per-CTA shapes (0..3 in 3D, 0 in 2D; the same indices
+ * fnpf_autotune returns) of the FP64 and FP32 operator kernels by hand and
+ * marks the mesh as tuned, so that no later solve re-tunes it.  Host-only.
+ * Errors: EINVAL (index out of range). */
+fnpf_status fnpf_set_shapes(fnpf_mesh* mesh, int variant64, int variant32);
 
 /* Instrumentation (tracing): when enabled, every operator application issued
  * by a solve is bracketed by CUDA events on the solve's stream, and the

@@ -53,6 +53,11 @@ fnpf_status fnpf_diagonal(fnpf_mesh* m, const double* eta, double* d, void* stre
   return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "diagonal");
 }
 
+fnpf_status fnpf_precond_apply(fnpf_mesh* m, const double* eta, const double* r, double* z, void* stream) {
+  if (!m || !eta || !r || !z) return FNPF_EINVAL;
+  return fnpf::precond_apply(m, eta, r, z, (cudaStream_t)stream);
+}
+
 fnpf_status fnpf_laplace_solve(fnpf_mesh* m, const double* eta, const double* phis, double* phi,
                                fnpf_solve_info* info, void* stream) {
   if (!m || !eta || !phis || !phi) return FNPF_EINVAL;
@@ -280,6 +285,22 @@ fnpf_status fnpf_autotune(fnpf_mesh* m, const double* eta, int* variant64, int* 
   if (variant64) *variant64 = m->variant64;
   if (variant32) *variant32 = m->variant32;
   return st;
+}
+
+fnpf_status fnpf_set_shapes(fnpf_mesh* m, int variant64, int variant32) {
+  if (!m) return FNPF_EINVAL;
+  const int nv = fnpf::apply_variants(m->g.n, m->g.dim);
+  if (variant64 < 0 || variant64 >= nv || variant32 < 0 || variant32 >= nv) {
+    m->err = "shape index out of range";
+    return FNPF_EINVAL;
+  }
+  m->variant64 = variant64;
+  m->variant32 = variant32;
+  m->tuned = true;
+  for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);   // captured launches use the shapes
+  if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
+  m->step_exec = nullptr;
+  return FNPF_OK;
 }
 
 fnpf_status fnpf_profile_enable(fnpf_mesh* m, int on) {

@@ -32,7 +32,7 @@ cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, 
   return dispatch<T>(g, t, a, AX_DIAG, 1, s);
 }
 
-int apply_variants(int n, int dim) { return dim == 2 ? 1 : 3; }
+int apply_variants(int n, int dim) { return dim == 2 ? 1 : kCtaVariants; }
 
 int64_t geom_points(const Geom& g) { return (int64_t)g.nz * g.n_ecol * g.n * g.lines; }
 

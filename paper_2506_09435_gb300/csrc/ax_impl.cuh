@@ -558,25 +558,31 @@ cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& 
   return launch_gather<T, DIM>(g, a.ring, a.yI, a.ys, a.skip, s);
 }
 
-// Elements-per-CTA candidates for order N (3D); 2D uses one shape.
+// Elements-per-CTA candidates for order N (3D); 2D uses one shape.  The
+// fourth choice gives grids that fill the 152 SMs evenly for common column
+// counts (e.g. 7 columns of N = 7: 147 CTAs for 32 x 32 columns, where 2 and 4
+// leave a partial second wave on a third of the SMs).
 template <int N>
 struct CtaChoices;
-template <> struct CtaChoices<2> { static constexpr int c[3] = {16, 32, 64}; };
-template <> struct CtaChoices<3> { static constexpr int c[3] = {7, 14, 28}; };
-template <> struct CtaChoices<4> { static constexpr int c[3] = {4, 8, 16}; };
-template <> struct CtaChoices<5> { static constexpr int c[3] = {3, 5, 10}; };
-template <> struct CtaChoices<6> { static constexpr int c[3] = {2, 4, 8}; };
-template <> struct CtaChoices<7> { static constexpr int c[3] = {1, 2, 4}; };
-template <> struct CtaChoices<8> { static constexpr int c[3] = {1, 2, 4}; };
-template <> struct CtaChoices<9> { static constexpr int c[3] = {1, 2, 3}; };
+template <> struct CtaChoices<2> { static constexpr int c[4] = {16, 32, 64, 8}; };
+template <> struct CtaChoices<3> { static constexpr int c[4] = {7, 14, 28, 4}; };
+template <> struct CtaChoices<4> { static constexpr int c[4] = {4, 8, 16, 2}; };
+template <> struct CtaChoices<5> { static constexpr int c[4] = {3, 5, 10, 2}; };
+template <> struct CtaChoices<6> { static constexpr int c[4] = {2, 4, 8, 6}; };
+template <> struct CtaChoices<7> { static constexpr int c[4] = {1, 2, 4, 7}; };
+template <> struct CtaChoices<8> { static constexpr int c[4] = {1, 2, 4, 3}; };
+template <> struct CtaChoices<9> { static constexpr int c[4] = {1, 2, 3, 4}; };
+static_assert(sizeof(CtaChoices<7>::c) / sizeof(int) == kCtaVariants, "one shape per variant");
 
 template <typename T, int N>
 cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, int variant,
                         cudaStream_t s) {
   if (g.dim == 2) return launch_ax_shape<T, N, 2, (128 + N - 1) / N>(g, t, a, mode, s);
   constexpr int C0 = CtaChoices<N>::c[0], C1 = CtaChoices<N>::c[1], C2 = CtaChoices<N>::c[2];
+  constexpr int C3 = CtaChoices<N>::c[3];
   if (mode == AX_DIAG || mode == AX_GEOM || variant == 1) return launch_ax_shape<T, N, 3, C1>(g, t, a, mode, s);
   if (variant == 0) return launch_ax_shape<T, N, 3, C0>(g, t, a, mode, s);
+  if (variant == 3) return launch_ax_shape<T, N, 3, C3>(g, t, a, mode, s);
   return launch_ax_shape<T, N, 3, C2>(g, t, a, mode, s);
 }
 

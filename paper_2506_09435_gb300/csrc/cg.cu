@@ -417,6 +417,83 @@ __global__ void __launch_bounds__(NT) negate_kernel(int64_t n, const double* a, 
   GRID_LOOP(i, n) b[i] = -a[i];
 }
 
+__global__ void __launch_bounds__(NT) scale_kernel(int64_t n, const double* d, const double* a, double* b) {
+  GRID_LOOP(i, n) b[i] = d[i] * a[i];
+}
+
+// Validates the multigrid options, creates the hierarchy at the first use and
+// passes the coarse-solver choice on.
+fnpf_status ensure_mg(fnpf_mesh* m) {
+  if (m->opts.cheb_degree < 1 || m->opts.cheb_degree >= kMaxChebDegree || m->opts.coarse_iters < 1 ||
+      m->opts.coarse_iters >= kMaxChebDegree) {
+    m->err = "Chebyshev degrees must be in 1..63";
+    return FNPF_EINVAL;
+  }
+  if (m->opts.coarse_solver != FNPF_COARSE_CLUSTER && m->opts.coarse_solver != FNPF_COARSE_LAUNCHES) {
+    m->err = "coarse_solver must be FNPF_COARSE_CLUSTER or FNPF_COARSE_LAUNCHES";
+    return FNPF_EINVAL;
+  }
+  if (m->opts.cheb_kind != FNPF_CHEB_FIRST && m->opts.cheb_kind != FNPF_CHEB_FOURTH) {
+    m->err = "cheb_kind must be FNPF_CHEB_FIRST or FNPF_CHEB_FOURTH";
+    return FNPF_EINVAL;
+  }
+  if (!m->mg) {
+    std::string why;
+    m->mg = mg_create(m->g, m->h, m->Xs, m->Ys, m->iso, m->Lx, m->Ly, &why);
+    if (!m->mg) {
+      m->err = why;
+      return FNPF_ENOMEM;
+    }
+  }
+  mg_set_coarse(m->mg, m->opts.coarse_solver);
+  mg_set_kind(m->mg, m->opts.cheb_kind);
+  return FNPF_OK;
+}
+
+// Allocates the stored FP64 metric at its first use.
+fnpf_status ensure_g64(fnpf_mesh* m) {
+  if (m->G64) return FNPF_OK;
+  const int64_t ng = (m->g.dim == 3 ? 6 : 3) * geom_points(m->g);
+  if (cudaMalloc((void**)&m->G64, ng * sizeof(double)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    m->G64 = nullptr;
+    m->err = "cannot allocate the stored metric";
+    return FNPF_ENOMEM;
+  }
+  return FNPF_OK;
+}
+
+fnpf_status precond_apply(fnpf_mesh* m, const double* eta, const double* r, double* z, cudaStream_t s) {
+  const Geom& g = m->g;
+  const Tables<double> t = m->tables();
+  const int nb = vec_blocks(g.NI);
+  if (m->opts.precond != FNPF_PMG) {
+    FNPF_CK(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
+    vec::invert_kernel<double><<<nb, NT, 0, s>>>(g.NI, m->dinv);
+    scale_kernel<<<nb, NT, 0, s>>>(g.NI, m->dinv, r, z);
+    FNPF_CK(cudaGetLastError());
+    return FNPF_OK;
+  }
+  fnpf_status st = ensure_mg(m);
+  if (st != FNPF_OK) return st;
+  m->g64_active = false;
+  if (m->opts.store_metric) {
+    if ((st = ensure_g64(m)) != FNPF_OK) return st;
+    FNPF_CK(launch_geom<double>(g, t, eta, m->G64, s));
+    m->g64_active = true;
+  }
+  cudaError_t e = mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64,
+                                     m->opts.cheb_degree, m->opts.coarse_iters, true, s);
+  if (e == cudaSuccess)
+    e = mg_apply<double>(m->mg, t, eta, level0_G<double>(m), r, z, m->ring, m->variant64, m->opts.cheb_degree,
+                         m->opts.coarse_iters, nullptr, s, &m->launches);
+  m->g64_active = false;
+  m->cheb_valid[0] = false;   // the next solve estimates its own intervals
+  FNPF_CK(e);
+  FNPF_CK(cudaGetLastError());
+  return FNPF_OK;
+}
+
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, double* x, fnpf_solve_info* info,
                      cudaStream_t s, const double* rhs) {
   const Geom& g = m->g;
@@ -426,18 +503,9 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   CgScalars* sc = m->sc;
   const bool mixed = m->opts.precision == FNPF_MIXED;
   const bool pmg = m->opts.precond == FNPF_PMG;
-  if (pmg && (m->opts.cheb_degree < 1 || m->opts.cheb_degree >= kMaxChebDegree || m->opts.coarse_iters < 1 ||
-              m->opts.coarse_iters >= kMaxChebDegree)) {
-    m->err = "Chebyshev degrees must be in 1..63";
-    return FNPF_EINVAL;
-  }
-  if (pmg && !m->mg) {
-    std::string why;
-    m->mg = mg_create(g, m->h, m->Xs, m->Ys, m->iso, m->Lx, m->Ly, &why);
-    if (!m->mg) {
-      m->err = why;
-      return FNPF_ENOMEM;
-    }
+  if (pmg) {
+    const fnpf_status st = ensure_mg(m);
+    if (st != FNPF_OK) return st;
   }
   if (info) FNPF_CK(cudaEventRecord(m->ev0, s));
   // the solve reads eta from a mesh-owned copy, so captured graphs keep valid pointers
@@ -449,14 +517,8 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   // operator application of the solve (fewer FP64 instructions per point)
   m->g64_active = false;
   if (!mixed && m->opts.store_metric) {
-    if (!m->G64) {
-      const int64_t ng = (g.dim == 3 ? 6 : 3) * geom_points(g);
-      if (cudaMalloc((void**)&m->G64, ng * sizeof(double)) != cudaSuccess) {
-        m->G64 = nullptr;
-        m->err = "cannot allocate the stored metric";
-        return FNPF_ENOMEM;
-      }
-    }
+    const fnpf_status st = ensure_g64(m);
+    if (st != FNPF_OK) return st;
     FNPF_CK(launch_geom<double>(g, t, eta, m->G64, s));
     m->g64_active = true;
     m->launches += 1;

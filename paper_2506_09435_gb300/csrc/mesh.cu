@@ -272,6 +272,8 @@ void fnpf_default_opts(fnpf_opts* o) {
   o->max_outer = 20;
   o->use_graphs = 1;
   o->store_metric = 1;
+  o->coarse_solver = FNPF_COARSE_CLUSTER;
+  o->cheb_kind = FNPF_CHEB_FIRST;
 }
 
 fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, fnpf_mesh** out) {
@@ -413,6 +415,8 @@ fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
   m->step_exec = nullptr;
   m->cheb_valid[0] = m->cheb_valid[1] = false;
+  fnpf::mg_set_coarse(m->mg, o->coarse_solver);
+  fnpf::mg_set_kind(m->mg, o->cheb_kind);
   return FNPF_OK;
 }
 

@@ -147,4 +147,6 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
 // or of A_II x = rhs when rhs [NI] is given (phis is then unused).
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,
                      cudaStream_t s, const double* rhs = nullptr);
+// z = M r with the FP64 preconditioner set up from eta (fnpf_precond_apply).
+fnpf_status precond_apply(fnpf_mesh* m, const double* eta, const double* r, double* z, cudaStream_t s);
 }  // namespace fnpf

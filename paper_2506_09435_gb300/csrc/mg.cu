@@ -9,9 +9,11 @@
 // factors exactly like the fine one.  Transfers: see mg_impl.cuh.
 //
 // Smoother: Chebyshev iteration on D^-1 A over [lmax / range, lmax] (Saad,
-// Iterative Methods, Algorithm 12.1, with the Jacobi diagonal), degree d pre-
+// Iterative Methods, Algorithm 12.1, with the Jacobi diagonal), or the
+// fourth-kind Chebyshev smoother on [0, lmax] (see lz_eig_kernel), degree d pre-
 // and post-smoothing; the coarsest level gets one Chebyshev sweep of degree
-// d_c over a wider interval.  Every sweep is a fixed polynomial in D^-1 A, so
+// d_c over a wider interval (on one thread-block cluster when the coarsest
+// level is small, see coarse_cheb_kernel).  Every sweep is a fixed polynomial in D^-1 A, so
 // the V-cycle is a fixed symmetric operator and plain PCG applies.
 // lmax per level comes from a 10-step Jacobi-CG Lanczos run on a fixed
 // pseudo-random right-hand side; the largest eigenvalue of the Lanczos
@@ -38,6 +40,13 @@ constexpr int kMaxLevels = 5;
 constexpr int kLanczos = 10;
 constexpr double kSafety = 1.1;
 constexpr double kSmoothRange = 20.0;
+
+// Cluster solve of the coarsest level: one cluster of kCoarseCluster CTAs
+// (the portable maximum), kCoarseRows unknowns per thread at most.
+constexpr int kCoarseCluster = 8;
+constexpr int kCoarseThreads = 1024;
+constexpr int kCoarseRows = 4;
+constexpr int64_t kCoarseMaxRows = (int64_t)kCoarseCluster * kCoarseThreads * kCoarseRows;
 
 inline cudaError_t launch_transfer(const Geom& gf, const Geom& gc, const double* J, const double* in, double* out,
                                    double* ring, int mode, const int* skip, cudaStream_t s) {
@@ -124,9 +133,11 @@ __global__ void __launch_bounds__(vec::NT) lz_init_finish_kernel(CgScalars* sc, 
 
 // Largest eigenvalue of the Lanczos tridiagonal matrix from the CG coefficients
 // (T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_j,j+1 = sqrt(b_j)/a_j), by Sturm-count
-// bisection; writes the Chebyshev interval.
+// bisection; writes the smoother's step coefficients for kind 1 (first-kind
+// Chebyshev on [lmax / range, lmax]) or kind 4 (fourth-kind Chebyshev on
+// [0, lmax], no lower bound needed).
 __global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, int kmax, double safety, double range,
-                              ChebParams* out) {
+                              int kind, ChebParams* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int k = sc->iters < kmax ? sc->iters : kmax;
   double a[32], b[32];
@@ -162,6 +173,21 @@ __global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, int kmax,
   }
   out->lmax = safety * lmax;
   out->range = range;
+  if (kind == FNPF_CHEB_FOURTH) {
+    // Fourth-kind Chebyshev smoother (Lottes, "Optimal polynomial smoothers for
+    // multigrid V-cycles", Numer. Linear Algebra Appl. 2023): with rho = lmax,
+    // d_0 = 4 / (3 rho) D^-1 r_0 and, for k >= 1,
+    // d_k = (2k - 1) / (2k + 3) d_{k-1} + (8k + 4) / ((2k + 3) rho) D^-1 r_k.
+    const double rho = out->lmax;
+    out->inv_theta = 4.0 / (3.0 * rho);
+    out->c1[0] = 0.0;
+    out->c2[0] = 0.0;
+    for (int k = 1; k < kMaxChebDegree; ++k) {
+      out->c1[k] = (2.0 * k - 1.0) / (2.0 * k + 3.0);
+      out->c2[k] = (8.0 * k + 4.0) / ((2.0 * k + 3.0) * rho);
+    }
+    return;
+  }
   // Chebyshev recurrence on [lmax / range, lmax]: theta = centre, delta = half
   // width, sigma = theta / delta, rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1})
   const double lm = out->lmax, lmin = lm / range;
@@ -218,6 +244,227 @@ template <typename T>
 __global__ void __launch_bounds__(vec::NT) residual_kernel(int64_t n, const T* b, const T* w, T* r, const int* skip) {
   if (skip && *skip) return;
   FNPF_GRID_LOOP(i, n) r[i] = (b ? b[i] : r[i]) - w[i];
+}
+
+// ---------------------------------------------------------------------------- coarsest level on one cluster
+//
+// At p = 1 every unknown couples only to the 3 x 3 x 3 (3 x 3 in 2D) node block
+// around it, so the level operator is a structured stencil.  stencil_kernel
+// assembles it from the level's stored metric G (the same quadrature as the
+// matrix-free operator: y = sum_e Dhat^T G Dhat x at the element's GLL points);
+// coarse_cheb_kernel then runs the whole Chebyshev sweep on it inside one
+// thread-block cluster, with a hardware cluster barrier between steps instead
+// of one operator, gather and update launch per step.
+
+template <int DIM>
+struct Stencil {
+  static constexpr int slots = DIM == 3 ? 27 : 9;
+  // slot of the neighbour at offset (dx, dy, dz), each in -1..1
+  __host__ __device__ static constexpr int slot(int dx, int dy, int dz) {
+    return DIM == 3 ? (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1) : (dz + 1) * 3 + (dx + 1);
+  }
+};
+
+// One row per thread: the node's row of A_II, summed over the (up to 8)
+// elements that hold it in a fixed order.  coef[slot * NI + row].
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) stencil_kernel(Geom g, const T* __restrict__ D, const T* __restrict__ G,
+                                                      T* coef) {
+  constexpr int NSL = Stencil<DIM>::slots;
+  constexpr int LQ = DIM == 3 ? 4 : 2;       // vertical lines of a p = 1 element column
+  constexpr int NJ = DIM == 3 ? 2 : 1;
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= g.NI) return;
+  const int k = (int)(row / g.ns), col = (int)(row - (int64_t)k * g.ns);
+  const int ix = col % g.ncx, iy = col / g.ncx;
+  T acc[NSL];
+#pragma unroll
+  for (int q = 0; q < NSL; ++q) acc[q] = T(0);
+  int ex[2], ia[2], ey[2] = {0, 0}, jb[2] = {0, 0};
+  const int nxo = line_owners(ix, 1, g.nx, g.px, ex, ia);
+  const int nyo = DIM == 3 ? line_owners(iy, 1, g.ny, g.py, ey, jb) : 1;
+  const int64_t PT = (int64_t)g.nz * g.n_ecol * 2 * LQ;
+  for (int c = 0; c < 2; ++c) {           // local vertical index of the node in element layer l
+    const int l = k - c;
+    if (l < 0 || l >= g.nz) continue;
+    for (int yo = 0; yo < nyo; ++yo)
+      for (int xo = 0; xo < nxo; ++xo) {
+        const int a = ia[xo], b = jb[yo];
+        const int ecol = ey[yo] * g.nx + ex[xo];
+        for (int qk = 0; qk < 2; ++qk)
+          for (int qj = 0; qj < NJ; ++qj)
+            for (int qi = 0; qi < 2; ++qi) {
+              // reference gradient of the node's basis function at GLL point q
+              const T gr = (qj == b && qk == c) ? D[qi * 2 + a] : T(0);
+              const T gs = (DIM == 3 && qi == a && qk == c) ? D[qj * 2 + b] : T(0);
+              const T gt = (qi == a && qj == b) ? D[qk * 2 + c] : T(0);
+              if (gr == T(0) && gs == T(0) && gt == T(0)) continue;
+              const int64_t pt = (((int64_t)l * g.n_ecol + ecol) * 2 + qk) * LQ + qj * 2 + qi;
+              T vr, vs = T(0), vt;
+              if (DIM == 3) {
+                const T grr = G[pt], grs = G[PT + pt], gss = G[2 * PT + pt];
+                const T grt = G[3 * PT + pt], gst = G[4 * PT + pt], gtt = G[5 * PT + pt];
+                vr = grr * gr + grs * gs + grt * gt;
+                vs = grs * gr + gss * gs + gst * gt;
+                vt = grt * gr + gst * gs + gtt * gt;
+              } else {
+                const T grr = G[pt], grt = G[PT + pt], gtt = G[2 * PT + pt];
+                vr = grr * gr + grt * gt;
+                vt = grt * gr + gtt * gt;
+              }
+              for (int c2 = 0; c2 < 2; ++c2)
+                for (int b2 = 0; b2 < NJ; ++b2)
+                  for (int a2 = 0; a2 < 2; ++a2) {
+                    const T hr = (qj == b2 && qk == c2) ? D[qi * 2 + a2] : T(0);
+                    const T hs = (DIM == 3 && qi == a2 && qk == c2) ? D[qj * 2 + b2] : T(0);
+                    const T ht = (qi == a2 && qj == b2) ? D[qk * 2 + c2] : T(0);
+                    acc[Stencil<DIM>::slot(a2 - a, b2 - b, c2 - c)] += hr * vr + hs * vs + ht * vt;
+                  }
+            }
+      }
+  }
+  // the plane above the last interior one is the Dirichlet surface: not in A_II
+  if (k + 1 > g.nv - 2)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        if (DIM == 3 || dy == 0) acc[Stencil<DIM>::slot(dx, dy, 1)] = T(0);
+#pragma unroll
+  for (int q = 0; q < NSL; ++q) coef[(int64_t)q * g.NI + row] = acc[q];
+}
+
+// Neighbour index along one direction (-1 outside a walled boundary).
+__device__ __forceinline__ int nbr_index(int i, int o, int n, int periodic) {
+  int a = i + o;
+  if (a < 0) a = periodic ? a + n : -1;
+  else if (a >= n) a = periodic ? a - n : -1;
+  return a;
+}
+
+// (A_II d)_row from the stencil; d is read through L2 only (other CTAs of the
+// cluster wrote it before the last cluster barrier).
+template <typename T, int DIM>
+__device__ __forceinline__ T stencil_row(const Geom& g, const T* __restrict__ coef, const T* d, int64_t row) {
+  const int k = (int)(row / g.ns), col = (int)(row - (int64_t)k * g.ns);
+  const int ix = col % g.ncx, iy = col / g.ncx;
+  int xs[3], ys[3] = {-1, 0, -1};
+#pragma unroll
+  for (int o = -1; o <= 1; ++o) {
+    xs[o + 1] = nbr_index(ix, o, g.ncx, g.px);
+    if (DIM == 3) ys[o + 1] = nbr_index(iy, o, g.ncy, g.py);
+  }
+  T w = T(0);
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int kk = k + dz;
+    if (kk < 0 || kk > g.nv - 2) continue;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (DIM == 2 && dy != 0) continue;
+      const int yy = ys[dy + 1];
+      if (yy < 0) continue;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = xs[dx + 1];
+        if (xx < 0) continue;
+        const T cv = coef[(int64_t)Stencil<DIM>::slot(dx, dy, dz) * g.NI + row];
+        w += cv * __ldcg(d + (int64_t)kk * g.ns + (int64_t)yy * g.ncx + xx);
+      }
+    }
+  }
+  return w;
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The coarsest level's Chebyshev sweep from x = 0 (the same recurrence as
+// cheb_start_kernel / cheb_step_kernel) in one launch of one cluster.  Each
+// thread keeps its rows' r, x and direction in registers; directions are
+// exchanged through the double buffer dbuf [2][NI] in global memory, one
+// cluster barrier per step.  Uniform control flow: every thread reaches every
+// barrier.
+template <typename T, int DIM>
+__global__ void __cluster_dims__(kCoarseCluster, 1, 1) __launch_bounds__(kCoarseThreads)
+    coarse_cheb_kernel(Geom g, const T* __restrict__ coef, const T* __restrict__ dinv, const T* __restrict__ b,
+                       T* x, T* dbuf, const ChebParams* cp, int degree, const int* skip) {
+  if (skip && *skip) return;   // the same value for every CTA of the cluster
+  const int64_t n = g.NI;
+  const int nthr = kCoarseCluster * kCoarseThreads;
+  const int tid = blockIdx.x * kCoarseThreads + threadIdx.x;
+  T r[kCoarseRows], xv[kCoarseRows], dv[kCoarseRows];
+  const T it = (T)cp->inv_theta;
+#pragma unroll
+  for (int m = 0; m < kCoarseRows; ++m) {
+    const int64_t row = tid + (int64_t)m * nthr;
+    r[m] = xv[m] = dv[m] = T(0);
+    if (row < n) {
+      r[m] = b[row];
+      dv[m] = it * dinv[row] * r[m];
+      xv[m] = dv[m];
+      dbuf[row] = dv[m];
+    }
+  }
+  for (int k = 1; k < degree; ++k) {
+    cluster_barrier();
+    const T* dc = dbuf + (int64_t)((k - 1) & 1) * n;
+    T* dn = dbuf + (int64_t)(k & 1) * n;
+    const T c1 = (T)cp->c1[k], c2 = (T)cp->c2[k];
+#pragma unroll
+    for (int m = 0; m < kCoarseRows; ++m) {
+      const int64_t row = tid + (int64_t)m * nthr;
+      if (row < n) {
+        r[m] -= stencil_row<T, DIM>(g, coef, dc, row);
+        dv[m] = c1 * dv[m] + c2 * dinv[row] * r[m];
+        xv[m] += dv[m];
+        dn[row] = dv[m];
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kCoarseRows; ++m) {
+    const int64_t row = tid + (int64_t)m * nthr;
+    if (row < n) x[row] = xv[m];
+  }
+}
+
+template <typename T>
+cudaError_t launch_stencil(const Geom& g, const T* D, const T* G, T* coef, cudaStream_t s) {
+  const unsigned nb = (unsigned)((g.NI + 127) / 128);
+  if (g.dim == 3) stencil_kernel<T, 3><<<nb, 128, 0, s>>>(g, D, G, coef);
+  else stencil_kernel<T, 2><<<nb, 128, 0, s>>>(g, D, G, coef);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarse_cheb(const Geom& g, const T* coef, const T* dinv, const T* b, T* x, T* dbuf,
+                               const ChebParams* cp, int degree, const int* skip, cudaStream_t s) {
+  if (g.dim == 3)
+    coarse_cheb_kernel<T, 3><<<kCoarseCluster, kCoarseThreads, 0, s>>>(g, coef, dinv, b, x, dbuf, cp, degree, skip);
+  else
+    coarse_cheb_kernel<T, 2><<<kCoarseCluster, kCoarseThreads, 0, s>>>(g, coef, dinv, b, x, dbuf, cp, degree, skip);
+  return cudaGetLastError();
+}
+
+// Whether one cluster of the coarse kernel can be resident on this device.
+bool cluster_launch_ok() {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCoarseCluster);
+  cfg.blockDim = dim3(kCoarseThreads);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCoarseCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, (const void*)coarse_cheb_kernel<double, 3>, &cfg);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return nc > 0;
 }
 
 // ---------------------------------------------------------------------------- host helpers
@@ -289,7 +536,12 @@ struct Mg {
   double* hist = nullptr;         // [L][2 * kLanczos]
   CgScalars* sc = nullptr;        // [L] Lanczos scalars
   double* part = nullptr;         // [4 * kVecBlocks]
+  bool fusable = false;           // the coarsest level fits the cluster kernel
+  int coarse_mode = FNPF_COARSE_CLUSTER;
+  int cheb_kind = FNPF_CHEB_FIRST;
   std::vector<void*> allocs;
+
+  bool fused() const { return fusable && coarse_mode == FNPF_COARSE_CLUSTER; }
 
   template <typename T>
   MgLevelBufs<T>* bufs();
@@ -312,6 +564,13 @@ void mg_destroy(Mg* mg) {
 }
 
 int mg_levels(const Mg* mg) { return mg ? mg->L : 0; }
+void mg_set_coarse(Mg* mg, int mode) {
+  if (mg) mg->coarse_mode = mode;
+}
+void mg_set_kind(Mg* mg, int kind) {
+  if (mg) mg->cheb_kind = kind;
+}
+bool mg_coarse_fused(const Mg* mg) { return mg && mg->fused(); }
 
 Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<double>& X0,
               const std::vector<double>& Y0, bool iso, double Lx, double Ly, std::string* err) {
@@ -416,6 +675,19 @@ Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<d
     F.Js = sJs;
     F.eta = seta;
   }
+  // coarsest level on one cluster: stencil, direction buffers, FP32 metric
+  const Geom& gc = mg->g[mg->L - 1];
+  mg->fusable = mg->L >= 2 && gc.p == 1 && gc.NI <= kCoarseMaxRows && cluster_launch_ok();
+  if (mg->fusable) {
+    MgLevelBufs<double>& B = mg->b64[mg->L - 1];
+    MgLevelBufs<float>& F = mg->b32[mg->L - 1];
+    const int nsl = gc.dim == 3 ? Stencil<3>::slots : Stencil<2>::slots;
+    alloc((void**)&B.coef, (size_t)nsl * gc.NI * sizeof(double));
+    alloc((void**)&B.dbuf, (size_t)2 * gc.NI * sizeof(double));
+    alloc((void**)&F.coef, (size_t)nsl * gc.NI * sizeof(float));
+    alloc((void**)&F.dbuf, (size_t)2 * gc.NI * sizeof(float));
+    alloc((void**)&F.G, (size_t)(gc.dim == 3 ? 6 : 3) * geom_points(gc) * sizeof(float));
+  }
   alloc((void**)&mg->cheb64, mg->L * sizeof(ChebParams));
   alloc((void**)&mg->cheb32, mg->L * sizeof(ChebParams));
   alloc((void**)&mg->hist, mg->L * 2 * kLanczos * sizeof(double));
@@ -494,8 +766,15 @@ template <typename T>
 cudaError_t vcycle(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* G0, const T* b, T* x, T* ring,
                    int variant, int degree, int coarse_degree, const int* skip, cudaStream_t s, int64_t* nl) {
   cudaError_t e;
-  if (l == mg->L - 1)
+  if (l == mg->L - 1) {
+    if (mg->fused()) {
+      MgLevelBufs<T>& C = mg->bufs<T>()[l];
+      *nl += 1;
+      return launch_coarse_cheb<T>(mg->g[l], C.coef, C.dinv, b, x, C.dbuf, mg->cheb<T>() + l, coarse_degree, skip,
+                                   s);
+    }
     return cheb_sweep<T>(mg, l, t0, eta0, G0, b, x, coarse_degree, true, false, ring, variant, skip, s, nl);
+  }
   MgLevelBufs<T>* Lv = mg->bufs<T>();
   if ((e = cheb_sweep<T>(mg, l, t0, eta0, G0, b, x, degree, true, true, ring, variant, skip, s, nl)) != cudaSuccess)
     return e;
@@ -533,8 +812,11 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
     const int lv = l == 0 ? variant : 1;
     if ((e = launch_diag<T>(g, t, eta, L.dinv, nullptr, ring, s)) != cudaSuccess) return e;
     vec::invert_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.dinv);
-    if (l > 0 && G0 && L.G)
+    const bool coarse_fused = l == mg->L - 1 && mg->fused();
+    if (l > 0 && L.G && (G0 || coarse_fused))
       if ((e = launch_geom<T>(g, t, eta, L.G, s)) != cudaSuccess) return e;
+    if (coarse_fused)
+      if ((e = launch_stencil<T>(g, t.D, L.G, L.coef, s)) != cudaSuccess) return e;
     if (!estimate) continue;
     const T* Gl = l == 0 ? G0 : (G0 ? L.G : nullptr);
     // Lanczos through Jacobi-CG: x = X, r = R, z = Dd, p = P, q = W
@@ -551,7 +833,7 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
       vec::pupdate_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.Dd, L.P, mg->part, nb, hist);
     }
     const double range = l == mg->L - 1 ? fmax(kSmoothRange, 0.25 * coarse_degree * coarse_degree) : kSmoothRange;
-    lz_eig_kernel<<<1, 1, 0, s>>>(sc, hist, kLanczos, kSafety, range, mg->cheb<T>() + l);
+    lz_eig_kernel<<<1, 1, 0, s>>>(sc, hist, kLanczos, kSafety, range, mg->cheb_kind, mg->cheb<T>() + l);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

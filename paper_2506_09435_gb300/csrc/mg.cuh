@@ -34,7 +34,10 @@ struct MgLevelBufs {
   T* Dd = nullptr;      // [NI] Chebyshev direction
   T* W = nullptr;       // [NI] operator output
   T* P = nullptr;       // [NI] CG direction of the Lanczos estimate
-  T* G = nullptr;         // stored metric of this level (FP64 solves, levels >= 1)
+  T* G = nullptr;         // stored metric of this level (FP64 solves, levels >= 1; the
+                          // coarsest level in both precisions when it is solved by the cluster kernel)
+  T* coef = nullptr;      // coarsest level: assembled 27-point (9 in 2D) stencil, [slot][NI]
+  T* dbuf = nullptr;      // coarsest level: two Chebyshev direction buffers [2][NI]
   const T* J = nullptr;   // [n_{l-1} x n_l] prolongation from this level to level l-1 (levels >= 1)
   const T* Js = nullptr;  // [n_l x n_0] surface interpolation from level 0 (levels >= 1)
 };
@@ -47,6 +50,16 @@ Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<d
               const std::vector<double>& Y0, bool iso, double Lx, double Ly, std::string* err);
 void mg_destroy(Mg* mg);
 int mg_levels(const Mg* mg);
+// Coarse solver of the next set-ups and V-cycles: FNPF_COARSE_CLUSTER runs the
+// coarsest level's Chebyshev sweep as one thread-block-cluster kernel on an
+// assembled stencil (used when the level fits, see mg.cu), FNPF_COARSE_LAUNCHES
+// as one operator launch per step.
+void mg_set_coarse(Mg* mg, int mode);
+// Polynomial of the Chebyshev smoothers of the next set-ups: FNPF_CHEB_FIRST
+// or FNPF_CHEB_FOURTH.
+void mg_set_kind(Mg* mg, int kind);
+// True when the coarsest level is solved by the cluster kernel.
+bool mg_coarse_fused(const Mg* mg);
 
 // Per-solve set-up in precision T: eta at every level, Jacobi diagonals, the
 // stored metric of the coarser levels when G0 is given, and (when `estimate`)

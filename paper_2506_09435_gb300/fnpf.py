@@ -18,6 +18,8 @@ FNPF_OK, FNPF_EINVAL, FNPF_ENOMEM, FNPF_ECUDA, FNPF_ENOCONV, FNPF_EBREAKDOWN, FN
 FNPF_BOX, FNPF_ISOPARAMETRIC = 0, 1
 FNPF_FP64, FNPF_MIXED = 0, 1
 FNPF_JACOBI, FNPF_PMG = 0, 1
+FNPF_COARSE_LAUNCHES, FNPF_COARSE_CLUSTER = 0, 1
+FNPF_CHEB_FIRST, FNPF_CHEB_FOURTH = 1, 4
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -33,7 +35,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int), ("store_metric", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int), ("store_metric", ctypes.c_int),
+                ("coarse_solver", ctypes.c_int), ("cheb_kind", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -65,6 +68,7 @@ def load():
         "fnpf_surface_coords": [vp, _dp, _dp],
         "fnpf_apply": [vp, vp, vp, vp, vp],
         "fnpf_diagonal": [vp, vp, vp, vp],
+        "fnpf_precond_apply": [vp, vp, vp, vp, vp],
         "fnpf_apply_f32": [vp, vp, vp, vp, vp],
         "fnpf_laplace_solve": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_dtn": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
@@ -77,6 +81,7 @@ def load():
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
+        "fnpf_set_shapes": [vp, ctypes.c_int, ctypes.c_int],
         "fnpf_profile_enable": [vp, ctypes.c_int],
         "fnpf_profile_read": [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p, ctypes.c_int],
         "fnpf_profile_read_fp32": [vp, ctypes.POINTER(ctypes.c_double), i64p],
@@ -222,6 +227,11 @@ class Mesh:
     def diagonal(self, eta, d, stream=None):
         self._check(_LIB.fnpf_diagonal(self._h, _ptr(eta), _ptr(d), _stream(stream)))
 
+    def precond_apply(self, eta, r, z, stream=None):
+        """z = M r, the FP64 preconditioner (p-multigrid V-cycle or Jacobi) set
+        up from eta; r, z have the N_I interior unknowns."""
+        self._check(_LIB.fnpf_precond_apply(self._h, _ptr(eta), _ptr(r), _ptr(z), _stream(stream)))
+
     def laplace_solve(self, eta, phis, phi, stream=None, info=True, check=True):
         inf = SolveInfo() if info else None
         st = _LIB.fnpf_laplace_solve(self._h, _ptr(eta), _ptr(phis), _ptr(phi),
@@ -261,6 +271,9 @@ class Mesh:
         self._check(_LIB.fnpf_step_adjoint(self._h, _ptr(eta), _ptr(phis), _ptr(lam_eta), _ptr(lam_phis),
                                            _ptr(lam_eta_out), _ptr(lam_phis_out), _ptr(lam_h), float(t),
                                            float(dt), _stream(stream)))
+
+    def set_shapes(self, variant64, variant32):
+        self._check(_LIB.fnpf_set_shapes(self._h, int(variant64), int(variant32)))
 
     def autotune(self, eta, stream=None):
         v64, v32 = ctypes.c_int(), ctypes.c_int()

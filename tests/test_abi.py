@@ -49,3 +49,4 @@ def test_count_dofs_rejects_bad_descriptors(fnpf, bad):
 def test_default_opts(fnpf):
     o = fnpf.default_opts()
     assert o.precision == fnpf.FNPF_FP64 and o.rtol == 1e-10 and o.max_iter > 0 and o.check_every > 0
+    assert o.coarse_iters == 6 and o.store_metric == 1 and o.coarse_solver == fnpf.FNPF_COARSE_CLUSTER

@@ -139,3 +139,44 @@ def test_standing_wave_2d_full_run_matches_oracle(fnpf):
         assert np.linalg.norm(p - pr) / amp_p < 1e-10
     assert rel_l2(hist[239][1], hist[239][3]) < 1e-10     # t = 3.75 T: phi_eta at its peak
     assert rel_l2(hist[255][0], hist[255][2]) < 1e-10     # t = 4 T: eta at its peak
+
+
+SHAPE_SHAPES = [(3, 5, 3, 2, 6, True, False), (3, 5, 3, 2, 4, False, True), (3, 4, 3, 1, 8, True, True),
+                (3, 7, 2, 2, 3, False, False)]
+
+
+@pytest.mark.parametrize("shape", SHAPE_SHAPES, ids=ids)
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_cta_shape_matches_oracle(fnpf, shape, variant):
+    """Each elements-per-CTA shape of the operator kernels (the autotuner's
+    candidates, including ragged last CTAs) gives the oracle's operator in
+    FP64 and FP32, and the oracle's solution through the stored-metric
+    p-multigrid solve."""
+    c = Case(fnpf, *shape, opts=fnpf.default_opts(rtol=1e-13, precond=fnpf.FNPF_PMG, max_iter=5000))
+    c.gm.set_shapes(variant, variant)
+    op = oop.Operator(c.om, c.eta, c.h)
+    x = c.rng.standard_normal(c.om.N)
+    y_ref = op.A @ x
+    y = torch.empty(c.om.N, dtype=torch.float64, device=c.dev)
+    c.gm.apply(c.t(c.eta), c.t(x), y)
+    y32 = torch.empty(c.om.N, dtype=torch.float32, device=c.dev)
+    c.gm.apply_f32(c.t(c.eta).float(), c.t(x).float(), y32)
+    torch.cuda.synchronize()
+    assert rel_max(y.cpu().numpy(), y_ref) < 1e-12
+    assert rel_max(y32.double().cpu().numpy(), y_ref) < 2e-6
+    phi_ref = osolve.laplace_solve(c.om, c.eta, c.h, c.phis)
+    phi = torch.zeros(c.om.N, dtype=torch.float64, device=c.dev)
+    info = c.gm.laplace_solve(c.t(c.eta), c.t(c.phis), phi)
+    assert info["status"] == 0
+    assert rel_l2(phi.cpu().numpy(), phi_ref) < 1e-10
+
+
+def test_set_shapes_rejects_out_of_range(fnpf):
+    c = Case(fnpf, *SHAPE_SHAPES[0])
+    for bad in [(-1, 0), (0, 4), (4, 0)]:
+        with pytest.raises(fnpf.FnpfError) as e:
+            c.gm.set_shapes(*bad)
+        assert e.value.status == fnpf.FNPF_EINVAL
+    c2 = Case(fnpf, *SHAPES[0])
+    with pytest.raises(fnpf.FnpfError):
+        c2.gm.set_shapes(1, 0)

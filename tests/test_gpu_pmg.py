@@ -95,3 +95,93 @@ def test_stored_metric_matches_on_the_fly_metric(fnpf, precond):
     assert rel_l2(sol[1], sol[0]) < 1e-12
     phi_ref = osolve.laplace_solve(c.om, c.eta, c.h, c.phis)
     assert rel_l2(sol[1], phi_ref) < 1e-10
+
+
+def _precond(c, fnpf, r, **kw):
+    c.gm.set_opts(pmg(fnpf, **kw))
+    z = torch.zeros_like(r)
+    c.gm.profile_read(reset=True)
+    c.gm.precond_apply(c.t(c.eta), r, z)
+    torch.cuda.synchronize()
+    return z, c.gm.profile_read(reset=True)["launches"]
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1], SHAPES[3], SHAPES[4], SHAPES[6], SHAPES[9],
+                                   (3, 32, 32, 2, 6, True, True)], ids=ids)
+@pytest.mark.parametrize("coarse", [6, 31])
+def test_cluster_coarse_solve_matches_per_step_launches(fnpf, shape, coarse):
+    """The coarsest level's Chebyshev sweep on one thread-block cluster (stencil
+    assembled from the level metric) applies the same polynomial as the
+    per-step operator launches: the V-cycles agree to rounding, in far fewer
+    launches."""
+    c = Case(fnpf, *shape)
+    r = torch.as_tensor(c.rng.standard_normal(c.gm.N - c.gm.ns), device=c.dev)
+    zl, nl = _precond(c, fnpf, r, coarse_iters=coarse, coarse_solver=fnpf.FNPF_COARSE_LAUNCHES)
+    zc, nc = _precond(c, fnpf, r, coarse_iters=coarse, coarse_solver=fnpf.FNPF_COARSE_CLUSTER)
+    assert nc < nl, (nc, nl)
+    assert rel_l2(zc.cpu().numpy(), zl.cpu().numpy()) < 1e-11
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[3], SHAPES[4], SHAPES[7]], ids=ids)
+@pytest.mark.parametrize("coarse_solver,kind", [("cluster", 1), ("launches", 1), ("cluster", 4), ("launches", 4)])
+def test_pmg_preconditioner_is_symmetric_positive_definite(fnpf, shape, coarse_solver, kind):
+    """PCG needs a fixed SPD preconditioner: <M r1, r2> = <r1, M r2> to
+    rounding and <M r, r> > 0 (symmetric V-cycle, restriction = prolongation^T,
+    polynomial smoothers of either kind, symmetric coarse stencil)."""
+    c = Case(fnpf, *shape)
+    mode = fnpf.FNPF_COARSE_CLUSTER if coarse_solver == "cluster" else fnpf.FNPF_COARSE_LAUNCHES
+    n = c.gm.N - c.gm.ns
+    r1 = torch.as_tensor(c.rng.standard_normal(n), device=c.dev)
+    r2 = torch.as_tensor(c.rng.standard_normal(n), device=c.dev)
+    z1, _ = _precond(c, fnpf, r1, coarse_solver=mode, cheb_kind=kind)
+    z2, _ = _precond(c, fnpf, r2, coarse_solver=mode, cheb_kind=kind)
+    a, b = float(torch.dot(z1, r2)), float(torch.dot(r1, z2))
+    scale = float(torch.linalg.norm(z1) * torch.linalg.norm(r2))
+    assert abs(a - b) < 1e-12 * scale, (a, b)
+    assert float(torch.dot(z1, r1)) > 0 and float(torch.dot(z2, r2)) > 0
+
+
+def test_jacobi_preconditioner_apply_is_inverse_diagonal(fnpf):
+    c = Case(fnpf, *SHAPES[3])
+    c.gm.set_opts(fnpf.default_opts())
+    n = c.gm.N - c.gm.ns
+    r = torch.as_tensor(c.rng.standard_normal(n), device=c.dev)
+    z = torch.zeros_like(r)
+    d = torch.zeros(c.gm.N, dtype=torch.float64, device=c.dev)
+    c.gm.precond_apply(c.t(c.eta), r, z)
+    c.gm.diagonal(c.t(c.eta), d)
+    torch.cuda.synchronize()
+    assert rel_l2(z.cpu().numpy(), (r / d[:n]).cpu().numpy()) < 1e-15
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1], SHAPES[3], SHAPES[5], SHAPES[7]], ids=ids)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fourth_kind_smoother_solve_matches_oracle(fnpf, shape, precision):
+    prec = fnpf.FNPF_MIXED if precision == "mixed" else fnpf.FNPF_FP64
+    c = Case(fnpf, *shape, opts=pmg(fnpf, precision=prec, cheb_kind=fnpf.FNPF_CHEB_FOURTH, inner_rtol=1e-5))
+    phi_ref = osolve.laplace_solve(c.om, c.eta, c.h, c.phis)
+    phi = torch.zeros(c.om.N, dtype=torch.float64, device=c.dev)
+    info = c.gm.laplace_solve(c.t(c.eta), c.t(c.phis), phi)
+    assert info["status"] == 0 and info["rel_res"] <= 1e-13
+    assert rel_l2(phi.cpu().numpy(), phi_ref) < 1e-10
+
+
+def test_fourth_kind_one_step_is_scaled_jacobi(fnpf):
+    """A p = 1 mesh has one multigrid level, so M is the coarse sweep alone; of
+    degree 1 it is 4/(3 rho) D^-1 (fourth kind) or D^-1 / theta (first kind):
+    z / (D^-1 r) is one constant, and rho = 4 / (3 const) is the same as the
+    first kind's lmax = 2 theta / (1 + 1/20)."""
+    c = Case(fnpf, *SHAPES[7])
+    n = c.gm.N - c.gm.ns
+    r = torch.as_tensor(c.rng.standard_normal(n), device=c.dev)
+    d = torch.zeros(c.gm.N, dtype=torch.float64, device=c.dev)
+    c.gm.diagonal(c.t(c.eta), d)
+    ratios = []
+    for kind in (fnpf.FNPF_CHEB_FOURTH, fnpf.FNPF_CHEB_FIRST):
+        z, _ = _precond(c, fnpf, r, coarse_iters=1, cheb_kind=kind)
+        q = (z * d[:n] / r).cpu().numpy()
+        assert np.ptp(q) < 1e-12 * abs(q.mean())
+        ratios.append(q.mean())
+    rho4 = 4.0 / (3.0 * ratios[0])
+    rho1 = 2.0 / (ratios[1] * (1.0 + 1.0 / 20.0))
+    assert abs(rho4 - rho1) < 1e-10 * rho1 and 1.0 < rho4 < 20.0
