@@ -43,13 +43,15 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--precond", default="pmg", choices=["pmg", "jacobi"])
-    ap.add_argument("--cheb-degree", type=int, default=2, help="Chebyshev degree of the FP64 path's smoothers")
+    ap.add_argument("--cheb-degree", type=int, default=3, help="Chebyshev degree of the FP64 path's smoothers")
     ap.add_argument("--mixed-cheb-degree", type=int, default=3, help="... of the mixed path's FP32 smoothers")
     ap.add_argument("--coarse-degree", type=int, default=6)
     ap.add_argument("--shape", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="elements-per-CTA shape of the operator kernels (-1: autotuned)")
     ap.add_argument("--cheb-kind", type=int, default=1, choices=[1, 4],
                     help="Chebyshev smoother: 1 = first kind on [lmax/20, lmax], 4 = fourth kind on [0, lmax]")
+    ap.add_argument("--cheb-range", type=float, default=160.0,
+                    help="first-kind Chebyshev smoothers target [lmax / range, lmax]")
     ap.add_argument("--coarse-solver", default="cluster", choices=["cluster", "launches"],
                     help="coarsest multigrid level on one thread-block cluster, or one launch per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -215,7 +217,8 @@ def main_gb300(args):
     cdeg = args.mixed_cheb_degree if args.precision == "mixed" else args.cheb_degree
     opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000, precond=pre, cheb_degree=cdeg,
                              coarse_iters=args.coarse_degree, coarse_solver=coarse_mode(args),
-                             cheb_kind=args.cheb_kind, precision=prec)
+                             cheb_kind=args.cheb_kind, cheb_range=args.cheb_range,
+                             precision=prec)
     ncx = d["p"] * d["nx"]
     h = np.full(ncx * ncx, d["h0"])
     mesh = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
@@ -273,9 +276,12 @@ def main_gb300(args):
     if not args.no_mixed:
         mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
                                   precond=pre, cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
-                                  coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind)
+                                  coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
+                                  cheb_range=args.cheb_range)
         mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
                        opts=mopts)
+        if args.shape >= 0:
+            mm.set_shapes(args.shape, args.shape)
         em = torch.tensor(eta0, dtype=torch.float64, device=dev)
         pm = torch.tensor(phi0, dtype=torch.float64, device=dev)
         tm = 0.0
@@ -416,6 +422,7 @@ def main_gb300(args):
             "config": {"workload": WORKLOAD, "dof": mesh.N, "surface_dof": mesh.ns, "precision": "fp64",
                        "precond": args.precond, "cheb_degree": cdeg, "coarse_degree": args.coarse_degree,
                        "coarse_solver": args.coarse_solver, "cheb_kind": args.cheb_kind,
+                       "cheb_range": args.cheb_range,
                        "cta_shape": "autotuned" if args.shape < 0 else args.shape,
                        "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
@@ -504,7 +511,8 @@ def main_ensemble(args):
     tanks = W.ensemble_tanks(n=args.tanks, seed=5)
     opts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=1e-5,
                              cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
-                             coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind, max_iter=50000)
+                             coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
+                             cheb_range=args.cheb_range, max_iter=50000)
     meshes, etas, phiss, dts = [], [], [], []
     for d in tanks:
         ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"]

@@ -63,7 +63,7 @@ enum { FNPF_JACOBI = 0, FNPF_PMG = 1 };
  * launch per Chebyshev step).  Both apply the same polynomial. */
 enum { FNPF_COARSE_LAUNCHES = 0, FNPF_COARSE_CLUSTER = 1 };
 /* Chebyshev smoothers of FNPF_PMG: FNPF_CHEB_FIRST = first-kind Chebyshev
- * acceleration of Jacobi on [lmax/20, lmax] (Saad, Iterative Methods, Alg.
+ * acceleration of Jacobi on [lmax/cheb_range, lmax] (Saad, Iterative Methods, Alg.
  * 12.1); FNPF_CHEB_FOURTH = fourth-kind Chebyshev smoother on [0, lmax]
  * (Lottes, Numer. Linear Algebra Appl. 2023).  lmax of D^-1 A is estimated per
  * level on the device. */
@@ -103,6 +103,7 @@ typedef struct {
                               every application; 0 = rebuild it per application */
   int coarse_solver;       /* FNPF_COARSE_CLUSTER or FNPF_COARSE_LAUNCHES (FNPF_PMG) */
   int cheb_kind;           /* FNPF_CHEB_FIRST or FNPF_CHEB_FOURTH (FNPF_PMG)        */
+  double cheb_range;       /* FNPF_CHEB_FIRST smooths [lmax / cheb_range, lmax] (> 1) */
 } fnpf_opts;
 
 typedef struct {
@@ -122,7 +123,7 @@ fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t*
 /* Fills *opts with the defaults: FP64, Jacobi, rtol 1e-10, atol 0,
  * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 6,
  * inner_rtol 1e-5, max_outer 20, use_graphs 1, store_metric 1,
- * coarse_solver FNPF_COARSE_CLUSTER, cheb_kind FNPF_CHEB_FIRST. */
+ * coarse_solver FNPF_COARSE_CLUSTER, cheb_kind FNPF_CHEB_FIRST, cheb_range 160. */
 void fnpf_default_opts(fnpf_opts* opts);
 
 /* Creates a mesh on the current CUDA device: GLL tables, horizontal metric,

@@ -21,8 +21,12 @@ static cudaError_t dispatch(const Geom& g, const Tables<T>& t, const AxPtrs<T>& 
 
 template <typename T>
 cudaError_t launch_apply(const Geom& g, const Tables<T>& t, const T* eta, const T* xI, const T* xs, T* yI, T* ys,
-                         T* ring, int variant, cudaStream_t s, const int* skip) {
+                         T* ring, int variant, cudaStream_t s, const int* skip, const Epilogue<T>* ep) {
   AxPtrs<T> a{eta, xI, xs, yI, ys, ring, skip, nullptr};
+  if (ep) {
+    if (ys) return cudaErrorInvalidValue;
+    a.ep = *ep;
+  }
   return dispatch<T>(g, t, a, AX_APPLY, variant, s);
 }
 
@@ -44,23 +48,30 @@ cudaError_t launch_geom(const Geom& g, const Tables<T>& t, const T* eta, T* G, c
 
 template <typename T>
 cudaError_t launch_apply_g(const Geom& g, const Tables<T>& t, const T* G, const T* xI, const T* xs, T* yI, T* ys,
-                           T* ring, int variant, cudaStream_t s, const int* skip) {
+                           T* ring, int variant, cudaStream_t s, const int* skip, const Epilogue<T>* ep) {
   AxPtrs<T> a{nullptr, xI, xs, yI, ys, ring, skip, const_cast<T*>(G)};
+  if (ep) {
+    if (ys) return cudaErrorInvalidValue;
+    a.ep = *ep;
+  }
   return dispatch<T>(g, t, a, AX_APPLY_G, variant, s);
 }
 
 template cudaError_t launch_geom<double>(const Geom&, const Tables<double>&, const double*, double*, cudaStream_t);
 template cudaError_t launch_geom<float>(const Geom&, const Tables<float>&, const float*, float*, cudaStream_t);
 template cudaError_t launch_apply_g<double>(const Geom&, const Tables<double>&, const double*, const double*,
-                                            const double*, double*, double*, double*, int, cudaStream_t, const int*);
+                                            const double*, double*, double*, double*, int, cudaStream_t, const int*,
+                                            const Epilogue<double>*);
 template cudaError_t launch_apply_g<float>(const Geom&, const Tables<float>&, const float*, const float*,
-                                           const float*, float*, float*, float*, int, cudaStream_t, const int*);
+                                           const float*, float*, float*, float*, int, cudaStream_t, const int*,
+                                           const Epilogue<float>*);
 
 template cudaError_t launch_apply<double>(const Geom&, const Tables<double>&, const double*, const double*,
                                           const double*, double*, double*, double*, int, cudaStream_t,
-                                          const int*);
+                                          const int*, const Epilogue<double>*);
 template cudaError_t launch_apply<float>(const Geom&, const Tables<float>&, const float*, const float*, const float*,
-                                         float*, float*, float*, int, cudaStream_t, const int*);
+                                         float*, float*, float*, int, cudaStream_t, const int*,
+                                         const Epilogue<float>*);
 template cudaError_t launch_diag<double>(const Geom&, const Tables<double>&, const double*, double*, double*,
                                          double*, cudaStream_t);
 template cudaError_t launch_diag<float>(const Geom&, const Tables<float>&, const float*, float*, float*, float*,

@@ -501,6 +501,39 @@ __global__ void ring_gather_kernel(Geom g, const T* __restrict__ ring, T* yI, T*
   else yI[(int64_t)plane * g.ns + col] = s;
 }
 
+// Gather fused with a vector update: one thread per interior unknown; the
+// operator output w_i is read from yI on column-interior lines (written there
+// by the operator kernel) or summed from the ring buffer on element-boundary
+// lines (same owners and order as ring_gather_kernel), then the Epilogue
+// update is applied; yI itself is left as the operator kernel wrote it.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) gather_update_kernel(Geom g, const T* __restrict__ ring,
+                                                            const T* __restrict__ yI, const int* skip,
+                                                            Epilogue<T> ep) {
+  if (skip && *skip) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.NI) return;
+  const int plane = (int)(i / g.ns);
+  const int col = (int)(i - (int64_t)plane * g.ns);
+  const int ix = col % g.ncx, iy = col / g.ncx;
+  const int p = g.p;
+  T w;
+  if (ix % p != 0 && (DIM == 2 || iy % p != 0)) {
+    w = yI[i];
+  } else {
+    int exo[2], io[2], eyo[2] = {0, 0}, jo[2] = {0, 0};
+    const int cx = line_owners(ix, p, g.nx, g.px, exo, io);
+    const int cy = DIM == 3 ? line_owners(iy, p, g.ny, g.py, eyo, jo) : 1;
+    w = T(0);
+    for (int u = 0; u < cx; ++u)
+      for (int v = 0; v < cy; ++v) {
+        const int ecol = eyo[v] * g.nx + exo[u];
+        w += ring[((int64_t)plane * g.n_ecol + ecol) * g.ring + ring_slot(DIM, p, io[u], jo[v])];
+      }
+  }
+  apply_epilogue(ep, i, w);
+}
+
 inline int64_t ring_columns(const Geom& g) {
   const int nlx = g.nx + (g.px ? 0 : 1);
   if (g.dim == 2) return nlx;
@@ -517,6 +550,15 @@ cudaError_t launch_gather(const Geom& g, const T* ring, T* yI, T* ys, const int*
   const int threads = 256;
   const int64_t blocks = (total + threads - 1) / threads;
   ring_gather_kernel<T, DIM><<<(unsigned)blocks, threads, 0, s>>>(g, ring, yI, ys, nplanes, nrc, skip);
+  return cudaGetLastError();
+}
+
+template <typename T, int DIM>
+cudaError_t launch_gather_update(const Geom& g, const T* ring, const T* yI, const int* skip, const Epilogue<T>& ep,
+                                 cudaStream_t s) {
+  if (g.NI == 0) return cudaSuccess;
+  const int64_t blocks = (g.NI + 255) / 256;
+  gather_update_kernel<T, DIM><<<(unsigned)blocks, 256, 0, s>>>(g, ring, yI, skip, ep);
   return cudaGetLastError();
 }
 
@@ -555,6 +597,7 @@ cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (a.ep.op != EP_NONE) return launch_gather_update<T, DIM>(g, a.ring, a.yI, a.skip, a.ep, s);
   return launch_gather<T, DIM>(g, a.ring, a.yI, a.ys, a.skip, s);
 }
 

@@ -114,6 +114,46 @@ bool build_hmetric(const Geom& g, const double* xi, const double* w, const doubl
                    const double* Xs, const double* Ys, std::vector<double>* hm, std::vector<double>* mass,
                    std::vector<double>* xs, std::vector<double>* ys);
 
+// Vector update fused into the gather stage of an operator application: the
+// gather kernel visits every interior unknown i once the element kernel has
+// finished, forms w_i = (A x)_i and applies
+//   EP_RES:       r_i = (b ? b_i : r_i) - w_i
+//   EP_RES_START: r_i = b_i - w_i;  d_i = c2 dinv_i r_i;  x_i += d_i    (x updated in place)
+//   EP_CHEB:      r_i -= w_i;  d_i = c1 d_i + c2 dinv_i r_i;  x_i += d_i (d = x updated in place)
+// instead of a separate vector kernel.  The operator's input may be updated in
+// place because the element kernel has read all of it before the gather runs.
+enum { EP_NONE = 0, EP_RES = 1, EP_RES_START = 2, EP_CHEB = 3 };
+template <typename T>
+struct Epilogue {
+  int op = EP_NONE;
+  T* r = nullptr;
+  const T* b = nullptr;
+  const T* dinv = nullptr;
+  T* d = nullptr;
+  T* x = nullptr;
+  const double* c1 = nullptr;   // device scalars (Chebyshev step coefficients)
+  const double* c2 = nullptr;
+};
+
+template <typename T>
+__device__ __forceinline__ void apply_epilogue(const Epilogue<T>& e, int64_t i, T w) {
+  if (e.op == EP_RES) {
+    e.r[i] = (e.b ? e.b[i] : e.r[i]) - w;
+  } else if (e.op == EP_RES_START) {
+    const T rn = e.b[i] - w;
+    e.r[i] = rn;
+    const T dd = (T)(*e.c2) * e.dinv[i] * rn;
+    e.d[i] = dd;
+    e.x[i] += dd;
+  } else {
+    const T rn = e.r[i] - w;
+    e.r[i] = rn;
+    const T dd = (T)(*e.c1) * e.d[i] + (T)(*e.c2) * e.dinv[i] * rn;
+    e.d[i] = dd;
+    e.x[i] += dd;
+  }
+}
+
 // Pointers of one operator application.
 template <typename T>
 struct AxPtrs {
@@ -125,6 +165,7 @@ struct AxPtrs {
   T* ring;
   const int* skip;   // if non-null and *skip != 0 the launch does nothing (converged solve)
   T* G = nullptr;    // stored metric (AX_GEOM output, AX_APPLY_G input)
+  Epilogue<T> ep{};  // update fused into the gather (AX_APPLY, AX_APPLY_G); yI is scratch then
 };
 
 enum { AX_APPLY = 0, AX_DIAG = 1, AX_GEOM = 2, AX_APPLY_G = 3 };
@@ -137,9 +178,12 @@ cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, i
 // Operator launches (ax_dispatch.cu).  xI == nullptr means zero interior;
 // xs == nullptr means zero surface plane; ys == nullptr: surface rows not
 // written.  `ring` is scratch of size nv * n_ecol * g.ring.
+// A non-null `ep` fuses that update into the gather (ys must be null; yI is
+// then scratch for the element kernel's column-interior lines).
 template <typename T>
 cudaError_t launch_apply(const Geom& g, const Tables<T>& t, const T* eta, const T* xI, const T* xs, T* yI,
-                         T* ys, T* ring, int variant, cudaStream_t s, const int* skip = nullptr);
+                         T* ys, T* ring, int variant, cudaStream_t s, const int* skip = nullptr,
+                         const Epilogue<T>* ep = nullptr);
 template <typename T>
 cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, T* ds, T* ring, cudaStream_t s);
 constexpr int kCtaVariants = 4;      // elements-per-CTA shapes of the 3D operator kernels
@@ -151,7 +195,8 @@ template <typename T>
 cudaError_t launch_geom(const Geom& g, const Tables<T>& t, const T* eta, T* G, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply_g(const Geom& g, const Tables<T>& t, const T* G, const T* xI, const T* xs, T* yI, T* ys,
-                           T* ring, int variant, cudaStream_t s, const int* skip = nullptr);
+                           T* ring, int variant, cudaStream_t s, const int* skip = nullptr,
+                           const Epilogue<T>* ep = nullptr);
 
 // Surface kernels (surface.cu).
 struct StageArgs {

@@ -274,6 +274,7 @@ void fnpf_default_opts(fnpf_opts* o) {
   o->store_metric = 1;
   o->coarse_solver = FNPF_COARSE_CLUSTER;
   o->cheb_kind = FNPF_CHEB_FIRST;
+  o->cheb_range = 160.0;
 }
 
 fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, fnpf_mesh** out) {
@@ -416,7 +417,7 @@ fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   m->step_exec = nullptr;
   m->cheb_valid[0] = m->cheb_valid[1] = false;
   fnpf::mg_set_coarse(m->mg, o->coarse_solver);
-  fnpf::mg_set_kind(m->mg, o->cheb_kind);
+  fnpf::mg_set_kind(m->mg, o->cheb_kind, o->cheb_range);
   return FNPF_OK;
 }
 

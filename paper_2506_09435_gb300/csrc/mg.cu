@@ -39,7 +39,6 @@ namespace {
 constexpr int kMaxLevels = 5;
 constexpr int kLanczos = 10;
 constexpr double kSafety = 1.1;
-constexpr double kSmoothRange = 20.0;
 
 // Cluster solve of the coarsest level: one cluster of kCoarseCluster CTAs
 // (the portable maximum), kCoarseRows unknowns per thread at most.
@@ -204,7 +203,10 @@ __global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, int kmax,
   }
 }
 
-// Step 0 of a Chebyshev sweep: (r = b if b given); d = dinv r / theta; x = d or x += d.
+// Step 0 of a Chebyshev sweep from x = 0 or a given x: (r = b if b given);
+// d = dinv r / theta; x = d or x += d.  Steps k >= 1 (r -= A d;
+// d = c1[k] d + c2[k] dinv r; x += d) and residuals are fused into the
+// gather stage of the operator launches (Epilogue).
 template <typename T>
 __global__ void __launch_bounds__(vec::NT) cheb_start_kernel(int64_t n, const T* b, T* r, const T* dinv, T* d, T* x,
                                                              const ChebParams* cp, int x_zero, const int* skip) {
@@ -222,28 +224,6 @@ __global__ void __launch_bounds__(vec::NT) cheb_start_kernel(int64_t n, const T*
     d[i] = dd;
     x[i] = x_zero ? dd : x[i] + dd;
   }
-}
-
-// Step k >= 1: r -= w (w = A d_{k-1}); d = rho_k rho_{k-1} d + (2 rho_k / delta) dinv r; x += d.
-template <typename T>
-__global__ void __launch_bounds__(vec::NT) cheb_step_kernel(int64_t n, const T* w, T* r, const T* dinv, T* d, T* x,
-                                                            const ChebParams* cp, int k, const int* skip) {
-  if (skip && *skip) return;
-  const T c1 = (T)cp->c1[k], c2 = (T)cp->c2[k];
-  FNPF_GRID_LOOP(i, n) {
-    const T rn = r[i] - w[i];
-    r[i] = rn;
-    const T dd = c1 * d[i] + c2 * dinv[i] * rn;
-    d[i] = dd;
-    x[i] += dd;
-  }
-}
-
-// r = b - w, or r -= w when b is null.
-template <typename T>
-__global__ void __launch_bounds__(vec::NT) residual_kernel(int64_t n, const T* b, const T* w, T* r, const int* skip) {
-  if (skip && *skip) return;
-  FNPF_GRID_LOOP(i, n) r[i] = (b ? b[i] : r[i]) - w[i];
 }
 
 // ---------------------------------------------------------------------------- coarsest level on one cluster
@@ -378,8 +358,9 @@ __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// The coarsest level's Chebyshev sweep from x = 0 (the same recurrence as
-// cheb_start_kernel / cheb_step_kernel) in one launch of one cluster.  Each
+// The coarsest level's Chebyshev sweep from x = 0 (the recurrence of
+// cheb_sweep: cheb_start_kernel, then EP_CHEB gather-updates) in one
+// launch of one cluster.  Each
 // thread keeps its rows' r, x and direction in registers; directions are
 // exchanged through the double buffer dbuf [2][NI] in global memory, one
 // cluster barrier per step.  Uniform control flow: every thread reaches every
@@ -539,6 +520,7 @@ struct Mg {
   bool fusable = false;           // the coarsest level fits the cluster kernel
   int coarse_mode = FNPF_COARSE_CLUSTER;
   int cheb_kind = FNPF_CHEB_FIRST;
+  double cheb_range = 160.0;
   std::vector<void*> allocs;
 
   bool fused() const { return fusable && coarse_mode == FNPF_COARSE_CLUSTER; }
@@ -567,8 +549,10 @@ int mg_levels(const Mg* mg) { return mg ? mg->L : 0; }
 void mg_set_coarse(Mg* mg, int mode) {
   if (mg) mg->coarse_mode = mode;
 }
-void mg_set_kind(Mg* mg, int kind) {
-  if (mg) mg->cheb_kind = kind;
+void mg_set_kind(Mg* mg, int kind, double range) {
+  if (!mg) return;
+  mg->cheb_kind = kind;
+  mg->cheb_range = range;
 }
 bool mg_coarse_fused(const Mg* mg) { return mg && mg->fused(); }
 
@@ -718,9 +702,9 @@ const T* level_eta(Mg* mg, int l, const T* eta0) {
 // Operator of level l (level 0 reads the stored metric when given).
 template <typename T>
 cudaError_t level_apply(const Geom& g, const Tables<T>& t, const T* eta, const T* G, const T* x, T* y, T* ring,
-                        int variant, const int* skip, cudaStream_t s) {
-  if (G) return launch_apply_g<T>(g, t, G, x, nullptr, y, nullptr, ring, variant, s, skip);
-  return launch_apply<T>(g, t, eta, x, nullptr, y, nullptr, ring, variant, s, skip);
+                        int variant, const int* skip, cudaStream_t s, const Epilogue<T>* ep = nullptr) {
+  if (G) return launch_apply_g<T>(g, t, G, x, nullptr, y, nullptr, ring, variant, s, skip, ep);
+  return launch_apply<T>(g, t, eta, x, nullptr, y, nullptr, ring, variant, s, skip, ep);
 }
 
 // One Chebyshev sweep of `degree` steps on level l solving A x = b.
@@ -740,24 +724,38 @@ cudaError_t cheb_sweep(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const 
   variant = l == 0 ? variant : 1;   // the autotuned shape is for the finest order
   const int nb = vec::blocks_for(g.NI);
   cudaError_t e;
+  // the residual and Chebyshev updates ride on the operator's gather stage
+  // (Epilogue), so each step is one element kernel plus one gather-update
+  Epilogue<T> ep;
+  ep.r = L.R;
+  ep.dinv = L.dinv;
+  ep.d = L.Dd;
+  ep.x = x;
   if (x_zero) {
     cheb_start_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, b, L.R, L.dinv, L.Dd, x, cp, 1, skip);
     *nl += 1;
   } else {
-    if ((e = level_apply<T>(g, t, eta, G, x, L.W, ring, variant, skip, s)) != cudaSuccess) return e;
-    residual_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, b, L.W, L.R, skip);
-    cheb_start_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, nullptr, L.R, L.dinv, L.Dd, x, cp, 0, skip);
-    *nl += 4;
+    // r = b - A x; d = dinv r / theta; x += d (x is the operator input)
+    ep.op = EP_RES_START;
+    ep.b = b;
+    ep.c2 = &cp->inv_theta;
+    if ((e = level_apply<T>(g, t, eta, G, x, L.W, ring, variant, skip, s, &ep)) != cudaSuccess) return e;
+    *nl += 2;
   }
   for (int k = 1; k < degree; ++k) {
-    if ((e = level_apply<T>(g, t, eta, G, L.Dd, L.W, ring, variant, skip, s)) != cudaSuccess) return e;
-    cheb_step_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.W, L.R, L.dinv, L.Dd, x, cp, k, skip);
-    *nl += 3;
+    // r -= A d; d = c1 d + c2 dinv r; x += d (d is the operator input)
+    ep.op = EP_CHEB;
+    ep.b = nullptr;
+    ep.c1 = &cp->c1[k];
+    ep.c2 = &cp->c2[k];
+    if ((e = level_apply<T>(g, t, eta, G, L.Dd, L.W, ring, variant, skip, s, &ep)) != cudaSuccess) return e;
+    *nl += 2;
   }
   if (final_residual) {
-    if ((e = level_apply<T>(g, t, eta, G, L.Dd, L.W, ring, variant, skip, s)) != cudaSuccess) return e;
-    residual_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, nullptr, L.W, L.R, skip);
-    *nl += 3;
+    ep.op = EP_RES;
+    ep.b = nullptr;
+    if ((e = level_apply<T>(g, t, eta, G, L.Dd, L.W, ring, variant, skip, s, &ep)) != cudaSuccess) return e;
+    *nl += 2;
   }
   return cudaGetLastError();
 }
@@ -832,7 +830,8 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
                                                    hist);
       vec::pupdate_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.Dd, L.P, mg->part, nb, hist);
     }
-    const double range = l == mg->L - 1 ? fmax(kSmoothRange, 0.25 * coarse_degree * coarse_degree) : kSmoothRange;
+    const double range =
+        l == mg->L - 1 ? fmax(mg->cheb_range, 0.25 * coarse_degree * coarse_degree) : mg->cheb_range;
     lz_eig_kernel<<<1, 1, 0, s>>>(sc, hist, kLanczos, kSafety, range, mg->cheb_kind, mg->cheb<T>() + l);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

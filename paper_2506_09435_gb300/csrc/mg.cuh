@@ -56,8 +56,8 @@ int mg_levels(const Mg* mg);
 // as one operator launch per step.
 void mg_set_coarse(Mg* mg, int mode);
 // Polynomial of the Chebyshev smoothers of the next set-ups: FNPF_CHEB_FIRST
-// or FNPF_CHEB_FOURTH.
-void mg_set_kind(Mg* mg, int kind);
+// on [lmax / range, lmax] or FNPF_CHEB_FOURTH on [0, lmax].
+void mg_set_kind(Mg* mg, int kind, double range);
 // True when the coarsest level is solved by the cluster kernel.
 bool mg_coarse_fused(const Mg* mg);
 

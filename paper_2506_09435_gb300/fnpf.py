@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
                 ("atol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int), ("store_metric", ctypes.c_int),
-                ("coarse_solver", ctypes.c_int), ("cheb_kind", ctypes.c_int)]
+                ("coarse_solver", ctypes.c_int), ("cheb_kind", ctypes.c_int), ("cheb_range", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -50,3 +50,4 @@ def test_default_opts(fnpf):
     o = fnpf.default_opts()
     assert o.precision == fnpf.FNPF_FP64 and o.rtol == 1e-10 and o.max_iter > 0 and o.check_every > 0
     assert o.coarse_iters == 6 and o.store_metric == 1 and o.coarse_solver == fnpf.FNPF_COARSE_CLUSTER
+    assert o.cheb_kind == fnpf.FNPF_CHEB_FIRST and o.cheb_range == 160.0

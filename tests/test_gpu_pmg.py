@@ -183,5 +183,5 @@ def test_fourth_kind_one_step_is_scaled_jacobi(fnpf):
         assert np.ptp(q) < 1e-12 * abs(q.mean())
         ratios.append(q.mean())
     rho4 = 4.0 / (3.0 * ratios[0])
-    rho1 = 2.0 / (ratios[1] * (1.0 + 1.0 / 20.0))
+    rho1 = 2.0 / (ratios[1] * (1.0 + 1.0 / fnpf.default_opts().cheb_range))
     assert abs(rho4 - rho1) < 1e-10 * rho1 and 1.0 < rho4 < 20.0
