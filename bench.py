@@ -325,6 +325,7 @@ def main_gb300(args):
                  "outer_iters_per_solve_mean": statistics.mean(i["outer_iters"] for inf in minfos for i in inf),
                  "max_rel_res": max(i["rel_res"] for inf in minfos for i in inf),
                  "fp32_apply_ms": mprof["apply32_ms"] / max(1, mprof["apply32_count"]),
+                 "element_columns_per_cta_fp32": mm.get_shapes()[3],
                  "gpu_launches": mlaunch}
         assert all(i["status"] == 0 for inf in minfos for i in inf)
         del mm
@@ -423,7 +424,8 @@ def main_gb300(args):
                        "precond": args.precond, "cheb_degree": cdeg, "coarse_degree": args.coarse_degree,
                        "coarse_solver": args.coarse_solver, "cheb_kind": args.cheb_kind,
                        "cheb_range": args.cheb_range,
-                       "cta_shape": "autotuned" if args.shape < 0 else args.shape,
+                       "cta_shape": ("autotuned" if args.shape < 0 else "forced"),
+                       "element_columns_per_cta": mesh.get_shapes()[2],
                        "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "cg_iters_per_solve_mean": statistics.mean(iters), "max_rel_res": rel_res,

@@ -228,6 +228,10 @@ fnpf_status fnpf_autotune(fnpf_mesh* mesh, const double* eta, int* variant64, in
  * Errors: EINVAL (index out of range). */
 fnpf_status fnpf_set_shapes(fnpf_mesh* mesh, int variant64, int variant32);
 
+/* The current shape indices and the element columns per CTA they stand for
+ * (any pointer may be NULL).  Host-only.  Errors: EINVAL (mesh NULL). */
+fnpf_status fnpf_get_shapes(const fnpf_mesh* mesh, int* variant64, int* variant32, int* columns64, int* columns32);
+
 /* Instrumentation (tracing): when enabled, every operator application issued
  * by a solve is bracketed by CUDA events on the solve's stream, and the
  * elapsed device time and count are accumulated.  The launch counter counts

@@ -303,6 +303,15 @@ fnpf_status fnpf_set_shapes(fnpf_mesh* m, int variant64, int variant32) {
   return FNPF_OK;
 }
 
+fnpf_status fnpf_get_shapes(const fnpf_mesh* m, int* variant64, int* variant32, int* columns64, int* columns32) {
+  if (!m) return FNPF_EINVAL;
+  if (variant64) *variant64 = m->variant64;
+  if (variant32) *variant32 = m->variant32;
+  if (columns64) *columns64 = fnpf::cta_columns(m->g.n, m->g.dim, m->variant64);
+  if (columns32) *columns32 = fnpf::cta_columns(m->g.n, m->g.dim, m->variant32);
+  return FNPF_OK;
+}
+
 fnpf_status fnpf_profile_enable(fnpf_mesh* m, int on) {
   if (!m) return FNPF_EINVAL;
   if (on && m->prof_ev.empty()) {

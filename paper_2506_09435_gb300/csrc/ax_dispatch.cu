@@ -1,5 +1,5 @@
 // Order dispatch of the operator kernels (instantiated per order in ax_n<N>.cu).
-#include "fnpf_internal.cuh"
+#include "ax_impl.cuh"
 
 namespace fnpf {
 
@@ -37,6 +37,22 @@ cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, 
 }
 
 int apply_variants(int n, int dim) { return dim == 2 ? 1 : kCtaVariants; }
+
+int cta_columns(int n, int dim, int variant) {
+  if (dim == 2) return (128 + n - 1) / n;
+  if (variant < 0 || variant >= kCtaVariants) return 0;
+  switch (n) {
+    case 2: return CtaChoices<2>::c[variant];
+    case 3: return CtaChoices<3>::c[variant];
+    case 4: return CtaChoices<4>::c[variant];
+    case 5: return CtaChoices<5>::c[variant];
+    case 6: return CtaChoices<6>::c[variant];
+    case 7: return CtaChoices<7>::c[variant];
+    case 8: return CtaChoices<8>::c[variant];
+    case 9: return CtaChoices<9>::c[variant];
+    default: return 0;
+  }
+}
 
 int64_t geom_points(const Geom& g) { return (int64_t)g.nz * g.n_ecol * g.n * g.lines; }
 

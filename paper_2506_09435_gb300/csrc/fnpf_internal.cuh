@@ -188,6 +188,7 @@ template <typename T>
 cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, T* ds, T* ring, cudaStream_t s);
 constexpr int kCtaVariants = 4;      // elements-per-CTA shapes of the 3D operator kernels
 int apply_variants(int n, int dim);   // number of elements-per-CTA variants for order n-1
+int cta_columns(int n, int dim, int variant);   // element columns per CTA of a variant
 // Stored metric: G (6 entries per point in 3D, 3 in 2D; geom_points(g) points)
 // computed from eta once, and the operator reading it.
 int64_t geom_points(const Geom& g);

@@ -17,10 +17,11 @@
 // the V-cycle is a fixed symmetric operator and plain PCG applies.
 // lmax per level comes from a 10-step Jacobi-CG Lanczos run on a fixed
 // pseudo-random right-hand side; the largest eigenvalue of the Lanczos
-// tridiagonal matrix is found by bisection on the device and multiplied by a
+// tridiagonal matrix is found by Sturm multisection on the device and multiplied by a
 // safety factor, so the set-up needs no host synchronisation.
 #include <math.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -41,7 +42,8 @@ constexpr int kLanczos = 10;
 constexpr double kSafety = 1.1;
 
 // Cluster solve of the coarsest level: one cluster of kCoarseCluster CTAs
-// (the portable maximum), kCoarseRows unknowns per thread at most.
+// (the portable maximum) of at most kCoarseThreads threads, kCoarseRows
+// unknowns per thread at most.
 constexpr int kCoarseCluster = 8;
 constexpr int kCoarseThreads = 1024;
 constexpr int kCoarseRows = 4;
@@ -131,47 +133,69 @@ __global__ void __launch_bounds__(vec::NT) lz_init_finish_kernel(CgScalars* sc, 
 }
 
 // Largest eigenvalue of the Lanczos tridiagonal matrix from the CG coefficients
-// (T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_j,j+1 = sqrt(b_j)/a_j), by Sturm-count
-// bisection; writes the smoother's step coefficients for kind 1 (first-kind
-// Chebyshev on [lmax / range, lmax]) or kind 4 (fourth-kind Chebyshev on
-// [0, lmax], no lower bound needed).
-__global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, int kmax, double safety, double range,
-                              int kind, ChebParams* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int k = sc->iters < kmax ? sc->iters : kmax;
-  double a[32], b[32];
-  if (k > 32) k = 32;
-  for (int j = 0; j < k; ++j) {
-    const double al = hist[2 * j];
-    a[j] = 1.0 / al + (j > 0 ? hist[2 * (j - 1) + 1] / hist[2 * (j - 1)] : 0.0);
-    b[j] = j + 1 < k ? sqrt(fmax(hist[2 * j + 1], 0.0)) / al : 0.0;
+// (T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_j,j+1 = sqrt(b_j)/a_j), by Sturm counts:
+// one warp evaluates 32 points of the bracketing interval per round
+// (multisection; 16 rounds shrink it by 33^16, as 80 bisection steps would);
+// then lane 0 writes the smoother's step coefficients 1..ncoef-1 for kind 1
+// (first-kind Chebyshev on [lmax / range, lmax]) or kind 4 (fourth-kind
+// Chebyshev on [0, lmax], no lower bound needed).  Launch with one warp.
+__global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, double safety, double range, int kind,
+                              int ncoef, ChebParams* out) {
+  const int lane = threadIdx.x;
+  int k = sc->iters < kLanczos ? sc->iters : kLanczos;
+  double a[kLanczos], b2[kLanczos];   // diagonal and squared off-diagonal
+  double hi = 0.0;
+#pragma unroll
+  for (int j = 0; j < kLanczos; ++j) {
+    a[j] = 0.0;
+    b2[j] = 0.0;
+    if (j < k) {
+      const double al = hist[2 * j];
+      a[j] = 1.0 / al + (j > 0 ? hist[2 * (j - 1) + 1] / hist[2 * (j - 1)] : 0.0);
+      const double bj = j + 1 < k ? sqrt(fmax(hist[2 * j + 1], 0.0)) / al : 0.0;
+      b2[j] = bj * bj;
+    }
   }
+#pragma unroll
+  for (int j = 0; j < kLanczos; ++j)   // Gershgorin bound
+    if (j < k) hi = fmax(hi, a[j] + sqrt(b2[j]) + (j > 0 ? sqrt(b2[j - 1]) : 0.0));
   double lmax;
   if (k == 0) {
     lmax = out->lmax > 0 ? out->lmax : 2.0;
   } else {
-    double hi = 0.0;
-    for (int j = 0; j < k; ++j) {
-      const double r = a[j] + fabs(b[j]) + (j > 0 ? fabs(b[j - 1]) : 0.0);
-      hi = fmax(hi, r);
-    }
     double lo = 0.0;
-    for (int it = 0; it < 80; ++it) {
-      const double x = 0.5 * (lo + hi);
+    for (int round = 0; round < 16; ++round) {
+      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
       int below = 0;
       double d = 1.0;
-      for (int j = 0; j < k; ++j) {
-        d = a[j] - x - (j > 0 ? b[j - 1] * b[j - 1] / d : 0.0);
-        if (d == 0.0) d = -1e-300;
-        if (d < 0) ++below;
+#pragma unroll
+      for (int j = 0; j < kLanczos; ++j) {
+        if (j < k) {
+          d = a[j] - x - (j > 0 ? b2[j - 1] / d : 0.0);
+          if (d == 0.0) d = -1e-300;
+          if (d < 0) ++below;
+        }
       }
-      if (below == k) hi = x;   // every eigenvalue lies below x
-      else lo = x;
+      // first point with every eigenvalue below it brackets lmax from above
+      const unsigned all_below = __ballot_sync(0xffffffffu, below == k);
+      const double xl = __shfl_up_sync(0xffffffffu, x, 1);
+      if (all_below == 0u) {
+        lo = __shfl_sync(0xffffffffu, x, 31);
+      } else {
+        const int jf = __ffs(all_below) - 1;
+        const double nlo = jf == 0 ? lo : __shfl_sync(0xffffffffu, xl, jf);
+        hi = __shfl_sync(0xffffffffu, x, jf);
+        lo = nlo;
+      }
     }
     lmax = hi;
   }
+  if (lane != 0) return;
+  const int nc = ncoef < kMaxChebDegree ? ncoef : kMaxChebDegree;
   out->lmax = safety * lmax;
   out->range = range;
+  out->c1[0] = 0.0;
+  out->c2[0] = 0.0;
   if (kind == FNPF_CHEB_FOURTH) {
     // Fourth-kind Chebyshev smoother (Lottes, "Optimal polynomial smoothers for
     // multigrid V-cycles", Numer. Linear Algebra Appl. 2023): with rho = lmax,
@@ -179,11 +203,9 @@ __global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, int kmax,
     // d_k = (2k - 1) / (2k + 3) d_{k-1} + (8k + 4) / ((2k + 3) rho) D^-1 r_k.
     const double rho = out->lmax;
     out->inv_theta = 4.0 / (3.0 * rho);
-    out->c1[0] = 0.0;
-    out->c2[0] = 0.0;
-    for (int k = 1; k < kMaxChebDegree; ++k) {
-      out->c1[k] = (2.0 * k - 1.0) / (2.0 * k + 3.0);
-      out->c2[k] = (8.0 * k + 4.0) / ((2.0 * k + 3.0) * rho);
+    for (int m = 1; m < nc; ++m) {
+      out->c1[m] = (2.0 * m - 1.0) / (2.0 * m + 3.0);
+      out->c2[m] = (8.0 * m + 4.0) / ((2.0 * m + 3.0) * rho);
     }
     return;
   }
@@ -193,12 +215,10 @@ __global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, int kmax,
   const double theta = 0.5 * (lm + lmin), delta = 0.5 * (lm - lmin), sigma = theta / delta;
   out->inv_theta = 1.0 / theta;
   double rho_old = 1.0 / sigma;
-  out->c1[0] = 0.0;
-  out->c2[0] = 0.0;
-  for (int k = 1; k < kMaxChebDegree; ++k) {
+  for (int m = 1; m < nc; ++m) {
     const double rho = 1.0 / (2.0 * sigma - rho_old);
-    out->c1[k] = rho * rho_old;
-    out->c2[k] = 2.0 * rho / delta;
+    out->c1[m] = rho * rho_old;
+    out->c2[m] = 2.0 * rho / delta;
     rho_old = rho;
   }
 }
@@ -371,8 +391,8 @@ __global__ void __cluster_dims__(kCoarseCluster, 1, 1) __launch_bounds__(kCoarse
                        T* x, T* dbuf, const ChebParams* cp, int degree, const int* skip) {
   if (skip && *skip) return;   // the same value for every CTA of the cluster
   const int64_t n = g.NI;
-  const int nthr = kCoarseCluster * kCoarseThreads;
-  const int tid = blockIdx.x * kCoarseThreads + threadIdx.x;
+  const int nthr = kCoarseCluster * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   T r[kCoarseRows], xv[kCoarseRows], dv[kCoarseRows];
   const T it = (T)cp->inv_theta;
 #pragma unroll
@@ -417,13 +437,19 @@ cudaError_t launch_stencil(const Geom& g, const T* D, const T* G, T* coef, cudaS
   return cudaGetLastError();
 }
 
+// CTAs only as large as the level needs (one row per thread up to
+// kCoarseThreads threads, then up to kCoarseRows rows per thread), so that
+// small coarse levels, e.g. of the tanks of an ensemble running side by side,
+// leave the rest of their SMs to other kernels.
 template <typename T>
 cudaError_t launch_coarse_cheb(const Geom& g, const T* coef, const T* dinv, const T* b, T* x, T* dbuf,
                                const ChebParams* cp, int degree, const int* skip, cudaStream_t s) {
+  const int64_t per_cta = (g.NI + kCoarseCluster - 1) / kCoarseCluster;
+  const int threads = (int)std::min<int64_t>(kCoarseThreads, std::max<int64_t>(32, (per_cta + 31) / 32 * 32));
   if (g.dim == 3)
-    coarse_cheb_kernel<T, 3><<<kCoarseCluster, kCoarseThreads, 0, s>>>(g, coef, dinv, b, x, dbuf, cp, degree, skip);
+    coarse_cheb_kernel<T, 3><<<kCoarseCluster, threads, 0, s>>>(g, coef, dinv, b, x, dbuf, cp, degree, skip);
   else
-    coarse_cheb_kernel<T, 2><<<kCoarseCluster, kCoarseThreads, 0, s>>>(g, coef, dinv, b, x, dbuf, cp, degree, skip);
+    coarse_cheb_kernel<T, 2><<<kCoarseCluster, threads, 0, s>>>(g, coef, dinv, b, x, dbuf, cp, degree, skip);
   return cudaGetLastError();
 }
 
@@ -794,7 +820,6 @@ cudaError_t vcycle(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* G
 template <typename T>
 cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, T* ring, int variant,
                        int cheb_degree, int coarse_degree, bool estimate, cudaStream_t s) {
-  (void)cheb_degree;
   cudaError_t e;
   MgLevelBufs<T>* Lv = mg->bufs<T>();
   for (int l = 1; l < mg->L; ++l) {
@@ -832,7 +857,8 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
     }
     const double range =
         l == mg->L - 1 ? fmax(mg->cheb_range, 0.25 * coarse_degree * coarse_degree) : mg->cheb_range;
-    lz_eig_kernel<<<1, 1, 0, s>>>(sc, hist, kLanczos, kSafety, range, mg->cheb_kind, mg->cheb<T>() + l);
+    const int ncoef = l == mg->L - 1 ? coarse_degree : cheb_degree;
+    lz_eig_kernel<<<1, 32, 0, s>>>(sc, hist, kSafety, range, mg->cheb_kind, ncoef, mg->cheb<T>() + l);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -82,6 +82,7 @@ def load():
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
         "fnpf_set_shapes": [vp, ctypes.c_int, ctypes.c_int],
+        "fnpf_get_shapes": [vp] + [ctypes.POINTER(ctypes.c_int)] * 4,
         "fnpf_profile_enable": [vp, ctypes.c_int],
         "fnpf_profile_read": [vp, ctypes.POINTER(ctypes.c_double), i64p, i64p, ctypes.c_int],
         "fnpf_profile_read_fp32": [vp, ctypes.POINTER(ctypes.c_double), i64p],
@@ -274,6 +275,12 @@ class Mesh:
 
     def set_shapes(self, variant64, variant32):
         self._check(_LIB.fnpf_set_shapes(self._h, int(variant64), int(variant32)))
+
+    def get_shapes(self):
+        """(variant64, variant32, columns per CTA fp64, columns per CTA fp32)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(_LIB.fnpf_get_shapes(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def autotune(self, eta, stream=None):
         v64, v32 = ctypes.c_int(), ctypes.c_int()

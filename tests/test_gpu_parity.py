@@ -154,6 +154,8 @@ def test_every_cta_shape_matches_oracle(fnpf, shape, variant):
     p-multigrid solve."""
     c = Case(fnpf, *shape, opts=fnpf.default_opts(rtol=1e-13, precond=fnpf.FNPF_PMG, max_iter=5000))
     c.gm.set_shapes(variant, variant)
+    v64, v32, c64, c32 = c.gm.get_shapes()
+    assert (v64, v32) == (variant, variant) and c64 == c32 and c64 >= 1
     op = oop.Operator(c.om, c.eta, c.h)
     x = c.rng.standard_normal(c.om.N)
     y_ref = op.A @ x
