@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--coarse-degree", type=int, default=6)
     ap.add_argument("--shape", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="elements-per-CTA shape of the operator kernels (-1: autotuned)")
+    ap.add_argument("--model", default="fnpf", choices=["fnpf", "lpf"],
+                    help="fnpf: fully nonlinear (the configuration's method); lpf: linear potential flow")
     ap.add_argument("--cheb-kind", type=int, default=1, choices=[1, 4],
                     help="Chebyshev smoother: 1 = first kind on [lmax/20, lmax], 4 = fourth kind on [0, lmax]")
     ap.add_argument("--cheb-range", type=float, default=160.0,
@@ -218,6 +220,7 @@ def main_gb300(args):
     opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000, precond=pre, cheb_degree=cdeg,
                              coarse_iters=args.coarse_degree, coarse_solver=coarse_mode(args),
                              cheb_kind=args.cheb_kind, cheb_range=args.cheb_range,
+                             model=model_id(args),
                              precision=prec)
     ncx = d["p"] * d["nx"]
     h = np.full(ncx * ncx, d["h0"])
@@ -277,7 +280,7 @@ def main_gb300(args):
         mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
                                   precond=pre, cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
                                   coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
-                                  cheb_range=args.cheb_range)
+                                  cheb_range=args.cheb_range, model=model_id(args))
         mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
                        opts=mopts)
         if args.shape >= 0:
@@ -359,7 +362,7 @@ def main_gb300(args):
 
     # --- adjoint step (reverse mode, FP64, same mesh and state) against the forward step
     adjoint = None
-    if not args.no_adjoint:
+    if not args.no_adjoint and args.model == "fnpf":   # the adjoint is built for the nonlinear model
         le = torch.ones(mesh.ns, dtype=torch.float64, device=dev) / mesh.ns
         lp = torch.zeros_like(le)
         oe, op_ = torch.empty_like(le), torch.empty_like(le)
@@ -423,7 +426,7 @@ def main_gb300(args):
             "config": {"workload": WORKLOAD, "dof": mesh.N, "surface_dof": mesh.ns, "precision": "fp64",
                        "precond": args.precond, "cheb_degree": cdeg, "coarse_degree": args.coarse_degree,
                        "coarse_solver": args.coarse_solver, "cheb_kind": args.cheb_kind,
-                       "cheb_range": args.cheb_range,
+                       "cheb_range": args.cheb_range, "model": args.model,
                        "cta_shape": ("autotuned" if args.shape < 0 else "forced"),
                        "element_columns_per_cta": mesh.get_shapes()[2],
                        "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
@@ -570,6 +573,11 @@ def main_ensemble(args):
         "orders": sorted(set(d["p"] for d in tanks)), "finite": ok, "gpu_launches": launches,
         "clocks": clk.summary(), "data": "synthetic"}))
     return 0
+
+
+def model_id(args):
+    from paper_2506_09435_gb300 import fnpf
+    return fnpf.FNPF_LINEAR if args.model == "lpf" else fnpf.FNPF_NONLINEAR
 
 
 def coarse_mode(args):

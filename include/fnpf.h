@@ -68,6 +68,13 @@ enum { FNPF_COARSE_LAUNCHES = 0, FNPF_COARSE_CLUSTER = 1 };
  * (Lottes, Numer. Linear Algebra Appl. 2023).  lmax of D^-1 A is estimated per
  * level on the device. */
 enum { FNPF_CHEB_FIRST = 1, FNPF_CHEB_FOURTH = 4 };
+/* Free-surface model.  FNPF_NONLINEAR: fully nonlinear potential flow, the
+ * mesh follows eta (Sec. 3.1.2) and the Zakharov conditions give the
+ * right-hand side (Sec. 2).  FNPF_LINEAR: linear potential flow (the paper's
+ * LPF, Sec. 1 and 2): the Laplace problem is solved on the still-water domain
+ * (the geometry takes eta = 0 wherever it would take eta) and the surface
+ * conditions are d eta/dt = w, d phi/dt = -g eta. */
+enum { FNPF_NONLINEAR = 0, FNPF_LINEAR = 1 };
 
 /* Mesh descriptor.  All arrays are HOST pointers, copied at creation. */
 typedef struct {
@@ -104,6 +111,7 @@ typedef struct {
   int coarse_solver;       /* FNPF_COARSE_CLUSTER or FNPF_COARSE_LAUNCHES (FNPF_PMG) */
   int cheb_kind;           /* FNPF_CHEB_FIRST or FNPF_CHEB_FOURTH (FNPF_PMG)        */
   double cheb_range;       /* FNPF_CHEB_FIRST smooths [lmax / cheb_range, lmax] (> 1) */
+  int model;               /* FNPF_NONLINEAR or FNPF_LINEAR                        */
 } fnpf_opts;
 
 typedef struct {
@@ -123,7 +131,8 @@ fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t*
 /* Fills *opts with the defaults: FP64, Jacobi, rtol 1e-10, atol 0,
  * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 6,
  * inner_rtol 1e-5, max_outer 20, use_graphs 1, store_metric 1,
- * coarse_solver FNPF_COARSE_CLUSTER, cheb_kind FNPF_CHEB_FIRST, cheb_range 160. */
+ * coarse_solver FNPF_COARSE_CLUSTER, cheb_kind FNPF_CHEB_FIRST, cheb_range 160,
+ * model FNPF_NONLINEAR. */
 void fnpf_default_opts(fnpf_opts* opts);
 
 /* Creates a mesh on the current CUDA device: GLL tables, horizontal metric,

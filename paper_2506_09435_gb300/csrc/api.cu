@@ -70,7 +70,7 @@ fnpf_status fnpf_dtn(fnpf_mesh* m, const double* eta, const double* phis, double
   cudaStream_t s = (cudaStream_t)stream;
   fnpf_status st = solve_into(m, eta, phis, m->phi, info, s);
   if (st != FNPF_OK) return st;
-  cudaError_t e = fnpf::launch_w(m->g, m->tables(), eta, phis, m->phi, w, s);
+  cudaError_t e = fnpf::launch_w(m->g, m->tables(), m->geom_eta(eta), phis, m->phi, w, s);
   m->launches += 1;
   return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "w recovery");
 }
@@ -80,6 +80,8 @@ fnpf_status fnpf_zakharov_rhs(fnpf_mesh* m, const double* eta, const double* phi
   if (!m || !eta || !phis || !w || !deta || !dphis) return FNPF_EINVAL;
   fnpf::StageArgs a{};
   a.eta = eta;
+  a.geo = m->geom_eta(eta);
+  a.linear = m->linear() ? 1 : 0;
   a.phis = phis;
   a.w_in = w;
   a.deta = deta;
@@ -99,6 +101,8 @@ StageArgs stage_args(fnpf_mesh* m, double* eta, double* phis, const double* ce, 
   const double cn[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
   StageArgs a{};
   a.eta = ce;
+  a.geo = m->geom_eta(ce);
+  a.linear = m->linear() ? 1 : 0;
   a.phis = cp;
   a.phi = m->phi;
   a.y0_eta = eta;

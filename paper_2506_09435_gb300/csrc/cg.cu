@@ -477,8 +477,10 @@ fnpf_status ensure_g64(fnpf_mesh* m) {
   return FNPF_OK;
 }
 
-fnpf_status precond_apply(fnpf_mesh* m, const double* eta, const double* r, double* z, cudaStream_t s) {
+fnpf_status precond_apply(fnpf_mesh* m, const double* eta_in, const double* r, double* z, cudaStream_t s) {
   const Geom& g = m->g;
+  const double* eta = m->geom_eta(eta_in);
+  m->lpf_ready[0] = false;   // the set-up below overwrites the kept one
   const Tables<double> t = m->tables();
   const int nb = vec_blocks(g.NI);
   if (m->opts.precond != FNPF_PMG) {
@@ -523,32 +525,38 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   }
   if (info) FNPF_CK(cudaEventRecord(m->ev0, s));
   // the solve reads eta from a mesh-owned copy, so captured graphs keep valid pointers
-  FNPF_CK(cudaMemcpyAsync(m->eta64, eta_in, g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  FNPF_CK(cudaMemcpyAsync(m->eta64, m->geom_eta(eta_in), g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
   const double* eta = m->eta64;
   FNPF_CK(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
   FNPF_CK(launch_check_state(g, eta, rhs ? eta : phis, m->dh, &sc->status, &sc->done, s));
   // FP64 solves: the metric is rebuilt from this eta once and read by every
   // operator application of the solve (fewer FP64 instructions per point)
+  // linear potential flow: the geometry is fixed, so the FP64 set-up of the
+  // first solve is kept (lpf_ready) and later solves skip it
+  const bool keep64 = m->linear() && m->lpf_ready[0];
   m->g64_active = false;
   if (!mixed && m->opts.store_metric) {
     const fnpf_status st = ensure_g64(m);
     if (st != FNPF_OK) return st;
-    FNPF_CK(launch_geom<double>(g, t, eta, m->G64, s));
+    if (!keep64) {
+      FNPF_CK(launch_geom<double>(g, t, eta, m->G64, s));
+      m->launches += 1;
+    }
     m->g64_active = true;
-    m->launches += 1;
   }
   if (!m->tuned) {
     const fnpf_status st = autotune(m, eta, m->g64_active ? m->G64 : nullptr, s);
     if (st != FNPF_OK) return st;
   }
-  if (!mixed && !pmg) {
+  if (!mixed && !pmg && !keep64) {
     FNPF_CK(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
     vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
   }
-  if (!mixed && pmg) {
+  if (!mixed && pmg && !keep64) {
     FNPF_CK(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
                                m->opts.coarse_iters, want_estimate(m, 0), s));
   }
+  if (!mixed && m->linear()) m->lpf_ready[0] = true;
   FNPF_CK(cudaGetLastError());
   // lift: r = A [0; phis]_I = -b (or r = -rhs); q = A [x; 0]_I; then b, r = b - q (, z, p)
   if (rhs) {
@@ -580,13 +588,16 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
 
   // ---- mixed precision: FP64 defect correction around FP32 Jacobi-PCG
   const Tables<float> t32 = m->tables32();
-  to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
-  if (pmg) {
-    FNPF_CK(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
-                              m->opts.cheb_degree, m->opts.coarse_iters, want_estimate(m, 1), s));
-  } else {
-    FNPF_CK(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
-    vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+  if (!(m->linear() && m->lpf_ready[1])) {
+    to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+    if (pmg) {
+      FNPF_CK(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
+                                m->opts.cheb_degree, m->opts.coarse_iters, want_estimate(m, 1), s));
+    } else {
+      FNPF_CK(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
+      vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+    }
+    if (m->linear()) m->lpf_ready[1] = true;
   }
   FNPF_CK(cudaGetLastError());
   m->launches += 4;
@@ -746,21 +757,24 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
       return e;                        \
     }                                  \
   } while (0)
-  ENQ(cudaMemcpyAsync(m->eta64, eta_in, g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  ENQ(cudaMemcpyAsync(m->eta64, m->geom_eta(eta_in), g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
   const double* eta = m->eta64;
   ENQ(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
   ENQ(cudaMemsetAsync(m->inner_total, 0, sizeof(int), s));
   ENQ(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
+  // linear potential flow: a host-driven step has done the set-up (lpf_ready)
+  const bool keep64 = m->linear() && m->lpf_ready[0];
+  const bool keep32 = m->linear() && m->lpf_ready[1];
   m->g64_active = false;
   if (!mixed && m->opts.store_metric && m->G64) {
-    ENQ(launch_geom<double>(g, t, eta, m->G64, s));
+    if (!keep64) ENQ(launch_geom<double>(g, t, eta, m->G64, s));
     m->g64_active = true;
   }
-  if (!mixed && !pmg) {
+  if (!mixed && !pmg && !keep64) {
     ENQ(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
     vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
   }
-  if (!mixed && pmg)
+  if (!mixed && pmg && !keep64)
     ENQ(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
                            m->opts.coarse_iters, estimate, s));
   ENQ(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
@@ -789,13 +803,15 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
     }));
   } else {
     const Tables<float> t32 = m->tables32();
-    to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
-    if (pmg) {
-      ENQ(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
-                            m->opts.cheb_degree, m->opts.coarse_iters, estimate, s));
-    } else {
-      ENQ(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
-      vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+    if (!keep32) {
+      to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+      if (pmg) {
+        ENQ(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
+                              m->opts.cheb_degree, m->opts.coarse_iters, estimate, s));
+      } else {
+        ENQ(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
+        vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+      }
     }
     const int max_outer = std::max(1, m->opts.max_outer);
     const double in_rtol2 = m->opts.inner_rtol * m->opts.inner_rtol;

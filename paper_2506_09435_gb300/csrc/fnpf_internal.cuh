@@ -202,6 +202,8 @@ cudaError_t launch_apply_g(const Geom& g, const Tables<T>& t, const T* G, const 
 // Surface kernels (surface.cu).
 struct StageArgs {
   const double* eta;     // stage state (read, neighbours)
+  const double* geo;     // eta of the geometry (z_t of the w recovery): eta, or zeros (linear)
+  int linear;            // 1: d eta/dt = w, d phi/dt = -g eta (linear potential flow)
   const double* phis;
   const double* phi;     // volume potential of this stage (top planes)
   const double* y0_eta;  // y_n (pointwise)

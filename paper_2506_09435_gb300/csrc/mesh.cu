@@ -205,6 +205,7 @@ void free_mesh(fnpf_mesh* m) {
     if (p) cudaFree(p);
   if (m->b) cudaFree(m->b);
   if (m->eta64) cudaFree(m->eta64);
+  if (m->zero_eta) cudaFree(m->zero_eta);
   if (m->G64) cudaFree(m->G64);
   if (m->adj) cudaFree(m->adj);
   double* rptrs[] = {m->rx_cr, m->rx_gen, m->dxs, m->dys};
@@ -275,6 +276,7 @@ void fnpf_default_opts(fnpf_opts* o) {
   o->coarse_solver = FNPF_COARSE_CLUSTER;
   o->cheb_kind = FNPF_CHEB_FIRST;
   o->cheb_range = 160.0;
+  o->model = FNPF_NONLINEAR;
 }
 
 fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, fnpf_mesh** out) {
@@ -292,6 +294,10 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
       g_create_error = "depth h must be finite and > 0 at every surface node";
       return FNPF_EINVAL;
     }
+  }
+  if (opts && opts->model != FNPF_NONLINEAR && opts->model != FNPF_LINEAR) {
+    g_create_error = "model must be FNPF_NONLINEAR or FNPF_LINEAR";
+    return FNPF_EINVAL;
   }
   fnpf_mesh* m = new fnpf_mesh();
   m->g = g;
@@ -352,6 +358,7 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   A(&m->acc_phi, g.ns);
   A(&m->b, g.NI);
   A(&m->eta64, g.ns);
+  A(&m->zero_eta, g.ns);
   auto AF = [&](float** ptr, size_t cnt) {
     if (e == cudaSuccess) e = dalloc(ptr, cnt);
   };
@@ -386,6 +393,7 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   if (e == cudaSuccess) e = cudaMemcpy(m->dh, m->h.data(), g.ns * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->dminv, m->minv.data(), g.ns * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->phi, 0, g.N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(m->zero_eta, 0, g.ns * sizeof(double));
   {
     auto up32 = [&](float* dst, const std::vector<double>& src) {
       std::vector<float> f(src.begin(), src.end());
@@ -411,11 +419,16 @@ void fnpf_destroy_mesh(fnpf_mesh* m) { free_mesh(m); }
 
 fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   if (!m || !o) return FNPF_EINVAL;
+  if (o->model != FNPF_NONLINEAR && o->model != FNPF_LINEAR) {
+    m->err = "model must be FNPF_NONLINEAR or FNPF_LINEAR";
+    return FNPF_EINVAL;
+  }
   m->opts = *o;
   for (GraphSlot& gs : m->g_iter) fnpf::graph_reset(&gs);   // captured arguments depend on the options
   if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
   m->step_exec = nullptr;
   m->cheb_valid[0] = m->cheb_valid[1] = false;
+  m->lpf_ready[0] = m->lpf_ready[1] = false;
   fnpf::mg_set_coarse(m->mg, o->coarse_solver);
   fnpf::mg_set_kind(m->mg, o->cheb_kind, o->cheb_range);
   return FNPF_OK;

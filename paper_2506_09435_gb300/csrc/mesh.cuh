@@ -70,6 +70,7 @@ struct fnpf_mesh {
   float* dinv32 = nullptr;
   double* b = nullptr;              // NI: lifted right-hand side
   double* eta64 = nullptr;          // ns: copy of the solve's eta
+  double* zero_eta = nullptr;       // ns zeros: the geometry of FNPF_LINEAR
   double* G64 = nullptr;            // stored metric of FP64 solves (allocated at the first one)
   bool g64_active = false;          // the current FP64 solve reads G64
   fnpf::CgScalars* sc_in = nullptr; // inner-solve scalars
@@ -89,6 +90,10 @@ struct fnpf_mesh {
   // p-multigrid hierarchy (created at the first FNPF_PMG solve)
   fnpf::Mg* mg = nullptr;
   bool cheb_valid[2] = {false, false};   // Chebyshev intervals estimated (FP64, FP32)
+  // FNPF_LINEAR: the solver set-up for the fixed still-water geometry (stored
+  // metric, diagonals, multigrid levels, Chebyshev intervals) is done (FP64,
+  // FP32) and is reused by later solves
+  bool lpf_ready[2] = {false, false};
   int64_t solve_count[2] = {0, 0};
   bool iso = false;
   double Lx = 0, Ly = 0;
@@ -124,6 +129,9 @@ struct fnpf_mesh {
   int64_t launches = 0;
 
   fnpf::Tables<double> tables() const { return fnpf::Tables<double>{dD, dxi, dw, dhm, dh, dminv}; }
+  bool linear() const { return opts.model == FNPF_LINEAR; }
+  // eta as the mesh geometry sees it: the state's eta, or zero for FNPF_LINEAR
+  const double* geom_eta(const double* eta) const { return linear() ? zero_eta : eta; }
   fnpf::Tables<float> tables32() const { return fnpf::Tables<float>{fD, fxi, fw, fhm, fh, nullptr}; }
 };
 

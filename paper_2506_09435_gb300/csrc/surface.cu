@@ -11,6 +11,8 @@
 // combined with the lumped-mass weights w_i w_j |det H|:
 //     d eta/dt = sum_e W_e f_eta,e / sum_e W_e  (likewise for phi).
 // The 1/2 |grad phi|^2 term carries the sign of the strong (Bernoulli) form.
+// Linear potential flow (model FNPF_LINEAR) takes z_t from the still-water
+// depth and the linear conditions d eta/dt = w, d phi/dt = -g eta.
 #include <math.h>
 
 #include "fnpf_internal.cuh"
@@ -27,22 +29,16 @@ __device__ inline double top_w(const Geom& g, const double* D, const double* phi
   return s * (2.0 * g.nz) / (eta[col] + h[col]);
 }
 
-__global__ void stage_kernel(Geom g, Tables<double> t, StageArgs a) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= g.ns) return;
+// Zakharov right-hand side at surface column col (ix, iy): the conditions in
+// every element sharing the node, combined with the lumped-mass weights.
+__device__ inline void zakharov_node(const Geom& g, const Tables<double>& t, const StageArgs& a, int col, int ix,
+                                     int iy, double w, double e0, double* ke, double* kp) {
   const int P = g.p, n = g.n;
-  const int ix = col % g.ncx, iy = col / g.ncx;
-  const double e0 = a.eta[col];
-  const double hh = t.h[col];
-  if (!(e0 + hh > 0.0) || !isfinite(e0) || !isfinite(a.phis[col])) {
-    if (a.status) atomicExch(a.status, (int)FNPF_EDIVERGED);
-  }
-  const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.eta, col);
   int exo[2], io[2], eyo[2] = {0, 0}, jo[2] = {0, 0};
   const int cx = line_owners(ix, P, g.nx, g.px, exo, io);
   const int cy = g.dim == 3 ? line_owners(iy, P, g.ny, g.py, eyo, jo) : 1;
   const int64_t hstride = (int64_t)g.n_ecol * g.lines;
-  double se = 0, sp = 0, sw = 0;
+  double se = 0, sp = 0;
   for (int u = 0; u < cx; ++u) {
     for (int v = 0; v < cy; ++v) {
       const int ex = exo[u], ey = eyo[v], i = io[u], j = jo[v];
@@ -73,11 +69,30 @@ __global__ void stage_kernel(Geom g, Tables<double> t, StageArgs a) {
       const double fp = -g.g * e0 - 0.5 * (px_ * px_ + py_ * py_) + 0.5 * w * w * ge2;
       se += cw * fe;
       sp += cw * fp;
-      sw += cw;
     }
   }
-  (void)sw;
-  const double ke = se * t.minv[col], kp = sp * t.minv[col];
+  *ke = se * t.minv[col];
+  *kp = sp * t.minv[col];
+}
+
+__global__ void stage_kernel(Geom g, Tables<double> t, StageArgs a) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= g.ns) return;
+  const int ix = col % g.ncx, iy = col / g.ncx;
+  const double e0 = a.eta[col];
+  const double hh = t.h[col];
+  if (!(e0 + hh > 0.0) || !isfinite(e0) || !isfinite(a.phis[col])) {
+    if (a.status) atomicExch(a.status, (int)FNPF_EDIVERGED);
+  }
+  const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.geo ? a.geo : a.eta, col);
+  double ke, kp;
+  if (a.linear) {
+    // linear potential flow: the surface conditions linearised about z = 0
+    ke = w;
+    kp = -g.g * e0;
+  } else {
+    zakharov_node(g, t, a, col, ix, iy, w, e0, &ke, &kp);
+  }
   if (a.deta) {
     a.deta[col] = ke;
     a.dphis[col] = kp;

@@ -20,6 +20,7 @@ FNPF_FP64, FNPF_MIXED = 0, 1
 FNPF_JACOBI, FNPF_PMG = 0, 1
 FNPF_COARSE_LAUNCHES, FNPF_COARSE_CLUSTER = 0, 1
 FNPF_CHEB_FIRST, FNPF_CHEB_FOURTH = 1, 4
+FNPF_NONLINEAR, FNPF_LINEAR = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -36,7 +37,8 @@ class Opts(ctypes.Structure):
                 ("atol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int), ("store_metric", ctypes.c_int),
-                ("coarse_solver", ctypes.c_int), ("cheb_kind", ctypes.c_int), ("cheb_range", ctypes.c_double)]
+                ("coarse_solver", ctypes.c_int), ("cheb_kind", ctypes.c_int), ("cheb_range", ctypes.c_double),
+                ("model", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
