@@ -16,5 +16,6 @@ Modules
   solve    -- Dirichlet-Neumann Laplace solve, vertical velocity recovery
   surface  -- Zakharov right-hand side, ERK4, relaxation, diagnostics
   tlm      -- exact tangent-linear model of one RK4 step (complex step)
+  filter   -- modal filter of free-surface fields
 """
-from . import gll, mesh, operator, solve, surface, tlm  # noqa: F401
+from . import filter, gll, mesh, operator, solve, surface, tlm  # noqa: F401
