@@ -270,6 +270,27 @@ typedef struct {
 } fnpf_relaxation;
 fnpf_status fnpf_set_relaxation(fnpf_mesh* mesh, const fnpf_relaxation* relax);
 
+/* Modal filter of free-surface fields (Sec. 3.2, modal filtering; applied in
+ * Step 4.7).  On every surface element the nodal values are mapped to the
+ * coefficients of the tensor-product orthonormal Legendre basis (Vandermonde
+ * matrix at the GLL nodes), mode (a, b) is scaled by sigma_a sigma_b with
+ *   sigma_k = 1 (k <= cutoff),  exp(-alpha ((k - cutoff) / (p - cutoff))^order) (k > cutoff),
+ * and the result is mapped back; the element-interior nodes take the filtered
+ * values, nodes shared between elements keep theirs.  Once set, every RK4 step
+ * filters eta and phi after the relaxation.  alpha = 0 (or a NULL filter)
+ * turns it off.  Errors: EINVAL (alpha < 0 or not finite, order < 1,
+ * cutoff outside 0..p-1). */
+typedef struct {
+  double alpha;            /* damping of the highest mode: sigma_p = exp(-alpha) */
+  int order;               /* s >= 1 */
+  int cutoff;              /* N_c in 0..p-1: modes up to N_c are kept */
+} fnpf_filter;
+fnpf_status fnpf_set_filter(fnpf_mesh* mesh, const fnpf_filter* filter);
+
+/* Applies the filter set by fnpf_set_filter to one surface field f [Ns]
+ * (device, in place), on `stream`.  Errors: EINVAL (no filter set). */
+fnpf_status fnpf_filter_apply(fnpf_mesh* mesh, double* f, void* stream);
+
 /* Ensembles of independent tanks (batched form).  An ensemble groups existing
  * meshes (not owned; they must outlive it).  fnpf_ensemble_rk4_step advances
  * tank i by one RK4 step of size dts[i] from time ts[i], state etas[i],

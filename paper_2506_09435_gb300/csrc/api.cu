@@ -3,6 +3,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "mesh.cuh"
 
@@ -134,6 +136,18 @@ StageArgs stage_args(fnpf_mesh* m, double* eta, double* phis, const double* ce, 
   return a;
 }
 
+// Step 4.7 filtering of the new state (eta, phis) in place, through the free
+// stage buffers, when a filter is set.
+cudaError_t enqueue_filter_step(fnpf_mesh* m, double* eta, double* phis, cudaStream_t s) {
+  if (!m->filter_on) return cudaSuccess;
+  const size_t bytes = m->g.ns * sizeof(double);
+  cudaError_t e = launch_filter(m->g, m->dfilter, eta, m->s_eta[0], phis, m->s_phi[0], s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(eta, m->s_eta[0], bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(phis, m->s_phi[0], bytes, cudaMemcpyDeviceToDevice, s);
+  m->launches += 1;
+  return e;
+}
+
 // Captures one RK4 step of mesh m (state arrays eta, phis, step dt; the time is
 // read from m->t_dev) on the capturing stream s: four device-driven solves and
 // stage kernels, then the per-stage summaries copied to pinned host memory.
@@ -148,6 +162,8 @@ cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cud
     ce = a.out_eta;
     cp = a.out_phi;
   }
+  cudaError_t e = enqueue_filter_step(m, eta, phis, s);
+  if (e != cudaSuccess) return e;
   return cudaMemcpyAsync(m->stage_info_host, m->stage_info, 4 * sizeof(StageInfo), cudaMemcpyDeviceToHost, s);
 }
 
@@ -240,6 +256,8 @@ fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, dou
     ce = a.out_eta;
     cp = a.out_phi;
   }
+  cudaError_t e = fnpf::enqueue_filter_step(m, eta, phis, s);
+  if (e != cudaSuccess) return cuda_fail(m, e, "filter");
   m->warm = true;
   return FNPF_OK;
 }
@@ -281,6 +299,99 @@ fnpf_status fnpf_set_relaxation(fnpf_mesh* m, const fnpf_relaxation* r) {
   m->relax.gen = nullptr;
   m->relax_on = true;
   return FNPF_OK;
+}
+
+fnpf_status fnpf_set_filter(fnpf_mesh* m, const fnpf_filter* f) {
+  if (!m) return FNPF_EINVAL;
+  const int p = m->g.p, n = m->g.n;
+  if (f && !(f->alpha >= 0.0 && std::isfinite(f->alpha))) {
+    m->err = "filter alpha must be finite and >= 0";
+    return FNPF_EINVAL;
+  }
+  if (f && f->alpha > 0.0 && (f->order < 1 || f->cutoff < 0 || f->cutoff >= p)) {
+    m->err = "filter order must be >= 1 and cutoff in 0..p-1";
+    return FNPF_EINVAL;
+  }
+  // the captured step includes or omits the filter
+  if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
+  m->step_exec = nullptr;
+  if (!f || f->alpha == 0.0) {
+    m->filter_on = false;
+    return FNPF_OK;
+  }
+  // V_ij = P~_j(xi_i) (orthonormal Legendre at the GLL nodes), F = V diag(sigma) V^-1
+  std::vector<double> V(n * n), Vi(n * n, 0.0), F(n * n, 0.0), sig(n, 1.0);
+  for (int i = 0; i < n; ++i) {
+    const double x = m->xi[i];
+    double pm = 1.0, pc = x;
+    for (int j = 0; j < n; ++j) {
+      double pj;
+      if (j == 0) pj = 1.0;
+      else if (j == 1) pj = x;
+      else {
+        pj = ((2.0 * j - 1.0) * x * pc - (j - 1.0) * pm) / j;
+        pm = pc;
+        pc = pj;
+      }
+      V[i * n + j] = pj * std::sqrt((2.0 * j + 1.0) / 2.0);
+    }
+  }
+  for (int k = f->cutoff + 1; k <= p; ++k)
+    sig[k] = std::exp(-f->alpha * std::pow((double)(k - f->cutoff) / (double)(p - f->cutoff), f->order));
+  // V^-1 by Gauss-Jordan elimination with partial pivoting (n <= 9)
+  std::vector<double> A = V;
+  for (int i = 0; i < n; ++i) Vi[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) {
+      m->err = "singular Vandermonde matrix";
+      return FNPF_EINVAL;
+    }
+    for (int k = 0; k < n; ++k) {
+      std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(Vi[c * n + k], Vi[piv * n + k]);
+    }
+    const double d = A[c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[c * n + k] /= d;
+      Vi[c * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double fr = A[r * n + c];
+      for (int k = 0; k < n; ++k) {
+        A[r * n + k] -= fr * A[c * n + k];
+        Vi[r * n + k] -= fr * Vi[c * n + k];
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += V[i * n + k] * sig[k] * Vi[k * n + j];
+      F[i * n + j] = s;
+    }
+  cudaError_t e = cudaSuccess;
+  if (!m->dfilter) e = cudaMalloc((void**)&m->dfilter, n * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(m->dfilter, F.data(), n * n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(m, e, "filter set-up");
+  m->filter_on = true;
+  return FNPF_OK;
+}
+
+fnpf_status fnpf_filter_apply(fnpf_mesh* m, double* f, void* stream) {
+  if (!m || !f) return FNPF_EINVAL;
+  if (!m->filter_on) {
+    m->err = "no filter set";
+    return FNPF_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = fnpf::launch_filter(m->g, m->dfilter, f, m->s_eta[0], nullptr, nullptr, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f, m->s_eta[0], m->g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  m->launches += 1;
+  return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "filter");
 }
 
 fnpf_status fnpf_autotune(fnpf_mesh* m, const double* eta, int* variant64, int* variant32, void* stream) {

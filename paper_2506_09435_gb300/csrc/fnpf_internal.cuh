@@ -231,6 +231,11 @@ struct StageArgs {
 cudaError_t launch_stage(const Geom& g, const Tables<double>& t, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_w(const Geom& g, const Tables<double>& t, const double* eta, const double* phis,
                      const double* phi, double* w, cudaStream_t s);
+// Modal filter (surface.cu): out = the filtered copy of in (element-interior
+// nodes filtered with the 1D matrix F [n * n] in each direction, other nodes
+// copied); two fields at once (in1/out1 may be null).
+cudaError_t launch_filter(const Geom& g, const double* F, const double* in0, double* out0, const double* in1,
+                          double* out1, cudaStream_t s);
 cudaError_t launch_check_state(const Geom& g, const double* eta, const double* phis, const double* h, int* status,
                                int* done, cudaStream_t s);
 

@@ -206,6 +206,7 @@ void free_mesh(fnpf_mesh* m) {
   if (m->b) cudaFree(m->b);
   if (m->eta64) cudaFree(m->eta64);
   if (m->zero_eta) cudaFree(m->zero_eta);
+  if (m->dfilter) cudaFree(m->dfilter);
   if (m->G64) cudaFree(m->G64);
   if (m->adj) cudaFree(m->adj);
   double* rptrs[] = {m->rx_cr, m->rx_gen, m->dxs, m->dys};

@@ -83,6 +83,10 @@ struct fnpf_mesh {
   fnpf_relaxation relax{};          // scalar parameters (array pointers unused)
   bool relax_on = false;
 
+  // modal filter (fnpf_set_filter): the 1D matrix V diag(sigma) V^-1, [n * n]
+  double* dfilter = nullptr;
+  bool filter_on = false;
+
   // adjoint step workspaces (allocated at the first fnpf_step_adjoint)
   double* adj = nullptr;            // one block holding all of them
   size_t adj_bytes = 0;
@@ -145,6 +149,7 @@ void prof_collect(fnpf_mesh* m, int iters_done);
 void graph_reset(GraphSlot* g);
 // Captured RK4 steps (api.cu).
 cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cudaStream_t s);
+cudaError_t enqueue_filter_step(fnpf_mesh* m, double* eta, double* phis, cudaStream_t s);
 fnpf_status read_step_info(fnpf_mesh* m, fnpf_solve_info* info, float ms);
 bool graph_mode(const fnpf_mesh* m);
 int64_t graph_kernel_nodes(cudaGraph_t g);

@@ -164,6 +164,51 @@ cudaError_t launch_w(const Geom& g, const Tables<double>& t, const double* eta, 
   return cudaGetLastError();
 }
 
+namespace {
+
+// One thread per surface column: an element-interior node (i, j) of element
+// column (ex, ey) gets sum_a sum_b F[i][a] F[j][b] f(a, b) (sum_a F[i][a] f(a)
+// in a 2D slice); every other node is copied.
+__global__ void filter_kernel(Geom g, const double* __restrict__ F, const double* __restrict__ in0,
+                              double* __restrict__ out0, const double* __restrict__ in1,
+                              double* __restrict__ out1) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= g.ns) return;
+  const int P = g.p, n = g.n;
+  const int ix = col % g.ncx, iy = col / g.ncx;
+  const int i = ix % P, j = g.dim == 3 ? iy % P : 0;
+  const bool interior = i != 0 && (g.dim == 2 || j != 0);
+  if (!interior) {
+    out0[col] = in0[col];
+    if (in1) out1[col] = in1[col];
+    return;
+  }
+  const int ex = ix / P, ey = g.dim == 3 ? iy / P : 0;
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = 0; b < (g.dim == 3 ? n : 1); ++b) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int a = 0; a < n; ++a) {
+      const int c = node_col(g, ex, ey, a, b);
+      t0 += F[i * n + a] * in0[c];
+      if (in1) t1 += F[i * n + a] * in1[c];
+    }
+    const double fj = g.dim == 3 ? F[j * n + b] : 1.0;
+    s0 += fj * t0;
+    s1 += fj * t1;
+  }
+  out0[col] = s0;
+  if (in1) out1[col] = s1;
+}
+
+}  // namespace
+
+cudaError_t launch_filter(const Geom& g, const double* F, const double* in0, double* out0, const double* in1,
+                          double* out1, cudaStream_t s) {
+  const int threads = 128;
+  filter_kernel<<<(g.ns + threads - 1) / threads, threads, 0, s>>>(g, F, in0, out0, in1, out1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_state(const Geom& g, const double* eta, const double* phis, const double* h, int* status,
                                int* done, cudaStream_t s) {
   const int threads = 128;

@@ -50,6 +50,10 @@ class SolveInfo(ctypes.Structure):
                     ms=self.ms)
 
 
+class Filter(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("order", ctypes.c_int), ("cutoff", ctypes.c_int)]
+
+
 class Relaxation(ctypes.Structure):
     _fields_ = [("cr", _dp), ("gen", _dp), ("amp", ctypes.c_double), ("kx", ctypes.c_double),
                 ("ky", ctypes.c_double), ("omega", ctypes.c_double), ("phase", ctypes.c_double),
@@ -71,6 +75,8 @@ def load():
         "fnpf_apply": [vp, vp, vp, vp, vp],
         "fnpf_diagonal": [vp, vp, vp, vp],
         "fnpf_precond_apply": [vp, vp, vp, vp, vp],
+        "fnpf_set_filter": [vp, ctypes.POINTER(Filter)],
+        "fnpf_filter_apply": [vp, vp, vp],
         "fnpf_apply_f32": [vp, vp, vp, vp, vp],
         "fnpf_laplace_solve": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_dtn": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
@@ -229,6 +235,14 @@ class Mesh:
 
     def diagonal(self, eta, d, stream=None):
         self._check(_LIB.fnpf_diagonal(self._h, _ptr(eta), _ptr(d), _stream(stream)))
+
+    def set_filter(self, alpha, order=2, cutoff=0):
+        """Modal filter of eta and phi after every RK4 step (alpha = 0: off)."""
+        f = Filter(float(alpha), int(order), int(cutoff))
+        self._check(_LIB.fnpf_set_filter(self._h, ctypes.byref(f)))
+
+    def filter_apply(self, f, stream=None):
+        self._check(_LIB.fnpf_filter_apply(self._h, _ptr(f), _stream(stream)))
 
     def precond_apply(self, eta, r, z, stream=None):
         """z = M r, the FP64 preconditioner (p-multigrid V-cycle or Jacobi) set
