@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "ensemble"],
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "ensemble", "convergence"],
                     help="step: RK4 steps (the benchmark); apply: operator applications only; "
-                         "ensemble: 64 seeded tanks in one launch per step vs one tank at a time")
+                         "ensemble: 64 seeded tanks in one launch per step vs one tank at a time; "
+                         "convergence: error of a stream-function wave after one period vs p and h")
     ap.add_argument("--tanks", type=int, default=64)
     ap.add_argument("--p", type=int, default=6)
     ap.add_argument("--nz", type=int, default=2)
@@ -585,8 +586,46 @@ def coarse_mode(args):
     return fnpf.FNPF_COARSE_CLUSTER if args.coarse_solver == "cluster" else fnpf.FNPF_COARSE_LAUNCHES
 
 
+def main_convergence(args):
+    """Accuracy study on a steady nonlinear wave (the paper's nonlinear
+    convergence tests, Sec. 4): a stream-function wave of steepness H/L = 0.05
+    at kh = 1 in a periodic 2D tank of one wavelength, 2 vertical elements,
+    carried for one period (dt = T/128); max-norm errors of eta (over H) and
+    of phi_eta (relative) against the exact travelling wave, for p = 3..8 at
+    4 elements per wavelength and for 2..16 elements at p = 4."""
+    import numpy as np
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    from paper_2506_09435_gb300 import workloads as W
+
+    def run(p, nx, nsteps=128):
+        d, wave = W.stream_function_tank_2d(nx=nx, nz=2, p=p, steepness=0.05)
+        gm = fnpf.Mesh(2, nx, 1, 2, p, True, False, np.full(p * nx, d["h0"]), Lx=d["Lx"], g=d["g"],
+                       opts=fnpf.default_opts(rtol=1e-13, max_iter=50000, precond=fnpf.FNPF_PMG))
+        x, _ = gm.surface_coords()
+        dev = torch.device("cuda:0")
+        eta = torch.tensor(wave.eta(x), dtype=torch.float64, device=dev)
+        phis = torch.tensor(wave.phis(x), dtype=torch.float64, device=dev)
+        T = wave.period()
+        for n in range(nsteps):
+            gm.rk4_step(eta, phis, n * T / nsteps, T / nsteps)
+        torch.cuda.synchronize()
+        ref = wave.phis(x, T)
+        return {"p": p, "nx": nx, "dof": gm.N,
+                "err_eta_over_H": float(np.max(np.abs(eta.cpu().numpy() - wave.eta(x, T))) / wave.H),
+                "err_phi_rel": float(np.max(np.abs(phis.cpu().numpy() - ref)) / np.max(np.abs(ref)))}
+
+    rows = [run(p, 4) for p in range(3, 9)] + [run(4, nx) for nx in (2, 8, 16)]
+    print(json.dumps({"mode": "convergence", "wave": "stream function, kh = 1, H/L = 0.05, one period, dt = T/128",
+                      "rows": rows}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "convergence":
+        return main_convergence(args)
     if args.mode == "ensemble":
         return main_ensemble(args)
     if args.impl == "reference":

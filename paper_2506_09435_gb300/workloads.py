@@ -238,3 +238,121 @@ def manufactured_potential(x, y, z, h, kx, ky):
     phi = np.cosh(kap * (z + h)) * np.cos(kx * x) * np.cos(ky * y)
     dphidz = kap * np.sinh(kap * (z + h)) * np.cos(kx * x) * np.cos(ky * y)
     return phi, dphidz
+
+
+# ----------------------------------------------------------------------------
+# steady nonlinear travelling waves (stream-function theory)
+
+class StreamFunctionWave:
+    """Steady periodic wave of height H and wavelength L = 2 pi / k on depth d,
+    travelling in +x with celerity c, by the Fourier approximation method of
+    Rienecker and Fenton (J. Fluid Mech. 104, 1981), written here from its
+    equations (an input generator and reference solution; not the FNPF method).
+
+    In the frame moving with the wave (X = x - c t), y the height above the
+    bed, the stream function is
+        psi(X, y) = B_0 y + sum_{j=1..N} B_j sinh(j k y) / cosh(j k d) cos(j k X)
+    (the bed y = 0 is the streamline psi = 0) and the velocity potential
+        Phi(X, y) = B_0 X + sum_j B_j cosh(j k y) / cosh(j k d) sin(j k X).
+    Unknowns: B_0..B_N, the elevations eta_m at X_m = m L / (2N), m = 0..N
+    (crest at X = 0), and the constants Q, R.  Equations at every X_m (on
+    y = d + eta_m): psi = -Q (kinematic) and 1/2 |grad psi|^2 + g eta_m = R
+    (dynamic); plus the mean of eta = 0 (trapezoid rule over a wavelength) and
+    eta_0 - eta_N = H.  With no mean current (Stokes' first definition) c = -B_0.
+    Solved by Newton's method with a finite-difference Jacobian, stepping the
+    height up from H / steps.
+
+    In the fixed frame, phi = Phi(x - c t, y) + c (x - c t) + (c^2 / 2 - R) t
+    solves the Bernoulli condition without a constant (d phi/dt + |grad phi|^2 / 2
+    + g eta = 0 on the surface), so the surface potential at time t is
+        phi_eta(x, t) = sum_j B_j cosh(j k (d + eta)) / cosh(j k d) sin(j k (x - c t))
+                        + (c^2 / 2 - R) t,   eta = eta(x - c t).
+    """
+
+    def __init__(self, d, L, H, g=G_DEFAULT, N=24, steps=4, tol=1e-13):
+        self.d, self.L, self.H, self.g, self.N = float(d), float(L), float(H), float(g), int(N)
+        self.k = 2 * math.pi / self.L
+        N, k = self.N, self.k
+        self.X = np.arange(N + 1) * self.L / (2 * N)
+        c0 = math.sqrt(g / k * math.tanh(k * d))
+        # unknown vector: eta_0..eta_N, B_0..B_N, Q, R
+        x = np.zeros(2 * N + 4)
+        for s in range(1, steps + 1):
+            Hs = H * s / steps
+            if s == 1:
+                x[:N + 1] = 0.5 * Hs * np.cos(k * self.X)
+                x[N + 1] = -c0
+                x[N + 2] = c0 * 0.5 * Hs / math.tanh(k * d)
+                x[2 * N + 2] = c0 * d
+                x[2 * N + 3] = 0.5 * c0 * c0
+            else:
+                x[:N + 1] *= Hs / (H * (s - 1) / steps)
+            for _ in range(60):
+                r = self._residual(x, Hs)
+                if np.max(np.abs(r)) < tol * max(1.0, c0 * c0):
+                    break
+                J = np.empty((r.size, x.size))
+                for i in range(x.size):
+                    dx = 1e-7 * max(1.0, abs(x[i]))
+                    xp, xm = x.copy(), x.copy()
+                    xp[i] += dx
+                    xm[i] -= dx
+                    J[:, i] = (self._residual(xp, Hs) - self._residual(xm, Hs)) / (2 * dx)
+                x = x - np.linalg.solve(J, r)
+            else:
+                raise RuntimeError("stream-function iteration did not converge")
+        self.eta_m = x[:N + 1].copy()
+        self.B = x[N + 1:2 * N + 2].copy()
+        self.Q, self.R = x[2 * N + 2], x[2 * N + 3]
+        self.c = -self.B[0]
+        self.residual = float(np.max(np.abs(self._residual(x, H))))
+        # cosine coefficients of eta(X) interpolating eta_m (DCT-I pair)
+        m = np.arange(N + 1)
+        w = np.ones(N + 1)
+        w[0] = w[N] = 0.5
+        self.E = np.array([2.0 / N * np.sum(w * self.eta_m * np.cos(j * m * math.pi / N)) for j in range(N + 1)])
+
+    def _residual(self, x, H):
+        N, k, d, g = self.N, self.k, self.d, self.g
+        eta, B, Q, R = x[:N + 1], x[N + 1:2 * N + 2], x[2 * N + 2], x[2 * N + 3]
+        y = d + eta
+        j = np.arange(1, N + 1)[None, :]
+        kx = j * k * self.X[:, None]
+        sh = np.sinh(j * k * y[:, None]) / np.cosh(j * k * d)
+        ch = np.cosh(j * k * y[:, None]) / np.cosh(j * k * d)
+        psi = B[0] * y + np.sum(B[1:] * sh * np.cos(kx), axis=1)
+        U = B[0] + np.sum(j * k * B[1:] * ch * np.cos(kx), axis=1)
+        W = np.sum(j * k * B[1:] * sh * np.sin(kx), axis=1)
+        wt = np.ones(N + 1)
+        wt[0] = wt[N] = 0.5
+        return np.concatenate([psi + Q, 0.5 * (U * U + W * W) + g * eta - R,
+                               [np.sum(wt * eta) / N, eta[0] - eta[N] - H]])
+
+    def eta(self, x, t=0.0):
+        X = np.asarray(x, dtype=np.float64) - self.c * t
+        j = np.arange(self.N + 1)
+        w = np.ones(self.N + 1)
+        w[0] = w[self.N] = 0.5
+        return np.sum(w * self.E * np.cos(j * self.k * X[..., None]), axis=-1)
+
+    def phis(self, x, t=0.0):
+        X = np.asarray(x, dtype=np.float64) - self.c * t
+        y = self.d + self.eta(x, t)
+        j = np.arange(1, self.N + 1)
+        ch = np.cosh(j * self.k * y[..., None]) / np.cosh(j * self.k * self.d)
+        return np.sum(self.B[1:] * ch * np.sin(j * self.k * X[..., None]), axis=-1) \
+            + (0.5 * self.c * self.c - self.R) * t
+
+    def period(self):
+        return self.L / self.c
+
+
+def stream_function_tank_2d(nx=4, nz=2, p=6, kh=1.0, steepness=0.05, h=1.0, g=G_DEFAULT, N=24):
+    """2D periodic tank of one wavelength holding a stream-function wave of
+    height H = steepness L (the paper's nonlinear convergence studies use
+    stream-function waves, Sec. 3.3)."""
+    k = kh / h
+    L = 2 * math.pi / k
+    wave = StreamFunctionWave(h, L, steepness * L, g=g, N=N)
+    return dict(dim=2, nx=nx, ny=1, nz=nz, p=p, periodic_x=True, periodic_y=False,
+                Lx=L, Ly=1.0, h0=h, k=k, g=g), wave
