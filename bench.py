@@ -50,6 +50,8 @@ def parse():
                     help="elements-per-CTA shape of the operator kernels (-1: autotuned)")
     ap.add_argument("--model", default="fnpf", choices=["fnpf", "lpf"],
                     help="fnpf: fully nonlinear (the configuration's method); lpf: linear potential flow")
+    ap.add_argument("--mg-schedule", default="halve", choices=["halve", "two", "step2"],
+                    help="multigrid orders: p, p/2, ..., 1 (halve); p, 1 (two); p, p-2, ..., 1 (step2)")
     ap.add_argument("--cheb-kind", type=int, default=1, choices=[1, 4],
                     help="Chebyshev smoother: 1 = first kind on [lmax/20, lmax], 4 = fourth kind on [0, lmax]")
     ap.add_argument("--cheb-range", type=float, default=160.0,
@@ -221,7 +223,7 @@ def main_gb300(args):
     opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000, precond=pre, cheb_degree=cdeg,
                              coarse_iters=args.coarse_degree, coarse_solver=coarse_mode(args),
                              cheb_kind=args.cheb_kind, cheb_range=args.cheb_range,
-                             model=model_id(args),
+                             model=model_id(args), mg_schedule=schedule_id(args),
                              precision=prec)
     ncx = d["p"] * d["nx"]
     h = np.full(ncx * ncx, d["h0"])
@@ -281,7 +283,7 @@ def main_gb300(args):
         mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
                                   precond=pre, cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
                                   coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
-                                  cheb_range=args.cheb_range, model=model_id(args))
+                                  cheb_range=args.cheb_range, model=model_id(args), mg_schedule=schedule_id(args))
         mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
                        opts=mopts)
         if args.shape >= 0:
@@ -427,7 +429,7 @@ def main_gb300(args):
             "config": {"workload": WORKLOAD, "dof": mesh.N, "surface_dof": mesh.ns, "precision": "fp64",
                        "precond": args.precond, "cheb_degree": cdeg, "coarse_degree": args.coarse_degree,
                        "coarse_solver": args.coarse_solver, "cheb_kind": args.cheb_kind,
-                       "cheb_range": args.cheb_range, "model": args.model,
+                       "cheb_range": args.cheb_range, "model": args.model, "mg_schedule": args.mg_schedule,
                        "cta_shape": ("autotuned" if args.shape < 0 else "forced"),
                        "element_columns_per_cta": mesh.get_shapes()[2],
                        "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
@@ -574,6 +576,10 @@ def main_ensemble(args):
         "orders": sorted(set(d["p"] for d in tanks)), "finite": ok, "gpu_launches": launches,
         "clocks": clk.summary(), "data": "synthetic"}))
     return 0
+
+
+def schedule_id(args):
+    return {"halve": 0, "two": 1, "step2": 2}[args.mg_schedule]
 
 
 def model_id(args):

@@ -75,6 +75,9 @@ enum { FNPF_CHEB_FIRST = 1, FNPF_CHEB_FOURTH = 4 };
  * (the geometry takes eta = 0 wherever it would take eta) and the surface
  * conditions are d eta/dt = w, d phi/dt = -g eta. */
 enum { FNPF_NONLINEAR = 0, FNPF_LINEAR = 1 };
+/* Order sequence of the p-multigrid levels: FNPF_MG_HALVE p -> p/2 -> ... -> 1,
+ * FNPF_MG_TWO_LEVEL p -> 1, FNPF_MG_STEP2 p -> p-2 -> ... -> 1. */
+enum { FNPF_MG_HALVE = 0, FNPF_MG_TWO_LEVEL = 1, FNPF_MG_STEP2 = 2 };
 
 /* Mesh descriptor.  All arrays are HOST pointers, copied at creation. */
 typedef struct {
@@ -112,6 +115,7 @@ typedef struct {
   int cheb_kind;           /* FNPF_CHEB_FIRST or FNPF_CHEB_FOURTH (FNPF_PMG)        */
   double cheb_range;       /* FNPF_CHEB_FIRST smooths [lmax / cheb_range, lmax] (> 1) */
   int model;               /* FNPF_NONLINEAR or FNPF_LINEAR                        */
+  int mg_schedule;         /* FNPF_MG_HALVE, FNPF_MG_TWO_LEVEL or FNPF_MG_STEP2     */
 } fnpf_opts;
 
 typedef struct {
@@ -132,7 +136,7 @@ fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t*
  * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 6,
  * inner_rtol 1e-5, max_outer 20, use_graphs 1, store_metric 1,
  * coarse_solver FNPF_COARSE_CLUSTER, cheb_kind FNPF_CHEB_FIRST, cheb_range 160,
- * model FNPF_NONLINEAR. */
+ * model FNPF_NONLINEAR, mg_schedule FNPF_MG_HALVE. */
 void fnpf_default_opts(fnpf_opts* opts);
 
 /* Creates a mesh on the current CUDA device: GLL tables, horizontal metric,

@@ -451,9 +451,18 @@ fnpf_status ensure_mg(fnpf_mesh* m) {
     m->err = "cheb_range must be in (1, 1e12)";
     return FNPF_EINVAL;
   }
+  if (m->opts.mg_schedule != FNPF_MG_HALVE && m->opts.mg_schedule != FNPF_MG_TWO_LEVEL &&
+      m->opts.mg_schedule != FNPF_MG_STEP2) {
+    m->err = "mg_schedule must be FNPF_MG_HALVE, FNPF_MG_TWO_LEVEL or FNPF_MG_STEP2";
+    return FNPF_EINVAL;
+  }
+  if (m->mg && mg_schedule(m->mg) != m->opts.mg_schedule) {
+    mg_destroy(m->mg);
+    m->mg = nullptr;
+  }
   if (!m->mg) {
     std::string why;
-    m->mg = mg_create(m->g, m->h, m->Xs, m->Ys, m->iso, m->Lx, m->Ly, &why);
+    m->mg = mg_create(m->g, m->h, m->Xs, m->Ys, m->iso, m->Lx, m->Ly, m->opts.mg_schedule, &why);
     if (!m->mg) {
       m->err = why;
       return FNPF_ENOMEM;

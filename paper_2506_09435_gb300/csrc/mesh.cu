@@ -278,6 +278,7 @@ void fnpf_default_opts(fnpf_opts* o) {
   o->cheb_kind = FNPF_CHEB_FIRST;
   o->cheb_range = 160.0;
   o->model = FNPF_NONLINEAR;
+  o->mg_schedule = FNPF_MG_HALVE;
 }
 
 fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, fnpf_mesh** out) {
@@ -430,6 +431,11 @@ fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   m->step_exec = nullptr;
   m->cheb_valid[0] = m->cheb_valid[1] = false;
   m->lpf_ready[0] = m->lpf_ready[1] = false;
+  m->warm = false;   // the next step is host-driven: it rebuilds what the new options need
+  if (m->mg && fnpf::mg_schedule(m->mg) != o->mg_schedule) {
+    fnpf::mg_destroy(m->mg);
+    m->mg = nullptr;
+  }
   fnpf::mg_set_coarse(m->mg, o->coarse_solver);
   fnpf::mg_set_kind(m->mg, o->cheb_kind, o->cheb_range);
   return FNPF_OK;

@@ -476,7 +476,11 @@ bool cluster_launch_ok() {
 
 // ---------------------------------------------------------------------------- host helpers
 
-int next_p(int p) { return p / 2 > 1 ? p / 2 : 1; }
+int next_p(int p, int schedule) {
+  if (schedule == FNPF_MG_TWO_LEVEL) return 1;
+  if (schedule == FNPF_MG_STEP2) return p - 2 > 1 ? p - 2 : 1;
+  return p / 2 > 1 ? p / 2 : 1;
+}
 
 std::vector<double> interp_matrix(const std::vector<double>& xf, const std::vector<double>& xc) {
   const int nf = (int)xf.size(), nc = (int)xc.size();
@@ -544,6 +548,7 @@ struct Mg {
   CgScalars* sc = nullptr;        // [L] Lanczos scalars
   double* part = nullptr;         // [4 * kVecBlocks]
   bool fusable = false;           // the coarsest level fits the cluster kernel
+  int schedule = FNPF_MG_HALVE;
   int coarse_mode = FNPF_COARSE_CLUSTER;
   int cheb_kind = FNPF_CHEB_FIRST;
   double cheb_range = 160.0;
@@ -572,6 +577,7 @@ void mg_destroy(Mg* mg) {
 }
 
 int mg_levels(const Mg* mg) { return mg ? mg->L : 0; }
+int mg_schedule(const Mg* mg) { return mg ? mg->schedule : FNPF_MG_HALVE; }
 void mg_set_coarse(Mg* mg, int mode) {
   if (mg) mg->coarse_mode = mode;
 }
@@ -583,13 +589,14 @@ void mg_set_kind(Mg* mg, int kind, double range) {
 bool mg_coarse_fused(const Mg* mg) { return mg && mg->fused(); }
 
 Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<double>& X0,
-              const std::vector<double>& Y0, bool iso, double Lx, double Ly, std::string* err) {
+              const std::vector<double>& Y0, bool iso, double Lx, double Ly, int schedule, std::string* err) {
   Mg* mg = new Mg();
   int p = g0.p;
+  mg->schedule = schedule;
   mg->g[0] = g0;
   mg->L = 1;
   while (p > 1 && mg->L < kMaxLevels) {
-    p = next_p(p);
+    p = next_p(p, schedule);
     mg->g[mg->L] = level_geom(g0, p);
     ++mg->L;
   }

@@ -47,7 +47,8 @@ struct Mg;   // opaque; owned by the mesh
 // Builds the hierarchy p -> p/2 -> ... -> 1 for the mesh sizes g0 (host work and
 // device allocations).  Returns nullptr and sets *err on failure.
 Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<double>& X0,
-              const std::vector<double>& Y0, bool iso, double Lx, double Ly, std::string* err);
+              const std::vector<double>& Y0, bool iso, double Lx, double Ly, int schedule, std::string* err);
+int mg_schedule(const Mg* mg);
 void mg_destroy(Mg* mg);
 int mg_levels(const Mg* mg);
 // Coarse solver of the next set-ups and V-cycles: FNPF_COARSE_CLUSTER runs the

@@ -1,4 +1,5 @@
-// Instantiations of the p-multigrid transfer kernels (double).
+// Instantiations of the p-multigrid transfer kernels for the order pairs of the
+// level schedules (halving, two-level, steps of two) (double).
 #include "mg_impl.cuh"
 
 namespace fnpf {
@@ -14,6 +15,15 @@ cudaError_t launch_transfer_double(const Geom& gf, const Geom& gc, const double*
     case 5 * 16 + 3: return launch_transfer_t<double, 5, 3>(gf, gc, J, in, out, ring, mode, skip, s);
     case 4 * 16 + 2: return launch_transfer_t<double, 4, 2>(gf, gc, J, in, out, ring, mode, skip, s);
     case 3 * 16 + 2: return launch_transfer_t<double, 3, 2>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 9 * 16 + 7: return launch_transfer_t<double, 9, 7>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 8 * 16 + 6: return launch_transfer_t<double, 8, 6>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 7 * 16 + 5: return launch_transfer_t<double, 7, 5>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 6 * 16 + 4: return launch_transfer_t<double, 6, 4>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 9 * 16 + 2: return launch_transfer_t<double, 9, 2>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 8 * 16 + 2: return launch_transfer_t<double, 8, 2>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 7 * 16 + 2: return launch_transfer_t<double, 7, 2>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 6 * 16 + 2: return launch_transfer_t<double, 6, 2>(gf, gc, J, in, out, ring, mode, skip, s);
+    case 5 * 16 + 2: return launch_transfer_t<double, 5, 2>(gf, gc, J, in, out, ring, mode, skip, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -21,6 +21,7 @@ FNPF_JACOBI, FNPF_PMG = 0, 1
 FNPF_COARSE_LAUNCHES, FNPF_COARSE_CLUSTER = 0, 1
 FNPF_CHEB_FIRST, FNPF_CHEB_FOURTH = 1, 4
 FNPF_NONLINEAR, FNPF_LINEAR = 0, 1
+FNPF_MG_HALVE, FNPF_MG_TWO_LEVEL, FNPF_MG_STEP2 = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -38,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int), ("store_metric", ctypes.c_int),
                 ("coarse_solver", ctypes.c_int), ("cheb_kind", ctypes.c_int), ("cheb_range", ctypes.c_double),
-                ("model", ctypes.c_int)]
+                ("model", ctypes.c_int), ("mg_schedule", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

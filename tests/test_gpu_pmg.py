@@ -185,3 +185,25 @@ def test_fourth_kind_one_step_is_scaled_jacobi(fnpf):
     rho4 = 4.0 / (3.0 * ratios[0])
     rho1 = 2.0 / (ratios[1] * (1.0 + 1.0 / fnpf.default_opts().cheb_range))
     assert abs(rho4 - rho1) < 1e-10 * rho1 and 1.0 < rho4 < 20.0
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1], SHAPES[3], SHAPES[4], SHAPES[5]], ids=ids)
+@pytest.mark.parametrize("schedule", ["two", "step2"])
+def test_level_schedules_solve_and_stay_spd(fnpf, shape, schedule):
+    """The two-level (p -> 1) and steps-of-two (p -> p-2 -> ... -> 1) level
+    sequences give the oracle's solution and a symmetric positive definite
+    V-cycle."""
+    sched = fnpf.FNPF_MG_TWO_LEVEL if schedule == "two" else fnpf.FNPF_MG_STEP2
+    c = Case(fnpf, *shape, opts=pmg(fnpf, mg_schedule=sched))
+    phi_ref = osolve.laplace_solve(c.om, c.eta, c.h, c.phis)
+    phi = torch.zeros(c.om.N, dtype=torch.float64, device=c.dev)
+    info = c.gm.laplace_solve(c.t(c.eta), c.t(c.phis), phi)
+    assert info["status"] == 0 and rel_l2(phi.cpu().numpy(), phi_ref) < 1e-10
+    n = c.gm.N - c.gm.ns
+    r1 = torch.as_tensor(c.rng.standard_normal(n), device=c.dev)
+    r2 = torch.as_tensor(c.rng.standard_normal(n), device=c.dev)
+    z1, _ = _precond(c, fnpf, r1, mg_schedule=sched)
+    z2, _ = _precond(c, fnpf, r2, mg_schedule=sched)
+    a, b = float(torch.dot(z1, r2)), float(torch.dot(r1, z2))
+    assert abs(a - b) < 1e-12 * float(torch.linalg.norm(z1) * torch.linalg.norm(r2))
+    assert float(torch.dot(z1, r1)) > 0
