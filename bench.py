@@ -276,12 +276,13 @@ def main_gb300(args):
     assert all(i["status"] == 0 for inf in infos for i in inf)
     assert torch.isfinite(eta).all() and torch.isfinite(phis).all()
 
-    # --- mixed precision on the same workload from the same initial state: FP32 operator and
-    #     inner Jacobi-PCG, FP64 defect correction to the same rtol; error vs the FP64 path
-    mixed = None
-    if not args.no_mixed:
-        mopts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
-                                  precond=pre, cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
+    # --- the other precision forms on the same workload from the same initial state, each
+    #     reported with its error against the FP64 path: FNPF_MIXED (FP64 defect correction
+    #     around an FP32 operator, FP32 p-MG and FP32 PCG) and FNPF_FP64_PC32 (FP64 PCG with
+    #     the p-MG preconditioner in FP32)
+    def precision_form(prec_id, cheb):
+        mopts = fnpf.default_opts(precision=prec_id, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
+                                  precond=pre, cheb_degree=cheb, coarse_iters=args.coarse_degree,
                                   coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
                                   cheb_range=args.cheb_range, model=model_id(args), mg_schedule=schedule_id(args))
         mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
@@ -324,17 +325,27 @@ def main_gb300(args):
             tm += dt
         torch.cuda.synchronize()
         mprof = mm.profile_read(reset=True)
-        mixed = {"value": world * mesh.N * args.steps / (m_ms * 1e-3), "unit": UNIT,
-                 "ms_per_step": m_ms / args.steps, "dtype": "f32 inner / f64 outer",
-                 "rel_l2_vs_fp64_path": {"eta": err_e, "phis": err_p},
-                 "inner_iters_per_solve_mean": statistics.mean(i["iters"] for inf in minfos for i in inf),
-                 "outer_iters_per_solve_mean": statistics.mean(i["outer_iters"] for inf in minfos for i in inf),
-                 "max_rel_res": max(i["rel_res"] for inf in minfos for i in inf),
-                 "fp32_apply_ms": mprof["apply32_ms"] / max(1, mprof["apply32_count"]),
-                 "element_columns_per_cta_fp32": mm.get_shapes()[3],
-                 "gpu_launches": mlaunch}
+        out = {"value": world * mesh.N * args.steps / (m_ms * 1e-3), "unit": UNIT,
+               "ms_per_step": m_ms / args.steps,
+               "dtype": "f32 inner / f64 outer" if prec_id == fnpf.FNPF_MIXED
+               else "f64 PCG, f32 p-multigrid preconditioner",
+               "cheb_degree": cheb,
+               "rel_l2_vs_fp64_path": {"eta": err_e, "phis": err_p},
+               "inner_iters_per_solve_mean": statistics.mean(i["iters"] for inf in minfos for i in inf),
+               "outer_iters_per_solve_mean": statistics.mean(i["outer_iters"] for inf in minfos for i in inf),
+               "max_rel_res": max(i["rel_res"] for inf in minfos for i in inf),
+               "fp32_apply_ms": mprof["apply32_ms"] / max(1, mprof["apply32_count"]),
+               "element_columns_per_cta_fp32": mm.get_shapes()[3],
+               "gpu_launches": mlaunch}
         assert all(i["status"] == 0 for inf in minfos for i in inf)
         del mm
+        return out
+
+    mixed = pc32 = None
+    if not args.no_mixed:
+        mixed = precision_form(fnpf.FNPF_MIXED, args.mixed_cheb_degree)
+        if pre == fnpf.FNPF_PMG:
+            pc32 = precision_form(fnpf.FNPF_FP64_PC32, args.cheb_degree)
 
     # --- dominant kernel: the operator application inside the solves, timed live with
     #     CUDA events on the solve's stream over a further 3 RK4 steps
@@ -437,7 +448,7 @@ def main_gb300(args):
                        "cg_iters_per_solve_mean": statistics.mean(iters), "max_rel_res": rel_res,
                        "wall_s": wall},
             "roofline": roofline,
-            "mixed": mixed,
+            "mixed": mixed, "fp64_pc32": pc32,
             "adjoint": adjoint,
             "cpu_baseline": cpu,
             "e2e": e2e,

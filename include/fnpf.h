@@ -54,7 +54,12 @@ typedef enum {
 } fnpf_status;
 
 enum { FNPF_BOX = 0, FNPF_ISOPARAMETRIC = 1 };
-enum { FNPF_FP64 = 0, FNPF_MIXED = 1 };
+/* FNPF_FP64: everything in FP64.  FNPF_MIXED: FP64 defect correction around
+ * an FP32 PCG with FP32 operator and FP32 p-multigrid.  FNPF_FP64_PC32: FP64
+ * PCG (FP64 operator, vectors, dot products) whose p-multigrid preconditioner
+ * runs in FP32 on the rounded residual (FNPF_PMG only; with FNPF_JACOBI it is
+ * FNPF_FP64). */
+enum { FNPF_FP64 = 0, FNPF_MIXED = 1, FNPF_FP64_PC32 = 2 };
 enum { FNPF_JACOBI = 0, FNPF_PMG = 1 };
 /* Coarsest multigrid level (p = 1): FNPF_COARSE_CLUSTER assembles its 27-point
  * (9-point in 2D) stencil once per solve and runs the whole coarse Chebyshev
@@ -95,7 +100,7 @@ typedef struct {
 
 /* Solver options (fnpf_default_opts fills every field). */
 typedef struct {
-  int precision;           /* FNPF_FP64 or FNPF_MIXED (FP32 inner, FP64 outer)     */
+  int precision;           /* FNPF_FP64, FNPF_MIXED or FNPF_FP64_PC32              */
   int precond;             /* FNPF_JACOBI or FNPF_PMG                              */
   double rtol;             /* stop when ||r||_2 <= max(rtol ||b||_2, atol)         */
   double atol;

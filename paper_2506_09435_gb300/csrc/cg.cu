@@ -174,6 +174,21 @@ __global__ void __launch_bounds__(NT) to_float_kernel(int64_t n, const double* a
   GRID_LOOP(i, n) b[i] = (float)a[i];
 }
 
+// Residual into the FP32 preconditioner and its result back (FNPF_FP64_PC32).
+__global__ void __launch_bounds__(NT) narrow_kernel(const int* skip, int64_t n, const double* a, float* b) {
+  if (skip && *skip) return;
+  GRID_LOOP(i, n) b[i] = (float)a[i];
+}
+__global__ void __launch_bounds__(NT) widen_kernel(const int* skip, int64_t n, const float* a, double* b) {
+  if (skip && *skip) return;
+  GRID_LOOP(i, n) b[i] = (double)a[i];
+}
+
+// An FP64 solve whose p-multigrid preconditioner runs in FP32.
+inline bool pc32(const fnpf_mesh* m) {
+  return m->opts.precision == FNPF_FP64_PC32 && m->opts.precond == FNPF_PMG;
+}
+
 inline int vec_blocks(int64_t n) { return vec::blocks_for(n); }
 
 // Host-driven solves re-estimate the Chebyshev intervals on the first solve of
@@ -308,6 +323,28 @@ struct PcgBufs {
   CgScalars* sc;
 };
 
+// z = M r with the p-multigrid V-cycle in the solve's precision, or, for an
+// FNPF_FP64_PC32 solve, the FP32 V-cycle on the residual rounded to FP32 (its
+// FP32 set-up done by mg_prepare<float> on eta32).
+template <typename T>
+cudaError_t apply_precond(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T* r, T* z, const int* skip,
+                          cudaStream_t s) {
+  if (sizeof(T) == 8 && pc32(m)) {
+    const int64_t NI = m->g.NI;
+    const int nb = vec_blocks(NI);
+    narrow_kernel<<<nb, NT, 0, s>>>(skip, NI, reinterpret_cast<const double*>(r), m->r32);
+    cudaError_t e = mg_apply<float>(m->mg, m->tables32(), m->eta32, nullptr, m->r32, m->z32,
+                                    reinterpret_cast<float*>(m->ring), m->variant32, m->opts.cheb_degree,
+                                    m->opts.coarse_iters, skip, s, &m->launches);
+    if (e != cudaSuccess) return e;
+    widen_kernel<<<nb, NT, 0, s>>>(skip, NI, m->z32, reinterpret_cast<double*>(z));
+    m->launches += 2;
+    return cudaGetLastError();
+  }
+  return mg_apply<T>(m->mg, t, eta, level0_G<T>(m), r, z, reinterpret_cast<T*>(m->ring), m->variant<T>(),
+                     m->opts.cheb_degree, m->opts.coarse_iters, skip, s, &m->launches);
+}
+
 // One PCG iteration (iteration parity it & 1), enqueued on s.
 template <typename T>
 cudaError_t enqueue_iteration(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>& B, int it, cudaStream_t s) {
@@ -321,8 +358,7 @@ cudaError_t enqueue_iteration(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>
   vec::update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, pmg ? nullptr : B.dinv,
                                           m->partials, nb, nullptr);
   if (pmg) {
-    e = mg_apply<T>(m->mg, t, B.eta, level0_G<T>(m), B.r, B.z, reinterpret_cast<T*>(m->ring), m->variant<T>(),
-                    m->opts.cheb_degree, m->opts.coarse_iters, skip, s, &m->launches);
+    e = apply_precond<T>(m, t, B.eta, B.r, B.z, skip, s);
     if (e != cudaSuccess) return e;
     vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.r, B.z, m->partials + 1 * nb);
     m->launches += 1;
@@ -389,8 +425,7 @@ template <typename T>
 fnpf_status pmg_start(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T* r, T* z, T* p, cudaStream_t s) {
   const int64_t NI = m->g.NI;
   const int nb = vec_blocks(NI);
-  FNPF_CK(mg_apply<T>(m->mg, t, eta, level0_G<T>(m), r, z, reinterpret_cast<T*>(m->ring), m->variant<T>(),
-                      m->opts.cheb_degree, m->opts.coarse_iters, nullptr, s, &m->launches));
+  FNPF_CK(apply_precond<T>(m, t, eta, r, z, nullptr, s));
   vec::copy_kernel<T><<<nb, NT, 0, s>>>(NI, z, p, nullptr);
   vec::dot_kernel<T><<<nb, NT, 0, s>>>(nullptr, NI, r, z, m->partials + 1 * nb);
   m->launches += 2;
@@ -562,8 +597,14 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
   }
   if (!mixed && pmg && !keep64) {
-    FNPF_CK(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
-                               m->opts.coarse_iters, want_estimate(m, 0), s));
+    if (pc32(m)) {
+      to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+      FNPF_CK(mg_prepare<float>(m->mg, m->tables32(), m->eta32, nullptr, reinterpret_cast<float*>(m->ring),
+                                m->variant32, m->opts.cheb_degree, m->opts.coarse_iters, want_estimate(m, 1), s));
+    } else {
+      FNPF_CK(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
+                                 m->opts.coarse_iters, want_estimate(m, 0), s));
+    }
   }
   if (!mixed && m->linear()) m->lpf_ready[0] = true;
   FNPF_CK(cudaGetLastError());
@@ -783,16 +824,22 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
     ENQ(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
     vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
   }
-  if (!mixed && pmg && !keep64)
-    ENQ(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
-                           m->opts.coarse_iters, estimate, s));
+  if (!mixed && pmg && !keep64) {
+    if (pc32(m)) {
+      to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+      ENQ(mg_prepare<float>(m->mg, m->tables32(), m->eta32, nullptr, reinterpret_cast<float*>(m->ring),
+                            m->variant32, m->opts.cheb_degree, m->opts.coarse_iters, estimate, s));
+    } else {
+      ENQ(mg_prepare<double>(m->mg, t, eta, level0_G<double>(m), m->ring, m->variant64, m->opts.cheb_degree,
+                             m->opts.coarse_iters, estimate, s));
+    }
+  }
   ENQ(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
   ENQ(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
   cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
                                    mixed ? m->b : nullptr, m->partials, nb);
   if (!mixed && pmg) {
-    ENQ(mg_apply<double>(m->mg, t, eta, level0_G<double>(m), m->r, m->z, m->ring, m->variant64,
-                         m->opts.cheb_degree, m->opts.coarse_iters, nullptr, s, &m->launches));
+    ENQ(apply_precond<double>(m, t, eta, m->r, m->z, nullptr, s));
     vec::copy_kernel<double><<<nb, NT, 0, s>>>(NI, m->z, m->p, nullptr);
     vec::dot_kernel<double><<<nb, NT, 0, s>>>(nullptr, NI, m->r, m->z, m->partials + 1 * nb);
   }

@@ -301,6 +301,10 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
     g_create_error = "model must be FNPF_NONLINEAR or FNPF_LINEAR";
     return FNPF_EINVAL;
   }
+  if (opts && (opts->precision < FNPF_FP64 || opts->precision > FNPF_FP64_PC32)) {
+    g_create_error = "precision must be FNPF_FP64, FNPF_MIXED or FNPF_FP64_PC32";
+    return FNPF_EINVAL;
+  }
   fnpf_mesh* m = new fnpf_mesh();
   m->g = g;
   if (opts) m->opts = *opts;
@@ -423,6 +427,10 @@ fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   if (!m || !o) return FNPF_EINVAL;
   if (o->model != FNPF_NONLINEAR && o->model != FNPF_LINEAR) {
     m->err = "model must be FNPF_NONLINEAR or FNPF_LINEAR";
+    return FNPF_EINVAL;
+  }
+  if (o->precision < FNPF_FP64 || o->precision > FNPF_FP64_PC32) {
+    m->err = "precision must be FNPF_FP64, FNPF_MIXED or FNPF_FP64_PC32";
     return FNPF_EINVAL;
   }
   m->opts = *o;

@@ -18,6 +18,7 @@ FNPF_OK, FNPF_EINVAL, FNPF_ENOMEM, FNPF_ECUDA, FNPF_ENOCONV, FNPF_EBREAKDOWN, FN
 FNPF_BOX, FNPF_ISOPARAMETRIC = 0, 1
 FNPF_FP64, FNPF_MIXED = 0, 1
 FNPF_JACOBI, FNPF_PMG = 0, 1
+FNPF_FP64_PC32 = 2
 FNPF_COARSE_LAUNCHES, FNPF_COARSE_CLUSTER = 0, 1
 FNPF_CHEB_FIRST, FNPF_CHEB_FOURTH = 1, 4
 FNPF_NONLINEAR, FNPF_LINEAR = 0, 1

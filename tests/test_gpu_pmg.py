@@ -207,3 +207,32 @@ def test_level_schedules_solve_and_stay_spd(fnpf, shape, schedule):
     a, b = float(torch.dot(z1, r2)), float(torch.dot(r1, z2))
     assert abs(a - b) < 1e-12 * float(torch.linalg.norm(z1) * torch.linalg.norm(r2))
     assert float(torch.dot(z1, r1)) > 0
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1], SHAPES[3], SHAPES[4], SHAPES[6]], ids=ids)
+def test_fp64_pcg_with_fp32_multigrid_matches_oracle(fnpf, shape):
+    """FNPF_FP64_PC32: FP64 PCG (FP64 operator, residuals, dots) with the
+    p-multigrid V-cycle in FP32 reaches the oracle's solution at rtol 1e-13."""
+    c = Case(fnpf, *shape, opts=pmg(fnpf, precision=fnpf.FNPF_FP64_PC32))
+    phi_ref = osolve.laplace_solve(c.om, c.eta, c.h, c.phis)
+    phi = torch.zeros(c.om.N, dtype=torch.float64, device=c.dev)
+    info = c.gm.laplace_solve(c.t(c.eta), c.t(c.phis), phi)
+    assert info["status"] == 0 and info["rel_res"] <= 1e-13
+    assert rel_l2(phi.cpu().numpy(), phi_ref) < 1e-10
+
+
+@pytest.mark.parametrize("model", ["fnpf", "lpf"])
+def test_fp64_pc32_rk4_steps_match_oracle(fnpf, model):
+    """Host-driven and graph-replayed RK4 steps with the FP32 preconditioner."""
+    lin = model == "lpf"
+    c = Case(fnpf, 3, 5, 3, 2, 5, True, False,
+             opts=pmg(fnpf, precision=fnpf.FNPF_FP64_PC32, model=fnpf.FNPF_LINEAR if lin else fnpf.FNPF_NONLINEAR))
+    dt = 0.01
+    eta_r, phi_r = c.eta.copy(), c.phis.copy()
+    eta, phis = c.t(c.eta), c.t(c.phis)
+    for n in range(4):
+        eta_r, phi_r = osurf.rk4_step(c.om, c.h, eta_r, phi_r, dt, 9.81, linear=lin)
+        c.gm.rk4_step(eta, phis, n * dt, dt)
+    torch.cuda.synchronize()
+    assert rel_l2(eta.cpu().numpy(), eta_r) < 1e-10
+    assert rel_l2(phis.cpu().numpy(), phi_r) < 1e-10
