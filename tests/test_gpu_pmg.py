@@ -107,7 +107,10 @@ def _precond(c, fnpf, r, **kw):
 
 
 @pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1], SHAPES[3], SHAPES[4], SHAPES[6], SHAPES[9],
-                                   (3, 32, 32, 2, 6, True, True)], ids=ids)
+                                   (3, 32, 32, 2, 6, True, True),
+                                   (3, 96, 72, 2, 2, True, True),      # 13,824 coarse rows: 2 per thread
+                                   (3, 60, 50, 3, 2, False, False)],   # 9,333 coarse rows, walls
+                         ids=ids)
 @pytest.mark.parametrize("coarse", [6, 31])
 def test_cluster_coarse_solve_matches_per_step_launches(fnpf, shape, coarse):
     """The coarsest level's Chebyshev sweep on one thread-block cluster (stencil
