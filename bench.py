@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "pc32"],
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
     ap.add_argument("--mode", default="step", choices=["step", "apply", "ensemble", "convergence"],
@@ -218,7 +218,7 @@ def main_gb300(args):
     d = workload(args.nx)
     h = None
     pre = fnpf.FNPF_PMG if args.precond == "pmg" else fnpf.FNPF_JACOBI
-    prec = fnpf.FNPF_MIXED if args.precision == "mixed" else fnpf.FNPF_FP64
+    prec = {"fp64": fnpf.FNPF_FP64, "mixed": fnpf.FNPF_MIXED, "pc32": fnpf.FNPF_FP64_PC32}[args.precision]
     cdeg = args.mixed_cheb_degree if args.precision == "mixed" else args.cheb_degree
     opts = fnpf.default_opts(rtol=args.rtol, max_iter=50000, precond=pre, cheb_degree=cdeg,
                              coarse_iters=args.coarse_degree, coarse_solver=coarse_mode(args),
@@ -436,8 +436,9 @@ def main_gb300(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dof": mesh.N, "surface_dof": mesh.ns, "precision": "fp64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dof": mesh.N, "surface_dof": mesh.ns, "precision": args.precision,
                        "precond": args.precond, "cheb_degree": cdeg, "coarse_degree": args.coarse_degree,
                        "coarse_solver": args.coarse_solver, "cheb_kind": args.cheb_kind,
                        "cheb_range": args.cheb_range, "model": args.model, "mg_schedule": args.mg_schedule,
