@@ -501,7 +501,8 @@ __global__ void ring_gather_kernel(Geom g, const T* __restrict__ ring, T* yI, T*
   else yI[(int64_t)plane * g.ns + col] = s;
 }
 
-// Gather fused with a vector update: one thread per interior unknown; the
+// Gather fused with a vector update: one thread per interior unknown (a 2D
+// grid of columns x interior planes, so no 64-bit index division); the
 // operator output w_i is read from yI on column-interior lines (written there
 // by the operator kernel) or summed from the ring buffer on element-boundary
 // lines (same owners and order as ring_gather_kernel), then the Epilogue
@@ -511,11 +512,11 @@ __global__ void __launch_bounds__(256) gather_update_kernel(Geom g, const T* __r
                                                             const T* __restrict__ yI, const int* skip,
                                                             Epilogue<T> ep) {
   if (skip && *skip) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.NI) return;
-  const int plane = (int)(i / g.ns);
-  const int col = (int)(i - (int64_t)plane * g.ns);
-  const int ix = col % g.ncx, iy = col / g.ncx;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (columns, interior planes)
+  if (col >= g.ns) return;
+  const int plane = blockIdx.y;
+  const int64_t i = (int64_t)plane * g.ns + col;
+  const int iy = col / g.ncx, ix = col - iy * g.ncx;
   const int p = g.p;
   T w;
   if (ix % p != 0 && (DIM == 2 || iy % p != 0)) {
@@ -557,8 +558,8 @@ template <typename T, int DIM>
 cudaError_t launch_gather_update(const Geom& g, const T* ring, const T* yI, const int* skip, const Epilogue<T>& ep,
                                  cudaStream_t s) {
   if (g.NI == 0) return cudaSuccess;
-  const int64_t blocks = (g.NI + 255) / 256;
-  gather_update_kernel<T, DIM><<<(unsigned)blocks, 256, 0, s>>>(g, ring, yI, skip, ep);
+  const dim3 grid((unsigned)((g.ns + 255) / 256), (unsigned)(g.nv - 1));
+  gather_update_kernel<T, DIM><<<grid, 256, 0, s>>>(g, ring, yI, skip, ep);
   return cudaGetLastError();
 }
 
