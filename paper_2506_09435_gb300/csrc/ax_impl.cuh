@@ -141,6 +141,20 @@ __global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
   ax_prologue<T, N, DIM, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, i, j, ecol, active, col, lg);
   const int slot = ring_slot(DIM, P, i, j);
   const T inv_nz = T(1) / T(g.nz);
+  // FP32: the D entries of this thread's r- and s-contractions are kept in
+  // registers, so that the field values are the only shared-memory operand
+  // there (the FP32 kernel is bound by shared-memory loads).  FP64 reads them
+  // from shared memory: that kernel is bound by the FP64 pipe, and its
+  // latency-bound coarse-level instances run better with fewer registers.
+  constexpr bool kDReg = sizeof(T) == 4;
+  T Di[N], Dj[N], DiT[N], DjT[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    Di[m] = sD[i * N + m];
+    Dj[m] = sD[j * N + m];
+    DiT[m] = sD[m * N + i];
+    DjT[m] = sD[m * N + j];
+  }
 
   T carry = 0;
   for (int l = 0; l < g.nz; ++l) {
@@ -168,10 +182,10 @@ __global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
       const T* uk = sU + (c * N + k) * L;
       T ur = 0, us = 0, ut = 0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) ur += sD[i * N + m] * uk[j * N + m];
+      for (int m = 0; m < N; ++m) ur += (kDReg ? Di[m] : sD[i * N + m]) * uk[j * N + m];
       if (DIM == 3) {
 #pragma unroll
-        for (int m = 0; m < N; ++m) us += sD[j * N + m] * uk[m * N + i];
+        for (int m = 0; m < N; ++m) us += (kDReg ? Dj[m] : sD[j * N + m]) * uk[m * N + i];
       }
 #pragma unroll
       for (int m = 0; m < N; ++m) ut += sD[k * N + m] * u[m];
@@ -195,10 +209,10 @@ __global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
       const T* sk = sS + (c * N + k) * L;
       T s = 0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) s += sD[m * N + i] * rk[j * N + m];
+      for (int m = 0; m < N; ++m) s += (kDReg ? DiT[m] : sD[m * N + i]) * rk[j * N + m];
       if (DIM == 3) {
 #pragma unroll
-        for (int m = 0; m < N; ++m) s += sD[m * N + j] * sk[m * N + i];
+        for (int m = 0; m < N; ++m) s += (kDReg ? DjT[m] : sD[m * N + j]) * sk[m * N + i];
       }
 #pragma unroll
       for (int m = 0; m < N; ++m) s += sD[m * N + k] * ft[m];
@@ -381,6 +395,15 @@ __global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
   const int64_t PT = (int64_t)g.nz * g.n_ecol * N * L;
   const T* G = a.G;
   __syncthreads();
+  constexpr bool kDReg = sizeof(T) == 4;   // as in ax_kernel
+  T Di[N], Dj[N], DiT[N], DjT[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    Di[m] = sD[i * N + m];
+    Dj[m] = sD[j * N + m];
+    DiT[m] = sD[m * N + i];
+    DjT[m] = sD[m * N + j];
+  }
   T carry = 0;
   for (int l = 0; l < g.nz; ++l) {
     T u[N];
@@ -408,10 +431,10 @@ __global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
       const T* uk = sU + (c * N + k) * L;
       T ur = 0, us = 0, ut = 0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) ur += sD[i * N + m] * uk[j * N + m];
+      for (int m = 0; m < N; ++m) ur += (kDReg ? Di[m] : sD[i * N + m]) * uk[j * N + m];
       if (DIM == 3) {
 #pragma unroll
-        for (int m = 0; m < N; ++m) us += sD[j * N + m] * uk[m * N + i];
+        for (int m = 0; m < N; ++m) us += (kDReg ? Dj[m] : sD[j * N + m]) * uk[m * N + i];
       }
 #pragma unroll
       for (int m = 0; m < N; ++m) ut += sD[k * N + m] * u[m];
@@ -436,10 +459,10 @@ __global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
       const T* sk = sS + (c * N + k) * L;
       T s = 0;
 #pragma unroll
-      for (int m = 0; m < N; ++m) s += sD[m * N + i] * rk[j * N + m];
+      for (int m = 0; m < N; ++m) s += (kDReg ? DiT[m] : sD[m * N + i]) * rk[j * N + m];
       if (DIM == 3) {
 #pragma unroll
-        for (int m = 0; m < N; ++m) s += sD[m * N + j] * sk[m * N + i];
+        for (int m = 0; m < N; ++m) s += (kDReg ? DjT[m] : sD[m * N + j]) * sk[m * N + i];
       }
 #pragma unroll
       for (int m = 0; m < N; ++m) s += sD[m * N + k] * ft[m];
