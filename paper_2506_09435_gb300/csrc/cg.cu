@@ -45,7 +45,7 @@ using vec::reduce_partials;
 // b = -y (y = A [0; phis]_I), r = b - q (q = A x), z = dinv r, p = z; partials bb, rz, rr.
 __global__ void __launch_bounds__(NT) cg_init_kernel(int64_t n, double* r, const double* q, const double* dinv,
                                                      double* z, double* p, double* b_out, double* part, int nb) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[vec::kShared];
   double sbb = 0, srz = 0, srr = 0;
   GRID_LOOP(i, n) {
     const double b = -r[i];
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(NT) cg_init_kernel(int64_t n, double* r, const
 // Sets bb, rz[0], rr, tol2 from the partials; done if already converged.
 __global__ void __launch_bounds__(NT) cg_init_finish_kernel(CgScalars* sc, const double* part, int nb, double rtol2,
                                                             double atol2) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[vec::kShared];
   const double bb = reduce_partials(part, nb, sh);
   const double rz = reduce_partials(part + nb, nb, sh);
   const double rr = reduce_partials(part + 2 * nb, nb, sh);
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(NT) cg_init_finish_kernel(CgScalars* sc, const
 // p = z; partials rz, rr (FP64).
 __global__ void __launch_bounds__(NT) inner_init_kernel(int64_t n, const double* r64, float* r, float* e, float* z,
                                                         float* p, const float* dinv, double* part, int nb) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[vec::kShared];
   double srz = 0, srr = 0;
   GRID_LOOP(i, n) {
     const float rn = (float)r64[i];
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(NT) inner_init_kernel(int64_t n, const double*
 
 __global__ void __launch_bounds__(NT) inner_init_finish_kernel(CgScalars* sc, const double* part, int nb,
                                                                double rtol2) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[vec::kShared];
   const double rz = reduce_partials(part + nb, nb, sh);
   const double rr = reduce_partials(part + 2 * nb, nb, sh);
   if (threadIdx.x == 0) {
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NT) add_correction_kernel(int64_t n, double* x
 
 __global__ void __launch_bounds__(NT) outer_residual_kernel(int64_t n, const double* b, const double* q, double* r,
                                                             double* part, int nb) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[vec::kShared];
   double srr = 0;
   GRID_LOOP(i, n) {
     const double rn = b[i] - q[i];
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(NT) outer_residual_kernel(int64_t n, const dou
 }
 
 __global__ void __launch_bounds__(NT) outer_finish_kernel(CgScalars* sc, const double* part, int nb) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[vec::kShared];
   const double rr = reduce_partials(part + 2 * nb, nb, sh);
   if (threadIdx.x == 0) {
     sc->rr = rr;
@@ -354,13 +354,13 @@ cudaError_t enqueue_iteration(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>
   const int* skip = &B.sc->done;
   cudaError_t e = timed_apply<T>(m, t, B.eta, B.p, nullptr, B.q, s, skip, it);
   if (e != cudaSuccess) return e;
-  vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.p, B.q, m->partials + 3 * nb);
+  vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.p, B.q, m->partials + 3 * nb, B.sc, 3);
   vec::update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, pmg ? nullptr : B.dinv,
                                           m->partials, nb, nullptr);
   if (pmg) {
     e = apply_precond<T>(m, t, B.eta, B.r, B.z, skip, s);
     if (e != cudaSuccess) return e;
-    vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.r, B.z, m->partials + 1 * nb);
+    vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.r, B.z, m->partials + 1 * nb, B.sc, 1);
     m->launches += 1;
   }
   vec::pupdate_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.z, B.p, m->partials, nb, nullptr);

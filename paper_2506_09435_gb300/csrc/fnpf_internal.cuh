@@ -56,6 +56,11 @@ struct CgScalars {
   int iters;
   int status;
   int outer;     // defect-correction steps of a mixed-precision solve
+  // reduced sums of the partial slots 0..3 (written by the last block of the
+  // kernel producing the partials) and that kernel's block tickets, which the
+  // last block returns to zero
+  double red[4];
+  unsigned int ticket[4];
 };
 
 // Per-stage summary of a solve run inside a captured RK4-step graph.

@@ -99,7 +99,7 @@ __global__ void random_kernel(int64_t n, T* r) {
 template <typename T>
 __global__ void __launch_bounds__(vec::NT) lz_init_kernel(int64_t n, const T* r, const T* dinv, T* x, T* z, T* p,
                                                           double* part, int nb) {
-  __shared__ double sh[vec::NT / 32];
+  __shared__ double sh[vec::kShared];
   double srz = 0, srr = 0;
   FNPF_GRID_LOOP(i, n) {
     const T zz = dinv[i] * r[i];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(vec::NT) lz_init_kernel(int64_t n, const T* r,
 }
 
 __global__ void __launch_bounds__(vec::NT) lz_init_finish_kernel(CgScalars* sc, const double* part, int nb) {
-  __shared__ double sh[vec::NT / 32];
+  __shared__ double sh[vec::kShared];
   const double rz = vec::reduce_partials(part + nb, nb, sh);
   const double rr = vec::reduce_partials(part + 2 * nb, nb, sh);
   if (threadIdx.x == 0) {
@@ -711,6 +711,7 @@ Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<d
   alloc((void**)&mg->sc, mg->L * sizeof(CgScalars));
   alloc((void**)&mg->part, 4 * kVecBlocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(mg->cheb64, 0, mg->L * sizeof(ChebParams));
+  if (e == cudaSuccess) e = cudaMemset(mg->sc, 0, mg->L * sizeof(CgScalars));   // reduction tickets start at 0
   if (e == cudaSuccess) e = cudaMemset(mg->cheb32, 0, mg->L * sizeof(ChebParams));
   if (e != cudaSuccess) {
     *err = std::string("multigrid set-up failed: ") + cudaGetErrorString(e);
@@ -857,7 +858,7 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
     lz_init_finish_kernel<<<1, vec::NT, 0, s>>>(sc, mg->part, nb);
     for (int it = 0; it < kLanczos; ++it) {
       if ((e = level_apply<T>(g, t, eta, Gl, L.P, L.W, ring, lv, &sc->done, s)) != cudaSuccess) return e;
-      vec::dot_kernel<T><<<nb, vec::NT, 0, s>>>(&sc->done, g.NI, L.P, L.W, mg->part + 3 * nb);
+      vec::dot_kernel<T><<<nb, vec::NT, 0, s>>>(&sc->done, g.NI, L.P, L.W, mg->part + 3 * nb, sc, 3);
       vec::update_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.X, L.R, L.Dd, L.P, L.W, L.dinv, mg->part, nb,
                                                    hist);
       vec::pupdate_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.Dd, L.P, mg->part, nb, hist);

@@ -1,7 +1,7 @@
 // Vector kernels shared by the CG solves and the Lanczos eigenvalue estimates of
 // the p-multigrid smoothers.  Reductions are deterministic: each block writes
-// one FP64 partial; consumers re-reduce all partials in a fixed order, so every
-// block obtains the same bits.
+// one FP64 partial and the last block of the kernel reduces all partials in a
+// fixed order (finish_partials), whatever the order the blocks finish in.
 #pragma once
 
 #include <math.h>
@@ -16,21 +16,53 @@ constexpr int NT = kVecThreads;
 #define FNPF_GRID_LOOP(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)vec::NT + threadIdx.x; i < (n); i += (int64_t)gridDim.x * vec::NT)
 
+constexpr int kShared = NT / 32 + 1;   // doubles of shared memory block_sum needs
+
+// Sum over the block, returned to every thread: warp butterflies, then one
+// thread adds the warp sums in a fixed order and broadcasts (each FP64 add of
+// a full warp occupies the FP64 pipe for many cycles on this GPU, so the last
+// stage is not repeated by every thread).
 __device__ inline double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) sh[wid] = v;
   __syncthreads();
-  double s = 0;
-  for (int k = 0; k < NT / 32; ++k) s += sh[k];
-  return s;
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < NT / 32; ++k) s += sh[k];
+    sh[NT / 32] = s;
+  }
+  __syncthreads();
+  return sh[NT / 32];
 }
 
 __device__ inline double reduce_partials(const double* part, int nb, double* sh) {
   double v = 0;
-  for (int k = threadIdx.x; k < nb; k += NT) v += part[k];
+  for (int k = threadIdx.x; k < nb; k += NT) v += __ldcg(part + k);
   return block_sum(v, sh);
+}
+
+// Called by every block after thread 0 has written the block's partials of the
+// given slots: the last block to finish reduces each slot's partials (in the
+// same fixed order as reduce_partials) into sc->red[slot] and resets the
+// ticket, so consumers read one scalar instead of re-reducing.
+__device__ inline void finish_partials(CgScalars* sc, const double* part, int nb, int slot0, int nslots,
+                                       double* sh) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&sc->ticket[slot0], 1u);
+    last = t == (unsigned)gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int k = 0; k < nslots; ++k) {
+    const double v = reduce_partials(part + (slot0 + k) * nb, nb, sh);
+    if (threadIdx.x == 0) sc->red[slot0 + k] = v;
+  }
+  if (threadIdx.x == 0) sc->ticket[slot0] = 0u;
 }
 
 inline int blocks_for(int64_t n) {
@@ -51,15 +83,18 @@ __global__ void __launch_bounds__(NT) copy_kernel(int64_t n, const T* a, T* b, c
   FNPF_GRID_LOOP(i, n) b[i] = a[i];
 }
 
-// part[blockIdx] = sum p q (FP64 accumulation)
+// part[blockIdx] = sum p q (FP64 accumulation); with sc, the last block also
+// writes the total to sc->red[slot] (part must then be the slot's array).
 template <typename T>
-__global__ void __launch_bounds__(NT) dot_kernel(const int* skip, int64_t n, const T* p, const T* q, double* part) {
+__global__ void __launch_bounds__(NT) dot_kernel(const int* skip, int64_t n, const T* p, const T* q, double* part,
+                                                 CgScalars* sc = nullptr, int slot = 0) {
   if (skip && *skip) return;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[kShared];
   double s = 0;
   FNPF_GRID_LOOP(i, n) s += (double)p[i] * (double)q[i];
   s = block_sum(s, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
+  if (sc) finish_partials(sc, part - slot * gridDim.x, gridDim.x, slot, 1, sh);
 }
 
 // alpha = rz / pq; x += alpha p; r -= alpha q; with dinv: z = dinv r and
@@ -69,9 +104,9 @@ template <typename T>
 __global__ void __launch_bounds__(NT) update_kernel(CgScalars* sc, int it, int64_t n, T* x, T* r, T* z, const T* p,
                                                     const T* q, const T* dinv, double* part, int nb, double* hist) {
   if (sc->done) return;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[kShared];
   __shared__ double s_alpha;
-  const double pq = reduce_partials(part + 3 * nb, nb, sh);
+  const double pq = sc->red[3];   // reduced by the dot kernel's last block
   if (!(pq > 0.0) || !isfinite(pq)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       sc->status = FNPF_EBREAKDOWN;
@@ -104,6 +139,8 @@ __global__ void __launch_bounds__(NT) update_kernel(CgScalars* sc, int it, int64
     if (dinv) part[1 * nb + blockIdx.x] = srz;
     part[2 * nb + blockIdx.x] = srr;
   }
+  if (dinv) finish_partials(sc, part, nb, 1, 2, sh);
+  else finish_partials(sc, part, nb, 2, 1, sh);
 }
 
 // beta = rz_new / rz; p = z + beta p; block 0 advances the scalars and tests
@@ -113,11 +150,12 @@ __global__ void __launch_bounds__(NT) update_kernel(CgScalars* sc, int it, int64
 template <typename T>
 __global__ void __launch_bounds__(NT) pupdate_kernel(CgScalars* sc, int it, int64_t n, const T* z, T* p,
                                                      const double* part, int nb, double* hist) {
+  (void)part;
+  (void)nb;
   if (sc->done) return;
-  __shared__ double sh[NT / 32];
   __shared__ double s_beta;
-  const double rz_new = reduce_partials(part + nb, nb, sh);
-  const double rr = reduce_partials(part + 2 * nb, nb, sh);
+  const double rz_new = sc->red[1];   // reduced by the previous kernels' last blocks
+  const double rr = sc->red[2];
   if (threadIdx.x == 0) s_beta = rz_new / sc->rz[it & 1];
   __syncthreads();
   const double beta_d = s_beta;
