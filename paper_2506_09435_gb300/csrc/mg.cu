@@ -21,6 +21,8 @@
 // safety factor, so the set-up needs no host synchronisation.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -253,8 +255,9 @@ __global__ void __launch_bounds__(vec::NT) cheb_start_kernel(int64_t n, const T*
 // assembles it from the level's stored metric G (the same quadrature as the
 // matrix-free operator: y = sum_e Dhat^T G Dhat x at the element's GLL points);
 // coarse_cheb_kernel then runs the whole Chebyshev sweep on it inside one
-// thread-block cluster, with a hardware cluster barrier between steps instead
-// of one operator, gather and update launch per step.
+// thread-block cluster, exchanging directions through distributed shared
+// memory with a hardware cluster barrier between steps, instead of one
+// operator, gather and update launch per step.
 
 template <int DIM>
 struct Stencil {
@@ -340,18 +343,22 @@ __device__ __forceinline__ int nbr_index(int i, int o, int n, int periodic) {
   return a;
 }
 
-// (A_II d)_row from the stencil; d is read through L2 only (other CTAs of the
-// cluster wrote it before the last cluster barrier).
+// (A_II d)_row from the stencil.  The direction d lives in the shared memory
+// of the cluster's CTAs: rank c holds rows [c R, (c + 1) R) (R a power of two)
+// in the buffer `cur` of its shared memory, read here through distributed
+// shared memory.
 template <typename T, int DIM>
-__device__ __forceinline__ T stencil_row(const Geom& g, const T* __restrict__ coef, const T* d, int64_t row) {
-  const int k = (int)(row / g.ns), col = (int)(row - (int64_t)k * g.ns);
-  const int ix = col % g.ncx, iy = col / g.ncx;
+__device__ __forceinline__ T stencil_row(const Geom& g, const T* __restrict__ coef,
+                                         cooperative_groups::cluster_group& cl, T* cur, int log_r, int row) {
+  const int k = row / g.ns, col = row - k * g.ns;
+  const int iy = col / g.ncx, ix = col - iy * g.ncx;
   int xs[3], ys[3] = {-1, 0, -1};
 #pragma unroll
   for (int o = -1; o <= 1; ++o) {
     xs[o + 1] = nbr_index(ix, o, g.ncx, g.px);
     if (DIM == 3) ys[o + 1] = nbr_index(iy, o, g.ncy, g.py);
   }
+  const int rmask = (1 << log_r) - 1;
   T w = T(0);
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz) {
@@ -367,65 +374,68 @@ __device__ __forceinline__ T stencil_row(const Geom& g, const T* __restrict__ co
         const int xx = xs[dx + 1];
         if (xx < 0) continue;
         const T cv = coef[(int64_t)Stencil<DIM>::slot(dx, dy, dz) * g.NI + row];
-        w += cv * __ldcg(d + (int64_t)kk * g.ns + (int64_t)yy * g.ncx + xx);
+        const int nr = kk * g.ns + yy * g.ncx + xx;
+        const T* owner = cl.map_shared_rank(cur, (unsigned)(nr >> log_r));
+        w += cv * owner[nr & rmask];
       }
     }
   }
   return w;
 }
 
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // The coarsest level's Chebyshev sweep from x = 0 (the recurrence of
-// cheb_sweep: cheb_start_kernel, then EP_CHEB gather-updates) in one
-// launch of one cluster.  Each
-// thread keeps its rows' r, x and direction in registers; directions are
-// exchanged through the double buffer dbuf [2][NI] in global memory, one
-// cluster barrier per step.  Uniform control flow: every thread reaches every
-// barrier.
+// cheb_sweep: cheb_start_kernel, then EP_CHEB gather-updates) in one launch of
+// one cluster.  CTA rank c owns rows [c R, (c + 1) R); each thread keeps its
+// rows' r, x and direction in registers and publishes the direction in its
+// CTA's shared memory (double buffer [2][R]), which the other CTAs read through
+// distributed shared memory after the step's cluster barrier.  A last barrier
+// keeps every CTA resident until no other CTA can read its shared memory.
+// Uniform control flow: every thread reaches every barrier.
 template <typename T, int DIM>
 __global__ void __cluster_dims__(kCoarseCluster, 1, 1) __launch_bounds__(kCoarseThreads)
     coarse_cheb_kernel(Geom g, const T* __restrict__ coef, const T* __restrict__ dinv, const T* __restrict__ b,
-                       T* x, T* dbuf, const ChebParams* cp, int degree, const int* skip) {
+                       T* x, int log_r, const ChebParams* cp, int degree, const int* skip) {
   if (skip && *skip) return;   // the same value for every CTA of the cluster
-  const int64_t n = g.NI;
-  const int nthr = kCoarseCluster * blockDim.x;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ __align__(16) unsigned char coarse_smem[];
+  T* sdir = reinterpret_cast<T*>(coarse_smem);
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  const int R = 1 << log_r;
+  const int n = (int)g.NI;
+  const int row0 = (int)cl.block_rank() * R;
   T r[kCoarseRows], xv[kCoarseRows], dv[kCoarseRows];
   const T it = (T)cp->inv_theta;
 #pragma unroll
   for (int m = 0; m < kCoarseRows; ++m) {
-    const int64_t row = tid + (int64_t)m * nthr;
+    const int lr = threadIdx.x + m * blockDim.x, row = row0 + lr;
     r[m] = xv[m] = dv[m] = T(0);
-    if (row < n) {
+    if (lr < R && row < n) {
       r[m] = b[row];
       dv[m] = it * dinv[row] * r[m];
       xv[m] = dv[m];
-      dbuf[row] = dv[m];
+      sdir[lr] = dv[m];
     }
   }
   for (int k = 1; k < degree; ++k) {
-    cluster_barrier();
-    const T* dc = dbuf + (int64_t)((k - 1) & 1) * n;
-    T* dn = dbuf + (int64_t)(k & 1) * n;
+    cl.sync();
+    T* cur = sdir + ((k - 1) & 1) * R;
+    T* nxt = sdir + (k & 1) * R;
     const T c1 = (T)cp->c1[k], c2 = (T)cp->c2[k];
 #pragma unroll
     for (int m = 0; m < kCoarseRows; ++m) {
-      const int64_t row = tid + (int64_t)m * nthr;
-      if (row < n) {
-        r[m] -= stencil_row<T, DIM>(g, coef, dc, row);
+      const int lr = threadIdx.x + m * blockDim.x, row = row0 + lr;
+      if (lr < R && row < n) {
+        r[m] -= stencil_row<T, DIM>(g, coef, cl, cur, log_r, row);
         dv[m] = c1 * dv[m] + c2 * dinv[row] * r[m];
         xv[m] += dv[m];
-        dn[row] = dv[m];
+        nxt[lr] = dv[m];
       }
     }
   }
+  cl.sync();
 #pragma unroll
   for (int m = 0; m < kCoarseRows; ++m) {
-    const int64_t row = tid + (int64_t)m * nthr;
-    if (row < n) x[row] = xv[m];
+    const int lr = threadIdx.x + m * blockDim.x, row = row0 + lr;
+    if (lr < R && row < n) x[row] = xv[m];
   }
 }
 
@@ -437,27 +447,49 @@ cudaError_t launch_stencil(const Geom& g, const T* D, const T* G, T* coef, cudaS
   return cudaGetLastError();
 }
 
-// CTAs only as large as the level needs (one row per thread up to
-// kCoarseThreads threads, then up to kCoarseRows rows per thread), so that
-// small coarse levels, e.g. of the tanks of an ensemble running side by side,
-// leave the rest of their SMs to other kernels.
+// Rows per CTA: the power of two R >= NI / kCoarseCluster; CTAs only as large
+// as that needs (one row per thread up to kCoarseThreads threads, then up to
+// kCoarseRows rows per thread), so that small coarse levels, e.g. of the tanks
+// of an ensemble running side by side, leave the rest of their SMs to other
+// kernels.  Shared memory: 2 R values per CTA.
+int coarse_log_rows(int64_t NI) {
+  int log_r = 0;
+  while (((int64_t)kCoarseCluster << log_r) < NI) ++log_r;
+  return log_r;
+}
+
 template <typename T>
-cudaError_t launch_coarse_cheb(const Geom& g, const T* coef, const T* dinv, const T* b, T* x, T* dbuf,
-                               const ChebParams* cp, int degree, const int* skip, cudaStream_t s) {
-  const int64_t per_cta = (g.NI + kCoarseCluster - 1) / kCoarseCluster;
-  const int threads = (int)std::min<int64_t>(kCoarseThreads, std::max<int64_t>(32, (per_cta + 31) / 32 * 32));
+cudaError_t launch_coarse_cheb(const Geom& g, const T* coef, const T* dinv, const T* b, T* x, const ChebParams* cp,
+                               int degree, const int* skip, cudaStream_t s) {
+  const int log_r = coarse_log_rows(g.NI);
+  const int R = 1 << log_r;
+  const int threads = std::min(kCoarseThreads, std::max(32, (R + 31) / 32 * 32));
+  const size_t smem = 2 * (size_t)R * sizeof(T);
   if (g.dim == 3)
-    coarse_cheb_kernel<T, 3><<<kCoarseCluster, threads, 0, s>>>(g, coef, dinv, b, x, dbuf, cp, degree, skip);
+    coarse_cheb_kernel<T, 3><<<kCoarseCluster, threads, smem, s>>>(g, coef, dinv, b, x, log_r, cp, degree, skip);
   else
-    coarse_cheb_kernel<T, 2><<<kCoarseCluster, threads, 0, s>>>(g, coef, dinv, b, x, dbuf, cp, degree, skip);
+    coarse_cheb_kernel<T, 2><<<kCoarseCluster, threads, smem, s>>>(g, coef, dinv, b, x, log_r, cp, degree, skip);
   return cudaGetLastError();
 }
 
-// Whether one cluster of the coarse kernel can be resident on this device.
+// Whether one cluster of the coarse kernel, with its largest shared-memory
+// footprint, can be resident on this device (also raises the kernels'
+// dynamic shared-memory limit, once per process).
 bool cluster_launch_ok() {
+  constexpr int kMaxSmem = 2 * (kCoarseMaxRows / kCoarseCluster) * (int)sizeof(double);
+  static bool attrs = false;
+  if (!attrs) {
+    cudaFuncSetAttribute(coarse_cheb_kernel<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(coarse_cheb_kernel<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(coarse_cheb_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(coarse_cheb_kernel<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (cudaGetLastError() != cudaSuccess) return false;
+    attrs = true;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kCoarseCluster);
   cfg.blockDim = dim3(kCoarseThreads);
+  cfg.dynamicSmemBytes = kMaxSmem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = kCoarseCluster;
@@ -700,9 +732,7 @@ Mg* mg_create(const Geom& g0, const std::vector<double>& h0, const std::vector<d
     MgLevelBufs<float>& F = mg->b32[mg->L - 1];
     const int nsl = gc.dim == 3 ? Stencil<3>::slots : Stencil<2>::slots;
     alloc((void**)&B.coef, (size_t)nsl * gc.NI * sizeof(double));
-    alloc((void**)&B.dbuf, (size_t)2 * gc.NI * sizeof(double));
     alloc((void**)&F.coef, (size_t)nsl * gc.NI * sizeof(float));
-    alloc((void**)&F.dbuf, (size_t)2 * gc.NI * sizeof(float));
     alloc((void**)&F.G, (size_t)(gc.dim == 3 ? 6 : 3) * geom_points(gc) * sizeof(float));
   }
   alloc((void**)&mg->cheb64, mg->L * sizeof(ChebParams));
@@ -802,8 +832,7 @@ cudaError_t vcycle(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const T* G
     if (mg->fused()) {
       MgLevelBufs<T>& C = mg->bufs<T>()[l];
       *nl += 1;
-      return launch_coarse_cheb<T>(mg->g[l], C.coef, C.dinv, b, x, C.dbuf, mg->cheb<T>() + l, coarse_degree, skip,
-                                   s);
+      return launch_coarse_cheb<T>(mg->g[l], C.coef, C.dinv, b, x, mg->cheb<T>() + l, coarse_degree, skip, s);
     }
     return cheb_sweep<T>(mg, l, t0, eta0, G0, b, x, coarse_degree, true, false, ring, variant, skip, s, nl);
   }

@@ -37,7 +37,6 @@ struct MgLevelBufs {
   T* G = nullptr;         // stored metric of this level (FP64 solves, levels >= 1; the
                           // coarsest level in both precisions when it is solved by the cluster kernel)
   T* coef = nullptr;      // coarsest level: assembled 27-point (9 in 2D) stencil, [slot][NI]
-  T* dbuf = nullptr;      // coarsest level: two Chebyshev direction buffers [2][NI]
   const T* J = nullptr;   // [n_{l-1} x n_l] prolongation from this level to level l-1 (levels >= 1)
   const T* Js = nullptr;  // [n_l x n_0] surface interpolation from level 0 (levels >= 1)
 };
