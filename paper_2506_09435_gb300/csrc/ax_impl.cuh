@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
 
 // Sums the ring contributions of every element-boundary node column, in a
 // fixed order (x owners outer, y owners inner), and writes the output field.
-template <typename T, int DIM>
+template <typename T, int N, int DIM>
 __global__ void ring_gather_kernel(Geom g, const T* __restrict__ ring, T* yI, T* ys, int nplanes,
                                    int64_t nring_cols, const int* skip) {
   if (skip && *skip) return;
@@ -488,7 +488,7 @@ __global__ void ring_gather_kernel(Geom g, const T* __restrict__ ring, T* yI, T*
   if (idx >= nring_cols * nplanes) return;
   const int plane = (int)(idx / nring_cols);
   const int64_t rc = idx - (int64_t)plane * nring_cols;
-  const int p = g.p;
+  constexpr int p = N - 1;   // the order as a constant: divisions by p fold
   const int nlx = g.nx + (g.px ? 0 : 1);
   int ix, iy;
   if (DIM == 2) {
@@ -500,11 +500,14 @@ __global__ void ring_gather_kernel(Geom g, const T* __restrict__ ring, T* yI, T*
       ix = (int)(rc % nlx) * p;
       iy = (int)(rc / nlx);
     } else {
+      // element-interior x positions on the y-boundary lines (none at p = 1,
+      // where this branch is never taken; pm1 keeps the divisor non-zero)
+      constexpr int pm1 = p > 1 ? p - 1 : 1;
       const int64_t m = rc - part1;
-      const int per = g.nx * (p - 1);
+      const int per = g.nx * pm1;
       const int ly = (int)(m / per);
       const int mm = (int)(m - (int64_t)ly * per);
-      ix = (mm / (p - 1)) * p + 1 + mm % (p - 1);
+      ix = (mm / pm1) * p + 1 + mm % pm1;
       iy = ly * p;
     }
   }
@@ -530,7 +533,7 @@ __global__ void ring_gather_kernel(Geom g, const T* __restrict__ ring, T* yI, T*
 // by the operator kernel) or summed from the ring buffer on element-boundary
 // lines (same owners and order as ring_gather_kernel), then the Epilogue
 // update is applied; yI itself is left as the operator kernel wrote it.
-template <typename T, int DIM>
+template <typename T, int N, int DIM>
 __global__ void __launch_bounds__(256) gather_update_kernel(Geom g, const T* __restrict__ ring,
                                                             const T* __restrict__ yI, const int* skip,
                                                             Epilogue<T> ep) {
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(256) gather_update_kernel(Geom g, const T* __r
   const int plane = blockIdx.y;
   const int64_t i = (int64_t)plane * g.ns + col;
   const int iy = col / g.ncx, ix = col - iy * g.ncx;
-  const int p = g.p;
+  constexpr int p = N - 1;
   T w;
   if (ix % p != 0 && (DIM == 2 || iy % p != 0)) {
     w = yI[i];
@@ -565,7 +568,7 @@ inline int64_t ring_columns(const Geom& g) {
   return (int64_t)nlx * g.ncy + (int64_t)nly * g.nx * (g.p - 1);
 }
 
-template <typename T, int DIM>
+template <typename T, int N, int DIM>
 cudaError_t launch_gather(const Geom& g, const T* ring, T* yI, T* ys, const int* skip, cudaStream_t s) {
   const int nplanes = ys ? g.nv : g.nv - 1;
   const int64_t nrc = ring_columns(g);
@@ -573,16 +576,16 @@ cudaError_t launch_gather(const Geom& g, const T* ring, T* yI, T* ys, const int*
   if (total == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (total + threads - 1) / threads;
-  ring_gather_kernel<T, DIM><<<(unsigned)blocks, threads, 0, s>>>(g, ring, yI, ys, nplanes, nrc, skip);
+  ring_gather_kernel<T, N, DIM><<<(unsigned)blocks, threads, 0, s>>>(g, ring, yI, ys, nplanes, nrc, skip);
   return cudaGetLastError();
 }
 
-template <typename T, int DIM>
+template <typename T, int N, int DIM>
 cudaError_t launch_gather_update(const Geom& g, const T* ring, const T* yI, const int* skip, const Epilogue<T>& ep,
                                  cudaStream_t s) {
   if (g.NI == 0) return cudaSuccess;
   const dim3 grid((unsigned)((g.ns + 255) / 256), (unsigned)(g.nv - 1));
-  gather_update_kernel<T, DIM><<<grid, 256, 0, s>>>(g, ring, yI, skip, ep);
+  gather_update_kernel<T, N, DIM><<<grid, 256, 0, s>>>(g, ring, yI, skip, ep);
   return cudaGetLastError();
 }
 
@@ -621,8 +624,8 @@ cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.ep.op != EP_NONE) return launch_gather_update<T, DIM>(g, a.ring, a.yI, a.skip, a.ep, s);
-  return launch_gather<T, DIM>(g, a.ring, a.yI, a.ys, a.skip, s);
+  if (a.ep.op != EP_NONE) return launch_gather_update<T, N, DIM>(g, a.ring, a.yI, a.skip, a.ep, s);
+  return launch_gather<T, N, DIM>(g, a.ring, a.yI, a.ys, a.skip, s);
 }
 
 // Elements-per-CTA candidates for order N (3D); 2D uses one shape.  The

@@ -211,8 +211,8 @@ cudaError_t launch_transfer_t(const Geom& gf, const Geom& gc, const T* J, const 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || prolong) return e;
-  if (gc.dim == 3) return launch_gather<T, 3>(gc, ring, out, nullptr, skip, s);
-  return launch_gather<T, 2>(gc, ring, out, nullptr, skip, s);
+  if (gc.dim == 3) return launch_gather<T, NC, 3>(gc, ring, out, nullptr, skip, s);
+  return launch_gather<T, NC, 2>(gc, ring, out, nullptr, skip, s);
 }
 
 }  // namespace fnpf
