@@ -64,11 +64,13 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "pc32"],
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "ensemble", "convergence"],
+    ap.add_argument("--mode", default="step", choices=["step", "apply", "ensemble", "convergence", "bar"],
                     help="step: RK4 steps (the benchmark); apply: operator applications only; "
                          "ensemble: 64 seeded tanks in one launch per step vs one tank at a time; "
-                         "convergence: error of a stream-function wave after one period vs p and h")
+                         "convergence: error of a stream-function wave after one period vs p and h; "
+                         "bar: the submerged-bar flume in FP64 and both mixed-precision forms")
     ap.add_argument("--tanks", type=int, default=64)
+    ap.add_argument("--bar-steps", type=int, default=150, help="RK4 steps of the bar-flume accuracy run")
     ap.add_argument("--p", type=int, default=6)
     ap.add_argument("--nz", type=int, default=2)
     return ap.parse_args()
@@ -640,10 +642,84 @@ def main_convergence(args):
     return 0
 
 
+def main_bar(args):
+    """The submerged-bar flume (256 x 16 x 3 elements, p = 5, 1,660,176 DOF,
+    walls, variable depth; incident T = 2.02 s, H = 0.02 m through a
+    generation zone, absorption zone at the outlet), run from rest for
+    `--bar-steps` RK4 steps of dt = T/100 in FP64, in the defect-correction
+    mixed form and in FP64 PCG with the FP32 p-multigrid preconditioner.
+    Throughput from `--steps` timed steps after `--warmup`; accuracy of each
+    mixed form against the FP64 run at 8 probes spread over x = 8 ... 30 m at
+    y = 0.5 m (the nearest surface node)."""
+    import numpy as np
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    from paper_2506_09435_gb300 import workloads as W
+
+    d = W.bar_flume()
+    dims = (3, d["nx"], d["ny"], d["nz"], d["p"], False, False)
+    ncx = d["p"] * d["nx"] + 1
+    ncy = d["p"] * d["ny"] + 1
+    probe = fnpf.Mesh(*dims, np.full(ncx * ncy, d["h0"]), Lx=d["Lx"], Ly=d["Ly"], g=d["g"])
+    x, y = probe.surface_coords()
+    del probe
+    h = W.bar_depth(x)
+    cr, gen = W.flume_zones(d, x)
+    wave = W.flume_wave(d)
+    px = np.linspace(8.0, 30.0, 8)
+    pcols = [int(np.argmin((x - xp) ** 2 + (y - 0.5) ** 2)) for xp in px]
+    dt = d["T"] / 100
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    rows, ref = [], None
+    for name, prec in (("fp64", fnpf.FNPF_FP64), ("mixed", fnpf.FNPF_MIXED), ("pc32", fnpf.FNPF_FP64_PC32)):
+        opts = fnpf.default_opts(precision=prec, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=1e-5,
+                                 max_iter=50000, cheb_degree=args.cheb_degree, coarse_iters=args.coarse_degree)
+        gm = fnpf.Mesh(*dims, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"], opts=opts)
+        gm.set_relaxation(cr, gen, **wave)
+        eta = torch.zeros(gm.ns, dtype=torch.float64, device=dev)
+        phis = torch.zeros_like(eta)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        iters = []
+        for n in range(max(args.bar_steps, args.warmup + args.steps)):
+            k = n - args.warmup
+            timed = 0 <= k < args.steps
+            if timed:
+                flush.zero_()
+                ev[k][0].record(stream)
+            inf = gm.rk4_step(eta, phis, n * dt, dt, info=timed)
+            if timed:
+                ev[k][1].record(stream)
+                iters += [i["iters"] for i in inf]
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        e = eta.cpu().numpy()
+        row = {"precision": name, "value": gm.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+               "cg_iters_per_solve_mean": statistics.mean(iters)}
+        if ref is None:
+            ref = e
+            row["probe_eta_max"] = float(np.max(np.abs(e[pcols])))
+        else:
+            row["probe_rel_err_vs_fp64"] = float(np.max(np.abs(e[pcols] - ref[pcols])) / np.max(np.abs(ref[pcols])))
+            row["field_rel_l2_vs_fp64"] = float(np.linalg.norm(e - ref) / np.linalg.norm(ref))
+        rows.append(row)
+        del gm
+    print(json.dumps({"mode": "bar", "workload": "submerged-bar flume 256x16x3, p=5, walls, relaxation zones",
+                      "dof": ncx * ncy * (d["p"] * d["nz"] + 1),
+                      "steps_run": max(args.bar_steps, args.warmup + args.steps), "dt": dt, "probes_x": px.tolist(),
+                      "rows": rows, "data": "synthetic"}))
+    return 0
+
+
 def main():
     args = parse()
     if args.mode == "convergence":
         return main_convergence(args)
+    if args.mode == "bar":
+        return main_bar(args)
     if args.mode == "ensemble":
         return main_ensemble(args)
     if args.impl == "reference":
