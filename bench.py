@@ -64,11 +64,13 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "pc32"],
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
-    ap.add_argument("--mode", default="step", choices=["step", "apply", "ensemble", "convergence", "bar"],
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "apply", "ensemble", "convergence", "bar", "cylinder"],
                     help="step: RK4 steps (the benchmark); apply: operator applications only; "
                          "ensemble: 64 seeded tanks in one launch per step vs one tank at a time; "
                          "convergence: error of a stream-function wave after one period vs p and h; "
-                         "bar: the submerged-bar flume in FP64 and both mixed-precision forms")
+                         "bar: the submerged-bar flume in FP64 and both mixed-precision forms; "
+                         "cylinder: adjoint cost on the O-grid around a cylinder")
     ap.add_argument("--tanks", type=int, default=64)
     ap.add_argument("--bar-steps", type=int, default=150, help="RK4 steps of the bar-flume accuracy run")
     ap.add_argument("--p", type=int, default=6)
@@ -714,12 +716,95 @@ def main_bar(args):
     return 0
 
 
+def main_cylinder(args):
+    """Adjoint form on the cylinder O-grid (64 azimuthal x 24 radial x 3
+    elements, p = 4, isoparametric, 322,816 DOF; ka = kh = 1, outer radius 10a
+    with a sponge ring over 0.8 R .. R; linear incident wave of steepness
+    0.01, dt = T/64), FP64 p-multigrid: the forward RK4 step, the hand-written
+    adjoint step, and a checkpointed gradient (checkpoints every 16 steps)
+    through the torch.autograd.Function of 2 x 16 steps."""
+    import numpy as np
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    from paper_2506_09435_gb300 import workloads as W
+    from paper_2506_09435_gb300.autograd import rk4_run
+
+    d = W.cylinder_case()
+    dims = (3, d["nx"], d["ny"], d["nz"], d["p"], True, False)
+    ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"] + 1
+    box = fnpf.Mesh(*dims, np.full(ncx * ncy, d["h0"]), Lx=d["Lx"], Ly=d["Ly"], g=d["g"])
+    th, sr = box.surface_coords()
+    del box
+    X, Y = W.ogrid_map(th, sr, a=d["a"], R=d["R"])
+    h = np.full(X.size, d["h0"])
+    opts = fnpf.default_opts(precond=fnpf.FNPF_PMG, rtol=args.rtol, max_iter=50000, cheb_degree=args.cheb_degree,
+                             coarse_iters=args.coarse_degree)
+    mesh = fnpf.Mesh(*dims, h, X=X, Y=Y, g=d["g"], opts=opts)
+    r = np.hypot(X, Y)
+    cr = np.where(r >= 0.8 * d["R"], W.relaxation_weight((d["R"] - r) / (0.2 * d["R"])), 0.0)
+    om = 2 * np.pi / d["T"]
+    mesh.set_relaxation(cr, np.zeros_like(cr), amp=0.0, kx=d["k"], omega=om, ramp_time=5 * d["T"])
+    amp = 0.5 * 0.01 * 2 * np.pi / d["k"]
+    eta0 = amp * np.cos(d["k"] * X)
+    phi0 = d["g"] * amp / om * np.cosh(d["k"] * (eta0 + h)) / np.cosh(d["k"] * h) * np.sin(d["k"] * X)
+    dev = torch.device("cuda", 0)
+    eta = torch.tensor(eta0, dtype=torch.float64, device=dev)
+    phis = torch.tensor(phi0, dtype=torch.float64, device=dev)
+    dt = d["T"] / 64
+    stream = torch.cuda.current_stream()
+    t = 0.0
+    for _ in range(args.warmup):
+        mesh.rk4_step(eta, phis, t, dt)
+        t += dt
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a_, b_ in ev:
+            a_.record(stream)
+            fn()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev)
+
+    fwd_ms = timed(lambda: mesh.rk4_step(eta, phis, t, dt), args.steps)
+    le = torch.ones(mesh.ns, dtype=torch.float64, device=dev) / mesh.ns
+    lp = torch.zeros_like(le)
+    oe, op_, lh = torch.empty_like(le), torch.empty_like(le), torch.zeros_like(le)
+    mesh.step_adjoint(eta, phis, le, lp, oe, op_, lh, t, dt)
+    adj_ms = timed(lambda: mesh.step_adjoint(eta, phis, le, lp, oe, op_, lh, t, dt), max(1, args.steps // 2))
+    # checkpointed gradient of J = sum eta_N^2 over 32 steps, checkpoints every 16
+    e0 = eta.detach().clone().requires_grad_(True)
+    p0 = phis.detach().clone().requires_grad_(True)
+    ht = torch.tensor(h, dtype=torch.float64, device=dev, requires_grad=True)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    eN, pN = rk4_run(mesh, e0, p0, ht, t, dt, 32, every=16)
+    torch.cuda.synchronize()
+    w1 = time.perf_counter()
+    (eN * eN).sum().backward()
+    torch.cuda.synchronize()
+    w2 = time.perf_counter()
+    finite = bool(torch.isfinite(e0.grad).all() and torch.isfinite(p0.grad).all() and torch.isfinite(ht.grad).all())
+    print(json.dumps({"mode": "cylinder", "workload": "cylinder O-grid 64x24x3, p=4, ka=kh=1, R=10a, sponge ring",
+                      "dof": mesh.N, "forward_ms_per_step": fwd_ms, "adjoint_ms_per_step": adj_ms,
+                      "adjoint_ratio_to_forward": adj_ms / fwd_ms,
+                      "checkpointed_gradient": {"steps": 32, "every": 16, "forward_s": w1 - w0,
+                                                "backward_s": w2 - w1, "ratio": (w2 - w1) / (w1 - w0),
+                                                "finite": finite},
+                      "data": "synthetic"}))
+    return 0
+
+
 def main():
     args = parse()
     if args.mode == "convergence":
         return main_convergence(args)
     if args.mode == "bar":
         return main_bar(args)
+    if args.mode == "cylinder":
+        return main_cylinder(args)
     if args.mode == "ensemble":
         return main_ensemble(args)
     if args.impl == "reference":
