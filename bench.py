@@ -33,6 +33,17 @@ METRIC = "DOF·RK4-steps/s at 1e-8 rel error, FP64 vs mixed-precision; adjoint c
 UNIT = "DOF·steps/s"
 WORKLOAD = "periodic-box-3d kh=2, 32x32x2 hex, GLL p=6, Airy H/L=0.05 + seeded spectrum, dt=T/100, rtol 1e-10"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz
+
+
+def measured_hbm_gbs():
+    """Measured copy bandwidth of this GPU model (MEASURED_PEAKS.json beside
+    this file), else the figure measured earlier on the same model."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6785.2
 
 
 def parse():
@@ -376,7 +387,7 @@ def main_gb300(args):
                 "peak_note": "FP64 FMA peak derived from unit counts and max clock (152 SM x 2 DFMA/clk x "
                              "2070 MHz); the FP64 path is ALU-bound on GB300",
                 "bytes_per_application": 2 * 8 * mesh.N + 6 * 8 * E * n ** 3,
-                "hbm_frac_of_measured": (2 * 8 * mesh.N + 6 * 8 * E * n ** 3) / (apply_ms * 1e-3) / 1e9 / 6785.2}
+                "hbm_frac_of_measured": (2 * 8 * mesh.N + 6 * 8 * E * n ** 3) / (apply_ms * 1e-3) / 1e9 / measured_hbm_gbs()}
 
     # --- adjoint step (reverse mode, FP64, same mesh and state) against the forward step
     adjoint = None
@@ -480,11 +491,13 @@ def main_apply(args):
     ncx = d["p"] * d["nx"]
     mesh = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, np.full(ncx * ncx, d["h0"]),
                      Lx=d["Lx"], Ly=d["Ly"], g=d["g"])
-    if args.shape >= 0:
-        mesh.set_shapes(args.shape, args.shape)
     x, y = mesh.surface_coords()
     eta0, _ = W.airy_plus_spectrum_state(d, x, y, seed=2)
     dev = torch.device("cuda", 0)
+    if args.shape >= 0:
+        mesh.set_shapes(args.shape, args.shape)
+    else:                               # shapes timed for this mesh (fnpf_apply uses the on-the-fly metric)
+        mesh.autotune(torch.tensor(eta0, dtype=torch.float64, device=dev))
     eta = torch.tensor(eta0, dtype=torch.float64, device=dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(5)
@@ -510,12 +523,17 @@ def main_apply(args):
     n = d["p"] + 1
     E = d["nx"] * d["ny"] * d["nz"]
     flops = (12 * n ** 4 + 45 * n ** 3) * E      # on-the-fly metric: contractions + metric rebuild + G . grad u
-    print(json.dumps({"mode": "apply", "precision": "fp32" if args.precision == "mixed" else "fp64",
+    fp32 = args.precision == "mixed"
+    tflops = flops / (ms * 1e-3) / 1e12
+    gbs = (2 * xv.element_size() * mesh.N + 2 * xv.element_size() * mesh.ns) / (ms * 1e-3) / 1e9
+    print(json.dumps({"mode": "apply", "precision": "fp32" if fp32 else "fp64",
                       "dof": mesh.N, "p": d["p"], "nx": d["nx"], "nz": d["nz"],
-                      "ms_per_apply": ms, "applies_per_s": 1e3 / ms, "tflops_alg": flops / (ms * 1e-3) / 1e12,
-                      "frac_fp64_peak": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                      "gbs_alg": (2 * xv.element_size() * mesh.N + 2 * xv.element_size() * mesh.ns)
-                      / (ms * 1e-3) / 1e9}))
+                      "element_columns_per_cta": mesh.get_shapes()[3 if fp32 else 2],
+                      "ms_per_apply": ms, "applies_per_s": 1e3 / ms, "tflops_alg": tflops,
+                      "frac_alu_peak": tflops / (FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS),
+                      "alu_peak_tflops": FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS,
+                      "gbs_alg": gbs, "frac_hbm_measured": gbs / measured_hbm_gbs(),
+                      "l2": "flushed before every timed application"}))
     return 0
 
 
