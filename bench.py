@@ -134,6 +134,40 @@ def oracle_sample_desc(nxy, steps):
             % (steps, nxy, nxy))
 
 
+class Ranks:
+    """Ranks of a torchrun launch (RANK, LOCAL_RANK, WORLD_SIZE from the
+    environment): one process per GPU, each timing its own tank (replicas, no
+    data-path collective); the only collectives are barriers and the maximum
+    over ranks of a timing."""
+
+    def __init__(self, backend="nccl"):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, value, device):
+        """The largest value over all ranks (the job's time is its slowest rank's)."""
+        if self.dist is None:
+            return value
+        import torch
+        t = torch.tensor([value], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
 def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -218,18 +252,10 @@ def main_gb300(args):
     from paper_2506_09435_gb300 import fnpf
     from paper_2506_09435_gb300 import workloads as W
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ranks = Ranks("nccl")
+    world, rank, local = ranks.world, ranks.rank, ranks.local
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = ranks.barrier
 
     d = workload(args.nx)
     h = None
@@ -282,10 +308,7 @@ def main_gb300(args):
     eta64_end, phi64_end = eta.clone(), phis.clone()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if dist is not None:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = ranks.max(total_ms, dev)
     value = world * mesh.N * args.steps / (total_ms * 1e-3)
     iters = [i["iters"] for inf in infos for i in inf]
     rel_res = max(i["rel_res"] for inf in infos for i in inf)
@@ -328,10 +351,7 @@ def main_gb300(args):
         barrier()
         mlaunch = mm.profile_read(reset=True)["launches"]
         m_ms = sum(a.elapsed_time(b) for a, b in mev)
-        if dist is not None:
-            tt = torch.tensor([m_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            m_ms = float(tt.item())
+        m_ms = ranks.max(m_ms, dev)
         err_e = float(torch.linalg.norm(em - eta64_end) / torch.linalg.norm(eta64_end))
         err_p = float(torch.linalg.norm(pm - phi64_end) / torch.linalg.norm(phi64_end))
         mm.profile_enable(True)
@@ -434,10 +454,7 @@ def main_gb300(args):
     torch.cuda.synchronize()
     barrier()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-    if dist is not None:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = ranks.max(e2e_ms, dev)
     e2e = {"value": world * mesh.N * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": 2 * 8 * mesh.ns, "d2h_bytes_per_step": 2 * 8 * mesh.ns}
 
@@ -473,8 +490,7 @@ def main_gb300(args):
             "clocks": clk.summary(),
         }
         print(json.dumps(line))
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
