@@ -106,13 +106,16 @@ typedef struct {
   double atol;
   int max_iter;            /* CG iteration cap per solve (ENOCONV beyond)          */
   int check_every;         /* host reads the convergence flag every k iterations  */
-  int cheb_degree;         /* Chebyshev smoother degree (FNPF_PMG)                 */
-  int coarse_iters;        /* fixed coarse-level iterations (FNPF_PMG)             */
+  int cheb_degree;         /* degree of the pre- and post-smoothing Chebyshev
+                              sweeps on every level but the coarsest (FNPF_PMG)   */
+  int coarse_iters;        /* degree of the coarsest level's Chebyshev sweep
+                              (FNPF_PMG)                                          */
   double inner_rtol;       /* inner FP32 solve tolerance (FNPF_MIXED)              */
   int max_outer;           /* defect-correction cap (FNPF_MIXED)                   */
   int use_graphs;          /* 1: replay CG iterations as CUDA graphs (not while
                               instrumentation is enabled); 0: plain launches      */
-  int store_metric;        /* FNPF_FP64 solves: 1 = rebuild the metric G from eta
+  int store_metric;        /* FP64 operator of FNPF_FP64 and FNPF_FP64_PC32 solves:
+                              1 = rebuild the metric G from eta
                               once per solve into device memory (6 doubles per
                               point, allocated at the first solve) and read it in
                               every application; 0 = rebuild it per application */
@@ -125,7 +128,7 @@ typedef struct {
 
 typedef struct {
   int iters;               /* CG iterations (inner iterations for FNPF_MIXED)     */
-  int outer_iters;         /* defect-correction steps (0 for FNPF_FP64)            */
+  int outer_iters;         /* defect-correction steps (0 unless FNPF_MIXED)        */
   double rel_res;          /* final ||r|| / ||b|| (FP64 residual)                  */
   int status;              /* fnpf_status of this solve                            */
   float ms;                /* device time of the solve                             */
