@@ -147,6 +147,11 @@ class Ranks:
         self.dist = None
         if self.world > 1:
             import torch.distributed as dist
+            if backend == "nccl":
+                # bind this rank to its own GPU before the process group
+                # exists, so that NCCL's barriers and reductions use it
+                import torch
+                torch.cuda.set_device(self.local)
             dist.init_process_group(backend)
             self.dist = dist
 

@@ -221,7 +221,11 @@ fnpf_status fnpf_rk4_step(fnpf_mesh* mesh, double* eta, double* phis, double t, 
  * allocation could fail or stall.  Computes y = A(eta) x exactly as
  * fnpf_apply does, for an FNPF_BOX mesh described by desc (host struct; its
  * h, X, Y pointers are ignored) with the depth h [Ns], eta [Ns], x [N] and
- * y [N] given as caller-owned DEVICE arrays.
+ * y [N] given as caller-owned DEVICE arrays.  The lengths are not passed and
+ * cannot be checked: the caller guarantees them.  Every h and eta + h must be
+ * positive and finite (the vertical Jacobian (eta + h) / (2 Nz) is divided
+ * by); unlike fnpf_create_mesh, this call does not check the depth, and a
+ * zero or negative value gives inf or NaN in y.
  * The GLL tables, the box metric and the operator's scratch live in one
  * file-scope device array of 16 MiB (2,097,152 doubles) that every GPU
  * loading the library holds until exit; a mesh needs

@@ -48,5 +48,17 @@ class RK4Run(torch.autograd.Function):
 
 def rk4_run(mesh, eta0, phis0, h, t0, dt, nsteps, every=16):
     """(eta_N, phi_N) after nsteps RK4 steps; differentiable in eta0, phis0 and h
-    (the gradient for h is dJ/dh at the surface nodes; the mesh keeps its own h)."""
+    (the gradient for h is dJ/dh at the surface nodes).
+
+    The forward runs on the depth the mesh was created with, so `h` must be
+    that depth (the same values, [Ns] doubles): it is the handle through which
+    autograd reports dJ/dh, and a different h would label the gradient of one
+    depth with another.  A mismatch raises ValueError."""
+    mesh_h = mesh.depth()
+    if tuple(h.shape) != (mesh.ns,):
+        raise ValueError("h must have the mesh's %d surface nodes, got shape %s" % (mesh.ns, tuple(h.shape)))
+    hd = h.detach().to(device="cpu", dtype=torch.float64)
+    if not torch.equal(hd, mesh_h):
+        raise ValueError("h differs from the depth the mesh was created with (max |difference| %.3e); "
+                         "create a mesh with this depth instead" % float((hd - mesh_h).abs().max()))
     return RK4Run.apply(eta0, phis0, h, mesh, t0, dt, nsteps, every)

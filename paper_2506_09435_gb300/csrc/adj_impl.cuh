@@ -119,8 +119,9 @@ cudaError_t launch_geom_vjp_t(const Geom& g, const Tables<T>& t, const T* eta, c
                               const T* phiS, T* out, cudaStream_t s) {
   constexpr int C = DIM == 3 ? CtaChoices<N>::c[1] : (128 + N - 1) / N;
   using S = AxShape<T, N, DIM, C>;
-  static bool attr = false;
-  set_smem_attr<T, N, DIM, C>(geom_vjp_kernel<T, N, DIM, C>, &attr);
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = set_smem_attr<T, N, DIM, C>(geom_vjp_kernel<T, N, DIM, C>, &attr);
+  if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((g.n_ecol + C - 1) / C);
   geom_vjp_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, eta, psiI, phiI, phiS, out);
   return cudaGetLastError();

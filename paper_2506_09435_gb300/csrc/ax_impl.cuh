@@ -590,12 +590,8 @@ cudaError_t launch_gather_update(const Geom& g, const T* ring, const T* yI, cons
 }
 
 template <typename T, int N, int DIM, int C, typename K>
-void set_smem_attr(K kernel, bool* done) {
-  using S = AxShape<T, N, DIM, C>;
-  if (!*done && S::SMEM > 48 * 1024) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-    *done = true;
-  }
+cudaError_t set_smem_attr(K kernel, std::atomic<uint64_t>* done) {
+  return smem_optin(kernel, AxShape<T, N, DIM, C>::SMEM, done);
 }
 
 // mode: AX_APPLY (on-the-fly geometry), AX_DIAG, AX_GEOM (store G), AX_APPLY_G (stored G)
@@ -603,26 +599,27 @@ template <typename T, int N, int DIM, int C>
 cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, cudaStream_t s) {
   using S = AxShape<T, N, DIM, C>;
   const unsigned blocks = (unsigned)((g.n_ecol + C - 1) / C);
+  cudaError_t e;
   if (mode == AX_GEOM) {
-    static bool attr = false;
-    set_smem_attr<T, N, DIM, C>(geom_kernel<T, N, DIM, C>, &attr);
+    static std::atomic<uint64_t> attr{0};
+    if ((e = set_smem_attr<T, N, DIM, C>(geom_kernel<T, N, DIM, C>, &attr)) != cudaSuccess) return e;
     geom_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
     return cudaGetLastError();
   }
   if (mode == AX_APPLY_G) {
-    static bool attr = false;
-    set_smem_attr<T, N, DIM, C>(axg_kernel<T, N, DIM, C>, &attr);
+    static std::atomic<uint64_t> attr{0};
+    if ((e = set_smem_attr<T, N, DIM, C>(axg_kernel<T, N, DIM, C>, &attr)) != cudaSuccess) return e;
     axg_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
   } else if (mode == AX_DIAG) {
-    static bool attr = false;
-    set_smem_attr<T, N, DIM, C>(diag_kernel<T, N, DIM, C>, &attr);
+    static std::atomic<uint64_t> attr{0};
+    if ((e = set_smem_attr<T, N, DIM, C>(diag_kernel<T, N, DIM, C>, &attr)) != cudaSuccess) return e;
     diag_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
   } else {
-    static bool attr = false;
-    set_smem_attr<T, N, DIM, C>(ax_kernel<T, N, DIM, C>, &attr);
+    static std::atomic<uint64_t> attr{0};
+    if ((e = set_smem_attr<T, N, DIM, C>(ax_kernel<T, N, DIM, C>, &attr)) != cudaSuccess) return e;
     ax_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.ep.op != EP_NONE) return launch_gather_update<T, N, DIM>(g, a.ring, a.yI, a.skip, a.ep, s);
   return launch_gather<T, N, DIM>(g, a.ring, a.yI, a.ys, a.skip, s);

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -243,5 +244,23 @@ cudaError_t launch_filter(const Geom& g, const double* F, const double* in0, dou
                           double* out1, cudaStream_t s);
 cudaError_t launch_check_state(const Geom& g, const double* eta, const double* phis, const double* h, int* status,
                                int* done, cudaStream_t s);
+
+// Opts `kernel` in to `bytes` of dynamic shared memory when that is above the
+// 48 KB default.  The attribute belongs to the (kernel, device) pair, so the
+// record of it is a bit per device (devices 0..63; beyond that the attribute
+// is set at every launch); two host threads may both set it, which is
+// harmless.  Returns the error of cudaFuncSetAttribute.
+template <typename K>
+cudaError_t smem_optin(K kernel, size_t bytes, std::atomic<uint64_t>* done) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? uint64_t(1) << dev : 0;
+  if (bit && (done->load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && bit) done->fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 }  // namespace fnpf

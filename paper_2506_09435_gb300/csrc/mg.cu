@@ -474,18 +474,15 @@ cudaError_t launch_coarse_cheb(const Geom& g, const T* coef, const T* dinv, cons
 
 // Whether one cluster of the coarse kernel, with its largest shared-memory
 // footprint, can be resident on this device (also raises the kernels'
-// dynamic shared-memory limit, once per process).
+// dynamic shared-memory limit on the current device, once per device).
 bool cluster_launch_ok() {
   constexpr int kMaxSmem = 2 * (kCoarseMaxRows / kCoarseCluster) * (int)sizeof(double);
-  static bool attrs = false;
-  if (!attrs) {
-    cudaFuncSetAttribute(coarse_cheb_kernel<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    cudaFuncSetAttribute(coarse_cheb_kernel<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    cudaFuncSetAttribute(coarse_cheb_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    cudaFuncSetAttribute(coarse_cheb_kernel<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    if (cudaGetLastError() != cudaSuccess) return false;
-    attrs = true;
-  }
+  static std::atomic<uint64_t> a64_3{0}, a64_2{0}, a32_3{0}, a32_2{0};
+  if (smem_optin(coarse_cheb_kernel<double, 3>, kMaxSmem, &a64_3) != cudaSuccess ||
+      smem_optin(coarse_cheb_kernel<double, 2>, kMaxSmem, &a64_2) != cudaSuccess ||
+      smem_optin(coarse_cheb_kernel<float, 3>, kMaxSmem, &a32_3) != cudaSuccess ||
+      smem_optin(coarse_cheb_kernel<float, 2>, kMaxSmem, &a32_2) != cudaSuccess)
+    return false;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kCoarseCluster);
   cfg.blockDim = dim3(kCoarseThreads);

@@ -123,7 +123,8 @@ extern "C" fnpf_status fnpf_apply_noalloc(const fnpf_mesh_desc* desc, const doub
       double* p = nullptr;
       e = cudaGetSymbolAddress((void**)&p, g_scratch);
       if (e != cudaSuccess || !p) {
-        fnpf::set_create_error("fnpf_apply_noalloc: cudaGetSymbolAddress failed");
+        fnpf::set_create_error((std::string("fnpf_apply_noalloc: cudaGetSymbolAddress failed: ") +
+                                cudaGetErrorString(e)).c_str());
         return FNPF_ECUDA;
       }
       g_scratch_ptr[dev] = p;
@@ -140,8 +141,15 @@ extern "C" fnpf_status fnpf_apply_noalloc(const fnpf_mesh_desc* desc, const doub
   const int blocks = (int)((work + threads - 1) / threads < 1024 ? (work + threads - 1) / threads : 1024);
   fill_box_tables_kernel<<<blocks, threads, 0, s>>>(g, tb, base, base + off_xi, base + off_w, base + off_hm);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return FNPF_ECUDA;
+  if (e != cudaSuccess) {
+    fnpf::set_create_error((std::string("fnpf_apply_noalloc: table fill launch failed: ") + cudaGetErrorString(e)).c_str());
+    return FNPF_ECUDA;
+  }
   const fnpf::Tables<double> t{base, base + off_xi, base + off_w, base + off_hm, h, nullptr};
   e = fnpf::launch_apply<double>(g, t, eta, x, x + g.NI, y, y + g.NI, base + off_ring, 1, s);
-  return e == cudaSuccess ? FNPF_OK : FNPF_ECUDA;
+  if (e != cudaSuccess) {
+    fnpf::set_create_error((std::string("fnpf_apply_noalloc: operator launch failed: ") + cudaGetErrorString(e)).c_str());
+    return FNPF_ECUDA;
+  }
+  return FNPF_OK;
 }

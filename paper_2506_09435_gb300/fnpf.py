@@ -137,13 +137,43 @@ def default_opts(**kw):
     return o
 
 
-def _ptr(t):
-    """Device pointer of a contiguous CUDA tensor (or None -> NULL)."""
+def _check_meta(t, n, dtype, name):
+    import torch
+    want = getattr(torch, dtype)
+    if t.dtype != want:
+        raise ValueError("%s: expected dtype %s, got %s" % (name, want, t.dtype))
+    if n is not None and t.numel() != n:
+        raise ValueError("%s: expected %d elements, got %d" % (name, n, t.numel()))
+
+
+def _ptr(t, n=None, dtype="float64", device=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or None -> NULL).
+
+    The C ABI receives bare pointers and trusts their lengths, so every array
+    is checked here before a call: of the expected dtype, with exactly n
+    elements (when n is given), a contiguous CUDA tensor on `device` (the
+    mesh's device; default: the current device).  A mismatch raises
+    ValueError before anything is enqueued."""
     if t is None:
         return None
+    import torch
+    _check_meta(t, n, dtype, name)
     if not t.is_cuda or not t.is_contiguous():
-        raise ValueError("expected a contiguous CUDA tensor")
+        raise ValueError("%s: expected a contiguous CUDA tensor" % name)
+    dev = torch.cuda.current_device() if device is None else device
+    if t.device.index != dev:
+        raise ValueError("%s: on cuda:%d, expected cuda:%d" % (name, t.device.index, dev))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptrs(device, *specs):
+    """Checked pointers of several arrays, spec = (tensor, n, dtype, name):
+    dtypes and lengths of all of them first, then placement, so that a wrong
+    size is reported as such whatever the order of the arguments."""
+    for t, n, dtype, name in specs:
+        if t is not None:
+            _check_meta(t, n, dtype, name)
+    return [_ptr(t, n, dtype, device, name) for t, n, dtype, name in specs]
 
 
 def _stream(stream):
@@ -183,7 +213,12 @@ def apply_noalloc(dim, nx, ny, nz, p, periodic_x, periodic_y, Lx, Ly, h, eta, x,
     h, eta, x, y are CUDA tensors."""
     d = MeshDesc(dim=dim, nx=nx, ny=ny, nz=nz, p=p, periodic_x=int(periodic_x), periodic_y=int(periodic_y),
                  horiz_kind=FNPF_BOX, Lx=Lx, Ly=Ly, g=9.81)
-    st = _LIB.fnpf_apply_noalloc(ctypes.byref(d), _ptr(h), _ptr(eta), _ptr(x), _ptr(y), _stream(stream))
+    # the entry point gets no array lengths: derive them from the box here
+    # (fnpf_count_dofs is host arithmetic) and check every tensor against them
+    n, ns = count_dofs(dim, nx, ny, nz, p, periodic_x, periodic_y)
+    f64 = "float64"
+    args = _ptrs(None, (h, ns, f64, "h"), (eta, ns, f64, "eta"), (x, n, f64, "x"), (y, n, f64, "y"))
+    st = _LIB.fnpf_apply_noalloc(ctypes.byref(d), *args, _stream(stream))
     if st != FNPF_OK:
         raise FnpfError(st, _LIB.fnpf_last_error(None).decode())
 
@@ -203,10 +238,20 @@ class Mesh:
             raise FnpfError(st, _LIB.fnpf_last_error(None).decode())
         self._h = handle
         self.g = g
+        self._depth = np.array(keep[0], dtype=np.float64)   # host copy of the depth the mesh was created with
         nv, ns = ctypes.c_int64(), ctypes.c_int64()
         _LIB.fnpf_mesh_sizes(self._h, ctypes.byref(nv), ctypes.byref(ns))
         self.N, self.ns = nv.value, ns.value
         self.n_interior = self.N - self.ns
+        import torch
+        self.device = torch.cuda.current_device()   # the device the mesh's memory lives on
+
+    def _args(self, *specs, dtype="float64"):
+        """Checked pointers of this mesh's arrays, spec = (tensor, name, kind):
+        kind "s" a surface field [Ns], "v" a volume field [N], "i" the
+        interior unknowns [N_I]."""
+        size = {"s": self.ns, "v": self.N, "i": self.n_interior}
+        return _ptrs(self.device, *[(t, size[k], dtype, nm) for t, nm, k in specs])
 
     def close(self):
         if getattr(self, "_h", None):
@@ -220,6 +265,12 @@ class Mesh:
         if st != FNPF_OK:
             raise FnpfError(st, _LIB.fnpf_last_error(self._h).decode())
 
+    def depth(self):
+        """The still-water depth h [Ns] the mesh was created with (a host
+        float64 tensor)."""
+        import torch
+        return torch.from_numpy(self._depth.copy())
+
     def set_opts(self, opts):
         self._check(_LIB.fnpf_set_opts(self._h, ctypes.byref(opts)))
 
@@ -230,13 +281,15 @@ class Mesh:
         return x, y
 
     def apply(self, eta, x, y, stream=None):
-        self._check(_LIB.fnpf_apply(self._h, _ptr(eta), _ptr(x), _ptr(y), _stream(stream)))
+        a = self._args((eta, "eta", "s"), (x, "x", "v"), (y, "y", "v"))
+        self._check(_LIB.fnpf_apply(self._h, *a, _stream(stream)))
 
     def apply_f32(self, eta, x, y, stream=None):
-        self._check(_LIB.fnpf_apply_f32(self._h, _ptr(eta), _ptr(x), _ptr(y), _stream(stream)))
+        a = self._args((eta, "eta", "s"), (x, "x", "v"), (y, "y", "v"), dtype="float32")
+        self._check(_LIB.fnpf_apply_f32(self._h, *a, _stream(stream)))
 
     def diagonal(self, eta, d, stream=None):
-        self._check(_LIB.fnpf_diagonal(self._h, _ptr(eta), _ptr(d), _stream(stream)))
+        self._check(_LIB.fnpf_diagonal(self._h, *self._args((eta, "eta", "s"), (d, "d", "v")), _stream(stream)))
 
     def set_filter(self, alpha, order=2, cutoff=0):
         """Modal filter of eta and phi after every RK4 step (alpha = 0: off)."""
@@ -244,16 +297,18 @@ class Mesh:
         self._check(_LIB.fnpf_set_filter(self._h, ctypes.byref(f)))
 
     def filter_apply(self, f, stream=None):
-        self._check(_LIB.fnpf_filter_apply(self._h, _ptr(f), _stream(stream)))
+        self._check(_LIB.fnpf_filter_apply(self._h, *self._args((f, "f", "s")), _stream(stream)))
 
     def precond_apply(self, eta, r, z, stream=None):
         """z = M r, the FP64 preconditioner (p-multigrid V-cycle or Jacobi) set
         up from eta; r, z have the N_I interior unknowns."""
-        self._check(_LIB.fnpf_precond_apply(self._h, _ptr(eta), _ptr(r), _ptr(z), _stream(stream)))
+        a = self._args((eta, "eta", "s"), (r, "r", "i"), (z, "z", "i"))
+        self._check(_LIB.fnpf_precond_apply(self._h, *a, _stream(stream)))
 
     def laplace_solve(self, eta, phis, phi, stream=None, info=True, check=True):
         inf = SolveInfo() if info else None
-        st = _LIB.fnpf_laplace_solve(self._h, _ptr(eta), _ptr(phis), _ptr(phi),
+        a = self._args((eta, "eta", "s"), (phis, "phis", "s"), (phi, "phi", "v"))
+        st = _LIB.fnpf_laplace_solve(self._h, *a,
                                      ctypes.byref(inf) if inf is not None else None, _stream(stream))
         if check:
             self._check(st)
@@ -261,15 +316,17 @@ class Mesh:
 
     def dtn(self, eta, phis, w, stream=None, info=True, check=True):
         inf = SolveInfo() if info else None
-        st = _LIB.fnpf_dtn(self._h, _ptr(eta), _ptr(phis), _ptr(w),
+        a = self._args((eta, "eta", "s"), (phis, "phis", "s"), (w, "w", "s"))
+        st = _LIB.fnpf_dtn(self._h, *a,
                            ctypes.byref(inf) if inf is not None else None, _stream(stream))
         if check:
             self._check(st)
         return inf.as_dict() if inf is not None else st
 
     def zakharov_rhs(self, eta, phis, w, deta, dphis, stream=None):
-        self._check(_LIB.fnpf_zakharov_rhs(self._h, _ptr(eta), _ptr(phis), _ptr(w), _ptr(deta), _ptr(dphis),
-                                           _stream(stream)))
+        a = self._args((eta, "eta", "s"), (phis, "phis", "s"), (w, "w", "s"), (deta, "deta", "s"),
+                       (dphis, "dphis", "s"))
+        self._check(_LIB.fnpf_zakharov_rhs(self._h, *a, _stream(stream)))
 
     def set_relaxation(self, cr, gen, amp=0.0, kx=0.0, ky=0.0, omega=1.0, phase=0.0, ramp_time=1.0):
         """Relaxation zones applied after every RK4 step (cr=None removes them)."""
@@ -287,9 +344,10 @@ class Mesh:
     def step_adjoint(self, eta, phis, lam_eta, lam_phis, lam_eta_out, lam_phis_out, lam_h=None, t=0.0, dt=0.01,
                      stream=None):
         """dJ/dy_n from dJ/dy_{n+1} for one RK4 step from (eta, phis); adds dJ/dh into lam_h."""
-        self._check(_LIB.fnpf_step_adjoint(self._h, _ptr(eta), _ptr(phis), _ptr(lam_eta), _ptr(lam_phis),
-                                           _ptr(lam_eta_out), _ptr(lam_phis_out), _ptr(lam_h), float(t),
-                                           float(dt), _stream(stream)))
+        args = self._args(*[(t_, n_, "s") for t_, n_ in ((eta, "eta"), (phis, "phis"), (lam_eta, "lam_eta"),
+                                                          (lam_phis, "lam_phis"), (lam_eta_out, "lam_eta_out"),
+                                                          (lam_phis_out, "lam_phis_out"), (lam_h, "lam_h"))])
+        self._check(_LIB.fnpf_step_adjoint(self._h, *args, float(t), float(dt), _stream(stream)))
 
     def set_shapes(self, variant64, variant32):
         self._check(_LIB.fnpf_set_shapes(self._h, int(variant64), int(variant32)))
@@ -302,7 +360,8 @@ class Mesh:
 
     def autotune(self, eta, stream=None):
         v64, v32 = ctypes.c_int(), ctypes.c_int()
-        self._check(_LIB.fnpf_autotune(self._h, _ptr(eta), ctypes.byref(v64), ctypes.byref(v32), _stream(stream)))
+        a = self._args((eta, "eta", "s"))
+        self._check(_LIB.fnpf_autotune(self._h, *a, ctypes.byref(v64), ctypes.byref(v32), _stream(stream)))
         return v64.value, v32.value
 
     def profile_enable(self, on=True):
@@ -319,7 +378,8 @@ class Mesh:
 
     def rk4_step(self, eta, phis, t, dt, stream=None, info=False, check=True):
         infos = (SolveInfo * 4)() if info else None
-        st = _LIB.fnpf_rk4_step(self._h, _ptr(eta), _ptr(phis), float(t), float(dt), infos, _stream(stream))
+        a = self._args((eta, "eta", "s"), (phis, "phis", "s"))
+        st = _LIB.fnpf_rk4_step(self._h, *a, float(t), float(dt), infos, _stream(stream))
         if check:
             self._check(st)
         return [i.as_dict() for i in infos] if infos is not None else st
@@ -348,8 +408,12 @@ class Ensemble:
 
     def rk4_step(self, etas, phiss, ts, dts, stream=None, info=False):
         n = len(self.meshes)
-        e = (ctypes.c_void_p * n)(*[t.data_ptr() for t in etas])
-        p = (ctypes.c_void_p * n)(*[t.data_ptr() for t in phiss])
+        if len(etas) != n or len(phiss) != n or len(ts) != n or len(dts) != n:
+            raise ValueError("expected one state, time and step size per tank (%d)" % n)
+        ptrs = [m._args((a, "etas[%d]" % i, "s"), (b, "phiss[%d]" % i, "s"))
+                for i, (m, a, b) in enumerate(zip(self.meshes, etas, phiss))]
+        e = (ctypes.c_void_p * n)(*[q[0].value for q in ptrs])
+        p = (ctypes.c_void_p * n)(*[q[1].value for q in ptrs])
         tt = (ctypes.c_double * n)(*[float(v) for v in ts])
         dd = (ctypes.c_double * n)(*[float(v) for v in dts])
         infos = (SolveInfo * (4 * n))() if info else None

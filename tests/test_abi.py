@@ -51,3 +51,43 @@ def test_default_opts(fnpf):
     assert o.precision == fnpf.FNPF_FP64 and o.rtol == 1e-10 and o.max_iter > 0 and o.check_every > 0
     assert o.coarse_iters == 6 and o.store_metric == 1 and o.coarse_solver == fnpf.FNPF_COARSE_CLUSTER
     assert o.cheb_kind == fnpf.FNPF_CHEB_FIRST and o.cheb_range == 160.0
+
+
+def test_noalloc_wrapper_rejects_bad_tensors_before_any_call(fnpf):
+    """fnpf_apply_noalloc gets no array lengths, so the binding checks dtype,
+    length and placement first: a float32, a short or a host tensor raises
+    ValueError before the library is called."""
+    import torch
+    n, ns = fnpf.count_dofs(3, 3, 2, 2, 4, True, False)
+    good_s = torch.zeros(ns, dtype=torch.float64)
+    good_v = torch.zeros(n, dtype=torch.float64)
+    cases = [
+        (good_s.float(), good_s, good_v, good_v, "dtype"),
+        (good_s, good_s[:-1], good_v, good_v, "elements"),
+        (good_s, good_s, good_v, torch.zeros(n - 7, dtype=torch.float64), "elements"),
+        (good_s, good_s, good_v.float(), good_v, "dtype"),
+        (good_s, good_s, good_v, good_v, "CUDA"),   # right sizes, but host memory
+    ]
+    for h, eta, x, y, what in cases:
+        with pytest.raises(ValueError) as e:
+            fnpf.apply_noalloc(3, 3, 2, 2, 4, True, False, 1.0, 1.0, h, eta, x, y)
+        assert what in str(e.value)
+
+
+def test_mesh_methods_check_lengths_and_dtypes(fnpf):
+    """The Mesh methods check every tensor against the mesh's N and Ns (a
+    stand-in object with those sizes, so no GPU is needed)."""
+    import torch
+    m = fnpf.Mesh.__new__(fnpf.Mesh)
+    m._h, m.N, m.ns, m.n_interior, m.device = None, 90, 10, 80, 0
+    eta = torch.zeros(10, dtype=torch.float64)
+    with pytest.raises(ValueError, match="elements"):
+        m.apply(eta, torch.zeros(89, dtype=torch.float64), torch.zeros(90, dtype=torch.float64))
+    with pytest.raises(ValueError, match="dtype"):
+        m.apply_f32(eta, torch.zeros(90, dtype=torch.float32), torch.zeros(90, dtype=torch.float32))
+    with pytest.raises(ValueError, match="elements"):
+        m.rk4_step(eta, torch.zeros(11, dtype=torch.float64), 0.0, 0.1)
+    with pytest.raises(ValueError, match="elements"):
+        m.precond_apply(eta, torch.zeros(90, dtype=torch.float64), torch.zeros(80, dtype=torch.float64))
+    with pytest.raises(ValueError, match="dtype"):
+        m.step_adjoint(eta, eta, eta, eta, eta, eta, torch.zeros(10, dtype=torch.float32))

@@ -2,7 +2,7 @@
 allocate device memory (a plug-in inside an application that owns all device
 memory through its own pool, or a loop with a fixed memory budget): called
 through the C ABI, it must give the same y = A(eta) x as fnpf_apply, on two
-calls in a row (different meshes, so stale contents of the shared device
+calls in a row and a third in 2D (different meshes, so stale contents of the shared device
 array from the first call would show up in the second).  Collected last on
 purpose."""
 import numpy as np
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_noalloc_apply_matches_apply_on_two_calls(fnpf):
-    shapes = [(3, 5, 4, 2, 5, True, False), (3, 3, 3, 3, 4, False, True)]
+    shapes = [(3, 5, 4, 2, 5, True, False), (3, 3, 3, 3, 4, False, True), (2, 8, 1, 2, 4, True, False)]
     for k, shape in enumerate(shapes):
         c = Case(fnpf, *shape, seed=k)
         dim, nx, ny, nz, p, px, py = shape
