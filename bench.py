@@ -70,6 +70,8 @@ def parse():
                     help="first-kind Chebyshev smoothers target [lmax / range, lmax]")
     ap.add_argument("--coarse-solver", default="cluster", choices=["cluster", "launches"],
                     help="coarsest multigrid level on one thread-block cluster, or one launch per step")
+    ap.add_argument("--projection", type=int, default=8,
+                    help="initial guess of each solve projected onto the last N solutions (0: previous solution)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -77,12 +79,13 @@ def parse():
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
     ap.add_argument("--mode", default="step",
-                    choices=["step", "apply", "ensemble", "convergence", "bar", "cylinder"],
+                    choices=["step", "apply", "ensemble", "convergence", "bar", "cylinder", "peaks"],
                     help="step: RK4 steps (the benchmark); apply: operator applications only; "
                          "ensemble: 64 seeded tanks in one launch per step vs one tank at a time; "
                          "convergence: error of a stream-function wave after one period vs p and h; "
                          "bar: the submerged-bar flume in FP64 and both mixed-precision forms; "
-                         "cylinder: adjoint cost on the O-grid around a cylinder")
+                         "cylinder: adjoint cost on the O-grid around a cylinder; "
+                         "peaks: measured FP64 / FP32 FMA throughput")
     ap.add_argument("--tanks", type=int, default=64)
     ap.add_argument("--bar-steps", type=int, default=150, help="RK4 steps of the bar-flume accuracy run")
     ap.add_argument("--p", type=int, default=6)
@@ -103,7 +106,7 @@ sys.path.insert(0, {root!r})
 import numpy as np
 from oracle import mesh, surface
 from paper_2506_09435_gb300 import workloads as W
-nxy, steps, warm = {nxy}, {steps}, {warm}
+nxy, steps, warm, out = {nxy}, {steps}, {warm}, {out!r}
 d = W.periodic_box_3d(nx=nxy, ny=nxy, nz=2, p=6, kh=2.0)
 m = mesh.Mesh(3, nxy, nxy, 2, 6, True, True, d['Lx'], d['Ly'])
 x, y = m.surface_coords()
@@ -117,15 +120,61 @@ for _ in range(steps):
     t0 = time.perf_counter()
     eta, phis = surface.rk4_step(m, h, eta, phis, dt, d['g'], method='pcg')
     times.append(time.perf_counter() - t0)
+if out:
+    np.savez(out, eta=eta, phis=phis)
 print(json.dumps(dict(N=m.N, times=times)))
 """
 
+ONE_THREAD = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
 
-def run_oracle_sample(nxy, steps, warm):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SAMPLE.format(root=ROOT, nxy=nxy, steps=steps, warm=warm)
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])
+
+def run_oracle_sample(nxy, steps, warm, out=""):
+    """The oracle on the sample tank in a child process with one thread;
+    with `out`, the state after warm + steps RK4 steps is saved there (npz)."""
+    env = dict(os.environ, **ONE_THREAD)
+    code = ORACLE_SAMPLE.format(root=ROOT, nxy=nxy, steps=steps, warm=warm, out=out)
+    res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_replicas(nxy, steps, procs):
+    """`procs` copies of the oracle sample at once, one thread each (the host's
+    cores busy with independent tanks, as replicas of the workload); returns
+    the aggregate DOF x steps / s over the slowest copy's timed steps."""
+    env = dict(os.environ, **ONE_THREAD)
+    code = ORACLE_SAMPLE.format(root=ROOT, nxy=nxy, steps=steps, warm=0, out="")
+    ps = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                           stderr=subprocess.DEVNULL, text=True) for _ in range(procs)]
+    res = []
+    for p in ps:
+        o, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle replica failed")
+        res.append(json.loads(o.strip().splitlines()[-1]))
+    slowest = max(sum(r["times"]) for r in res)
+    return procs * res[0]["N"] * steps / slowest, res[0]["N"]
+
+
+def host_cpu():
+    """nproc and the CPU model of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model}
 
 
 def oracle_sample_desc(nxy, steps):
@@ -192,6 +241,35 @@ def main_reference(args):
     }
     print(json.dumps(line))
     return 0
+
+
+# ----------------------------------------------------------------------------- FMA peaks
+
+def measure_fma_peaks(dev, reps=5):
+    """Measured FP64 and FP32 FMA throughput (fnpf_fma_probe: 8 independent
+    FMA chains per thread, 16 CTAs of 256 threads per SM), best of `reps`
+    launches timed with CUDA events on the launching stream, TFLOP/s."""
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec, dtype, iters in (("fp64", fnpf.FNPF_FP64, torch.float64, 400),
+                                     ("fp32", fnpf.FNPF_MIXED, torch.float32, 8000)):
+        buf = torch.zeros(1, dtype=dtype, device=dev)
+        blocks = 152 * 16
+        fnpf.fma_probe(prec, blocks, iters, buf)
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            flops = fnpf.fma_probe(prec, blocks, iters, buf)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        out[name] = {"tflops": flops / (best * 1e-3) / 1e12, "ms": best, "flops": flops}
+    return out
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -271,7 +349,7 @@ def main_gb300(args):
                              coarse_iters=args.coarse_degree, coarse_solver=coarse_mode(args),
                              cheb_kind=args.cheb_kind, cheb_range=args.cheb_range,
                              model=model_id(args), mg_schedule=schedule_id(args),
-                             precision=prec)
+                             precision=prec, projection=args.projection)
     ncx = d["p"] * d["nx"]
     h = np.full(ncx * ncx, d["h0"])
     mesh = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
@@ -293,6 +371,7 @@ def main_gb300(args):
     torch.cuda.synchronize()
 
     # --- timed region: K RK4 steps, L2 flushed before each, device time per step
+    eta_start, phi_start = eta.clone(), phis.clone()     # for the mass and energy drift over the timed steps
     mesh.profile_read(reset=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     infos = []
@@ -311,6 +390,14 @@ def main_gb300(args):
         wall = time.perf_counter() - wall0
     launches = mesh.profile_read(reset=True)["launches"]
     eta64_end, phi64_end = eta.clone(), phis.clone()
+    # conserved quantities before and after the timed steps (fnpf_invariants, outside the timed region)
+    m0, e0 = mesh.invariants(eta_start, phi_start)
+    m1, e1 = mesh.invariants(eta64_end, phi64_end)
+    wave_h = 0.05 * 2 * math.pi / d["k"]          # H = steepness x wavelength
+    drift = {"steps": args.steps, "mass_start": m0, "mass_end": m1, "energy_start": e0, "energy_end": e1,
+             "mass_drift_over_H_area": abs(m1 - m0) / (wave_h * d["Lx"] * d["Ly"]),
+             "energy_drift_rel": abs(e1 - e0) / abs(e0),
+             "how": "M = sum W eta, E = 1/2 phi^T A phi + 1/2 g sum W eta^2 (lumped GLL mass W), fnpf_invariants"}
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     total_ms = ranks.max(total_ms, dev)
@@ -328,7 +415,8 @@ def main_gb300(args):
         mopts = fnpf.default_opts(precision=prec_id, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
                                   precond=pre, cheb_degree=cheb, coarse_iters=args.coarse_degree,
                                   coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
-                                  cheb_range=args.cheb_range, model=model_id(args), mg_schedule=schedule_id(args))
+                                  cheb_range=args.cheb_range, model=model_id(args), mg_schedule=schedule_id(args),
+                                  projection=args.projection)
         mm = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],
                        opts=mopts)
         if args.shape >= 0:
@@ -463,12 +551,56 @@ def main_gb300(args):
     e2e = {"value": world * mesh.N * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": 2 * 8 * mesh.ns, "d2h_bytes_per_step": 2 * 8 * mesh.ns}
 
-    cpu = None
+    # --- measured FMA throughput (the ALU roofline's attainable peak), outside the timed region
+    peaks = measure_fma_peaks(dev)
+    roofline["peak_measured"] = peaks["fp64"]["tflops"]
+    roofline["frac_of_measured_peak"] = roofline["achieved"] / peaks["fp64"]["tflops"]
+
+    cpu = cpu_all = vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = run_oracle_sample(8, 2, 0)
+        host = host_cpu()
+        sample_path = os.path.join(tempfile.gettempdir(), "fnpf_oracle_sample_%d.npz" % os.getpid())
+        res = run_oracle_sample(8, 2, 0, out=sample_path)
         tot = sum(res["times"])
         cpu = {"value": res["N"] * len(res["times"]) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": oracle_sample_desc(8, len(res["times"]))}
+               "sample": oracle_sample_desc(8, len(res["times"])), "host": host}
+        procs = host["nproc"] or 1
+        agg, n_s = run_oracle_replicas(8, 1, procs)
+        cpu_all = {"value": agg, "unit": UNIT, "cores": procs, "kind": "oracle",
+                   "sample": "%d copies of the oracle at once, one thread each, 1 RK4 step each of the 8x8x2 "
+                             "sample tank (N=%d); aggregate over the slowest copy" % (procs, n_s), "host": host}
+        # the GPU paths on the oracle's sample, from the same initial state, at the benchmark's rtol
+        ref = np.load(sample_path)
+        os.remove(sample_path)
+        vs_oracle = {"sample": "8x8x2 elements, p=6, same seeded state, 2 RK4 steps; oracle solves to rtol 1e-14",
+                     "rtol": args.rtol}
+        ds = workload(8)
+        hs = np.full((ds["p"] * 8) ** 2, ds["h0"])
+        for name, prec_id, cheb in (("fp64", fnpf.FNPF_FP64, args.cheb_degree),
+                                    ("mixed", fnpf.FNPF_MIXED, args.mixed_cheb_degree),
+                                    ("fp64_pc32", fnpf.FNPF_FP64_PC32, args.cheb_degree)):
+            if prec_id == fnpf.FNPF_FP64_PC32 and pre != fnpf.FNPF_PMG:
+                continue
+            so = fnpf.default_opts(precision=prec_id, rtol=args.rtol, max_iter=50000, precond=pre,
+                                   cheb_degree=cheb, coarse_iters=args.coarse_degree,
+                                   coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
+                                   cheb_range=args.cheb_range, model=model_id(args), mg_schedule=schedule_id(args),
+                                   projection=args.projection)
+            sm = fnpf.Mesh(3, 8, 8, 2, ds["p"], True, True, hs, Lx=ds["Lx"], Ly=ds["Ly"], g=ds["g"], opts=so)
+            sx, sy = sm.surface_coords()
+            se0, sp0 = W.airy_plus_spectrum_state(ds, sx, sy, seed=2)
+            se = torch.tensor(se0, dtype=torch.float64, device=dev)
+            sp = torch.tensor(sp0, dtype=torch.float64, device=dev)
+            sdt = W.period(ds["k"], ds["h0"], ds["g"]) / 100
+            for k in range(2):
+                sm.rk4_step(se, sp, k * sdt, sdt)
+            torch.cuda.synchronize()
+            ge, gp = se.cpu().numpy(), sp.cpu().numpy()
+            vs_oracle[name] = {"eta": float(np.linalg.norm(ge - ref["eta"]) / np.linalg.norm(ref["eta"])),
+                               "phis": float(np.linalg.norm(gp - ref["phis"]) / np.linalg.norm(ref["phis"]))}
+            del sm
+        if args.model != "fnpf":
+            vs_oracle = None      # the oracle sample is the nonlinear model
 
     if rank == 0:
         line = {
@@ -480,6 +612,7 @@ def main_gb300(args):
                        "precond": args.precond, "cheb_degree": cdeg, "coarse_degree": args.coarse_degree,
                        "coarse_solver": args.coarse_solver, "cheb_kind": args.cheb_kind,
                        "cheb_range": args.cheb_range, "model": args.model, "mg_schedule": args.mg_schedule,
+                       "projection": args.projection,
                        "cta_shape": ("autotuned" if args.shape < 0 else "forced"),
                        "element_columns_per_cta": mesh.get_shapes()[2],
                        "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
@@ -489,7 +622,11 @@ def main_gb300(args):
             "roofline": roofline,
             "mixed": mixed, "fp64_pc32": pc32,
             "adjoint": adjoint,
+            "rel_l2_vs_oracle": vs_oracle,
+            "drift": drift,
+            "fma_peaks_measured": peaks,
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
@@ -837,8 +974,27 @@ def main_cylinder(args):
     return 0
 
 
+def main_peaks(args):
+    """Measured FP64 and FP32 FMA throughput of this GPU (fnpf_fma_probe),
+    with the SM clocks sampled while the probes run."""
+    import torch
+    dev = torch.device("cuda", 0)
+    with ClockSampler(0) as clk:
+        peaks = measure_fma_peaks(dev, reps=20)
+    derived = {"fp64": FP64_PEAK_TFLOPS, "fp32": FP32_PEAK_TFLOPS}
+    for k in peaks:
+        peaks[k]["derived_tflops"] = derived[k]
+        peaks[k]["frac_of_derived"] = peaks[k]["tflops"] / derived[k]
+    print(json.dumps({"mode": "peaks", "fma": peaks, "clocks": clk.summary(),
+                      "how": "8 independent FMA chains per thread, 152 x 16 CTAs of 256 threads, best of 20 "
+                             "launches timed with CUDA events; derived = 152 SM x FMA/clk x 2 flop x 2070 MHz"}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "peaks":
+        return main_peaks(args)
     if args.mode == "convergence":
         return main_convergence(args)
     if args.mode == "bar":

@@ -124,6 +124,15 @@ typedef struct {
   double cheb_range;       /* FNPF_CHEB_FIRST smooths [lmax / cheb_range, lmax] (> 1) */
   int model;               /* FNPF_NONLINEAR or FNPF_LINEAR                        */
   int mg_schedule;         /* FNPF_MG_HALVE, FNPF_MG_TWO_LEVEL or FNPF_MG_STEP2     */
+  int projection;          /* 0..8: initial guess of a Laplace solve = the Galerkin
+                              projection of the solution onto the span of the last
+                              `projection` solutions of this mesh (and of the
+                              caller's guess), in the current operator (Fischer's
+                              projection for successive right-hand sides); 0 keeps
+                              the caller's guess.  Costs `projection` operator
+                              applications and 2 x projection x N_I doubles
+                              per mesh (allocated at the first solve); adjoint
+                              solves never project. */
 } fnpf_opts;
 
 typedef struct {
@@ -144,7 +153,7 @@ fnpf_status fnpf_count_dofs(const fnpf_mesh_desc* desc, int64_t* n_vol, int64_t*
  * max_iter 20000, check_every 16, cheb_degree 3, coarse_iters 6,
  * inner_rtol 1e-5, max_outer 20, use_graphs 1, store_metric 1,
  * coarse_solver FNPF_COARSE_CLUSTER, cheb_kind FNPF_CHEB_FIRST, cheb_range 160,
- * model FNPF_NONLINEAR, mg_schedule FNPF_MG_HALVE. */
+ * model FNPF_NONLINEAR, mg_schedule FNPF_MG_HALVE, projection 8. */
 void fnpf_default_opts(fnpf_opts* opts);
 
 /* Creates a mesh on the current CUDA device: GLL tables, horizontal metric,
@@ -341,6 +350,30 @@ const char* fnpf_ensemble_last_error(const fnpf_ensemble* ens);
 fnpf_status fnpf_step_adjoint(fnpf_mesh* mesh, const double* eta_n, const double* phis_n, const double* lam_eta,
                               const double* lam_phis, double* lam_eta_out, double* lam_phis_out, double* lam_h,
                               double t, double dt, void* stream);
+
+/* Conserved quantities of the state (eta, phis) [Ns] (the diagnostics of the
+ * paper's conservation checks): mass M = sum_c W_c eta_c and energy
+ * E = 1/2 phi^T A(eta) phi + 1/2 g sum_c W_c eta_c^2 (unit density), with W_c
+ * the lumped GLL surface mass (Sec. 3.1.1, Eq. free_surface_weak), phi the
+ * Laplace solution with phi = phis on the surface (Sec. 2, Eq. Laplace_strong;
+ * the mesh's solver and options, into the mesh-owned potential) and A(eta)
+ * the stiffness matrix of Eq. Laplace_weak in the geometry of the mesh's
+ * model.  Writes the two HOST doubles *mass and *energy; waits for the
+ * stream.  An N-double workspace is allocated at the first call.  info may be
+ * NULL (the solve's report otherwise).  Errors: EINVAL (NULL), ENOMEM, ECUDA,
+ * the solve's ENOCONV / EBREAKDOWN / EDIVERGED. */
+fnpf_status fnpf_invariants(fnpf_mesh* mesh, const double* eta, const double* phis, double* mass, double* energy,
+                            fnpf_solve_info* info, void* stream);
+
+/* Measurement utility (no counterpart in the paper): enqueues `blocks` CTAs of
+ * 256 threads that each run 8 independent FMA chains for iters x 16 steps in
+ * FP64 (precision FNPF_FP64) or FP32 (FNPF_MIXED), and reports in *flops (host,
+ * may be NULL) the floating-point operations that launch performs (2 per FMA).
+ * The caller times the launch on `stream`; flops / time is the FMA pipe's
+ * throughput, the denominator of an ALU roofline.  out is a device scratch
+ * element of that precision (never written for the inputs used).
+ * Errors: EINVAL (blocks or iters < 1, out NULL, other precision), ECUDA. */
+fnpf_status fnpf_fma_probe(int precision, int blocks, int iters, void* out, double* flops, void* stream);
 
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */

@@ -554,6 +554,240 @@ fnpf_status precond_apply(fnpf_mesh* m, const double* eta_in, const double* r, d
   return FNPF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Initial guess by projection onto previous solutions (Fischer, "Projection
+// techniques for iterative solution of Ax = b with successive right-hand
+// sides", Comput. Methods Appl. Mech. Engrg. 163 (1998)).  The solves of an
+// RK4 run have right-hand sides and operators that change smoothly from stage
+// to stage, so the last L solutions H_0 (newest) .. H_{L-1} nearly span the
+// next one.  With the basis X = [guess?, H_0 .. H_{L-1}] and the current
+// operator A (the Gram system built in this solve's geometry),
+//     x0 = X c,   (X^T A X) c = X^T b,
+// is the A-orthogonal projection of the solution onto span X: its A-norm error
+// is no larger than that of any basis vector, the guess included.  The first
+// CG residual b - A x0 = b - (A X) c needs no further operator application.
+// Near-dependent basis vectors (successive solutions differ by a few per cent)
+// are dropped by the Cholesky factorisation of the Gram matrix when their new
+// pivot falls below 1e-14 of their diagonal entry; non-finite ones likewise.
+
+namespace {
+
+struct ProjBasis {
+  const double* x[kMaxProjection + 1];
+  const double* ax[kMaxProjection + 1];
+};
+
+template <int K>
+struct ProjSize {
+  static constexpr int NP = K * (K + 1) / 2 + K;   // upper triangle of X^T A X, then X^T b
+};
+constexpr int kProjMaxNP = ProjSize<kMaxProjection + 1>::NP;
+
+// Per-block partials of G_ac = x_a . (A x_c) (a <= c) and f_a = x_a . b, b = -r.
+template <int K>
+__global__ void __launch_bounds__(NT) proj_gram_kernel(int64_t n, ProjBasis B, const double* r, double* part, int nb) {
+  constexpr int NP = ProjSize<K>::NP;
+  double acc[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+  GRID_LOOP(i, n) {
+    double xv[K], av[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      xv[j] = B.x[j][i];
+      av[j] = B.ax[j][i];
+    }
+    const double b = -r[i];
+    int q = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int c = a; c < K; ++c) acc[q++] += xv[a] * av[c];
+#pragma unroll
+    for (int a = 0; a < K; ++a) acc[q++] += xv[a] * b;
+  }
+  __shared__ double sh[NT / 32][NP];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid][q] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < NP; q += NT) {
+    double v = 0.0;
+    for (int w = 0; w < NT / 32; ++w) v += sh[w][q];
+    part[(int64_t)q * nb + blockIdx.x] = v;
+  }
+}
+
+// One block: every sum over the partials in a fixed order (one warp per sum),
+// then thread 0 solves the K x K Gram system by Cholesky with dropping and
+// writes the coefficients c (0 for dropped vectors) to coef.
+template <int K>
+__global__ void __launch_bounds__(NT) proj_solve_kernel(const double* part, int nb, double* coef) {
+  constexpr int NP = ProjSize<K>::NP;
+  __shared__ double red[NP];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = wid; q < NP; q += NT / 32) {
+    double v = 0.0;
+    for (int k = lane; k < nb; k += 32) v += part[(int64_t)q * nb + k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double G[K][K], f[K], Lw[K][K], z[K], c[K];
+  bool act[K];
+  int q = 0;
+  for (int a = 0; a < K; ++a)
+    for (int b = a; b < K; ++b) G[a][b] = G[b][a] = red[q++];
+  for (int a = 0; a < K; ++a) f[a] = red[q++];
+  for (int k = 0; k < K; ++k) {
+    double d = G[k][k];
+    for (int j = 0; j < k; ++j)
+      if (act[j]) d -= Lw[k][j] * Lw[k][j];
+    act[k] = isfinite(f[k]) && G[k][k] > 0.0 && isfinite(G[k][k]) && d > 1e-14 * G[k][k];
+    if (!act[k]) continue;
+    Lw[k][k] = sqrt(d);
+    for (int i = k + 1; i < K; ++i) {
+      double v = G[i][k];
+      for (int j = 0; j < k; ++j)
+        if (act[j]) v -= Lw[i][j] * Lw[k][j];
+      Lw[i][k] = v / Lw[k][k];
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    z[k] = 0.0;
+    if (!act[k]) continue;
+    double v = f[k];
+    for (int j = 0; j < k; ++j)
+      if (act[j]) v -= Lw[k][j] * z[j];
+    z[k] = v / Lw[k][k];
+  }
+  for (int k = K - 1; k >= 0; --k) {
+    c[k] = 0.0;
+    if (!act[k]) continue;
+    double v = z[k];
+    for (int j = k + 1; j < K; ++j)
+      if (act[j]) v -= Lw[j][k] * c[j];
+    c[k] = v / Lw[k][k];
+  }
+  for (int k = 0; k < K; ++k) coef[k] = c[k];
+}
+
+// x0 = X c and A x0 = (A X) c (x and q may be basis vectors 0: read first).
+template <int K>
+__global__ void __launch_bounds__(NT) proj_combine_kernel(int64_t n, ProjBasis B, const double* coef, double* x,
+                                                          double* q) {
+  double c[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) c[j] = coef[j];
+  GRID_LOOP(i, n) {
+    double sx = 0.0, sq = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (c[j] != 0.0) {
+        sx += c[j] * B.x[j][i];
+        sq += c[j] * B.ax[j][i];
+      }
+    }
+    x[i] = sx;
+    q[i] = sq;
+  }
+}
+
+// History push after a solve: H_j <- H_{j-1} (j = L-1 .. 1), H_0 <- x.
+__global__ void __launch_bounds__(NT) proj_push_kernel(int64_t n, int L, double* H, const double* x) {
+  GRID_LOOP(i, n) {
+    for (int j = L - 1; j > 0; --j) H[(int64_t)j * n + i] = H[(int64_t)(j - 1) * n + i];
+    H[i] = x[i];
+  }
+}
+
+template <int K>
+void launch_projection_k(int64_t n, const ProjBasis& B, const double* r, double* part, int nb, double* coef,
+                         double* x, double* q, cudaStream_t s) {
+  proj_gram_kernel<K><<<nb, NT, 0, s>>>(n, B, r, part, nb);
+  proj_solve_kernel<K><<<1, NT, 0, s>>>(part, nb, coef);
+  proj_combine_kernel<K><<<nb, NT, 0, s>>>(n, B, coef, x, q);
+}
+
+// Allocates the history (zeroed: zero vectors are dropped) at the first use.
+fnpf_status ensure_projection(fnpf_mesh* m) {
+  const int L = m->opts.projection;
+  if (L <= 0 || m->proj_alloc >= L) return FNPF_OK;
+  if (m->projH) cudaFree(m->projH);
+  if (m->proj_part) cudaFree(m->proj_part);
+  m->projH = m->proj_part = nullptr;
+  m->proj_alloc = 0;
+  const size_t hbytes = (size_t)2 * L * m->g.NI * sizeof(double);
+  const size_t pbytes = ((size_t)kProjMaxNP * kVecBlocks + 16) * sizeof(double);
+  if (cudaMalloc((void**)&m->projH, std::max<size_t>(hbytes, 8)) != cudaSuccess ||
+      cudaMalloc((void**)&m->proj_part, pbytes) != cudaSuccess) {
+    if (m->projH) cudaFree(m->projH);
+    m->projH = nullptr;
+    m->err = "projection history: device allocation failed";
+    return FNPF_ENOMEM;
+  }
+  if (cudaMemset(m->projH, 0, hbytes) != cudaSuccess) return FNPF_ECUDA;
+  m->proj_alloc = L;
+  return FNPF_OK;
+}
+
+// Replaces x by the projected initial guess and q by A x (r holds -b).  The
+// caller's guess x is a basis vector when with_guess.
+cudaError_t enqueue_projection(fnpf_mesh* m, const Tables<double>& t, const double* eta, double* x, bool with_guess,
+                               cudaStream_t s) {
+  const int L = m->opts.projection;
+  if (L <= 0) return cudaSuccess;
+  const int64_t NI = m->g.NI;
+  double* H = m->projH;
+  double* AH = H + (int64_t)L * NI;
+  for (int j = 0; j < L; ++j) {
+    cudaError_t e = timed_apply<double>(m, t, eta, H + (int64_t)j * NI, nullptr, AH + (int64_t)j * NI, s, nullptr,
+                                        -1);
+    if (e != cudaSuccess) return e;
+  }
+  ProjBasis B{};
+  int K = 0;
+  if (with_guess) {
+    B.x[K] = x;
+    B.ax[K] = m->q;
+    ++K;
+  }
+  for (int j = 0; j < L; ++j, ++K) {
+    B.x[K] = H + (int64_t)j * NI;
+    B.ax[K] = AH + (int64_t)j * NI;
+  }
+  const int nb = vec_blocks(NI);
+  double* coef = m->proj_part + (int64_t)kProjMaxNP * kVecBlocks;
+  switch (K) {
+    case 1: launch_projection_k<1>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+    case 2: launch_projection_k<2>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+    case 3: launch_projection_k<3>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+    case 4: launch_projection_k<4>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+    case 5: launch_projection_k<5>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+    case 6: launch_projection_k<6>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+    case 7: launch_projection_k<7>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+    case 8: launch_projection_k<8>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+    default: launch_projection_k<9>(NI, B, m->r, m->proj_part, nb, coef, x, m->q, s); break;
+  }
+  m->launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_projection_push(fnpf_mesh* m, const double* x, cudaStream_t s) {
+  const int L = m->opts.projection;
+  if (L <= 0) return cudaSuccess;
+  proj_push_kernel<<<vec_blocks(m->g.NI), NT, 0, s>>>(m->g.NI, L, m->projH, x);
+  m->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, double* x, fnpf_solve_info* info,
                      cudaStream_t s, const double* rhs) {
   const Geom& g = m->g;
@@ -616,6 +850,12 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     FNPF_CK(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
   }
   FNPF_CK(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
+  const bool project = !rhs && m->opts.projection > 0;   // adjoint solves (rhs given) keep their guess
+  if (project) {
+    const fnpf_status st = ensure_projection(m);
+    if (st != FNPF_OK) return st;
+    FNPF_CK(enqueue_projection(m, t, eta, x, x != m->phi, s));
+  }
   cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
                                    mixed ? m->b : nullptr, m->partials, nb);
   if (!mixed && pmg) {
@@ -633,6 +873,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     PcgBufs<double> B{eta, x, m->r, m->z, m->p, m->q, m->dinv, sc};
     fnpf_status st = pcg_loop<double>(m, t, B, max_iter, s, &h, &done);
     if (st != FNPF_OK) return st;
+    if (project) FNPF_CK(enqueue_projection_push(m, x, s));
     return finish(m, h, done, h.iters, 0, info, s);
   }
 
@@ -692,6 +933,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     m->launches += 3;
     ++outer;
   }
+  if (project) FNPF_CK(enqueue_projection_push(m, x, s));
   return finish(m, h, done, inner_total, outer, info, s);
 }
 
@@ -836,6 +1078,9 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
   }
   ENQ(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
   ENQ(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
+  // the history buffers exist: a host-driven solve of the same options ran before
+  const bool project = m->opts.projection > 0 && m->proj_alloc >= m->opts.projection;
+  if (project) ENQ(enqueue_projection(m, t, eta, x, x != m->phi, s));
   cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
                                    mixed ? m->b : nullptr, m->partials, nb);
   if (!mixed && pmg) {
@@ -909,6 +1154,7 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
       return cudaGetLastError();
     }));
   }
+  if (project) ENQ(enqueue_projection_push(m, x, s));
   stage_info_kernel<<<1, 1, 0, s>>>(sc, m->inner_total, mixed ? 1 : 0, info_dev);
   m->g64_active = false;
   return cudaGetLastError();

@@ -19,6 +19,7 @@ constexpr int kMaxP = 8;
 constexpr int kMaxN = kMaxP + 1;
 constexpr int kVecBlocks = 608;      // 4 x 152 SMs: grid of the vector kernels
 constexpr int kVecThreads = 256;
+constexpr int kMaxProjection = 8;    // most previous solutions in the initial-guess projection
 
 // Mesh sizes, passed by value to every kernel.
 struct Geom {

@@ -209,6 +209,9 @@ void free_mesh(fnpf_mesh* m) {
   if (m->dfilter) cudaFree(m->dfilter);
   if (m->G64) cudaFree(m->G64);
   if (m->adj) cudaFree(m->adj);
+  if (m->inv_work) cudaFree(m->inv_work);
+  if (m->projH) cudaFree(m->projH);
+  if (m->proj_part) cudaFree(m->proj_part);
   double* rptrs[] = {m->rx_cr, m->rx_gen, m->dxs, m->dys};
   for (double* p : rptrs)
     if (p) cudaFree(p);
@@ -279,6 +282,7 @@ void fnpf_default_opts(fnpf_opts* o) {
   o->cheb_range = 160.0;
   o->model = FNPF_NONLINEAR;
   o->mg_schedule = FNPF_MG_HALVE;
+  o->projection = 8;
 }
 
 fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, fnpf_mesh** out) {
@@ -299,6 +303,10 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
   }
   if (opts && opts->model != FNPF_NONLINEAR && opts->model != FNPF_LINEAR) {
     g_create_error = "model must be FNPF_NONLINEAR or FNPF_LINEAR";
+    return FNPF_EINVAL;
+  }
+  if (opts && (opts->projection < 0 || opts->projection > fnpf::kMaxProjection)) {
+    g_create_error = "projection must be in 0..8";
     return FNPF_EINVAL;
   }
   if (opts && (opts->precision < FNPF_FP64 || opts->precision > FNPF_FP64_PC32)) {
@@ -431,6 +439,10 @@ fnpf_status fnpf_set_opts(fnpf_mesh* m, const fnpf_opts* o) {
   }
   if (o->precision < FNPF_FP64 || o->precision > FNPF_FP64_PC32) {
     m->err = "precision must be FNPF_FP64, FNPF_MIXED or FNPF_FP64_PC32";
+    return FNPF_EINVAL;
+  }
+  if (o->projection < 0 || o->projection > fnpf::kMaxProjection) {
+    m->err = "projection must be in 0..8";
     return FNPF_EINVAL;
   }
   m->opts = *o;

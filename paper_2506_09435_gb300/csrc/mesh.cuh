@@ -87,6 +87,17 @@ struct fnpf_mesh {
   double* dfilter = nullptr;
   bool filter_on = false;
 
+  // projection of the initial guess (opts.projection = L > 0; allocated at the
+  // first solve): projH = [L history solutions | L operator images], [2L][NI],
+  // history 0 = newest; proj_part: per-block partials of the Gram system, then
+  // the coefficients
+  double* projH = nullptr;
+  double* proj_part = nullptr;
+  int proj_alloc = 0;               // L the buffers were sized for
+
+  // fnpf_invariants: A phi of the energy [N] (allocated at the first call)
+  double* inv_work = nullptr;
+
   // adjoint step workspaces (allocated at the first fnpf_step_adjoint)
   double* adj = nullptr;            // one block holding all of them
   size_t adj_bytes = 0;

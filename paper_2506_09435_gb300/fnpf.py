@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("use_graphs", ctypes.c_int), ("store_metric", ctypes.c_int),
                 ("coarse_solver", ctypes.c_int), ("cheb_kind", ctypes.c_int), ("cheb_range", ctypes.c_double),
-                ("model", ctypes.c_int), ("mg_schedule", ctypes.c_int)]
+                ("model", ctypes.c_int), ("mg_schedule", ctypes.c_int), ("projection", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -85,6 +85,9 @@ def load():
         "fnpf_zakharov_rhs": [vp, vp, vp, vp, vp, vp, vp],
         "fnpf_rk4_step": [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(SolveInfo), vp],
         "fnpf_apply_noalloc": [ctypes.POINTER(MeshDesc), vp, vp, vp, vp, vp],
+        "fnpf_invariants": [vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(SolveInfo), vp],
+        "fnpf_fma_probe": [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double), vp],
         "fnpf_set_relaxation": [vp, ctypes.POINTER(Relaxation)],
         "fnpf_step_adjoint": [vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp],
         "fnpf_ensemble_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
@@ -223,6 +226,19 @@ def apply_noalloc(dim, nx, ny, nz, p, periodic_x, periodic_y, Lx, Ly, h, eta, x,
         raise FnpfError(st, _LIB.fnpf_last_error(None).decode())
 
 
+def fma_probe(precision, blocks, iters, out, stream=None):
+    """Enqueues the FMA-throughput probe (fnpf_fma_probe) on `stream`;
+    `out` is a one-element CUDA tensor of the probe's precision.  Returns the
+    floating-point operations of the launch."""
+    dtype = "float64" if precision == FNPF_FP64 else "float32"
+    fl = ctypes.c_double()
+    st = _LIB.fnpf_fma_probe(int(precision), int(blocks), int(iters), _ptr(out, 1, dtype, name="out"),
+                             ctypes.byref(fl), _stream(stream))
+    if st != FNPF_OK:
+        raise FnpfError(st, "fma probe")
+    return fl.value
+
+
 class Mesh:
     """Owns one fnpf_mesh (device workspaces on the current CUDA device)."""
 
@@ -348,6 +364,15 @@ class Mesh:
                                                           (lam_phis, "lam_phis"), (lam_eta_out, "lam_eta_out"),
                                                           (lam_phis_out, "lam_phis_out"), (lam_h, "lam_h"))])
         self._check(_LIB.fnpf_step_adjoint(self._h, *args, float(t), float(dt), _stream(stream)))
+
+    def invariants(self, eta, phis, stream=None):
+        """(mass, energy) of the state: M = sum W eta, E = 1/2 phi^T A phi +
+        1/2 g sum W eta^2 (fnpf_invariants; one Laplace solve)."""
+        a = self._args((eta, "eta", "s"), (phis, "phis", "s"))
+        ms, en = ctypes.c_double(), ctypes.c_double()
+        self._check(_LIB.fnpf_invariants(self._h, *a, ctypes.byref(ms), ctypes.byref(en), None,
+                                         _stream(stream)))
+        return ms.value, en.value
 
     def set_shapes(self, variant64, variant32):
         self._check(_LIB.fnpf_set_shapes(self._h, int(variant64), int(variant32)))

@@ -30,9 +30,16 @@ def test_noalloc_apply_matches_apply_on_two_calls(fnpf):
 
 
 def test_noalloc_rejects_mesh_beyond_the_fixed_scratch(fnpf):
+    """Called through the C ABI directly (the Python wrapper would reject the
+    short arrays first): the library refuses a mesh whose tables and scratch
+    exceed the fixed device array before it touches any array."""
+    import ctypes
     dev = torch.device("cuda:0")
     t = torch.zeros(8, dtype=torch.float64, device=dev)
-    with pytest.raises(fnpf.FnpfError) as e:
-        fnpf.apply_noalloc(3, 200, 200, 4, 6, True, True, 1.0, 1.0, t, t, t, t)
-    assert e.value.status == fnpf.FNPF_EINVAL
-    assert "16 MiB" in str(e.value)
+    d = fnpf.MeshDesc(dim=3, nx=200, ny=200, nz=4, p=6, periodic_x=1, periodic_y=1, horiz_kind=fnpf.FNPF_BOX,
+                      Lx=1.0, Ly=1.0, g=9.81)
+    ptr = ctypes.c_void_p(t.data_ptr())
+    st = fnpf.lib().fnpf_apply_noalloc(ctypes.byref(d), ptr, ptr, ptr, ptr,
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == fnpf.FNPF_EINVAL
+    assert "16 MiB" in fnpf.lib().fnpf_last_error(None).decode()
