@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--cheb-degree", type=int, default=3, help="Chebyshev degree of the FP64 path's smoothers")
     ap.add_argument("--mixed-cheb-degree", type=int, default=3, help="... of the mixed path's FP32 smoothers")
     ap.add_argument("--coarse-degree", type=int, default=6)
-    ap.add_argument("--shape", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+    ap.add_argument("--shape", type=int, default=-1, choices=list(range(-1, 8)),
                     help="elements-per-CTA shape of the operator kernels (-1: autotuned)")
     ap.add_argument("--model", default="fnpf", choices=["fnpf", "lpf"],
                     help="fnpf: fully nonlinear (the configuration's method); lpf: linear potential flow")

@@ -38,6 +38,17 @@ cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, 
 
 int apply_variants(int n, int dim) { return dim == 2 ? 1 : kCtaVariants; }
 
+cudaError_t ax_prepare(int n) {
+  Geom g{};
+  g.n = n;
+  const Tables<double> t{};
+  const Tables<float> t32{};
+  const AxPtrs<double> a{};
+  const AxPtrs<float> a32{};
+  cudaError_t e = dispatch<double>(g, t, a, AX_INIT, 0, nullptr);
+  return e == cudaSuccess ? dispatch<float>(g, t32, a32, AX_INIT, 0, nullptr) : e;
+}
+
 int cta_columns(int n, int dim, int variant) {
   if (dim == 2) return (128 + n - 1) / n;
   if (variant < 0 || variant >= kCtaVariants) return 0;

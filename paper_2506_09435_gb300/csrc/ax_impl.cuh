@@ -625,28 +625,67 @@ cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& 
   return launch_gather<T, N, DIM>(g, a.ring, a.yI, a.ys, a.skip, s);
 }
 
-// Elements-per-CTA candidates for order N (3D); 2D uses one shape.  The
-// fourth choice gives grids that fill the 152 SMs evenly for common column
+}  // namespace fnpf
+
+#include "axl_impl.cuh"
+
+namespace fnpf {
+
+// Elements-per-CTA candidates for order N (3D); 2D uses one shape.  Variants
+// 0-3 are the one-thread-per-vertical-line kernels (ax_kernel, axg_kernel);
+// the fourth choice gives grids that fill the 152 SMs evenly for common column
 // counts (e.g. 7 columns of N = 7: 147 CTAs for 32 x 32 columns, where 2 and 4
-// leave a partial second wave on a third of the SMs).
+// leave a partial second wave on a third of the SMs).  Variants 4-7 are the
+// line-decomposed kernel (axl_kernel) with these element columns per CTA.
 template <int N>
 struct CtaChoices;
-template <> struct CtaChoices<2> { static constexpr int c[4] = {16, 32, 64, 8}; };
-template <> struct CtaChoices<3> { static constexpr int c[4] = {7, 14, 28, 4}; };
-template <> struct CtaChoices<4> { static constexpr int c[4] = {4, 8, 16, 2}; };
-template <> struct CtaChoices<5> { static constexpr int c[4] = {3, 5, 10, 2}; };
-template <> struct CtaChoices<6> { static constexpr int c[4] = {2, 4, 8, 6}; };
-template <> struct CtaChoices<7> { static constexpr int c[4] = {1, 2, 4, 7}; };
-template <> struct CtaChoices<8> { static constexpr int c[4] = {1, 2, 4, 3}; };
-template <> struct CtaChoices<9> { static constexpr int c[4] = {1, 2, 3, 4}; };
+template <> struct CtaChoices<2> { static constexpr int c[8] = {16, 32, 64, 8, 32, 64, 128, 16}; };
+template <> struct CtaChoices<3> { static constexpr int c[8] = {7, 14, 28, 4, 16, 32, 56, 8}; };
+template <> struct CtaChoices<4> { static constexpr int c[8] = {4, 8, 16, 2, 8, 16, 32, 4}; };
+template <> struct CtaChoices<5> { static constexpr int c[8] = {3, 5, 10, 2, 8, 16, 4, 12}; };
+template <> struct CtaChoices<6> { static constexpr int c[8] = {2, 4, 8, 6, 4, 8, 14, 2}; };
+template <> struct CtaChoices<7> { static constexpr int c[8] = {1, 2, 4, 7, 7, 4, 10, 2}; };
+template <> struct CtaChoices<8> { static constexpr int c[8] = {1, 2, 4, 3, 2, 4, 8, 3}; };
+template <> struct CtaChoices<9> { static constexpr int c[8] = {1, 2, 3, 4, 2, 4, 6, 3}; };
 static_assert(sizeof(CtaChoices<7>::c) / sizeof(int) == kCtaVariants, "one shape per variant");
+constexpr int kLineVariant0 = 4;   // first variant of the line-decomposed kernel
+
+// Line-decomposed kernel launch (3D, AX_APPLY or AX_APPLY_G), then the gather.
+template <typename T, int N, int C>
+cudaError_t launch_axl_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, cudaStream_t s) {
+  using S = AxlShape<T, N, C>;
+  cudaError_t e = eo_upload();
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((g.n_ecol + C - 1) / C);
+  if (mode == AX_APPLY_G) {
+    static std::atomic<uint64_t> attr{0};
+    if ((e = smem_optin(axl_kernel<T, N, C, true>, S::SMEM, &attr)) != cudaSuccess) return e;
+    axl_kernel<T, N, C, true><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+  } else {
+    static std::atomic<uint64_t> attr{0};
+    if ((e = smem_optin(axl_kernel<T, N, C, false>, S::SMEM, &attr)) != cudaSuccess) return e;
+    axl_kernel<T, N, C, false><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.ep.op != EP_NONE) return launch_gather_update<T, N, 3>(g, a.ring, a.yI, a.skip, a.ep, s);
+  return launch_gather<T, N, 3>(g, a.ring, a.yI, a.ys, a.skip, s);
+}
 
 template <typename T, int N>
 cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, int variant,
                         cudaStream_t s) {
+  if (mode == AX_INIT) return eo_upload();
   if (g.dim == 2) return launch_ax_shape<T, N, 2, (128 + N - 1) / N>(g, t, a, mode, s);
   constexpr int C0 = CtaChoices<N>::c[0], C1 = CtaChoices<N>::c[1], C2 = CtaChoices<N>::c[2];
   constexpr int C3 = CtaChoices<N>::c[3];
+  if (variant >= kLineVariant0 && (mode == AX_APPLY || mode == AX_APPLY_G)) {
+    switch (variant - kLineVariant0) {
+      case 0: return launch_axl_shape<T, N, CtaChoices<N>::c[4]>(g, t, a, mode, s);
+      case 1: return launch_axl_shape<T, N, CtaChoices<N>::c[5]>(g, t, a, mode, s);
+      case 2: return launch_axl_shape<T, N, CtaChoices<N>::c[6]>(g, t, a, mode, s);
+      default: return launch_axl_shape<T, N, CtaChoices<N>::c[7]>(g, t, a, mode, s);
+    }
+  }
   if (mode == AX_DIAG || mode == AX_GEOM || variant == 1) return launch_ax_shape<T, N, 3, C1>(g, t, a, mode, s);
   if (variant == 0) return launch_ax_shape<T, N, 3, C0>(g, t, a, mode, s);
   if (variant == 3) return launch_ax_shape<T, N, 3, C3>(g, t, a, mode, s);

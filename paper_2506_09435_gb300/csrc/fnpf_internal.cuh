@@ -175,7 +175,7 @@ struct AxPtrs {
   Epilogue<T> ep{};  // update fused into the gather (AX_APPLY, AX_APPLY_G); yI is scratch then
 };
 
-enum { AX_APPLY = 0, AX_DIAG = 1, AX_GEOM = 2, AX_APPLY_G = 3 };
+enum { AX_APPLY = 0, AX_DIAG = 1, AX_GEOM = 2, AX_APPLY_G = 3, AX_INIT = 4 };
 
 // Per-order operator launcher, explicitly instantiated in ax_n<N>.cu.
 template <typename T, int N>
@@ -193,8 +193,11 @@ cudaError_t launch_apply(const Geom& g, const Tables<T>& t, const T* eta, const 
                          const Epilogue<T>* ep = nullptr);
 template <typename T>
 cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, T* ds, T* ring, cudaStream_t s);
-constexpr int kCtaVariants = 4;      // elements-per-CTA shapes of the 3D operator kernels
+constexpr int kCtaVariants = 8;      // elements-per-CTA shapes of the 3D operator kernels
 int apply_variants(int n, int dim);   // number of elements-per-CTA variants for order n-1
+// Fills the constant tables of the line-decomposed operator kernels for order
+// n - 1 on the current device (synchronous: call outside stream capture).
+cudaError_t ax_prepare(int n);
 int cta_columns(int n, int dim, int variant);   // element columns per CTA of a variant
 // Stored metric: G (6 entries per point in 3D, 3 in 2D; geom_points(g) points)
 // computed from eta once, and the operator reading it.

@@ -419,6 +419,9 @@ fnpf_status fnpf_create_mesh(const fnpf_mesh_desc* desc, const fnpf_opts* opts, 
     up32(m->fhm, m->hm);
     up32(m->fh, m->h);
   }
+  // constant tables of the line-decomposed operator kernels of every order
+  // (the multigrid levels use lower orders), once per device
+  for (int nn = 2; nn <= fnpf::kMaxN && e == cudaSuccess; ++nn) e = fnpf::ax_prepare(nn);
   if (e != cudaSuccess) {
     g_create_error = std::string("device set-up failed: ") + cudaGetErrorString(e);
     const fnpf_status ret = (e == cudaErrorMemoryAllocation) ? FNPF_ENOMEM : FNPF_ECUDA;
