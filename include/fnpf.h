@@ -131,8 +131,9 @@ typedef struct {
                               projection for successive right-hand sides); 0 keeps
                               the caller's guess.  Costs `projection` operator
                               applications and 2 x projection x N_I doubles
-                              per mesh (allocated at the first solve); adjoint
-                              solves never project. */
+                              per mesh (allocated at the first solve); the
+                              adjoint solves of fnpf_step_adjoint project onto
+                              their own history (as much memory again). */
 } fnpf_opts;
 
 typedef struct {
@@ -314,6 +315,26 @@ typedef struct {
   int cutoff;              /* N_c in 0..p-1: modes up to N_c are kept */
 } fnpf_filter;
 fnpf_status fnpf_set_filter(fnpf_mesh* mesh, const fnpf_filter* filter);
+
+/* Over-integration of the nonlinear free-surface terms (Sec. 3.2, with the
+ * modal filter; reading: collocation is replaced on each surface element by
+ * an exactly integrated projection).  With points = M > 0, every Zakharov
+ * right-hand side of FNPF_NONLINEAR (fnpf_rk4_step stages, fnpf_zakharov_rhs)
+ * is evaluated as follows: eta, phi_eta and w are interpolated from the GLL
+ * nodes to the M x M (2D: M) Gauss-Legendre points of each surface element,
+ * with the horizontal gradients of the interpolants; f_eta and f_phi are
+ * evaluated there and replaced by their L2 projection onto the degree-p
+ * polynomials of the element's reference coordinates (exact Gauss sums of the
+ * Legendre coefficients), evaluated at the GLL nodes; shared nodes combine the
+ * element values with the lumped-mass weights w_i w_j |det H|.  Polynomial
+ * right-hand sides of degree <= p per direction are unchanged; modes above p
+ * are dropped instead of aliased.  Quadratic terms are integrated exactly
+ * from M >= (3p + 1) / 2 + 1, cubic ones from M >= 2p + 1 on affine elements.
+ * points = 0 turns it off.  Tables and the Gauss-point metric are built on the
+ * host and copied (synchronous); the adjoint step returns EUNSUPPORTED while
+ * it is on.  Errors: EINVAL (points outside 0 or p+1..17, singular
+ * horizontal Jacobian), ENOMEM, ECUDA. */
+fnpf_status fnpf_set_dealias(fnpf_mesh* mesh, int points);
 
 /* Applies the filter set by fnpf_set_filter to one surface field f [Ns]
  * (device, in place), on `stream`.  Errors: EINVAL (no filter set). */

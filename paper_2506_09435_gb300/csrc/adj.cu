@@ -213,8 +213,8 @@ extern "C" fnpf_status fnpf_step_adjoint(fnpf_mesh* m, const double* eta_n, cons
                                          double* lam_phis_out, double* lam_h, double t, double dt, void* stream) {
   if (!m || !eta_n || !phis_n || !lam_eta || !lam_phis || !lam_eta_out || !lam_phis_out || !(dt > 0))
     return FNPF_EINVAL;
-  if (m->linear() || m->filter_on) {
-    m->err = "the adjoint step is built for FNPF_NONLINEAR without the modal filter";
+  if (m->linear() || m->filter_on || m->dealias_M > 0) {
+    m->err = "the adjoint step is built for FNPF_NONLINEAR without the modal filter or over-integration";
     return FNPF_EUNSUPPORTED;
   }
   cudaStream_t s = (cudaStream_t)stream;

@@ -88,7 +88,12 @@ fnpf_status fnpf_zakharov_rhs(fnpf_mesh* m, const double* eta, const double* phi
   a.w_in = w;
   a.deta = deta;
   a.dphis = dphis;
-  cudaError_t e = fnpf::launch_stage(m->g, m->tables(), a, (cudaStream_t)stream);
+  cudaError_t e = cudaSuccess;
+  if (m->dealias_M > 0 && !m->linear()) {
+    e = fnpf::enqueue_dealias_rhs(m, eta, phis, w, (cudaStream_t)stream);
+    a.rhs_in = fnpf::dealias_rhs(m);
+  }
+  if (e == cudaSuccess) e = fnpf::launch_stage(m->g, m->tables(), a, (cudaStream_t)stream);
   return e == cudaSuccess ? FNPF_OK : cuda_fail(m, e, "rhs");
 }
 
@@ -136,6 +141,17 @@ StageArgs stage_args(fnpf_mesh* m, double* eta, double* phis, const double* ce, 
   return a;
 }
 
+// The stage kernel, preceded (when set) by the over-integrated right-hand
+// side of the stage state, which it then reads.
+cudaError_t launch_stage_rhs(fnpf_mesh* m, StageArgs a, cudaStream_t s) {
+  if (m->dealias_M > 0 && !m->linear()) {
+    cudaError_t e = enqueue_dealias_rhs(m, a.eta, a.phis, nullptr, s);
+    if (e != cudaSuccess) return e;
+    a.rhs_in = dealias_rhs(m);
+  }
+  return launch_stage(m->g, m->tables(), a, s);
+}
+
 // Step 4.7 filtering of the new state (eta, phis) in place, through the free
 // stage buffers, when a filter is set.
 cudaError_t enqueue_filter_step(fnpf_mesh* m, double* eta, double* phis, cudaStream_t s) {
@@ -158,7 +174,7 @@ cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cud
     cudaError_t e = enqueue_solve_device(m, ce, cp, m->phi, m->stage_info + st, s, st == 0);
     if (e != cudaSuccess) return e;
     const StageArgs a = stage_args(m, eta, phis, ce, cp, st, 0.0, dt, m->t_dev);
-    if ((e = launch_stage(m->g, m->tables(), a, s)) != cudaSuccess) return e;
+    if ((e = launch_stage_rhs(m, a, s)) != cudaSuccess) return e;
     ce = a.out_eta;
     cp = a.out_phi;
   }
@@ -250,7 +266,7 @@ fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, dou
     fnpf_status r = fnpf::cg_solve(m, ce, cp, m->phi, info ? info + st : nullptr, s);
     if (r != FNPF_OK) return r;
     const fnpf::StageArgs a = fnpf::stage_args(m, eta, phis, ce, cp, st, t, dt, nullptr);
-    cudaError_t e = fnpf::launch_stage(m->g, m->tables(), a, s);
+    cudaError_t e = fnpf::launch_stage_rhs(m, a, s);
     m->launches += 1;
     if (e != cudaSuccess) return cuda_fail(m, e, "stage");
     ce = a.out_eta;

@@ -714,36 +714,43 @@ void launch_projection_k(int64_t n, const ProjBasis& B, const double* r, double*
   proj_combine_kernel<K><<<nb, NT, 0, s>>>(n, B, coef, x, q);
 }
 
-// Allocates the history (zeroed: zero vectors are dropped) at the first use.
-fnpf_status ensure_projection(fnpf_mesh* m) {
+// Allocates a history (zeroed: zero vectors are dropped) at its first use:
+// the forward solves' (adj = false) or the adjoint solves' (adj = true).
+fnpf_status ensure_projection(fnpf_mesh* m, bool adj) {
   const int L = m->opts.projection;
-  if (L <= 0 || m->proj_alloc >= L) return FNPF_OK;
-  if (m->projH) cudaFree(m->projH);
-  if (m->proj_part) cudaFree(m->proj_part);
-  m->projH = m->proj_part = nullptr;
-  m->proj_alloc = 0;
+  double*& Hbuf = adj ? m->projHa : m->projH;
+  int& alloc = adj ? m->proj_alloc_a : m->proj_alloc;
+  if (L <= 0 || alloc >= L) return FNPF_OK;
+  if (Hbuf) cudaFree(Hbuf);
+  Hbuf = nullptr;
+  alloc = 0;
   const size_t hbytes = (size_t)2 * L * m->g.NI * sizeof(double);
-  const size_t pbytes = ((size_t)kProjMaxNP * kVecBlocks + 16) * sizeof(double);
-  if (cudaMalloc((void**)&m->projH, std::max<size_t>(hbytes, 8)) != cudaSuccess ||
-      cudaMalloc((void**)&m->proj_part, pbytes) != cudaSuccess) {
-    if (m->projH) cudaFree(m->projH);
-    m->projH = nullptr;
+  if (cudaMalloc((void**)&Hbuf, std::max<size_t>(hbytes, 8)) != cudaSuccess) {
+    Hbuf = nullptr;
     m->err = "projection history: device allocation failed";
     return FNPF_ENOMEM;
   }
-  if (cudaMemset(m->projH, 0, hbytes) != cudaSuccess) return FNPF_ECUDA;
-  m->proj_alloc = L;
+  if (!m->proj_part) {
+    const size_t pbytes = ((size_t)kProjMaxNP * kVecBlocks + 16) * sizeof(double);
+    if (cudaMalloc((void**)&m->proj_part, pbytes) != cudaSuccess) {
+      m->proj_part = nullptr;
+      m->err = "projection history: device allocation failed";
+      return FNPF_ENOMEM;
+    }
+  }
+  if (cudaMemset(Hbuf, 0, hbytes) != cudaSuccess) return FNPF_ECUDA;
+  alloc = L;
   return FNPF_OK;
 }
 
-// Replaces x by the projected initial guess and q by A x (r holds -b).  The
+// Replaces x by the projected initial guess and q by A x (r holds -b), with
+// the history H ([2L][NI]: solutions, then their operator images).  The
 // caller's guess x is a basis vector when with_guess.
 cudaError_t enqueue_projection(fnpf_mesh* m, const Tables<double>& t, const double* eta, double* x, bool with_guess,
-                               cudaStream_t s) {
+                               double* H, cudaStream_t s) {
   const int L = m->opts.projection;
   if (L <= 0) return cudaSuccess;
   const int64_t NI = m->g.NI;
-  double* H = m->projH;
   double* AH = H + (int64_t)L * NI;
   for (int j = 0; j < L; ++j) {
     cudaError_t e = timed_apply<double>(m, t, eta, H + (int64_t)j * NI, nullptr, AH + (int64_t)j * NI, s, nullptr,
@@ -778,10 +785,10 @@ cudaError_t enqueue_projection(fnpf_mesh* m, const Tables<double>& t, const doub
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_projection_push(fnpf_mesh* m, const double* x, cudaStream_t s) {
+cudaError_t enqueue_projection_push(fnpf_mesh* m, const double* x, double* H, cudaStream_t s) {
   const int L = m->opts.projection;
   if (L <= 0) return cudaSuccess;
-  proj_push_kernel<<<vec_blocks(m->g.NI), NT, 0, s>>>(m->g.NI, L, m->projH, x);
+  proj_push_kernel<<<vec_blocks(m->g.NI), NT, 0, s>>>(m->g.NI, L, H, x);
   m->launches += 1;
   return cudaGetLastError();
 }
@@ -850,11 +857,14 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     FNPF_CK(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
   }
   FNPF_CK(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
-  const bool project = !rhs && m->opts.projection > 0;   // adjoint solves (rhs given) keep their guess
+  // forward solves project onto the forward history, adjoint solves (rhs
+  // given) onto their own
+  const bool project = m->opts.projection > 0;
+  double*& hist = rhs ? m->projHa : m->projH;
   if (project) {
-    const fnpf_status st = ensure_projection(m);
+    const fnpf_status st = ensure_projection(m, rhs != nullptr);
     if (st != FNPF_OK) return st;
-    FNPF_CK(enqueue_projection(m, t, eta, x, x != m->phi, s));
+    FNPF_CK(enqueue_projection(m, t, eta, x, x != m->phi, hist, s));
   }
   cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
                                    mixed ? m->b : nullptr, m->partials, nb);
@@ -873,7 +883,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     PcgBufs<double> B{eta, x, m->r, m->z, m->p, m->q, m->dinv, sc};
     fnpf_status st = pcg_loop<double>(m, t, B, max_iter, s, &h, &done);
     if (st != FNPF_OK) return st;
-    if (project) FNPF_CK(enqueue_projection_push(m, x, s));
+    if (project) FNPF_CK(enqueue_projection_push(m, x, hist, s));
     return finish(m, h, done, h.iters, 0, info, s);
   }
 
@@ -933,7 +943,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     m->launches += 3;
     ++outer;
   }
-  if (project) FNPF_CK(enqueue_projection_push(m, x, s));
+  if (project) FNPF_CK(enqueue_projection_push(m, x, hist, s));
   return finish(m, h, done, inner_total, outer, info, s);
 }
 
@@ -1080,7 +1090,7 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
   ENQ(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
   // the history buffers exist: a host-driven solve of the same options ran before
   const bool project = m->opts.projection > 0 && m->proj_alloc >= m->opts.projection;
-  if (project) ENQ(enqueue_projection(m, t, eta, x, x != m->phi, s));
+  if (project) ENQ(enqueue_projection(m, t, eta, x, x != m->phi, m->projH, s));
   cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
                                    mixed ? m->b : nullptr, m->partials, nb);
   if (!mixed && pmg) {
@@ -1154,7 +1164,7 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
       return cudaGetLastError();
     }));
   }
-  if (project) ENQ(enqueue_projection_push(m, x, s));
+  if (project) ENQ(enqueue_projection_push(m, x, m->projH, s));
   stage_info_kernel<<<1, 1, 0, s>>>(sc, m->inner_total, mixed ? 1 : 0, info_dev);
   m->g64_active = false;
   return cudaGetLastError();

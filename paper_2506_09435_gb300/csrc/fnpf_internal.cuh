@@ -229,6 +229,7 @@ struct StageArgs {
   double* deta;          // plain right-hand-side output (may be null)
   double* dphis;
   const double* w_in;    // if non-null, use this w instead of recovering it from phi
+  const double* rhs_in;  // if non-null (nonlinear model): the right-hand side [2][ns], precomputed
   int* status;           // set to FNPF_EDIVERGED on a non-finite or folded state
   // relaxation after the last stage (cr null: none)
   const double* cr;

@@ -210,7 +210,9 @@ void free_mesh(fnpf_mesh* m) {
   if (m->G64) cudaFree(m->G64);
   if (m->adj) cudaFree(m->adj);
   if (m->inv_work) cudaFree(m->inv_work);
+  if (m->dl_buf) cudaFree(m->dl_buf);
   if (m->projH) cudaFree(m->projH);
+  if (m->projHa) cudaFree(m->projHa);
   if (m->proj_part) cudaFree(m->proj_part);
   double* rptrs[] = {m->rx_cr, m->rx_gen, m->dxs, m->dys};
   for (double* p : rptrs)

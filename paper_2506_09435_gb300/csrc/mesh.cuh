@@ -83,6 +83,12 @@ struct fnpf_mesh {
   fnpf_relaxation relax{};          // scalar parameters (array pointers unused)
   bool relax_on = false;
 
+  // over-integrated right-hand side (fnpf_set_dealias): Gauss points per
+  // direction (0: off) and one buffer of tables, Gauss-point metric, element
+  // values, right-hand side and w (dealias.cu)
+  int dealias_M = 0;
+  double* dl_buf = nullptr;
+
   // modal filter (fnpf_set_filter): the 1D matrix V diag(sigma) V^-1, [n * n]
   double* dfilter = nullptr;
   bool filter_on = false;
@@ -92,8 +98,10 @@ struct fnpf_mesh {
   // history 0 = newest; proj_part: per-block partials of the Gram system, then
   // the coefficients
   double* projH = nullptr;
+  double* projHa = nullptr;         // the same for the adjoint solves
   double* proj_part = nullptr;
   int proj_alloc = 0;               // L the buffers were sized for
+  int proj_alloc_a = 0;
 
   // fnpf_invariants: A phi of the energy [N] (allocated at the first call)
   double* inv_work = nullptr;
@@ -167,6 +175,11 @@ int64_t graph_kernel_nodes(cudaGraph_t g);
 // Device-driven solve for graph capture (see cg.cu).
 cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const double* phis, double* x,
                                  StageInfo* info_dev, cudaStream_t s, bool estimate);
+// Over-integrated Zakharov right-hand side of (eta, phis) into dealias_rhs(m)
+// (w given, or recovered from m->phi when NULL) -- dealias.cu.
+cudaError_t enqueue_dealias_rhs(fnpf_mesh* m, const double* eta, const double* phis, const double* w,
+                                cudaStream_t s);
+const double* dealias_rhs(const fnpf_mesh* m);
 // CG solve of A_II x = -A_IS phis for the interior part x [NI] (in: initial guess),
 // or of A_II x = rhs when rhs [NI] is given (phis is then unused).
 fnpf_status cg_solve(fnpf_mesh* m, const double* eta, const double* phis, double* x, fnpf_solve_info* info,

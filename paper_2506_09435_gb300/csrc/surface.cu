@@ -84,13 +84,18 @@ __global__ void stage_kernel(Geom g, Tables<double> t, StageArgs a) {
   if (!(e0 + hh > 0.0) || !isfinite(e0) || !isfinite(a.phis[col])) {
     if (a.status) atomicExch(a.status, (int)FNPF_EDIVERGED);
   }
-  const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.geo ? a.geo : a.eta, col);
   double ke, kp;
-  if (a.linear) {
+  if (a.rhs_in && !a.linear) {
+    // over-integrated right-hand side (dealias.cu)
+    ke = a.rhs_in[col];
+    kp = a.rhs_in[g.ns + col];
+  } else if (a.linear) {
+    const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.geo ? a.geo : a.eta, col);
     // linear potential flow: the surface conditions linearised about z = 0
     ke = w;
     kp = -g.g * e0;
   } else {
+    const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.geo ? a.geo : a.eta, col);
     zakharov_node(g, t, a, col, ix, iy, w, e0, &ke, &kp);
   }
   if (a.deta) {

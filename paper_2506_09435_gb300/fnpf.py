@@ -78,6 +78,7 @@ def load():
         "fnpf_diagonal": [vp, vp, vp, vp],
         "fnpf_precond_apply": [vp, vp, vp, vp, vp],
         "fnpf_set_filter": [vp, ctypes.POINTER(Filter)],
+        "fnpf_set_dealias": [vp, ctypes.c_int],
         "fnpf_filter_apply": [vp, vp, vp],
         "fnpf_apply_f32": [vp, vp, vp, vp, vp],
         "fnpf_laplace_solve": [vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
@@ -311,6 +312,11 @@ class Mesh:
         """Modal filter of eta and phi after every RK4 step (alpha = 0: off)."""
         f = Filter(float(alpha), int(order), int(cutoff))
         self._check(_LIB.fnpf_set_filter(self._h, ctypes.byref(f)))
+
+    def set_dealias(self, points):
+        """Over-integrated Zakharov right-hand sides on `points` Gauss points per
+        direction (0: collocation)."""
+        self._check(_LIB.fnpf_set_dealias(self._h, int(points)))
 
     def filter_apply(self, f, stream=None):
         self._check(_LIB.fnpf_filter_apply(self._h, *self._args((f, "f", "s")), _stream(stream)))
