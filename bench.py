@@ -35,6 +35,7 @@ UNIT = "DOF·steps/s"
 WORKLOAD = "periodic-box-3d kh=2, 32x32x2 hex, GLL p=6, Airy H/L=0.05 + seeded spectrum, dt=T/100, rtol 1e-10"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz
+AXG_C2_DRAM_BYTES = 34.060544e6 + 768.0             # ncu dram__bytes_read.sum + dram__bytes_write.sum
 
 
 def measured_hbm_gbs():
@@ -493,8 +494,11 @@ def main_gb300(args):
     # 6 one-dimensional contractions (12 n^4 per element) + G . grad u (18 n^3)
     flops = (12 * n ** 4 + 18 * n ** 3) * E
     achieved = flops / (apply_ms * 1e-3) / 1e12
+    # dram bytes per application of axg_kernel<double,7,3,7> on this tank from one ncu capture
+    # of that kernel, valid while the autotuner picks that shape
+    traffic = AXG_C2_DRAM_BYTES if (mesh.get_shapes()[0] == 3 and n == 7 and d["nx"] == 32) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "axg_kernel<double,7,3,C> + ring_gather (one FP64 operator application, stored metric)",
                 "flops_per_application": flops,
                 "apply_ms": apply_ms, "applications": prof["apply_count"],
