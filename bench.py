@@ -499,7 +499,9 @@ def main_gb300(args):
     traffic = AXG_C2_DRAM_BYTES if (mesh.get_shapes()[0] == 3 and n == 7 and d["nx"] == 32) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "axg_kernel<double,7,3,C> + ring_gather (one FP64 operator application, stored metric)",
+                "kernel": ("axg_kernel<double,7,3,C>" if mesh.get_shapes()[0] < 4 else "axl_kernel<double,7,C,true>")
+                          + " + ring_gather (one FP64 operator application, stored metric), shape %d, C = %d"
+                          % (mesh.get_shapes()[0], mesh.get_shapes()[2]),
                 "flops_per_application": flops,
                 "apply_ms": apply_ms, "applications": prof["apply_count"],
                 "peak_note": "FP64 FMA peak derived from unit counts and max clock (152 SM x 2 DFMA/clk x "
@@ -619,6 +621,7 @@ def main_gb300(args):
                        "projection": args.projection,
                        "cta_shape": ("autotuned" if args.shape < 0 else "forced"),
                        "element_columns_per_cta": mesh.get_shapes()[2],
+                       "cta_shape_fp64": mesh.get_shapes()[0], "cta_shape_fp32": mesh.get_shapes()[1],
                        "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "cg_iters_per_solve_mean": statistics.mean(iters), "max_rel_res": rel_res,
