@@ -509,27 +509,61 @@ def main_gb300(args):
                 "bytes_per_application": 2 * 8 * mesh.N + 6 * 8 * E * n ** 3,
                 "hbm_frac_of_measured": (2 * 8 * mesh.N + 6 * 8 * E * n ** 3) / (apply_ms * 1e-3) / 1e9 / measured_hbm_gbs()}
 
-    # --- adjoint step (reverse mode, FP64, same mesh and state) against the forward step
+    # --- adjoint (reverse mode, FP64, same mesh): K forward steps recording the tape (the
+    #     recompute of a checkpointed gradient), the K taped reverse steps, and the adjoint
+    #     that recomputes its step, each over the same sequence of states in reverse order
     adjoint = None
     if not args.no_adjoint and args.model == "fnpf":   # the adjoint is built for the nonlinear model
+        K = max(2, args.steps // 2)
+
+        def ev_pair():
+            return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        states, fwd_t, rev_t, rec_t = [], [], [], []
+        mesh.tape_begin(K)
+        for k in range(K):
+            states.append((eta.clone(), phis.clone(), t))
+            flush.zero_()
+            a_, b_ = ev_pair()
+            a_.record(stream)
+            mesh.rk4_step(eta, phis, t, dt)
+            b_.record(stream)
+            fwd_t.append((a_, b_))
+            t += dt
+        mesh.tape_end()
         le = torch.ones(mesh.ns, dtype=torch.float64, device=dev) / mesh.ns
         lp = torch.zeros_like(le)
-        oe, op_ = torch.empty_like(le), torch.empty_like(le)
         lh = torch.zeros_like(le)
-        mesh.step_adjoint(eta, phis, le, lp, oe, op_, lh, t, dt)      # workspace allocation, warm
-        torch.cuda.synchronize()
-        aev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(max(1, args.steps // 2))]
-        for a_, b_ in aev:
+        for k in reversed(range(K)):
             flush.zero_()
+            a_, b_ = ev_pair()
             a_.record(stream)
-            mesh.step_adjoint(eta, phis, le, lp, oe, op_, lh, t, dt)
+            mesh.step_adjoint_taped(k, le, lp, le, lp, lh, dt)
             b_.record(stream)
+            rev_t.append((a_, b_))
+        le2 = torch.ones(mesh.ns, dtype=torch.float64, device=dev) / mesh.ns
+        lp2, lh2 = torch.zeros_like(le2), torch.zeros_like(le2)
+        for k in reversed(range(K)):
+            es, ps, tk = states[k]
+            flush.zero_()
+            a_, b_ = ev_pair()
+            a_.record(stream)
+            mesh.step_adjoint(es, ps, le2, lp2, le2, lp2, lh2, tk, dt)
+            b_.record(stream)
+            rec_t.append((a_, b_))
         torch.cuda.synchronize()
-        adj_ms = statistics.mean(a_.elapsed_time(b_) for a_, b_ in aev)
-        adjoint = {"ms_per_step": adj_ms, "ratio_to_forward": adj_ms / (total_ms / args.steps),
-                   "note": "recomputes the step's four forward solves (host-driven) and runs four adjoint "
-                           "solves plus the vector-Jacobian products; forward = the timed graph-replayed step"}
+        ms = lambda evs: statistics.mean(x.elapsed_time(y) for x, y in evs)
+        fwd_step = total_ms / args.steps
+        tape_ms, rev_ms, rec_ms = ms(fwd_t), ms(rev_t), ms(rec_t)
+        grad_diff = float(torch.linalg.norm(le - le2) / torch.linalg.norm(le2))
+        adjoint = {"ms_per_step": rev_ms, "tape_forward_ms_per_step": tape_ms,
+                   "ratio_to_forward": (tape_ms + rev_ms) / fwd_step,
+                   "reverse_only_ratio": rev_ms / fwd_step,
+                   "recomputing_adjoint_ms_per_step": rec_ms, "recomputing_ratio": rec_ms / fwd_step,
+                   "taped_vs_recomputing_rel_l2": grad_diff, "steps": K,
+                   "note": "ratio_to_forward = (forward step recording the tape + taped reverse step) / "
+                           "graph-replayed forward step: the cost per step of a checkpointed gradient beyond "
+                           "its forward run; recomputing = fnpf_step_adjoint, which re-solves the step itself"}
 
     # --- end to end through the public API: pinned host state in, step, state out
     eta_h = torch.empty(mesh.ns, dtype=torch.float64, pin_memory=True)
@@ -720,15 +754,18 @@ def main_ensemble(args):
     opts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=1e-5,
                              cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
                              coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
-                             cheb_range=args.cheb_range, max_iter=50000)
-    meshes, etas, phiss, dts = [], [], [], []
+                             cheb_range=args.cheb_range, max_iter=50000, projection=args.projection)
+    meshes, etas, phiss, dts, init = [], [], [], [], []
     for d in tanks:
         ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"]
         m = fnpf.Mesh(3, d["nx"], d["ny"], 2, d["p"], True, True, np.full(ncx * ncy, d["h0"]), Lx=d["Lx"],
                       Ly=d["Ly"], g=d["g"], opts=opts)
+        if args.shape >= 0:
+            m.set_shapes(args.shape, args.shape)
         x, y = m.surface_coords()
         e0, p0 = W.airy_plus_spectrum_state(d, x, y, seed=d["seed"], steepness=d["steepness"])
         meshes.append(m)
+        init.append((e0, p0))
         etas.append(torch.tensor(e0, dtype=torch.float64, device=dev))
         phiss.append(torch.tensor(p0, dtype=torch.float64, device=dev))
         dts.append(W.period(d["k"], d["h0"], d["g"]) / 100)
@@ -740,6 +777,7 @@ def main_ensemble(args):
         ens.rk4_step(etas, phiss, [k * dt for k, dt in zip(steps, dts)], dts)
         steps = [k + 1 for k in steps]
     torch.cuda.synchronize()
+    n_warm = steps[0]
     for m in meshes:
         m.profile_read(reset=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -753,6 +791,23 @@ def main_ensemble(args):
         torch.cuda.synchronize()
     ens_ms = sum(a.elapsed_time(b) for a, b in ev)
     launches = sum(m.profile_read(reset=True)["launches"] for m in meshes)
+    # error of the batched mixed-precision states against the FP64 path: every tank
+    # stepped in FP64 from the same initial state for the same steps, one at a time
+    n_done = steps[0]
+    err = []
+    o64 = fnpf.default_opts(precond=fnpf.FNPF_PMG, rtol=args.rtol, max_iter=50000, projection=args.projection)
+    for d, (e0, p0), e_b, p_b, dt in zip(tanks, init, etas, phiss, dts):
+        ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"]
+        m64 = fnpf.Mesh(3, d["nx"], d["ny"], 2, d["p"], True, True, np.full(ncx * ncy, d["h0"]), Lx=d["Lx"],
+                        Ly=d["Ly"], g=d["g"], opts=o64)
+        e64 = torch.tensor(e0, dtype=torch.float64, device=dev)
+        p64 = torch.tensor(p0, dtype=torch.float64, device=dev)
+        for k in range(n_done):
+            m64.rk4_step(e64, p64, k * dt, dt)
+        err.append(max(float(torch.linalg.norm(e_b - e64) / torch.linalg.norm(e64)),
+                       float(torch.linalg.norm(p_b - p64) / torch.linalg.norm(p64))))
+        del m64
+    torch.cuda.synchronize()
     # the same tanks, one launch (captured step graph) at a time
     for m, e, p, dt, s_ in zip(meshes, etas, phiss, dts, steps):
         m.rk4_step(e, p, s_ * dt, dt)           # warm the single-tank graphs
@@ -774,6 +829,8 @@ def main_ensemble(args):
         "speedup_vs_one_at_a_time": one_ms / ens_ms, "tanks": len(meshes), "total_dof": ndof,
         "ms_per_ensemble_step": ens_ms / args.steps, "steps": args.steps, "dtype": "f32 inner / f64 outer",
         "orders": sorted(set(d["p"] for d in tanks)), "finite": ok, "gpu_launches": launches,
+        "launches_per_ensemble_step": launches / args.steps,
+        "rel_l2_vs_fp64_path_max_over_tanks": max(err), "steps_compared": n_done, "projection": args.projection,
         "clocks": clk.summary(), "data": "synthetic"}))
     return 0
 
@@ -953,11 +1010,17 @@ def main_cylinder(args):
         return statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev)
 
     fwd_ms = timed(lambda: mesh.rk4_step(eta, phis, t, dt), args.steps)
+    # adjoint steps over a sequence of states in reverse order (as in a gradient): K forward
+    # steps recording the tape, then the K taped reverse steps
+    K = max(2, args.steps // 2)
+    mesh.tape_begin(K)
+    tape_ms = timed(lambda: mesh.rk4_step(eta, phis, t, dt), K)
+    mesh.tape_end()
     le = torch.ones(mesh.ns, dtype=torch.float64, device=dev) / mesh.ns
     lp = torch.zeros_like(le)
-    oe, op_, lh = torch.empty_like(le), torch.empty_like(le), torch.zeros_like(le)
-    mesh.step_adjoint(eta, phis, le, lp, oe, op_, lh, t, dt)
-    adj_ms = timed(lambda: mesh.step_adjoint(eta, phis, le, lp, oe, op_, lh, t, dt), max(1, args.steps // 2))
+    lh = torch.zeros_like(le)
+    slots = list(reversed(range(K)))
+    adj_ms = timed(lambda: mesh.step_adjoint_taped(slots.pop(0), le, lp, le, lp, lh, dt), K)
     # checkpointed gradient of J = sum eta_N^2 over 32 steps, checkpoints every 16
     e0 = eta.detach().clone().requires_grad_(True)
     p0 = phis.detach().clone().requires_grad_(True)
@@ -973,7 +1036,8 @@ def main_cylinder(args):
     finite = bool(torch.isfinite(e0.grad).all() and torch.isfinite(p0.grad).all() and torch.isfinite(ht.grad).all())
     print(json.dumps({"mode": "cylinder", "workload": "cylinder O-grid 64x24x3, p=4, ka=kh=1, R=10a, sponge ring",
                       "dof": mesh.N, "forward_ms_per_step": fwd_ms, "adjoint_ms_per_step": adj_ms,
-                      "adjoint_ratio_to_forward": adj_ms / fwd_ms,
+                      "tape_forward_ms_per_step": tape_ms,
+                      "adjoint_ratio_to_forward": (tape_ms + adj_ms) / fwd_ms,
                       "checkpointed_gradient": {"steps": 32, "every": 16, "forward_s": w1 - w0,
                                                 "backward_s": w2 - w1, "ratio": (w2 - w1) / (w1 - w0),
                                                 "finite": finite},

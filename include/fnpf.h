@@ -399,6 +399,26 @@ fnpf_status fnpf_invariants(fnpf_mesh* mesh, const double* eta, const double* ph
  * Errors: EINVAL (blocks or iters < 1, out NULL, other precision), ECUDA. */
 fnpf_status fnpf_fma_probe(int precision, int blocks, int iters, void* out, double* flops, void* stream);
 
+/* Tape of forward steps for the adjoint (the checkpointed reverse sweep of the
+ * differentiation form built around the paper's RK4 step, Sec. 3.2).  After
+ * fnpf_tape_begin(mesh, capacity), every successful fnpf_rk4_step records the
+ * four stage states and stage potentials of the step into the next slot
+ * (0, 1, ...; capacity slots of 4 N_I + 8 Ns doubles, allocated here; a step
+ * beyond the capacity fails with EINVAL) until fnpf_tape_end.  Both invalidate
+ * the captured step graph once (recording is part of the capture).
+ * fnpf_step_adjoint_taped then runs the reverse sweep of fnpf_step_adjoint for
+ * the step recorded in `slot` without recomputing its forward solves: the same
+ * result up to the solver tolerance, at the cost of the four adjoint solves and
+ * the vector-Jacobian products.  The tape holds the slots until the next
+ * fnpf_tape_begin.  Errors: EINVAL (NULL, capacity < 1, slot not recorded
+ * since the last fnpf_tape_begin), ENOMEM, EUNSUPPORTED (as
+ * fnpf_step_adjoint), ECUDA. */
+fnpf_status fnpf_tape_begin(fnpf_mesh* mesh, int capacity);
+fnpf_status fnpf_tape_end(fnpf_mesh* mesh);
+fnpf_status fnpf_step_adjoint_taped(fnpf_mesh* mesh, int slot, const double* lam_eta, const double* lam_phis,
+                                    double* lam_eta_out, double* lam_phis_out, double* lam_h, double dt,
+                                    void* stream);
+
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */
 const char* fnpf_last_error(const fnpf_mesh* mesh);

@@ -2,9 +2,11 @@
 
 Forward: `nsteps` calls of fnpf_rk4_step on one work buffer, storing (eta,
 phi_eta) every `every` steps.  Backward: for each segment, newest first, the
-segment is recomputed from its checkpoint (keeping each step's input state) and
-fnpf_step_adjoint runs over its steps in reverse, accumulating dJ/dh.  Every
-computation runs in libfnpf's kernels; this module only orders the calls.
+segment is recomputed from its checkpoint with the mesh's tape recording the
+stage states and potentials of each step (fnpf_tape_begin), and
+fnpf_step_adjoint_taped runs over its steps in reverse, accumulating dJ/dh, so
+no forward solve is repeated inside the adjoint steps.  Every computation runs
+in libfnpf's kernels; this module only orders the calls.
 """
 import torch
 
@@ -35,14 +37,14 @@ class RK4Run(torch.autograd.Function):
             n1 = min(n0 + every, nsteps)
             work_e.copy_(e0)
             work_p.copy_(p0)
-            states = []
-            for n in range(n0, n1):
-                states.append((work_e.clone(), work_p.clone()))
-                if n + 1 < n1:
+            mesh.tape_begin(n1 - n0)
+            try:
+                for n in range(n0, n1):
                     mesh.rk4_step(work_e, work_p, t0 + n * dt, dt)
+            finally:
+                mesh.tape_end()
             for n in reversed(range(n0, n1)):
-                es, ps = states[n - n0]
-                mesh.step_adjoint(es, ps, lam_e, lam_p, lam_e, lam_p, lam_h, t0 + n * dt, dt)
+                mesh.step_adjoint_taped(n - n0, lam_e, lam_p, lam_e, lam_p, lam_h, dt)
         return lam_e, lam_p, lam_h, None, None, None, None, None
 
 

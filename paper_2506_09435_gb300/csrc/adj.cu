@@ -208,19 +208,38 @@ __global__ void sub_kernel(int n, const double* x, double* y) {
 
 using fnpf::Geom;
 
-extern "C" fnpf_status fnpf_step_adjoint(fnpf_mesh* m, const double* eta_n, const double* phis_n,
-                                         const double* lam_eta, const double* lam_phis, double* lam_eta_out,
-                                         double* lam_phis_out, double* lam_h, double t, double dt, void* stream) {
-  if (!m || !eta_n || !phis_n || !lam_eta || !lam_phis || !lam_eta_out || !lam_phis_out || !(dt > 0))
-    return FNPF_EINVAL;
+namespace {
+
+// Tape slot layout: [4][NI] stage potentials (interior), then [4][2][ns] stage states.
+inline int64_t tape_stride(const Geom& g) { return 4 * g.NI + 8 * (int64_t)g.ns; }
+
+__global__ void tape_record_kernel(int64_t NI, int ns, const int* slot, int cap, double* tape, int64_t stride, int st,
+                                   const double* phi, const double* ce, const double* cp) {
+  const int k = *slot;
+  if (k < 0 || k >= cap) return;
+  double* base = tape + (int64_t)k * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NI; i += (int64_t)gridDim.x * blockDim.x)
+    base[(int64_t)st * NI + i] = phi[i];
+  double* Y = base + 4 * NI;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
+    Y[(int64_t)(2 * st) * ns + i] = ce[i];
+    Y[(int64_t)(2 * st + 1) * ns + i] = cp[i];
+  }
+}
+
+fnpf_status check_adjoint_supported(fnpf_mesh* m) {
   if (m->linear() || m->filter_on || m->dealias_M > 0) {
     m->err = "the adjoint step is built for FNPF_NONLINEAR without the modal filter or over-integration";
     return FNPF_EUNSUPPORTED;
   }
-  cudaStream_t s = (cudaStream_t)stream;
+  return FNPF_OK;
+}
+
+// The adjoint workspace (stage data of the recompute, reverse-sweep scratch),
+// allocated at the first use.
+fnpf_status ensure_adj(fnpf_mesh* m) {
   const Geom& g = m->g;
   const int64_t ns = g.ns, NI = g.NI, LS = (int64_t)g.n_ecol * g.lines;
-  // workspace layout (doubles)
   const int64_t n_phi = 4 * NI, n_y = 8 * ns, n_k = 8 * ns, n_surf = 10 * ns, n_eb = 6 * LS, n_lb = 5 * LS;
   const int64_t n_vol = 3 * NI;
   const size_t bytes = (size_t)(n_phi + n_y + n_k + n_surf + n_eb + n_lb + n_vol) * sizeof(double);
@@ -234,15 +253,23 @@ extern "C" fnpf_status fnpf_step_adjoint(fnpf_mesh* m, const double* eta_n, cons
     }
     m->adj_bytes = bytes;
   }
-  double* Phi = m->adj;                         // [4][NI] stage potentials (interior)
-  double* Y = Phi + n_phi;                      // [4][2][ns] stage states (eta, phis)
-  double* KB = Y + n_y;                         // [4][2][ns] kbar
-  double* S = KB + n_k;                         // surface scratch
-  double* fe = S, *fp = S + ns, *oute = S + 2 * ns, *outp = S + 3 * ns, *ebar = S + 4 * ns, *pbar = S + 5 * ns,
-         *wbar = S + 6 * ns, *hbar = S + 7 * ns, *wv = S + 8 * ns, *ysurf = S + 9 * ns;
-  double* EB = S + n_surf;
-  double* LB = EB + n_eb;
-  double* badj = LB + n_lb;
+  return FNPF_OK;
+}
+
+// Reverse sweep of one RK4 step from the stage potentials Phi [4][NI] and
+// stage states Y [4][2][ns] of the forward step.
+fnpf_status adjoint_reverse(fnpf_mesh* m, const double* Phi, const double* Y, const double* lam_eta,
+                            const double* lam_phis, double* lam_eta_out, double* lam_phis_out, double* lam_h,
+                            double dt, cudaStream_t s) {
+  const Geom& g = m->g;
+  const int64_t ns = g.ns, NI = g.NI, LS = (int64_t)g.n_ecol * g.lines;
+  double* KB = m->adj + 4 * NI + 8 * ns;        // [4][2][ns] kbar
+  double* S = KB + 8 * ns;                      // surface scratch
+  double* oute = S + 2 * ns, *outp = S + 3 * ns, *ebar = S + 4 * ns, *pbar = S + 5 * ns, *wbar = S + 6 * ns,
+         *hbar = S + 7 * ns, *wv = S + 8 * ns, *ysurf = S + 9 * ns;
+  double* EB = S + 10 * ns;
+  double* LB = EB + 6 * LS;
+  double* badj = LB + 5 * LS;
   double* psi = badj + NI;
   double* tmp = psi + NI;
   const fnpf::Tables<double> tb = m->tables();
@@ -255,23 +282,6 @@ extern "C" fnpf_status fnpf_step_adjoint(fnpf_mesh* m, const double* eta_n, cons
       return FNPF_ECUDA;                                              \
     }                                                                 \
   } while (0)
-  // ---- forward recompute from y_n, storing Y_s and phi_s
-  ACK(cudaMemcpyAsync(fe, eta_n, ns * 8, cudaMemcpyDeviceToDevice, s));
-  ACK(cudaMemcpyAsync(fp, phis_n, ns * 8, cudaMemcpyDeviceToDevice, s));
-  const double* ce = fe;
-  const double* cp = fp;
-  for (int st = 0; st < 4; ++st) {
-    ACK(cudaMemcpyAsync(Y + (2 * st) * ns, ce, ns * 8, cudaMemcpyDeviceToDevice, s));
-    ACK(cudaMemcpyAsync(Y + (2 * st + 1) * ns, cp, ns * 8, cudaMemcpyDeviceToDevice, s));
-    fnpf_status r = fnpf::cg_solve(m, ce, cp, m->phi, nullptr, s);
-    if (r != FNPF_OK) return r;
-    ACK(cudaMemcpyAsync(Phi + st * NI, m->phi, NI * 8, cudaMemcpyDeviceToDevice, s));
-    fnpf::StageArgs a = fnpf::stage_args(m, fe, fp, ce, cp, st, t, dt, nullptr);
-    a.cr = nullptr;   // the relaxation of y_{n+1} is not needed: only its Jacobian enters
-    ACK(fnpf::launch_stage(g, tb, a, s));
-    ce = a.out_eta;
-    cp = a.out_phi;
-  }
   // ---- reverse sweep
   const double* cr = m->relax_on ? m->rx_cr : nullptr;
   fnpf::scale_kernel<<<sb, fnpf::TB, 0, s>>>((int)ns, lam_eta, cr, 1.0, oute);
@@ -319,4 +329,115 @@ extern "C" fnpf_status fnpf_step_adjoint(fnpf_mesh* m, const double* eta_n, cons
   ACK(cudaGetLastError());
 #undef ACK
   return FNPF_OK;
+}
+
+}  // namespace
+
+cudaError_t fnpf::enqueue_tape_record(fnpf_mesh* m, int st, const double* ce, const double* cp, cudaStream_t s) {
+  const Geom& g = m->g;
+  tape_record_kernel<<<fnpf::kVecBlocks, 256, 0, s>>>(g.NI, g.ns, m->tape_slot_dev, m->tape_cap, m->tape,
+                                                      tape_stride(g), st, m->phi, ce, cp);
+  m->launches += 1;
+  return cudaGetLastError();
+}
+
+extern "C" fnpf_status fnpf_step_adjoint(fnpf_mesh* m, const double* eta_n, const double* phis_n,
+                                         const double* lam_eta, const double* lam_phis, double* lam_eta_out,
+                                         double* lam_phis_out, double* lam_h, double t, double dt, void* stream) {
+  if (!m || !eta_n || !phis_n || !lam_eta || !lam_phis || !lam_eta_out || !lam_phis_out || !(dt > 0))
+    return FNPF_EINVAL;
+  fnpf_status st0 = check_adjoint_supported(m);
+  if (st0 == FNPF_OK) st0 = ensure_adj(m);
+  if (st0 != FNPF_OK) return st0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geom& g = m->g;
+  const int64_t ns = g.ns, NI = g.NI;
+  double* Phi = m->adj;                         // [4][NI] stage potentials (interior)
+  double* Y = Phi + 4 * NI;                     // [4][2][ns] stage states (eta, phis)
+  double* S = Y + 16 * ns;                      // surface scratch (after the kbar block)
+  double* fe = S, *fp = S + ns;
+  const fnpf::Tables<double> tb = m->tables();
+  cudaError_t e = cudaSuccess;
+#define ACK(call)                                                     \
+  do {                                                                \
+    if ((e = (call)) != cudaSuccess) {                                \
+      m->err = std::string("adjoint: ") + cudaGetErrorString(e);     \
+      return FNPF_ECUDA;                                              \
+    }                                                                 \
+  } while (0)
+  // ---- forward recompute from y_n, storing Y_s and phi_s
+  ACK(cudaMemcpyAsync(fe, eta_n, ns * 8, cudaMemcpyDeviceToDevice, s));
+  ACK(cudaMemcpyAsync(fp, phis_n, ns * 8, cudaMemcpyDeviceToDevice, s));
+  const double* ce = fe;
+  const double* cp = fp;
+  for (int st = 0; st < 4; ++st) {
+    ACK(cudaMemcpyAsync(Y + (2 * st) * ns, ce, ns * 8, cudaMemcpyDeviceToDevice, s));
+    ACK(cudaMemcpyAsync(Y + (2 * st + 1) * ns, cp, ns * 8, cudaMemcpyDeviceToDevice, s));
+    fnpf_status r = fnpf::cg_solve(m, ce, cp, m->phi, nullptr, s);
+    if (r != FNPF_OK) return r;
+    ACK(cudaMemcpyAsync(Phi + st * NI, m->phi, NI * 8, cudaMemcpyDeviceToDevice, s));
+    fnpf::StageArgs a = fnpf::stage_args(m, fe, fp, ce, cp, st, t, dt, nullptr);
+    a.cr = nullptr;   // the relaxation of y_{n+1} is not needed: only its Jacobian enters
+    ACK(fnpf::launch_stage(g, tb, a, s));
+    ce = a.out_eta;
+    cp = a.out_phi;
+  }
+#undef ACK
+  return adjoint_reverse(m, Phi, Y, lam_eta, lam_phis, lam_eta_out, lam_phis_out, lam_h, dt, s);
+}
+
+extern "C" fnpf_status fnpf_tape_begin(fnpf_mesh* m, int capacity) {
+  if (!m || capacity < 1) return FNPF_EINVAL;
+  const Geom& g = m->g;
+  if (!m->tape_slot_dev) {
+    if (cudaMalloc((void**)&m->tape_slot_dev, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&m->tape_slot_host, sizeof(int)) != cudaSuccess) {
+      m->err = "tape: allocation failed";
+      return FNPF_ENOMEM;
+    }
+  }
+  if (m->tape_cap < capacity) {
+    if (m->tape) cudaFree(m->tape);
+    m->tape = nullptr;
+    m->tape_cap = 0;
+    if (cudaMalloc((void**)&m->tape, (size_t)capacity * tape_stride(g) * sizeof(double)) != cudaSuccess) {
+      m->tape = nullptr;
+      m->err = "tape: device allocation failed";
+      return FNPF_ENOMEM;
+    }
+    m->tape_cap = capacity;
+  }
+  if (!m->tape_on && m->step_exec) {   // the captured step gains the tape kernels
+    cudaGraphExecDestroy(m->step_exec);
+    m->step_exec = nullptr;
+  }
+  m->tape_on = true;
+  m->tape_next = 0;
+  return FNPF_OK;
+}
+
+extern "C" fnpf_status fnpf_tape_end(fnpf_mesh* m) {
+  if (!m) return FNPF_EINVAL;
+  if (m->tape_on && m->step_exec) {
+    cudaGraphExecDestroy(m->step_exec);
+    m->step_exec = nullptr;
+  }
+  m->tape_on = false;
+  return FNPF_OK;
+}
+
+extern "C" fnpf_status fnpf_step_adjoint_taped(fnpf_mesh* m, int slot, const double* lam_eta, const double* lam_phis,
+                                               double* lam_eta_out, double* lam_phis_out, double* lam_h, double dt,
+                                               void* stream) {
+  if (!m || !lam_eta || !lam_phis || !lam_eta_out || !lam_phis_out || !(dt > 0)) return FNPF_EINVAL;
+  if (slot < 0 || slot >= m->tape_next || slot >= m->tape_cap || !m->tape) {
+    m->err = "tape slot not recorded";
+    return FNPF_EINVAL;
+  }
+  fnpf_status st0 = check_adjoint_supported(m);
+  if (st0 == FNPF_OK) st0 = ensure_adj(m);
+  if (st0 != FNPF_OK) return st0;
+  const double* base = m->tape + (int64_t)slot * tape_stride(m->g);
+  return adjoint_reverse(m, base, base + 4 * m->g.NI, lam_eta, lam_phis, lam_eta_out, lam_phis_out, lam_h, dt,
+                         (cudaStream_t)stream);
 }

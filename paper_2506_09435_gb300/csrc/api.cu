@@ -173,6 +173,7 @@ cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cud
   for (int st = 0; st < 4; ++st) {
     cudaError_t e = enqueue_solve_device(m, ce, cp, m->phi, m->stage_info + st, s, st == 0);
     if (e != cudaSuccess) return e;
+    if (m->tape_on && (e = enqueue_tape_record(m, st, ce, cp, s)) != cudaSuccess) return e;
     const StageArgs a = stage_args(m, eta, phis, ce, cp, st, 0.0, dt, m->t_dev);
     if ((e = launch_stage_rhs(m, a, s)) != cudaSuccess) return e;
     ce = a.out_eta;
@@ -237,12 +238,11 @@ bool graph_mode(const fnpf_mesh* m) { return m->opts.use_graphs && !m->prof_on &
 
 }  // namespace fnpf
 
-extern "C" {
+namespace fnpf {
 
-fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, double dt, fnpf_solve_info* info,
-                          void* stream) {
-  if (!m || !eta || !phis || !(dt > 0) || !isfinite(dt)) return FNPF_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
+// The RK4 step of fnpf_rk4_step (graph replay or host-driven).
+fnpf_status rk4_step_run(fnpf_mesh* m, double* eta, double* phis, double t, double dt, fnpf_solve_info* info,
+                              cudaStream_t s) {
   if (fnpf::graph_mode(m)) {
     // one replay of the captured step: no host work between the kernels
     if (!m->step_exec || m->step_key[0] != eta || m->step_key[1] != phis || m->step_dt != dt) {
@@ -265,6 +265,10 @@ fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, dou
   for (int st = 0; st < 4; ++st) {
     fnpf_status r = fnpf::cg_solve(m, ce, cp, m->phi, info ? info + st : nullptr, s);
     if (r != FNPF_OK) return r;
+    if (m->tape_on) {
+      cudaError_t e = fnpf::enqueue_tape_record(m, st, ce, cp, s);
+      if (e != cudaSuccess) return cuda_fail(m, e, "tape");
+    }
     const fnpf::StageArgs a = fnpf::stage_args(m, eta, phis, ce, cp, st, t, dt, nullptr);
     cudaError_t e = fnpf::launch_stage_rhs(m, a, s);
     m->launches += 1;
@@ -276,6 +280,29 @@ fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, dou
   if (e != cudaSuccess) return cuda_fail(m, e, "filter");
   m->warm = true;
   return FNPF_OK;
+}
+
+}  // namespace fnpf
+
+extern "C" {
+
+fnpf_status fnpf_rk4_step(fnpf_mesh* m, double* eta, double* phis, double t, double dt, fnpf_solve_info* info,
+                          void* stream) {
+  if (!m || !eta || !phis || !(dt > 0) || !isfinite(dt)) return FNPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m->tape_on) {
+    // the slot this step records into, read on the device by the tape kernels
+    if (m->tape_next >= m->tape_cap) {
+      m->err = "tape full: fnpf_tape_begin with more slots";
+      return FNPF_EINVAL;
+    }
+    *m->tape_slot_host = m->tape_next;
+    cudaError_t e = cudaMemcpyAsync(m->tape_slot_dev, m->tape_slot_host, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(m, e, "tape slot");
+  }
+  fnpf_status done = fnpf::rk4_step_run(m, eta, phis, t, dt, info, s);
+  if (done == FNPF_OK && m->tape_on) ++m->tape_next;
+  return done;
 }
 
 fnpf_status fnpf_set_relaxation(fnpf_mesh* m, const fnpf_relaxation* r) {

@@ -212,6 +212,9 @@ void free_mesh(fnpf_mesh* m) {
   if (m->inv_work) cudaFree(m->inv_work);
   if (m->dl_buf) cudaFree(m->dl_buf);
   if (m->projH) cudaFree(m->projH);
+  if (m->tape) cudaFree(m->tape);
+  if (m->tape_slot_dev) cudaFree(m->tape_slot_dev);
+  if (m->tape_slot_host) cudaFreeHost(m->tape_slot_host);
   if (m->projHa) cudaFree(m->projHa);
   if (m->proj_part) cudaFree(m->proj_part);
   double* rptrs[] = {m->rx_cr, m->rx_gen, m->dxs, m->dys};

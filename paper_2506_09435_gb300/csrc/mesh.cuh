@@ -106,6 +106,16 @@ struct fnpf_mesh {
   // fnpf_invariants: A phi of the energy [N] (allocated at the first call)
   double* inv_work = nullptr;
 
+  // tape of forward steps for the adjoint (fnpf_tape_begin): per slot the four
+  // stage potentials [4][NI] and stage states [4][2][ns]; the slot a step
+  // records into is read on the device from tape_slot_dev (graph replays)
+  double* tape = nullptr;
+  int tape_cap = 0;                 // slots allocated
+  bool tape_on = false;
+  int tape_next = 0;                // slot of the next recorded step
+  int* tape_slot_dev = nullptr;
+  int* tape_slot_host = nullptr;    // pinned
+
   // adjoint step workspaces (allocated at the first fnpf_step_adjoint)
   double* adj = nullptr;            // one block holding all of them
   size_t adj_bytes = 0;
@@ -175,6 +185,9 @@ int64_t graph_kernel_nodes(cudaGraph_t g);
 // Device-driven solve for graph capture (see cg.cu).
 cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const double* phis, double* x,
                                  StageInfo* info_dev, cudaStream_t s, bool estimate);
+// Tape recording of stage st (potential m->phi and stage state ce, cp) into the
+// slot *m->tape_slot_dev (adj.cu).
+cudaError_t enqueue_tape_record(fnpf_mesh* m, int st, const double* ce, const double* cp, cudaStream_t s);
 // Over-integrated Zakharov right-hand side of (eta, phis) into dealias_rhs(m)
 // (w given, or recovered from m->phi when NULL) -- dealias.cu.
 cudaError_t enqueue_dealias_rhs(fnpf_mesh* m, const double* eta, const double* phis, const double* w,

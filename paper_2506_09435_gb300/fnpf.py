@@ -91,6 +91,9 @@ def load():
         "fnpf_fma_probe": [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double), vp],
         "fnpf_set_relaxation": [vp, ctypes.POINTER(Relaxation)],
         "fnpf_step_adjoint": [vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp],
+        "fnpf_tape_begin": [vp, ctypes.c_int],
+        "fnpf_tape_end": [vp],
+        "fnpf_step_adjoint_taped": [vp, ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_double, vp],
         "fnpf_ensemble_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
@@ -379,6 +382,21 @@ class Mesh:
         self._check(_LIB.fnpf_invariants(self._h, *a, ctypes.byref(ms), ctypes.byref(en), None,
                                          _stream(stream)))
         return ms.value, en.value
+
+    def tape_begin(self, capacity):
+        """Record the stage data of the next `capacity` RK4 steps (slots 0, 1, ...)."""
+        self._check(_LIB.fnpf_tape_begin(self._h, int(capacity)))
+
+    def tape_end(self):
+        self._check(_LIB.fnpf_tape_end(self._h))
+
+    def step_adjoint_taped(self, slot, lam_eta, lam_phis, lam_eta_out, lam_phis_out, lam_h=None, dt=0.01,
+                           stream=None):
+        """fnpf_step_adjoint for the step recorded in tape slot `slot` (no forward recompute)."""
+        args = self._args(*[(t_, n_, "s") for t_, n_ in ((lam_eta, "lam_eta"), (lam_phis, "lam_phis"),
+                                                          (lam_eta_out, "lam_eta_out"),
+                                                          (lam_phis_out, "lam_phis_out"), (lam_h, "lam_h"))])
+        self._check(_LIB.fnpf_step_adjoint_taped(self._h, int(slot), *args, float(dt), _stream(stream)))
 
     def set_shapes(self, variant64, variant32):
         self._check(_LIB.fnpf_set_shapes(self._h, int(variant64), int(variant32)))

@@ -92,3 +92,32 @@ def test_checkpointed_gradient_matches_finite_differences(fnpf):
     fdA = (run(c.eta, c.phis, c.h - sA * bump) - run(c.eta, c.phis, c.h + sA * bump)) / (2 * sA)
     adA = -(gh @ bump)
     assert abs(fdA - adA) <= 1e-5 * abs(adA), (fdA, adA)
+
+
+def test_taped_adjoint_equals_recomputing_adjoint(fnpf):
+    """fnpf_step_adjoint_taped on the stage data recorded by fnpf_rk4_step
+    (graph-replayed steps) gives fnpf_step_adjoint's result (which recomputes
+    the step) to the solver tolerance, on every recorded step."""
+    shape = (3, 4, 3, 2, 4, True, False)
+    c = Case(fnpf, *shape, amp=0.05, opts=fnpf.default_opts(rtol=1e-13, precond=fnpf.FNPF_PMG, max_iter=50000))
+    dt, nsteps = 0.02, 3
+    eta, phis = c.t(c.eta), c.t(c.phis)
+    c.gm.rk4_step(eta.clone(), phis.clone(), 0.0, dt)       # host-driven warm-up: the next steps replay graphs
+    states = []
+    c.gm.tape_begin(nsteps)
+    for n in range(nsteps):
+        states.append((eta.clone(), phis.clone()))
+        c.gm.rk4_step(eta, phis, n * dt, dt)
+    c.gm.tape_end()
+    rng = np.random.default_rng(2)
+    le, lp = c.t(rng.standard_normal(c.om.ns)), c.t(rng.standard_normal(c.om.ns))
+    for n in range(nsteps):
+        a = [torch.empty_like(le) for _ in range(2)] + [torch.zeros_like(le)]
+        b = [torch.empty_like(le) for _ in range(2)] + [torch.zeros_like(le)]
+        c.gm.step_adjoint(states[n][0], states[n][1], le, lp, a[0], a[1], a[2], n * dt, dt)
+        c.gm.step_adjoint_taped(n, le, lp, b[0], b[1], b[2], dt)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert float(torch.linalg.norm(x - y) / torch.linalg.norm(x)) < 1e-10
+    with pytest.raises(fnpf.FnpfError):
+        c.gm.step_adjoint_taped(nsteps, le, lp, le.clone(), lp.clone(), None, dt)

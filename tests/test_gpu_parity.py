@@ -142,7 +142,8 @@ def test_standing_wave_2d_full_run_matches_oracle(fnpf):
 
 
 SHAPE_SHAPES = [(3, 5, 3, 2, 6, True, False), (3, 5, 3, 2, 4, False, True), (3, 4, 3, 1, 8, True, True),
-                (3, 7, 2, 2, 3, False, False)]
+                (3, 7, 2, 2, 3, False, False), (3, 4, 3, 2, 5, True, True), (3, 3, 4, 1, 7, False, True),
+                (3, 6, 2, 2, 2, True, False), (3, 9, 2, 1, 1, True, True)]
 
 
 @pytest.mark.parametrize("shape", SHAPE_SHAPES, ids=ids)
