@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--cheb-degree", type=int, default=3, help="Chebyshev degree of the FP64 path's smoothers")
     ap.add_argument("--mixed-cheb-degree", type=int, default=3, help="... of the mixed path's FP32 smoothers")
     ap.add_argument("--coarse-degree", type=int, default=6)
-    ap.add_argument("--shape", type=int, default=-1, choices=list(range(-1, 8)),
+    ap.add_argument("--shape", type=int, default=-1, choices=list(range(-1, 12)),
                     help="elements-per-CTA shape of the operator kernels (-1: autotuned)")
     ap.add_argument("--model", default="fnpf", choices=["fnpf", "lpf"],
                     help="fnpf: fully nonlinear (the configuration's method); lpf: linear potential flow")
@@ -71,6 +71,8 @@ def parse():
                     help="first-kind Chebyshev smoothers target [lmax / range, lmax]")
     ap.add_argument("--coarse-solver", default="cluster", choices=["cluster", "launches"],
                     help="coarsest multigrid level on one thread-block cluster, or one launch per step")
+    ap.add_argument("--inner-rtol", type=float, default=1e-5,
+                    help="relative tolerance of the FP32 inner solves of the defect-correction form")
     ap.add_argument("--projection", type=int, default=8,
                     help="initial guess of each solve projected onto the last N solutions (0: previous solution)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -413,7 +415,7 @@ def main_gb300(args):
     #     around an FP32 operator, FP32 p-MG and FP32 PCG) and FNPF_FP64_PC32 (FP64 PCG with
     #     the p-MG preconditioner in FP32)
     def precision_form(prec_id, cheb):
-        mopts = fnpf.default_opts(precision=prec_id, rtol=args.rtol, inner_rtol=1e-5, max_iter=50000,
+        mopts = fnpf.default_opts(precision=prec_id, rtol=args.rtol, inner_rtol=args.inner_rtol, max_iter=50000,
                                   precond=pre, cheb_degree=cheb, coarse_iters=args.coarse_degree,
                                   coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
                                   cheb_range=args.cheb_range, model=model_id(args), mg_schedule=schedule_id(args),
@@ -556,14 +558,15 @@ def main_gb300(args):
         fwd_step = total_ms / args.steps
         tape_ms, rev_ms, rec_ms = ms(fwd_t), ms(rev_t), ms(rec_t)
         grad_diff = float(torch.linalg.norm(le - le2) / torch.linalg.norm(le2))
-        adjoint = {"ms_per_step": rev_ms, "tape_forward_ms_per_step": tape_ms,
-                   "ratio_to_forward": (tape_ms + rev_ms) / fwd_step,
-                   "reverse_only_ratio": rev_ms / fwd_step,
+        adjoint = {"ms_per_step": rev_ms, "ratio_to_forward": rev_ms / fwd_step,
+                   "tape_forward_ms_per_step": tape_ms,
+                   "checkpointed_ratio": (tape_ms + rev_ms) / fwd_step,
                    "recomputing_adjoint_ms_per_step": rec_ms, "recomputing_ratio": rec_ms / fwd_step,
                    "taped_vs_recomputing_rel_l2": grad_diff, "steps": K,
-                   "note": "ratio_to_forward = (forward step recording the tape + taped reverse step) / "
-                           "graph-replayed forward step: the cost per step of a checkpointed gradient beyond "
-                           "its forward run; recomputing = fnpf_step_adjoint, which re-solves the step itself"}
+                   "note": "ratio_to_forward = taped adjoint (reverse) step / graph-replayed forward step; "
+                           "checkpointed_ratio adds the forward recompute that records the tape (the cost per "
+                           "step of a checkpointed gradient beyond its forward run); recomputing = "
+                           "fnpf_step_adjoint, which re-solves the step itself"}
 
     # --- end to end through the public API: pinned host state in, step, state out
     eta_h = torch.empty(mesh.ns, dtype=torch.float64, pin_memory=True)
@@ -751,7 +754,7 @@ def main_ensemble(args):
 
     dev = torch.device("cuda", 0)
     tanks = W.ensemble_tanks(n=args.tanks, seed=5)
-    opts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=1e-5,
+    opts = fnpf.default_opts(precision=fnpf.FNPF_MIXED, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=args.inner_rtol,
                              cheb_degree=args.mixed_cheb_degree, coarse_iters=args.coarse_degree,
                              coarse_solver=coarse_mode(args), cheb_kind=args.cheb_kind,
                              cheb_range=args.cheb_range, max_iter=50000, projection=args.projection)
@@ -794,30 +797,39 @@ def main_ensemble(args):
     # error of the batched mixed-precision states against the FP64 path: every tank
     # stepped in FP64 from the same initial state for the same steps, one at a time
     n_done = steps[0]
-    err = []
+    err, failures = [], []
     o64 = fnpf.default_opts(precond=fnpf.FNPF_PMG, rtol=args.rtol, max_iter=50000, projection=args.projection)
-    for d, (e0, p0), e_b, p_b, dt in zip(tanks, init, etas, phiss, dts):
+    for i, (d, (e0, p0), e_b, p_b, dt) in enumerate(zip(tanks, init, etas, phiss, dts)):
         ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"]
         m64 = fnpf.Mesh(3, d["nx"], d["ny"], 2, d["p"], True, True, np.full(ncx * ncy, d["h0"]), Lx=d["Lx"],
                         Ly=d["Ly"], g=d["g"], opts=o64)
         e64 = torch.tensor(e0, dtype=torch.float64, device=dev)
         p64 = torch.tensor(p0, dtype=torch.float64, device=dev)
+        st = 0
         for k in range(n_done):
-            m64.rk4_step(e64, p64, k * dt, dt)
-        err.append(max(float(torch.linalg.norm(e_b - e64) / torch.linalg.norm(e64)),
-                       float(torch.linalg.norm(p_b - p64) / torch.linalg.norm(p64))))
+            st = m64.rk4_step(e64, p64, k * dt, dt, check=False)
+            if st != 0:
+                failures.append({"tank": i, "phase": "fp64 reference", "step": k, "status": st})
+                break
+        if st == 0:
+            err.append(max(float(torch.linalg.norm(e_b - e64) / torch.linalg.norm(e64)),
+                           float(torch.linalg.norm(p_b - p64) / torch.linalg.norm(p64))))
         del m64
     torch.cuda.synchronize()
     # the same tanks, one launch (captured step graph) at a time
-    for m, e, p, dt, s_ in zip(meshes, etas, phiss, dts, steps):
-        m.rk4_step(e, p, s_ * dt, dt)           # warm the single-tank graphs
+    for i, (m, e, p, dt, s_) in enumerate(zip(meshes, etas, phiss, dts, steps)):
+        st = m.rk4_step(e, p, s_ * dt, dt, check=False)   # warm the single-tank graphs
+        if st != 0:
+            failures.append({"tank": i, "phase": "one at a time (first)", "step": s_, "status": st})
     steps = [s_ + 1 for s_ in steps]
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
         for i, (m, e, p, dt) in enumerate(zip(meshes, etas, phiss, dts)):
-            m.rk4_step(e, p, steps[i] * dt, dt)
+            st = m.rk4_step(e, p, steps[i] * dt, dt, check=False)
+            if st != 0:
+                failures.append({"tank": i, "phase": "one at a time", "step": steps[i], "status": st})
         steps = [s_ + 1 for s_ in steps]
     e1.record(stream)
     torch.cuda.synchronize()
@@ -830,7 +842,8 @@ def main_ensemble(args):
         "ms_per_ensemble_step": ens_ms / args.steps, "steps": args.steps, "dtype": "f32 inner / f64 outer",
         "orders": sorted(set(d["p"] for d in tanks)), "finite": ok, "gpu_launches": launches,
         "launches_per_ensemble_step": launches / args.steps,
-        "rel_l2_vs_fp64_path_max_over_tanks": max(err), "steps_compared": n_done, "projection": args.projection,
+        "rel_l2_vs_fp64_path_max_over_tanks": max(err) if err else None, "steps_compared": n_done,
+        "projection": args.projection, "failures": failures,
         "clocks": clk.summary(), "data": "synthetic"}))
     return 0
 
@@ -918,7 +931,7 @@ def main_bar(args):
     stream = torch.cuda.current_stream()
     rows, ref = [], None
     for name, prec in (("fp64", fnpf.FNPF_FP64), ("mixed", fnpf.FNPF_MIXED), ("pc32", fnpf.FNPF_FP64_PC32)):
-        opts = fnpf.default_opts(precision=prec, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=1e-5,
+        opts = fnpf.default_opts(precision=prec, precond=fnpf.FNPF_PMG, rtol=args.rtol, inner_rtol=args.inner_rtol,
                                  max_iter=50000, cheb_degree=args.cheb_degree, coarse_iters=args.coarse_degree)
         gm = fnpf.Mesh(*dims, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"], opts=opts)
         gm.set_relaxation(cr, gen, **wave)

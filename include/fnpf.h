@@ -255,12 +255,13 @@ fnpf_status fnpf_apply_noalloc(const fnpf_mesh_desc* desc, const double* h, cons
  * operator kernel on this mesh (eta [Ns]) and keeps the fastest of each (3D:
  * shapes 0-3 run one thread per vertical GLL line, shapes 4-7 the
  * line-decomposed kernel whose contractions use the even-odd symmetry of the
- * GLL derivative matrix); the
+ * GLL derivative matrix, shapes 8-11 one thread per vertical line with two
+ * element layers in flight); the
  * chosen shape indices are returned when the pointers are non-NULL.  Runs
  * automatically before the first solve of a mesh; waits for the stream. */
 fnpf_status fnpf_autotune(fnpf_mesh* mesh, const double* eta, int* variant64, int* variant32, void* stream);
 
-/* Sets the elements-per-CTA shapes (0..7 in 3D, 0 in 2D; the same indices
+/* Sets the elements-per-CTA shapes (0..11 in 3D, 0 in 2D; the same indices
  * fnpf_autotune returns) of the FP64 and FP32 operator kernels by hand and
  * marks the mesh as tuned, so that no later solve re-tunes it.  Host-only.
  * Errors: EINVAL (index out of range). */

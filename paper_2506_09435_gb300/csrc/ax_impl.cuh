@@ -628,6 +628,7 @@ cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& 
 }  // namespace fnpf
 
 #include "axl_impl.cuh"
+#include "axz_impl.cuh"
 
 namespace fnpf {
 
@@ -636,19 +637,43 @@ namespace fnpf {
 // the fourth choice gives grids that fill the 152 SMs evenly for common column
 // counts (e.g. 7 columns of N = 7: 147 CTAs for 32 x 32 columns, where 2 and 4
 // leave a partial second wave on a third of the SMs).  Variants 4-7 are the
-// line-decomposed kernel (axl_kernel) with these element columns per CTA.
+// line-decomposed kernel (axl_kernel) with these element columns per CTA;
+// variants 8-11 the vertical-line kernels with two element layers in flight
+// (axz_kernel).
 template <int N>
 struct CtaChoices;
-template <> struct CtaChoices<2> { static constexpr int c[8] = {16, 32, 64, 8, 32, 64, 128, 16}; };
-template <> struct CtaChoices<3> { static constexpr int c[8] = {7, 14, 28, 4, 16, 32, 56, 8}; };
-template <> struct CtaChoices<4> { static constexpr int c[8] = {4, 8, 16, 2, 8, 16, 32, 4}; };
-template <> struct CtaChoices<5> { static constexpr int c[8] = {3, 5, 10, 2, 8, 16, 4, 12}; };
-template <> struct CtaChoices<6> { static constexpr int c[8] = {2, 4, 8, 6, 4, 8, 14, 2}; };
-template <> struct CtaChoices<7> { static constexpr int c[8] = {1, 2, 4, 7, 7, 4, 10, 2}; };
-template <> struct CtaChoices<8> { static constexpr int c[8] = {1, 2, 4, 3, 2, 4, 8, 3}; };
-template <> struct CtaChoices<9> { static constexpr int c[8] = {1, 2, 3, 4, 2, 4, 6, 3}; };
+template <> struct CtaChoices<2> { static constexpr int c[12] = {16, 32, 64, 8, 32, 64, 128, 16, 16, 32, 64, 8}; };
+template <> struct CtaChoices<3> { static constexpr int c[12] = {7, 14, 28, 4, 16, 32, 56, 8, 7, 14, 28, 4}; };
+template <> struct CtaChoices<4> { static constexpr int c[12] = {4, 8, 16, 2, 8, 16, 32, 4, 4, 8, 16, 2}; };
+template <> struct CtaChoices<5> { static constexpr int c[12] = {3, 5, 10, 2, 8, 16, 4, 12, 3, 5, 10, 2}; };
+template <> struct CtaChoices<6> { static constexpr int c[12] = {2, 4, 8, 6, 4, 8, 14, 2, 2, 4, 8, 6}; };
+template <> struct CtaChoices<7> { static constexpr int c[12] = {1, 2, 4, 7, 7, 4, 10, 2, 1, 2, 4, 7}; };
+template <> struct CtaChoices<8> { static constexpr int c[12] = {1, 2, 4, 3, 2, 4, 8, 3, 1, 2, 4, 3}; };
+template <> struct CtaChoices<9> { static constexpr int c[12] = {1, 2, 3, 4, 2, 4, 6, 3, 1, 2, 3, 4}; };
 static_assert(sizeof(CtaChoices<7>::c) / sizeof(int) == kCtaVariants, "one shape per variant");
 constexpr int kLineVariant0 = 4;   // first variant of the line-decomposed kernel
+constexpr int kLayerVariant0 = 8;  // first variant of the layer-parallel kernel
+
+// Layer-parallel kernel launch (3D, AX_APPLY or AX_APPLY_G), then the gather.
+template <typename T, int N, int C>
+cudaError_t launch_axz_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, cudaStream_t s) {
+  constexpr int NZL = 2;
+  using S = AxzShape<T, N, C, NZL>;
+  const unsigned blocks = (unsigned)((g.n_ecol + C - 1) / C);
+  cudaError_t e;
+  if (mode == AX_APPLY_G) {
+    static std::atomic<uint64_t> attr{0};
+    if ((e = smem_optin(axz_kernel<T, N, C, NZL, true>, S::SMEM, &attr)) != cudaSuccess) return e;
+    axz_kernel<T, N, C, NZL, true><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+  } else {
+    static std::atomic<uint64_t> attr{0};
+    if ((e = smem_optin(axz_kernel<T, N, C, NZL, false>, S::SMEM, &attr)) != cudaSuccess) return e;
+    axz_kernel<T, N, C, NZL, false><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.ep.op != EP_NONE) return launch_gather_update<T, N, 3>(g, a.ring, a.yI, a.skip, a.ep, s);
+  return launch_gather<T, N, 3>(g, a.ring, a.yI, a.ys, a.skip, s);
+}
 
 // Line-decomposed kernel launch (3D, AX_APPLY or AX_APPLY_G), then the gather.
 template <typename T, int N, int C>
@@ -678,6 +703,14 @@ cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, i
   if (g.dim == 2) return launch_ax_shape<T, N, 2, (128 + N - 1) / N>(g, t, a, mode, s);
   constexpr int C0 = CtaChoices<N>::c[0], C1 = CtaChoices<N>::c[1], C2 = CtaChoices<N>::c[2];
   constexpr int C3 = CtaChoices<N>::c[3];
+  if (variant >= kLayerVariant0 && (mode == AX_APPLY || mode == AX_APPLY_G)) {
+    switch (variant - kLayerVariant0) {
+      case 0: return launch_axz_shape<T, N, CtaChoices<N>::c[8]>(g, t, a, mode, s);
+      case 1: return launch_axz_shape<T, N, CtaChoices<N>::c[9]>(g, t, a, mode, s);
+      case 2: return launch_axz_shape<T, N, CtaChoices<N>::c[10]>(g, t, a, mode, s);
+      default: return launch_axz_shape<T, N, CtaChoices<N>::c[11]>(g, t, a, mode, s);
+    }
+  }
   if (variant >= kLineVariant0 && (mode == AX_APPLY || mode == AX_APPLY_G)) {
     switch (variant - kLineVariant0) {
       case 0: return launch_axl_shape<T, N, CtaChoices<N>::c[4]>(g, t, a, mode, s);

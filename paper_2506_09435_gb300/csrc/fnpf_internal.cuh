@@ -193,7 +193,7 @@ cudaError_t launch_apply(const Geom& g, const Tables<T>& t, const T* eta, const 
                          const Epilogue<T>* ep = nullptr);
 template <typename T>
 cudaError_t launch_diag(const Geom& g, const Tables<T>& t, const T* eta, T* dI, T* ds, T* ring, cudaStream_t s);
-constexpr int kCtaVariants = 8;      // elements-per-CTA shapes of the 3D operator kernels
+constexpr int kCtaVariants = 12;     // elements-per-CTA shapes of the 3D operator kernels
 int apply_variants(int n, int dim);   // number of elements-per-CTA variants for order n-1
 // Fills the constant tables of the line-decomposed operator kernels for order
 // n - 1 on the current device (synchronous: call outside stream capture).

@@ -147,7 +147,7 @@ SHAPE_SHAPES = [(3, 5, 3, 2, 6, True, False), (3, 5, 3, 2, 4, False, True), (3, 
 
 
 @pytest.mark.parametrize("shape", SHAPE_SHAPES, ids=ids)
-@pytest.mark.parametrize("variant", list(range(8)))
+@pytest.mark.parametrize("variant", list(range(12)))
 def test_every_cta_shape_matches_oracle(fnpf, shape, variant):
     """Each elements-per-CTA shape of the operator kernels (the autotuner's
     candidates, including ragged last CTAs) gives the oracle's operator in
@@ -176,7 +176,7 @@ def test_every_cta_shape_matches_oracle(fnpf, shape, variant):
 
 def test_set_shapes_rejects_out_of_range(fnpf):
     c = Case(fnpf, *SHAPE_SHAPES[0])
-    for bad in [(-1, 0), (0, 8), (8, 0)]:
+    for bad in [(-1, 0), (0, 12), (12, 0)]:
         with pytest.raises(fnpf.FnpfError) as e:
             c.gm.set_shapes(*bad)
         assert e.value.status == fnpf.FNPF_EINVAL
