@@ -400,6 +400,21 @@ fnpf_status fnpf_invariants(fnpf_mesh* mesh, const double* eta, const double* ph
  * Errors: EINVAL (blocks or iters < 1, out NULL, other precision), ECUDA. */
 fnpf_status fnpf_fma_probe(int precision, int blocks, int iters, void* out, double* flops, void* stream);
 
+/* Vector-Jacobian product of the Laplace solve (the differentiation form
+ * around Sec. 3.4 Steps 4.1-4.3): for phi [N] = fnpf_laplace_solve(eta, phis)
+ * (passed in: the forward solution, interior and surface plane) and a
+ * cotangent gbar [N] of phi, ADDS
+ *   lam_phis += gbar_S - A_SI psi,   lam_eta (, lam_h) -= d(psi^T A(eta, h) phi)/d(eta, h),
+ * with psi the solution of the adjoint problem A_II psi = gbar_I (the mesh's
+ * PCG; A is symmetric).  This is what a user-defined functional of the
+ * volume potential (e.g. a force on a structure) needs to be differentiated
+ * with respect to the state and the depth.  lam_h may be NULL.  FP64, nonlinear
+ * model only (EUNSUPPORTED as fnpf_step_adjoint).  Waits for the stream.
+ * Errors: EINVAL (NULL), ENOMEM, ECUDA, the solve's statuses. */
+fnpf_status fnpf_laplace_solve_vjp(fnpf_mesh* mesh, const double* eta, const double* phis, const double* phi,
+                                   const double* gbar, double* lam_eta, double* lam_phis, double* lam_h,
+                                   void* stream);
+
 /* Tape of forward steps for the adjoint (the checkpointed reverse sweep of the
  * differentiation form built around the paper's RK4 step, Sec. 3.2).  After
  * fnpf_tape_begin(mesh, capacity), every successful fnpf_rk4_step records the

@@ -56,6 +56,11 @@ def rk4_run(mesh, eta0, phis0, h, t0, dt, nsteps, every=16):
     that depth (the same values, [Ns] doubles): it is the handle through which
     autograd reports dJ/dh, and a different h would label the gradient of one
     depth with another.  A mismatch raises ValueError."""
+    _check_depth(mesh, h)
+    return RK4Run.apply(eta0, phis0, h, mesh, t0, dt, nsteps, every)
+
+
+def _check_depth(mesh, h):
     mesh_h = mesh.depth()
     if tuple(h.shape) != (mesh.ns,):
         raise ValueError("h must have the mesh's %d surface nodes, got shape %s" % (mesh.ns, tuple(h.shape)))
@@ -63,4 +68,68 @@ def rk4_run(mesh, eta0, phis0, h, t0, dt, nsteps, every=16):
     if not torch.equal(hd, mesh_h):
         raise ValueError("h differs from the depth the mesh was created with (max |difference| %.3e); "
                          "create a mesh with this depth instead" % float((hd - mesh_h).abs().max()))
-    return RK4Run.apply(eta0, phis0, h, mesh, t0, dt, nsteps, every)
+
+
+class RK4Trajectory(torch.autograd.Function):
+    """The states after steps keep_from, ..., nsteps of an RK4 run, stacked
+    ([K, Ns] each), differentiable in eta0, phis0 and h: the reverse sweep adds
+    the cotangent of every kept state as it passes that step (the adjoint of a
+    time-integrated objective).  Checkpoints every `every` steps, segments
+    recomputed with the tape, as in RK4Run."""
+
+    @staticmethod
+    def forward(ctx, eta0, phis0, h, mesh, t0, dt, nsteps, keep_from, every):
+        work_e = eta0.detach().clone().contiguous()
+        work_p = phis0.detach().clone().contiguous()
+        ckpts, kept_e, kept_p = [], [], []
+        for n in range(nsteps + 1):
+            if n >= keep_from:
+                kept_e.append(work_e.clone())
+                kept_p.append(work_p.clone())
+            if n == nsteps:
+                break
+            if n % every == 0:
+                ckpts.append((n, work_e.clone(), work_p.clone()))
+            mesh.rk4_step(work_e, work_p, t0 + n * dt, dt)
+        ctx.mesh, ctx.t0, ctx.dt, ctx.nsteps, ctx.keep_from, ctx.every = mesh, t0, dt, nsteps, keep_from, every
+        ctx.ckpts, ctx.work = ckpts, (work_e, work_p)
+        ctx.h_shape = h.shape
+        return torch.stack(kept_e), torch.stack(kept_p)
+
+    @staticmethod
+    def backward(ctx, g_eta, g_phis):
+        mesh, t0, dt, nsteps, k0, every = ctx.mesh, ctx.t0, ctx.dt, ctx.nsteps, ctx.keep_from, ctx.every
+        work_e, work_p = ctx.work
+        K = nsteps - k0 + 1
+        g_eta = g_eta if g_eta is not None else torch.zeros((K,) + work_e.shape, dtype=work_e.dtype,
+                                                            device=work_e.device)
+        g_phis = g_phis if g_phis is not None else torch.zeros_like(g_eta)
+        lam_e = g_eta[K - 1].detach().clone().contiguous()
+        lam_p = g_phis[K - 1].detach().clone().contiguous()
+        lam_h = torch.zeros(ctx.h_shape, dtype=lam_e.dtype, device=lam_e.device)
+        for n0, e0, p0 in reversed(ctx.ckpts):
+            n1 = min(n0 + every, nsteps)
+            work_e.copy_(e0)
+            work_p.copy_(p0)
+            mesh.tape_begin(n1 - n0)
+            try:
+                for n in range(n0, n1):
+                    mesh.rk4_step(work_e, work_p, t0 + n * dt, dt)
+            finally:
+                mesh.tape_end()
+            for n in reversed(range(n0, n1)):
+                mesh.step_adjoint_taped(n - n0, lam_e, lam_p, lam_e, lam_p, lam_h, dt)
+                if n >= k0:
+                    lam_e += g_eta[n - k0]
+                    lam_p += g_phis[n - k0]
+        return lam_e, lam_p, lam_h, None, None, None, None, None, None
+
+
+def rk4_trajectory(mesh, eta0, phis0, h, t0, dt, nsteps, keep_from=0, every=16):
+    """(etas, phiss) [K, Ns]: the states after steps keep_from .. nsteps of an
+    RK4 run (K = nsteps - keep_from + 1), differentiable in eta0, phis0 and h;
+    h must be the depth the mesh was created with (as for rk4_run)."""
+    if not 0 <= keep_from <= nsteps:
+        raise ValueError("need 0 <= keep_from <= nsteps")
+    _check_depth(mesh, h)
+    return RK4Trajectory.apply(eta0, phis0, h, mesh, t0, dt, nsteps, keep_from, every)

@@ -441,3 +441,47 @@ extern "C" fnpf_status fnpf_step_adjoint_taped(fnpf_mesh* m, int slot, const dou
   return adjoint_reverse(m, base, base + 4 * m->g.NI, lam_eta, lam_phis, lam_eta_out, lam_phis_out, lam_h, dt,
                          (cudaStream_t)stream);
 }
+
+extern "C" fnpf_status fnpf_laplace_solve_vjp(fnpf_mesh* m, const double* eta, const double* phis, const double* phi,
+                                              const double* gbar, double* lam_eta, double* lam_phis, double* lam_h,
+                                              void* stream) {
+  if (!m || !eta || !phis || !phi || !gbar || !lam_eta || !lam_phis) return FNPF_EINVAL;
+  fnpf_status st0 = check_adjoint_supported(m);
+  if (st0 == FNPF_OK) st0 = ensure_adj(m);
+  if (st0 != FNPF_OK) return st0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geom& g = m->g;
+  const int64_t ns = g.ns, NI = g.NI, LS = (int64_t)g.n_ecol * g.lines;
+  double* S = m->adj + 4 * NI + 16 * ns;        // surface scratch of the adjoint workspace
+  double* hbar = S + 7 * ns, *ysurf = S + 9 * ns;
+  double* LB = S + 10 * ns + 6 * LS;
+  double* psi = LB + 5 * LS + NI;
+  double* tmp = psi + NI;
+  const fnpf::Tables<double> tb = m->tables();
+  const int sb = fnpf::blocks(ns);
+  cudaError_t e = cudaSuccess;
+#define ACK(call)                                                          \
+  do {                                                                     \
+    if ((e = (call)) != cudaSuccess) {                                     \
+      m->err = std::string("laplace_solve_vjp: ") + cudaGetErrorString(e);  \
+      return FNPF_ECUDA;                                                   \
+    }                                                                      \
+  } while (0)
+  // adjoint solve A_II psi = gbar_I (A is symmetric)
+  ACK(cudaMemsetAsync(psi, 0, NI * 8, s));
+  fnpf_status r = fnpf::cg_solve(m, eta, phis, psi, nullptr, s, gbar);
+  if (r != FNPF_OK) return r;
+  // lam_phis += gbar_S - (A [psi; 0])_S
+  ACK(fnpf::launch_apply<double>(g, tb, eta, psi, nullptr, tmp, ysurf, m->ring, m->variant64, s));
+  fnpf::axpy_kernel<<<sb, fnpf::TB, 0, s>>>((int)ns, 1.0, gbar + NI, lam_phis);
+  fnpf::sub_kernel<<<sb, fnpf::TB, 0, s>>>((int)ns, ysurf, lam_phis);
+  // lam_eta, lam_h -= d(psi^T A(eta, h) phi)/d(eta, h)
+  ACK(cudaMemsetAsync(hbar, 0, ns * 8, s));
+  ACK(fnpf::launch_geom_vjp(g, tb, eta, psi, phi, phi + NI, LB, s));
+  fnpf::geom_vjp_gather_kernel<<<sb, fnpf::TB, 0, s>>>(g, tb, LB, lam_eta, hbar);
+  if (lam_h) fnpf::axpy_kernel<<<sb, fnpf::TB, 0, s>>>((int)ns, 1.0, hbar, lam_h);
+  ACK(cudaGetLastError());
+  m->launches += 7;
+#undef ACK
+  return FNPF_OK;
+}

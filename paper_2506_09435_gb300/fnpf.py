@@ -91,6 +91,7 @@ def load():
         "fnpf_fma_probe": [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double), vp],
         "fnpf_set_relaxation": [vp, ctypes.POINTER(Relaxation)],
         "fnpf_step_adjoint": [vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp],
+        "fnpf_laplace_solve_vjp": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "fnpf_tape_begin": [vp, ctypes.c_int],
         "fnpf_tape_end": [vp],
         "fnpf_step_adjoint_taped": [vp, ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_double, vp],
@@ -259,6 +260,8 @@ class Mesh:
         self._h = handle
         self.g = g
         self._depth = np.array(keep[0], dtype=np.float64)   # host copy of the depth the mesh was created with
+        self.dim, self.nx, self.ny, self.nz, self.p = dim, nx, (ny if dim == 3 else 1), nz, p
+        self.periodic_x, self.periodic_y = bool(periodic_x), bool(periodic_y) and dim == 3
         nv, ns = ctypes.c_int64(), ctypes.c_int64()
         _LIB.fnpf_mesh_sizes(self._h, ctypes.byref(nv), ctypes.byref(ns))
         self.N, self.ns = nv.value, ns.value
@@ -382,6 +385,13 @@ class Mesh:
         self._check(_LIB.fnpf_invariants(self._h, *a, ctypes.byref(ms), ctypes.byref(en), None,
                                          _stream(stream)))
         return ms.value, en.value
+
+    def laplace_solve_vjp(self, eta, phis, phi, gbar, lam_eta, lam_phis, lam_h=None, stream=None):
+        """Adds the cotangents of (eta, phis[, h]) for a cotangent gbar [N] of
+        the potential phi = laplace_solve(eta, phis) (fnpf_laplace_solve_vjp)."""
+        a = self._args((eta, "eta", "s"), (phis, "phis", "s"), (phi, "phi", "v"), (gbar, "gbar", "v"),
+                       (lam_eta, "lam_eta", "s"), (lam_phis, "lam_phis", "s"), (lam_h, "lam_h", "s"))
+        self._check(_LIB.fnpf_laplace_solve_vjp(self._h, *a, _stream(stream)))
 
     def tape_begin(self, capacity):
         """Record the stage data of the next `capacity` RK4 steps (slots 0, 1, ...)."""
