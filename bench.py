@@ -1065,7 +1065,7 @@ def main_cylinder(args):
     torch.cuda.synchronize()
     v2 = time.perf_counter()
     force = {"objective": "J = int F_x dt over steps 16..32 (force on the cylinder, still-water wetted surface)",
-             "J": float(Jf), "forward_s": v1 - v0, "backward_s": v2 - v1, "ratio": (v2 - v1) / (v1 - v0),
+             "J": float(Jf.detach()), "forward_s": v1 - v0, "backward_s": v2 - v1, "ratio": (v2 - v1) / (v1 - v0),
              "grad_norm_eta0": float(torch.linalg.norm(f0.grad)), "grad_norm_h": float(torch.linalg.norm(hf.grad)),
              "finite": bool(torch.isfinite(f0.grad).all() and torch.isfinite(hf.grad).all())}
     print(json.dumps({"mode": "cylinder", "workload": "cylinder O-grid 64x24x3, p=4, ka=kh=1, R=10a, sponge ring",
