@@ -746,7 +746,9 @@ def main_ensemble(args):
     """Batched ensemble form: seeded independent periodic tanks (nx, ny in 8..96, 2
     layers, p in 3..7, kh in 0.5..3, steepness 0.01..0.06), FP32 operator and
     p-multigrid inside FP64 defect correction, each ensemble RK4 step one launch of
-    a captured graph; the same tanks stepped one launch at a time for comparison.
+    a captured graph in which the tanks of each order share every kernel launch
+    (batched groups); for comparison the same graph with one branch of per-tank
+    kernels per tank (fork/join) and the tanks stepped one launch at a time.
     The working set (tens of millions of DOF) is far larger than L2, so no flush."""
     import numpy as np
     import torch
@@ -796,6 +798,24 @@ def main_ensemble(args):
         torch.cuda.synchronize()
     ens_ms = sum(a.elapsed_time(b) for a, b in ev)
     launches = sum(m.profile_read(reset=True)["launches"] for m in meshes)
+    groups = ens.stats()
+    # the same ensemble as one fork/join branch of per-tank kernels per tank
+    ens.set_batching(False)
+    ens.rk4_step(etas, phiss, [s_ * dt for s_, dt in zip(steps, dts)], dts)   # re-capture
+    steps = [s_ + 1 for s_ in steps]
+    for m in meshes:
+        m.profile_read(reset=True)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for k in range(args.steps):
+        ens.rk4_step(etas, phiss, [s_ * dt for s_, dt in zip(steps, dts)], dts)
+        steps = [s_ + 1 for s_ in steps]
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fj_ms = f0.elapsed_time(f1)
+    fj_launches = sum(m.profile_read(reset=True)["launches"] for m in meshes)
+    ens.set_batching(True)
     # error of the batched mixed-precision states against the FP64 path: every tank
     # stepped in FP64 from the same initial state for the same steps, one at a time
     n_done = steps[0]
@@ -841,6 +861,10 @@ def main_ensemble(args):
         "mode": "ensemble", "metric": "aggregate DOF·RK4-steps/s (batched ensemble)", "unit": UNIT,
         "value": ndof * args.steps / (ens_ms * 1e-3), "one_at_a_time": ndof * args.steps / (one_ms * 1e-3),
         "speedup_vs_one_at_a_time": one_ms / ens_ms, "tanks": len(meshes), "total_dof": ndof,
+        "batched_groups": groups["groups"], "batched_tanks": groups["batched_tanks"],
+        "fork_join": {"value": ndof * args.steps / (fj_ms * 1e-3), "ms_per_ensemble_step": fj_ms / args.steps,
+                      "launches_per_ensemble_step": fj_launches / args.steps},
+        "launch_reduction_vs_fork_join": fj_launches / max(1, launches),
         "ms_per_ensemble_step": ens_ms / args.steps, "steps": args.steps, "dtype": "f32 inner / f64 outer",
         "orders": sorted(set(d["p"] for d in tanks)), "finite": ok, "gpu_launches": launches,
         "launches_per_ensemble_step": launches / args.steps,

@@ -341,22 +341,37 @@ fnpf_status fnpf_set_dealias(fnpf_mesh* mesh, int points);
  * (device, in place), on `stream`.  Errors: EINVAL (no filter set). */
 fnpf_status fnpf_filter_apply(fnpf_mesh* mesh, double* f, void* stream);
 
-/* Ensembles of independent tanks (batched form).  An ensemble groups existing
- * meshes (not owned; they must outlive it).  fnpf_ensemble_rk4_step advances
- * tank i by one RK4 step of size dts[i] from time ts[i], state etas[i],
- * phiss[i] (device arrays, in place), exactly as fnpf_rk4_step would: from the
- * second call on, all tanks' steps run as one launch of a captured CUDA graph
- * (fork/join branches, device-side CG loops), with one host synchronisation per
- * ensemble step; the first call steps each tank on its own (set-up, autotuning).
- * The graph is re-captured when a state pointer or step size changes.  info may
- * be NULL or point to 4 n structs (tank-major).  Returns the first failing
- * tank's status; fnpf_ensemble_last_error names it. */
+/* Ensembles of independent tanks (batched form; Sec. 3.4's RK4 step, Steps
+ * 4.1-4.7, for many tanks at once).  An ensemble groups existing meshes (not
+ * owned; they must outlive it).  fnpf_ensemble_rk4_step advances tank i by one
+ * RK4 step of size dts[i] from time ts[i], state etas[i], phiss[i] (device
+ * arrays, in place), exactly as fnpf_rk4_step would.  The first call steps each
+ * tank on its own (set-up, autotuning); from the second call on, all tanks'
+ * steps run as one launch of a captured CUDA graph with one host
+ * synchronisation per ensemble step.  In that graph, tanks whose steps are the
+ * same sequence of kernels (same order, dimension and options) form batched
+ * groups: every kernel of the step is ONE launch over all tanks of the group
+ * (the grids concatenated, each block working on its own tank), every CG or
+ * defect-correction loop one device-side loop that runs while any tank's loop
+ * runs, a tank whose loop has finished skipping its work; the tanks of an order
+ * are given the kernel shapes the autotuner chose for the largest of them
+ * (fnpf_set_shapes).  Groups of up to 64 tanks and the tanks that cannot be
+ * batched (tape on, over-integration) run as concurrent branches.  The graph is
+ * re-captured when a state pointer or step size changes.  info may be NULL or
+ * point to 4 n structs (tank-major).  Returns the first failing tank's status;
+ * fnpf_ensemble_last_error names it. */
 typedef struct fnpf_ensemble fnpf_ensemble;
 fnpf_status fnpf_ensemble_create(fnpf_mesh* const* meshes, int n, fnpf_ensemble** out);
 void fnpf_ensemble_destroy(fnpf_ensemble* ens);
 fnpf_status fnpf_ensemble_rk4_step(fnpf_ensemble* ens, double* const* etas, double* const* phiss, const double* ts,
                                    const double* dts, fnpf_solve_info* info, void* stream);
 const char* fnpf_ensemble_last_error(const fnpf_ensemble* ens);
+/* Batched groups on (1, the default) or off (0: every tank its own branch of
+ * per-tank kernels); takes effect at the next step.  Errors: EINVAL. */
+fnpf_status fnpf_ensemble_set_batching(fnpf_ensemble* ens, int on);
+/* Batched groups and the tanks in them of the current graph, and the kernels
+ * the last ensemble step launched (any pointer may be NULL).  Errors: EINVAL. */
+fnpf_status fnpf_ensemble_stats(const fnpf_ensemble* ens, int* groups, int* batched_tanks, int64_t* kernels);
 
 /* Adjoint of one RK4 step (reverse mode; the differentiation form built around
  * the paper's method, Sec. 3.2 and Sec. 3.4 Steps 4.1-4.7).  Given the step's

@@ -158,8 +158,8 @@ cudaError_t enqueue_filter_step(fnpf_mesh* m, double* eta, double* phis, cudaStr
   if (!m->filter_on) return cudaSuccess;
   const size_t bytes = m->g.ns * sizeof(double);
   cudaError_t e = launch_filter(m->g, m->dfilter, eta, m->s_eta[0], phis, m->s_phi[0], s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(eta, m->s_eta[0], bytes, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(phis, m->s_phi[0], bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = memcpy_async(eta, m->s_eta[0], bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = memcpy_async(phis, m->s_phi[0], bytes, cudaMemcpyDeviceToDevice, s);
   m->launches += 1;
   return e;
 }
@@ -181,21 +181,25 @@ cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cud
   }
   cudaError_t e = enqueue_filter_step(m, eta, phis, s);
   if (e != cudaSuccess) return e;
-  return cudaMemcpyAsync(m->stage_info_host, m->stage_info, 4 * sizeof(StageInfo), cudaMemcpyDeviceToHost, s);
+  return memcpy_async(m->stage_info_host, m->stage_info, 4 * sizeof(StageInfo), cudaMemcpyDeviceToHost, s);
 }
 
-// Reads the per-stage summaries after a replayed step (stream synchronised) and
-// adds the kernels the replay executed to the launch counter: the top-level
-// kernel nodes plus the loop bodies once per body execution (a CG body holds
-// two iterations).
-fnpf_status read_step_info(fnpf_mesh* m, fnpf_solve_info* info, float ms) {
+// Reads the per-stage summaries after a replayed step (stream synchronised) and,
+// with count, adds the kernels the replay executed to the launch counter: the
+// top-level kernel nodes plus the loop bodies once per body execution (a CG
+// body holds two iterations).
+fnpf_status read_step_info(fnpf_mesh* m, fnpf_solve_info* info, float ms, bool count) {
   fnpf_status st = FNPF_OK;
   const bool mixed = m->opts.precision == FNPF_MIXED;
-  m->launches += m->step_kernels;
+  if (count) m->launches += m->step_kernels;
   for (int k = 0; k < 4; ++k) {
     const StageInfo& si = m->stage_info_host[k];
-    if (mixed) m->launches += si.outer * m->body_kernels[0] + (si.iters + 1) / 2 * m->body_kernels[1];
-    else m->launches += (si.iters + 1) / 2 * m->body_kernels[0];
+    if (!count) {
+    } else if (mixed) {
+      m->launches += si.outer * m->body_kernels[0] + (si.iters + 1) / 2 * m->body_kernels[1];
+    } else {
+      m->launches += (si.iters + 1) / 2 * m->body_kernels[0];
+    }
     if (si.status != 0 && st == FNPF_OK) st = (fnpf_status)si.status;
     if (info) {
       info[k].iters = si.iters;

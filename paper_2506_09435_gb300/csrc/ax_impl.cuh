@@ -118,201 +118,205 @@ __device__ __forceinline__ void ax_prologue(const Geom& g, const Tables<T>& t, c
 }
 
 template <typename T, int N, int DIM, int C>
-__global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
-    ax_kernel(Geom g, Tables<T> t, AxPtrs<T> a) {
-  using S = AxShape<T, N, DIM, C>;
-  constexpr int P = N - 1, L = S::L;
-  extern __shared__ __align__(16) unsigned char ax_smem[];
-  T* sU = reinterpret_cast<T*>(ax_smem);
-  T* sR = sU + S::BUF;
-  T* sS = sR + S::BUF;
-  T* sD = sS + S::BUF;
-  T* sXi = sD + N * N;
-  T* sW = sXi + N;
-  T* sE = sW + N;
-  T* sH = sE + C * L;
-  if (a.skip && *a.skip) return;
-  const int c = threadIdx.x / L, line = threadIdx.x - c * L;
-  const int i = line % N, j = line / N;
-  const int ecol = blockIdx.x * C + c;
-  const bool active = ecol < g.n_ecol;
-  int col;
-  LineGeom<T> lg;
-  ax_prologue<T, N, DIM, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, i, j, ecol, active, col, lg);
-  const int slot = ring_slot(DIM, P, i, j);
-  const T inv_nz = T(1) / T(g.nz);
-  // FP32: the D entries of this thread's r- and s-contractions are kept in
-  // registers, so that the field values are the only shared-memory operand
-  // there (the FP32 kernel is bound by shared-memory loads).  FP64 reads them
-  // from shared memory: that kernel is bound by the FP64 pipe, and its
-  // latency-bound coarse-level instances run better with fewer registers.
-  constexpr bool kDReg = sizeof(T) == 4;
-  T Di[N], Dj[N], DiT[N], DjT[N];
-#pragma unroll
-  for (int m = 0; m < N; ++m) {
-    Di[m] = sD[i * N + m];
-    Dj[m] = sD[j * N + m];
-    DiT[m] = sD[m * N + i];
-    DjT[m] = sD[m * N + j];
-  }
+struct ax_kernel {
+  static constexpr int kThreads = AxShape<T, N, DIM, C>::THREADS;
+  __device__ static void run(Blk bk, Geom g, Tables<T> t, AxPtrs<T> a) {
+    using S = AxShape<T, N, DIM, C>;
+    constexpr int P = N - 1, L = S::L;
+    extern __shared__ __align__(16) unsigned char ax_smem[];
+    T* sU = reinterpret_cast<T*>(ax_smem);
+    T* sR = sU + S::BUF;
+    T* sS = sR + S::BUF;
+    T* sD = sS + S::BUF;
+    T* sXi = sD + N * N;
+    T* sW = sXi + N;
+    T* sE = sW + N;
+    T* sH = sE + C * L;
+    if (a.skip && *a.skip) return;
+    const int c = threadIdx.x / L, line = threadIdx.x - c * L;
+    const int i = line % N, j = line / N;
+    const int ecol = bk.x * C + c;
+    const bool active = ecol < g.n_ecol;
+    int col;
+    LineGeom<T> lg;
+    ax_prologue<T, N, DIM, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, i, j, ecol, active, col, lg);
+    const int slot = ring_slot(DIM, P, i, j);
+    const T inv_nz = T(1) / T(g.nz);
+    // FP32: the D entries of this thread's r- and s-contractions are kept in
+    // registers, so that the field values are the only shared-memory operand
+    // there (the FP32 kernel is bound by shared-memory loads).  FP64 reads them
+    // from shared memory: that kernel is bound by the FP64 pipe, and its
+    // latency-bound coarse-level instances run better with fewer registers.
+    constexpr bool kDReg = sizeof(T) == 4;
+    T Di[N], Dj[N], DiT[N], DjT[N];
+  #pragma unroll
+    for (int m = 0; m < N; ++m) {
+      Di[m] = sD[i * N + m];
+      Dj[m] = sD[j * N + m];
+      DiT[m] = sD[m * N + i];
+      DjT[m] = sD[m * N + j];
+    }
 
-  T carry = 0;
-  for (int l = 0; l < g.nz; ++l) {
-    T u[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int plane = l * P + k;
-      T v = 0;
-      if (active) {
-        if (plane < g.nv - 1) {
-          if (a.xI) v = a.xI[(int64_t)plane * g.ns + col];
-        } else if (a.xs) {
-          v = a.xs[col];
+    T carry = 0;
+    for (int l = 0; l < g.nz; ++l) {
+      T u[N];
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int plane = l * P + k;
+        T v = 0;
+        if (active) {
+          if (plane < g.nv - 1) {
+            if (a.xI) v = a.xI[(int64_t)plane * g.ns + col];
+          } else if (a.xs) {
+            v = a.xs[col];
+          }
         }
+        u[k] = v;
       }
-      u[k] = v;
-    }
-    __syncthreads();   // readers of the previous layer's slices are done
-#pragma unroll
-    for (int k = 0; k < N; ++k) sU[(c * N + k) * L + line] = u[k];
-    __syncthreads();
-    T ft[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T* uk = sU + (c * N + k) * L;
-      T ur = 0, us = 0, ut = 0;
-#pragma unroll
-      for (int m = 0; m < N; ++m) ur += (kDReg ? Di[m] : sD[i * N + m]) * uk[j * N + m];
-      if (DIM == 3) {
-#pragma unroll
-        for (int m = 0; m < N; ++m) us += (kDReg ? Dj[m] : sD[j * N + m]) * uk[m * N + i];
+      __syncthreads();   // readers of the previous layer's slices are done
+  #pragma unroll
+      for (int k = 0; k < N; ++k) sU[(c * N + k) * L + line] = u[k];
+      __syncthreads();
+      T ft[N];
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T* uk = sU + (c * N + k) * L;
+        T ur = 0, us = 0, ut = 0;
+  #pragma unroll
+        for (int m = 0; m < N; ++m) ur += (kDReg ? Di[m] : sD[i * N + m]) * uk[j * N + m];
+        if (DIM == 3) {
+  #pragma unroll
+          for (int m = 0; m < N; ++m) us += (kDReg ? Dj[m] : sD[j * N + m]) * uk[m * N + i];
+        }
+  #pragma unroll
+        for (int m = 0; m < N; ++m) ut += sD[k * N + m] * u[m];
+        const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
+        const T wk = sW[k];
+        const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
+        const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
+        const T wc = wk * lg.cw;
+        const T grt = -wc * (lg.rx * ax + lg.ry * ay);
+        const T gst = -wc * (lg.sx * ax + lg.sy * ay);
+        const T gtt = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
+        sR[(c * N + k) * L + line] = wk * (lg.grr * ur + lg.grs * us) + grt * ut;
+        if (DIM == 3) sS[(c * N + k) * L + line] = wk * (lg.grs * ur + lg.gss * us) + gst * ut;
+        ft[k] = grt * ur + gst * us + gtt * ut;
       }
-#pragma unroll
-      for (int m = 0; m < N; ++m) ut += sD[k * N + m] * u[m];
-      const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
-      const T wk = sW[k];
-      const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
-      const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
-      const T wc = wk * lg.cw;
-      const T grt = -wc * (lg.rx * ax + lg.ry * ay);
-      const T gst = -wc * (lg.sx * ax + lg.sy * ay);
-      const T gtt = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
-      sR[(c * N + k) * L + line] = wk * (lg.grr * ur + lg.grs * us) + grt * ut;
-      if (DIM == 3) sS[(c * N + k) * L + line] = wk * (lg.grs * ur + lg.gss * us) + gst * ut;
-      ft[k] = grt * ur + gst * us + gtt * ut;
-    }
-    __syncthreads();
-    T y[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T* rk = sR + (c * N + k) * L;
-      const T* sk = sS + (c * N + k) * L;
-      T s = 0;
-#pragma unroll
-      for (int m = 0; m < N; ++m) s += (kDReg ? DiT[m] : sD[m * N + i]) * rk[j * N + m];
-      if (DIM == 3) {
-#pragma unroll
-        for (int m = 0; m < N; ++m) s += (kDReg ? DjT[m] : sD[m * N + j]) * sk[m * N + i];
+      __syncthreads();
+      T y[N];
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T* rk = sR + (c * N + k) * L;
+        const T* sk = sS + (c * N + k) * L;
+        T s = 0;
+  #pragma unroll
+        for (int m = 0; m < N; ++m) s += (kDReg ? DiT[m] : sD[m * N + i]) * rk[j * N + m];
+        if (DIM == 3) {
+  #pragma unroll
+          for (int m = 0; m < N; ++m) s += (kDReg ? DjT[m] : sD[m * N + j]) * sk[m * N + i];
+        }
+  #pragma unroll
+        for (int m = 0; m < N; ++m) s += sD[m * N + k] * ft[m];
+        y[k] = s;
       }
-#pragma unroll
-      for (int m = 0; m < N; ++m) s += sD[m * N + k] * ft[m];
-      y[k] = s;
+      y[0] += carry;
+      carry = y[P];
+      if (active) {
+  #pragma unroll
+        for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
+      }
     }
-    y[0] += carry;
-    carry = y[P];
-    if (active) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
-    }
+    if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
   }
-  if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
-}
+};
 
 // diag(A): per node (i, j, k) of an element,
 //   sum_m D_mi^2 G_rr(m,j,k) + sum_m D_mj^2 G_ss(i,m,k) + sum_m D_mk^2 G_tt(i,j,m)
 //   + 2 D_ii D_jj G_rs + 2 D_ii D_kk G_rt + 2 D_jj D_kk G_st   (all at (i,j,k)).
 template <typename T, int N, int DIM, int C>
-__global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
-    diag_kernel(Geom g, Tables<T> t, AxPtrs<T> a) {
-  using S = AxShape<T, N, DIM, C>;
-  constexpr int P = N - 1, L = S::L;
-  extern __shared__ __align__(16) unsigned char ax_smem[];
-  T* sU = reinterpret_cast<T*>(ax_smem);
-  T* sR = sU + S::BUF;
-  T* sS = sR + S::BUF;
-  T* sD = sS + S::BUF;
-  T* sXi = sD + N * N;
-  T* sW = sXi + N;
-  T* sE = sW + N;
-  T* sH = sE + C * L;
-  (void)sS;
-  const int c = threadIdx.x / L, line = threadIdx.x - c * L;
-  const int i = line % N, j = line / N;
-  const int ecol = blockIdx.x * C + c;
-  const bool active = ecol < g.n_ecol;
-  int col;
-  LineGeom<T> lg;
-  ax_prologue<T, N, DIM, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, i, j, ecol, active, col, lg);
-  const int slot = ring_slot(DIM, P, i, j);
-  const T inv_nz = T(1) / T(g.nz);
-  const T Dii = sD[i * N + i];
-  const T Djj = DIM == 3 ? sD[j * N + j] : T(0);
+struct diag_kernel {
+  static constexpr int kThreads = AxShape<T, N, DIM, C>::THREADS;
+  __device__ static void run(Blk bk, Geom g, Tables<T> t, AxPtrs<T> a) {
+    using S = AxShape<T, N, DIM, C>;
+    constexpr int P = N - 1, L = S::L;
+    extern __shared__ __align__(16) unsigned char ax_smem[];
+    T* sU = reinterpret_cast<T*>(ax_smem);
+    T* sR = sU + S::BUF;
+    T* sS = sR + S::BUF;
+    T* sD = sS + S::BUF;
+    T* sXi = sD + N * N;
+    T* sW = sXi + N;
+    T* sE = sW + N;
+    T* sH = sE + C * L;
+    (void)sS;
+    const int c = threadIdx.x / L, line = threadIdx.x - c * L;
+    const int i = line % N, j = line / N;
+    const int ecol = bk.x * C + c;
+    const bool active = ecol < g.n_ecol;
+    int col;
+    LineGeom<T> lg;
+    ax_prologue<T, N, DIM, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, i, j, ecol, active, col, lg);
+    const int slot = ring_slot(DIM, P, i, j);
+    const T inv_nz = T(1) / T(g.nz);
+    const T Dii = sD[i * N + i];
+    const T Djj = DIM == 3 ? sD[j * N + j] : T(0);
 
-  T carry = 0;
-  for (int l = 0; l < g.nz; ++l) {
-    T grt[N], gst[N], gtt[N];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
-      const T wk = sW[k];
-      const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
-      const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
-      const T wc = wk * lg.cw;
-      grt[k] = -wc * (lg.rx * ax + lg.ry * ay);
-      gst[k] = -wc * (lg.sx * ax + lg.sy * ay);
-      gtt[k] = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
-      sU[(c * N + k) * L + line] = wk * lg.grr;
-      sR[(c * N + k) * L + line] = wk * lg.gss;
-    }
-    __syncthreads();
-    T y[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T* uk = sU + (c * N + k) * L;
-      const T* rk = sR + (c * N + k) * L;
-      T s = 0;
-#pragma unroll
-      for (int m = 0; m < N; ++m) {
-        const T d = sD[m * N + i];
-        s += d * d * uk[j * N + m];
+    T carry = 0;
+    for (int l = 0; l < g.nz; ++l) {
+      T grt[N], gst[N], gtt[N];
+      __syncthreads();
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
+        const T wk = sW[k];
+        const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
+        const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
+        const T wc = wk * lg.cw;
+        grt[k] = -wc * (lg.rx * ax + lg.ry * ay);
+        gst[k] = -wc * (lg.sx * ax + lg.sy * ay);
+        gtt[k] = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
+        sU[(c * N + k) * L + line] = wk * lg.grr;
+        sR[(c * N + k) * L + line] = wk * lg.gss;
       }
-      if (DIM == 3) {
-#pragma unroll
+      __syncthreads();
+      T y[N];
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T* uk = sU + (c * N + k) * L;
+        const T* rk = sR + (c * N + k) * L;
+        T s = 0;
+  #pragma unroll
         for (int m = 0; m < N; ++m) {
-          const T d = sD[m * N + j];
-          s += d * d * rk[m * N + i];
+          const T d = sD[m * N + i];
+          s += d * d * uk[j * N + m];
         }
+        if (DIM == 3) {
+  #pragma unroll
+          for (int m = 0; m < N; ++m) {
+            const T d = sD[m * N + j];
+            s += d * d * rk[m * N + i];
+          }
+        }
+  #pragma unroll
+        for (int m = 0; m < N; ++m) {
+          const T d = sD[m * N + k];
+          s += d * d * gtt[m];
+        }
+        const T Dkk = sD[k * N + k];
+        s += T(2) * Dii * Dkk * grt[k];
+        if (DIM == 3) s += T(2) * (Dii * Djj * sW[k] * lg.grs + Djj * Dkk * gst[k]);
+        y[k] = s;
       }
-#pragma unroll
-      for (int m = 0; m < N; ++m) {
-        const T d = sD[m * N + k];
-        s += d * d * gtt[m];
+      y[0] += carry;
+      carry = y[P];
+      if (active) {
+  #pragma unroll
+        for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
       }
-      const T Dkk = sD[k * N + k];
-      s += T(2) * Dii * Dkk * grt[k];
-      if (DIM == 3) s += T(2) * (Dii * Djj * sW[k] * lg.grs + Djj * Dkk * gst[k]);
-      y[k] = s;
     }
-    y[0] += carry;
-    carry = y[P];
-    if (active) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
-    }
+    if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
   }
-  if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
-}
+};
 
 // Number of stored metric entries per point: (rr, rs, ss, rt, st, tt) in 3D,
 // (rr, rt, tt) in 2D.  Layout G[e][pt], pt = ((l n_ecol + ecol) N + k) L + line,
@@ -325,207 +329,214 @@ struct NGeo {
 // G of every element point, from eta, h and the horizontal metric (the same
 // formulas as the on-the-fly operator); run once per solve.
 template <typename T, int N, int DIM, int C>
-__global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
-    geom_kernel(Geom g, Tables<T> t, AxPtrs<T> a) {
-  using S = AxShape<T, N, DIM, C>;
-  constexpr int L = S::L;
-  extern __shared__ __align__(16) unsigned char ax_smem[];
-  T* sD = reinterpret_cast<T*>(ax_smem) + 3 * S::BUF;
-  T* sXi = sD + N * N;
-  T* sW = sXi + N;
-  T* sE = sW + N;
-  T* sH = sE + C * L;
-  const int c = threadIdx.x / L, line = threadIdx.x - c * L;
-  const int i = line % N, j = line / N;
-  const int ecol = blockIdx.x * C + c;
-  const bool active = ecol < g.n_ecol;
-  int col;
-  LineGeom<T> lg;
-  ax_prologue<T, N, DIM, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, i, j, ecol, active, col, lg);
-  if (!active) return;
-  const T inv_nz = T(1) / T(g.nz);
-  const int64_t P = (int64_t)g.nz * g.n_ecol * N * L;
-  T* G = a.G;
-  for (int l = 0; l < g.nz; ++l) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
-      const T wk = sW[k];
-      const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
-      const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
-      const T wc = wk * lg.cw;
-      const int64_t pt = (((int64_t)l * g.n_ecol + ecol) * N + k) * L + line;
-      if (DIM == 3) {
-        G[pt] = wk * lg.grr;
-        G[P + pt] = wk * lg.grs;
-        G[2 * P + pt] = wk * lg.gss;
-        G[3 * P + pt] = -wc * (lg.rx * ax + lg.ry * ay);
-        G[4 * P + pt] = -wc * (lg.sx * ax + lg.sy * ay);
-        G[5 * P + pt] = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
-      } else {
-        G[pt] = wk * lg.grr;
-        G[P + pt] = -wc * (lg.rx * ax);
-        G[2 * P + pt] = wc * (ax * ax + T(1)) * lg.Ainv;
+struct geom_kernel {
+  static constexpr int kThreads = AxShape<T, N, DIM, C>::THREADS;
+  __device__ static void run(Blk bk, Geom g, Tables<T> t, AxPtrs<T> a) {
+    using S = AxShape<T, N, DIM, C>;
+    constexpr int L = S::L;
+    extern __shared__ __align__(16) unsigned char ax_smem[];
+    T* sD = reinterpret_cast<T*>(ax_smem) + 3 * S::BUF;
+    T* sXi = sD + N * N;
+    T* sW = sXi + N;
+    T* sE = sW + N;
+    T* sH = sE + C * L;
+    const int c = threadIdx.x / L, line = threadIdx.x - c * L;
+    const int i = line % N, j = line / N;
+    const int ecol = bk.x * C + c;
+    const bool active = ecol < g.n_ecol;
+    int col;
+    LineGeom<T> lg;
+    ax_prologue<T, N, DIM, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, i, j, ecol, active, col, lg);
+    if (!active) return;
+    const T inv_nz = T(1) / T(g.nz);
+    const int64_t P = (int64_t)g.nz * g.n_ecol * N * L;
+    T* G = a.G;
+    for (int l = 0; l < g.nz; ++l) {
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
+        const T wk = sW[k];
+        const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
+        const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
+        const T wc = wk * lg.cw;
+        const int64_t pt = (((int64_t)l * g.n_ecol + ecol) * N + k) * L + line;
+        if (DIM == 3) {
+          G[pt] = wk * lg.grr;
+          G[P + pt] = wk * lg.grs;
+          G[2 * P + pt] = wk * lg.gss;
+          G[3 * P + pt] = -wc * (lg.rx * ax + lg.ry * ay);
+          G[4 * P + pt] = -wc * (lg.sx * ax + lg.sy * ay);
+          G[5 * P + pt] = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
+        } else {
+          G[pt] = wk * lg.grr;
+          G[P + pt] = -wc * (lg.rx * ax);
+          G[2 * P + pt] = wc * (ax * ax + T(1)) * lg.Ainv;
+        }
       }
     }
   }
-}
+};
 
 // The operator with G read from memory instead of rebuilt: fewer FP64
 // instructions per point, for the FP64 solves where the FP64 pipe is the bound.
 template <typename T, int N, int DIM, int C>
-__global__ void __launch_bounds__(AxShape<T, N, DIM, C>::THREADS)
-    axg_kernel(Geom g, Tables<T> t, AxPtrs<T> a) {
-  using S = AxShape<T, N, DIM, C>;
-  constexpr int P = N - 1, L = S::L;
-  extern __shared__ __align__(16) unsigned char ax_smem[];
-  T* sU = reinterpret_cast<T*>(ax_smem);
-  T* sR = sU + S::BUF;
-  T* sS = sR + S::BUF;
-  T* sD = sS + S::BUF;
-  if (a.skip && *a.skip) return;
-  const int c = threadIdx.x / L, line = threadIdx.x - c * L;
-  const int i = line % N, j = line / N;
-  const int ecol = blockIdx.x * C + c;
-  const bool active = ecol < g.n_ecol;
-  for (int q = threadIdx.x; q < N * N; q += S::THREADS) sD[q] = t.D[q];
-  int col = 0;
-  if (active) col = node_col(g, ecol % g.nx, ecol / g.nx, i, j);
-  const int slot = ring_slot(DIM, P, i, j);
-  const int64_t PT = (int64_t)g.nz * g.n_ecol * N * L;
-  const T* G = a.G;
-  __syncthreads();
-  constexpr bool kDReg = sizeof(T) == 4;   // as in ax_kernel
-  T Di[N], Dj[N], DiT[N], DjT[N];
-#pragma unroll
-  for (int m = 0; m < N; ++m) {
-    Di[m] = sD[i * N + m];
-    Dj[m] = sD[j * N + m];
-    DiT[m] = sD[m * N + i];
-    DjT[m] = sD[m * N + j];
-  }
-  T carry = 0;
-  for (int l = 0; l < g.nz; ++l) {
-    T u[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int plane = l * P + k;
-      T v = 0;
-      if (active) {
-        if (plane < g.nv - 1) {
-          if (a.xI) v = a.xI[(int64_t)plane * g.ns + col];
-        } else if (a.xs) {
-          v = a.xs[col];
+struct axg_kernel {
+  static constexpr int kThreads = AxShape<T, N, DIM, C>::THREADS;
+  __device__ static void run(Blk bk, Geom g, Tables<T> t, AxPtrs<T> a) {
+    using S = AxShape<T, N, DIM, C>;
+    constexpr int P = N - 1, L = S::L;
+    extern __shared__ __align__(16) unsigned char ax_smem[];
+    T* sU = reinterpret_cast<T*>(ax_smem);
+    T* sR = sU + S::BUF;
+    T* sS = sR + S::BUF;
+    T* sD = sS + S::BUF;
+    if (a.skip && *a.skip) return;
+    const int c = threadIdx.x / L, line = threadIdx.x - c * L;
+    const int i = line % N, j = line / N;
+    const int ecol = bk.x * C + c;
+    const bool active = ecol < g.n_ecol;
+    for (int q = threadIdx.x; q < N * N; q += S::THREADS) sD[q] = t.D[q];
+    int col = 0;
+    if (active) col = node_col(g, ecol % g.nx, ecol / g.nx, i, j);
+    const int slot = ring_slot(DIM, P, i, j);
+    const int64_t PT = (int64_t)g.nz * g.n_ecol * N * L;
+    const T* G = a.G;
+    __syncthreads();
+    constexpr bool kDReg = sizeof(T) == 4;   // as in ax_kernel
+    T Di[N], Dj[N], DiT[N], DjT[N];
+  #pragma unroll
+    for (int m = 0; m < N; ++m) {
+      Di[m] = sD[i * N + m];
+      Dj[m] = sD[j * N + m];
+      DiT[m] = sD[m * N + i];
+      DjT[m] = sD[m * N + j];
+    }
+    T carry = 0;
+    for (int l = 0; l < g.nz; ++l) {
+      T u[N];
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int plane = l * P + k;
+        T v = 0;
+        if (active) {
+          if (plane < g.nv - 1) {
+            if (a.xI) v = a.xI[(int64_t)plane * g.ns + col];
+          } else if (a.xs) {
+            v = a.xs[col];
+          }
+        }
+        u[k] = v;
+      }
+      __syncthreads();
+  #pragma unroll
+      for (int k = 0; k < N; ++k) sU[(c * N + k) * L + line] = u[k];
+      __syncthreads();
+      T ft[N];
+      const int64_t pt0 = (((int64_t)l * g.n_ecol + (active ? ecol : 0)) * N) * L + line;
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T* uk = sU + (c * N + k) * L;
+        T ur = 0, us = 0, ut = 0;
+  #pragma unroll
+        for (int m = 0; m < N; ++m) ur += (kDReg ? Di[m] : sD[i * N + m]) * uk[j * N + m];
+        if (DIM == 3) {
+  #pragma unroll
+          for (int m = 0; m < N; ++m) us += (kDReg ? Dj[m] : sD[j * N + m]) * uk[m * N + i];
+        }
+  #pragma unroll
+        for (int m = 0; m < N; ++m) ut += sD[k * N + m] * u[m];
+        const int64_t pt = pt0 + (int64_t)k * L;
+        if (DIM == 3) {
+          const T grr = G[pt], grs = G[PT + pt], gss = G[2 * PT + pt];
+          const T grt = G[3 * PT + pt], gst = G[4 * PT + pt], gtt = G[5 * PT + pt];
+          sR[(c * N + k) * L + line] = grr * ur + grs * us + grt * ut;
+          sS[(c * N + k) * L + line] = grs * ur + gss * us + gst * ut;
+          ft[k] = grt * ur + gst * us + gtt * ut;
+        } else {
+          const T grr = G[pt], grt = G[PT + pt], gtt = G[2 * PT + pt];
+          sR[(c * N + k) * L + line] = grr * ur + grt * ut;
+          ft[k] = grt * ur + gtt * ut;
         }
       }
-      u[k] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < N; ++k) sU[(c * N + k) * L + line] = u[k];
-    __syncthreads();
-    T ft[N];
-    const int64_t pt0 = (((int64_t)l * g.n_ecol + (active ? ecol : 0)) * N) * L + line;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T* uk = sU + (c * N + k) * L;
-      T ur = 0, us = 0, ut = 0;
-#pragma unroll
-      for (int m = 0; m < N; ++m) ur += (kDReg ? Di[m] : sD[i * N + m]) * uk[j * N + m];
-      if (DIM == 3) {
-#pragma unroll
-        for (int m = 0; m < N; ++m) us += (kDReg ? Dj[m] : sD[j * N + m]) * uk[m * N + i];
+      __syncthreads();
+      T y[N];
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T* rk = sR + (c * N + k) * L;
+        const T* sk = sS + (c * N + k) * L;
+        T s = 0;
+  #pragma unroll
+        for (int m = 0; m < N; ++m) s += (kDReg ? DiT[m] : sD[m * N + i]) * rk[j * N + m];
+        if (DIM == 3) {
+  #pragma unroll
+          for (int m = 0; m < N; ++m) s += (kDReg ? DjT[m] : sD[m * N + j]) * sk[m * N + i];
+        }
+  #pragma unroll
+        for (int m = 0; m < N; ++m) s += sD[m * N + k] * ft[m];
+        y[k] = s;
       }
-#pragma unroll
-      for (int m = 0; m < N; ++m) ut += sD[k * N + m] * u[m];
-      const int64_t pt = pt0 + (int64_t)k * L;
-      if (DIM == 3) {
-        const T grr = G[pt], grs = G[PT + pt], gss = G[2 * PT + pt];
-        const T grt = G[3 * PT + pt], gst = G[4 * PT + pt], gtt = G[5 * PT + pt];
-        sR[(c * N + k) * L + line] = grr * ur + grs * us + grt * ut;
-        sS[(c * N + k) * L + line] = grs * ur + gss * us + gst * ut;
-        ft[k] = grt * ur + gst * us + gtt * ut;
-      } else {
-        const T grr = G[pt], grt = G[PT + pt], gtt = G[2 * PT + pt];
-        sR[(c * N + k) * L + line] = grr * ur + grt * ut;
-        ft[k] = grt * ur + gtt * ut;
+      y[0] += carry;
+      carry = y[P];
+      if (active) {
+  #pragma unroll
+        for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
       }
     }
-    __syncthreads();
-    T y[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T* rk = sR + (c * N + k) * L;
-      const T* sk = sS + (c * N + k) * L;
-      T s = 0;
-#pragma unroll
-      for (int m = 0; m < N; ++m) s += (kDReg ? DiT[m] : sD[m * N + i]) * rk[j * N + m];
-      if (DIM == 3) {
-#pragma unroll
-        for (int m = 0; m < N; ++m) s += (kDReg ? DjT[m] : sD[m * N + j]) * sk[m * N + i];
-      }
-#pragma unroll
-      for (int m = 0; m < N; ++m) s += sD[m * N + k] * ft[m];
-      y[k] = s;
-    }
-    y[0] += carry;
-    carry = y[P];
-    if (active) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
-    }
+    if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
   }
-  if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
-}
+};
 
 // Sums the ring contributions of every element-boundary node column, in a
 // fixed order (x owners outer, y owners inner), and writes the output field.
 template <typename T, int N, int DIM>
-__global__ void ring_gather_kernel(Geom g, const T* __restrict__ ring, T* yI, T* ys, int nplanes,
-                                   int64_t nring_cols, const int* skip) {
-  if (skip && *skip) return;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nring_cols * nplanes) return;
-  const int plane = (int)(idx / nring_cols);
-  const int64_t rc = idx - (int64_t)plane * nring_cols;
-  constexpr int p = N - 1;   // the order as a constant: divisions by p fold
-  const int nlx = g.nx + (g.px ? 0 : 1);
-  int ix, iy;
-  if (DIM == 2) {
-    ix = (int)rc * p;
-    iy = 0;
-  } else {
-    const int64_t part1 = (int64_t)nlx * g.ncy;
-    if (rc < part1) {
-      ix = (int)(rc % nlx) * p;
-      iy = (int)(rc / nlx);
+struct ring_gather_kernel {
+  static constexpr int kThreads = 256;
+  __device__ static void run(Blk bk, Geom g, const T* __restrict__ ring, T* yI, T* ys, int nplanes,
+                             int64_t nring_cols, const int* skip) {
+    if (skip && *skip) return;
+    const int64_t idx = (int64_t)bk.x * blockDim.x + threadIdx.x;
+    if (idx >= nring_cols * nplanes) return;
+    const int plane = (int)(idx / nring_cols);
+    const int64_t rc = idx - (int64_t)plane * nring_cols;
+    constexpr int p = N - 1;   // the order as a constant: divisions by p fold
+    const int nlx = g.nx + (g.px ? 0 : 1);
+    int ix, iy;
+    if (DIM == 2) {
+      ix = (int)rc * p;
+      iy = 0;
     } else {
-      // element-interior x positions on the y-boundary lines (none at p = 1,
-      // where this branch is never taken; pm1 keeps the divisor non-zero)
-      constexpr int pm1 = p > 1 ? p - 1 : 1;
-      const int64_t m = rc - part1;
-      const int per = g.nx * pm1;
-      const int ly = (int)(m / per);
-      const int mm = (int)(m - (int64_t)ly * per);
-      ix = (mm / pm1) * p + 1 + mm % pm1;
-      iy = ly * p;
+      const int64_t part1 = (int64_t)nlx * g.ncy;
+      if (rc < part1) {
+        ix = (int)(rc % nlx) * p;
+        iy = (int)(rc / nlx);
+      } else {
+        // element-interior x positions on the y-boundary lines (none at p = 1,
+        // where this branch is never taken; pm1 keeps the divisor non-zero)
+        constexpr int pm1 = p > 1 ? p - 1 : 1;
+        const int64_t m = rc - part1;
+        const int per = g.nx * pm1;
+        const int ly = (int)(m / per);
+        const int mm = (int)(m - (int64_t)ly * per);
+        ix = (mm / pm1) * p + 1 + mm % pm1;
+        iy = ly * p;
+      }
     }
-  }
-  int exo[2], io[2], eyo[2] = {0, 0}, jo[2] = {0, 0};
-  const int cx = line_owners(ix, p, g.nx, g.px, exo, io);
-  const int cy = DIM == 3 ? line_owners(iy, p, g.ny, g.py, eyo, jo) : 1;
-  T s = 0;
-  for (int u = 0; u < cx; ++u) {
-    for (int v = 0; v < cy; ++v) {
-      const int ecol = eyo[v] * g.nx + exo[u];
-      const int slot = ring_slot(DIM, p, io[u], jo[v]);
-      s += ring[((int64_t)plane * g.n_ecol + ecol) * g.ring + slot];
+    int exo[2], io[2], eyo[2] = {0, 0}, jo[2] = {0, 0};
+    const int cx = line_owners(ix, p, g.nx, g.px, exo, io);
+    const int cy = DIM == 3 ? line_owners(iy, p, g.ny, g.py, eyo, jo) : 1;
+    T s = 0;
+    for (int u = 0; u < cx; ++u) {
+      for (int v = 0; v < cy; ++v) {
+        const int ecol = eyo[v] * g.nx + exo[u];
+        const int slot = ring_slot(DIM, p, io[u], jo[v]);
+        s += ring[((int64_t)plane * g.n_ecol + ecol) * g.ring + slot];
+      }
     }
+    const int col = iy * g.ncx + ix;
+    if (plane == g.nv - 1) ys[col] = s;
+    else yI[(int64_t)plane * g.ns + col] = s;
   }
-  const int col = iy * g.ncx + ix;
-  if (plane == g.nv - 1) ys[col] = s;
-  else yI[(int64_t)plane * g.ns + col] = s;
-}
+};
 
 // Gather fused with a vector update: one thread per interior unknown (a 2D
 // grid of columns x interior planes, so no 64-bit index division); the
@@ -534,32 +545,34 @@ __global__ void ring_gather_kernel(Geom g, const T* __restrict__ ring, T* yI, T*
 // lines (same owners and order as ring_gather_kernel), then the Epilogue
 // update is applied; yI itself is left as the operator kernel wrote it.
 template <typename T, int N, int DIM>
-__global__ void __launch_bounds__(256) gather_update_kernel(Geom g, const T* __restrict__ ring,
-                                                            const T* __restrict__ yI, const int* skip,
-                                                            Epilogue<T> ep) {
-  if (skip && *skip) return;
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;   // grid: (columns, interior planes)
-  if (col >= g.ns) return;
-  const int plane = blockIdx.y;
-  const int64_t i = (int64_t)plane * g.ns + col;
-  const int iy = col / g.ncx, ix = col - iy * g.ncx;
-  constexpr int p = N - 1;
-  T w;
-  if (ix % p != 0 && (DIM == 2 || iy % p != 0)) {
-    w = yI[i];
-  } else {
-    int exo[2], io[2], eyo[2] = {0, 0}, jo[2] = {0, 0};
-    const int cx = line_owners(ix, p, g.nx, g.px, exo, io);
-    const int cy = DIM == 3 ? line_owners(iy, p, g.ny, g.py, eyo, jo) : 1;
-    w = T(0);
-    for (int u = 0; u < cx; ++u)
-      for (int v = 0; v < cy; ++v) {
-        const int ecol = eyo[v] * g.nx + exo[u];
-        w += ring[((int64_t)plane * g.n_ecol + ecol) * g.ring + ring_slot(DIM, p, io[u], jo[v])];
-      }
+struct gather_update_kernel {
+  static constexpr int kThreads = 256;
+  __device__ static void run(Blk bk, Geom g, const T* __restrict__ ring, const T* __restrict__ yI, const int* skip,
+                             Epilogue<T> ep) {
+    if (skip && *skip) return;
+    const int col = bk.x * blockDim.x + threadIdx.x;   // grid: (columns, interior planes)
+    if (col >= g.ns) return;
+    const int plane = bk.y;
+    const int64_t i = (int64_t)plane * g.ns + col;
+    const int iy = col / g.ncx, ix = col - iy * g.ncx;
+    constexpr int p = N - 1;
+    T w;
+    if (ix % p != 0 && (DIM == 2 || iy % p != 0)) {
+      w = yI[i];
+    } else {
+      int exo[2], io[2], eyo[2] = {0, 0}, jo[2] = {0, 0};
+      const int cx = line_owners(ix, p, g.nx, g.px, exo, io);
+      const int cy = DIM == 3 ? line_owners(iy, p, g.ny, g.py, eyo, jo) : 1;
+      w = T(0);
+      for (int u = 0; u < cx; ++u)
+        for (int v = 0; v < cy; ++v) {
+          const int ecol = eyo[v] * g.nx + exo[u];
+          w += ring[((int64_t)plane * g.n_ecol + ecol) * g.ring + ring_slot(DIM, p, io[u], jo[v])];
+        }
+    }
+    apply_epilogue(ep, i, w);
   }
-  apply_epilogue(ep, i, w);
-}
+};
 
 inline int64_t ring_columns(const Geom& g) {
   const int nlx = g.nx + (g.px ? 0 : 1);
@@ -576,7 +589,7 @@ cudaError_t launch_gather(const Geom& g, const T* ring, T* yI, T* ys, const int*
   if (total == 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (total + threads - 1) / threads;
-  ring_gather_kernel<T, N, DIM><<<(unsigned)blocks, threads, 0, s>>>(g, ring, yI, ys, nplanes, nrc, skip);
+  launch<ring_gather_kernel<T, N, DIM>>((unsigned)blocks, threads, 0, s, g, ring, yI, ys, nplanes, nrc, skip);
   return cudaGetLastError();
 }
 
@@ -585,7 +598,7 @@ cudaError_t launch_gather_update(const Geom& g, const T* ring, const T* yI, cons
                                  cudaStream_t s) {
   if (g.NI == 0) return cudaSuccess;
   const dim3 grid((unsigned)((g.ns + 255) / 256), (unsigned)(g.nv - 1));
-  gather_update_kernel<T, N, DIM><<<grid, 256, 0, s>>>(g, ring, yI, skip, ep);
+  launch<gather_update_kernel<T, N, DIM>>(grid, 256, 0, s, g, ring, yI, skip, ep);
   return cudaGetLastError();
 }
 
@@ -602,22 +615,22 @@ cudaError_t launch_ax_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>& 
   cudaError_t e;
   if (mode == AX_GEOM) {
     static std::atomic<uint64_t> attr{0};
-    if ((e = set_smem_attr<T, N, DIM, C>(geom_kernel<T, N, DIM, C>, &attr)) != cudaSuccess) return e;
-    geom_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    if ((e = set_smem_attr<T, N, DIM, C>(kernel_one<geom_kernel<T, N, DIM, C>>(), &attr)) != cudaSuccess) return e;
+    launch<geom_kernel<T, N, DIM, C>>(blocks, S::THREADS, S::SMEM, s, g, t, a);
     return cudaGetLastError();
   }
   if (mode == AX_APPLY_G) {
     static std::atomic<uint64_t> attr{0};
-    if ((e = set_smem_attr<T, N, DIM, C>(axg_kernel<T, N, DIM, C>, &attr)) != cudaSuccess) return e;
-    axg_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    if ((e = set_smem_attr<T, N, DIM, C>(kernel_one<axg_kernel<T, N, DIM, C>>(), &attr)) != cudaSuccess) return e;
+    launch<axg_kernel<T, N, DIM, C>>(blocks, S::THREADS, S::SMEM, s, g, t, a);
   } else if (mode == AX_DIAG) {
     static std::atomic<uint64_t> attr{0};
-    if ((e = set_smem_attr<T, N, DIM, C>(diag_kernel<T, N, DIM, C>, &attr)) != cudaSuccess) return e;
-    diag_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    if ((e = set_smem_attr<T, N, DIM, C>(kernel_one<diag_kernel<T, N, DIM, C>>(), &attr)) != cudaSuccess) return e;
+    launch<diag_kernel<T, N, DIM, C>>(blocks, S::THREADS, S::SMEM, s, g, t, a);
   } else {
     static std::atomic<uint64_t> attr{0};
-    if ((e = set_smem_attr<T, N, DIM, C>(ax_kernel<T, N, DIM, C>, &attr)) != cudaSuccess) return e;
-    ax_kernel<T, N, DIM, C><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    if ((e = set_smem_attr<T, N, DIM, C>(kernel_one<ax_kernel<T, N, DIM, C>>(), &attr)) != cudaSuccess) return e;
+    launch<ax_kernel<T, N, DIM, C>>(blocks, S::THREADS, S::SMEM, s, g, t, a);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -663,12 +676,12 @@ cudaError_t launch_axz_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>&
   cudaError_t e;
   if (mode == AX_APPLY_G) {
     static std::atomic<uint64_t> attr{0};
-    if ((e = smem_optin(axz_kernel<T, N, C, NZL, true>, S::SMEM, &attr)) != cudaSuccess) return e;
-    axz_kernel<T, N, C, NZL, true><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    if ((e = smem_optin(kernel_one<axz_kernel<T, N, C, NZL, true>>(), S::SMEM, &attr)) != cudaSuccess) return e;
+    launch<axz_kernel<T, N, C, NZL, true>>(blocks, S::THREADS, S::SMEM, s, g, t, a);
   } else {
     static std::atomic<uint64_t> attr{0};
-    if ((e = smem_optin(axz_kernel<T, N, C, NZL, false>, S::SMEM, &attr)) != cudaSuccess) return e;
-    axz_kernel<T, N, C, NZL, false><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    if ((e = smem_optin(kernel_one<axz_kernel<T, N, C, NZL, false>>(), S::SMEM, &attr)) != cudaSuccess) return e;
+    launch<axz_kernel<T, N, C, NZL, false>>(blocks, S::THREADS, S::SMEM, s, g, t, a);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.ep.op != EP_NONE) return launch_gather_update<T, N, 3>(g, a.ring, a.yI, a.skip, a.ep, s);
@@ -684,12 +697,12 @@ cudaError_t launch_axl_shape(const Geom& g, const Tables<T>& t, const AxPtrs<T>&
   const unsigned blocks = (unsigned)((g.n_ecol + C - 1) / C);
   if (mode == AX_APPLY_G) {
     static std::atomic<uint64_t> attr{0};
-    if ((e = smem_optin(axl_kernel<T, N, C, true>, S::SMEM, &attr)) != cudaSuccess) return e;
-    axl_kernel<T, N, C, true><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    if ((e = smem_optin(kernel_one<axl_kernel<T, N, C, true>>(), S::SMEM, &attr)) != cudaSuccess) return e;
+    launch<axl_kernel<T, N, C, true>>(blocks, S::THREADS, S::SMEM, s, g, t, a);
   } else {
     static std::atomic<uint64_t> attr{0};
-    if ((e = smem_optin(axl_kernel<T, N, C, false>, S::SMEM, &attr)) != cudaSuccess) return e;
-    axl_kernel<T, N, C, false><<<blocks, S::THREADS, S::SMEM, s>>>(g, t, a);
+    if ((e = smem_optin(kernel_one<axl_kernel<T, N, C, false>>(), S::SMEM, &attr)) != cudaSuccess) return e;
+    launch<axl_kernel<T, N, C, false>>(blocks, S::THREADS, S::SMEM, s, g, t, a);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.ep.op != EP_NONE) return launch_gather_update<T, N, 3>(g, a.ring, a.yI, a.skip, a.ep, s);

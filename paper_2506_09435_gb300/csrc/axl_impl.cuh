@@ -45,139 +45,141 @@ struct AxlShape {
 };
 
 template <typename T, int N, int C, bool STORED>
-__global__ void __launch_bounds__(AxlShape<T, N, C>::THREADS)
-    axl_kernel(Geom g, Tables<T> t, AxPtrs<T> a) {
-  using S = AxlShape<T, N, C>;
-  constexpr int P = N - 1, L = S::L, SJ = S::SJ, SK = S::SK, COL = S::COL;
-  extern __shared__ __align__(16) unsigned char ax_smem[];
-  T* buf = reinterpret_cast<T*>(ax_smem);
-  T* sD = buf + 4 * C * COL;
-  T* sXi = sD + N * N;
-  T* sW = sXi + N;
-  T* sE = sW + N;
-  T* sH = sE + C * L;
-  if (a.skip && *a.skip) return;
-  const int c = threadIdx.x / L, line = threadIdx.x - c * L;
-  const int qa = line % N, qb = line / N;
-  const int ecol = blockIdx.x * C + c;
-  const bool active = ecol < g.n_ecol;
-  T* f0 = buf + c * COL;              // u, then the metric product R
-  T* f1 = buf + (C + c) * COL;        // u_r, then D_r^T R
-  T* f2 = buf + (2 * C + c) * COL;    // u_s, then D_s^T S
-  T* f3 = buf + (3 * C + c) * COL;    // the metric product S
-  const int vo = qb * SJ + qa;        // V role (i, j) = (qa, qb): + k * SK
-  const int ro = qb * SK + qa * SJ;   // R role (j, k) = (qa, qb): + i
-  const int so = qb * SK + qa;        // S role (i, k) = (qa, qb): + j * SJ
-  int col = 0;
-  LineGeom<T> lg{};
-  if constexpr (STORED) {
-    if (active) col = node_col(g, ecol % g.nx, ecol / g.nx, qa, qb);
-  } else {
-    ax_prologue<T, N, 3, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, qa, qb, ecol, active, col, lg);
-  }
-  const int slot = ring_slot(3, P, qa, qb);
-  const T inv_nz = T(1) / T(g.nz);
-  const int64_t PT = (int64_t)g.nz * g.n_ecol * N * L;
-  T carry = 0;
-  for (int l = 0; l < g.nz; ++l) {
-    // ---- V: load the line into shared memory
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int plane = l * P + k;
-      T v = 0;
-      if (active) {
-        if (plane < g.nv - 1) {
-          if (a.xI) v = a.xI[(int64_t)plane * g.ns + col];
-        } else if (a.xs) {
-          v = a.xs[col];
+struct axl_kernel {
+  static constexpr int kThreads = AxlShape<T, N, C>::THREADS;
+  __device__ static void run(Blk bk, Geom g, Tables<T> t, AxPtrs<T> a) {
+    using S = AxlShape<T, N, C>;
+    constexpr int P = N - 1, L = S::L, SJ = S::SJ, SK = S::SK, COL = S::COL;
+    extern __shared__ __align__(16) unsigned char ax_smem[];
+    T* buf = reinterpret_cast<T*>(ax_smem);
+    T* sD = buf + 4 * C * COL;
+    T* sXi = sD + N * N;
+    T* sW = sXi + N;
+    T* sE = sW + N;
+    T* sH = sE + C * L;
+    if (a.skip && *a.skip) return;
+    const int c = threadIdx.x / L, line = threadIdx.x - c * L;
+    const int qa = line % N, qb = line / N;
+    const int ecol = bk.x * C + c;
+    const bool active = ecol < g.n_ecol;
+    T* f0 = buf + c * COL;              // u, then the metric product R
+    T* f1 = buf + (C + c) * COL;        // u_r, then D_r^T R
+    T* f2 = buf + (2 * C + c) * COL;    // u_s, then D_s^T S
+    T* f3 = buf + (3 * C + c) * COL;    // the metric product S
+    const int vo = qb * SJ + qa;        // V role (i, j) = (qa, qb): + k * SK
+    const int ro = qb * SK + qa * SJ;   // R role (j, k) = (qa, qb): + i
+    const int so = qb * SK + qa;        // S role (i, k) = (qa, qb): + j * SJ
+    int col = 0;
+    LineGeom<T> lg{};
+    if constexpr (STORED) {
+      if (active) col = node_col(g, ecol % g.nx, ecol / g.nx, qa, qb);
+    } else {
+      ax_prologue<T, N, 3, C>(g, t, a.eta, sD, sXi, sW, sE, sH, c, line, qa, qb, ecol, active, col, lg);
+    }
+    const int slot = ring_slot(3, P, qa, qb);
+    const T inv_nz = T(1) / T(g.nz);
+    const int64_t PT = (int64_t)g.nz * g.n_ecol * N * L;
+    T carry = 0;
+    for (int l = 0; l < g.nz; ++l) {
+      // ---- V: load the line into shared memory
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int plane = l * P + k;
+        T v = 0;
+        if (active) {
+          if (plane < g.nv - 1) {
+            if (a.xI) v = a.xI[(int64_t)plane * g.ns + col];
+          } else if (a.xs) {
+            v = a.xs[col];
+          }
         }
+        f0[k * SK + vo] = v;
       }
-      f0[k * SK + vo] = v;
-    }
-    __syncthreads();
-    // ---- R and S: r- and s-contractions of u
-    {
-      T v[N], r[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) v[i] = f0[ro + i];
-      eo_mul<T, N, 0>(v, r);
-#pragma unroll
-      for (int i = 0; i < N; ++i) f1[ro + i] = r[i];
-#pragma unroll
-      for (int j = 0; j < N; ++j) v[j] = f0[so + j * SJ];
-      eo_mul<T, N, 0>(v, r);
-#pragma unroll
-      for (int j = 0; j < N; ++j) f2[so + j * SJ] = r[j];
-    }
-    __syncthreads();
-    // ---- V: t-contraction of the thread's own line (re-read: fewer live
-    //      registers across the barriers), metric product (R, S to shared
-    //      memory, T in registers)
-    T tt[N], ut[N];
-    {
-      T u[N];
-#pragma unroll
-      for (int k = 0; k < N; ++k) u[k] = f0[k * SK + vo];
-      eo_mul<T, N, 0>(u, ut);
-    }
-    const int64_t pt0 = (((int64_t)l * g.n_ecol + (active ? ecol : 0)) * N) * L + line;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const T ur = f1[k * SK + vo], us = f2[k * SK + vo], uz = ut[k];
-      T R, Sv;
-      if constexpr (STORED) {
-        const int64_t pt = pt0 + (int64_t)k * L;
-        const T* G = a.G;
-        const T grr = G[pt], grs = G[PT + pt], gss = G[2 * PT + pt];
-        const T grt = G[3 * PT + pt], gst = G[4 * PT + pt], gtt = G[5 * PT + pt];
-        R = grr * ur + grs * us + grt * uz;
-        Sv = grs * ur + gss * us + gst * uz;
-        tt[k] = grt * ur + gst * us + gtt * uz;
-      } else {
-        const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
-        const T wk = sW[k];
-        const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
-        const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
-        const T wc = wk * lg.cw;
-        const T grt = -wc * (lg.rx * ax + lg.ry * ay);
-        const T gst = -wc * (lg.sx * ax + lg.sy * ay);
-        const T gtt = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
-        R = wk * (lg.grr * ur + lg.grs * us) + grt * uz;
-        Sv = wk * (lg.grs * ur + lg.gss * us) + gst * uz;
-        tt[k] = grt * ur + gst * us + gtt * uz;
+      __syncthreads();
+      // ---- R and S: r- and s-contractions of u
+      {
+        T v[N], r[N];
+  #pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = f0[ro + i];
+        eo_mul<T, N, 0>(v, r);
+  #pragma unroll
+        for (int i = 0; i < N; ++i) f1[ro + i] = r[i];
+  #pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = f0[so + j * SJ];
+        eo_mul<T, N, 0>(v, r);
+  #pragma unroll
+        for (int j = 0; j < N; ++j) f2[so + j * SJ] = r[j];
       }
-      f0[k * SK + vo] = R;
-      f3[k * SK + vo] = Sv;
+      __syncthreads();
+      // ---- V: t-contraction of the thread's own line (re-read: fewer live
+      //      registers across the barriers), metric product (R, S to shared
+      //      memory, T in registers)
+      T tt[N], ut[N];
+      {
+        T u[N];
+  #pragma unroll
+        for (int k = 0; k < N; ++k) u[k] = f0[k * SK + vo];
+        eo_mul<T, N, 0>(u, ut);
+      }
+      const int64_t pt0 = (((int64_t)l * g.n_ecol + (active ? ecol : 0)) * N) * L + line;
+  #pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T ur = f1[k * SK + vo], us = f2[k * SK + vo], uz = ut[k];
+        T R, Sv;
+        if constexpr (STORED) {
+          const int64_t pt = pt0 + (int64_t)k * L;
+          const T* G = a.G;
+          const T grr = G[pt], grs = G[PT + pt], gss = G[2 * PT + pt];
+          const T grt = G[3 * PT + pt], gst = G[4 * PT + pt], gtt = G[5 * PT + pt];
+          R = grr * ur + grs * us + grt * uz;
+          Sv = grs * ur + gss * us + gst * uz;
+          tt[k] = grt * ur + gst * us + gtt * uz;
+        } else {
+          const T sigma = (T(l) + T(0.5) * (T(1) + sXi[k])) * inv_nz;
+          const T wk = sW[k];
+          const T zr = lg.Pr + sigma * lg.Qr, zs = lg.Ps + sigma * lg.Qs;
+          const T ax = zr * lg.rx + zs * lg.sx, ay = zr * lg.ry + zs * lg.sy;
+          const T wc = wk * lg.cw;
+          const T grt = -wc * (lg.rx * ax + lg.ry * ay);
+          const T gst = -wc * (lg.sx * ax + lg.sy * ay);
+          const T gtt = wc * (ax * ax + ay * ay + T(1)) * lg.Ainv;
+          R = wk * (lg.grr * ur + lg.grs * us) + grt * uz;
+          Sv = wk * (lg.grs * ur + lg.gss * us) + gst * uz;
+          tt[k] = grt * ur + gst * us + gtt * uz;
+        }
+        f0[k * SK + vo] = R;
+        f3[k * SK + vo] = Sv;
+      }
+      __syncthreads();
+      // ---- R and S: transposed contractions
+      {
+        T v[N], r[N];
+  #pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = f0[ro + i];
+        eo_mul<T, N, 1>(v, r);
+  #pragma unroll
+        for (int i = 0; i < N; ++i) f1[ro + i] = r[i];
+  #pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = f3[so + j * SJ];
+        eo_mul<T, N, 1>(v, r);
+  #pragma unroll
+        for (int j = 0; j < N; ++j) f2[so + j * SJ] = r[j];
+      }
+      __syncthreads();
+      // ---- V: transposed t-contraction, sum, vertical assembly, stores
+      T y[N];
+      eo_mul<T, N, 1>(tt, y);
+  #pragma unroll
+      for (int k = 0; k < N; ++k) y[k] += f1[k * SK + vo] + f2[k * SK + vo];
+      y[0] += carry;
+      carry = y[P];
+      if (active) {
+  #pragma unroll
+        for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
+      }
     }
-    __syncthreads();
-    // ---- R and S: transposed contractions
-    {
-      T v[N], r[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) v[i] = f0[ro + i];
-      eo_mul<T, N, 1>(v, r);
-#pragma unroll
-      for (int i = 0; i < N; ++i) f1[ro + i] = r[i];
-#pragma unroll
-      for (int j = 0; j < N; ++j) v[j] = f3[so + j * SJ];
-      eo_mul<T, N, 1>(v, r);
-#pragma unroll
-      for (int j = 0; j < N; ++j) f2[so + j * SJ] = r[j];
-    }
-    __syncthreads();
-    // ---- V: transposed t-contraction, sum, vertical assembly, stores
-    T y[N];
-    eo_mul<T, N, 1>(tt, y);
-#pragma unroll
-    for (int k = 0; k < N; ++k) y[k] += f1[k * SK + vo] + f2[k * SK + vo];
-    y[0] += carry;
-    carry = y[P];
-    if (active) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) ax_put(g, a, ecol, col, slot, l * P + k, y[k]);
-    }
+    if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
   }
-  if (active) ax_put(g, a, ecol, col, slot, g.nv - 1, carry);
-}
+};
 
 }  // namespace fnpf

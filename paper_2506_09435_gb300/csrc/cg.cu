@@ -24,6 +24,7 @@
 #include "mesh.cuh"
 #include "mg.cuh"
 #include "vec.cuh"
+#include "graphs.cuh"
 
 #define FNPF_CK(call)                                              \
   do {                                                             \
@@ -43,146 +44,173 @@ using vec::reduce_partials;
 #define GRID_LOOP(i, n) FNPF_GRID_LOOP(i, n)
 
 // b = -y (y = A [0; phis]_I), r = b - q (q = A x), z = dinv r, p = z; partials bb, rz, rr.
-__global__ void __launch_bounds__(NT) cg_init_kernel(int64_t n, double* r, const double* q, const double* dinv,
-                                                     double* z, double* p, double* b_out, double* part, int nb) {
-  __shared__ double sh[vec::kShared];
-  double sbb = 0, srz = 0, srr = 0;
-  GRID_LOOP(i, n) {
-    const double b = -r[i];
-    const double rn = b - q[i];
-    if (b_out) b_out[i] = b;
-    r[i] = rn;
-    sbb += b * b;
-    srr += rn * rn;
-    if (dinv) {
-      const double zz = dinv[i] * rn;
-      z[i] = zz;
-      p[i] = zz;
-      srz += rn * zz;
+struct cg_init_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, double* r, const double* q, const double* dinv, double* z, double* p,
+                             double* b_out, double* part, int nb) {
+    __shared__ double sh[vec::kShared];
+    double sbb = 0, srz = 0, srr = 0;
+    GRID_LOOP(i, n) {
+      const double b = -r[i];
+      const double rn = b - q[i];
+      if (b_out) b_out[i] = b;
+      r[i] = rn;
+      sbb += b * b;
+      srr += rn * rn;
+      if (dinv) {
+        const double zz = dinv[i] * rn;
+        z[i] = zz;
+        p[i] = zz;
+        srz += rn * zz;
+      }
+    }
+    sbb = block_sum(sbb, sh);
+    srz = block_sum(srz, sh);
+    srr = block_sum(srr, sh);
+    if (threadIdx.x == 0) {
+      part[0 * nb + bk.x] = sbb;
+      part[1 * nb + bk.x] = srz;
+      part[2 * nb + bk.x] = srr;
     }
   }
-  sbb = block_sum(sbb, sh);
-  srz = block_sum(srz, sh);
-  srr = block_sum(srr, sh);
-  if (threadIdx.x == 0) {
-    part[0 * nb + blockIdx.x] = sbb;
-    part[1 * nb + blockIdx.x] = srz;
-    part[2 * nb + blockIdx.x] = srr;
-  }
-}
+};
 
 // Sets bb, rz[0], rr, tol2 from the partials; done if already converged.
-__global__ void __launch_bounds__(NT) cg_init_finish_kernel(CgScalars* sc, const double* part, int nb, double rtol2,
-                                                            double atol2) {
-  __shared__ double sh[vec::kShared];
-  const double bb = reduce_partials(part, nb, sh);
-  const double rz = reduce_partials(part + nb, nb, sh);
-  const double rr = reduce_partials(part + 2 * nb, nb, sh);
-  if (threadIdx.x == 0) {
-    sc->bb = bb;
-    sc->rz[0] = rz;
-    sc->rr = rr;
-    sc->iters = 0;
-    double tol2 = fmax(rtol2 * bb, atol2);
-    if (bb == 0.0) tol2 = fmax(rtol2 * rr, atol2);
-    sc->tol2 = tol2;
-    if (!isfinite(rr) || !isfinite(bb)) {
-      if (sc->status == 0) sc->status = FNPF_EDIVERGED;
-      sc->done = 1;
-    } else if (rr <= tol2) {
-      sc->done = 1;
+struct cg_init_finish_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, CgScalars* sc, const double* part, int nb, double rtol2, double atol2) {
+    __shared__ double sh[vec::kShared];
+    const double bb = reduce_partials(part, nb, sh);
+    const double rz = reduce_partials(part + nb, nb, sh);
+    const double rr = reduce_partials(part + 2 * nb, nb, sh);
+    if (threadIdx.x == 0) {
+      sc->bb = bb;
+      sc->rz[0] = rz;
+      sc->rr = rr;
+      sc->iters = 0;
+      double tol2 = fmax(rtol2 * bb, atol2);
+      if (bb == 0.0) tol2 = fmax(rtol2 * rr, atol2);
+      sc->tol2 = tol2;
+      if (!isfinite(rr) || !isfinite(bb)) {
+        if (sc->status == 0) sc->status = FNPF_EDIVERGED;
+        sc->done = 1;
+      } else if (rr <= tol2) {
+        sc->done = 1;
+      }
     }
   }
-}
+};
 
 // Inner (FP32) solve start from the FP64 residual: r32 = r64, e = 0, z = dinv r,
 // p = z; partials rz, rr (FP64).
-__global__ void __launch_bounds__(NT) inner_init_kernel(int64_t n, const double* r64, float* r, float* e, float* z,
-                                                        float* p, const float* dinv, double* part, int nb) {
-  __shared__ double sh[vec::kShared];
-  double srz = 0, srr = 0;
-  GRID_LOOP(i, n) {
-    const float rn = (float)r64[i];
-    r[i] = rn;
-    e[i] = 0.0f;
-    srr += (double)rn * (double)rn;
-    if (dinv) {
-      const float zz = dinv[i] * rn;
-      z[i] = zz;
-      p[i] = zz;
-      srz += (double)rn * (double)zz;
+struct inner_init_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, const double* r64, float* r, float* e, float* z, float* p,
+                             const float* dinv, double* part, int nb) {
+    __shared__ double sh[vec::kShared];
+    double srz = 0, srr = 0;
+    GRID_LOOP(i, n) {
+      const float rn = (float)r64[i];
+      r[i] = rn;
+      e[i] = 0.0f;
+      srr += (double)rn * (double)rn;
+      if (dinv) {
+        const float zz = dinv[i] * rn;
+        z[i] = zz;
+        p[i] = zz;
+        srz += (double)rn * (double)zz;
+      }
+    }
+    srz = block_sum(srz, sh);
+    srr = block_sum(srr, sh);
+    if (threadIdx.x == 0) {
+      if (dinv) part[1 * nb + bk.x] = srz;
+      part[2 * nb + bk.x] = srr;
     }
   }
-  srz = block_sum(srz, sh);
-  srr = block_sum(srr, sh);
-  if (threadIdx.x == 0) {
-    if (dinv) part[1 * nb + blockIdx.x] = srz;
-    part[2 * nb + blockIdx.x] = srr;
-  }
-}
+};
 
-__global__ void __launch_bounds__(NT) inner_init_finish_kernel(CgScalars* sc, const double* part, int nb,
-                                                               double rtol2) {
-  __shared__ double sh[vec::kShared];
-  const double rz = reduce_partials(part + nb, nb, sh);
-  const double rr = reduce_partials(part + 2 * nb, nb, sh);
-  if (threadIdx.x == 0) {
-    sc->bb = rr;
-    sc->rz[0] = rz;
-    sc->rr = rr;
-    sc->iters = 0;
-    sc->tol2 = rtol2 * rr;
-    sc->done = (rr == 0.0 || !isfinite(rr)) ? 1 : 0;
-    if (!isfinite(rr)) sc->status = FNPF_EDIVERGED;
+struct inner_init_finish_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, CgScalars* sc, const double* part, int nb, double rtol2) {
+    __shared__ double sh[vec::kShared];
+    const double rz = reduce_partials(part + nb, nb, sh);
+    const double rr = reduce_partials(part + 2 * nb, nb, sh);
+    if (threadIdx.x == 0) {
+      sc->bb = rr;
+      sc->rz[0] = rz;
+      sc->rr = rr;
+      sc->iters = 0;
+      sc->tol2 = rtol2 * rr;
+      sc->done = (rr == 0.0 || !isfinite(rr)) ? 1 : 0;
+      if (!isfinite(rr)) sc->status = FNPF_EDIVERGED;
+    }
   }
-}
+};
 
 // x += e (FP64 += FP32); the outer residual r = b - q follows q = A64 x.
-__global__ void __launch_bounds__(NT) add_correction_kernel(int64_t n, double* x, const float* e) {
-  GRID_LOOP(i, n) x[i] += (double)e[i];
-}
-
-__global__ void __launch_bounds__(NT) outer_residual_kernel(int64_t n, const double* b, const double* q, double* r,
-                                                            double* part, int nb) {
-  __shared__ double sh[vec::kShared];
-  double srr = 0;
-  GRID_LOOP(i, n) {
-    const double rn = b[i] - q[i];
-    r[i] = rn;
-    srr += rn * rn;
+struct add_correction_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, double* x, const float* e) {
+    GRID_LOOP(i, n) x[i] += (double)e[i];
   }
-  srr = block_sum(srr, sh);
-  if (threadIdx.x == 0) part[2 * nb + blockIdx.x] = srr;
-}
+};
 
-__global__ void __launch_bounds__(NT) outer_finish_kernel(CgScalars* sc, const double* part, int nb) {
-  __shared__ double sh[vec::kShared];
-  const double rr = reduce_partials(part + 2 * nb, nb, sh);
-  if (threadIdx.x == 0) {
-    sc->rr = rr;
-    sc->outer += 1;
-    if (!isfinite(rr)) {
-      sc->status = FNPF_EDIVERGED;
-      sc->done = 1;
-    } else if (rr <= sc->tol2) {
-      sc->done = 1;
+struct outer_residual_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, const double* b, const double* q, double* r, double* part, int nb) {
+    __shared__ double sh[vec::kShared];
+    double srr = 0;
+    GRID_LOOP(i, n) {
+      const double rn = b[i] - q[i];
+      r[i] = rn;
+      srr += rn * rn;
+    }
+    srr = block_sum(srr, sh);
+    if (threadIdx.x == 0) part[2 * nb + bk.x] = srr;
+  }
+};
+
+struct outer_finish_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, CgScalars* sc, const double* part, int nb) {
+    __shared__ double sh[vec::kShared];
+    const double rr = reduce_partials(part + 2 * nb, nb, sh);
+    if (threadIdx.x == 0) {
+      sc->rr = rr;
+      sc->outer += 1;
+      if (!isfinite(rr)) {
+        sc->status = FNPF_EDIVERGED;
+        sc->done = 1;
+      } else if (rr <= sc->tol2) {
+        sc->done = 1;
+      }
     }
   }
-}
+};
 
-__global__ void __launch_bounds__(NT) to_float_kernel(int64_t n, const double* a, float* b) {
-  GRID_LOOP(i, n) b[i] = (float)a[i];
-}
+struct to_float_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, const double* a, float* b) {
+    GRID_LOOP(i, n) b[i] = (float)a[i];
+  }
+};
 
 // Residual into the FP32 preconditioner and its result back (FNPF_FP64_PC32).
-__global__ void __launch_bounds__(NT) narrow_kernel(const int* skip, int64_t n, const double* a, float* b) {
-  if (skip && *skip) return;
-  GRID_LOOP(i, n) b[i] = (float)a[i];
-}
-__global__ void __launch_bounds__(NT) widen_kernel(const int* skip, int64_t n, const float* a, double* b) {
-  if (skip && *skip) return;
-  GRID_LOOP(i, n) b[i] = (double)a[i];
-}
+struct narrow_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, const int* skip, int64_t n, const double* a, float* b) {
+    if (skip && *skip) return;
+    GRID_LOOP(i, n) b[i] = (float)a[i];
+  }
+};
+struct widen_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, const int* skip, int64_t n, const float* a, double* b) {
+    if (skip && *skip) return;
+    GRID_LOOP(i, n) b[i] = (double)a[i];
+  }
+};
 
 // An FP64 solve whose p-multigrid preconditioner runs in FP32.
 inline bool pc32(const fnpf_mesh* m) {
@@ -275,7 +303,7 @@ fnpf_status autotune(fnpf_mesh* m, const double* eta, const double* G, cudaStrea
   const Geom& g = m->g;
   FNPF_CK(cudaMemsetAsync(m->p, 0, g.NI * sizeof(double), s));
   FNPF_CK(cudaMemsetAsync(m->p32, 0, g.NI * sizeof(float), s));
-  to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+  launch<to_float_kernel>(vec_blocks(g.ns), NT, 0, s, g.ns, eta, m->eta32);
   FNPF_CK(cudaGetLastError());
   fnpf_status st = tune_one<double>(m, m->tables(), eta, G, m->p, m->q, s, &m->variant64);
   if (st == FNPF_OK) st = tune_one<float>(m, m->tables32(), m->eta32, nullptr, m->p32, m->q32, s, &m->variant32);
@@ -332,12 +360,12 @@ cudaError_t apply_precond(fnpf_mesh* m, const Tables<T>& t, const T* eta, const 
   if (sizeof(T) == 8 && pc32(m)) {
     const int64_t NI = m->g.NI;
     const int nb = vec_blocks(NI);
-    narrow_kernel<<<nb, NT, 0, s>>>(skip, NI, reinterpret_cast<const double*>(r), m->r32);
+    launch<narrow_kernel>(nb, NT, 0, s, skip, NI, reinterpret_cast<const double*>(r), m->r32);
     cudaError_t e = mg_apply<float>(m->mg, m->tables32(), m->eta32, nullptr, m->r32, m->z32,
                                     reinterpret_cast<float*>(m->ring), m->variant32, m->opts.cheb_degree,
                                     m->opts.coarse_iters, skip, s, &m->launches);
     if (e != cudaSuccess) return e;
-    widen_kernel<<<nb, NT, 0, s>>>(skip, NI, m->z32, reinterpret_cast<double*>(z));
+    launch<widen_kernel>(nb, NT, 0, s, skip, NI, m->z32, reinterpret_cast<double*>(z));
     m->launches += 2;
     return cudaGetLastError();
   }
@@ -354,16 +382,16 @@ cudaError_t enqueue_iteration(fnpf_mesh* m, const Tables<T>& t, const PcgBufs<T>
   const int* skip = &B.sc->done;
   cudaError_t e = timed_apply<T>(m, t, B.eta, B.p, nullptr, B.q, s, skip, it);
   if (e != cudaSuccess) return e;
-  vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.p, B.q, m->partials + 3 * nb, B.sc, 3);
-  vec::update_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, pmg ? nullptr : B.dinv,
+  launch<vec::dot_kernel<T>>(nb, NT, 0, s, skip, NI, B.p, B.q, m->partials + 3 * nb, B.sc, 3);
+  launch<vec::update_kernel<T>>(nb, NT, 0, s, B.sc, it, NI, B.x, B.r, B.z, B.p, B.q, pmg ? nullptr : B.dinv,
                                           m->partials, nb, nullptr);
   if (pmg) {
     e = apply_precond<T>(m, t, B.eta, B.r, B.z, skip, s);
     if (e != cudaSuccess) return e;
-    vec::dot_kernel<T><<<nb, NT, 0, s>>>(skip, NI, B.r, B.z, m->partials + 1 * nb, B.sc, 1);
+    launch<vec::dot_kernel<T>>(nb, NT, 0, s, skip, NI, B.r, B.z, m->partials + 1 * nb, B.sc, 1);
     m->launches += 1;
   }
-  vec::pupdate_kernel<T><<<nb, NT, 0, s>>>(B.sc, it, NI, B.z, B.p, m->partials, nb, nullptr);
+  launch<vec::pupdate_kernel<T>>(nb, NT, 0, s, B.sc, it, NI, B.z, B.p, m->partials, nb, nullptr);
   m->launches += 3;
   return cudaGetLastError();
 }
@@ -426,8 +454,8 @@ fnpf_status pmg_start(fnpf_mesh* m, const Tables<T>& t, const T* eta, const T* r
   const int64_t NI = m->g.NI;
   const int nb = vec_blocks(NI);
   FNPF_CK(apply_precond<T>(m, t, eta, r, z, nullptr, s));
-  vec::copy_kernel<T><<<nb, NT, 0, s>>>(NI, z, p, nullptr);
-  vec::dot_kernel<T><<<nb, NT, 0, s>>>(nullptr, NI, r, z, m->partials + 1 * nb);
+  launch<vec::copy_kernel<T>>(nb, NT, 0, s, NI, z, p, nullptr);
+  launch<vec::dot_kernel<T>>(nb, NT, 0, s, nullptr, NI, r, z, m->partials + 1 * nb, nullptr, 0);
   m->launches += 2;
   FNPF_CK(cudaGetLastError());
   return FNPF_OK;
@@ -458,13 +486,19 @@ fnpf_status finish(fnpf_mesh* m, const CgScalars& h, bool done, int iters, int o
 
 }  // namespace
 
-__global__ void __launch_bounds__(NT) negate_kernel(int64_t n, const double* a, double* b) {
-  GRID_LOOP(i, n) b[i] = -a[i];
-}
+struct negate_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, const double* a, double* b) {
+    GRID_LOOP(i, n) b[i] = -a[i];
+  }
+};
 
-__global__ void __launch_bounds__(NT) scale_kernel(int64_t n, const double* d, const double* a, double* b) {
-  GRID_LOOP(i, n) b[i] = d[i] * a[i];
-}
+struct scale_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, const double* d, const double* a, double* b) {
+    GRID_LOOP(i, n) b[i] = d[i] * a[i];
+  }
+};
 
 // Validates the multigrid options, creates the hierarchy at the first use and
 // passes the coarse-solver choice on.
@@ -529,8 +563,8 @@ fnpf_status precond_apply(fnpf_mesh* m, const double* eta_in, const double* r, d
   const int nb = vec_blocks(g.NI);
   if (m->opts.precond != FNPF_PMG) {
     FNPF_CK(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
-    vec::invert_kernel<double><<<nb, NT, 0, s>>>(g.NI, m->dinv);
-    scale_kernel<<<nb, NT, 0, s>>>(g.NI, m->dinv, r, z);
+    launch<vec::invert_kernel<double>>(nb, NT, 0, s, g.NI, m->dinv);
+    launch<scale_kernel>(nb, NT, 0, s, g.NI, m->dinv, r, z);
     FNPF_CK(cudaGetLastError());
     return FNPF_OK;
   }
@@ -585,133 +619,144 @@ constexpr int kProjMaxNP = ProjSize<kMaxProjection + 1>::NP;
 
 // Per-block partials of G_ac = x_a . (A x_c) (a <= c) and f_a = x_a . b, b = -r.
 template <int K>
-__global__ void __launch_bounds__(NT) proj_gram_kernel(int64_t n, ProjBasis B, const double* r, double* part, int nb) {
-  constexpr int NP = ProjSize<K>::NP;
-  double acc[NP];
-#pragma unroll
-  for (int q = 0; q < NP; ++q) acc[q] = 0.0;
-  GRID_LOOP(i, n) {
-    double xv[K], av[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      xv[j] = B.x[j][i];
-      av[j] = B.ax[j][i];
+struct proj_gram_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, ProjBasis B, const double* r, double* part, int nb) {
+    constexpr int NP = ProjSize<K>::NP;
+    double acc[NP];
+  #pragma unroll
+    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+    GRID_LOOP(i, n) {
+      double xv[K], av[K];
+  #pragma unroll
+      for (int j = 0; j < K; ++j) {
+        xv[j] = B.x[j][i];
+        av[j] = B.ax[j][i];
+      }
+      const double b = -r[i];
+      int q = 0;
+  #pragma unroll
+      for (int a = 0; a < K; ++a)
+  #pragma unroll
+        for (int c = a; c < K; ++c) acc[q++] += xv[a] * av[c];
+  #pragma unroll
+      for (int a = 0; a < K; ++a) acc[q++] += xv[a] * b;
     }
-    const double b = -r[i];
-    int q = 0;
-#pragma unroll
-    for (int a = 0; a < K; ++a)
-#pragma unroll
-      for (int c = a; c < K; ++c) acc[q++] += xv[a] * av[c];
-#pragma unroll
-    for (int a = 0; a < K; ++a) acc[q++] += xv[a] * b;
+    __shared__ double sh[NT / 32][NP];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  #pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[wid][q] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NP; q += NT) {
+      double v = 0.0;
+      for (int w = 0; w < NT / 32; ++w) v += sh[w][q];
+      part[(int64_t)q * nb + bk.x] = v;
+    }
   }
-  __shared__ double sh[NT / 32][NP];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    double v = acc[q];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[wid][q] = v;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < NP; q += NT) {
-    double v = 0.0;
-    for (int w = 0; w < NT / 32; ++w) v += sh[w][q];
-    part[(int64_t)q * nb + blockIdx.x] = v;
-  }
-}
+};
 
 // One block: every sum over the partials in a fixed order (one warp per sum),
 // then thread 0 solves the K x K Gram system by Cholesky with dropping and
 // writes the coefficients c (0 for dropped vectors) to coef.
 template <int K>
-__global__ void __launch_bounds__(NT) proj_solve_kernel(const double* part, int nb, double* coef) {
-  constexpr int NP = ProjSize<K>::NP;
-  __shared__ double red[NP];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int q = wid; q < NP; q += NT / 32) {
-    double v = 0.0;
-    for (int k = lane; k < nb; k += 32) v += part[(int64_t)q * nb + k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  double G[K][K], f[K], Lw[K][K], z[K], c[K];
-  bool act[K];
-  int q = 0;
-  for (int a = 0; a < K; ++a)
-    for (int b = a; b < K; ++b) G[a][b] = G[b][a] = red[q++];
-  for (int a = 0; a < K; ++a) f[a] = red[q++];
-  for (int k = 0; k < K; ++k) {
-    double d = G[k][k];
-    for (int j = 0; j < k; ++j)
-      if (act[j]) d -= Lw[k][j] * Lw[k][j];
-    act[k] = isfinite(f[k]) && G[k][k] > 0.0 && isfinite(G[k][k]) && d > 1e-14 * G[k][k];
-    if (!act[k]) continue;
-    Lw[k][k] = sqrt(d);
-    for (int i = k + 1; i < K; ++i) {
-      double v = G[i][k];
-      for (int j = 0; j < k; ++j)
-        if (act[j]) v -= Lw[i][j] * Lw[k][j];
-      Lw[i][k] = v / Lw[k][k];
+struct proj_solve_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, const double* part, int nb, double* coef) {
+    constexpr int NP = ProjSize<K>::NP;
+    __shared__ double red[NP];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = wid; q < NP; q += NT / 32) {
+      double v = 0.0;
+      for (int k = lane; k < nb; k += 32) v += part[(int64_t)q * nb + k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[q] = v;
     }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double G[K][K], f[K], Lw[K][K], z[K], c[K];
+    bool act[K];
+    int q = 0;
+    for (int a = 0; a < K; ++a)
+      for (int b = a; b < K; ++b) G[a][b] = G[b][a] = red[q++];
+    for (int a = 0; a < K; ++a) f[a] = red[q++];
+    for (int k = 0; k < K; ++k) {
+      double d = G[k][k];
+      for (int j = 0; j < k; ++j)
+        if (act[j]) d -= Lw[k][j] * Lw[k][j];
+      act[k] = isfinite(f[k]) && G[k][k] > 0.0 && isfinite(G[k][k]) && d > 1e-14 * G[k][k];
+      if (!act[k]) continue;
+      Lw[k][k] = sqrt(d);
+      for (int i = k + 1; i < K; ++i) {
+        double v = G[i][k];
+        for (int j = 0; j < k; ++j)
+          if (act[j]) v -= Lw[i][j] * Lw[k][j];
+        Lw[i][k] = v / Lw[k][k];
+      }
+    }
+    for (int k = 0; k < K; ++k) {
+      z[k] = 0.0;
+      if (!act[k]) continue;
+      double v = f[k];
+      for (int j = 0; j < k; ++j)
+        if (act[j]) v -= Lw[k][j] * z[j];
+      z[k] = v / Lw[k][k];
+    }
+    for (int k = K - 1; k >= 0; --k) {
+      c[k] = 0.0;
+      if (!act[k]) continue;
+      double v = z[k];
+      for (int j = k + 1; j < K; ++j)
+        if (act[j]) v -= Lw[j][k] * c[j];
+      c[k] = v / Lw[k][k];
+    }
+    for (int k = 0; k < K; ++k) coef[k] = c[k];
   }
-  for (int k = 0; k < K; ++k) {
-    z[k] = 0.0;
-    if (!act[k]) continue;
-    double v = f[k];
-    for (int j = 0; j < k; ++j)
-      if (act[j]) v -= Lw[k][j] * z[j];
-    z[k] = v / Lw[k][k];
-  }
-  for (int k = K - 1; k >= 0; --k) {
-    c[k] = 0.0;
-    if (!act[k]) continue;
-    double v = z[k];
-    for (int j = k + 1; j < K; ++j)
-      if (act[j]) v -= Lw[j][k] * c[j];
-    c[k] = v / Lw[k][k];
-  }
-  for (int k = 0; k < K; ++k) coef[k] = c[k];
-}
+};
 
 // x0 = X c and A x0 = (A X) c (x and q may be basis vectors 0: read first).
 template <int K>
-__global__ void __launch_bounds__(NT) proj_combine_kernel(int64_t n, ProjBasis B, const double* coef, double* x,
-                                                          double* q) {
-  double c[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) c[j] = coef[j];
-  GRID_LOOP(i, n) {
-    double sx = 0.0, sq = 0.0;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      if (c[j] != 0.0) {
-        sx += c[j] * B.x[j][i];
-        sq += c[j] * B.ax[j][i];
+struct proj_combine_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, ProjBasis B, const double* coef, double* x, double* q) {
+    double c[K];
+  #pragma unroll
+    for (int j = 0; j < K; ++j) c[j] = coef[j];
+    GRID_LOOP(i, n) {
+      double sx = 0.0, sq = 0.0;
+  #pragma unroll
+      for (int j = 0; j < K; ++j) {
+        if (c[j] != 0.0) {
+          sx += c[j] * B.x[j][i];
+          sq += c[j] * B.ax[j][i];
+        }
       }
+      x[i] = sx;
+      q[i] = sq;
     }
-    x[i] = sx;
-    q[i] = sq;
   }
-}
+};
 
 // History push after a solve: H_j <- H_{j-1} (j = L-1 .. 1), H_0 <- x.
-__global__ void __launch_bounds__(NT) proj_push_kernel(int64_t n, int L, double* H, const double* x) {
-  GRID_LOOP(i, n) {
-    for (int j = L - 1; j > 0; --j) H[(int64_t)j * n + i] = H[(int64_t)(j - 1) * n + i];
-    H[i] = x[i];
+struct proj_push_kernel {
+  static constexpr int kThreads = NT;
+  __device__ static void run(Blk bk, int64_t n, int L, double* H, const double* x) {
+    GRID_LOOP(i, n) {
+      for (int j = L - 1; j > 0; --j) H[(int64_t)j * n + i] = H[(int64_t)(j - 1) * n + i];
+      H[i] = x[i];
+    }
   }
-}
+};
 
 template <int K>
 void launch_projection_k(int64_t n, const ProjBasis& B, const double* r, double* part, int nb, double* coef,
                          double* x, double* q, cudaStream_t s) {
-  proj_gram_kernel<K><<<nb, NT, 0, s>>>(n, B, r, part, nb);
-  proj_solve_kernel<K><<<1, NT, 0, s>>>(part, nb, coef);
-  proj_combine_kernel<K><<<nb, NT, 0, s>>>(n, B, coef, x, q);
+  launch<proj_gram_kernel<K>>(nb, NT, 0, s, n, B, r, part, nb);
+  launch<proj_solve_kernel<K>>(1, NT, 0, s, part, nb, coef);
+  launch<proj_combine_kernel<K>>(nb, NT, 0, s, n, B, coef, x, q);
 }
 
 // Allocates a history (zeroed: zero vectors are dropped) at its first use:
@@ -788,7 +833,7 @@ cudaError_t enqueue_projection(fnpf_mesh* m, const Tables<double>& t, const doub
 cudaError_t enqueue_projection_push(fnpf_mesh* m, const double* x, double* H, cudaStream_t s) {
   const int L = m->opts.projection;
   if (L <= 0) return cudaSuccess;
-  proj_push_kernel<<<vec_blocks(m->g.NI), NT, 0, s>>>(m->g.NI, L, H, x);
+  launch<proj_push_kernel>(vec_blocks(m->g.NI), NT, 0, s, m->g.NI, L, H, x);
   m->launches += 1;
   return cudaGetLastError();
 }
@@ -835,11 +880,11 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   }
   if (!mixed && !pmg && !keep64) {
     FNPF_CK(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
-    vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
+    launch<vec::invert_kernel<double>>(nb, NT, 0, s, NI, m->dinv);
   }
   if (!mixed && pmg && !keep64) {
     if (pc32(m)) {
-      to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+      launch<to_float_kernel>(vec_blocks(g.ns), NT, 0, s, g.ns, eta, m->eta32);
       FNPF_CK(mg_prepare<float>(m->mg, m->tables32(), m->eta32, nullptr, reinterpret_cast<float*>(m->ring),
                                 m->variant32, m->opts.cheb_degree, m->opts.coarse_iters, want_estimate(m, 1), s));
     } else {
@@ -851,7 +896,7 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   FNPF_CK(cudaGetLastError());
   // lift: r = A [0; phis]_I = -b (or r = -rhs); q = A [x; 0]_I; then b, r = b - q (, z, p)
   if (rhs) {
-    negate_kernel<<<nb, NT, 0, s>>>(NI, rhs, m->r);
+    launch<negate_kernel>(nb, NT, 0, s, NI, rhs, m->r);
     FNPF_CK(cudaGetLastError());
   } else {
     FNPF_CK(timed_apply<double>(m, t, eta, nullptr, phis, m->r, s, nullptr, -1));
@@ -866,13 +911,13 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     if (st != FNPF_OK) return st;
     FNPF_CK(enqueue_projection(m, t, eta, x, x != m->phi, hist, s));
   }
-  cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
+  launch<cg_init_kernel>(nb, NT, 0, s, NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
                                    mixed ? m->b : nullptr, m->partials, nb);
   if (!mixed && pmg) {
     fnpf_status st = pmg_start<double>(m, t, eta, m->r, m->z, m->p, s);
     if (st != FNPF_OK) return st;
   }
-  cg_init_finish_kernel<<<1, NT, 0, s>>>(sc, m->partials, nb, m->opts.rtol * m->opts.rtol,
+  launch<cg_init_finish_kernel>(1, NT, 0, s, sc, m->partials, nb, m->opts.rtol * m->opts.rtol,
                                          m->opts.atol * m->opts.atol);
   FNPF_CK(cudaGetLastError());
   m->launches += 4 + (mixed ? 0 : 3);
@@ -890,13 +935,13 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   // ---- mixed precision: FP64 defect correction around FP32 Jacobi-PCG
   const Tables<float> t32 = m->tables32();
   if (!(m->linear() && m->lpf_ready[1])) {
-    to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+    launch<to_float_kernel>(vec_blocks(g.ns), NT, 0, s, g.ns, eta, m->eta32);
     if (pmg) {
       FNPF_CK(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
                                 m->opts.cheb_degree, m->opts.coarse_iters, want_estimate(m, 1), s));
     } else {
       FNPF_CK(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
-      vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+      launch<vec::invert_kernel<float>>(nb, NT, 0, s, NI, m->dinv32);
     }
     if (m->linear()) m->lpf_ready[1] = true;
   }
@@ -915,13 +960,13 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
     // inner solve A32 e = r (FP32, Jacobi-PCG, relative tolerance inner_rtol)
     CgScalars* si = m->sc_in;
     FNPF_CK(cudaMemsetAsync(si, 0, sizeof(CgScalars), s));
-    inner_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->r32, m->e32, m->z32, m->p32, pmg ? nullptr : m->dinv32,
+    launch<inner_init_kernel>(nb, NT, 0, s, NI, m->r, m->r32, m->e32, m->z32, m->p32, pmg ? nullptr : m->dinv32,
                                         m->partials, nb);
     if (pmg) {
       fnpf_status st = pmg_start<float>(m, t32, m->eta32, m->r32, m->z32, m->p32, s);
       if (st != FNPF_OK) return st;
     }
-    inner_init_finish_kernel<<<1, NT, 0, s>>>(si, m->partials, nb, in_rtol2);
+    launch<inner_init_finish_kernel>(1, NT, 0, s, si, m->partials, nb, in_rtol2);
     FNPF_CK(cudaGetLastError());
     m->launches += 2;
     PcgBufs<float> B{m->eta32, m->e32, m->r32, m->z32, m->p32, m->q32, m->dinv32, si};
@@ -935,10 +980,10 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
       break;
     }
     // x += e; r = b - A64 x
-    add_correction_kernel<<<nb, NT, 0, s>>>(NI, x, m->e32);
+    launch<add_correction_kernel>(nb, NT, 0, s, NI, x, m->e32);
     FNPF_CK(timed_apply<double>(m, t, eta, x, nullptr, m->q, s, nullptr, -1));
-    outer_residual_kernel<<<nb, NT, 0, s>>>(NI, m->b, m->q, m->r, m->partials, nb);
-    outer_finish_kernel<<<1, NT, 0, s>>>(sc, m->partials, nb);
+    launch<outer_residual_kernel>(nb, NT, 0, s, NI, m->b, m->q, m->r, m->partials, nb);
+    launch<outer_finish_kernel>(1, NT, 0, s, sc, m->partials, nb);
     FNPF_CK(cudaGetLastError());
     m->launches += 3;
     ++outer;
@@ -959,26 +1004,59 @@ __global__ void set_cond_kernel(const CgScalars* sc, cudaGraphConditionalHandle 
   cudaGraphSetConditional(h, (!sc->done && cnt < cap) ? 1u : 0u);
 }
 
-// inner solve finished: propagate a breakdown to the outer scalars
-__global__ void inner_done_kernel(const CgScalars* si, CgScalars* so, int* inner_total) {
-  *inner_total += si->iters;
-  if (si->status == FNPF_EBREAKDOWN || si->status == FNPF_EDIVERGED) {
-    so->status = si->status;
-    so->done = 1;
+// Sets the loop condition h from the scalars (a recorded operation while a
+// Recorder is active).
+cudaError_t set_cond(const CgScalars* sc, cudaGraphConditionalHandle h, int cap, int use_outer, cudaStream_t s) {
+  if (Recorder* r = active_recorder()) {
+    Op op;
+    op.kind = OP_COND;
+    op.handle = (int)h;
+    op.sc = sc;
+    op.cap = cap;
+    op.use_outer = use_outer;
+    r->ops.push_back(std::move(op));
+    return cudaSuccess;
   }
+  set_cond_kernel<<<1, 1, 0, s>>>(sc, h, cap, use_outer);
+  return cudaPeekAtLastError();
 }
 
-__global__ void stage_info_kernel(const CgScalars* sc, const int* inner_total, int mixed, StageInfo* out) {
-  out->rr = sc->rr;
-  out->bb = sc->bb;
-  out->iters = mixed ? *inner_total : sc->iters;
-  out->outer = mixed ? sc->outer : 0;
-  int st = sc->status;
-  if (st == 0 && !sc->done) st = FNPF_ENOCONV;
-  out->status = st;
-}
+// inner solve finished: propagate a breakdown to the outer scalars
+struct inner_done_kernel {
+  static constexpr int kThreads = 1;
+  __device__ static void run(Blk bk, const CgScalars* si, CgScalars* so, int* inner_total) {
+    *inner_total += si->iters;
+    if (si->status == FNPF_EBREAKDOWN || si->status == FNPF_EDIVERGED) {
+      so->status = si->status;
+      so->done = 1;
+    }
+  }
+};
+
+struct stage_info_kernel {
+  static constexpr int kThreads = 1;
+  __device__ static void run(Blk bk, const CgScalars* sc, const int* inner_total, int mixed, StageInfo* out) {
+    out->rr = sc->rr;
+    out->bb = sc->bb;
+    out->iters = mixed ? *inner_total : sc->iters;
+    out->outer = mixed ? sc->outer : 0;
+    int st = sc->status;
+    if (st == 0 && !sc->done) st = FNPF_ENOCONV;
+    out->status = st;
+  }
+};
+
+}  // namespace
 
 cudaError_t new_handle(cudaStream_t s, cudaGraphConditionalHandle* h) {
+  if (Recorder* r = active_recorder()) {
+    Op op;
+    op.kind = OP_HANDLE;
+    op.handle = r->handles;
+    *h = (cudaGraphConditionalHandle)r->handles++;
+    r->ops.push_back(std::move(op));
+    return cudaSuccess;
+  }
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
@@ -1000,41 +1078,6 @@ int64_t kernel_nodes(cudaGraph_t g) {
   }
   return k;
 }
-
-// Appends a WHILE node controlled by h to the graph captured on s and captures
-// body(bs) into its body graph on stream bs; *body_kernels receives the number
-// of kernel nodes of the body.
-template <typename F>
-cudaError_t capture_while(cudaStream_t s, cudaStream_t bs, cudaGraphConditionalHandle h, int64_t* body_kernels,
-                          F&& body) {
-  cudaStreamCaptureStatus st;
-  cudaGraph_t g = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  const cudaGraphEdgeData* ed = nullptr;
-  size_t nd = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &ed, &nd);
-  if (e != cudaSuccess) return e;
-  cudaGraphNodeParams p{};
-  p.type = cudaGraphNodeTypeConditional;
-  p.conditional.handle = h;
-  p.conditional.type = cudaGraphCondTypeWhile;
-  p.conditional.size = 1;
-  cudaGraphNode_t node;
-  if ((e = cudaGraphAddNode(&node, g, deps, ed, nd, &p)) != cudaSuccess) return e;
-  if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
-    return e;
-  cudaGraph_t bodyg = p.conditional.phGraph_out[0];
-  if ((e = cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
-      cudaSuccess)
-    return e;
-  cudaError_t eb = body(bs);
-  cudaGraph_t out = nullptr;
-  e = cudaStreamEndCapture(bs, &out);
-  if (e == cudaSuccess && out) *body_kernels = kernel_nodes(out);
-  return eb != cudaSuccess ? eb : e;
-}
-
-}  // namespace
 
 int64_t graph_kernel_nodes(cudaGraph_t g) { return kernel_nodes(g); }
 
@@ -1059,10 +1102,10 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
       return e;                        \
     }                                  \
   } while (0)
-  ENQ(cudaMemcpyAsync(m->eta64, m->geom_eta(eta_in), g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  ENQ(memcpy_async(m->eta64, m->geom_eta(eta_in), g.ns * sizeof(double), cudaMemcpyDeviceToDevice, s));
   const double* eta = m->eta64;
-  ENQ(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
-  ENQ(cudaMemsetAsync(m->inner_total, 0, sizeof(int), s));
+  ENQ(memset_async(sc, 0, sizeof(CgScalars), s));
+  ENQ(memset_async(m->inner_total, 0, sizeof(int), s));
   ENQ(launch_check_state(g, eta, phis, m->dh, &sc->status, &sc->done, s));
   // linear potential flow: a host-driven step has done the set-up (lpf_ready)
   const bool keep64 = m->linear() && m->lpf_ready[0];
@@ -1074,11 +1117,11 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
   }
   if (!mixed && !pmg && !keep64) {
     ENQ(launch_diag<double>(g, t, eta, m->dinv, nullptr, m->ring, s));
-    vec::invert_kernel<double><<<nb, NT, 0, s>>>(NI, m->dinv);
+    launch<vec::invert_kernel<double>>(nb, NT, 0, s, NI, m->dinv);
   }
   if (!mixed && pmg && !keep64) {
     if (pc32(m)) {
-      to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+      launch<to_float_kernel>(vec_blocks(g.ns), NT, 0, s, g.ns, eta, m->eta32);
       ENQ(mg_prepare<float>(m->mg, m->tables32(), m->eta32, nullptr, reinterpret_cast<float*>(m->ring),
                             m->variant32, m->opts.cheb_degree, m->opts.coarse_iters, estimate, s));
     } else {
@@ -1091,81 +1134,81 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
   // the history buffers exist: a host-driven solve of the same options ran before
   const bool project = m->opts.projection > 0 && m->proj_alloc >= m->opts.projection;
   if (project) ENQ(enqueue_projection(m, t, eta, x, x != m->phi, m->projH, s));
-  cg_init_kernel<<<nb, NT, 0, s>>>(NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
+  launch<cg_init_kernel>(nb, NT, 0, s, NI, m->r, m->q, (mixed || pmg) ? nullptr : m->dinv, m->z, m->p,
                                    mixed ? m->b : nullptr, m->partials, nb);
   if (!mixed && pmg) {
     ENQ(apply_precond<double>(m, t, eta, m->r, m->z, nullptr, s));
-    vec::copy_kernel<double><<<nb, NT, 0, s>>>(NI, m->z, m->p, nullptr);
-    vec::dot_kernel<double><<<nb, NT, 0, s>>>(nullptr, NI, m->r, m->z, m->partials + 1 * nb);
+    launch<vec::copy_kernel<double>>(nb, NT, 0, s, NI, m->z, m->p, nullptr);
+    launch<vec::dot_kernel<double>>(nb, NT, 0, s, nullptr, NI, m->r, m->z, m->partials + 1 * nb, nullptr, 0);
   }
-  cg_init_finish_kernel<<<1, NT, 0, s>>>(sc, m->partials, nb, m->opts.rtol * m->opts.rtol,
+  launch<cg_init_finish_kernel>(1, NT, 0, s, sc, m->partials, nb, m->opts.rtol * m->opts.rtol,
                                          m->opts.atol * m->opts.atol);
   ENQ(cudaGetLastError());
   if (!mixed) {
     cudaGraphConditionalHandle h;
     ENQ(new_handle(s, &h));
-    set_cond_kernel<<<1, 1, 0, s>>>(sc, h, max_iter, 0);
+    set_cond(sc, h, max_iter, 0, s);
     PcgBufs<double> B{eta, x, m->r, m->z, m->p, m->q, m->dinv, sc};
     ENQ(capture_while(s, m->bstream[0], h, &m->body_kernels[0], [&](cudaStream_t bs) -> cudaError_t {
       cudaError_t eb = enqueue_iteration<double>(m, t, B, 0, bs);
       if (eb == cudaSuccess) eb = enqueue_iteration<double>(m, t, B, 1, bs);
-      set_cond_kernel<<<1, 1, 0, bs>>>(sc, h, max_iter, 0);
+      set_cond(sc, h, max_iter, 0, bs);
       return eb == cudaSuccess ? cudaGetLastError() : eb;
     }));
   } else {
     const Tables<float> t32 = m->tables32();
     if (!keep32) {
-      to_float_kernel<<<vec_blocks(g.ns), NT, 0, s>>>(g.ns, eta, m->eta32);
+      launch<to_float_kernel>(vec_blocks(g.ns), NT, 0, s, g.ns, eta, m->eta32);
       if (pmg) {
         ENQ(mg_prepare<float>(m->mg, t32, m->eta32, nullptr, reinterpret_cast<float*>(m->ring), m->variant32,
                               m->opts.cheb_degree, m->opts.coarse_iters, estimate, s));
       } else {
         ENQ(launch_diag<float>(g, t32, m->eta32, m->dinv32, nullptr, reinterpret_cast<float*>(m->ring), s));
-        vec::invert_kernel<float><<<nb, NT, 0, s>>>(NI, m->dinv32);
+        launch<vec::invert_kernel<float>>(nb, NT, 0, s, NI, m->dinv32);
       }
     }
     const int max_outer = std::max(1, m->opts.max_outer);
     const double in_rtol2 = m->opts.inner_rtol * m->opts.inner_rtol;
     cudaGraphConditionalHandle ho;
     ENQ(new_handle(s, &ho));
-    set_cond_kernel<<<1, 1, 0, s>>>(sc, ho, max_outer, 1);
+    set_cond(sc, ho, max_outer, 1, s);
     ENQ(capture_while(s, m->bstream[0], ho, &m->body_kernels[0], [&](cudaStream_t bs) -> cudaError_t {
       CgScalars* si = m->sc_in;
-      cudaError_t eb = cudaMemsetAsync(si, 0, sizeof(CgScalars), bs);
+      cudaError_t eb = memset_async(si, 0, sizeof(CgScalars), bs);
       if (eb != cudaSuccess) return eb;
-      inner_init_kernel<<<nb, NT, 0, bs>>>(NI, m->r, m->r32, m->e32, m->z32, m->p32, pmg ? nullptr : m->dinv32,
+      launch<inner_init_kernel>(nb, NT, 0, bs, NI, m->r, m->r32, m->e32, m->z32, m->p32, pmg ? nullptr : m->dinv32,
                                            m->partials, nb);
       if (pmg) {
         if ((eb = mg_apply<float>(m->mg, t32, m->eta32, nullptr, m->r32, m->z32, reinterpret_cast<float*>(m->ring),
                                   m->variant32, m->opts.cheb_degree, m->opts.coarse_iters, nullptr, bs,
                                   &m->launches)) != cudaSuccess)
           return eb;
-        vec::copy_kernel<float><<<nb, NT, 0, bs>>>(NI, m->z32, m->p32, nullptr);
-        vec::dot_kernel<float><<<nb, NT, 0, bs>>>(nullptr, NI, m->r32, m->z32, m->partials + 1 * nb);
+        launch<vec::copy_kernel<float>>(nb, NT, 0, bs, NI, m->z32, m->p32, nullptr);
+        launch<vec::dot_kernel<float>>(nb, NT, 0, bs, nullptr, NI, m->r32, m->z32, m->partials + 1 * nb, nullptr, 0);
       }
-      inner_init_finish_kernel<<<1, NT, 0, bs>>>(si, m->partials, nb, in_rtol2);
+      launch<inner_init_finish_kernel>(1, NT, 0, bs, si, m->partials, nb, in_rtol2);
       cudaGraphConditionalHandle hi;
       if ((eb = new_handle(bs, &hi)) != cudaSuccess) return eb;
-      set_cond_kernel<<<1, 1, 0, bs>>>(si, hi, max_iter, 0);
+      set_cond(si, hi, max_iter, 0, bs);
       PcgBufs<float> B{m->eta32, m->e32, m->r32, m->z32, m->p32, m->q32, m->dinv32, si};
       eb = capture_while(bs, m->bstream[1], hi, &m->body_kernels[1], [&](cudaStream_t bs2) -> cudaError_t {
         cudaError_t e2 = enqueue_iteration<float>(m, t32, B, 0, bs2);
         if (e2 == cudaSuccess) e2 = enqueue_iteration<float>(m, t32, B, 1, bs2);
-        set_cond_kernel<<<1, 1, 0, bs2>>>(si, hi, max_iter, 0);
+        set_cond(si, hi, max_iter, 0, bs2);
         return e2 == cudaSuccess ? cudaGetLastError() : e2;
       });
       if (eb != cudaSuccess) return eb;
-      inner_done_kernel<<<1, 1, 0, bs>>>(si, sc, m->inner_total);
-      add_correction_kernel<<<nb, NT, 0, bs>>>(NI, x, m->e32);
+      launch<inner_done_kernel>(1, 1, 0, bs, si, sc, m->inner_total);
+      launch<add_correction_kernel>(nb, NT, 0, bs, NI, x, m->e32);
       if ((eb = timed_apply<double>(m, t, eta, x, nullptr, m->q, bs, nullptr, -1)) != cudaSuccess) return eb;
-      outer_residual_kernel<<<nb, NT, 0, bs>>>(NI, m->b, m->q, m->r, m->partials, nb);
-      outer_finish_kernel<<<1, NT, 0, bs>>>(sc, m->partials, nb);
-      set_cond_kernel<<<1, 1, 0, bs>>>(sc, ho, max_outer, 1);
+      launch<outer_residual_kernel>(nb, NT, 0, bs, NI, m->b, m->q, m->r, m->partials, nb);
+      launch<outer_finish_kernel>(1, NT, 0, bs, sc, m->partials, nb);
+      set_cond(sc, ho, max_outer, 1, bs);
       return cudaGetLastError();
     }));
   }
   if (project) ENQ(enqueue_projection_push(m, x, m->projH, s));
-  stage_info_kernel<<<1, 1, 0, s>>>(sc, m->inner_total, mixed ? 1 : 0, info_dev);
+  launch<stage_info_kernel>(1, 1, 0, s, sc, m->inner_total, mixed ? 1 : 0, info_dev);
   m->g64_active = false;
   return cudaGetLastError();
 #undef ENQ

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "fnpf.h"
+#include "launch.cuh"
 
 namespace fnpf {
 

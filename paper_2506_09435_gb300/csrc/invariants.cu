@@ -14,43 +14,49 @@
 namespace {
 
 namespace vec = fnpf::vec;
+using fnpf::Blk;
+using fnpf::launch;
 
 // Per-block partials of (phi . y, sum eta / minv, sum eta^2 / minv) into
-// part[slot * gridDim.x + blockIdx.x].
-__global__ void __launch_bounds__(fnpf::vec::NT)
-    invariant_partials_kernel(int64_t n, const double* phi, const double* y, int ns, const double* eta,
-                              const double* minv, double* part) {
-  __shared__ double sh[fnpf::vec::kShared];
-  double a = 0, b = 0, c = 0;
-  FNPF_GRID_LOOP(i, n) a += phi[i] * y[i];
-  FNPF_GRID_LOOP(i, (int64_t)ns) {
-    const double w = 1.0 / minv[i];
-    b += w * eta[i];
-    c += w * eta[i] * eta[i];
+// part[slot * blocks + block].
+struct invariant_partials_kernel {
+  static constexpr int kThreads = fnpf::vec::NT;
+  __device__ static void run(Blk bk, int64_t n, const double* phi, const double* y, int ns, const double* eta,
+                             const double* minv, double* part) {
+    __shared__ double sh[fnpf::vec::kShared];
+    double a = 0, b = 0, c = 0;
+    FNPF_GRID_LOOP(i, n) a += phi[i] * y[i];
+    FNPF_GRID_LOOP(i, (int64_t)ns) {
+      const double w = 1.0 / minv[i];
+      b += w * eta[i];
+      c += w * eta[i] * eta[i];
+    }
+    a = fnpf::vec::block_sum(a, sh);
+    b = fnpf::vec::block_sum(b, sh);
+    c = fnpf::vec::block_sum(c, sh);
+    if (threadIdx.x == 0) {
+      part[bk.x] = a;
+      part[bk.nx + bk.x] = b;
+      part[2 * bk.nx + bk.x] = c;
+    }
   }
-  a = fnpf::vec::block_sum(a, sh);
-  b = fnpf::vec::block_sum(b, sh);
-  c = fnpf::vec::block_sum(c, sh);
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = a;
-    part[gridDim.x + blockIdx.x] = b;
-    part[2 * gridDim.x + blockIdx.x] = c;
-  }
-}
+};
 
 // One block: the three sums over the partials in a fixed order, then
 // out = (mass, energy).
-__global__ void __launch_bounds__(fnpf::vec::NT)
-    invariant_finish_kernel(const double* part, int nb, double g, double* out) {
-  __shared__ double sh[fnpf::vec::kShared];
-  const double a = fnpf::vec::reduce_partials(part, nb, sh);
-  const double b = fnpf::vec::reduce_partials(part + nb, nb, sh);
-  const double c = fnpf::vec::reduce_partials(part + 2 * nb, nb, sh);
-  if (threadIdx.x == 0) {
-    out[0] = b;
-    out[1] = 0.5 * a + 0.5 * g * c;
+struct invariant_finish_kernel {
+  static constexpr int kThreads = fnpf::vec::NT;
+  __device__ static void run(Blk bk, const double* part, int nb, double g, double* out) {
+    __shared__ double sh[fnpf::vec::kShared];
+    const double a = fnpf::vec::reduce_partials(part, nb, sh);
+    const double b = fnpf::vec::reduce_partials(part + nb, nb, sh);
+    const double c = fnpf::vec::reduce_partials(part + 2 * nb, nb, sh);
+    if (threadIdx.x == 0) {
+      out[0] = b;
+      out[1] = 0.5 * a + 0.5 * g * c;
+    }
   }
-}
+};
 
 fnpf_status fail(fnpf_mesh* m, cudaError_t e, const char* what) {
   m->err = std::string("invariants: ") + what + ": " + cudaGetErrorString(e);
@@ -81,10 +87,10 @@ extern "C" fnpf_status fnpf_invariants(fnpf_mesh* m, const double* eta, const do
                                              m->variant64, s);
   if (e != cudaSuccess) return fail(m, e, "operator");
   const int nb = fnpf::kVecBlocks;
-  invariant_partials_kernel<<<nb, fnpf::vec::NT, 0, s>>>(g.N, m->phi, y, g.ns, eta, m->dminv, m->partials);
+  launch<invariant_partials_kernel>(nb, fnpf::vec::NT, 0, s, g.N, m->phi, y, g.ns, eta, m->dminv, m->partials);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(m, e, "partials");
   double* out = m->partials + 3 * nb;
-  invariant_finish_kernel<<<1, fnpf::vec::NT, 0, s>>>(m->partials, nb, g.g, out);
+  launch<invariant_finish_kernel>(1, fnpf::vec::NT, 0, s, m->partials, nb, g.g, out);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(m, e, "finish");
   m->launches += 4;
   double host[2];

@@ -179,7 +179,7 @@ void graph_reset(GraphSlot* g);
 // Captured RK4 steps (api.cu).
 cudaError_t enqueue_step(fnpf_mesh* m, double* eta, double* phis, double dt, cudaStream_t s);
 cudaError_t enqueue_filter_step(fnpf_mesh* m, double* eta, double* phis, cudaStream_t s);
-fnpf_status read_step_info(fnpf_mesh* m, fnpf_solve_info* info, float ms);
+fnpf_status read_step_info(fnpf_mesh* m, fnpf_solve_info* info, float ms, bool count = true);
 bool graph_mode(const fnpf_mesh* m);
 int64_t graph_kernel_nodes(cudaGraph_t g);
 // Device-driven solve for graph capture (see cg.cu).

@@ -64,75 +64,86 @@ inline cudaError_t launch_transfer(const Geom& gf, const Geom& gc, const float* 
 
 // eta at the level's surface nodes: evaluation of the fine element polynomial.
 template <typename T>
-__global__ void surface_interp_kernel(Geom g0, Geom gl, const T* Js, const T* eta0, T* etal) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= gl.ns) return;
-  const int ix = col % gl.ncx, iy = col / gl.ncx;
-  int ex[2], io[2], ey[2] = {0, 0}, jo[2] = {0, 0};
-  line_owners(ix, gl.p, gl.nx, gl.px, ex, io);
-  if (gl.dim == 3) line_owners(iy, gl.p, gl.ny, gl.py, ey, jo);
-  const int n0 = g0.n;
-  T s = 0;
-  if (gl.dim == 3) {
-    for (int b = 0; b < n0; ++b) {
-      T sb = 0;
-      for (int a = 0; a < n0; ++a) sb += Js[io[0] * n0 + a] * eta0[node_col(g0, ex[0], ey[0], a, b)];
-      s += Js[jo[0] * n0 + b] * sb;
+struct surface_interp_kernel {
+  static constexpr int kThreads = 128;
+  __device__ static void run(Blk bk, Geom g0, Geom gl, const T* Js, const T* eta0, T* etal) {
+    const int col = bk.x * blockDim.x + threadIdx.x;
+    if (col >= gl.ns) return;
+    const int ix = col % gl.ncx, iy = col / gl.ncx;
+    int ex[2], io[2], ey[2] = {0, 0}, jo[2] = {0, 0};
+    line_owners(ix, gl.p, gl.nx, gl.px, ex, io);
+    if (gl.dim == 3) line_owners(iy, gl.p, gl.ny, gl.py, ey, jo);
+    const int n0 = g0.n;
+    T s = 0;
+    if (gl.dim == 3) {
+      for (int b = 0; b < n0; ++b) {
+        T sb = 0;
+        for (int a = 0; a < n0; ++a) sb += Js[io[0] * n0 + a] * eta0[node_col(g0, ex[0], ey[0], a, b)];
+        s += Js[jo[0] * n0 + b] * sb;
+      }
+    } else {
+      for (int a = 0; a < n0; ++a) s += Js[io[0] * n0 + a] * eta0[node_col(g0, ex[0], 0, a, 0)];
     }
-  } else {
-    for (int a = 0; a < n0; ++a) s += Js[io[0] * n0 + a] * eta0[node_col(g0, ex[0], 0, a, 0)];
+    etal[col] = s;
   }
-  etal[col] = s;
-}
+};
 
 // Deterministic pseudo-random right-hand side in [-0.5, 0.5) (splitmix64 of the index).
 template <typename T>
-__global__ void random_kernel(int64_t n, T* r) {
-  FNPF_GRID_LOOP(i, n) {
-    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    r[i] = (T)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+struct random_kernel {
+  static constexpr int kThreads = vec::NT;
+  __device__ static void run(Blk bk, int64_t n, T* r) {
+    FNPF_GRID_LOOP(i, n) {
+      uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      r[i] = (T)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    }
   }
-}
+};
 
 // Lanczos start: x = 0, z = dinv r, p = z; partials rz, rr.
 template <typename T>
-__global__ void __launch_bounds__(vec::NT) lz_init_kernel(int64_t n, const T* r, const T* dinv, T* x, T* z, T* p,
-                                                          double* part, int nb) {
-  __shared__ double sh[vec::kShared];
-  double srz = 0, srr = 0;
-  FNPF_GRID_LOOP(i, n) {
-    const T zz = dinv[i] * r[i];
-    x[i] = T(0);
-    z[i] = zz;
-    p[i] = zz;
-    srz += (double)r[i] * (double)zz;
-    srr += (double)r[i] * (double)r[i];
+struct lz_init_kernel {
+  static constexpr int kThreads = vec::NT;
+  __device__ static void run(Blk bk, int64_t n, const T* r, const T* dinv, T* x, T* z, T* p, double* part, int nb) {
+    __shared__ double sh[vec::kShared];
+    double srz = 0, srr = 0;
+    FNPF_GRID_LOOP(i, n) {
+      const T zz = dinv[i] * r[i];
+      x[i] = T(0);
+      z[i] = zz;
+      p[i] = zz;
+      srz += (double)r[i] * (double)zz;
+      srr += (double)r[i] * (double)r[i];
+    }
+    srz = vec::block_sum(srz, sh);
+    srr = vec::block_sum(srr, sh);
+    if (threadIdx.x == 0) {
+      part[1 * nb + bk.x] = srz;
+      part[2 * nb + bk.x] = srr;
+    }
   }
-  srz = vec::block_sum(srz, sh);
-  srr = vec::block_sum(srr, sh);
-  if (threadIdx.x == 0) {
-    part[1 * nb + blockIdx.x] = srz;
-    part[2 * nb + blockIdx.x] = srr;
-  }
-}
+};
 
-__global__ void __launch_bounds__(vec::NT) lz_init_finish_kernel(CgScalars* sc, const double* part, int nb) {
-  __shared__ double sh[vec::kShared];
-  const double rz = vec::reduce_partials(part + nb, nb, sh);
-  const double rr = vec::reduce_partials(part + 2 * nb, nb, sh);
-  if (threadIdx.x == 0) {
-    sc->rz[0] = rz;
-    sc->rr = rr;
-    sc->bb = rr;
-    sc->iters = 0;
-    sc->tol2 = 1e-28 * rr;
-    sc->status = 0;
-    sc->done = (rr > 0.0 && isfinite(rr)) ? 0 : 1;
+struct lz_init_finish_kernel {
+  static constexpr int kThreads = vec::NT;
+  __device__ static void run(Blk bk, CgScalars* sc, const double* part, int nb) {
+    __shared__ double sh[vec::kShared];
+    const double rz = vec::reduce_partials(part + nb, nb, sh);
+    const double rr = vec::reduce_partials(part + 2 * nb, nb, sh);
+    if (threadIdx.x == 0) {
+      sc->rz[0] = rz;
+      sc->rr = rr;
+      sc->bb = rr;
+      sc->iters = 0;
+      sc->tol2 = 1e-28 * rr;
+      sc->status = 0;
+      sc->done = (rr > 0.0 && isfinite(rr)) ? 0 : 1;
+    }
   }
-}
+};
 
 // Largest eigenvalue of the Lanczos tridiagonal matrix from the CG coefficients
 // (T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_j,j+1 = sqrt(b_j)/a_j), by Sturm counts:
@@ -141,112 +152,118 @@ __global__ void __launch_bounds__(vec::NT) lz_init_finish_kernel(CgScalars* sc, 
 // then lane 0 writes the smoother's step coefficients 1..ncoef-1 for kind 1
 // (first-kind Chebyshev on [lmax / range, lmax]) or kind 4 (fourth-kind
 // Chebyshev on [0, lmax], no lower bound needed).  Launch with one warp.
-__global__ void lz_eig_kernel(const CgScalars* sc, const double* hist, double safety, double range, int kind,
-                              int ncoef, ChebParams* out) {
-  const int lane = threadIdx.x;
-  int k = sc->iters < kLanczos ? sc->iters : kLanczos;
-  double a[kLanczos], b2[kLanczos];   // diagonal and squared off-diagonal
-  double hi = 0.0;
-#pragma unroll
-  for (int j = 0; j < kLanczos; ++j) {
-    a[j] = 0.0;
-    b2[j] = 0.0;
-    if (j < k) {
-      const double al = hist[2 * j];
-      a[j] = 1.0 / al + (j > 0 ? hist[2 * (j - 1) + 1] / hist[2 * (j - 1)] : 0.0);
-      const double bj = j + 1 < k ? sqrt(fmax(hist[2 * j + 1], 0.0)) / al : 0.0;
-      b2[j] = bj * bj;
+struct lz_eig_kernel {
+  static constexpr int kThreads = 32;
+  __device__ static void run(Blk bk, const CgScalars* sc, const double* hist, double safety, double range, int kind,
+                             int ncoef, ChebParams* out) {
+    const int lane = threadIdx.x;
+    int k = sc->iters < kLanczos ? sc->iters : kLanczos;
+    double a[kLanczos], b2[kLanczos];   // diagonal and squared off-diagonal
+    double hi = 0.0;
+  #pragma unroll
+    for (int j = 0; j < kLanczos; ++j) {
+      a[j] = 0.0;
+      b2[j] = 0.0;
+      if (j < k) {
+        const double al = hist[2 * j];
+        a[j] = 1.0 / al + (j > 0 ? hist[2 * (j - 1) + 1] / hist[2 * (j - 1)] : 0.0);
+        const double bj = j + 1 < k ? sqrt(fmax(hist[2 * j + 1], 0.0)) / al : 0.0;
+        b2[j] = bj * bj;
+      }
     }
-  }
-#pragma unroll
-  for (int j = 0; j < kLanczos; ++j)   // Gershgorin bound
-    if (j < k) hi = fmax(hi, a[j] + sqrt(b2[j]) + (j > 0 ? sqrt(b2[j - 1]) : 0.0));
-  double lmax;
-  if (k == 0) {
-    lmax = out->lmax > 0 ? out->lmax : 2.0;
-  } else {
-    double lo = 0.0;
-    for (int round = 0; round < 16; ++round) {
-      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-      int below = 0;
-      double d = 1.0;
-#pragma unroll
-      for (int j = 0; j < kLanczos; ++j) {
-        if (j < k) {
-          d = a[j] - x - (j > 0 ? b2[j - 1] / d : 0.0);
-          if (d == 0.0) d = -1e-300;
-          if (d < 0) ++below;
+  #pragma unroll
+    for (int j = 0; j < kLanczos; ++j)   // Gershgorin bound
+      if (j < k) hi = fmax(hi, a[j] + sqrt(b2[j]) + (j > 0 ? sqrt(b2[j - 1]) : 0.0));
+    double lmax;
+    if (k == 0) {
+      lmax = out->lmax > 0 ? out->lmax : 2.0;
+    } else {
+      double lo = 0.0;
+      for (int round = 0; round < 16; ++round) {
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        int below = 0;
+        double d = 1.0;
+  #pragma unroll
+        for (int j = 0; j < kLanczos; ++j) {
+          if (j < k) {
+            d = a[j] - x - (j > 0 ? b2[j - 1] / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0) ++below;
+          }
+        }
+        // first point with every eigenvalue below it brackets lmax from above
+        const unsigned all_below = __ballot_sync(0xffffffffu, below == k);
+        const double xl = __shfl_up_sync(0xffffffffu, x, 1);
+        if (all_below == 0u) {
+          lo = __shfl_sync(0xffffffffu, x, 31);
+        } else {
+          const int jf = __ffs(all_below) - 1;
+          const double nlo = jf == 0 ? lo : __shfl_sync(0xffffffffu, xl, jf);
+          hi = __shfl_sync(0xffffffffu, x, jf);
+          lo = nlo;
         }
       }
-      // first point with every eigenvalue below it brackets lmax from above
-      const unsigned all_below = __ballot_sync(0xffffffffu, below == k);
-      const double xl = __shfl_up_sync(0xffffffffu, x, 1);
-      if (all_below == 0u) {
-        lo = __shfl_sync(0xffffffffu, x, 31);
-      } else {
-        const int jf = __ffs(all_below) - 1;
-        const double nlo = jf == 0 ? lo : __shfl_sync(0xffffffffu, xl, jf);
-        hi = __shfl_sync(0xffffffffu, x, jf);
-        lo = nlo;
+      lmax = hi;
+    }
+    if (lane != 0) return;
+    const int nc = ncoef < kMaxChebDegree ? ncoef : kMaxChebDegree;
+    out->lmax = safety * lmax;
+    out->range = range;
+    out->c1[0] = 0.0;
+    out->c2[0] = 0.0;
+    if (kind == FNPF_CHEB_FOURTH) {
+      // Fourth-kind Chebyshev smoother (Lottes, "Optimal polynomial smoothers for
+      // multigrid V-cycles", Numer. Linear Algebra Appl. 2023): with rho = lmax,
+      // d_0 = 4 / (3 rho) D^-1 r_0 and, for k >= 1,
+      // d_k = (2k - 1) / (2k + 3) d_{k-1} + (8k + 4) / ((2k + 3) rho) D^-1 r_k.
+      const double rho = out->lmax;
+      out->inv_theta = 4.0 / (3.0 * rho);
+      for (int m = 1; m < nc; ++m) {
+        out->c1[m] = (2.0 * m - 1.0) / (2.0 * m + 3.0);
+        out->c2[m] = (8.0 * m + 4.0) / ((2.0 * m + 3.0) * rho);
       }
+      return;
     }
-    lmax = hi;
-  }
-  if (lane != 0) return;
-  const int nc = ncoef < kMaxChebDegree ? ncoef : kMaxChebDegree;
-  out->lmax = safety * lmax;
-  out->range = range;
-  out->c1[0] = 0.0;
-  out->c2[0] = 0.0;
-  if (kind == FNPF_CHEB_FOURTH) {
-    // Fourth-kind Chebyshev smoother (Lottes, "Optimal polynomial smoothers for
-    // multigrid V-cycles", Numer. Linear Algebra Appl. 2023): with rho = lmax,
-    // d_0 = 4 / (3 rho) D^-1 r_0 and, for k >= 1,
-    // d_k = (2k - 1) / (2k + 3) d_{k-1} + (8k + 4) / ((2k + 3) rho) D^-1 r_k.
-    const double rho = out->lmax;
-    out->inv_theta = 4.0 / (3.0 * rho);
+    // Chebyshev recurrence on [lmax / range, lmax]: theta = centre, delta = half
+    // width, sigma = theta / delta, rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1})
+    const double lm = out->lmax, lmin = lm / range;
+    const double theta = 0.5 * (lm + lmin), delta = 0.5 * (lm - lmin), sigma = theta / delta;
+    out->inv_theta = 1.0 / theta;
+    double rho_old = 1.0 / sigma;
     for (int m = 1; m < nc; ++m) {
-      out->c1[m] = (2.0 * m - 1.0) / (2.0 * m + 3.0);
-      out->c2[m] = (8.0 * m + 4.0) / ((2.0 * m + 3.0) * rho);
+      const double rho = 1.0 / (2.0 * sigma - rho_old);
+      out->c1[m] = rho * rho_old;
+      out->c2[m] = 2.0 * rho / delta;
+      rho_old = rho;
     }
-    return;
   }
-  // Chebyshev recurrence on [lmax / range, lmax]: theta = centre, delta = half
-  // width, sigma = theta / delta, rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1})
-  const double lm = out->lmax, lmin = lm / range;
-  const double theta = 0.5 * (lm + lmin), delta = 0.5 * (lm - lmin), sigma = theta / delta;
-  out->inv_theta = 1.0 / theta;
-  double rho_old = 1.0 / sigma;
-  for (int m = 1; m < nc; ++m) {
-    const double rho = 1.0 / (2.0 * sigma - rho_old);
-    out->c1[m] = rho * rho_old;
-    out->c2[m] = 2.0 * rho / delta;
-    rho_old = rho;
-  }
-}
+};
 
 // Step 0 of a Chebyshev sweep from x = 0 or a given x: (r = b if b given);
 // d = dinv r / theta; x = d or x += d.  Steps k >= 1 (r -= A d;
 // d = c1[k] d + c2[k] dinv r; x += d) and residuals are fused into the
 // gather stage of the operator launches (Epilogue).
 template <typename T>
-__global__ void __launch_bounds__(vec::NT) cheb_start_kernel(int64_t n, const T* b, T* r, const T* dinv, T* d, T* x,
-                                                             const ChebParams* cp, int x_zero, const int* skip) {
-  if (skip && *skip) return;
-  const T it = (T)cp->inv_theta;
-  FNPF_GRID_LOOP(i, n) {
-    T rr;
-    if (b) {
-      rr = b[i];
-      r[i] = rr;
-    } else {
-      rr = r[i];
+struct cheb_start_kernel {
+  static constexpr int kThreads = vec::NT;
+  __device__ static void run(Blk bk, int64_t n, const T* b, T* r, const T* dinv, T* d, T* x, const ChebParams* cp,
+                             int x_zero, const int* skip) {
+    if (skip && *skip) return;
+    const T it = (T)cp->inv_theta;
+    FNPF_GRID_LOOP(i, n) {
+      T rr;
+      if (b) {
+        rr = b[i];
+        r[i] = rr;
+      } else {
+        rr = r[i];
+      }
+      const T dd = it * dinv[i] * rr;
+      d[i] = dd;
+      x[i] = x_zero ? dd : x[i] + dd;
     }
-    const T dd = it * dinv[i] * rr;
-    d[i] = dd;
-    x[i] = x_zero ? dd : x[i] + dd;
   }
-}
+};
 
 // ---------------------------------------------------------------------------- coarsest level on one cluster
 //
@@ -271,69 +288,71 @@ struct Stencil {
 // One row per thread: the node's row of A_II, summed over the (up to 8)
 // elements that hold it in a fixed order.  coef[slot * NI + row].
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128) stencil_kernel(Geom g, const T* __restrict__ D, const T* __restrict__ G,
-                                                      T* coef) {
-  constexpr int NSL = Stencil<DIM>::slots;
-  constexpr int LQ = DIM == 3 ? 4 : 2;       // vertical lines of a p = 1 element column
-  constexpr int NJ = DIM == 3 ? 2 : 1;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= g.NI) return;
-  const int k = (int)(row / g.ns), col = (int)(row - (int64_t)k * g.ns);
-  const int ix = col % g.ncx, iy = col / g.ncx;
-  T acc[NSL];
-#pragma unroll
-  for (int q = 0; q < NSL; ++q) acc[q] = T(0);
-  int ex[2], ia[2], ey[2] = {0, 0}, jb[2] = {0, 0};
-  const int nxo = line_owners(ix, 1, g.nx, g.px, ex, ia);
-  const int nyo = DIM == 3 ? line_owners(iy, 1, g.ny, g.py, ey, jb) : 1;
-  const int64_t PT = (int64_t)g.nz * g.n_ecol * 2 * LQ;
-  for (int c = 0; c < 2; ++c) {           // local vertical index of the node in element layer l
-    const int l = k - c;
-    if (l < 0 || l >= g.nz) continue;
-    for (int yo = 0; yo < nyo; ++yo)
-      for (int xo = 0; xo < nxo; ++xo) {
-        const int a = ia[xo], b = jb[yo];
-        const int ecol = ey[yo] * g.nx + ex[xo];
-        for (int qk = 0; qk < 2; ++qk)
-          for (int qj = 0; qj < NJ; ++qj)
-            for (int qi = 0; qi < 2; ++qi) {
-              // reference gradient of the node's basis function at GLL point q
-              const T gr = (qj == b && qk == c) ? D[qi * 2 + a] : T(0);
-              const T gs = (DIM == 3 && qi == a && qk == c) ? D[qj * 2 + b] : T(0);
-              const T gt = (qi == a && qj == b) ? D[qk * 2 + c] : T(0);
-              if (gr == T(0) && gs == T(0) && gt == T(0)) continue;
-              const int64_t pt = (((int64_t)l * g.n_ecol + ecol) * 2 + qk) * LQ + qj * 2 + qi;
-              T vr, vs = T(0), vt;
-              if (DIM == 3) {
-                const T grr = G[pt], grs = G[PT + pt], gss = G[2 * PT + pt];
-                const T grt = G[3 * PT + pt], gst = G[4 * PT + pt], gtt = G[5 * PT + pt];
-                vr = grr * gr + grs * gs + grt * gt;
-                vs = grs * gr + gss * gs + gst * gt;
-                vt = grt * gr + gst * gs + gtt * gt;
-              } else {
-                const T grr = G[pt], grt = G[PT + pt], gtt = G[2 * PT + pt];
-                vr = grr * gr + grt * gt;
-                vt = grt * gr + gtt * gt;
+struct stencil_kernel {
+  static constexpr int kThreads = 128;
+  __device__ static void run(Blk bk, Geom g, const T* __restrict__ D, const T* __restrict__ G, T* coef) {
+    constexpr int NSL = Stencil<DIM>::slots;
+    constexpr int LQ = DIM == 3 ? 4 : 2;       // vertical lines of a p = 1 element column
+    constexpr int NJ = DIM == 3 ? 2 : 1;
+    const int64_t row = (int64_t)bk.x * blockDim.x + threadIdx.x;
+    if (row >= g.NI) return;
+    const int k = (int)(row / g.ns), col = (int)(row - (int64_t)k * g.ns);
+    const int ix = col % g.ncx, iy = col / g.ncx;
+    T acc[NSL];
+  #pragma unroll
+    for (int q = 0; q < NSL; ++q) acc[q] = T(0);
+    int ex[2], ia[2], ey[2] = {0, 0}, jb[2] = {0, 0};
+    const int nxo = line_owners(ix, 1, g.nx, g.px, ex, ia);
+    const int nyo = DIM == 3 ? line_owners(iy, 1, g.ny, g.py, ey, jb) : 1;
+    const int64_t PT = (int64_t)g.nz * g.n_ecol * 2 * LQ;
+    for (int c = 0; c < 2; ++c) {           // local vertical index of the node in element layer l
+      const int l = k - c;
+      if (l < 0 || l >= g.nz) continue;
+      for (int yo = 0; yo < nyo; ++yo)
+        for (int xo = 0; xo < nxo; ++xo) {
+          const int a = ia[xo], b = jb[yo];
+          const int ecol = ey[yo] * g.nx + ex[xo];
+          for (int qk = 0; qk < 2; ++qk)
+            for (int qj = 0; qj < NJ; ++qj)
+              for (int qi = 0; qi < 2; ++qi) {
+                // reference gradient of the node's basis function at GLL point q
+                const T gr = (qj == b && qk == c) ? D[qi * 2 + a] : T(0);
+                const T gs = (DIM == 3 && qi == a && qk == c) ? D[qj * 2 + b] : T(0);
+                const T gt = (qi == a && qj == b) ? D[qk * 2 + c] : T(0);
+                if (gr == T(0) && gs == T(0) && gt == T(0)) continue;
+                const int64_t pt = (((int64_t)l * g.n_ecol + ecol) * 2 + qk) * LQ + qj * 2 + qi;
+                T vr, vs = T(0), vt;
+                if (DIM == 3) {
+                  const T grr = G[pt], grs = G[PT + pt], gss = G[2 * PT + pt];
+                  const T grt = G[3 * PT + pt], gst = G[4 * PT + pt], gtt = G[5 * PT + pt];
+                  vr = grr * gr + grs * gs + grt * gt;
+                  vs = grs * gr + gss * gs + gst * gt;
+                  vt = grt * gr + gst * gs + gtt * gt;
+                } else {
+                  const T grr = G[pt], grt = G[PT + pt], gtt = G[2 * PT + pt];
+                  vr = grr * gr + grt * gt;
+                  vt = grt * gr + gtt * gt;
+                }
+                for (int c2 = 0; c2 < 2; ++c2)
+                  for (int b2 = 0; b2 < NJ; ++b2)
+                    for (int a2 = 0; a2 < 2; ++a2) {
+                      const T hr = (qj == b2 && qk == c2) ? D[qi * 2 + a2] : T(0);
+                      const T hs = (DIM == 3 && qi == a2 && qk == c2) ? D[qj * 2 + b2] : T(0);
+                      const T ht = (qi == a2 && qj == b2) ? D[qk * 2 + c2] : T(0);
+                      acc[Stencil<DIM>::slot(a2 - a, b2 - b, c2 - c)] += hr * vr + hs * vs + ht * vt;
+                    }
               }
-              for (int c2 = 0; c2 < 2; ++c2)
-                for (int b2 = 0; b2 < NJ; ++b2)
-                  for (int a2 = 0; a2 < 2; ++a2) {
-                    const T hr = (qj == b2 && qk == c2) ? D[qi * 2 + a2] : T(0);
-                    const T hs = (DIM == 3 && qi == a2 && qk == c2) ? D[qj * 2 + b2] : T(0);
-                    const T ht = (qi == a2 && qj == b2) ? D[qk * 2 + c2] : T(0);
-                    acc[Stencil<DIM>::slot(a2 - a, b2 - b, c2 - c)] += hr * vr + hs * vs + ht * vt;
-                  }
-            }
-      }
+        }
+    }
+    // the plane above the last interior one is the Dirichlet surface: not in A_II
+    if (k + 1 > g.nv - 2)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx)
+          if (DIM == 3 || dy == 0) acc[Stencil<DIM>::slot(dx, dy, 1)] = T(0);
+  #pragma unroll
+    for (int q = 0; q < NSL; ++q) coef[(int64_t)q * g.NI + row] = acc[q];
   }
-  // the plane above the last interior one is the Dirichlet surface: not in A_II
-  if (k + 1 > g.nv - 2)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx)
-        if (DIM == 3 || dy == 0) acc[Stencil<DIM>::slot(dx, dy, 1)] = T(0);
-#pragma unroll
-  for (int q = 0; q < NSL; ++q) coef[(int64_t)q * g.NI + row] = acc[q];
-}
+};
 
 // Neighbour index along one direction (-1 outside a walled boundary).
 __device__ __forceinline__ int nbr_index(int i, int o, int n, int periodic) {
@@ -392,58 +411,63 @@ __device__ __forceinline__ T stencil_row(const Geom& g, const T* __restrict__ co
 // keeps every CTA resident until no other CTA can read its shared memory.
 // Uniform control flow: every thread reaches every barrier.
 template <typename T, int DIM>
-__global__ void __cluster_dims__(kCoarseCluster, 1, 1) __launch_bounds__(kCoarseThreads)
-    coarse_cheb_kernel(Geom g, const T* __restrict__ coef, const T* __restrict__ dinv, const T* __restrict__ b,
-                       T* x, int log_r, const ChebParams* cp, int degree, const int* skip) {
-  if (skip && *skip) return;   // the same value for every CTA of the cluster
-  extern __shared__ __align__(16) unsigned char coarse_smem[];
-  T* sdir = reinterpret_cast<T*>(coarse_smem);
-  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-  const int R = 1 << log_r;
-  const int n = (int)g.NI;
-  const int row0 = (int)cl.block_rank() * R;
-  T r[kCoarseRows], xv[kCoarseRows], dv[kCoarseRows];
-  const T it = (T)cp->inv_theta;
-#pragma unroll
-  for (int m = 0; m < kCoarseRows; ++m) {
-    const int lr = threadIdx.x + m * blockDim.x, row = row0 + lr;
-    r[m] = xv[m] = dv[m] = T(0);
-    if (lr < R && row < n) {
-      r[m] = b[row];
-      dv[m] = it * dinv[row] * r[m];
-      xv[m] = dv[m];
-      sdir[lr] = dv[m];
-    }
-  }
-  for (int k = 1; k < degree; ++k) {
-    cl.sync();
-    T* cur = sdir + ((k - 1) & 1) * R;
-    T* nxt = sdir + (k & 1) * R;
-    const T c1 = (T)cp->c1[k], c2 = (T)cp->c2[k];
-#pragma unroll
+struct coarse_cheb_kernel {
+  static constexpr int kThreads = kCoarseThreads;
+  static constexpr int kCluster = kCoarseCluster;
+  static constexpr bool kFlexBlock = true;   // rows are assigned by R, any block of at least the mesh's threads
+  __device__ static void run(Blk bk, Geom g, const T* __restrict__ coef, const T* __restrict__ dinv,
+                             const T* __restrict__ b, T* x, int log_r, const ChebParams* cp, int degree,
+                             const int* skip) {
+    if (skip && *skip) return;   // the same value for every CTA of the cluster
+    extern __shared__ __align__(16) unsigned char coarse_smem[];
+    T* sdir = reinterpret_cast<T*>(coarse_smem);
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    const int R = 1 << log_r;
+    const int n = (int)g.NI;
+    const int row0 = (int)cl.block_rank() * R;
+    T r[kCoarseRows], xv[kCoarseRows], dv[kCoarseRows];
+    const T it = (T)cp->inv_theta;
+  #pragma unroll
     for (int m = 0; m < kCoarseRows; ++m) {
       const int lr = threadIdx.x + m * blockDim.x, row = row0 + lr;
+      r[m] = xv[m] = dv[m] = T(0);
       if (lr < R && row < n) {
-        r[m] -= stencil_row<T, DIM>(g, coef, cl, cur, log_r, row);
-        dv[m] = c1 * dv[m] + c2 * dinv[row] * r[m];
-        xv[m] += dv[m];
-        nxt[lr] = dv[m];
+        r[m] = b[row];
+        dv[m] = it * dinv[row] * r[m];
+        xv[m] = dv[m];
+        sdir[lr] = dv[m];
       }
     }
+    for (int k = 1; k < degree; ++k) {
+      cl.sync();
+      T* cur = sdir + ((k - 1) & 1) * R;
+      T* nxt = sdir + (k & 1) * R;
+      const T c1 = (T)cp->c1[k], c2 = (T)cp->c2[k];
+  #pragma unroll
+      for (int m = 0; m < kCoarseRows; ++m) {
+        const int lr = threadIdx.x + m * blockDim.x, row = row0 + lr;
+        if (lr < R && row < n) {
+          r[m] -= stencil_row<T, DIM>(g, coef, cl, cur, log_r, row);
+          dv[m] = c1 * dv[m] + c2 * dinv[row] * r[m];
+          xv[m] += dv[m];
+          nxt[lr] = dv[m];
+        }
+      }
+    }
+    cl.sync();
+  #pragma unroll
+    for (int m = 0; m < kCoarseRows; ++m) {
+      const int lr = threadIdx.x + m * blockDim.x, row = row0 + lr;
+      if (lr < R && row < n) x[row] = xv[m];
+    }
   }
-  cl.sync();
-#pragma unroll
-  for (int m = 0; m < kCoarseRows; ++m) {
-    const int lr = threadIdx.x + m * blockDim.x, row = row0 + lr;
-    if (lr < R && row < n) x[row] = xv[m];
-  }
-}
+};
 
 template <typename T>
 cudaError_t launch_stencil(const Geom& g, const T* D, const T* G, T* coef, cudaStream_t s) {
   const unsigned nb = (unsigned)((g.NI + 127) / 128);
-  if (g.dim == 3) stencil_kernel<T, 3><<<nb, 128, 0, s>>>(g, D, G, coef);
-  else stencil_kernel<T, 2><<<nb, 128, 0, s>>>(g, D, G, coef);
+  if (g.dim == 3) launch<stencil_kernel<T, 3>>(nb, 128, 0, s, g, D, G, coef);
+  else launch<stencil_kernel<T, 2>>(nb, 128, 0, s, g, D, G, coef);
   return cudaGetLastError();
 }
 
@@ -466,10 +490,10 @@ cudaError_t launch_coarse_cheb(const Geom& g, const T* coef, const T* dinv, cons
   const int threads = std::min(kCoarseThreads, std::max(32, (R + 31) / 32 * 32));
   const size_t smem = 2 * (size_t)R * sizeof(T);
   if (g.dim == 3)
-    coarse_cheb_kernel<T, 3><<<kCoarseCluster, threads, smem, s>>>(g, coef, dinv, b, x, log_r, cp, degree, skip);
-  else
-    coarse_cheb_kernel<T, 2><<<kCoarseCluster, threads, smem, s>>>(g, coef, dinv, b, x, log_r, cp, degree, skip);
-  return cudaGetLastError();
+    return launch<coarse_cheb_kernel<T, 3>>(kCoarseCluster, threads, smem, s, g, coef, dinv, b, x, log_r, cp, degree,
+                                            skip);
+  return launch<coarse_cheb_kernel<T, 2>>(kCoarseCluster, threads, smem, s, g, coef, dinv, b, x, log_r, cp, degree,
+                                          skip);
 }
 
 // Whether one cluster of the coarse kernel, with its largest shared-memory
@@ -478,10 +502,10 @@ cudaError_t launch_coarse_cheb(const Geom& g, const T* coef, const T* dinv, cons
 bool cluster_launch_ok() {
   constexpr int kMaxSmem = 2 * (kCoarseMaxRows / kCoarseCluster) * (int)sizeof(double);
   static std::atomic<uint64_t> a64_3{0}, a64_2{0}, a32_3{0}, a32_2{0};
-  if (smem_optin(coarse_cheb_kernel<double, 3>, kMaxSmem, &a64_3) != cudaSuccess ||
-      smem_optin(coarse_cheb_kernel<double, 2>, kMaxSmem, &a64_2) != cudaSuccess ||
-      smem_optin(coarse_cheb_kernel<float, 3>, kMaxSmem, &a32_3) != cudaSuccess ||
-      smem_optin(coarse_cheb_kernel<float, 2>, kMaxSmem, &a32_2) != cudaSuccess)
+  if (smem_optin(kernel_one<coarse_cheb_kernel<double, 3>>(), kMaxSmem, &a64_3) != cudaSuccess ||
+      smem_optin(kernel_one<coarse_cheb_kernel<double, 2>>(), kMaxSmem, &a64_2) != cudaSuccess ||
+      smem_optin(kernel_one<coarse_cheb_kernel<float, 3>>(), kMaxSmem, &a32_3) != cudaSuccess ||
+      smem_optin(kernel_one<coarse_cheb_kernel<float, 2>>(), kMaxSmem, &a32_2) != cudaSuccess)
     return false;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kCoarseCluster);
@@ -495,7 +519,7 @@ bool cluster_launch_ok() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nc = 0;
-  const cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, (const void*)coarse_cheb_kernel<double, 3>, &cfg);
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, (const void*)kernel_one<coarse_cheb_kernel<double, 3>>(), &cfg);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return false;
@@ -793,7 +817,7 @@ cudaError_t cheb_sweep(Mg* mg, int l, const Tables<T>& t0, const T* eta0, const 
   ep.d = L.Dd;
   ep.x = x;
   if (x_zero) {
-    cheb_start_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, b, L.R, L.dinv, L.Dd, x, cp, 1, skip);
+    launch<cheb_start_kernel<T>>(nb, vec::NT, 0, s, g.NI, b, L.R, L.dinv, L.Dd, x, cp, 1, skip);
     *nl += 1;
   } else {
     // r = b - A x; d = dinv r / theta; x += d (x is the operator input)
@@ -858,7 +882,7 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
   MgLevelBufs<T>* Lv = mg->bufs<T>();
   for (int l = 1; l < mg->L; ++l) {
     const Geom& gl = mg->g[l];
-    surface_interp_kernel<T><<<(gl.ns + 127) / 128, 128, 0, s>>>(mg->g[0], gl, Lv[l].Js, eta0, Lv[l].eta);
+    launch<surface_interp_kernel<T>>((gl.ns + 127) / 128, 128, 0, s, mg->g[0], gl, Lv[l].Js, eta0, Lv[l].eta);
   }
   for (int l = 0; l < mg->L; ++l) {
     const Geom& g = mg->g[l];
@@ -868,7 +892,7 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
     const int nb = vec::blocks_for(g.NI);
     const int lv = l == 0 ? variant : 1;
     if ((e = launch_diag<T>(g, t, eta, L.dinv, nullptr, ring, s)) != cudaSuccess) return e;
-    vec::invert_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.dinv);
+    launch<vec::invert_kernel<T>>(nb, vec::NT, 0, s, g.NI, L.dinv);
     const bool coarse_fused = l == mg->L - 1 && mg->fused();
     if (l > 0 && L.G && (G0 || coarse_fused))
       if ((e = launch_geom<T>(g, t, eta, L.G, s)) != cudaSuccess) return e;
@@ -877,22 +901,22 @@ cudaError_t mg_prepare(Mg* mg, const Tables<T>& t0, const T* eta0, const T* G0, 
     if (!estimate) continue;
     const T* Gl = l == 0 ? G0 : (G0 ? L.G : nullptr);
     // Lanczos through Jacobi-CG: x = X, r = R, z = Dd, p = P, q = W
-    random_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.R);
+    launch<random_kernel<T>>(nb, vec::NT, 0, s, g.NI, L.R);
     CgScalars* sc = mg->sc + l;
     double* hist = mg->hist + 2 * kLanczos * l;
-    lz_init_kernel<T><<<nb, vec::NT, 0, s>>>(g.NI, L.R, L.dinv, L.X, L.Dd, L.P, mg->part, nb);
-    lz_init_finish_kernel<<<1, vec::NT, 0, s>>>(sc, mg->part, nb);
+    launch<lz_init_kernel<T>>(nb, vec::NT, 0, s, g.NI, L.R, L.dinv, L.X, L.Dd, L.P, mg->part, nb);
+    launch<lz_init_finish_kernel>(1, vec::NT, 0, s, sc, mg->part, nb);
     for (int it = 0; it < kLanczos; ++it) {
       if ((e = level_apply<T>(g, t, eta, Gl, L.P, L.W, ring, lv, &sc->done, s)) != cudaSuccess) return e;
-      vec::dot_kernel<T><<<nb, vec::NT, 0, s>>>(&sc->done, g.NI, L.P, L.W, mg->part + 3 * nb, sc, 3);
-      vec::update_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.X, L.R, L.Dd, L.P, L.W, L.dinv, mg->part, nb,
+      launch<vec::dot_kernel<T>>(nb, vec::NT, 0, s, &sc->done, g.NI, L.P, L.W, mg->part + 3 * nb, sc, 3);
+      launch<vec::update_kernel<T>>(nb, vec::NT, 0, s, sc, it, g.NI, L.X, L.R, L.Dd, L.P, L.W, L.dinv, mg->part, nb,
                                                    hist);
-      vec::pupdate_kernel<T><<<nb, vec::NT, 0, s>>>(sc, it, g.NI, L.Dd, L.P, mg->part, nb, hist);
+      launch<vec::pupdate_kernel<T>>(nb, vec::NT, 0, s, sc, it, g.NI, L.Dd, L.P, mg->part, nb, hist);
     }
     const double range =
         l == mg->L - 1 ? fmax(mg->cheb_range, 0.25 * coarse_degree * coarse_degree) : mg->cheb_range;
     const int ncoef = l == mg->L - 1 ? coarse_degree : cheb_degree;
-    lz_eig_kernel<<<1, 32, 0, s>>>(sc, hist, kSafety, range, mg->cheb_kind, ncoef, mg->cheb<T>() + l);
+    launch<lz_eig_kernel>(1, 32, 0, s, sc, hist, kSafety, range, mg->cheb_kind, ncoef, mg->cheb<T>() + l);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

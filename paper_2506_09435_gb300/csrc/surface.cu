@@ -75,97 +75,106 @@ __device__ inline void zakharov_node(const Geom& g, const Tables<double>& t, con
   *kp = sp * t.minv[col];
 }
 
-__global__ void stage_kernel(Geom g, Tables<double> t, StageArgs a) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= g.ns) return;
-  const int ix = col % g.ncx, iy = col / g.ncx;
-  const double e0 = a.eta[col];
-  const double hh = t.h[col];
-  if (!(e0 + hh > 0.0) || !isfinite(e0) || !isfinite(a.phis[col])) {
-    if (a.status) atomicExch(a.status, (int)FNPF_EDIVERGED);
-  }
-  double ke, kp;
-  if (a.rhs_in && !a.linear) {
-    // over-integrated right-hand side (dealias.cu)
-    ke = a.rhs_in[col];
-    kp = a.rhs_in[g.ns + col];
-  } else if (a.linear) {
-    const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.geo ? a.geo : a.eta, col);
-    // linear potential flow: the surface conditions linearised about z = 0
-    ke = w;
-    kp = -g.g * e0;
-  } else {
-    const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.geo ? a.geo : a.eta, col);
-    zakharov_node(g, t, a, col, ix, iy, w, e0, &ke, &kp);
-  }
-  if (a.deta) {
-    a.deta[col] = ke;
-    a.dphis[col] = kp;
-  }
-  if (a.out_eta) {
-    const double acc_e = (a.first ? 0.0 : a.acc_eta[col]) + a.bw * ke;
-    const double acc_p = (a.first ? 0.0 : a.acc_phi[col]) + a.bw * kp;
-    const double y0e = a.y0_eta[col], y0p = a.y0_phi[col];
-    if (a.last) {
-      double ye = y0e + a.dt * acc_e, yp = y0p + a.dt * acc_p;
-      if (a.cr) {
-        // relaxation zones: f <- (1 - C_r) f + C_r f_true at t + dt
-        const double c = a.cr[col];
-        if (c != 0.0) {
-          double te = 0.0, tp = 0.0;
-          if (a.gen[col] != 0.0) {
-            const double t_end = a.t_dev ? *a.t_dev + a.dt : a.t_end;
-            const double ramp = fmin(1.0, t_end / a.ramp_time);
-            const double th = a.kx * a.xs[col] + a.ky * a.ys[col] - a.omega * t_end + a.phase;
-            const double k = hypot(a.kx, a.ky);
-            te = ramp * a.amp * cos(th);
-            tp = ramp * (g.g * a.amp / a.omega) * cosh(k * (te + hh)) / cosh(k * hh) * sin(th);
-          }
-          ye = (1.0 - c) * ye + c * te;
-          yp = (1.0 - c) * yp + c * tp;
-        }
-      }
-      a.out_eta[col] = ye;
-      a.out_phi[col] = yp;
+struct stage_kernel {
+  static constexpr int kThreads = 128;
+  __device__ static void run(Blk bk, Geom g, Tables<double> t, StageArgs a) {
+    const int col = bk.x * blockDim.x + threadIdx.x;
+    if (col >= g.ns) return;
+    const int ix = col % g.ncx, iy = col / g.ncx;
+    const double e0 = a.eta[col];
+    const double hh = t.h[col];
+    if (!(e0 + hh > 0.0) || !isfinite(e0) || !isfinite(a.phis[col])) {
+      if (a.status) atomicExch(a.status, (int)FNPF_EDIVERGED);
+    }
+    double ke, kp;
+    if (a.rhs_in && !a.linear) {
+      // over-integrated right-hand side (dealias.cu)
+      ke = a.rhs_in[col];
+      kp = a.rhs_in[g.ns + col];
+    } else if (a.linear) {
+      const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.geo ? a.geo : a.eta, col);
+      // linear potential flow: the surface conditions linearised about z = 0
+      ke = w;
+      kp = -g.g * e0;
     } else {
-      a.acc_eta[col] = acc_e;
-      a.acc_phi[col] = acc_p;
-      a.out_eta[col] = y0e + a.cn * ke;
-      a.out_phi[col] = y0p + a.cn * kp;
+      const double w = a.w_in ? a.w_in[col] : top_w(g, t.D, a.phi, a.phis, t.h, a.geo ? a.geo : a.eta, col);
+      zakharov_node(g, t, a, col, ix, iy, w, e0, &ke, &kp);
+    }
+    if (a.deta) {
+      a.deta[col] = ke;
+      a.dphis[col] = kp;
+    }
+    if (a.out_eta) {
+      const double acc_e = (a.first ? 0.0 : a.acc_eta[col]) + a.bw * ke;
+      const double acc_p = (a.first ? 0.0 : a.acc_phi[col]) + a.bw * kp;
+      const double y0e = a.y0_eta[col], y0p = a.y0_phi[col];
+      if (a.last) {
+        double ye = y0e + a.dt * acc_e, yp = y0p + a.dt * acc_p;
+        if (a.cr) {
+          // relaxation zones: f <- (1 - C_r) f + C_r f_true at t + dt
+          const double c = a.cr[col];
+          if (c != 0.0) {
+            double te = 0.0, tp = 0.0;
+            if (a.gen[col] != 0.0) {
+              const double t_end = a.t_dev ? *a.t_dev + a.dt : a.t_end;
+              const double ramp = fmin(1.0, t_end / a.ramp_time);
+              const double th = a.kx * a.xs[col] + a.ky * a.ys[col] - a.omega * t_end + a.phase;
+              const double k = hypot(a.kx, a.ky);
+              te = ramp * a.amp * cos(th);
+              tp = ramp * (g.g * a.amp / a.omega) * cosh(k * (te + hh)) / cosh(k * hh) * sin(th);
+            }
+            ye = (1.0 - c) * ye + c * te;
+            yp = (1.0 - c) * yp + c * tp;
+          }
+        }
+        a.out_eta[col] = ye;
+        a.out_phi[col] = yp;
+      } else {
+        a.acc_eta[col] = acc_e;
+        a.acc_phi[col] = acc_p;
+        a.out_eta[col] = y0e + a.cn * ke;
+        a.out_phi[col] = y0p + a.cn * kp;
+      }
     }
   }
-}
+};
 
-__global__ void w_kernel(Geom g, Tables<double> t, const double* eta, const double* phis, const double* phi,
-                         double* w) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= g.ns) return;
-  w[col] = top_w(g, t.D, phi, phis, t.h, eta, col);
-}
-
-__global__ void check_state_kernel(Geom g, const double* eta, const double* phis, const double* h, int* status,
-                                   int* done) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= g.ns) return;
-  const double e = eta[col];
-  if (!(e + h[col] > 0.0) || !isfinite(e) || !isfinite(phis[col])) {
-    atomicExch(status, (int)FNPF_EDIVERGED);
-    atomicExch(done, 1);
+struct w_kernel {
+  static constexpr int kThreads = 128;
+  __device__ static void run(Blk bk, Geom g, Tables<double> t, const double* eta, const double* phis,
+                             const double* phi, double* w) {
+    const int col = bk.x * blockDim.x + threadIdx.x;
+    if (col >= g.ns) return;
+    w[col] = top_w(g, t.D, phi, phis, t.h, eta, col);
   }
-}
+};
+
+struct check_state_kernel {
+  static constexpr int kThreads = 128;
+  __device__ static void run(Blk bk, Geom g, const double* eta, const double* phis, const double* h, int* status,
+                             int* done) {
+    const int col = bk.x * blockDim.x + threadIdx.x;
+    if (col >= g.ns) return;
+    const double e = eta[col];
+    if (!(e + h[col] > 0.0) || !isfinite(e) || !isfinite(phis[col])) {
+      atomicExch(status, (int)FNPF_EDIVERGED);
+      atomicExch(done, 1);
+    }
+  }
+};
 
 }  // namespace
 
 cudaError_t launch_stage(const Geom& g, const Tables<double>& t, const StageArgs& a, cudaStream_t s) {
   const int threads = 128;
-  stage_kernel<<<(g.ns + threads - 1) / threads, threads, 0, s>>>(g, t, a);
+  launch<stage_kernel>((g.ns + threads - 1) / threads, threads, 0, s, g, t, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_w(const Geom& g, const Tables<double>& t, const double* eta, const double* phis,
                      const double* phi, double* w, cudaStream_t s) {
   const int threads = 128;
-  w_kernel<<<(g.ns + threads - 1) / threads, threads, 0, s>>>(g, t, eta, phis, phi, w);
+  launch<w_kernel>((g.ns + threads - 1) / threads, threads, 0, s, g, t, eta, phis, phi, w);
   return cudaGetLastError();
 }
 
@@ -174,50 +183,52 @@ namespace {
 // One thread per surface column: an element-interior node (i, j) of element
 // column (ex, ey) gets sum_a sum_b F[i][a] F[j][b] f(a, b) (sum_a F[i][a] f(a)
 // in a 2D slice); every other node is copied.
-__global__ void filter_kernel(Geom g, const double* __restrict__ F, const double* __restrict__ in0,
-                              double* __restrict__ out0, const double* __restrict__ in1,
-                              double* __restrict__ out1) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= g.ns) return;
-  const int P = g.p, n = g.n;
-  const int ix = col % g.ncx, iy = col / g.ncx;
-  const int i = ix % P, j = g.dim == 3 ? iy % P : 0;
-  const bool interior = i != 0 && (g.dim == 2 || j != 0);
-  if (!interior) {
-    out0[col] = in0[col];
-    if (in1) out1[col] = in1[col];
-    return;
-  }
-  const int ex = ix / P, ey = g.dim == 3 ? iy / P : 0;
-  double s0 = 0.0, s1 = 0.0;
-  for (int b = 0; b < (g.dim == 3 ? n : 1); ++b) {
-    double t0 = 0.0, t1 = 0.0;
-    for (int a = 0; a < n; ++a) {
-      const int c = node_col(g, ex, ey, a, b);
-      t0 += F[i * n + a] * in0[c];
-      if (in1) t1 += F[i * n + a] * in1[c];
+struct filter_kernel {
+  static constexpr int kThreads = 128;
+  __device__ static void run(Blk bk, Geom g, const double* __restrict__ F, const double* __restrict__ in0,
+                             double* __restrict__ out0, const double* __restrict__ in1, double* __restrict__ out1) {
+    const int col = bk.x * blockDim.x + threadIdx.x;
+    if (col >= g.ns) return;
+    const int P = g.p, n = g.n;
+    const int ix = col % g.ncx, iy = col / g.ncx;
+    const int i = ix % P, j = g.dim == 3 ? iy % P : 0;
+    const bool interior = i != 0 && (g.dim == 2 || j != 0);
+    if (!interior) {
+      out0[col] = in0[col];
+      if (in1) out1[col] = in1[col];
+      return;
     }
-    const double fj = g.dim == 3 ? F[j * n + b] : 1.0;
-    s0 += fj * t0;
-    s1 += fj * t1;
+    const int ex = ix / P, ey = g.dim == 3 ? iy / P : 0;
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = 0; b < (g.dim == 3 ? n : 1); ++b) {
+      double t0 = 0.0, t1 = 0.0;
+      for (int a = 0; a < n; ++a) {
+        const int c = node_col(g, ex, ey, a, b);
+        t0 += F[i * n + a] * in0[c];
+        if (in1) t1 += F[i * n + a] * in1[c];
+      }
+      const double fj = g.dim == 3 ? F[j * n + b] : 1.0;
+      s0 += fj * t0;
+      s1 += fj * t1;
+    }
+    out0[col] = s0;
+    if (in1) out1[col] = s1;
   }
-  out0[col] = s0;
-  if (in1) out1[col] = s1;
-}
+};
 
 }  // namespace
 
 cudaError_t launch_filter(const Geom& g, const double* F, const double* in0, double* out0, const double* in1,
                           double* out1, cudaStream_t s) {
   const int threads = 128;
-  filter_kernel<<<(g.ns + threads - 1) / threads, threads, 0, s>>>(g, F, in0, out0, in1, out1);
+  launch<filter_kernel>((g.ns + threads - 1) / threads, threads, 0, s, g, F, in0, out0, in1, out1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_check_state(const Geom& g, const double* eta, const double* phis, const double* h, int* status,
                                int* done, cudaStream_t s) {
   const int threads = 128;
-  check_state_kernel<<<(g.ns + threads - 1) / threads, threads, 0, s>>>(g, eta, phis, h, status, done);
+  launch<check_state_kernel>((g.ns + threads - 1) / threads, threads, 0, s, g, eta, phis, h, status, done);
   return cudaGetLastError();
 }
 

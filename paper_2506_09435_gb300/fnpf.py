@@ -96,6 +96,9 @@ def load():
         "fnpf_tape_end": [vp],
         "fnpf_step_adjoint_taped": [vp, ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_double, vp],
         "fnpf_ensemble_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
+        "fnpf_ensemble_set_batching": [vp, ctypes.c_int],
+        "fnpf_ensemble_stats": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int64)],
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
@@ -464,6 +467,22 @@ class Ensemble:
 
     def __del__(self):
         self.close()
+
+    def set_batching(self, on):
+        """Batched groups (True, the default) or one branch of per-tank kernels
+        per tank (False), from the next step on."""
+        st = _LIB.fnpf_ensemble_set_batching(self._h, 1 if on else 0)
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_ensemble_last_error(self._h).decode())
+
+    def stats(self):
+        """{"groups", "batched_tanks", "kernels"}: batched groups and their tanks
+        in the current graph, kernels launched by the last ensemble step."""
+        g, b, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        st = _LIB.fnpf_ensemble_stats(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(k))
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_ensemble_last_error(self._h).decode())
+        return {"groups": g.value, "batched_tanks": b.value, "kernels": k.value}
 
     def rk4_step(self, etas, phiss, ts, dts, stream=None, info=False):
         n = len(self.meshes)

@@ -1,0 +1,128 @@
+"""Batched groups of the ensemble: tanks of one order share every kernel
+launch of the RK4 step (one launch over the concatenated grids, device-side
+loops that run while any tank's loop runs, per-tank gates).  Each tank still
+executes exactly the operations of its own step, so the batched ensemble
+equals the tanks stepped one at a time bit for bit (with the same kernel
+shapes), equals the oracle's RK4 steps, and launches far fewer kernels than
+one branch of per-tank kernels per tank."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mesh as omesh
+from oracle import surface as osurf
+from paper_2506_09435_gb300 import workloads as W
+from tests.pairs import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp64": "FNPF_FP64", "mixed": "FNPF_MIXED", "pc32": "FNPF_FP64_PC32"}
+
+
+def ragged_tanks():
+    """Seven periodic tanks, three orders (p = 3, 3, 3, 4, 4, 5, 2), element
+    counts 3..7 per direction (nx != ny), kh and steepness from the ensemble
+    generator; the fourth p = 3 tank starts at rest, so its solves converge at
+    once while the others iterate."""
+    base = W.ensemble_tanks(n=7, seed=21, nmin=3, nmax=7, pmin=3, pmax=3)
+    orders = [3, 3, 3, 4, 4, 5, 2]
+    out = []
+    for d, p in zip(base, orders):
+        e = W.periodic_box_3d(nx=d["nx"], ny=d["ny"], nz=2, p=p, kh=d["k"] * d["h0"])
+        e.update(steepness=d["steepness"], seed=d["seed"])
+        out.append(e)
+    out[2]["rest"] = True
+    return out
+
+
+def build(fnpf, tanks, opts, shapes):
+    dev = torch.device("cuda:0")
+    meshes, etas, phiss, dts = [], [], [], []
+    for d in tanks:
+        ncx, ncy = d["p"] * d["nx"], d["p"] * d["ny"]
+        m = fnpf.Mesh(3, d["nx"], d["ny"], 2, d["p"], True, True, np.full(ncx * ncy, d["h0"]), Lx=d["Lx"],
+                      Ly=d["Ly"], g=d["g"], opts=opts)
+        if shapes is not None:
+            m.set_shapes(*shapes)
+        x, y = m.surface_coords()
+        e0, p0 = W.airy_plus_spectrum_state(d, x, y, seed=d["seed"], steepness=d["steepness"])
+        if d.get("rest"):
+            e0, p0 = np.zeros_like(e0), np.zeros_like(p0)
+        meshes.append(m)
+        etas.append(torch.tensor(e0, dtype=torch.float64, device=dev))
+        phiss.append(torch.tensor(p0, dtype=torch.float64, device=dev))
+        dts.append(W.period(d["k"], d["h0"], d["g"]) / 100)
+    return meshes, etas, phiss, dts
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "pc32"])
+def test_batched_groups_equal_tanks_stepped_one_at_a_time(fnpf, prec):
+    tanks = ragged_tanks()
+    o = fnpf.default_opts(rtol=1e-10, precond=fnpf.FNPF_PMG, precision=getattr(fnpf, PREC[prec]))
+    meshes, etas, phiss, dts = build(fnpf, tanks, o, (1, 1))
+    ens = fnpf.Ensemble(meshes)
+    infos = []
+    for k in range(4):
+        infos.append(ens.rk4_step(etas, phiss, [k * dt for dt in dts], dts, info=True))
+    torch.cuda.synchronize()
+    st = ens.stats()
+    assert st["groups"] == 4 and st["batched_tanks"] == len(tanks), st
+    ref_m, ref_e, ref_p, _ = build(fnpf, tanks, o, (1, 1))
+    ref_infos = []
+    for k in range(4):
+        ref_infos.append([m.rk4_step(e, p, k * dt, dt, info=True) for m, e, p, dt in zip(ref_m, ref_e, ref_p, dts)])
+    torch.cuda.synchronize()
+    for i, (a, b, c, d) in enumerate(zip(etas, ref_e, phiss, ref_p)):
+        assert torch.equal(a, b) and torch.equal(c, d), i
+    # the same iteration counts per tank and stage (batched steps 2..4)
+    for k in range(1, 4):
+        for i in range(len(tanks)):
+            for s in range(4):
+                assert infos[k][4 * i + s]["iters"] == ref_infos[k][i][s]["iters"], (k, i, s)
+    assert all(v == 0 for v in etas[2].cpu().numpy()) and all(v == 0 for v in phiss[2].cpu().numpy())
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-8), ("pc32", 1e-10)])
+def test_batched_groups_match_oracle(fnpf, prec, tol):
+    tanks = ragged_tanks()
+    o = fnpf.default_opts(rtol=1e-13, precond=fnpf.FNPF_PMG, precision=getattr(fnpf, PREC[prec]), max_iter=50000)
+    meshes, etas, phiss, dts = build(fnpf, tanks, o, None)
+    init = [(e.cpu().numpy(), p.cpu().numpy()) for e, p in zip(etas, phiss)]
+    ens = fnpf.Ensemble(meshes)
+    for k in range(3):
+        ens.rk4_step(etas, phiss, [k * dt for dt in dts], dts)
+    torch.cuda.synchronize()
+    assert ens.stats()["batched_tanks"] == len(tanks)
+    for i, d in enumerate(tanks):
+        om = omesh.Mesh(3, d["nx"], d["ny"], 2, d["p"], True, True, d["Lx"], d["Ly"])
+        h = np.full(om.ns, d["h0"])
+        e_r, p_r = init[i]
+        for _ in range(3):
+            e_r, p_r = osurf.rk4_step(om, h, e_r, p_r, dts[i], d["g"])
+        if d.get("rest"):
+            assert not np.any(etas[i].cpu().numpy()) and not np.any(phiss[i].cpu().numpy())
+            continue
+        assert rel_l2(etas[i].cpu().numpy(), e_r) < tol, (i, d["p"])
+        assert rel_l2(phiss[i].cpu().numpy(), p_r) < tol, (i, d["p"])
+
+
+def test_batching_cuts_kernel_launches(fnpf):
+    """The same ensemble step with and without batched groups: equal states,
+    and fewer kernels for the batched step (two groups of four tanks: a group
+    runs each loop as long as its slowest tank, so the cut is below 4x)."""
+    tanks = [t for t in ragged_tanks() if not t.get("rest")]
+    tanks = tanks[:2] + tanks[:2] + tanks[2:4] + tanks[2:4]      # 4 tanks of p = 3, 4 of p = 4
+    o = fnpf.default_opts(rtol=1e-10, precond=fnpf.FNPF_PMG, precision=fnpf.FNPF_MIXED)
+    out, kernels = [], []
+    for batching in (False, True):
+        meshes, etas, phiss, dts = build(fnpf, tanks, o, (1, 1))
+        ens = fnpf.Ensemble(meshes)
+        ens.set_batching(batching)
+        for k in range(3):
+            ens.rk4_step(etas, phiss, [k * dt for dt in dts], dts)
+        torch.cuda.synchronize()
+        kernels.append(ens.stats()["kernels"])
+        out.append([t.cpu().numpy() for t in etas + phiss])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    assert kernels[1] * 2 < kernels[0], kernels
