@@ -355,8 +355,8 @@ fnpf_status fnpf_filter_apply(fnpf_mesh* mesh, double* f, void* stream);
  * defect-correction loop one device-side loop that runs while any tank's loop
  * runs, a tank whose loop has finished skipping its work; the tanks of an order
  * are given the kernel shapes the autotuner chose for the largest of them
- * (fnpf_set_shapes).  Groups of up to 64 tanks and the tanks that cannot be
- * batched (tape on, over-integration) run as concurrent branches.  The graph is
+ * (fnpf_set_shapes).  Groups (fnpf_ensemble_set_batching) and the tanks that
+ * are not batched (tape on, over-integration) run as concurrent branches.  The graph is
  * re-captured when a state pointer or step size changes.  info may be NULL or
  * point to 4 n structs (tank-major).  Returns the first failing tank's status;
  * fnpf_ensemble_last_error names it. */
@@ -367,8 +367,12 @@ fnpf_status fnpf_ensemble_rk4_step(fnpf_ensemble* ens, double* const* etas, doub
                                    const double* dts, fnpf_solve_info* info, void* stream);
 const char* fnpf_ensemble_last_error(const fnpf_ensemble* ens);
 /* Batched groups on (1, the default) or off (0: every tank its own branch of
- * per-tank kernels); takes effect at the next step.  Errors: EINVAL. */
-fnpf_status fnpf_ensemble_set_batching(fnpf_ensemble* ens, int on);
+ * per-tank kernels), and the size of a group: at most max_tanks tanks (1..32;
+ * 0: 32) and at most max_dof degrees of freedom (<= 0: no limit; a tank larger
+ * than the limit runs on its own).  Tanks of a class fill groups in
+ * increasing size; a group of one tank runs as its own branch.  Takes effect
+ * at the next step.  Errors: EINVAL (max_tanks out of range). */
+fnpf_status fnpf_ensemble_set_batching(fnpf_ensemble* ens, int on, int max_tanks, int64_t max_dof);
 /* Batched groups and the tanks in them of the current graph, and the kernels
  * the last ensemble step launched (any pointer may be NULL).  Errors: EINVAL. */
 fnpf_status fnpf_ensemble_stats(const fnpf_ensemble* ens, int* groups, int* batched_tanks, int64_t* kernels);

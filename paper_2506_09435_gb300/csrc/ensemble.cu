@@ -10,13 +10,17 @@
 // -- same kernels and block shapes, same loop structure; in practice the tanks
 // of one order with the same options -- form a group.  A group's step is the
 // record replayed once: each kernel becomes one batched launch (k_many) over
-// the concatenated grids of all its tanks, each loop one WHILE node that runs
-// while any tank's loop runs, with a per-tank gate so that a tank whose loop
-// has finished does no work in it (every tank executes exactly the operations
-// of its own step, so the results equal the single-tank step bit for bit).
+// the concatenated grids of all its tanks (their arguments in the launch's
+// parameters), each loop one WHILE node that runs while any tank's loop runs,
+// with a per-tank gate so that a tank whose loop has finished does no work in
+// it (every tank executes exactly the operations of its own step, so the
+// results equal the single-tank step bit for bit).
 // The tanks of a group share the kernel shapes the autotuner chose for the
-// largest of them.  Groups, and tanks that cannot be recorded (adjoint tape,
-// over-integration), run as concurrent fork/join branches of one graph.
+// largest of them.  Groups (of up to kMaxBatch tanks), and tanks that cannot
+// be recorded (adjoint tape, over-integration), run as concurrent fork/join
+// branches of one graph.
+#include <stdint.h>
+
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -57,8 +61,7 @@ __global__ void __launch_bounds__(fnpf::kMaxBatch) batch_cond_kernel(const __gri
 struct Group {
   std::vector<int> tanks;                  // ensemble indices
   std::vector<fnpf::Recorder> rec;         // aligned records, one per tank
-  unsigned char* arena = nullptr;          // device: argument tables, gates, loop counters
-  std::vector<size_t> table_off;           // per operation (kernels): its argument table
+  unsigned char* arena = nullptr;          // device: loop gates and loop counters
   std::vector<size_t> gate_off;            // per loop handle: its gate [ntank]
   size_t count_off = 0;                    // loop counters [handles]
   int handles = 0;
@@ -95,6 +98,8 @@ struct fnpf_ensemble {
   std::vector<Group> groups;
   std::vector<int> solo;          // tanks stepped as their own branch
   bool batching = true;
+  int max_tanks = fnpf::kMaxBatch;        // tanks per batched group
+  int64_t max_dof = INT64_MAX;            // DOF per batched group
   int64_t last_kernels = 0;
   std::string err;
 };
@@ -159,19 +164,13 @@ std::vector<uint64_t> signature(const fnpf::Recorder& r) {
 
 inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Lays out and uploads a group's argument tables, gates and loop counters
-// (before the capture: synchronous copies).
+// Allocates a group's loop gates and counters and its streams (before the
+// capture).
 cudaError_t prepare_group(Group* G) {
   const int T = (int)G->tanks.size();
   const std::vector<fnpf::Op>& ops = G->rec[0].ops;
   G->handles = G->rec[0].handles;
-  G->table_off.assign(ops.size(), 0);
   size_t off = 0;
-  for (size_t i = 0; i < ops.size(); ++i) {
-    if (ops[i].kind != fnpf::OP_KERNEL) continue;
-    G->table_off[i] = off;
-    off = align16(off + (size_t)T * ops[i].args.size());
-  }
   G->gate_off.assign(G->handles, 0);
   for (int h = 0; h < G->handles; ++h) {
     G->gate_off[h] = off;
@@ -179,14 +178,8 @@ cudaError_t prepare_group(Group* G) {
   }
   G->count_off = off;
   off = align16(off + (size_t)std::max(1, G->handles) * sizeof(int));
-  std::vector<unsigned char> host(off, 0);
-  for (size_t i = 0; i < ops.size(); ++i) {
-    if (ops[i].kind != fnpf::OP_KERNEL) continue;
-    const size_t a = ops[i].args.size();
-    for (int t = 0; t < T; ++t) memcpy(host.data() + G->table_off[i] + t * a, G->rec[t].ops[i].args.data(), a);
-  }
   cudaError_t e = cudaMalloc(&G->arena, off);
-  if (e == cudaSuccess) e = cudaMemcpy(G->arena, host.data(), off, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(G->arena, 0, off);
   if (e == cudaSuccess) e = cudaMallocHost(&G->counts_host, (size_t)std::max(1, G->handles) * sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking);
   int depth = 0, maxd = 0;
@@ -214,25 +207,24 @@ cudaError_t emit_range(Group* G, size_t i0, size_t i1, cudaStream_t s, int depth
     const fnpf::Op& op = ops[i];
     cudaError_t e = cudaSuccess;
     if (op.kind == fnpf::OP_KERNEL) {
-      fnpf::BatchHead h{};
-      h.gate = gate;
-      h.args = G->arena + G->table_off[i];
-      h.ntank = T;
+      int off[fnpf::kMaxBatch + 1], gx[fnpf::kMaxBatch];
+      const unsigned char* args[fnpf::kMaxBatch];
       int64_t total = 0;
       unsigned threads = 0;
       size_t smem = 0;
       for (int t = 0; t < T; ++t) {
         const fnpf::Op& o = G->rec[t].ops[i];
-        h.off[t] = (int)total;
-        h.gx[t] = (int)std::max(1u, o.grid.x);
+        off[t] = (int)total;
+        gx[t] = (int)std::max(1u, o.grid.x);
+        args[t] = o.args.data();
         total += (int64_t)o.grid.x * o.grid.y;
         threads = std::max(threads, o.block.x);
         smem = std::max(smem, o.smem);
       }
       if (total >= (int64_t)1 << 31) return cudaErrorInvalidConfiguration;
-      h.off[T] = (int)total;
+      off[T] = (int)total;
       if (total == 0) continue;
-      e = op.emit(h, (unsigned)total, threads, smem, s);
+      e = op.emit(gate, T, off, gx, args, (unsigned)total, threads, smem, s);
       ++*kernels;
     } else if (op.kind == fnpf::OP_COPY_D2H) {
       for (int t = 0; t < T && e == cudaSuccess; ++t) {
@@ -304,17 +296,34 @@ cudaError_t plan(fnpf_ensemble* en, double* const* etas, double* const* phiss, c
     if (ok[i]) by_sig[signature(recs[i])].push_back(i);
     else en->solo.push_back(i);
   }
+  // within a class, tanks in increasing size fill groups up to the tank and
+  // DOF limits; a group of one runs as its own branch
   for (auto& kv : by_sig) {
-    const std::vector<int>& idx = kv.second;
-    for (size_t a = 0; a < idx.size(); a += fnpf::kMaxBatch) {
-      Group G;
-      for (size_t b = a; b < std::min(idx.size(), a + fnpf::kMaxBatch); ++b) {
-        G.tanks.push_back(idx[b]);
-        G.rec.push_back(std::move(recs[idx[b]]));
+    std::vector<int> idx = kv.second;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int b) { return en->meshes[a]->g.N < en->meshes[b]->g.N; });
+    size_t a = 0;
+    while (a < idx.size()) {
+      size_t b = a;
+      int64_t dof = 0;
+      while (b < idx.size() && (int)(b - a) < en->max_tanks &&
+             (b == a || dof + en->meshes[idx[b]]->g.N <= en->max_dof)) {
+        dof += en->meshes[idx[b]]->g.N;
+        ++b;
       }
-      en->groups.push_back(std::move(G));
-      const cudaError_t e = prepare_group(&en->groups.back());
-      if (e != cudaSuccess) return e;
+      if (b - a == 1) {
+        en->solo.push_back(idx[a]);
+      } else {
+        Group G;
+        for (size_t k = a; k < b; ++k) {
+          G.tanks.push_back(idx[k]);
+          G.rec.push_back(std::move(recs[idx[k]]));
+        }
+        en->groups.push_back(std::move(G));
+        const cudaError_t e = prepare_group(&en->groups.back());
+        if (e != cudaSuccess) return e;
+      }
+      a = b;
     }
   }
   return cudaSuccess;
@@ -417,10 +426,14 @@ void fnpf_ensemble_destroy(fnpf_ensemble* en) {
   delete en;
 }
 
-fnpf_status fnpf_ensemble_set_batching(fnpf_ensemble* en, int on) {
-  if (!en) return FNPF_EINVAL;
-  if (en->batching != (on != 0)) reset_graph(en);
+fnpf_status fnpf_ensemble_set_batching(fnpf_ensemble* en, int on, int max_tanks, int64_t max_dof) {
+  if (!en || max_tanks < 0 || max_tanks > fnpf::kMaxBatch) return FNPF_EINVAL;
+  const int mt = max_tanks > 0 ? max_tanks : fnpf::kMaxBatch;
+  const int64_t md = max_dof > 0 ? max_dof : INT64_MAX;
+  if (en->batching != (on != 0) || en->max_tanks != mt || en->max_dof != md) reset_graph(en);
   en->batching = on != 0;
+  en->max_tanks = mt;
+  en->max_dof = md;
   return FNPF_OK;
 }
 

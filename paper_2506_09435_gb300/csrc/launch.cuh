@@ -7,9 +7,9 @@
 // index.  k_many<K> runs the same body for several independent meshes in one
 // launch: its grid is the concatenation of the meshes' grids, a block finds
 // its mesh by a binary search over the first-block offsets in the launch's
-// parameters, reads that mesh's argument tuple from a device table and calls
-// K::run with its block position inside that mesh's grid, so every block does
-// exactly what it does in the mesh's own launch.  A per-mesh gate (an int per
+// parameters and calls K::run with that mesh's argument tuple (also in the
+// parameters) and its block position inside that mesh's grid, so every block
+// does exactly what it does in the mesh's own launch.  A per-mesh gate (an int per
 // mesh in device memory, set by the loop-condition kernels of a batched
 // graph) skips the meshes whose loop has finished.
 //
@@ -24,6 +24,7 @@
 
 #include <cuda/std/tuple>
 #include <cstring>
+#include <memory>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -39,15 +40,18 @@ __device__ __forceinline__ Blk this_blk() {
   return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
 }
 
-constexpr int kMaxBatch = 64;   // meshes per batched launch
+constexpr int kMaxBatch = 32;   // meshes per batched launch
 
-// Parameters of a batched launch (passed by value, read in place).
-struct BatchHead {
+// Parameters of a batched launch: the meshes' argument tuples travel in the
+// kernel's own parameter space (read in place, like a single launch's
+// parameters, so the batched form needs no extra registers for them).
+template <class... P>
+struct BatchParams {
   const int* gate;              // gate[t] == 0: mesh t's blocks return at once (null: none)
-  const void* args;             // [ntank] argument tuples
   int ntank;
   int off[kMaxBatch + 1];       // first block of mesh t; off[ntank] = total blocks
   int gx[kMaxBatch];            // grid.x of mesh t (its grid.y = blocks / gx)
+  cuda::std::tuple<P...> args[kMaxBatch];
 };
 
 template <class K, class = void>
@@ -88,7 +92,8 @@ __device__ __forceinline__ void run_tuple(const Blk& b, const Tup& t, std::index
 }
 
 template <class K, class... P>
-__global__ void __launch_bounds__(K::kThreads, min_blocks_of<K>::v) k_many(const __grid_constant__ BatchHead h) {
+__global__ void __launch_bounds__(K::kThreads, min_blocks_of<K>::v)
+    k_many(const __grid_constant__ BatchParams<P...> h) {
   const int bid = (int)blockIdx.x;
   int lo = 0, hi = h.ntank - 1;
   while (lo < hi) {
@@ -99,9 +104,7 @@ __global__ void __launch_bounds__(K::kThreads, min_blocks_of<K>::v) k_many(const
   if (h.gate && !h.gate[lo]) return;   // uniform over the block (and over a cluster: one mesh per cluster)
   const int li = bid - h.off[lo], gx = h.gx[lo];
   const Blk b{li % gx, li / gx, gx, (h.off[lo + 1] - h.off[lo]) / gx};
-  using Tup = cuda::std::tuple<P...>;
-  const Tup a = static_cast<const Tup*>(h.args)[lo];
-  run_tuple<K>(b, a, std::index_sequence_for<P...>{});
+  run_tuple<K>(b, h.args[lo], std::index_sequence_for<P...>{});
 }
 
 // ---------------------------------------------------------------------------
@@ -109,7 +112,11 @@ __global__ void __launch_bounds__(K::kThreads, min_blocks_of<K>::v) k_many(const
 
 enum OpKind { OP_KERNEL = 0, OP_COPY_D2H = 1, OP_HANDLE = 2, OP_COND = 3, OP_LOOP = 4, OP_END = 5 };
 
-using EmitFn = cudaError_t (*)(const BatchHead& h, unsigned blocks, unsigned threads, size_t smem, cudaStream_t s);
+// Launches the batched kernel of a recorded operation over ntank meshes: off,
+// gx and the argument tuples (args[t], as recorded) per mesh.
+using EmitFn = cudaError_t (*)(const int* gate, int ntank, const int* off, const int* gx,
+                               const unsigned char* const* args, unsigned blocks, unsigned threads, size_t smem,
+                               cudaStream_t s);
 
 struct Op {
   int kind = OP_KERNEL;
@@ -151,7 +158,21 @@ struct run_sig<void (*)(Blk, P...)> {
   }
 
   template <class K>
-  static cudaError_t emit(const BatchHead& h, unsigned blocks, unsigned threads, size_t smem, cudaStream_t s) {
+  static cudaError_t emit(const int* gate, int ntank, const int* off, const int* gx, const unsigned char* const* args,
+                          unsigned blocks, unsigned threads, size_t smem, cudaStream_t s) {
+    using Params = BatchParams<P...>;
+    static_assert(sizeof(Params) <= 31 * 1024, "batched parameters within the kernel parameter limit");
+    if (ntank < 1 || ntank > kMaxBatch) return cudaErrorInvalidValue;
+    std::unique_ptr<Params> hb(new Params());   // large: on the heap; the launch copies it
+    Params& hp = *hb;
+    hp.gate = gate;
+    hp.ntank = ntank;
+    for (int t = 0; t < ntank; ++t) {
+      hp.off[t] = off[t];
+      hp.gx[t] = gx[t];
+      memcpy(static_cast<void*>(&hp.args[t]), args[t], sizeof(Tup));
+    }
+    hp.off[ntank] = off[ntank];
     auto fn = &k_many<K, P...>;
     if (smem > 48 * 1024) {
       const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -170,9 +191,9 @@ struct run_sig<void (*)(Blk, P...)> {
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      return cudaLaunchKernelEx(&cfg, fn, h);
+      return cudaLaunchKernelEx(&cfg, fn, hp);
     } else {
-      fn<<<blocks, threads, smem, s>>>(h);
+      fn<<<blocks, threads, smem, s>>>(hp);
       return cudaPeekAtLastError();
     }
   }

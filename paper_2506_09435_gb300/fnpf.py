@@ -96,7 +96,7 @@ def load():
         "fnpf_tape_end": [vp],
         "fnpf_step_adjoint_taped": [vp, ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_double, vp],
         "fnpf_ensemble_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)],
-        "fnpf_ensemble_set_batching": [vp, ctypes.c_int],
+        "fnpf_ensemble_set_batching": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64],
         "fnpf_ensemble_stats": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int64)],
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
@@ -468,10 +468,11 @@ class Ensemble:
     def __del__(self):
         self.close()
 
-    def set_batching(self, on):
+    def set_batching(self, on, max_tanks=0, max_dof=0):
         """Batched groups (True, the default) or one branch of per-tank kernels
-        per tank (False), from the next step on."""
-        st = _LIB.fnpf_ensemble_set_batching(self._h, 1 if on else 0)
+        per tank (False), groups of at most max_tanks tanks (0: 32) and max_dof
+        degrees of freedom (0: no limit), from the next step on."""
+        st = _LIB.fnpf_ensemble_set_batching(self._h, 1 if on else 0, int(max_tanks), int(max_dof))
         if st != FNPF_OK:
             raise FnpfError(st, _LIB.fnpf_ensemble_last_error(self._h).decode())
 

@@ -66,7 +66,7 @@ def test_batched_groups_equal_tanks_stepped_one_at_a_time(fnpf, prec):
         infos.append(ens.rk4_step(etas, phiss, [k * dt for dt in dts], dts, info=True))
     torch.cuda.synchronize()
     st = ens.stats()
-    assert st["groups"] == 4 and st["batched_tanks"] == len(tanks), st
+    assert st["groups"] == 2 and st["batched_tanks"] == 5, st      # p = 3 (3 tanks), p = 4 (2); p = 5, 2 alone
     ref_m, ref_e, ref_p, _ = build(fnpf, tanks, o, (1, 1))
     ref_infos = []
     for k in range(4):
@@ -92,7 +92,7 @@ def test_batched_groups_match_oracle(fnpf, prec, tol):
     for k in range(3):
         ens.rk4_step(etas, phiss, [k * dt for dt in dts], dts)
     torch.cuda.synchronize()
-    assert ens.stats()["batched_tanks"] == len(tanks)
+    assert ens.stats()["batched_tanks"] == 5
     for i, d in enumerate(tanks):
         om = omesh.Mesh(3, d["nx"], d["ny"], 2, d["p"], True, True, d["Lx"], d["Ly"])
         h = np.full(om.ns, d["h0"])
@@ -104,6 +104,32 @@ def test_batched_groups_match_oracle(fnpf, prec, tol):
             continue
         assert rel_l2(etas[i].cpu().numpy(), e_r) < tol, (i, d["p"])
         assert rel_l2(phiss[i].cpu().numpy(), p_r) < tol, (i, d["p"])
+
+
+def test_group_limits(fnpf):
+    """Groups of at most max_tanks tanks and max_dof degrees of freedom, filled
+    in increasing size; a group of one runs on its own; the results stay
+    bitwise those of the tanks stepped one at a time."""
+    tanks = [t for t in ragged_tanks() if t["p"] == 3] * 2           # six p = 3 tanks (two at rest)
+    o = fnpf.default_opts(rtol=1e-10, precond=fnpf.FNPF_PMG, precision=fnpf.FNPF_FP64)
+    meshes, etas, phiss, dts = build(fnpf, tanks, o, (1, 1))
+    sizes = sorted(m.N for m in meshes)
+    ens = fnpf.Ensemble(meshes)
+    ens.set_batching(True, max_tanks=4, max_dof=sizes[0] + sizes[1] + sizes[2])
+    for k in range(3):
+        ens.rk4_step(etas, phiss, [k * dt for dt in dts], dts)
+    torch.cuda.synchronize()
+    st = ens.stats()
+    assert 1 <= st["groups"] <= 3 and st["batched_tanks"] <= 6, st
+    ref_m, ref_e, ref_p, _ = build(fnpf, tanks, o, (1, 1))
+    for k in range(3):
+        for m, e, p, dt in zip(ref_m, ref_e, ref_p, dts):
+            m.rk4_step(e, p, k * dt, dt)
+    torch.cuda.synchronize()
+    for a, b in zip(etas + phiss, ref_e + ref_p):
+        assert torch.equal(a, b)
+    with pytest.raises(fnpf.FnpfError):
+        ens.set_batching(True, max_tanks=33)
 
 
 def test_batching_cuts_kernel_launches(fnpf):
