@@ -354,7 +354,7 @@ def main_gb300(args):
                              coarse_iters=args.coarse_degree, coarse_solver=coarse_mode(args),
                              cheb_kind=args.cheb_kind, cheb_range=args.cheb_range,
                              model=model_id(args), mg_schedule=schedule_id(args),
-                             precision=prec, projection=args.projection)
+                             precision=prec, projection=args.projection, inner_rtol=args.inner_rtol)
     ncx = d["p"] * d["nx"]
     h = np.full(ncx * ncx, d["h0"])
     mesh = fnpf.Mesh(3, d["nx"], d["ny"], d["nz"], d["p"], True, True, h, Lx=d["Lx"], Ly=d["Ly"], g=d["g"],

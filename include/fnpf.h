@@ -114,7 +114,8 @@ typedef struct {
   int max_outer;           /* defect-correction cap (FNPF_MIXED)                   */
   int use_graphs;          /* 1: replay CG iterations as CUDA graphs (not while
                               instrumentation is enabled); 0: plain launches      */
-  int store_metric;        /* FP64 operator of FNPF_FP64 and FNPF_FP64_PC32 solves:
+  int store_metric;        /* FP64 operator (of every precision form; in FNPF_MIXED
+                              the lift, projection and outer residuals):
                               1 = rebuild the metric G from eta
                               once per solve into device memory (6 doubles per
                               point, allocated at the first solve) and read it in

@@ -859,13 +859,14 @@ fnpf_status cg_solve(fnpf_mesh* m, const double* eta_in, const double* phis, dou
   const double* eta = m->eta64;
   FNPF_CK(cudaMemsetAsync(sc, 0, sizeof(CgScalars), s));
   FNPF_CK(launch_check_state(g, eta, rhs ? eta : phis, m->dh, &sc->status, &sc->done, s));
-  // FP64 solves: the metric is rebuilt from this eta once and read by every
-  // operator application of the solve (fewer FP64 instructions per point)
+  // the FP64 operator (every application of an FP64 solve; the lift, the
+  // projection and the outer residuals of a mixed solve) reads a metric rebuilt
+  // from this eta once per solve (fewer FP64 instructions per point)
   // linear potential flow: the geometry is fixed, so the FP64 set-up of the
   // first solve is kept (lpf_ready) and later solves skip it
   const bool keep64 = m->linear() && m->lpf_ready[0];
   m->g64_active = false;
-  if (!mixed && m->opts.store_metric) {
+  if (m->opts.store_metric) {
     const fnpf_status st = ensure_g64(m);
     if (st != FNPF_OK) return st;
     if (!keep64) {
@@ -1111,7 +1112,7 @@ cudaError_t enqueue_solve_device(fnpf_mesh* m, const double* eta_in, const doubl
   const bool keep64 = m->linear() && m->lpf_ready[0];
   const bool keep32 = m->linear() && m->lpf_ready[1];
   m->g64_active = false;
-  if (!mixed && m->opts.store_metric && m->G64) {
+  if (m->opts.store_metric && m->G64) {
     if (!keep64) ENQ(launch_geom<double>(g, t, eta, m->G64, s));
     m->g64_active = true;
   }
