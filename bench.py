@@ -35,7 +35,10 @@ UNIT = "DOF·steps/s"
 WORKLOAD = "periodic-box-3d kh=2, 32x32x2 hex, GLL p=6, Airy H/L=0.05 + seeded spectrum, dt=T/100, rtol 1e-10"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz
-AXG_C2_DRAM_BYTES = 34.060544e6 + 768.0             # ncu dram__bytes_read.sum + dram__bytes_write.sum
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64 stored-metric operator on the
+# benchmark tank (kernel alone, cold cache): axg_kernel<double,7,3,7> (shape 3), axl_kernel<double,7,7,1> (shape 4)
+AXG_C2_DRAM_BYTES = 34.060544e6 + 768.0
+AXL_C2_DRAM_BYTES = 37.302272e6 + 768.0
 
 
 def measured_hbm_gbs():
@@ -61,6 +64,8 @@ def parse():
     ap.add_argument("--coarse-degree", type=int, default=6)
     ap.add_argument("--shape", type=int, default=-1, choices=list(range(-1, 12)),
                     help="elements-per-CTA shape of the operator kernels (-1: autotuned)")
+    ap.add_argument("--shapes", default="", help="FP64,FP32 elements-per-CTA shapes of the headline mesh "
+                    "(e.g. 4,3; default: autotuned, or --shape)")
     ap.add_argument("--model", default="fnpf", choices=["fnpf", "lpf"],
                     help="fnpf: fully nonlinear (the configuration's method); lpf: linear potential flow")
     ap.add_argument("--mg-schedule", default="halve", choices=["halve", "two", "step2"],
@@ -361,6 +366,8 @@ def main_gb300(args):
                      opts=opts)
     if args.shape >= 0:
         mesh.set_shapes(args.shape, args.shape)
+    if args.shapes:
+        mesh.set_shapes(*[int(v) for v in args.shapes.split(",")])
     x, y = mesh.surface_coords()
     eta0, phi0 = W.airy_plus_spectrum_state(d, x, y, seed=2)
     dt = W.period(d["k"], d["h0"], d["g"]) / 100
@@ -498,12 +505,14 @@ def main_gb300(args):
     # 6 one-dimensional contractions (12 n^4 per element) + G . grad u (18 n^3)
     flops = (12 * n ** 4 + 18 * n ** 3) * E
     achieved = flops / (apply_ms * 1e-3) / 1e12
-    # dram bytes per application of axg_kernel<double,7,3,7> on this tank from one ncu capture
-    # of that kernel, valid while the autotuner picks that shape
-    traffic = AXG_C2_DRAM_BYTES if (mesh.get_shapes()[0] == 3 and n == 7 and d["nx"] == 32) else None
+    # dram bytes per application of the chosen kernel on this tank from one ncu capture of it
+    # (shapes 3 and 4, the autotuner's picks here); none for other shapes or tanks
+    bench_tank = n == 7 and d["nx"] == 32 and d["nz"] == 2
+    traffic = {3: AXG_C2_DRAM_BYTES, 4: AXL_C2_DRAM_BYTES}.get(mesh.get_shapes()[0]) if bench_tank else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": ("axg_kernel<double,7,3,C>" if mesh.get_shapes()[0] < 4 else "axl_kernel<double,7,C,true>")
+                "kernel": ("axg_kernel<double,7,3,C>" if mesh.get_shapes()[0] < 4 else
+                           "axl_kernel<double,7,C,true>" if mesh.get_shapes()[0] < 8 else "axz_kernel<double,7,C,2,true>")
                           + " + ring_gather (one FP64 operator application, stored metric), shape %d, C = %d"
                           % (mesh.get_shapes()[0], mesh.get_shapes()[2]),
                 "flops_per_application": flops,
@@ -658,7 +667,7 @@ def main_gb300(args):
                        "coarse_solver": args.coarse_solver, "cheb_kind": args.cheb_kind,
                        "cheb_range": args.cheb_range, "model": args.model, "mg_schedule": args.mg_schedule,
                        "projection": args.projection,
-                       "cta_shape": ("autotuned" if args.shape < 0 else "forced"),
+                       "cta_shape": ("autotuned" if args.shape < 0 and not args.shapes else "forced"),
                        "element_columns_per_cta": mesh.get_shapes()[2],
                        "cta_shape_fp64": mesh.get_shapes()[0], "cta_shape_fp32": mesh.get_shapes()[1],
                        "headline_precision": args.precision, "l2": "flushed before every timed step (256 MB write, untimed)",

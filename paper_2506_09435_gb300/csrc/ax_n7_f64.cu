@@ -1,9 +1,7 @@
-// Instantiations of the operator kernels for GLL order p = 6.
+// Instantiations of the FP64 operator kernels for GLL order p = 6.
 #include "ax_impl.cuh"
 
 namespace fnpf {
 template cudaError_t launch_ax_n<double, 7>(const Geom&, const Tables<double>&, const AxPtrs<double>&, int, int,
                                             cudaStream_t);
-template cudaError_t launch_ax_n<float, 7>(const Geom&, const Tables<float>&, const AxPtrs<float>&, int, int,
-                                           cudaStream_t);
 }  // namespace fnpf

@@ -1,0 +1,7 @@
+// Instantiations of the FP32 operator kernels for GLL order p = 7.
+#include "ax_impl.cuh"
+
+namespace fnpf {
+template cudaError_t launch_ax_n<float, 8>(const Geom&, const Tables<float>&, const AxPtrs<float>&, int, int,
+                                           cudaStream_t);
+}  // namespace fnpf

@@ -28,7 +28,7 @@ struct EO {
 };
 constexpr int kEOMax = 2 * (kMaxN / 2) * (kMaxN / 2) + 2 * (kMaxN / 2);
 
-// One copy per translation unit (no relocatable device code): each ax_n<N>.cu
+// One copy per translation unit (no relocatable device code): each ax_n<N>_*.cu
 // fills its own through eo_upload, before its first line-kernel launch.
 static __constant__ double c_eo64[kMaxN + 1][2][kEOMax];
 static __constant__ float c_eo32[kMaxN + 1][2][kEOMax];

@@ -178,7 +178,7 @@ struct AxPtrs {
 
 enum { AX_APPLY = 0, AX_DIAG = 1, AX_GEOM = 2, AX_APPLY_G = 3, AX_INIT = 4 };
 
-// Per-order operator launcher, explicitly instantiated in ax_n<N>.cu.
+// Per-order operator launcher, explicitly instantiated in ax_n<N>_f32.cu / _f64.cu.
 template <typename T, int N>
 cudaError_t launch_ax_n(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, int variant,
                         cudaStream_t s);
