@@ -343,10 +343,11 @@ fnpf_status fnpf_set_dealias(fnpf_mesh* mesh, int points);
 fnpf_status fnpf_filter_apply(fnpf_mesh* mesh, double* f, void* stream);
 
 /* Ensembles of independent tanks (batched form; Sec. 3.4's RK4 step, Steps
- * 4.1-4.7, for many tanks at once).  An ensemble groups existing meshes (not
- * owned; they must outlive it).  fnpf_ensemble_rk4_step advances tank i by one
- * RK4 step of size dts[i] from time ts[i], state etas[i], phiss[i] (device
- * arrays, in place), exactly as fnpf_rk4_step would.  The first call steps each
+ * 4.1-4.7, for many tanks at once).  An ensemble groups existing, distinct
+ * meshes (not owned; they must outlive it; the same mesh twice is EINVAL).
+ * fnpf_ensemble_rk4_step advances tank i by one RK4 step of size dts[i] from
+ * time ts[i], state etas[i], phiss[i] (device arrays, in place), exactly as
+ * fnpf_rk4_step would.  The first call steps each
  * tank on its own (set-up, autotuning); from the second call on, all tanks'
  * steps run as one launch of a captured CUDA graph with one host
  * synchronisation per ensemble step.  In that graph, tanks whose steps are the

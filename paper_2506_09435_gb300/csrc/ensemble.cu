@@ -120,9 +120,11 @@ void reset_graph(fnpf_ensemble* en) {
 // capture) or recording failed.
 bool record_step(fnpf_ensemble* en, fnpf_mesh* m, double* eta, double* phis, double dt, fnpf::Recorder* rec) {
   if (cudaStreamBeginCapture(en->scratch, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  const int64_t launches = m->launches;   // the host code counts what it enqueues; nothing ran
   fnpf::active_recorder() = rec;
   const cudaError_t e = fnpf::enqueue_step(m, eta, phis, dt, en->scratch);
   fnpf::active_recorder() = nullptr;
+  m->launches = launches;
   cudaGraph_t graph = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(en->scratch, &graph);
   size_t nodes = 1;
@@ -395,8 +397,14 @@ extern "C" {
 fnpf_status fnpf_ensemble_create(fnpf_mesh* const* meshes, int n, fnpf_ensemble** out) {
   if (!out || !meshes || n < 1) return FNPF_EINVAL;
   *out = nullptr;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!meshes[i]) return FNPF_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i]) {
+        g_ens_error = "the same mesh twice in one ensemble";
+        return FNPF_EINVAL;
+      }
+  }
   fnpf_ensemble* en = new fnpf_ensemble();
   en->meshes.assign(meshes, meshes + n);
   en->join.assign(n, nullptr);

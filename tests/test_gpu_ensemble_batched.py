@@ -152,3 +152,11 @@ def test_batching_cuts_kernel_launches(fnpf):
     for a, b in zip(*out):
         assert np.array_equal(a, b)
     assert kernels[1] * 2 < kernels[0], kernels
+
+
+def test_same_mesh_twice_is_rejected(fnpf):
+    tanks = ragged_tanks()[:1]
+    o = fnpf.default_opts(rtol=1e-10)
+    meshes, _, _, _ = build(fnpf, tanks, o, None)
+    with pytest.raises(fnpf.FnpfError):
+        fnpf.Ensemble([meshes[0], meshes[0]])
