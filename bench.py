@@ -512,7 +512,8 @@ def main_gb300(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": ("axg_kernel<double,7,3,C>" if mesh.get_shapes()[0] < 4 else
-                           "axl_kernel<double,7,C,true>" if mesh.get_shapes()[0] < 8 else "axz_kernel<double,7,C,2,true>")
+                           "axl_kernel<double,7,C,true>" if mesh.get_shapes()[0] < 8 else
+                           "axz_kernel<double,7,C,2,true>")
                           + " + ring_gather (one FP64 operator application, stored metric), shape %d, C = %d"
                           % (mesh.get_shapes()[0], mesh.get_shapes()[2]),
                 "flops_per_application": flops,

@@ -208,13 +208,15 @@ cudaError_t launch_transfer_t(const Geom& gf, const Geom& gc, const T* J, const 
   const int add = mode == 2;
   if (gf.dim == 3) {
     if (prolong)
-      launch<prolong_kernel<T, NF, NC, 3>>(blocks, XferShape<T, NF, NC, 3>::THREADS, 0, s, gf, gc, J, in, out, add, skip);
+      launch<prolong_kernel<T, NF, NC, 3>>(blocks, XferShape<T, NF, NC, 3>::THREADS, 0, s, gf, gc, J, in, out, add,
+                                           skip);
     else
       launch<restrict_kernel<T, NF, NC, 3>>(blocks, XferShape<T, NF, NC, 3>::THREADS, 0, s, gf, gc, J, in, out, ring,
                                             skip);
   } else {
     if (prolong)
-      launch<prolong_kernel<T, NF, NC, 2>>(blocks, XferShape<T, NF, NC, 2>::THREADS, 0, s, gf, gc, J, in, out, add, skip);
+      launch<prolong_kernel<T, NF, NC, 2>>(blocks, XferShape<T, NF, NC, 2>::THREADS, 0, s, gf, gc, J, in, out, add,
+                                           skip);
     else
       launch<restrict_kernel<T, NF, NC, 2>>(blocks, XferShape<T, NF, NC, 2>::THREADS, 0, s, gf, gc, J, in, out, ring,
                                             skip);
