@@ -160,3 +160,77 @@ def test_same_mesh_twice_is_rejected(fnpf):
     meshes, _, _, _ = build(fnpf, tanks, o, None)
     with pytest.raises(fnpf.FnpfError):
         fnpf.Ensemble([meshes[0], meshes[0]])
+
+
+def relax_flumes(fnpf, opts):
+    """Three walled flumes of one order over the bar bathymetry (different
+    lengths, so different element counts), generation and absorption zones."""
+    out = []
+    for nx, Lx in ((8, 8.0), (10, 10.0), (12, 12.0)):
+        d = W.bar_flume(nx=nx, ny=2, nz=2, p=3, Lx=Lx)
+        d["zone"] = Lx / 4
+        gm = fnpf.Mesh(3, nx, 2, 2, 3, False, False, np.full((3 * nx + 1) * 7, d["h0"]), Lx=Lx, Ly=d["Ly"],
+                       g=d["g"], opts=opts)
+        x, _ = gm.surface_coords()
+        h = W.bar_depth(x * 38.0 / Lx)
+        gm = fnpf.Mesh(3, nx, 2, 2, 3, False, False, h, Lx=Lx, Ly=d["Ly"], g=d["g"], opts=opts)
+        gm.set_shapes(1, 1)
+        cr, gen = W.flume_zones(d, x)
+        gm.set_relaxation(cr, gen, **W.flume_wave(d))
+        out.append((d, gm))
+    return out
+
+
+def test_batched_relaxation_flumes_equal_one_at_a_time(fnpf):
+    """The relaxation blend of the last stage reads each tank's own step time
+    on the device (written by the host before every graph launch): a batched
+    group of flumes started at different times equals the flumes stepped one at
+    a time, bit for bit, and the generation zones have started their waves."""
+    o = fnpf.default_opts(rtol=1e-10, precond=fnpf.FNPF_PMG)
+    dev = torch.device("cuda:0")
+    runs = []
+    for batched in (True, False):
+        fl = relax_flumes(fnpf, o)
+        etas = [torch.zeros(m.ns, dtype=torch.float64, device=dev) for _, m in fl]
+        phiss = [torch.zeros_like(e) for e in etas]
+        dts = [d["T"] / 50 for d, _ in fl]
+        t0 = [0.0, 0.3, 0.7]
+        if batched:
+            ens = fnpf.Ensemble([m for _, m in fl])
+            for k in range(5):
+                ens.rk4_step(etas, phiss, [a + k * dt for a, dt in zip(t0, dts)], dts)
+            assert ens.stats()["batched_tanks"] == 3
+        else:
+            for k in range(5):
+                for (d, m), e, p, a, dt in zip(fl, etas, phiss, t0, dts):
+                    m.rk4_step(e, p, a + k * dt, dt)
+        torch.cuda.synchronize()
+        runs.append([t.cpu().numpy() for t in etas + phiss])
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+    assert all(np.max(np.abs(a)) > 0 for a in runs[0][:3])
+
+
+def test_failing_tank_in_a_batched_group(fnpf):
+    """A tank of a batched group whose state folds (eta + h <= 0) reports
+    EDIVERGED for the ensemble step, named by index; the other tanks of its
+    group still take exactly the step they take on their own."""
+    tanks = [t for t in ragged_tanks() if t["p"] == 3 and not t.get("rest")] * 2   # four p = 3 tanks
+    o = fnpf.default_opts(rtol=1e-10, precond=fnpf.FNPF_PMG)
+    meshes, etas, phiss, dts = build(fnpf, tanks, o, (1, 1))
+    ref_m, ref_e, ref_p, _ = build(fnpf, tanks, o, (1, 1))
+    ens = fnpf.Ensemble(meshes)
+    for k in range(2):
+        ens.rk4_step(etas, phiss, [k * dt for dt in dts], dts)
+        for m, e, p, dt in zip(ref_m, ref_e, ref_p, dts):
+            m.rk4_step(e, p, k * dt, dt)
+    assert ens.stats()["batched_tanks"] == 4
+    etas[2].fill_(-10.0)                         # folded: eta + h < 0 everywhere
+    ref_e[2].fill_(-10.0)
+    with pytest.raises(fnpf.FnpfError, match="tank 2"):
+        ens.rk4_step(etas, phiss, [2 * dt for dt in dts], dts)
+    for i in (0, 1, 3):
+        ref_m[i].rk4_step(ref_e[i], ref_p[i], 2 * dts[i], dts[i])
+    torch.cuda.synchronize()
+    for i in (0, 1, 3):
+        assert torch.equal(etas[i], ref_e[i]) and torch.equal(phiss[i], ref_p[i]), i
