@@ -1,7 +1,24 @@
-// Order dispatch of the operator kernels (instantiated per order in ax_n<N>.cu).
+// Order dispatch of the operator kernels (instantiated per order and precision
+// in ax_n<N>_f32.cu / ax_n<N>_f64.cu; declared extern here so that this unit
+// does not compile every kernel again).
 #include "ax_impl.cuh"
 
 namespace fnpf {
+
+#define FNPF_EXTERN_AX(T, N)                                                                              \
+  extern template cudaError_t launch_ax_n<T, N>(const Geom&, const Tables<T>&, const AxPtrs<T>&, int, int, \
+                                                cudaStream_t);
+#define FNPF_EXTERN_AX_ORDER(N) FNPF_EXTERN_AX(double, N) FNPF_EXTERN_AX(float, N)
+FNPF_EXTERN_AX_ORDER(2)
+FNPF_EXTERN_AX_ORDER(3)
+FNPF_EXTERN_AX_ORDER(4)
+FNPF_EXTERN_AX_ORDER(5)
+FNPF_EXTERN_AX_ORDER(6)
+FNPF_EXTERN_AX_ORDER(7)
+FNPF_EXTERN_AX_ORDER(8)
+FNPF_EXTERN_AX_ORDER(9)
+#undef FNPF_EXTERN_AX_ORDER
+#undef FNPF_EXTERN_AX
 
 template <typename T>
 static cudaError_t dispatch(const Geom& g, const Tables<T>& t, const AxPtrs<T>& a, int mode, int variant,
