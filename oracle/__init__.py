@@ -17,5 +17,7 @@ Modules
   surface  -- Zakharov right-hand side, ERK4, relaxation, diagnostics
   tlm      -- exact tangent-linear model of one RK4 step (complex step)
   filter   -- modal filter of free-surface fields
+  prism    -- prisms over an unstructured triangular surface mesh: operator,
+              Laplace solve, w
 """
-from . import filter, gll, mesh, operator, solve, surface, tlm  # noqa: F401
+from . import filter, gll, mesh, operator, prism, solve, surface, tlm  # noqa: F401

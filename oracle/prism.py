@@ -1,0 +1,235 @@
+"""Extruded prism elements on an unstructured triangular surface mesh (oracle).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+The paper builds its fluid mesh from a triangular mesh of the free surface,
+extruded vertically into N_z layers of prisms whose columns are translated
+vertically to follow the free surface (Sec. 3.1.2), with C0 nodal Lagrange
+elements of degree p (Sec. 3.1).  This module restates, for those prisms, what
+the hexahedral oracle computes: the stiffness operator of the weak Laplace
+form (Eq. Laplace_weak) by its quadrature definition, the Dirichlet-Neumann
+solve with phi = phi_eta on the surface (Eq. Laplace_strong), and the vertical
+surface velocity w (Steps 4.4-4.5).
+
+Readings (the paper names the element family, not its nodes or quadrature):
+  * element space on a prism: the degree-p polynomials on the triangle times
+    the degree-p GLL Lagrange basis in the vertical;
+  * triangle nodes: the Blyth-Pozrikidis set built from the 1D GLL points
+    v_m in [0, 1] -- node (i, j), k = p - i - j, at barycentric coordinates
+    lambda_B = (1 + 2 v_i - v_j - v_k) / 3, lambda_C = (1 + 2 v_j - v_i - v_k) / 3
+    (Blyth & Pozrikidis, IMA J. Appl. Math. 71, 2006); its edge nodes are the
+    GLL points, so neighbouring triangles share them;
+  * straight-sided (affine) triangles in (x, y); in the vertical the mesh of
+    the hexahedra: z = -h + sigma (eta + h), sigma = (l + (1 + t) / 2) / N_z,
+    with eta and h in the triangle's nodal basis;
+  * quadrature: a collapsed-coordinate Gauss-Legendre rule on the triangle,
+    exact for total degree 2p + 2, times GLL collocation (p + 1 points) in the
+    vertical, as for the hexahedra.
+Node numbering: surface nodes are the mesh vertices, then p - 1 nodes per
+edge (ordered from the lower to the higher vertex number), then the interior
+nodes of each triangle; volume node (plane k, surface node c) is k * Ns + c,
+the surface plane k = N_z p.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import gll
+
+
+def tri_index(p):
+    """Local node list (i, j), i + j <= p, in the order j outer, i inner."""
+    return [(i, j) for j in range(p + 1) for i in range(p + 1 - j)]
+
+
+def tri_nodes(p):
+    """Reference-triangle nodes (r, s) of order p on T = {r, s >= -1, r + s <= 0}
+    (vertices A = (-1, -1), B = (1, -1), C = (-1, 1))."""
+    v = (gll.nodes(p)[0] + 1.0) / 2.0
+    r, s = [], []
+    for i, j in tri_index(p):
+        k = p - i - j
+        lb = (1.0 + 2.0 * v[i] - v[j] - v[k]) / 3.0
+        lc = (1.0 + 2.0 * v[j] - v[i] - v[k]) / 3.0
+        r.append(2.0 * lb - 1.0)
+        s.append(2.0 * lc - 1.0)
+    return np.array(r), np.array(s)
+
+
+def tri_quadrature(n):
+    """n x n collapsed Gauss-Legendre rule on T: (r, s, w), exact for total
+    degree 2n - 2."""
+    a, wa = np.polynomial.legendre.leggauss(n)
+    r = ((1.0 + a[None, :]) * (1.0 - a[:, None]) / 2.0 - 1.0).ravel()
+    s = np.repeat(a, n)
+    w = (wa[None, :] * wa[:, None] * (1.0 - a[:, None]) / 2.0).ravel()
+    return r, s, w
+
+
+def _monomials(p, r, s):
+    """u^a v^b (u = (1+r)/2, v = (1+s)/2), a + b <= p, and their r- and
+    s-derivatives at the points: three [npts, nb] arrays."""
+    u, v = (1.0 + np.asarray(r)) / 2.0, (1.0 + np.asarray(s)) / 2.0
+    M, Mr, Ms = [], [], []
+    for a, b in tri_index(p):
+        M.append(u ** a * v ** b)
+        Mr.append(0.5 * a * u ** max(a - 1, 0) * v ** b if a > 0 else 0.0 * u)
+        Ms.append(0.5 * b * u ** a * v ** max(b - 1, 0) if b > 0 else 0.0 * u)
+    return np.stack(M, -1), np.stack(Mr, -1), np.stack(Ms, -1)
+
+
+def tri_basis(p, r, s):
+    """Values and (r, s)-derivatives of the nodal Lagrange basis of order p on
+    T at the points (r, s): three [npts, n_t] arrays (the cardinal functions of
+    tri_nodes, from the monomial Vandermonde matrix)."""
+    rn, sn = tri_nodes(p)
+    V = _monomials(p, rn, sn)[0]
+    C = np.linalg.inv(V)
+    M, Mr, Ms = _monomials(p, r, s)
+    return M @ C, Mr @ C, Ms @ C
+
+
+class TriMesh:
+    """Order-p nodal numbering of an unstructured triangular surface mesh."""
+
+    def __init__(self, verts, tris, p):
+        self.p = p
+        self.verts = np.asarray(verts, dtype=np.float64)
+        self.tris = np.asarray(tris, dtype=np.int64)
+        nv = len(self.verts)
+        idx = tri_index(p)
+        self.nt_loc = len(idx)
+        edges = {}
+        for t in self.tris:
+            for u, w in ((t[0], t[1]), (t[1], t[2]), (t[0], t[2])):
+                key = (min(u, w), max(u, w))
+                if key not in edges:
+                    edges[key] = nv + len(edges) * (p - 1)
+        n = nv + len(edges) * (p - 1)
+        nodes = np.zeros((len(self.tris), self.nt_loc), dtype=np.int64)
+        for e, (A, B, C) in enumerate(self.tris):
+            for q, (i, j) in enumerate(idx):
+                k = p - i - j
+                if (i, j) == (0, 0):
+                    g = A
+                elif (i, j) == (p, 0):
+                    g = B
+                elif (i, j) == (0, p):
+                    g = C
+                elif j == 0:                      # edge A -> B, GLL index i from A
+                    g = self._edge(edges, A, B, i)
+                elif k == 0:                      # edge B -> C, GLL index j from B
+                    g = self._edge(edges, B, C, j)
+                elif i == 0:                      # edge A -> C, GLL index j from A
+                    g = self._edge(edges, A, C, j)
+                else:
+                    g = n
+                    n += 1
+                nodes[e, q] = g
+        self.nodes = nodes
+        self.ns = n
+        rn, sn = tri_nodes(p)
+        xs = np.zeros(n)
+        ys = np.zeros(n)
+        for e, (A, B, C) in enumerate(self.tris):
+            lb, lc = (1.0 + rn) / 2.0, (1.0 + sn) / 2.0
+            la = 1.0 - lb - lc
+            P = la[:, None] * self.verts[A] + lb[:, None] * self.verts[B] + lc[:, None] * self.verts[C]
+            xs[nodes[e]] = P[:, 0]
+            ys[nodes[e]] = P[:, 1]
+        self.xs, self.ys = xs, ys
+
+    def _edge(self, edges, u, w, m):
+        p = self.p
+        base = edges[(min(u, w), max(u, w))]
+        mm = m if u < w else p - m
+        return base + mm - 1
+
+
+class PrismMesh:
+    """N_z layers of order-p prisms over a TriMesh."""
+
+    def __init__(self, tm, nz):
+        self.tm, self.p, self.nz = tm, tm.p, nz
+        self.n = tm.p + 1
+        self.rule = gll.Rule(tm.p)
+        self.ns = tm.ns
+        self.nv = nz * tm.p + 1
+        self.N = self.nv * self.ns
+        rq, sq, wq = tri_quadrature(tm.p + 2)
+        self.wq = wq
+        self.L, self.Lr, self.Ls = tri_basis(tm.p, rq, sq)
+
+    def element_matrix(self, e, lay, eta, h):
+        """Stiffness matrix [n_t (p+1)]^2 of prism (triangle e, layer lay); local
+        node (q, m) -> row m * n_t + q (triangle node q, vertical GLL node m)."""
+        tm, p, nz = self.tm, self.p, self.nz
+        nt = tm.nt_loc
+        A, B, C = tm.verts[tm.tris[e]]
+        xr, xs_ = (B[0] - A[0]) / 2.0, (C[0] - A[0]) / 2.0
+        yr, ys_ = (B[1] - A[1]) / 2.0, (C[1] - A[1]) / 2.0
+        cols = tm.nodes[e]
+        E, H = eta[cols], h[cols]
+        e_q, er, es = self.L @ E, self.Lr @ E, self.Ls @ E
+        h_q, hr, hs = self.L @ H, self.Lr @ H, self.Ls @ H
+        xi, wv, D = self.rule.xi, self.rule.w, self.rule.D
+        K = np.zeros((nt * (p + 1), nt * (p + 1)))
+        for k in range(p + 1):
+            sig = (lay + 0.5 * (1.0 + xi[k])) / nz
+            for q in range(len(self.wq)):
+                zr = -hr[q] + sig * (er[q] + hr[q])
+                zs = -hs[q] + sig * (es[q] + hs[q])
+                zt = (e_q[q] + h_q[q]) / (2.0 * nz)
+                J = np.array([[xr, xs_, 0.0], [yr, ys_, 0.0], [zr, zs, zt]])
+                det = np.linalg.det(J)
+                Jinv = np.linalg.inv(J)
+                # reference gradients of every local basis function at (q, t_k)
+                gref = np.zeros((3, nt * (p + 1)))
+                for m in range(p + 1):
+                    sl = slice(m * nt, (m + 1) * nt)
+                    if m == k:
+                        gref[0, sl] = self.Lr[q]
+                        gref[1, sl] = self.Ls[q]
+                    gref[2, sl] = self.L[q] * D[k, m]
+                g = Jinv.T @ gref
+                K += self.wq[q] * wv[k] * abs(det) * (g.T @ g)
+        return K
+
+    def local_to_global(self, e, lay):
+        tm, p, ns = self.tm, self.p, self.ns
+        return np.concatenate([(lay * p + m) * ns + tm.nodes[e] for m in range(p + 1)])
+
+    def assemble(self, eta, h):
+        """The global stiffness matrix A(eta) [N, N] (scipy CSR)."""
+        rows, cols, vals = [], [], []
+        for e in range(len(self.tm.tris)):
+            for lay in range(self.nz):
+                K = self.element_matrix(e, lay, eta, h)
+                gi = self.local_to_global(e, lay)
+                rows.append(np.repeat(gi, len(gi)))
+                cols.append(np.tile(gi, len(gi)))
+                vals.append(K.ravel())
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(self.N, self.N))
+
+
+def laplace_solve(pm, eta, h, phis):
+    """phi [N] with phi = phis on the surface plane and A_II phi_I = -A_IS phis
+    (homogeneous Neumann on the bottom and the lateral walls)."""
+    A = pm.assemble(eta, h)
+    NI = pm.N - pm.ns
+    phi = np.zeros(pm.N)
+    phi[NI:] = phis
+    rhs = -(A[:NI, NI:] @ phis)
+    phi[:NI] = spla.spsolve(A[:NI, :NI].tocsc(), rhs)
+    return phi
+
+
+def w_recovery(pm, eta, h, phi):
+    """w = d phi / dz at every surface node: phi_t / z_t on its vertical GLL
+    line in the top layer (the extrusion is vertical, so every prism sharing
+    the line gives this value)."""
+    p, ns, nz = pm.p, pm.ns, pm.nz
+    D = pm.rule.D
+    top = np.stack([phi[(pm.nv - 1 - p + m) * ns:(pm.nv - p + m) * ns] for m in range(p + 1)])
+    return (D[p] @ top) * 2.0 * nz / (eta + h)

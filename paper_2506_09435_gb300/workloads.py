@@ -232,6 +232,38 @@ def cylinder_case(nth=64, nr=24, nz=3, p=4, ka=1.0, kh=1.0, a=1.0, Rout=10.0, g=
                 a=a, R=Rout, h0=kh / k, k=k, g=g, T=period(k, kh / k, g))
 
 
+def triangulated_box(nx, ny, Lx=1.0, Ly=1.0, jitter=0.2, seed=7):
+    """Unstructured triangulation of the walled box [0, Lx] x [0, Ly] (the
+    paper's surface meshes are triangular, Sec. 3.1.2): an (nx+1) x (ny+1)
+    vertex lattice whose interior vertices are moved by up to `jitter` of the
+    spacing in each direction (splitmix64(seed) draws), each cell cut into two
+    triangles along a diagonal chosen by a draw.  Returns (vertices [nv, 2],
+    triangles [nt, 3] counter-clockwise)."""
+    dx, dy = Lx / nx, Ly / ny
+    u = uniform01(seed, 2 * (nx + 1) * (ny + 1) + nx * ny)
+    verts = np.zeros(((nx + 1) * (ny + 1), 2))
+    for j in range(ny + 1):
+        for i in range(nx + 1):
+            v = j * (nx + 1) + i
+            x, y = i * dx, j * dy
+            if 0 < i < nx:
+                x += jitter * dx * (2 * u[2 * v] - 1)
+            if 0 < j < ny:
+                y += jitter * dy * (2 * u[2 * v + 1] - 1)
+            verts[v] = (x, y)
+    tris = []
+    base = 2 * (nx + 1) * (ny + 1)
+    for j in range(ny):
+        for i in range(nx):
+            a, b = j * (nx + 1) + i, j * (nx + 1) + i + 1
+            c, d = a + nx + 1, b + nx + 1
+            if u[base + j * nx + i] < 0.5:
+                tris += [(a, b, d), (a, d, c)]
+            else:
+                tris += [(a, b, c), (b, d, c)]
+    return verts, np.array(tris, dtype=np.int64)
+
+
 def manufactured_potential(x, y, z, h, kx, ky):
     """Harmonic phi = cosh(kappa (z + h)) cos(kx x) cos(ky y) and its d/dz."""
     kap = math.hypot(kx, ky)

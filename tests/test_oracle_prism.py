@@ -1,0 +1,244 @@
+"""Pins of the prism oracle (oracle/prism.py): extruded prisms over an
+unstructured triangular surface mesh (Sec. 3.1.2).
+
+  * triangle nodes: count, vertices, edge nodes at the GLL points, symmetry;
+  * triangle quadrature: exact integrals of barycentric monomials,
+    int_T l1^a l2^b l3^c = 2 |T| a! b! c! / (a + b + c + 2)!;
+  * nodal basis: cardinal at the nodes, reproduces every polynomial of degree
+    <= p and its derivatives;
+  * numbering: every shared node gets one position from all its triangles;
+  * element matrix on a flat prism = the Kronecker form built from the
+    triangle's stiffness and mass integrated exactly in closed form (monomial
+    integrals, no quadrature) and the GLL vertical mass / exact 1D stiffness;
+  * assembled operator: symmetric, constants in its null space, positive
+    semi-definite on a curved (eta-following) mesh; a(I u, I v) converges to
+    int grad u . grad v over a domain with a curved surface and a bottom bump
+    (integrated independently in physical coordinates), which a wrong term
+    of the vertical metric breaks;
+  * Laplace solve + w: a constant potential is reproduced; the manufactured
+    harmonic potential cosh(kappa (z + h)) cos(kx x) cos(ky y) gives the exact
+    Dirichlet-to-Neumann map with errors falling exponentially in p and at
+    rates approaching p under refinement (flat and curved eta)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import gll
+from oracle import prism as P
+from paper_2506_09435_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_triangle_nodes(p):
+    r, s = P.tri_nodes(p)
+    assert len(r) == (p + 1) * (p + 2) // 2
+    pts = set(zip(np.round(r, 12), np.round(s, 12)))
+    assert {(-1.0, -1.0), (1.0, -1.0), (-1.0, 1.0)} <= pts
+    xi = gll.nodes(p)[0]
+    edge = np.sort(r[np.isclose(s, -1.0)])
+    assert np.allclose(edge, xi, atol=1e-14)                  # edge A-B carries the GLL points
+    assert np.allclose(np.sort(s[np.isclose(r, -1.0)]), xi, atol=1e-14)
+    hyp = np.isclose(r + s, 0.0)
+    assert hyp.sum() == p + 1
+    assert pts == set(zip(np.round(s, 12), np.round(r, 12)))  # mirror r <-> s
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_triangle_quadrature_exact(n):
+    r, s, w = P.tri_quadrature(n)
+    lb, lc = (1 + r) / 2, (1 + s) / 2
+    la = 1 - lb - lc
+    for a, b, c in itertools.product(range(2 * n), repeat=3):
+        if a + b + c > 2 * n - 2:
+            continue
+        exact = 2 * 2 * math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + 2)
+        assert abs((w * la ** a * lb ** b * lc ** c).sum() - exact) < 1e-14
+    assert abs(w.sum() - 2.0) < 1e-14
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_nodal_basis(p):
+    rn, sn = P.tri_nodes(p)
+    L = P.tri_basis(p, rn, sn)[0]
+    assert np.allclose(L, np.eye(len(rn)), atol=1e-12)
+    rq, sq, _ = P.tri_quadrature(p + 2)
+    L, Lr, Ls = P.tri_basis(p, rq, sq)
+    for a, b in itertools.product(range(p + 1), repeat=2):
+        if a + b > p:
+            continue
+        f = rn ** a * sn ** b
+        assert np.allclose(L @ f, rq ** a * sq ** b, atol=1e-12)
+        assert np.allclose(Lr @ f, a * rq ** max(a - 1, 0) * sq ** b if a else 0 * rq, atol=1e-11)
+        assert np.allclose(Ls @ f, b * rq ** a * sq ** max(b - 1, 0) if b else 0 * rq, atol=1e-11)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_numbering_is_conforming(p):
+    v, t = W.triangulated_box(4, 3, 2.0, 1.0)
+    tm = P.TriMesh(v, t, p)
+    nedge = len({(min(a, b), max(a, b)) for tr in t for a, b in ((tr[0], tr[1]), (tr[1], tr[2]), (tr[0], tr[2]))})
+    assert tm.ns == len(v) + nedge * (p - 1) + len(t) * (p - 1) * (p - 2) // 2
+    rn, sn = P.tri_nodes(p)
+    lb, lc = (1 + rn) / 2, (1 + sn) / 2
+    for e, (A, B, C) in enumerate(t):
+        X = (1 - lb - lc)[:, None] * v[A] + lb[:, None] * v[B] + lc[:, None] * v[C]
+        assert np.allclose(X[:, 0], tm.xs[tm.nodes[e]], atol=1e-14)
+        assert np.allclose(X[:, 1], tm.ys[tm.nodes[e]], atol=1e-14)
+    assert len(np.unique(np.round(np.stack([tm.xs, tm.ys], 1), 12), axis=0)) == tm.ns
+
+
+def exact_triangle_matrices(p, A, B, C):
+    """Stiffness and mass of the order-p nodal basis on the affine triangle
+    ABC, integrated exactly: the cardinal functions in monomials u^a v^b
+    (u, v the barycentric coordinates of B and C), int_T u^a v^b dr ds =
+    4 a! b! / (a + b + 2)!."""
+    rn, sn = P.tri_nodes(p)
+    ex = [(a, b) for b in range(p + 1) for a in range(p + 1 - b)]
+    un, vn = (1 + rn) / 2, (1 + sn) / 2
+    Cc = np.linalg.inv(np.array([[u ** a * vv ** b for a, b in ex] for u, vv in zip(un, vn)]))
+
+    def I(a, b):
+        return 0.0 if a < 0 or b < 0 else 4.0 * math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+
+    m = len(ex)
+    Mm, Srr, Srs, Sss = (np.zeros((m, m)) for _ in range(4))
+    for i, (a1, b1) in enumerate(ex):
+        for j, (a2, b2) in enumerate(ex):
+            Mm[i, j] = I(a1 + a2, b1 + b2)
+            Srr[i, j] = a1 * a2 / 4.0 * I(a1 + a2 - 2, b1 + b2)
+            Srs[i, j] = a1 * b2 / 4.0 * I(a1 + a2 - 1, b1 + b2 - 1)
+            Sss[i, j] = b1 * b2 / 4.0 * I(a1 + a2, b1 + b2 - 2)
+    J2 = np.array([[B[0] - A[0], C[0] - A[0]], [B[1] - A[1], C[1] - A[1]]]) / 2.0
+    det2 = abs(np.linalg.det(J2))
+    Gi = np.linalg.inv(J2) @ np.linalg.inv(J2).T * det2     # |det| J^-1 J^-T
+    S = Gi[0, 0] * Srr + Gi[0, 1] * (Srs + Srs.T) + Gi[1, 1] * Sss
+    return Cc.T @ S @ Cc, det2 * (Cc.T @ Mm @ Cc)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_flat_prism_equals_exact_kronecker_form(p):
+    v, t = W.triangulated_box(2, 2, 1.5, 1.0, jitter=0.3, seed=3)
+    tm = P.TriMesh(v, t, p)
+    nz, h0 = 3, 0.7
+    pm = P.PrismMesh(tm, nz)
+    eta, h = np.zeros(tm.ns), np.full(tm.ns, h0)
+    rule = gll.Rule(p)
+    S1 = rule.D.T @ np.diag(rule.w) @ rule.D                  # exact 1D stiffness (degree 2p-2)
+    zt = h0 / (2 * nz)
+    for e in range(len(t)):
+        ST, MT = exact_triangle_matrices(p, *v[t[e]])
+        K = np.kron(np.diag(rule.w) * zt, ST) + np.kron(S1 / zt, MT)
+        for lay in (0, nz - 1):
+            Ke = pm.element_matrix(e, lay, eta, h)
+            assert np.max(np.abs(Ke - K)) <= 1e-12 * np.max(np.abs(K))
+
+
+def curved_case(p, nx=3, nz=2, h0=0.6, amp=0.05):
+    v, t = W.triangulated_box(nx, nx, 1.0, 1.0)
+    tm = P.TriMesh(v, t, p)
+    pm = P.PrismMesh(tm, nz)
+    x, y = tm.xs, tm.ys
+    eta = amp * np.cos(math.pi * x) * np.sin(0.5 * math.pi * y)
+    h = h0 - 0.1 * np.exp(-((x - 0.5) ** 2 + (y - 0.4) ** 2) / 0.05)
+    return tm, pm, eta, h
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_assembled_operator_properties(p):
+    tm, pm, eta, h = curved_case(p, nx=2)
+    A = pm.assemble(eta, h).toarray()
+    assert np.max(np.abs(A - A.T)) <= 1e-12 * np.max(np.abs(A))
+    assert np.max(np.abs(A @ np.ones(pm.N))) <= 1e-11 * np.max(np.abs(A))
+    ev = np.linalg.eigvalsh(A)
+    assert ev[0] >= -1e-10 * ev[-1] and ev[1] > 1e-8 * ev[-1]   # one zero eigenvalue (constants), the rest > 0
+
+
+def test_constant_potential_reproduced():
+    tm, pm, eta, h = curved_case(3)
+    phi = P.laplace_solve(pm, eta, h, np.full(tm.ns, 2.5))
+    assert np.max(np.abs(phi - 2.5)) < 1e-12
+    assert np.max(np.abs(P.w_recovery(pm, eta, h, phi))) < 1e-11
+
+
+def dtn_error(nx, p, nz, h0=0.5, amp=0.0):
+    """Relative max error of w for cosh(kappa (z + h)) cos(pi x) cos(pi y) in
+    the walled unit box (zero normal derivative on every wall and the bottom)."""
+    v, t = W.triangulated_box(nx, nx, 1.0, 1.0)
+    tm = P.TriMesh(v, t, p)
+    pm = P.PrismMesh(tm, nz)
+    kx = ky = math.pi
+    kap = math.hypot(kx, ky)
+    x, y = tm.xs, tm.ys
+    eta = amp * np.cos(kx * x) * np.cos(ky * y)
+    h = np.full(tm.ns, h0)
+    phis = np.cosh(kap * (eta + h0)) * np.cos(kx * x) * np.cos(ky * y)
+    w = P.w_recovery(pm, eta, h, P.laplace_solve(pm, eta, h, phis))
+    wex = kap * np.sinh(kap * (eta + h0)) * np.cos(kx * x) * np.cos(ky * y)
+    return np.max(np.abs(w - wex)) / np.max(np.abs(wex))
+
+
+def test_dtn_converges_exponentially_in_p():
+    errs = [dtn_error(3, p, 2) for p in (1, 2, 3, 4, 5)]
+    assert errs[-1] < 5e-4
+    assert all(b < 0.35 * a for a, b in zip(errs, errs[1:])), errs
+    curved = [dtn_error(3, p, 2, amp=0.03) for p in (2, 3, 4, 5)]
+    assert curved[-1] < 1e-3 and all(b < 0.5 * a for a, b in zip(curved, curved[1:])), curved
+
+
+@pytest.mark.parametrize("p,rate", [(2, 1.7), (3, 2.6)])
+def test_dtn_converges_under_refinement(p, rate):
+    errs = [dtn_error(nx, p, max(1, nx // 2)) for nx in (2, 4, 8)]
+    assert math.log2(errs[1] / errs[2]) > rate, errs
+
+
+def test_bilinear_form_converges_on_curved_domain():
+    """a(I u, I v) = (I u)^T A (I v) for smooth u, v against int grad u . grad v
+    over the domain between the bottom z = -h(x, y) (a Gaussian bump) and the
+    surface z = eta(x, y), computed by a tensor Gauss rule in (x, y, zeta) with
+    z = -h + zeta (eta + h): it converges as p grows (a wrong sign of a
+    bathymetry or surface term of the metric does not)."""
+    def eta_f(x, y):
+        return 0.05 * np.cos(math.pi * x) * np.sin(0.5 * math.pi * y)
+
+    def h_f(x, y):
+        return 0.6 - 0.1 * np.exp(-((x - 0.5) ** 2 + (y - 0.4) ** 2) / 0.05)
+
+    def u(x, y, z):
+        return np.sin(x + 2 * y) * np.cosh(z)
+
+    def v(x, y, z):
+        return np.cos(2 * x - y) * np.exp(z)
+
+    def grads(x, y, z):
+        gu = np.stack([np.cos(x + 2 * y) * np.cosh(z), 2 * np.cos(x + 2 * y) * np.cosh(z),
+                       np.sin(x + 2 * y) * np.sinh(z)])
+        gv = np.stack([-2 * np.sin(2 * x - y) * np.exp(z), np.sin(2 * x - y) * np.exp(z),
+                       np.cos(2 * x - y) * np.exp(z)])
+        return gu, gv
+
+    g, w = np.polynomial.legendre.leggauss(40)
+    g, w = (g + 1) / 2, w / 2
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    WW = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    E, H = eta_f(X, Y), h_f(X, Y)
+    gu, gv = grads(X, Y, -H + Z * (E + H))
+    exact = (WW * (E + H) * (gu * gv).sum(0)).sum()
+    errs = []
+    for p in (2, 3, 4, 5):
+        v_, t_ = W.triangulated_box(3, 3, 1.0, 1.0)
+        tm = P.TriMesh(v_, t_, p)
+        pm = P.PrismMesh(tm, 2)
+        x, y = tm.xs, tm.ys
+        eta, h = eta_f(x, y), h_f(x, y)
+        xi = pm.rule.xi
+        zs = []
+        for k in range(pm.nv):
+            lay = min(k // p, pm.nz - 1)
+            sig = (lay + 0.5 * (1 + xi[k - lay * p])) / pm.nz
+            zs.append(-h + sig * (eta + h))
+        Zn, Xn, Yn = np.concatenate(zs), np.tile(x, pm.nv), np.tile(y, pm.nv)
+        ah = u(Xn, Yn, Zn) @ (pm.assemble(eta, h) @ v(Xn, Yn, Zn))
+        errs.append(abs(ah - exact) / abs(exact))
+    assert errs[-1] < 1.5e-4 and errs[2] < 3e-4 and errs[-1] < 0.1 * errs[0], errs
