@@ -8,8 +8,9 @@ vertically to follow the free surface (Sec. 3.1.2), with C0 nodal Lagrange
 elements of degree p (Sec. 3.1).  This module restates, for those prisms, what
 the hexahedral oracle computes: the stiffness operator of the weak Laplace
 form (Eq. Laplace_weak) by its quadrature definition, the Dirichlet-Neumann
-solve with phi = phi_eta on the surface (Eq. Laplace_strong), and the vertical
-surface velocity w (Steps 4.4-4.5).
+solve with phi = phi_eta on the surface (Eq. Laplace_strong), the vertical
+surface velocity w (Steps 4.4-4.5), the free-surface conditions projected
+with the consistent surface mass, and the RK4 step (Sec. 3.2).
 
 Readings (the paper names the element family, not its nodes or quadrature):
   * element space on a prism: the degree-p polynomials on the triangle times
@@ -233,3 +234,78 @@ def w_recovery(pm, eta, h, phi):
     D = pm.rule.D
     top = np.stack([phi[(pm.nv - 1 - p + m) * ns:(pm.nv - p + m) * ns] for m in range(p + 1)])
     return (D[p] @ top) * 2.0 * nz / (eta + h)
+
+
+# ----------------------------------------------------------------------------- free surface
+# The free-surface conditions on the triangular surface mesh.  Reading: the
+# paper solves its free-surface weak forms with the consistent mass
+# (Sec. 3.1.1, Eq. free_surface_weak; Sec. 4 solver settings); here each RHS
+# is the Galerkin projection M k = int f l_i dA onto the continuous nodal
+# space, f evaluated at the triangle quadrature points from the interpolants of
+# eta, phi_eta and w and the element gradients of eta and phi_eta.
+
+def surface_mass(pm):
+    """Consistent mass matrix M_ij = int l_i l_j dA of the surface space [Ns, Ns]."""
+    tm = pm.tm
+    rows, cols, vals = [], [], []
+    for e, (A, B, C) in enumerate(tm.tris):
+        va, vb, vc = tm.verts[A], tm.verts[B], tm.verts[C]
+        det2 = abs((vb[0] - va[0]) * (vc[1] - va[1]) - (vc[0] - va[0]) * (vb[1] - va[1])) / 4.0
+        Me = (pm.L * (pm.wq * det2)[:, None]).T @ pm.L
+        gi = tm.nodes[e]
+        rows.append(np.repeat(gi, len(gi)))
+        cols.append(np.tile(gi, len(gi)))
+        vals.append(Me.ravel())
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(pm.ns, pm.ns))
+
+
+def project_rhs(pm, eta, phis, w, g, linear=False):
+    """(k_eta, k_phi): the Galerkin projections of the kinematic and dynamic
+    free-surface conditions (Sec. 2)
+        f_eta = -grad eta . grad phi_eta + w (1 + |grad eta|^2)
+        f_phi = -g eta - 1/2 |grad phi_eta|^2 + 1/2 w^2 (1 + |grad eta|^2)
+    (linear: f_eta = w, f_phi = -g eta)."""
+    tm = pm.tm
+    b_eta = np.zeros(pm.ns)
+    b_phi = np.zeros(pm.ns)
+    for e, (A, B, C) in enumerate(tm.tris):
+        va, vb, vc = tm.verts[A], tm.verts[B], tm.verts[C]
+        J2 = np.array([[vb[0] - va[0], vc[0] - va[0]], [vb[1] - va[1], vc[1] - va[1]]]) / 2.0
+        Jit = np.linalg.inv(J2).T
+        det2 = abs(np.linalg.det(J2))
+        gi = tm.nodes[e]
+        E, F, Wn = eta[gi], phis[gi], w[gi]
+        eq, wq = pm.L @ E, pm.L @ Wn
+        ge = Jit @ np.stack([pm.Lr @ E, pm.Ls @ E])          # [2, nq] physical gradients
+        gp = Jit @ np.stack([pm.Lr @ F, pm.Ls @ F])
+        if linear:
+            fe, fp = wq, -g * eq
+        else:
+            q2 = 1.0 + (ge * ge).sum(0)
+            fe = -(ge * gp).sum(0) + wq * q2
+            fp = -g * eq - 0.5 * (gp * gp).sum(0) + 0.5 * wq * wq * q2
+        wt = pm.wq * det2
+        b_eta[gi] += pm.L.T @ (wt * fe)
+        b_phi[gi] += pm.L.T @ (wt * fp)
+    M = surface_mass(pm).tocsc()
+    return spla.spsolve(M, b_eta), spla.spsolve(M, b_phi)
+
+
+def rhs(pm, h, eta, phis, g, linear=False):
+    """The free-surface right-hand side at (eta, phi_eta): Laplace solve on the
+    eta-following prisms (on the still-water mesh when linear), w, projected
+    conditions."""
+    geo = np.zeros_like(eta) if linear else eta
+    phi = laplace_solve(pm, geo, h, phis)
+    w = w_recovery(pm, geo, h, phi)
+    return project_rhs(pm, eta, phis, w, g, linear)
+
+
+def rk4_step(pm, h, eta, phis, dt, g, linear=False):
+    """One classical RK4 step (Sec. 3.2) of (eta, phi_eta)."""
+    k1 = rhs(pm, h, eta, phis, g, linear)
+    k2 = rhs(pm, h, eta + 0.5 * dt * k1[0], phis + 0.5 * dt * k1[1], g, linear)
+    k3 = rhs(pm, h, eta + 0.5 * dt * k2[0], phis + 0.5 * dt * k2[1], g, linear)
+    k4 = rhs(pm, h, eta + dt * k3[0], phis + dt * k3[1], g, linear)
+    return (eta + dt / 6.0 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]),
+            phis + dt / 6.0 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]))
