@@ -456,6 +456,46 @@ fnpf_status fnpf_step_adjoint_taped(fnpf_mesh* mesh, int slot, const double* lam
                                     double* lam_eta_out, double* lam_phis_out, double* lam_h, double dt,
                                     void* stream);
 
+/* Prism elements over an unstructured triangular surface mesh (the paper's
+ * own mesh, Sec. 3.1.2: a triangular free-surface mesh extruded into N_z
+ * layers of prisms whose columns follow the free surface).  Element: degree-p
+ * polynomials on the triangle times the degree-p GLL basis in the vertical;
+ * triangle nodes of Blyth & Pozrikidis built from the 1D GLL points;
+ * straight-sided triangles; z = -h + sigma (eta + h); quadrature: the
+ * (p+2)^2-point collapsed Gauss-Legendre rule on the triangle times GLL
+ * collocation in the vertical.  Surface numbering: the vertices, then p - 1
+ * nodes per edge (edges in order of first appearance over the triangles'
+ * edges (A,B), (B,C), (A,C); nodes from the lower to the higher vertex
+ * number), then each triangle's interior nodes, local order (i, j) with j
+ * outer; volume node (plane k, surface node c) = k * Ns + c.  Walls (zero
+ * normal derivative) on the boundary and the bottom.
+ *
+ * fnpf_prism_numbering (host only): verts [2 nverts] (x, y), tris [3 ntris]
+ * (vertex numbers, counter-clockwise), order p (1..8) -> the surface node of
+ * every local triangle node tnodes [ntris][(p+1)(p+2)/2], the surface node
+ * coordinates x, y [Ns] (any of the three may be NULL) and *ns = Ns.
+ * fnpf_prism_tables (host only): values and r, s-derivatives of the nodal
+ * basis at the quadrature points L, Lr, Ls [nq][(p+1)(p+2)/2] and weights
+ * wq [nq] (any may be NULL), *nq = (p+2)^2.
+ * fnpf_prism_create copies the mesh (host arrays) to the device;
+ * fnpf_prism_apply computes y = A(eta, h) x (all device arrays: eta, h [Ns],
+ * x, y [N], N = (N_z p + 1) Ns; the full operator, surface rows included;
+ * eta + h > 0 assumed), deterministic (element results summed per node in a
+ * fixed order), asynchronous on stream.  Errors: EINVAL (NULL, sizes, a
+ * vertex out of range, a repeated vertex, a triangle of zero or negative
+ * area), ENOMEM, ECUDA; the message from fnpf_prism_last_error(mesh or NULL). */
+typedef struct fnpf_prism fnpf_prism;
+fnpf_status fnpf_prism_numbering(const double* verts, int nverts, const int* tris, int ntris, int p, int* tnodes,
+                                 double* x, double* y, int* ns);
+fnpf_status fnpf_prism_tables(int p, double* L, double* Lr, double* Ls, double* wq, int* nq);
+fnpf_status fnpf_prism_create(const double* verts, int nverts, const int* tris, int ntris, int p, int nz,
+                              fnpf_prism** out);
+void fnpf_prism_destroy(fnpf_prism* mesh);
+fnpf_status fnpf_prism_sizes(const fnpf_prism* mesh, int64_t* n_vol, int64_t* n_surf);
+fnpf_status fnpf_prism_apply(fnpf_prism* mesh, const double* eta, const double* h, const double* x, double* y,
+                             void* stream);
+const char* fnpf_prism_last_error(const fnpf_prism* mesh);
+
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */
 const char* fnpf_last_error(const fnpf_mesh* mesh);

@@ -99,6 +99,12 @@ def load():
         "fnpf_ensemble_set_batching": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64],
         "fnpf_ensemble_stats": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int64)],
+        "fnpf_prism_numbering": [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                 ctypes.POINTER(ctypes.c_int)],
+        "fnpf_prism_tables": [ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int)],
+        "fnpf_prism_create": [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
+        "fnpf_prism_sizes": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+        "fnpf_prism_apply": [vp, vp, vp, vp, vp, vp],
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
@@ -122,6 +128,10 @@ def load():
     lib.fnpf_ensemble_destroy.restype = None
     lib.fnpf_ensemble_last_error.argtypes = [vp]
     lib.fnpf_ensemble_last_error.restype = ctypes.c_char_p
+    lib.fnpf_prism_destroy.argtypes = [vp]
+    lib.fnpf_prism_destroy.restype = None
+    lib.fnpf_prism_last_error.argtypes = [vp]
+    lib.fnpf_prism_last_error.restype = ctypes.c_char_p
     lib.fnpf_status_string.argtypes = [ctypes.c_int]
     lib.fnpf_status_string.restype = ctypes.c_char_p
     return lib
@@ -500,3 +510,82 @@ class Ensemble:
         if st != FNPF_OK:
             raise FnpfError(st, _LIB.fnpf_ensemble_last_error(self._h).decode())
         return [i.as_dict() for i in infos] if infos is not None else None
+
+
+def _host_mesh_arrays(verts, tris):
+    import numpy as np
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    if v.ndim != 2 or v.shape[1] != 2 or t.ndim != 2 or t.shape[1] != 3:
+        raise ValueError("verts must be [nverts, 2] and tris [ntris, 3]")
+    return v, t
+
+
+def prism_numbering(verts, tris, p):
+    """(tnodes [ntris, (p+1)(p+2)/2], x [Ns], y [Ns]) of the order-p nodes of a
+    triangle mesh (fnpf_prism_numbering; host only)."""
+    import numpy as np
+    v, t = _host_mesh_arrays(verts, tris)
+    ns = ctypes.c_int()
+    st = _LIB.fnpf_prism_numbering(v.ctypes.data, len(v), t.ctypes.data, len(t), int(p), None, None, None,
+                                   ctypes.byref(ns))
+    if st != FNPF_OK:
+        raise FnpfError(st, "prism numbering")
+    nt = (p + 1) * (p + 2) // 2
+    tn = np.zeros((len(t), nt), dtype=np.int32)
+    x, y = np.zeros(ns.value), np.zeros(ns.value)
+    st = _LIB.fnpf_prism_numbering(v.ctypes.data, len(v), t.ctypes.data, len(t), int(p), tn.ctypes.data,
+                                   x.ctypes.data, y.ctypes.data, ctypes.byref(ns))
+    if st != FNPF_OK:
+        raise FnpfError(st, "prism numbering")
+    return tn, x, y
+
+
+def prism_tables(p):
+    """(L, Lr, Ls [nq, nt], wq [nq]): the nodal triangle basis and its r, s
+    derivatives at the quadrature points (fnpf_prism_tables; host only)."""
+    import numpy as np
+    nq = ctypes.c_int()
+    st = _LIB.fnpf_prism_tables(int(p), None, None, None, None, ctypes.byref(nq))
+    if st != FNPF_OK:
+        raise FnpfError(st, "prism tables")
+    nt = (p + 1) * (p + 2) // 2
+    L, Lr, Ls = (np.zeros((nq.value, nt)) for _ in range(3))
+    wq = np.zeros(nq.value)
+    st = _LIB.fnpf_prism_tables(int(p), L.ctypes.data, Lr.ctypes.data, Ls.ctypes.data, wq.ctypes.data,
+                                ctypes.byref(nq))
+    if st != FNPF_OK:
+        raise FnpfError(st, "prism tables")
+    return L, Lr, Ls, wq
+
+
+class PrismMesh:
+    """N_z layers of order-p prisms over an unstructured triangle mesh
+    (fnpf_prism_*): y = A(eta, h) x on the device."""
+
+    def __init__(self, verts, tris, p, nz):
+        v, t = _host_mesh_arrays(verts, tris)
+        h = ctypes.c_void_p()
+        st = _LIB.fnpf_prism_create(v.ctypes.data, len(v), t.ctypes.data, len(t), int(p), int(nz), ctypes.byref(h))
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_prism_last_error(None).decode())
+        self._h = h
+        self.p, self.nz = int(p), int(nz)
+        nv, ns = ctypes.c_int64(), ctypes.c_int64()
+        _LIB.fnpf_prism_sizes(h, ctypes.byref(nv), ctypes.byref(ns))
+        self.N, self.ns = nv.value, ns.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _LIB.fnpf_prism_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def apply(self, eta, h, x, y, stream=None):
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (x, self.N, "float64", "x"), (y, self.N, "float64", "y"))
+        st = _LIB.fnpf_prism_apply(self._h, *ptrs, _stream(stream))
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_prism_last_error(self._h).decode())
