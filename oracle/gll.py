@@ -1,7 +1,7 @@
 """Gauss-Lobatto-Legendre (GLL) rule of order p: nodes, weights, derivative matrix.
 
 Oracle (test infrastructure only).  The paper uses C0 nodal Lagrange elements
-of degree p (Sec. 3.1, definition of the space V_D); this build uses the
+of degree p (Sec. 3.1, definition of the space V_D); the hexahedral elements use the
 tensor-product GLL nodal basis, whose 1D ingredients are defined here from
 their textbook definitions:
 
