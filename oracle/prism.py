@@ -309,3 +309,63 @@ def rk4_step(pm, h, eta, phis, dt, g, linear=False):
     k4 = rhs(pm, h, eta + dt * k3[0], phis + dt * k3[1], g, linear)
     return (eta + dt / 6.0 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]),
             phis + dt / 6.0 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]))
+
+
+# ----------------------------------------------------------------------------- modal filter
+# The paper's modal filter on its triangular surface elements (Sec. 3.2): the
+# nodal values of an element are mapped to a modal basis on the reference
+# triangle R = {r, s >= -1, r + s <= 0}, g_hat = V^-1 g with V_ij = psi_j(r_i),
+# scaled by F and mapped back, V F V^-1 g.  Readings: psi_(i, j) the
+# orthonormal Dubiner (PKDO) basis on R; F = diag(sigma_(i+j)) with the
+# exponential weights of the quadrilateral filter by total degree,
+# sigma_d = 1 for d <= N_c and exp(-alpha ((d - N_c) / (p - N_c))^s) above;
+# the filtered values replace the element-interior nodes only (shared nodes
+# keep theirs), as for the quadrilaterals.
+
+def _jacobi_normalized(n, a, b, x):
+    """The Jacobi polynomial P_n^(a,b)(x) normalised to unit L2 norm with the
+    weight (1 - x)^a (1 + x)^b on [-1, 1]."""
+    from math import gamma
+    from scipy.special import eval_jacobi
+    norm = 2.0 ** (a + b + 1) / (2 * n + a + b + 1) * gamma(n + a + 1) * gamma(n + b + 1) / (
+        gamma(n + a + b + 1) * gamma(n + 1))
+    return eval_jacobi(n, a, b, x) / np.sqrt(norm)
+
+
+def dubiner(p, r, s):
+    """The orthonormal Dubiner basis psi_(i, j), i + j <= p (tri_index order),
+    at the points (r, s) of R: [npts, (p+1)(p+2)/2]."""
+    r, s = np.asarray(r, dtype=np.float64), np.asarray(s, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        a = np.where(np.isclose(s, 1.0), -1.0, 2.0 * (1.0 + r) / (1.0 - s) - 1.0)
+    out = []
+    for i, j in tri_index(p):
+        out.append(np.sqrt(2.0) * _jacobi_normalized(i, 0, 0, a) * _jacobi_normalized(j, 2 * i + 1, 0, s)
+                   * (1.0 - s) ** i)
+    return np.stack(out, -1)
+
+
+def filter_matrix(p, alpha, order, cutoff):
+    """V F V^-1 on the order-p triangle nodes."""
+    rn, sn = tri_nodes(p)
+    V = dubiner(p, rn, sn)
+    sig = []
+    for i, j in tri_index(p):
+        d = i + j
+        sig.append(1.0 if d <= cutoff else float(np.exp(-alpha * ((d - cutoff) / (p - cutoff)) ** order)))
+    return V @ np.diag(sig) @ np.linalg.inv(V)
+
+
+def apply_filter(tm, f, alpha, order=2, cutoff=0):
+    """Filtered copy of the surface field f [Ns]: on every triangle the
+    interior nodes take the values of V F V^-1 applied to the element's nodal
+    values; vertex and edge nodes keep theirs."""
+    p = tm.p
+    Fm = filter_matrix(p, alpha, order, cutoff)
+    idx = tri_index(p)
+    interior = np.array([i > 0 and j > 0 and i + j < p for i, j in idx])
+    out = np.array(f, dtype=np.float64, copy=True)
+    for e in range(len(tm.tris)):
+        g = tm.nodes[e]
+        out[g[interior]] = (Fm @ f[g])[interior]
+    return out

@@ -301,3 +301,40 @@ def test_linear_standing_wave_follows_dispersion_relation():
     (measured 2.0e-1, 8.0e-2, 1.2e-2 for p = 1, 2, 3)."""
     e = [standing_wave_error(p) for p in (1, 2, 3)]
     assert e[2] < 2e-2 and e[2] < 0.25 * e[1] and e[1] < 0.5 * e[0], e
+
+
+# ----------------------------------------------------------------------------- modal filter
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_dubiner_basis_orthonormal(p):
+    rq, sq, wq = P.tri_quadrature(p + 2)
+    B = P.dubiner(p, rq, sq)
+    assert np.max(np.abs(B.T @ (wq[:, None] * B) - np.eye(B.shape[1]))) < 1e-12
+    # total degree: psi_(i, j) is a polynomial of degree i + j (the monomial fit of degree i + j is exact)
+    for c, (i, j) in enumerate(P.tri_index(p)):
+        d = i + j
+        M = np.stack([rq ** a * sq ** b for b in range(d + 1) for a in range(d + 1 - b)], 1)
+        coef, *_ = np.linalg.lstsq(M, B[:, c], rcond=None)
+        assert np.max(np.abs(M @ coef - B[:, c])) < 1e-11
+
+
+@pytest.mark.parametrize("p", [3, 4, 5])
+def test_triangle_filter(p):
+    v, t = W.triangulated_box(3, 2, 1.3, 1.0)
+    tm = P.TriMesh(v, t, p)
+    x, y = tm.xs, tm.ys
+    cutoff = 1
+    # alpha = 0: the identity
+    f = np.sin(3 * x) * np.cos(2 * y)
+    assert np.max(np.abs(P.apply_filter(tm, f, 0.0) - f)) < 1e-13
+    # polynomials of total degree <= cutoff are unchanged
+    lin = 0.3 + 1.2 * x - 0.7 * y
+    assert np.max(np.abs(P.apply_filter(tm, lin, 36.0, 4, cutoff) - lin)) < 1e-12
+    # one top mode on one triangle: its interior values are scaled by exactly sigma_p
+    rn, sn = P.tri_nodes(p)
+    top = P.dubiner(p, rn, sn)[:, P.tri_index(p).index((p, 0))]
+    Fm = P.filter_matrix(p, 2.0, 2, 0)
+    assert np.max(np.abs(Fm @ top - np.exp(-2.0) * top)) < 1e-12
+    # a mode of degree d <= p is scaled by sigma_d
+    mid = P.dubiner(p, rn, sn)[:, P.tri_index(p).index((1, 1))]
+    assert np.max(np.abs(Fm @ mid - np.exp(-2.0 * (2 / p) ** 2) * mid)) < 1e-12
