@@ -9,8 +9,8 @@
 // its mesh by a binary search over the first-block offsets in the launch's
 // parameters and calls K::run with that mesh's argument tuple (also in the
 // parameters) and its block position inside that mesh's grid, so every block
-// does exactly what it does in the mesh's own launch.  A per-mesh gate (an int per
-// mesh in device memory, set by the loop-condition kernels of a batched
+// does exactly what it does in the mesh's own launch.  A per-mesh gate (an int
+// per mesh in device memory, set by the loop-condition kernels of a batched
 // graph) skips the meshes whose loop has finished.
 //
 // While a Recorder is active on the calling thread, launch<K>, memset_async,
@@ -43,8 +43,9 @@ __device__ __forceinline__ Blk this_blk() {
 constexpr int kMaxBatch = 32;   // meshes per batched launch
 
 // Parameters of a batched launch: the meshes' argument tuples travel in the
-// kernel's own parameter space (read in place, like a single launch's
-// parameters, so the batched form needs no extra registers for them).
+// kernel's own parameter space (read in place through a mesh index known only
+// at run time, so the compiler keeps them in registers: the batched operator
+// kernels use about 15 registers more than their single-launch forms).
 template <class... P>
 struct BatchParams {
   const int* gate;              // gate[t] == 0: mesh t's blocks return at once (null: none)
