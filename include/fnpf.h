@@ -496,6 +496,68 @@ fnpf_status fnpf_prism_apply(fnpf_prism* mesh, const double* eta, const double* 
                              void* stream);
 const char* fnpf_prism_last_error(const fnpf_prism* mesh);
 
+/* The Laplace solve, the Dirichlet-to-Neumann map and the RK4 step on the prism
+ * mesh (Sec. 3.1.2 mesh; Sec. 3.4 Steps 4.1-4.6; ERK4, Sec. 3.2).
+ *   geometry: G = w |det J| J^-1 J^-T at every quadrature point of every prism
+ *     from eta and h (z = -h + sigma (eta + h)), stored once per solve (the
+ *     operator of fnpf_prism_apply, Eq. Laplace_weak, with that stored metric);
+ *   solve: A_II phi_I = -A_IS phis (Eq. Laplace_strong: phi = phis on the
+ *     surface plane, zero normal derivative on the bottom and the walls) by
+ *     Jacobi-preconditioned CG to ||r|| <= rtol ||b||, the host reading one
+ *     scalar per dot product;
+ *   w = d phi / dz at the surface nodes: phi_t / z_t on the top layer's
+ *     vertical GLL line (the extrusion is vertical, so every prism sharing the
+ *     line gives the same value);
+ *   right-hand side: the kinematic and dynamic free-surface conditions (Sec. 2)
+ *     f_eta = -grad eta . grad phis + w (1 + |grad eta|^2),
+ *     f_phi = -g eta - |grad phis|^2 / 2 + w^2 (1 + |grad eta|^2) / 2
+ *     (FNPF_LINEAR: f_eta = w, f_phi = -g eta with the solve and w on the
+ *     still-water geometry eta = 0), evaluated at the triangle quadrature
+ *     points and projected onto the nodal surface space with the consistent
+ *     mass, M k = int f l_i dA (Eq. free_surface_weak; the mass solve by
+ *     Jacobi-PCG to mass_rtol on the matrix assembled at the first call);
+ *   RK4: the classical four stages and combination, (eta, phis) updated in
+ *     place only when all four stages succeed.
+ * Arrays are DEVICE pointers owned by the caller: eta, h, phis, w, k_eta,
+ * k_phis [Ns]; phi, diag, x, y [N] (layout of fnpf_prism_apply: plane-major,
+ * surface plane last).  fnpf_prism_laplace_solve reads phi's interior entries
+ * as the initial guess and writes the whole of phi (phis on the surface
+ * plane).  fnpf_prism_dtn, _rhs and _rk4_step solve into the mesh's own
+ * potential, which warm-starts the next solve.  fnpf_prism_diagonal writes the
+ * diagonal of A(eta, h) (the Jacobi preconditioner), fnpf_prism_apply_stored
+ * y = A(eta, h) x through the stored metric.  opts may be NULL (defaults).
+ * info: NULL, one struct, or 4 (fnpf_prism_rk4_step, one per stage): iters =
+ * Laplace CG iterations, rel_res = ||r|| / ||b||, status; outer_iters = 0 and
+ * ms = 0.  The first call on a mesh allocates its workspace (about
+ * 9 N + 72 nprisms (p + 1) (p + 2)^2 doubles, synchronising the device) and
+ * builds the surface tables; later calls allocate nothing.  Calls on one mesh
+ * must not overlap; each returns after its stream has finished its work (the
+ * CG loops wait for every dot product).  eta + h > 0 is assumed (not checked).
+ * Errors: EINVAL (NULL, non-finite dt, bad options), ENOMEM, ECUDA, ENOCONV
+ * (an iteration cap reached), EBREAKDOWN (p.Ap <= 0), EDIVERGED (non-finite
+ * residual); the message from fnpf_prism_last_error(mesh). */
+typedef struct {
+  double rtol;             /* Laplace CG: ||r|| <= rtol ||b|| (default 1e-10)     */
+  int max_iter;            /* its iteration cap (default 20000)                   */
+  double mass_rtol;        /* surface-mass CG tolerance (default 1e-13)           */
+  int mass_max_iter;       /* its cap (default 5000)                              */
+  double g;                /* gravitational acceleration (default 9.81)           */
+  int model;               /* FNPF_NONLINEAR (default) or FNPF_LINEAR             */
+} fnpf_prism_opts;
+void fnpf_prism_default_opts(fnpf_prism_opts* opts);
+fnpf_status fnpf_prism_diagonal(fnpf_prism* mesh, const double* eta, const double* h, double* diag, void* stream);
+fnpf_status fnpf_prism_apply_stored(fnpf_prism* mesh, const double* eta, const double* h, const double* x, double* y,
+                                    void* stream);
+fnpf_status fnpf_prism_laplace_solve(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta,
+                                     const double* h, const double* phis, double* phi, fnpf_solve_info* info,
+                                     void* stream);
+fnpf_status fnpf_prism_dtn(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta, const double* h,
+                           const double* phis, double* w, fnpf_solve_info* info, void* stream);
+fnpf_status fnpf_prism_rhs(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta, const double* h,
+                           const double* phis, double* k_eta, double* k_phis, fnpf_solve_info* info, void* stream);
+fnpf_status fnpf_prism_rk4_step(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* h, double* eta,
+                                double* phis, double dt, fnpf_solve_info* info, void* stream);
+
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */
 const char* fnpf_last_error(const fnpf_mesh* mesh);

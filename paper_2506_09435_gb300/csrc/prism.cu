@@ -27,20 +27,8 @@
 #include <vector>
 
 #include "fnpf_internal.cuh"
+#include "prism.cuh"
 
-struct fnpf_prism {
-  int p = 0, n = 0, nz = 0, nt = 0, nq = 0, ntri = 0;
-  int ns = 0, nv = 0;
-  int64_t N = 0;
-  std::vector<int> tnodes;   // host copy [ntri][nt]
-  std::vector<double> xs, ys;
-  int* d_tnodes = nullptr;
-  double* d_tab = nullptr;   // geo [ntri][4], L, Lr, Ls [nq][nt], wq [nq], xi, wv [n], D [n][n]
-  double* d_ye = nullptr;    // element results [ntri * nz][nt * n]
-  int64_t* d_off = nullptr;  // incidence offsets [N + 1]
-  int64_t* d_inc = nullptr;  // indices into d_ye
-  std::string err;
-};
 
 namespace {
 
@@ -388,6 +376,7 @@ fnpf_status fnpf_prism_tables(int p, double* L, double* Lr, double* Ls, double* 
 
 void fnpf_prism_destroy(fnpf_prism* m) {
   if (!m) return;
+  fnpf::prism_step_free(m);
   cudaFree(m->d_tnodes);
   cudaFree(m->d_tab);
   cudaFree(m->d_ye);

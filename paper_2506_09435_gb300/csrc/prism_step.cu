@@ -1,0 +1,251 @@
+// The Laplace solve, w and the RK4 step on prisms over an unstructured
+// triangular surface mesh (fnpf_prism_laplace_solve, fnpf_prism_dtn,
+// fnpf_prism_rhs, fnpf_prism_rk4_step; Sec. 3.1.2, Sec. 3.4 Steps 4.1-4.6,
+// Sec. 3.2): the items of prism_step.h launched one thread per item on the
+// caller's stream, the CG loops driven from the host (one read of a scalar per
+// dot product).  The workspace and the surface tables (the incidence of the
+// triangle slots and the consistent surface mass in CSR form) are built at a
+// mesh's first call.
+#include <limits.h>
+#include <math.h>
+
+#include <string>
+#include <vector>
+
+#include "fnpf_internal.cuh"
+#include "prism.cuh"
+#include "prism_step.h"
+
+namespace fnpf {
+
+constexpr int kItemThreads = 256;
+
+template <class It>
+__global__ void __launch_bounds__(kItemThreads) pstep_kernel(int64_t n, typename It::Args a) {
+  const int64_t i = (int64_t)blockIdx.x * kItemThreads + threadIdx.x;
+  if (i < n) It::at(i, a);
+}
+
+namespace {
+
+struct DeviceEx {
+  cudaStream_t s;
+  template <class It>
+  int run(int64_t n, const typename It::Args& a) {
+    const int64_t blocks = (n + kItemThreads - 1) / kItemThreads;
+    if (blocks < 1 || blocks > INT_MAX) return 1;
+    pstep_kernel<It><<<(unsigned)blocks, kItemThreads, 0, s>>>(n, a);
+    return cudaPeekAtLastError() != cudaSuccess;
+  }
+  int get(double* dst, const double* src, int count) {
+    if (cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess) return 1;
+    return cudaStreamSynchronize(s) != cudaSuccess;
+  }
+};
+
+}  // namespace
+
+struct PrismStepState {
+  pstep::PMesh pm{};
+  pstep::PWork w{};
+  double* d_work = nullptr;
+  int64_t* d_soff = nullptr;
+  int64_t* d_sinc = nullptr;
+  int64_t* d_mrow = nullptr;
+  int* d_mcol = nullptr;
+  double* d_mval = nullptr;
+  double* d_mdiag = nullptr;
+};
+
+void prism_step_free(fnpf_prism* m) {
+  if (!m || !m->step) return;
+  PrismStepState* st = m->step;
+  cudaFree(st->d_work);
+  cudaFree(st->d_soff);
+  cudaFree(st->d_sinc);
+  cudaFree(st->d_mrow);
+  cudaFree(st->d_mcol);
+  cudaFree(st->d_mval);
+  cudaFree(st->d_mdiag);
+  delete st;
+  m->step = nullptr;
+}
+
+namespace {
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  cudaError_t e = cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, src.size()));
+  if (e == cudaSuccess && !src.empty()) e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// The step workspace of m (built at the first call; every later call reuses it).
+fnpf_status ensure_step(fnpf_prism* m) {
+  if (m->step) return FNPF_OK;
+  PrismStepState* st = new PrismStepState();
+  pstep::PMesh& pm = st->pm;
+  pm.p = m->p;
+  pm.n = m->n;
+  pm.nz = m->nz;
+  pm.nt = m->nt;
+  pm.nq = m->nq;
+  pm.ntri = m->ntri;
+  pm.ns = m->ns;
+  pm.nv = m->nv;
+  pm.N = m->N;
+  pm.NI = m->N - m->ns;
+  pm.nelem = (int64_t)m->ntri * m->nz;
+  pm.tn = m->d_tnodes;
+  pm.voff = m->d_off;
+  pm.vinc = m->d_inc;
+  // host copy of the packed tables the kernels read (geo, L, wq for the mass matrix)
+  const size_t ntab = 4 * (size_t)m->ntri + 3 * (size_t)m->nq * m->nt + m->nq + 2 * (size_t)m->n +
+                      (size_t)m->n * m->n;
+  std::vector<double> tab(ntab);
+  cudaError_t e = cudaMemcpy(tab.data(), m->d_tab, sizeof(double) * ntab, cudaMemcpyDeviceToHost);
+  pstep::PMesh hm = pm;
+  pstep::bind_tables(&hm, tab.data());
+  pstep::bind_tables(&pm, m->d_tab);
+  std::vector<int64_t> soff, sinc, mrow;
+  std::vector<int> mcol;
+  std::vector<double> mval, mdiag;
+  pstep::surface_incidence(m->tnodes.data(), m->ntri, m->nt, m->ns, &soff, &sinc);
+  pstep::surface_mass(hm, m->tnodes.data(), hm.geo, hm.L, hm.wq, &mrow, &mcol, &mval, &mdiag);
+  int64_t total = 0;
+  pstep::carve(pm, &st->w, [&](double** p, int64_t cnt) {
+    (void)p;
+    total += (cnt + 31) / 32 * 32;   // 256-byte aligned buffers
+  });
+  if (e == cudaSuccess) e = cudaMalloc(&st->d_work, sizeof(double) * total);
+  if (e == cudaSuccess) e = cudaMemset(st->d_work, 0, sizeof(double) * total);
+  if (e == cudaSuccess) e = upload(&st->d_soff, soff);
+  if (e == cudaSuccess) e = upload(&st->d_sinc, sinc);
+  if (e == cudaSuccess) e = upload(&st->d_mrow, mrow);
+  if (e == cudaSuccess) e = upload(&st->d_mcol, mcol);
+  if (e == cudaSuccess) e = upload(&st->d_mval, mval);
+  if (e == cudaSuccess) e = upload(&st->d_mdiag, mdiag);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    m->err = std::string("prism step set-up: ") + cudaGetErrorString(e);
+    m->step = st;
+    prism_step_free(m);
+    return e == cudaErrorMemoryAllocation ? FNPF_ENOMEM : FNPF_ECUDA;
+  }
+  int64_t off = 0;
+  pstep::carve(pm, &st->w, [&](double** p, int64_t cnt) {
+    *p = st->d_work + off;
+    off += (cnt + 31) / 32 * 32;
+  });
+  pm.soff = st->d_soff;
+  pm.sinc = st->d_sinc;
+  pm.mrow = st->d_mrow;
+  pm.mcol = st->d_mcol;
+  pm.mval = st->d_mval;
+  pm.mdiag = st->d_mdiag;
+  m->step = st;
+  return FNPF_OK;
+}
+
+fnpf_status check_opts(const fnpf_prism_opts* o, pstep::Params* p, std::string* why) {
+  fnpf_prism_opts d;
+  fnpf_prism_default_opts(&d);
+  if (!o) o = &d;
+  if (!(o->rtol > 0) || !(o->mass_rtol > 0) || o->max_iter < 0 || o->mass_max_iter < 0 || !isfinite(o->g) ||
+      (o->model != FNPF_NONLINEAR && o->model != FNPF_LINEAR)) {
+    *why = "bad options (rtol, mass_rtol > 0; iteration caps >= 0; finite g; model NONLINEAR or LINEAR)";
+    return FNPF_EINVAL;
+  }
+  *p = pstep::Params{o->rtol, o->max_iter, o->mass_rtol, o->mass_max_iter, o->g, o->model == FNPF_LINEAR};
+  return FNPF_OK;
+}
+
+// Runs f(stepper, params) after the common checks; records the message of a failure.
+template <class F>
+fnpf_status with_stepper(fnpf_prism* m, const fnpf_prism_opts* opts, void* stream, const char* what, F f) {
+  pstep::Params prm{};
+  std::string why;
+  fnpf_status st = check_opts(opts, &prm, &why);
+  if (st != FNPF_OK) {
+    m->err = std::string(what) + ": " + why;
+    return st;
+  }
+  if ((st = ensure_step(m)) != FNPF_OK) return st;
+  DeviceEx ex{(cudaStream_t)stream};
+  pstep::Stepper<DeviceEx> sp{m->step->pm, m->step->w, ex};
+  st = f(sp, prm);
+  if (st == FNPF_ECUDA) {
+    m->err = std::string(what) + ": " + cudaGetErrorString(cudaGetLastError());
+  } else if (st != FNPF_OK) {
+    m->err = std::string(what) + ": " + fnpf_status_string(st);
+  }
+  return st;
+}
+
+}  // namespace
+}  // namespace fnpf
+
+extern "C" {
+
+void fnpf_prism_default_opts(fnpf_prism_opts* o) {
+  if (!o) return;
+  o->rtol = 1e-10;
+  o->max_iter = 20000;
+  o->mass_rtol = 1e-13;
+  o->mass_max_iter = 5000;
+  o->g = 9.81;
+  o->model = FNPF_NONLINEAR;
+}
+
+fnpf_status fnpf_prism_diagonal(fnpf_prism* m, const double* eta, const double* h, double* diag, void* stream) {
+  if (!m || !eta || !h || !diag) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, nullptr, stream, "prism diagonal", [&](auto& sp, const fnpf::pstep::Params&) {
+    fnpf_status st = sp.geometry(eta, h);
+    if (st == FNPF_OK) st = sp.template go<fnpf::pstep::CopyItem>(m->N, {sp.w.diag, diag});
+    return st;
+  });
+}
+
+fnpf_status fnpf_prism_apply_stored(fnpf_prism* m, const double* eta, const double* h, const double* x, double* y,
+                                    void* stream) {
+  if (!m || !eta || !h || !x || !y) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, nullptr, stream, "prism stored apply", [&](auto& sp, const fnpf::pstep::Params&) {
+    fnpf_status st = sp.geometry(eta, h);
+    if (st == FNPF_OK) st = sp.apply(x, y);
+    return st;
+  });
+}
+
+fnpf_status fnpf_prism_laplace_solve(fnpf_prism* m, const fnpf_prism_opts* opts, const double* eta, const double* h,
+                                     const double* phis, double* phi, fnpf_solve_info* info, void* stream) {
+  if (!m || !eta || !h || !phis || !phi) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, opts, stream, "prism Laplace solve", [&](auto& sp, const fnpf::pstep::Params& p) {
+    return sp.solve(eta, h, phis, phi, p, info);
+  });
+}
+
+fnpf_status fnpf_prism_dtn(fnpf_prism* m, const fnpf_prism_opts* opts, const double* eta, const double* h,
+                           const double* phis, double* w, fnpf_solve_info* info, void* stream) {
+  if (!m || !eta || !h || !phis || !w) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, opts, stream, "prism DtN", [&](auto& sp, const fnpf::pstep::Params& p) {
+    return sp.dtn(eta, h, phis, w, p, info);
+  });
+}
+
+fnpf_status fnpf_prism_rhs(fnpf_prism* m, const fnpf_prism_opts* opts, const double* eta, const double* h,
+                           const double* phis, double* k_eta, double* k_phis, fnpf_solve_info* info, void* stream) {
+  if (!m || !eta || !h || !phis || !k_eta || !k_phis) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, opts, stream, "prism right-hand side", [&](auto& sp, const fnpf::pstep::Params& p) {
+    return sp.rhs(eta, h, phis, k_eta, k_phis, p, info);
+  });
+}
+
+fnpf_status fnpf_prism_rk4_step(fnpf_prism* m, const fnpf_prism_opts* opts, const double* h, double* eta,
+                                double* phis, double dt, fnpf_solve_info* info, void* stream) {
+  if (!m || !h || !eta || !phis || !isfinite(dt)) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, opts, stream, "prism RK4 step", [&](auto& sp, const fnpf::pstep::Params& p) {
+    return sp.rk4(h, eta, phis, dt, p, info);
+  });
+}
+
+}  // extern "C"

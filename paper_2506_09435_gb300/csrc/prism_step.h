@@ -1,0 +1,804 @@
+// The Laplace solve, the Dirichlet-to-Neumann map and the RK4 step on prisms
+// over an unstructured triangular surface mesh (the paper's own mesh, Sec.
+// 3.1.2), as one-thread-per-item kernels and the host orchestration that
+// launches them.
+//
+// Every kernel of this path is an item struct with a static function
+// at(i, args) that one thread runs for item i (no shared memory, no
+// synchronisation inside a launch, every output written by exactly one item),
+// so the same bodies run as CUDA kernels (prism_step.cu: one thread per item)
+// and, compiled as plain C++, one item after another.  Stepper<Ex> orders the
+// launches; Ex supplies run<Item>(n, args) and get(host, src, count), the
+// device-to-host read of the scalars the host-driven CG loops test.
+//
+// Per RK4 stage (Sec. 3.4, Steps 4.1-4.6; ERK4, Sec. 3.2):
+//   geometry  G = w_q w_k |det J| J^-1 J^-T at every quadrature point of every
+//             prism, from eta and h (z = -h + sigma (eta + h)), stored for the
+//             solve, and the Jacobi diagonal from it;
+//   lift      b = -A_IS phi_eta (the operator applied to the surface values);
+//   PCG       A_II phi_I = b with the Jacobi preconditioner (Eq. Laplace_weak:
+//             element fluxes G grad u at the points, transposed contractions to
+//             the local nodes, element results summed per node in a fixed order);
+//   w         d phi / dz = phi_t / z_t on the top layer's vertical GLL lines;
+//   conditions the kinematic and dynamic conditions (Sec. 2) at the triangle
+//             quadrature points, projected onto the nodal surface space with the
+//             consistent mass, M k = int f l_i dA (Eq. free_surface_weak; the
+//             mass solve by Jacobi-PCG on the assembled CSR matrix);
+//   RK4       the classical stage states and combination.
+// Node and quadrature conventions are those of prism.cu (fnpf_prism_*).
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <utility>
+#include <vector>
+
+#include "fnpf.h"
+
+#if defined(__CUDACC__)
+#define FNPF_HD __host__ __device__
+#else
+#define FNPF_HD
+#endif
+
+namespace fnpf {
+namespace pstep {
+
+constexpr int kChunk = 256;   // entries per partial sum of a dot product
+
+// The mesh as the items read it (device pointers on the GPU).
+struct PMesh {
+  int p, n, nz, nt, nq, ntri;
+  int64_t ns, nv, N, NI, nelem;
+  const int* tn;                        // [ntri][nt] surface node of each local triangle node
+  const double* geo;                    // [ntri][4] x_r, x_s, y_r, y_s
+  const double *L, *Lr, *Ls;            // [nq][nt] nodal basis and its r, s derivatives
+  const double* wq;                     // [nq] triangle quadrature weights
+  const double *xi, *wv, *D;            // [n], [n], [n][n] GLL nodes, weights, D[k][m] = l'_m(xi_k)
+  const int64_t *voff, *vinc;           // volume node g: element results vinc[voff[g] .. voff[g+1])
+  const int64_t *soff, *sinc;           // surface node c: (triangle, local node) slots t nt + c'
+  const int64_t* mrow;                  // consistent surface mass, CSR [ns + 1]
+  const int* mcol;
+  const double* mval;
+  const double* mdiag;                  // [ns] its diagonal
+};
+
+// Points the table pointers of m into the packed tables of fnpf_prism_create:
+// geo [4 ntri], L, Lr, Ls [nq nt], wq [nq], xi [n], wv [n], D [n n].
+inline void bind_tables(PMesh* m, const double* tab) {
+  m->geo = tab;
+  m->L = m->geo + 4 * (int64_t)m->ntri;
+  m->Lr = m->L + (int64_t)m->nq * m->nt;
+  m->Ls = m->Lr + (int64_t)m->nq * m->nt;
+  m->wq = m->Ls + (int64_t)m->nq * m->nt;
+  m->xi = m->wq + m->nq;
+  m->wv = m->xi + m->n;
+  m->D = m->wv + m->n;
+}
+
+// Workspace of the path.
+struct PWork {
+  double *G, *F, *ye, *diag;            // [nelem n nq 6], [nelem n nq 3], [nelem nt n], [N]
+  double *xs, *r, *z, *pd, *q;          // Laplace PCG [N]
+  double *part, *scal;                  // dot-product partials, scalars
+  double *phi, *w;                      // the mesh's potential [N] (warm start), w [ns]
+  double *fq, *se, *be, *bp;            // [ntri nq 2], [ntri nt 2], [ns], [ns]
+  double *mr, *mz, *mp, *mq;            // surface-mass CG [ns]
+  double *ke, *kp, *es, *ps, *ae, *ap;  // RK4 stage right-hand side, stage state, accumulator [ns]
+  double* zero;                         // [ns] zeros (still-water geometry of the linear model)
+};
+
+inline int64_t dot_partials(int64_t n) { return (n + kChunk - 1) / kChunk; }
+
+// Carves the workspace: take(&ptr, count) is called for every buffer in a
+// fixed order (the caller allocates, or only counts).
+template <class Take>
+void carve(const PMesh& m, PWork* w, Take take) {
+  const int64_t pts = m.nelem * m.n * m.nq;
+  take(&w->G, pts * 6);
+  take(&w->F, pts * 3);
+  take(&w->ye, m.nelem * m.nt * m.n);
+  take(&w->diag, m.N);
+  take(&w->xs, m.N);
+  take(&w->r, m.N);
+  take(&w->z, m.N);
+  take(&w->pd, m.N);
+  take(&w->q, m.N);
+  take(&w->part, dot_partials(std::max<int64_t>(m.N, m.ns)));
+  take(&w->scal, 4);
+  take(&w->phi, m.N);
+  take(&w->w, m.ns);
+  take(&w->fq, (int64_t)m.ntri * m.nq * 2);
+  take(&w->se, (int64_t)m.ntri * m.nt * 2);
+  double** surf[] = {&w->be, &w->bp, &w->mr, &w->mz, &w->mp, &w->mq, &w->ke,
+                     &w->kp, &w->es, &w->ps, &w->ae, &w->ap, &w->zero};
+  for (double** s : surf) take(s, m.ns);
+}
+
+// ---------------------------------------------------------------------------
+// Host set-up: the surface incidence and the consistent surface mass.
+
+// Surface node c -> its (triangle, local node) slots t nt + c', in slot order.
+inline void surface_incidence(const int* tn, int ntri, int nt, int64_t ns, std::vector<int64_t>* off,
+                              std::vector<int64_t>* inc) {
+  off->assign(ns + 1, 0);
+  for (int64_t s = 0; s < (int64_t)ntri * nt; ++s) ++(*off)[tn[s] + 1];
+  for (int64_t c = 0; c < ns; ++c) (*off)[c + 1] += (*off)[c];
+  inc->assign((size_t)ntri * nt, 0);
+  std::vector<int64_t> fill(off->begin(), off->end() - 1);
+  for (int64_t s = 0; s < (int64_t)ntri * nt; ++s) (*inc)[fill[tn[s]]++] = s;
+}
+
+// M_ij = int l_i l_j dA (the triangle rule, exact for the degree-2p products),
+// assembled row by row with the columns ascending; equal columns summed in
+// triangle order.
+inline void surface_mass(const PMesh& m, const int* tn, const double* geo, const double* L, const double* wq,
+                         std::vector<int64_t>* row, std::vector<int>* col, std::vector<double>* val,
+                         std::vector<double>* diag) {
+  const int nt = m.nt, nq = m.nq;
+  std::vector<std::vector<std::pair<int, double>>> rows(m.ns);
+  std::vector<double> Me((size_t)nt * nt);
+  for (int t = 0; t < m.ntri; ++t) {
+    const double* gt = geo + 4 * (int64_t)t;
+    const double det = fabs(gt[0] * gt[3] - gt[1] * gt[2]);
+    for (int a = 0; a < nt; ++a)
+      for (int b = 0; b < nt; ++b) {
+        double s = 0;
+        for (int q = 0; q < nq; ++q) s += wq[q] * L[(int64_t)q * nt + a] * L[(int64_t)q * nt + b];
+        Me[(size_t)a * nt + b] = s * det;
+      }
+    const int* tt = tn + (int64_t)t * nt;
+    for (int a = 0; a < nt; ++a)
+      for (int b = 0; b < nt; ++b) rows[tt[a]].push_back({tt[b], Me[(size_t)a * nt + b]});
+  }
+  row->assign(m.ns + 1, 0);
+  col->clear();
+  val->clear();
+  diag->assign(m.ns, 0.0);
+  for (int64_t i = 0; i < m.ns; ++i) {
+    auto& r = rows[i];
+    std::stable_sort(r.begin(), r.end(), [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+      return x.first < y.first;
+    });
+    for (size_t j = 0; j < r.size();) {
+      const int c = r[j].first;
+      double s = 0;
+      for (; j < r.size() && r[j].first == c; ++j) s += r[j].second;
+      col->push_back(c);
+      val->push_back(s);
+      if (c == i) (*diag)[i] = s;
+    }
+    (*row)[i + 1] = (int64_t)col->size();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Items.
+
+// Prism point (elem, k, q) of item i over nelem n nq; elem = triangle nz + layer.
+struct PointIdx {
+  int64_t elem;
+  int e, l, k, q;
+};
+FNPF_HD inline PointIdx point_of(const PMesh& m, int64_t i) {
+  PointIdx r;
+  const int64_t per = (int64_t)m.n * m.nq;
+  r.elem = i / per;
+  const int pt = (int)(i - r.elem * per);
+  r.k = pt / m.nq;
+  r.q = pt - r.k * m.nq;
+  r.e = (int)(r.elem / m.nz);
+  r.l = (int)(r.elem - (int64_t)r.e * m.nz);
+  return r;
+}
+
+// G = w_q w_k |det J| J^-1 J^-T (6 entries: 00 01 02 11 12 22) at every point;
+// J = [[x_r, x_s, 0], [y_r, y_s, 0], [z_r, z_s, z_t]] with z from eta and h in
+// the triangle's nodal basis.
+struct GeomItem {
+  struct Args {
+    PMesh m;
+    const double *eta, *h;
+    double* G;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const PointIdx pi = point_of(m, i);
+    const int nt = m.nt;
+    const int* tn = m.tn + (int64_t)pi.e * nt;
+    const double* Lq = m.L + (int64_t)pi.q * nt;
+    const double* Lrq = m.Lr + (int64_t)pi.q * nt;
+    const double* Lsq = m.Ls + (int64_t)pi.q * nt;
+    double ev = 0, er = 0, es = 0, hv = 0, hr = 0, hs = 0;
+    for (int c = 0; c < nt; ++c) {
+      const double E = a.eta[tn[c]], H = a.h[tn[c]];
+      ev += Lq[c] * E;
+      er += Lrq[c] * E;
+      es += Lsq[c] * E;
+      hv += Lq[c] * H;
+      hr += Lrq[c] * H;
+      hs += Lsq[c] * H;
+    }
+    const double* gt = m.geo + 4 * (int64_t)pi.e;
+    const double xr = gt[0], xs = gt[1], yr = gt[2], ys = gt[3];
+    const double det2 = xr * ys - xs * yr;
+    const double sig = (pi.l + 0.5 * (1.0 + m.xi[pi.k])) / m.nz;
+    const double zr = -hr + sig * (er + hr), zs = -hs + sig * (es + hs), zt = (ev + hv) / (2.0 * m.nz);
+    const double det = det2 * zt;
+    // J^-1 by cofactors; its third column is (0, 0, det2 / det)
+    const double i00 = ys * zt / det, i01 = -xs * zt / det;
+    const double i10 = -yr * zt / det, i11 = xr * zt / det;
+    const double i20 = (yr * zs - ys * zr) / det, i21 = (xs * zr - xr * zs) / det, i22 = det2 / det;
+    const double wt = m.wq[pi.q] * m.wv[pi.k] * fabs(det);
+    double* G = a.G + 6 * i;
+    G[0] = wt * (i00 * i00 + i01 * i01);
+    G[1] = wt * (i00 * i10 + i01 * i11);
+    G[2] = wt * (i00 * i20 + i01 * i21);
+    G[3] = wt * (i10 * i10 + i11 * i11);
+    G[4] = wt * (i10 * i20 + i11 * i21);
+    G[5] = wt * (i20 * i20 + i21 * i21 + i22 * i22);
+  }
+};
+
+// Flux G grad_ref u at every point (u the volume field x).
+struct FluxItem {
+  struct Args {
+    PMesh m;
+    const double* G;
+    const double* x;
+    double* F;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const PointIdx pi = point_of(m, i);
+    const int nt = m.nt, n = m.n;
+    const int* tn = m.tn + (int64_t)pi.e * nt;
+    const double* Lq = m.L + (int64_t)pi.q * nt;
+    const double* Lrq = m.Lr + (int64_t)pi.q * nt;
+    const double* Lsq = m.Ls + (int64_t)pi.q * nt;
+    const double* Dk = m.D + (int64_t)pi.k * n;
+    const int64_t plane0 = (int64_t)pi.l * m.p;
+    double ur = 0, us = 0, ut = 0;
+    for (int c = 0; c < nt; ++c) {
+      const int64_t col = tn[c];
+      const double u = a.x[(plane0 + pi.k) * m.ns + col];
+      ur += Lrq[c] * u;
+      us += Lsq[c] * u;
+      double uc = 0;
+      for (int mm = 0; mm < n; ++mm) uc += Dk[mm] * a.x[(plane0 + mm) * m.ns + col];
+      ut += Lq[c] * uc;
+    }
+    const double* G = a.G + 6 * i;
+    double* F = a.F + 3 * i;
+    F[0] = G[0] * ur + G[1] * us + G[2] * ut;
+    F[1] = G[1] * ur + G[3] * us + G[4] * ut;
+    F[2] = G[2] * ur + G[4] * us + G[5] * ut;
+  }
+};
+
+// Local node (elem, mm, c) of item i over nelem nt n; slot = mm nt + c.
+struct NodeIdx {
+  int64_t elem, base;   // base: the element's first point
+  int mm, c;
+};
+FNPF_HD inline NodeIdx node_of(const PMesh& m, int64_t i) {
+  NodeIdx r;
+  const int64_t per = (int64_t)m.nt * m.n;
+  r.elem = i / per;
+  const int idx = (int)(i - r.elem * per);
+  r.c = idx % m.nt;
+  r.mm = idx / m.nt;
+  r.base = r.elem * m.n * m.nq;
+  return r;
+}
+
+// Element result at local node (c, mm): the transposed contractions of the
+// fluxes with the basis gradients, sum over the points (q, k) of
+// (delta_k,mm L_r[q][c], delta_k,mm L_s[q][c], L[q][c] D[k][mm]) . F(q, k).
+struct NodeItem {
+  struct Args {
+    PMesh m;
+    const double* F;
+    double* ye;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const NodeIdx ni = node_of(m, i);
+    const int nt = m.nt, nq = m.nq, n = m.n;
+    const double* Fm = a.F + 3 * (ni.base + (int64_t)ni.mm * nq);
+    double y = 0;
+    for (int q = 0; q < nq; ++q) y += m.Lr[(int64_t)q * nt + ni.c] * Fm[3 * q] + m.Ls[(int64_t)q * nt + ni.c] * Fm[3 * q + 1];
+    for (int k = 0; k < n; ++k) {
+      const double* Fk = a.F + 3 * (ni.base + (int64_t)k * nq);
+      double s = 0;
+      for (int q = 0; q < nq; ++q) s += m.L[(int64_t)q * nt + ni.c] * Fk[3 * q + 2];
+      y += m.D[(int64_t)k * n + ni.mm] * s;
+    }
+    a.ye[i] = y;
+  }
+};
+
+// Element diagonal at local node (c, mm): sum over the points of g^T G g with g
+// the reference gradient of that node's basis function.
+struct DiagItem {
+  struct Args {
+    PMesh m;
+    const double* G;
+    double* ye;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const NodeIdx ni = node_of(m, i);
+    const int nt = m.nt, nq = m.nq, n = m.n;
+    double d = 0;
+    for (int k = 0; k < n; ++k) {
+      const double dkm = m.D[(int64_t)k * n + ni.mm];
+      for (int q = 0; q < nq; ++q) {
+        const double* G = a.G + 6 * (ni.base + (int64_t)k * nq + q);
+        const double a0 = k == ni.mm ? m.Lr[(int64_t)q * nt + ni.c] : 0.0;
+        const double a1 = k == ni.mm ? m.Ls[(int64_t)q * nt + ni.c] : 0.0;
+        const double a2 = m.L[(int64_t)q * nt + ni.c] * dkm;
+        d += a0 * (G[0] * a0 + G[1] * a1 + G[2] * a2) + a1 * (G[1] * a0 + G[3] * a1 + G[4] * a2) +
+             a2 * (G[2] * a0 + G[4] * a1 + G[5] * a2);
+      }
+    }
+    a.ye[i] = d;
+  }
+};
+
+// y_g = sum of the element results of node g, in incidence order.
+struct GatherItem {
+  struct Args {
+    const int64_t *off, *inc;
+    const double* ye;
+    double* y;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    double s = 0;
+    for (int64_t j = a.off[i]; j < a.off[i + 1]; ++j) s += a.ye[a.inc[j]];
+    a.y[i] = s;
+  }
+};
+
+// x = [0 (interior); phis (surface plane)] over N.
+struct SurfaceOnlyItem {
+  struct Args {
+    int64_t NI;
+    const double* phis;
+    double* x;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.x[i] = i >= a.NI ? a.phis[i - a.NI] : 0.0; }
+};
+
+// out = [s src (interior); 0 (surface plane)] over N.
+struct InteriorItem {
+  struct Args {
+    int64_t NI;
+    double s;
+    const double* src;
+    double* out;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.out[i] = i < a.NI ? a.s * a.src[i] : 0.0; }
+};
+
+struct AxpyItem {   // y += s x
+  struct Args {
+    double s;
+    const double* x;
+    double* y;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.y[i] += a.s * a.x[i]; }
+};
+
+struct XpbyItem {   // y = x + s y
+  struct Args {
+    const double* x;
+    double s;
+    double* y;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.y[i] = a.x[i] + a.s * a.y[i]; }
+};
+
+struct LinItem {   // out = x + s y
+  struct Args {
+    const double* x;
+    double s;
+    const double* y;
+    double* out;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.out[i] = a.x[i] + a.s * a.y[i]; }
+};
+
+struct DivItem {   // out = x / d (the Jacobi preconditioner)
+  struct Args {
+    const double *x, *d;
+    double* out;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.out[i] = a.x[i] / a.d[i]; }
+};
+
+struct CopyItem {
+  struct Args {
+    const double* src;
+    double* dst;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.dst[i] = a.src[i]; }
+};
+
+struct FillItem {
+  struct Args {
+    double v;
+    double* dst;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.dst[i] = a.v; }
+};
+
+// part[i] = sum of x_j y_j over the i-th chunk of kChunk entries (fixed order).
+struct DotPartItem {
+  struct Args {
+    const double *x, *y;
+    int64_t n;
+    double* part;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const int64_t lo = i * kChunk, hi = lo + kChunk < a.n ? lo + kChunk : a.n;
+    double s = 0;
+    for (int64_t j = lo; j < hi; ++j) s += a.x[j] * a.y[j];
+    a.part[i] = s;
+  }
+};
+
+// out[0] = sum of the partials (one item).
+struct SumItem {
+  struct Args {
+    const double* part;
+    int64_t np;
+    double* out;
+  };
+  FNPF_HD static void at(int64_t, const Args& a) {
+    double s = 0;
+    for (int64_t j = 0; j < a.np; ++j) s += a.part[j];
+    a.out[0] = s;
+  }
+};
+
+// y = M x, M in CSR (rows in order, the stored column order).
+struct CsrItem {
+  struct Args {
+    const int64_t* row;
+    const int* col;
+    const double* val;
+    const double* x;
+    double* y;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    double s = 0;
+    for (int64_t j = a.row[i]; j < a.row[i + 1]; ++j) s += a.val[j] * a.x[a.col[j]];
+    a.y[i] = s;
+  }
+};
+
+// w = d phi / dz at surface node c: (sum_j D[p][j] phi(plane N_v - 1 - p + j)) 2 N_z / (eta + h).
+struct WItem {
+  struct Args {
+    PMesh m;
+    const double *eta, *h, *phi;
+    double* w;
+  };
+  FNPF_HD static void at(int64_t c, const Args& a) {
+    const PMesh& m = a.m;
+    const double* Dp = m.D + (int64_t)m.p * m.n;
+    const int64_t top = m.nv - 1 - m.p;
+    double s = 0;
+    for (int j = 0; j < m.n; ++j) s += Dp[j] * a.phi[(top + j) * m.ns + c];
+    a.w[c] = s * 2.0 * m.nz / (a.eta[c] + a.h[c]);
+  }
+};
+
+// The conditions at triangle quadrature point (t, q), times the rule's weight
+// and |det J_2|:
+//   f_eta = -grad eta . grad phi_eta + w (1 + |grad eta|^2)
+//   f_phi = -g eta - |grad phi_eta|^2 / 2 + w^2 (1 + |grad eta|^2) / 2
+// (linear: f_eta = w, f_phi = -g eta); grad = J_2^-T grad_ref.
+struct SurfQItem {
+  struct Args {
+    PMesh m;
+    const double *eta, *phis, *w;
+    double g;
+    int linear;
+    double* fq;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int nt = m.nt;
+    const int t = (int)(i / m.nq), q = (int)(i - (int64_t)t * m.nq);
+    const int* tn = m.tn + (int64_t)t * nt;
+    const double* Lq = m.L + (int64_t)q * nt;
+    const double* Lrq = m.Lr + (int64_t)q * nt;
+    const double* Lsq = m.Ls + (int64_t)q * nt;
+    double ev = 0, er = 0, es = 0, pr = 0, ps = 0, wv = 0;
+    for (int c = 0; c < nt; ++c) {
+      const int64_t g = tn[c];
+      const double E = a.eta[g], P = a.phis[g];
+      ev += Lq[c] * E;
+      er += Lrq[c] * E;
+      es += Lsq[c] * E;
+      pr += Lrq[c] * P;
+      ps += Lsq[c] * P;
+      wv += Lq[c] * a.w[g];
+    }
+    const double* gt = m.geo + 4 * (int64_t)t;
+    const double xr = gt[0], xs = gt[1], yr = gt[2], ys = gt[3];
+    const double det = xr * ys - xs * yr;
+    double fe, fp;
+    if (a.linear) {
+      fe = wv;
+      fp = -a.g * ev;
+    } else {
+      const double ex = (ys * er - yr * es) / det, ey = (xr * es - xs * er) / det;
+      const double px = (ys * pr - yr * ps) / det, py = (xr * ps - xs * pr) / det;
+      const double q2 = 1.0 + ex * ex + ey * ey;
+      fe = -(ex * px + ey * py) + wv * q2;
+      fp = -a.g * ev - 0.5 * (px * px + py * py) + 0.5 * wv * wv * q2;
+    }
+    const double wt = m.wq[q] * fabs(det);
+    a.fq[2 * i] = wt * fe;
+    a.fq[2 * i + 1] = wt * fp;
+  }
+};
+
+// Triangle slot (t, c): sum over the points of L[q][c] times the weighted conditions.
+struct SurfNodeItem {
+  struct Args {
+    PMesh m;
+    const double* fq;
+    double* se;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int t = (int)(i / m.nt), c = (int)(i - (int64_t)t * m.nt);
+    const double* f = a.fq + 2 * (int64_t)t * m.nq;
+    double se = 0, sp = 0;
+    for (int q = 0; q < m.nq; ++q) {
+      const double l = m.L[(int64_t)q * m.nt + c];
+      se += l * f[2 * q];
+      sp += l * f[2 * q + 1];
+    }
+    a.se[2 * i] = se;
+    a.se[2 * i + 1] = sp;
+  }
+};
+
+// Right-hand sides of the mass solves at surface node c: its slots summed in order.
+struct SurfGatherItem {
+  struct Args {
+    const int64_t *off, *inc;
+    const double* se;
+    double *be, *bp;
+  };
+  FNPF_HD static void at(int64_t c, const Args& a) {
+    double se = 0, sp = 0;
+    for (int64_t j = a.off[c]; j < a.off[c + 1]; ++j) {
+      se += a.se[2 * a.inc[j]];
+      sp += a.se[2 * a.inc[j] + 1];
+    }
+    a.be[c] = se;
+    a.bp[c] = sp;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Orchestration.
+
+struct Params {
+  double rtol;
+  int max_iter;
+  double mass_rtol;
+  int mass_max_iter;
+  double g;
+  int linear;
+};
+
+#define FNPF_PS_TRY(x)                   \
+  do {                                   \
+    const fnpf_status st_ = (x);         \
+    if (st_ != FNPF_OK) return st_;      \
+  } while (0)
+
+template <class Ex>
+struct Stepper {
+  const PMesh& m;
+  const PWork& w;
+  Ex& ex;
+
+  template <class It>
+  fnpf_status go(int64_t n, const typename It::Args& a) {
+    if (n <= 0) return FNPF_OK;
+    return ex.template run<It>(n, a) ? FNPF_ECUDA : FNPF_OK;
+  }
+
+  // *out = x . y over n entries (two launches and a read of the scalar).
+  fnpf_status dot(const double* x, const double* y, int64_t n, double* out) {
+    if (n <= 0) {
+      *out = 0;
+      return FNPF_OK;
+    }
+    const int64_t np = dot_partials(n);
+    FNPF_PS_TRY(go<DotPartItem>(np, {x, y, n, w.part}));
+    FNPF_PS_TRY(go<SumItem>(1, {w.part, np, w.scal}));
+    return ex.get(out, w.scal, 1) ? FNPF_ECUDA : FNPF_OK;
+  }
+
+  // G and the Jacobi diagonal for the geometry of (eta, h).
+  fnpf_status geometry(const double* eta, const double* h) {
+    FNPF_PS_TRY(go<GeomItem>(m.nelem * m.n * m.nq, {m, eta, h, w.G}));
+    FNPF_PS_TRY(go<DiagItem>(m.nelem * m.nt * m.n, {m, w.G, w.ye}));
+    return go<GatherItem>(m.N, {m.voff, m.vinc, w.ye, w.diag});
+  }
+
+  // y = A x with the stored G (the full operator, surface rows included).
+  fnpf_status apply(const double* x, double* y) {
+    FNPF_PS_TRY(go<FluxItem>(m.nelem * m.n * m.nq, {m, w.G, x, w.F}));
+    FNPF_PS_TRY(go<NodeItem>(m.nelem * m.nt * m.n, {m, w.F, w.ye}));
+    return go<GatherItem>(m.N, {m.voff, m.vinc, w.ye, y});
+  }
+
+  // phi = the solution of A_II phi_I = -A_IS phis (in: the interior guess),
+  // phi = phis on the surface plane; Jacobi-PCG to ||r|| <= rtol ||b||.
+  fnpf_status solve(const double* eta, const double* h, const double* phis, double* phi, const Params& o,
+                    fnpf_solve_info* info) {
+    const int64_t N = m.N, NI = m.NI;
+    if (info) *info = fnpf_solve_info{0, 0, 0.0, FNPF_OK, 0.0f};
+    FNPF_PS_TRY(geometry(eta, h));
+    FNPF_PS_TRY(go<SurfaceOnlyItem>(N, {NI, phis, w.xs}));
+    FNPF_PS_TRY(apply(w.xs, w.q));
+    FNPF_PS_TRY(go<InteriorItem>(N, {NI, -1.0, w.q, w.r}));   // r = b = -A_IS phis
+    double bb = 0;
+    FNPF_PS_TRY(dot(w.r, w.r, NI, &bb));
+    fnpf_status st = FNPF_OK;
+    int it = 0;
+    double rr = 0;
+    if (!(bb > 0)) {   // b = 0: the solution is zero
+      if (!(bb == 0)) st = FNPF_EDIVERGED;
+      FNPF_PS_TRY(go<FillItem>(NI, {0.0, phi}));
+    } else {
+      const double stop = o.rtol * sqrt(bb);
+      FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, phi, w.pd}));   // the guess, surface plane zero
+      FNPF_PS_TRY(apply(w.pd, w.q));
+      FNPF_PS_TRY(go<AxpyItem>(NI, {-1.0, w.q, w.r}));          // r = b - A_II x0
+      FNPF_PS_TRY(dot(w.r, w.r, NI, &rr));
+      if (sqrt(rr) > stop) {
+        FNPF_PS_TRY(go<DivItem>(NI, {w.r, w.diag, w.z}));
+        FNPF_PS_TRY(go<CopyItem>(NI, {w.z, w.pd}));
+        double rz = 0;
+        FNPF_PS_TRY(dot(w.r, w.z, NI, &rz));
+        st = FNPF_ENOCONV;
+        while (it < o.max_iter) {
+          FNPF_PS_TRY(apply(w.pd, w.q));
+          double pq = 0;
+          FNPF_PS_TRY(dot(w.pd, w.q, NI, &pq));
+          if (!(pq > 0)) {
+            st = isfinite(pq) ? FNPF_EBREAKDOWN : FNPF_EDIVERGED;
+            break;
+          }
+          const double alpha = rz / pq;
+          FNPF_PS_TRY(go<AxpyItem>(NI, {alpha, w.pd, phi}));
+          FNPF_PS_TRY(go<AxpyItem>(NI, {-alpha, w.q, w.r}));
+          ++it;
+          FNPF_PS_TRY(dot(w.r, w.r, NI, &rr));
+          if (!isfinite(rr)) {
+            st = FNPF_EDIVERGED;
+            break;
+          }
+          if (sqrt(rr) <= stop) {
+            st = FNPF_OK;
+            break;
+          }
+          FNPF_PS_TRY(go<DivItem>(NI, {w.r, w.diag, w.z}));
+          double rzn = 0;
+          FNPF_PS_TRY(dot(w.r, w.z, NI, &rzn));
+          const double beta = rzn / rz;
+          rz = rzn;
+          FNPF_PS_TRY(go<XpbyItem>(NI, {w.z, beta, w.pd}));
+        }
+      }
+    }
+    FNPF_PS_TRY(go<CopyItem>(m.ns, {phis, phi + NI}));
+    if (info) {
+      info->iters = it;
+      info->rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
+      info->status = st;
+    }
+    return st;
+  }
+
+  // x = M^-1 b on the surface (Jacobi-PCG on the consistent mass from x = 0).
+  fnpf_status mass_solve(const double* b, double* x, const Params& o) {
+    const int64_t ns = m.ns;
+    FNPF_PS_TRY(go<FillItem>(ns, {0.0, x}));
+    double bb = 0;
+    FNPF_PS_TRY(dot(b, b, ns, &bb));
+    if (!(bb > 0)) return bb == 0 ? FNPF_OK : FNPF_EDIVERGED;
+    const double stop = o.mass_rtol * sqrt(bb);
+    FNPF_PS_TRY(go<CopyItem>(ns, {b, w.mr}));
+    FNPF_PS_TRY(go<DivItem>(ns, {w.mr, m.mdiag, w.mz}));
+    FNPF_PS_TRY(go<CopyItem>(ns, {w.mz, w.mp}));
+    double rz = 0;
+    FNPF_PS_TRY(dot(w.mr, w.mz, ns, &rz));
+    for (int it = 0; it < o.mass_max_iter; ++it) {
+      FNPF_PS_TRY(go<CsrItem>(ns, {m.mrow, m.mcol, m.mval, w.mp, w.mq}));
+      double pq = 0;
+      FNPF_PS_TRY(dot(w.mp, w.mq, ns, &pq));
+      if (!(pq > 0)) return isfinite(pq) ? FNPF_EBREAKDOWN : FNPF_EDIVERGED;
+      const double alpha = rz / pq;
+      FNPF_PS_TRY(go<AxpyItem>(ns, {alpha, w.mp, x}));
+      FNPF_PS_TRY(go<AxpyItem>(ns, {-alpha, w.mq, w.mr}));
+      double rr = 0;
+      FNPF_PS_TRY(dot(w.mr, w.mr, ns, &rr));
+      if (!isfinite(rr)) return FNPF_EDIVERGED;
+      if (sqrt(rr) <= stop) return FNPF_OK;
+      FNPF_PS_TRY(go<DivItem>(ns, {w.mr, m.mdiag, w.mz}));
+      double rzn = 0;
+      FNPF_PS_TRY(dot(w.mr, w.mz, ns, &rzn));
+      const double beta = rzn / rz;
+      rz = rzn;
+      FNPF_PS_TRY(go<XpbyItem>(ns, {w.mz, beta, w.mp}));
+    }
+    return FNPF_ENOCONV;
+  }
+
+  // w [ns] at (eta, phis): the solve (warm-started from the mesh's potential) and w.
+  fnpf_status dtn(const double* eta, const double* h, const double* phis, double* wout, const Params& o,
+                  fnpf_solve_info* info) {
+    FNPF_PS_TRY(solve(eta, h, phis, w.phi, o, info));
+    return go<WItem>(m.ns, {m, eta, h, w.phi, wout});
+  }
+
+  // (k_eta, k_phi) = the projected free-surface conditions at (eta, phis)
+  // (linear: the solve and w on the still-water geometry).
+  fnpf_status rhs(const double* eta, const double* h, const double* phis, double* ke, double* kp, const Params& o,
+                  fnpf_solve_info* info) {
+    const double* geo = o.linear ? w.zero : eta;
+    FNPF_PS_TRY(dtn(geo, h, phis, w.w, o, info));
+    FNPF_PS_TRY(go<SurfQItem>((int64_t)m.ntri * m.nq, {m, eta, phis, w.w, o.g, o.linear, w.fq}));
+    FNPF_PS_TRY(go<SurfNodeItem>((int64_t)m.ntri * m.nt, {m, w.fq, w.se}));
+    FNPF_PS_TRY(go<SurfGatherItem>(m.ns, {m.soff, m.sinc, w.se, w.be, w.bp}));
+    FNPF_PS_TRY(mass_solve(w.be, ke, o));
+    return mass_solve(w.bp, kp, o);
+  }
+
+  // One classical RK4 step of (eta, phis) in place; info: NULL or [4].
+  fnpf_status rk4(const double* h, double* eta, double* phis, double dt, const Params& o, fnpf_solve_info* info) {
+    const int64_t ns = m.ns;
+    for (int s = 0; s < 4; ++s) {
+      const double* E = eta;
+      const double* P = phis;
+      if (s > 0) {
+        const double c = (s == 3 ? 1.0 : 0.5) * dt;
+        FNPF_PS_TRY(go<LinItem>(ns, {eta, c, w.ke, w.es}));
+        FNPF_PS_TRY(go<LinItem>(ns, {phis, c, w.kp, w.ps}));
+        E = w.es;
+        P = w.ps;
+      }
+      FNPF_PS_TRY(rhs(E, h, P, w.ke, w.kp, o, info ? info + s : nullptr));
+      if (s == 0) {
+        FNPF_PS_TRY(go<CopyItem>(ns, {w.ke, w.ae}));
+        FNPF_PS_TRY(go<CopyItem>(ns, {w.kp, w.ap}));
+      } else {
+        const double wgt = s == 3 ? 1.0 : 2.0;
+        FNPF_PS_TRY(go<AxpyItem>(ns, {wgt, w.ke, w.ae}));
+        FNPF_PS_TRY(go<AxpyItem>(ns, {wgt, w.kp, w.ap}));
+      }
+    }
+    FNPF_PS_TRY(go<AxpyItem>(ns, {dt / 6.0, w.ae, eta}));
+    return go<AxpyItem>(ns, {dt / 6.0, w.ap, phis});
+  }
+};
+
+#undef FNPF_PS_TRY
+
+}  // namespace pstep
+}  // namespace fnpf

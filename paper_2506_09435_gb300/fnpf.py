@@ -43,6 +43,11 @@ class Opts(ctypes.Structure):
                 ("model", ctypes.c_int), ("mg_schedule", ctypes.c_int), ("projection", ctypes.c_int)]
 
 
+class PrismOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mass_rtol", ctypes.c_double),
+                ("mass_max_iter", ctypes.c_int), ("g", ctypes.c_double), ("model", ctypes.c_int)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("status", ctypes.c_int), ("ms", ctypes.c_float)]
@@ -105,6 +110,13 @@ def load():
         "fnpf_prism_create": [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
         "fnpf_prism_sizes": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
         "fnpf_prism_apply": [vp, vp, vp, vp, vp, vp],
+        "fnpf_prism_diagonal": [vp, vp, vp, vp, vp],
+        "fnpf_prism_apply_stored": [vp, vp, vp, vp, vp, vp],
+        "fnpf_prism_laplace_solve": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
+        "fnpf_prism_dtn": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
+        "fnpf_prism_rhs": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
+        "fnpf_prism_rk4_step": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, ctypes.c_double,
+                                ctypes.POINTER(SolveInfo), vp],
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
@@ -130,6 +142,8 @@ def load():
     lib.fnpf_ensemble_last_error.restype = ctypes.c_char_p
     lib.fnpf_prism_destroy.argtypes = [vp]
     lib.fnpf_prism_destroy.restype = None
+    lib.fnpf_prism_default_opts.argtypes = [ctypes.POINTER(PrismOpts)]
+    lib.fnpf_prism_default_opts.restype = None
     lib.fnpf_prism_last_error.argtypes = [vp]
     lib.fnpf_prism_last_error.restype = ctypes.c_char_p
     lib.fnpf_status_string.argtypes = [ctypes.c_int]
@@ -589,3 +603,63 @@ class PrismMesh:
         st = _LIB.fnpf_prism_apply(self._h, *ptrs, _stream(stream))
         if st != FNPF_OK:
             raise FnpfError(st, _LIB.fnpf_prism_last_error(self._h).decode())
+
+    @staticmethod
+    def default_opts(**kw):
+        """fnpf_prism_opts with the library's defaults, fields overridden by kw."""
+        o = PrismOpts()
+        _LIB.fnpf_prism_default_opts(ctypes.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def _check(self, st, infos=None):
+        if st != FNPF_OK:
+            raise FnpfError(st, _LIB.fnpf_prism_last_error(self._h).decode())
+        return infos
+
+    def diagonal(self, eta, h, diag, stream=None):
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (diag, self.N, "float64", "diag"))
+        self._check(_LIB.fnpf_prism_diagonal(self._h, *ptrs, _stream(stream)))
+
+    def apply_stored(self, eta, h, x, y, stream=None):
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (x, self.N, "float64", "x"), (y, self.N, "float64", "y"))
+        self._check(_LIB.fnpf_prism_apply_stored(self._h, *ptrs, _stream(stream)))
+
+    def laplace_solve(self, eta, h, phis, phi, opts=None, stream=None):
+        """phi [N] (in: interior guess) = the potential with phi = phis on the
+        surface; returns the solve's info as a dict."""
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (phis, self.ns, "float64", "phis"), (phi, self.N, "float64", "phi"))
+        info = SolveInfo()
+        st = _LIB.fnpf_prism_laplace_solve(self._h, None if opts is None else ctypes.byref(opts), *ptrs,
+                                           ctypes.byref(info), _stream(stream))
+        return self._check(st, info.as_dict())
+
+    def dtn(self, eta, h, phis, w, opts=None, stream=None):
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (phis, self.ns, "float64", "phis"), (w, self.ns, "float64", "w"))
+        info = SolveInfo()
+        st = _LIB.fnpf_prism_dtn(self._h, None if opts is None else ctypes.byref(opts), *ptrs, ctypes.byref(info),
+                                 _stream(stream))
+        return self._check(st, info.as_dict())
+
+    def rhs(self, eta, h, phis, k_eta, k_phis, opts=None, stream=None):
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (phis, self.ns, "float64", "phis"), (k_eta, self.ns, "float64", "k_eta"),
+                     (k_phis, self.ns, "float64", "k_phis"))
+        info = SolveInfo()
+        st = _LIB.fnpf_prism_rhs(self._h, None if opts is None else ctypes.byref(opts), *ptrs, ctypes.byref(info),
+                                 _stream(stream))
+        return self._check(st, info.as_dict())
+
+    def rk4_step(self, h, eta, phis, dt, opts=None, stream=None):
+        """One RK4 step of (eta, phis) in place; returns the four stages' infos."""
+        ptrs = _ptrs(None, (h, self.ns, "float64", "h"), (eta, self.ns, "float64", "eta"),
+                     (phis, self.ns, "float64", "phis"))
+        infos = (SolveInfo * 4)()
+        st = _LIB.fnpf_prism_rk4_step(self._h, None if opts is None else ctypes.byref(opts), *ptrs, float(dt),
+                                      infos, _stream(stream))
+        return self._check(st, [infos[i].as_dict() for i in range(4)])

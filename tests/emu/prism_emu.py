@@ -1,0 +1,131 @@
+"""Build and call the host harness of the prism solve and step
+(tests/emu/prism_step_host.cpp): the library's kernel bodies and orchestration
+(paper_2506_09435_gb300/csrc/prism_step.h) compiled as plain C++ and run item
+by item on host arrays.  Tests only."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+PKG = os.path.join(ROOT, "paper_2506_09435_gb300")
+
+
+def asan_runtime():
+    """Path of the AddressSanitizer runtime of g++, or None."""
+    cxx = shutil.which("g++")
+    if not cxx:
+        return None
+    r = subprocess.run([cxx, "-print-file-name=libasan.so"], capture_output=True, text=True)
+    path = r.stdout.strip()
+    return path if r.returncode == 0 and os.path.isabs(path) and os.path.exists(path) else None
+
+
+def build(out_dir, asan=False):
+    """Compiles the harness against the in-tree libfnpf.so (its host
+    functions: numbering, tables); returns the path of the shared object."""
+    from paper_2506_09435_gb300 import build as B
+    B.build()
+    out = os.path.join(out_dir, "libprism_emu%s.so" % ("_asan" if asan else ""))
+    cmd = ["g++", "-std=c++17", "-shared", "-fPIC", "-Wall", "-Werror",
+           "-I" + os.path.join(ROOT, "include"), "-I" + os.path.join(PKG, "csrc"),
+           os.path.join(HERE, "prism_step_host.cpp"), "-L" + PKG, "-l:libfnpf.so", "-Wl,-rpath," + PKG, "-o", out]
+    cmd[1:1] = ["-O1", "-g", "-fsanitize=address", "-fno-omit-frame-pointer"] if asan else ["-O2"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("harness build failed:\n" + r.stdout + r.stderr)
+    return out
+
+
+class PrismOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mass_rtol", ctypes.c_double),
+                ("mass_max_iter", ctypes.c_int), ("g", ctypes.c_double), ("model", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("status", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+def _p(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Harness:
+    def __init__(self, path):
+        vp = ctypes.c_void_p
+        lib = ctypes.CDLL(path)
+        lib.emu_create.restype = vp
+        lib.emu_create.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.emu_destroy.argtypes = [vp]
+        lib.emu_destroy.restype = None
+        lib.emu_sizes.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int64)] * 3
+        lib.emu_sizes.restype = None
+        sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_laplace_solve": [vp] * 7,
+               "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, vp]}
+        for nm, args in sig.items():
+            getattr(lib, nm).argtypes = args
+            getattr(lib, nm).restype = ctypes.c_int
+        self.lib = lib
+
+    def mesh(self, verts, tris, p, nz):
+        return EmuMesh(self.lib, verts, tris, p, nz)
+
+
+class EmuMesh:
+    def __init__(self, lib, verts, tris, p, nz):
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        self.lib = lib
+        self.h = lib.emu_create(_p(v), len(v), t.ctypes.data_as(ctypes.c_void_p), len(t), int(p), int(nz))
+        if not self.h:
+            raise ValueError("bad prism mesh")
+        N, ns, _ = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lib.emu_sizes(self.h, ctypes.byref(N), ctypes.byref(ns), ctypes.byref(_))
+        self.N, self.ns = N.value, ns.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.emu_destroy(self.h)
+            self.h = None
+
+    def launches(self):
+        N, ns, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self.lib.emu_sizes(self.h, ctypes.byref(N), ctypes.byref(ns), ctypes.byref(n))
+        return n.value
+
+    def diagonal(self, eta, h):
+        d = np.zeros(self.N)
+        assert self.lib.emu_diagonal(self.h, _p(eta), _p(h), _p(d)) == 0
+        return d
+
+    def apply_stored(self, eta, h, x):
+        y = np.zeros(self.N)
+        assert self.lib.emu_apply_stored(self.h, _p(eta), _p(h), _p(x), _p(y)) == 0
+        return y
+
+    def laplace_solve(self, opts, eta, h, phis, phi):
+        info = SolveInfo()
+        st = self.lib.emu_laplace_solve(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(phis), _p(phi),
+                                        ctypes.byref(info))
+        return st, info
+
+    def dtn(self, opts, eta, h, phis):
+        w, info = np.zeros(self.ns), SolveInfo()
+        st = self.lib.emu_dtn(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(phis), _p(w), ctypes.byref(info))
+        return st, w
+
+    def rhs(self, opts, eta, h, phis):
+        ke, kp, info = np.zeros(self.ns), np.zeros(self.ns), SolveInfo()
+        st = self.lib.emu_rhs(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(phis), _p(ke), _p(kp),
+                              ctypes.byref(info))
+        return st, ke, kp
+
+    def rk4_step(self, opts, h, eta, phis, dt):
+        infos = (SolveInfo * 4)()
+        st = self.lib.emu_rk4_step(self.h, ctypes.byref(opts), _p(h), _p(eta), _p(phis), float(dt), infos)
+        return st, [infos[i].iters for i in range(4)]

@@ -1,0 +1,198 @@
+// Test harness (tests only): the items and the orchestration of the prism
+// solve and step (paper_2506_09435_gb300/csrc/prism_step.h) compiled as plain
+// C++ and run one item after another on host memory, so that a CPU test can
+// compare the kernels' own index arithmetic and arithmetic with the oracle
+// before they run on a GPU.  The mesh set-up calls the library's host
+// functions (numbering, triangle tables, GLL tables) and repeats the packing
+// of fnpf_prism_create; every table and workspace buffer is a separate
+// allocation of its exact size, so that a build with AddressSanitizer reports
+// any access outside a buffer.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <memory>
+#include <vector>
+
+#include "fnpf.h"
+#include "prism_step.h"
+
+namespace fnpf {
+void gll_tables(int p, double* xi, double* w, double* D);
+bool prism_tables(int p, std::vector<double>* rn, std::vector<double>* sn, std::vector<double>* wq,
+                  std::vector<double>* L, std::vector<double>* Lr, std::vector<double>* Ls);
+bool prism_numbering(const double* verts, int nverts, const int* tris, int ntri, int p, std::vector<int>* tnodes,
+                     std::vector<double>* xs, std::vector<double>* ys);
+}  // namespace fnpf
+
+namespace {
+
+using namespace fnpf::pstep;
+
+struct HostEx {
+  int64_t launches = 0;
+  template <class It>
+  int run(int64_t n, const typename It::Args& a) {
+    ++launches;
+    for (int64_t i = 0; i < n; ++i) It::at(i, a);
+    return 0;
+  }
+  int get(double* dst, const double* src, int count) {
+    memcpy(dst, src, sizeof(double) * count);
+    return 0;
+  }
+};
+
+struct Emu {
+  PMesh m{};
+  PWork w{};
+  std::vector<std::unique_ptr<double[]>> dbufs;
+  std::vector<int> tn, mcol;
+  std::vector<int64_t> voff, vinc, soff, sinc, mrow;
+  std::vector<double> mval, mdiag;
+  HostEx ex;
+
+  const double* table(const std::vector<double>& v, size_t off, size_t count) {
+    dbufs.emplace_back(new double[count]);
+    memcpy(dbufs.back().get(), v.data() + off, sizeof(double) * count);
+    return dbufs.back().get();
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void* emu_create(const double* verts, int nverts, const int* tris, int ntris, int p, int nz) {
+  std::unique_ptr<Emu> e(new Emu());
+  std::vector<double> xs, ys;
+  if (!fnpf::prism_numbering(verts, nverts, tris, ntris, p, &e->tn, &xs, &ys)) return nullptr;
+  std::vector<double> rn, sn, wq, L, Lr, Ls;
+  if (!fnpf::prism_tables(p, &rn, &sn, &wq, &L, &Lr, &Ls)) return nullptr;
+  PMesh& m = e->m;
+  m.p = p;
+  m.n = p + 1;
+  m.nz = nz;
+  m.nt = (int)rn.size();
+  m.nq = (int)wq.size();
+  m.ntri = ntris;
+  m.ns = (int64_t)xs.size();
+  m.nv = (int64_t)nz * p + 1;
+  m.N = m.nv * m.ns;
+  m.NI = m.N - m.ns;
+  m.nelem = (int64_t)ntris * nz;
+  const int n = m.n, nt = m.nt;
+  std::vector<double> geo(4 * (size_t)ntris);
+  for (int t = 0; t < ntris; ++t) {
+    const int A = tris[3 * t], B = tris[3 * t + 1], C = tris[3 * t + 2];
+    geo[4 * t] = 0.5 * (verts[2 * B] - verts[2 * A]);
+    geo[4 * t + 1] = 0.5 * (verts[2 * C] - verts[2 * A]);
+    geo[4 * t + 2] = 0.5 * (verts[2 * B + 1] - verts[2 * A + 1]);
+    geo[4 * t + 3] = 0.5 * (verts[2 * C + 1] - verts[2 * A + 1]);
+  }
+  std::vector<double> xi(n), wv(n), D(n * n);
+  fnpf::gll_tables(p, xi.data(), wv.data(), D.data());
+  m.tn = e->tn.data();
+  m.geo = e->table(geo, 0, geo.size());
+  m.L = e->table(L, 0, L.size());
+  m.Lr = e->table(Lr, 0, Lr.size());
+  m.Ls = e->table(Ls, 0, Ls.size());
+  m.wq = e->table(wq, 0, wq.size());
+  m.xi = e->table(xi, 0, xi.size());
+  m.wv = e->table(wv, 0, wv.size());
+  m.D = e->table(D, 0, D.size());
+  // volume incidence in (element, local node) order, as fnpf_prism_create
+  e->voff.assign(m.N + 1, 0);
+  for (int t = 0; t < ntris; ++t)
+    for (int l = 0; l < nz; ++l)
+      for (int mm = 0; mm < n; ++mm)
+        for (int q = 0; q < nt; ++q) ++e->voff[(int64_t)(l * p + mm) * m.ns + e->tn[(size_t)t * nt + q] + 1];
+  for (int64_t g = 0; g < m.N; ++g) e->voff[g + 1] += e->voff[g];
+  e->vinc.assign(e->voff[m.N], 0);
+  std::vector<int64_t> fill(e->voff.begin(), e->voff.end() - 1);
+  for (int t = 0; t < ntris; ++t)
+    for (int l = 0; l < nz; ++l)
+      for (int mm = 0; mm < n; ++mm)
+        for (int q = 0; q < nt; ++q) {
+          const int64_t g = (int64_t)(l * p + mm) * m.ns + e->tn[(size_t)t * nt + q];
+          e->vinc[fill[g]++] = ((int64_t)t * nz + l) * nt * n + (int64_t)mm * nt + q;
+        }
+  m.voff = e->voff.data();
+  m.vinc = e->vinc.data();
+  surface_incidence(e->tn.data(), ntris, nt, m.ns, &e->soff, &e->sinc);
+  surface_mass(m, e->tn.data(), m.geo, m.L, m.wq, &e->mrow, &e->mcol, &e->mval, &e->mdiag);
+  m.soff = e->soff.data();
+  m.sinc = e->sinc.data();
+  m.mrow = e->mrow.data();
+  m.mcol = e->mcol.data();
+  m.mval = e->mval.data();
+  m.mdiag = e->mdiag.data();
+  Emu* ep = e.get();
+  carve(m, &e->w, [ep](double** ptr, int64_t cnt) {
+    ep->dbufs.emplace_back(new double[cnt > 0 ? cnt : 1]());
+    *ptr = ep->dbufs.back().get();
+  });
+  return e.release();
+}
+
+void emu_destroy(void* h) { delete static_cast<Emu*>(h); }
+
+void emu_sizes(void* h, int64_t* N, int64_t* ns, int64_t* launches) {
+  Emu* e = static_cast<Emu*>(h);
+  *N = e->m.N;
+  *ns = e->m.ns;
+  *launches = e->ex.launches;
+}
+
+static Params params(const fnpf_prism_opts* o) {
+  fnpf_prism_opts d;
+  fnpf_prism_default_opts(&d);
+  if (!o) o = &d;
+  return Params{o->rtol, o->max_iter, o->mass_rtol, o->mass_max_iter, o->g, o->model == FNPF_LINEAR};
+}
+
+int emu_diagonal(void* h, const double* eta, const double* hh, double* diag) {
+  Emu* e = static_cast<Emu*>(h);
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  fnpf_status st = sp.geometry(eta, hh);
+  if (st == FNPF_OK) st = sp.go<CopyItem>(e->m.N, {e->w.diag, diag});
+  return st;
+}
+
+int emu_apply_stored(void* h, const double* eta, const double* hh, const double* x, double* y) {
+  Emu* e = static_cast<Emu*>(h);
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  fnpf_status st = sp.geometry(eta, hh);
+  if (st == FNPF_OK) st = sp.apply(x, y);
+  return st;
+}
+
+int emu_laplace_solve(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis,
+                      double* phi, fnpf_solve_info* info) {
+  Emu* e = static_cast<Emu*>(h);
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  return sp.solve(eta, hh, phis, phi, params(o), info);
+}
+
+int emu_dtn(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis, double* w,
+            fnpf_solve_info* info) {
+  Emu* e = static_cast<Emu*>(h);
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  return sp.dtn(eta, hh, phis, w, params(o), info);
+}
+
+int emu_rhs(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis, double* ke,
+            double* kp, fnpf_solve_info* info) {
+  Emu* e = static_cast<Emu*>(h);
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  return sp.rhs(eta, hh, phis, ke, kp, params(o), info);
+}
+
+int emu_rk4_step(void* h, const fnpf_prism_opts* o, const double* hh, double* eta, double* phis, double dt,
+                 fnpf_solve_info* info) {
+  Emu* e = static_cast<Emu*>(h);
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  return sp.rk4(hh, eta, phis, dt, params(o), info);
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+"""The prism solve, w, projected free-surface conditions and RK4 step on the
+GPU (fnpf_prism_diagonal, fnpf_prism_apply_stored, fnpf_prism_laplace_solve,
+fnpf_prism_dtn, fnpf_prism_rhs, fnpf_prism_rk4_step; Sec. 3.1.2 mesh, Sec. 3.4
+Steps 4.1-4.6, Sec. 3.2 ERK4) element by element against the prism oracle
+(oracle/prism.py) on the seeded inputs of tests/prism_cases.py; the operator
+with the stored metric also against the library's on-the-fly prism operator."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import prism as P
+from tests import prism_cases as C
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def opts(fnpf, rtol=1e-13, max_iter=20000, linear=False):
+    return fnpf.PrismMesh.default_opts(rtol=rtol, max_iter=max_iter, mass_rtol=1e-14, g=C.G,
+                                       model=fnpf.FNPF_LINEAR if linear else fnpf.FNPF_NONLINEAR)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("nz", [1, 3])
+def test_stored_operator_and_diagonal_match_oracle(fnpf, p, nz):
+    v, t, pm = C.mesh(p, nz)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, _ = C.fields(pm)
+    A = pm.assemble(eta, h)
+    x = np.random.default_rng(100 + 10 * p + nz).standard_normal(pm.N)
+    ref = A @ x
+    ys, yf, d = (torch.zeros(pm.N, dtype=torch.float64, device=DEV) for _ in range(3))
+    gm.apply_stored(T(eta), T(h), T(x), ys)
+    gm.apply(T(eta), T(h), T(x), yf)
+    gm.diagonal(T(eta), T(h), d)
+    torch.cuda.synchronize()
+    ys, yf, d = ys.cpu().numpy(), yf.cpu().numpy(), d.cpu().numpy()
+    assert np.max(np.abs(ys - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(ys - yf)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(d - A.diagonal())) <= 1e-13 * np.max(np.abs(A.diagonal()))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_laplace_solve_matches_oracle(fnpf, p):
+    nz = 2
+    v, t, pm = C.mesh(p, nz)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi = torch.zeros(pm.N, dtype=torch.float64, device=DEV)
+    info = gm.laplace_solve(T(eta), T(h), T(phis), phi, opts(fnpf))
+    assert info["status"] == 0 and info["iters"] > 0 and info["rel_res"] <= 1e-13
+    ref = P.laplace_solve(pm, eta, h, phis)
+    out = phi.cpu().numpy()
+    assert C.rel(out, ref) <= 1e-10
+    assert np.array_equal(out[pm.N - pm.ns:], phis)
+    info = gm.laplace_solve(T(eta), T(h), T(phis), phi, opts(fnpf, rtol=1e-10))
+    assert info["iters"] == 0 and C.rel(phi.cpu().numpy(), ref) <= 1e-10
+
+
+def test_solve_special_cases(fnpf):
+    p, nz = 3, 2
+    v, t, pm = C.mesh(p, nz)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi = T(np.random.default_rng(1).standard_normal(pm.N))
+    gm.laplace_solve(T(eta), T(h), T(np.full(pm.ns, 0.3)), phi, opts(fnpf))
+    assert float((phi - 0.3).abs().max()) <= 1e-12
+    phi = T(np.random.default_rng(2).standard_normal(pm.N))
+    info = gm.laplace_solve(T(eta), T(h), T(np.zeros(pm.ns)), phi, opts(fnpf))
+    assert info["iters"] == 0 and not bool(phi.any())
+    with pytest.raises(fnpf.FnpfError) as e:
+        gm.laplace_solve(T(eta), T(h), T(phis), torch.zeros(pm.N, dtype=torch.float64, device=DEV),
+                         opts(fnpf, max_iter=2))
+    assert e.value.status == fnpf.FNPF_ENOCONV
+    e0, p0 = T(eta), T(phis)
+    with pytest.raises(fnpf.FnpfError):
+        gm.rk4_step(T(h), e0, p0, 0.01, opts(fnpf, max_iter=2))
+    assert np.array_equal(e0.cpu().numpy(), eta) and np.array_equal(p0.cpu().numpy(), phis)
+
+
+@pytest.mark.parametrize("linear", [False, True])
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_dtn_and_projected_conditions_match_oracle(fnpf, p, linear):
+    nz = 2
+    v, t, pm = C.mesh(p, nz)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    geo = np.zeros_like(eta) if linear else eta
+    w = torch.zeros(pm.ns, dtype=torch.float64, device=DEV)
+    gm.dtn(T(geo), T(h), T(phis), w, opts(fnpf, linear=linear))
+    assert C.rel(w.cpu().numpy(), P.w_recovery(pm, geo, h, P.laplace_solve(pm, geo, h, phis))) <= 1e-10
+    ke, kp = (torch.zeros(pm.ns, dtype=torch.float64, device=DEV) for _ in range(2))
+    gm.rhs(T(eta), T(h), T(phis), ke, kp, opts(fnpf, linear=linear))
+    ko = P.rhs(pm, h, eta, phis, C.G, linear=linear)
+    assert C.rel(ke.cpu().numpy(), ko[0]) <= 1e-10 and C.rel(kp.cpu().numpy(), ko[1]) <= 1e-10
+
+
+@pytest.mark.parametrize("linear", [False, True])
+@pytest.mark.parametrize("p", [2, 4])
+def test_rk4_steps_match_oracle(fnpf, p, linear):
+    nz = 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.standing_wave(pm)
+    e1, p1, hd = T(eta), T(phis), T(h)
+    eo, po = eta.copy(), phis.copy()
+    dt = 0.02
+    for _ in range(3):
+        infos = gm.rk4_step(hd, e1, p1, dt, opts(fnpf, linear=linear))
+        assert all(i["status"] == 0 for i in infos) and max(i["iters"] for i in infos) > 0
+        eo, po = P.rk4_step(pm, h, eo, po, dt, C.G, linear=linear)
+    assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10

@@ -1,0 +1,155 @@
+"""The prism solve, w, projected free-surface conditions and RK4 step of the
+library (paper_2506_09435_gb300/csrc/prism_step.h: the kernels' per-thread
+bodies and the host orchestration that launches them) run item by item on the
+CPU through a test harness (tests/emu), against the prism oracle
+(oracle/prism.py): the operator with the stored metric and its diagonal against
+the assembled matrix, the Laplace solve against the direct solve, w, both
+projected conditions, three RK4 steps (nonlinear and linear), special cases
+(a constant surface potential, a zero right-hand side, an iteration cap), and
+every entry point under AddressSanitizer (each table and workspace buffer a
+separate allocation of its exact size), which checks the kernels' index
+arithmetic against their buffers before their first GPU run."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import prism as P
+from tests import prism_cases as C
+from tests.emu import prism_emu as E
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    return E.Harness(E.build(str(tmp_path_factory.mktemp("prism_emu"))))
+
+
+def opts(rtol=1e-13, max_iter=20000, mass_rtol=1e-14, linear=False):
+    return E.PrismOpts(rtol, max_iter, mass_rtol, 5000, C.G, int(linear))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("nz", [1, 3])
+def test_stored_operator_and_diagonal_match_oracle(harness, p, nz):
+    v, t, pm = C.mesh(p, nz)
+    em = harness.mesh(v, t, p, nz)
+    assert (em.N, em.ns) == (pm.N, pm.ns)
+    eta, h, _ = C.fields(pm)
+    A = pm.assemble(eta, h)
+    x = np.random.default_rng(100 + 10 * p + nz).standard_normal(pm.N)
+    ref = A @ x
+    assert np.max(np.abs(em.apply_stored(eta, h, x) - ref)) <= 1e-12 * np.max(np.abs(ref))
+    d = A.diagonal()
+    assert np.max(np.abs(em.diagonal(eta, h) - d)) <= 1e-13 * np.max(np.abs(d))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_laplace_solve_matches_oracle(harness, p):
+    nz = 2
+    v, t, pm = C.mesh(p, nz)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi = np.zeros(pm.N)
+    st, info = em.laplace_solve(opts(), eta, h, phis, phi)
+    assert st == 0 and info.status == 0 and info.iters > 0 and info.rel_res <= 1e-13
+    ref = P.laplace_solve(pm, eta, h, phis)
+    assert C.rel(phi, ref) <= 1e-10
+    assert np.array_equal(phi[pm.N - pm.ns:], phis)
+    # warm start from the solution: converged at once, the same potential
+    st, info = em.laplace_solve(opts(rtol=1e-10), eta, h, phis, phi)
+    assert st == 0 and info.iters == 0 and C.rel(phi, ref) <= 1e-10
+
+
+def test_solve_special_cases(harness):
+    p, nz = 3, 2
+    v, t, pm = C.mesh(p, nz)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, _ = C.fields(pm)
+    # a constant surface potential: the constant is harmonic with zero normal derivative
+    phi = np.random.default_rng(1).standard_normal(pm.N)
+    st, info = em.laplace_solve(opts(), eta, h, np.full(pm.ns, 0.3), phi)
+    assert st == 0 and np.max(np.abs(phi - 0.3)) <= 1e-12
+    # a zero right-hand side: phi = 0 whatever the guess, no iteration
+    phi = np.random.default_rng(2).standard_normal(pm.N)
+    st, info = em.laplace_solve(opts(), eta, h, np.zeros(pm.ns), phi)
+    assert st == 0 and info.iters == 0 and not phi.any()
+    # an iteration cap: ENOCONV, and an RK4 step leaves its state unchanged
+    _, _, phis = C.fields(pm)
+    st, info = em.laplace_solve(opts(max_iter=2), eta, h, phis, np.zeros(pm.N))
+    assert st == 4 and info.status == 4 and info.iters == 2
+    e0, p0 = eta.copy(), phis.copy()
+    st, _ = em.rk4_step(opts(max_iter=2), h, e0, p0, 0.01)
+    assert st == 4 and np.array_equal(e0, eta) and np.array_equal(p0, phis)
+
+
+@pytest.mark.parametrize("linear", [False, True])
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_dtn_and_projected_conditions_match_oracle(harness, p, linear):
+    nz = 2
+    v, t, pm = C.mesh(p, nz)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    geo = np.zeros_like(eta) if linear else eta
+    st, w = em.dtn(opts(linear=linear), geo, h, phis)
+    assert st == 0
+    assert C.rel(w, P.w_recovery(pm, geo, h, P.laplace_solve(pm, geo, h, phis))) <= 1e-10
+    st, ke, kp = em.rhs(opts(linear=linear), eta, h, phis)
+    assert st == 0
+    ko = P.rhs(pm, h, eta, phis, C.G, linear=linear)
+    assert C.rel(ke, ko[0]) <= 1e-10 and C.rel(kp, ko[1]) <= 1e-10
+
+
+@pytest.mark.parametrize("linear", [False, True])
+@pytest.mark.parametrize("p", [2, 4])
+def test_rk4_steps_match_oracle(harness, p, linear):
+    nz = 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.standing_wave(pm)
+    e1, p1 = eta.copy(), phis.copy()
+    eo, po = eta.copy(), phis.copy()
+    dt = 0.02
+    for _ in range(3):
+        st, iters = em.rk4_step(opts(linear=linear), h, e1, p1, dt)
+        assert st == 0 and max(iters) > 0
+        eo, po = P.rk4_step(pm, h, eo, po, dt, C.G, linear=linear)
+    assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
+
+
+ASAN_DRIVER = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[2])
+from tests import prism_cases as C
+from tests.emu import prism_emu as E
+hs = E.Harness(sys.argv[1])
+for p, nz, nx, ny in [(1, 1, 2, 2), (3, 2, 3, 2), (5, 3, 2, 3)]:
+    v, t, pm = C.mesh(p, nz, nx=nx, ny=ny)
+    em = hs.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    em.diagonal(eta, h)
+    em.apply_stored(eta, h, np.ones(pm.N))
+    o = E.PrismOpts(1e-10, 20000, 1e-13, 5000, C.G, 0)
+    assert em.laplace_solve(o, eta, h, phis, np.zeros(pm.N))[0] == 0
+    assert em.dtn(o, eta, h, phis)[0] == 0
+    assert em.rhs(o, eta, h, phis)[0] == 0
+    assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
+    o.model = 1
+    assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
+print("asan run ok")
+"""
+
+
+def test_every_entry_point_in_bounds_under_asan(tmp_path):
+    rt = E.asan_runtime()
+    if rt is None:
+        pytest.skip("no AddressSanitizer runtime")
+    lib = E.build(str(tmp_path), asan=True)
+    env = dict(os.environ, LD_PRELOAD=rt, ASAN_OPTIONS="detect_leaks=0:abort_on_error=0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", ASAN_DRIVER, lib, root], capture_output=True, text=True, env=env,
+                       timeout=600)
+    assert r.returncode == 0 and "AddressSanitizer" not in r.stderr, r.stderr[-4000:]
+    assert "asan run ok" in r.stdout
