@@ -558,6 +558,21 @@ fnpf_status fnpf_prism_rhs(fnpf_prism* mesh, const fnpf_prism_opts* opts, const 
 fnpf_status fnpf_prism_rk4_step(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* h, double* eta,
                                 double* phis, double dt, fnpf_solve_info* info, void* stream);
 
+/* Modal filter on the prism mesh's triangular surface elements (Sec. 3.2,
+ * modal filtering; applied in Step 4.7).  On every triangle the nodal values
+ * are mapped to the coefficients of the orthonormal Dubiner basis on the
+ * reference triangle (V[r][c] = psi_c(node r)), mode (i, j) is scaled by
+ * sigma_(i+j) with the weights of fnpf_filter (by total degree), and mapped
+ * back; the triangle-interior nodes (p >= 3) take the filtered values, nodes on
+ * edges and vertices keep theirs.  Once set, every fnpf_prism_rk4_step filters
+ * eta and phi_eta after the RK4 combination.  alpha = 0 (or NULL) turns it off.
+ * fnpf_prism_set_filter builds the matrix on the host and copies it
+ * (synchronous); fnpf_prism_filter_apply filters one field f [Ns] (device, in
+ * place) on `stream`.  Errors: EINVAL (alpha < 0 or not finite, order < 1,
+ * cutoff outside 0..p-1; apply without a filter), ENOMEM, ECUDA. */
+fnpf_status fnpf_prism_set_filter(fnpf_prism* mesh, const fnpf_filter* filter);
+fnpf_status fnpf_prism_filter_apply(fnpf_prism* mesh, double* f, void* stream);
+
 /* Message of the last failure on this mesh (or of the last create failure
  * when mesh is NULL).  Valid until the next call on the same mesh. */
 const char* fnpf_last_error(const fnpf_mesh* mesh);

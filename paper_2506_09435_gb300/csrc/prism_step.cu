@@ -18,6 +18,9 @@
 
 namespace fnpf {
 
+bool prism_tables(int p, std::vector<double>* rn, std::vector<double>* sn, std::vector<double>* wq,
+                  std::vector<double>* L, std::vector<double>* Lr, std::vector<double>* Ls);   // prism.cu
+
 constexpr int kItemThreads = 256;
 
 template <class It>
@@ -55,6 +58,8 @@ struct PrismStepState {
   int* d_mcol = nullptr;
   double* d_mval = nullptr;
   double* d_mdiag = nullptr;
+  double* d_filt = nullptr;    // [nt][nt] the modal filter (at the first fnpf_prism_set_filter)
+  int* d_interior = nullptr;   // [nt]
 };
 
 void prism_step_free(fnpf_prism* m) {
@@ -67,6 +72,8 @@ void prism_step_free(fnpf_prism* m) {
   cudaFree(st->d_mcol);
   cudaFree(st->d_mval);
   cudaFree(st->d_mdiag);
+  cudaFree(st->d_filt);
+  cudaFree(st->d_interior);
   delete st;
   m->step = nullptr;
 }
@@ -238,6 +245,52 @@ fnpf_status fnpf_prism_rhs(fnpf_prism* m, const fnpf_prism_opts* opts, const dou
   return fnpf::with_stepper(m, opts, stream, "prism right-hand side", [&](auto& sp, const fnpf::pstep::Params& p) {
     return sp.rhs(eta, h, phis, k_eta, k_phis, p, info);
   });
+}
+
+fnpf_status fnpf_prism_set_filter(fnpf_prism* m, const fnpf_filter* f) {
+  if (!m) return FNPF_EINVAL;
+  if (f && (!(f->alpha >= 0) || !isfinite(f->alpha) || f->order < 1 || f->cutoff < 0 || f->cutoff >= m->p)) {
+    m->err = "prism filter: alpha >= 0 and finite, order >= 1, cutoff in 0..p-1";
+    return FNPF_EINVAL;
+  }
+  fnpf_status st = fnpf::ensure_step(m);
+  if (st != FNPF_OK) return st;
+  fnpf::PrismStepState* ps = m->step;
+  if (!f || f->alpha == 0) {
+    ps->pm.filt = nullptr;
+    ps->pm.interior = nullptr;
+    return FNPF_OK;
+  }
+  std::vector<double> rn, sn, wq, L, Lr, Ls, F;
+  std::vector<int> interior;
+  if (!fnpf::prism_tables(m->p, &rn, &sn, &wq, &L, &Lr, &Ls) ||
+      !fnpf::pstep::triangle_filter(m->p, rn.data(), sn.data(), f->alpha, f->order, f->cutoff, &F, &interior)) {
+    m->err = "prism filter: singular Vandermonde matrix";
+    return FNPF_EINVAL;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!ps->d_filt) e = cudaMalloc(&ps->d_filt, sizeof(double) * F.size());
+  if (e == cudaSuccess && !ps->d_interior) e = cudaMalloc(&ps->d_interior, sizeof(int) * interior.size());
+  if (e == cudaSuccess) e = cudaMemcpy(ps->d_filt, F.data(), sizeof(double) * F.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ps->d_interior, interior.data(), sizeof(int) * interior.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    m->err = std::string("prism filter: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? FNPF_ENOMEM : FNPF_ECUDA;
+  }
+  ps->pm.filt = ps->d_filt;
+  ps->pm.interior = ps->d_interior;
+  return FNPF_OK;
+}
+
+fnpf_status fnpf_prism_filter_apply(fnpf_prism* m, double* f, void* stream) {
+  if (!m || !f) return FNPF_EINVAL;
+  if (!m->step || !m->step->pm.filt) {
+    m->err = "prism filter apply: no filter set";
+    return FNPF_EINVAL;
+  }
+  return fnpf::with_stepper(m, nullptr, stream, "prism filter apply",
+                            [&](auto& sp, const fnpf::pstep::Params&) { return sp.filter(f); });
 }
 
 fnpf_status fnpf_prism_rk4_step(fnpf_prism* m, const fnpf_prism_opts* opts, const double* h, double* eta,

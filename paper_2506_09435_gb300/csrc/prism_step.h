@@ -64,6 +64,8 @@ struct PMesh {
   const int* mcol;
   const double* mval;
   const double* mdiag;                  // [ns] its diagonal
+  const double* filt;                   // [nt][nt] modal filter V F V^-1 on the triangle nodes (null: none)
+  const int* interior;                  // [nt] 1 for the triangle-interior local nodes
 };
 
 // Points the table pointers of m into the packed tables of fnpf_prism_create:
@@ -89,6 +91,7 @@ struct PWork {
   double *mr, *mz, *mp, *mq;            // surface-mass CG [ns]
   double *ke, *kp, *es, *ps, *ae, *ap;  // RK4 stage right-hand side, stage state, accumulator [ns]
   double* zero;                         // [ns] zeros (still-water geometry of the linear model)
+  double* ft;                           // [ntri nt] filtered interior values
 };
 
 inline int64_t dot_partials(int64_t n) { return (n + kChunk - 1) / kChunk; }
@@ -116,6 +119,7 @@ void carve(const PMesh& m, PWork* w, Take take) {
   double** surf[] = {&w->be, &w->bp, &w->mr, &w->mz, &w->mp, &w->mq, &w->ke,
                      &w->kp, &w->es, &w->ps, &w->ae, &w->ap, &w->zero};
   for (double** s : surf) take(s, m.ns);
+  take(&w->ft, (int64_t)m.ntri * m.nt);
 }
 
 // ---------------------------------------------------------------------------
@@ -173,6 +177,106 @@ inline void surface_mass(const PMesh& m, const int* tn, const double* geo, const
     }
     (*row)[i + 1] = (int64_t)col->size();
   }
+}
+
+// The modal filter of the paper's triangular surface elements (Sec. 3.2): the
+// element's nodal values are mapped to the coefficients of a modal basis,
+// mode (i, j) is scaled by sigma_(i+j), and the result is mapped back:
+// F = V diag(sigma) V^-1 with V[r][c] = psi_c(node r).  psi_(i, j) is the
+// orthonormal Dubiner basis on R = {r, s >= -1, r + s <= 0} (Dubiner 1991;
+// Sherwin & Karniadakis):
+//   psi_(i, j)(r, s) = sqrt(2) Q_i^(0,0)(a) Q_j^(2i+1,0)(s) (1 - s)^i,
+//   a = 2 (1 + r) / (1 - s) - 1,
+// Q_n^(al,be) the Jacobi polynomial normalised to unit L2 norm under the weight
+// (1 - x)^al (1 + x)^be; sigma_d = 1 for d <= cutoff, else
+// exp(-alpha ((d - cutoff) / (p - cutoff))^order).  Local node order (i, j),
+// j outer (the numbering of prism.cu); interior[c] = 1 for i, j > 0, i + j < p.
+
+// P_n^(al,be)(x) by the three-term recurrence in n.
+inline long double jacobi(int n, int al, int be, long double x) {
+  long double p0 = 1, p1 = 0.5L * ((al + be + 2) * x + (al - be));
+  if (n == 0) return p0;
+  for (int k = 1; k < n; ++k) {
+    const long double c = 2 * k + al + be;
+    const long double a1 = 2 * (k + 1) * (k + al + be + 1) * c;
+    const long double a2 = (c + 1) * (al * al - be * be);
+    const long double a3 = c * (c + 1) * (c + 2);
+    const long double a4 = 2 * (k + al) * (k + be) * (c + 2);
+    const long double p2 = ((a2 + a3 * x) * p1 - a4 * p0) / a1;
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+// || P_n^(al,be) || under its weight on [-1, 1].
+inline long double jacobi_norm(int n, int al, int be) {
+  const long double v = powl(2.0L, al + be + 1) / (2 * n + al + be + 1) * tgammal(n + al + 1.0L) *
+                        tgammal(n + be + 1.0L) / (tgammal(n + al + be + 1.0L) * tgammal(n + 1.0L));
+  return sqrtl(v);
+}
+
+inline long double dubiner(int i, int j, long double r, long double s) {
+  const long double a = 1 - s > 1e-15L ? 2 * (1 + r) / (1 - s) - 1 : -1.0L;
+  return sqrtl(2.0L) * jacobi(i, 0, 0, a) / jacobi_norm(i, 0, 0) * jacobi(j, 2 * i + 1, 0, s) /
+         jacobi_norm(j, 2 * i + 1, 0) * powl(1 - s, i);
+}
+
+// F [nt][nt] and interior [nt] for order p, the triangle nodes (rn, sn); false
+// if V is singular.
+inline bool triangle_filter(int p, const double* rn, const double* sn, double alpha, int order, int cutoff,
+                            std::vector<double>* F, std::vector<int>* interior) {
+  std::vector<std::pair<int, int>> idx;
+  for (int j = 0; j <= p; ++j)
+    for (int i = 0; i + j <= p; ++i) idx.emplace_back(i, j);
+  const int nt = (int)idx.size();
+  std::vector<long double> V((size_t)nt * nt), Vi((size_t)nt * nt, 0.0L);
+  for (int r = 0; r < nt; ++r)
+    for (int c = 0; c < nt; ++c) V[(size_t)r * nt + c] = dubiner(idx[c].first, idx[c].second, rn[r], sn[r]);
+  // V^-1 by Gauss-Jordan elimination with partial pivoting
+  std::vector<long double> A = V;
+  for (int i = 0; i < nt; ++i) Vi[(size_t)i * nt + i] = 1;
+  for (int c = 0; c < nt; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < nt; ++r)
+      if (fabsl(A[(size_t)r * nt + c]) > fabsl(A[(size_t)piv * nt + c])) piv = r;
+    if (fabsl(A[(size_t)piv * nt + c]) < 1e-300L) return false;
+    for (int k = 0; k < nt; ++k) {
+      std::swap(A[(size_t)c * nt + k], A[(size_t)piv * nt + k]);
+      std::swap(Vi[(size_t)c * nt + k], Vi[(size_t)piv * nt + k]);
+    }
+    const long double d = A[(size_t)c * nt + c];
+    for (int k = 0; k < nt; ++k) {
+      A[(size_t)c * nt + k] /= d;
+      Vi[(size_t)c * nt + k] /= d;
+    }
+    for (int r = 0; r < nt; ++r) {
+      if (r == c) continue;
+      const long double f = A[(size_t)r * nt + c];
+      if (f == 0) continue;
+      for (int k = 0; k < nt; ++k) {
+        A[(size_t)r * nt + k] -= f * A[(size_t)c * nt + k];
+        Vi[(size_t)r * nt + k] -= f * Vi[(size_t)c * nt + k];
+      }
+    }
+  }
+  std::vector<long double> sig(nt);
+  for (int c = 0; c < nt; ++c) {
+    const int d = idx[c].first + idx[c].second;
+    sig[c] = d <= cutoff ? 1.0L : expl(-alpha * powl((long double)(d - cutoff) / (p - cutoff), order));
+  }
+  F->assign((size_t)nt * nt, 0.0);
+  interior->assign(nt, 0);
+  for (int r = 0; r < nt; ++r) {
+    for (int c = 0; c < nt; ++c) {
+      long double v = 0;
+      for (int k = 0; k < nt; ++k) v += V[(size_t)r * nt + k] * sig[k] * Vi[(size_t)k * nt + c];
+      (*F)[(size_t)r * nt + c] = (double)v;
+    }
+    const int i = idx[r].first, j = idx[r].second;
+    (*interior)[r] = i > 0 && j > 0 && i + j < p;
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -590,6 +694,40 @@ struct SurfGatherItem {
   }
 };
 
+// Filtered value of triangle slot (t, c) for the interior local nodes: row c
+// of F applied to the triangle's nodal values of f.
+struct FilterItem {
+  struct Args {
+    PMesh m;
+    const double* f;
+    double* ft;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int t = (int)(i / m.nt), c = (int)(i - (int64_t)t * m.nt);
+    if (!m.interior[c]) return;
+    const int* tn = m.tn + (int64_t)t * m.nt;
+    const double* Fc = m.filt + (int64_t)c * m.nt;
+    double s = 0;
+    for (int k = 0; k < m.nt; ++k) s += Fc[k] * a.f[tn[k]];
+    a.ft[i] = s;
+  }
+};
+
+// f at the interior nodes = the filtered values (each interior node belongs to
+// one triangle only).
+struct FilterWriteItem {
+  struct Args {
+    PMesh m;
+    const double* ft;
+    double* f;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const int c = (int)(i % a.m.nt);
+    if (a.m.interior[c]) a.f[a.m.tn[i]] = a.ft[i];
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Orchestration.
 
@@ -770,7 +908,16 @@ struct Stepper {
     return mass_solve(w.bp, kp, o);
   }
 
-  // One classical RK4 step of (eta, phis) in place; info: NULL or [4].
+  // f [ns] in place through the modal filter (EINVAL without one).
+  fnpf_status filter(double* f) {
+    if (!m.filt) return FNPF_EINVAL;
+    const int64_t slots = (int64_t)m.ntri * m.nt;
+    FNPF_PS_TRY(go<FilterItem>(slots, {m, f, w.ft}));
+    return go<FilterWriteItem>(slots, {m, w.ft, f});
+  }
+
+  // One classical RK4 step of (eta, phis) in place, then the modal filter of
+  // both (when one is set); info: NULL or [4].
   fnpf_status rk4(const double* h, double* eta, double* phis, double dt, const Params& o, fnpf_solve_info* info) {
     const int64_t ns = m.ns;
     for (int s = 0; s < 4; ++s) {
@@ -794,7 +941,10 @@ struct Stepper {
       }
     }
     FNPF_PS_TRY(go<AxpyItem>(ns, {dt / 6.0, w.ae, eta}));
-    return go<AxpyItem>(ns, {dt / 6.0, w.ap, phis});
+    FNPF_PS_TRY(go<AxpyItem>(ns, {dt / 6.0, w.ap, phis}));
+    if (!m.filt) return FNPF_OK;
+    FNPF_PS_TRY(filter(eta));
+    return filter(phis);
   }
 };
 

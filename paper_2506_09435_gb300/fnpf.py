@@ -111,6 +111,8 @@ def load():
         "fnpf_prism_sizes": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
         "fnpf_prism_apply": [vp, vp, vp, vp, vp, vp],
         "fnpf_prism_diagonal": [vp, vp, vp, vp, vp],
+        "fnpf_prism_set_filter": [vp, ctypes.POINTER(Filter)],
+        "fnpf_prism_filter_apply": [vp, vp, vp],
         "fnpf_prism_apply_stored": [vp, vp, vp, vp, vp, vp],
         "fnpf_prism_laplace_solve": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_dtn": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
@@ -655,8 +657,19 @@ class PrismMesh:
                                  _stream(stream))
         return self._check(st, info.as_dict())
 
+    def set_filter(self, alpha, order=2, cutoff=0):
+        """The modal filter of the triangular surface elements (alpha = 0: off);
+        every later rk4_step filters eta and phis."""
+        f = Filter(float(alpha), int(order), int(cutoff))
+        self._check(_LIB.fnpf_prism_set_filter(self._h, ctypes.byref(f)))
+
+    def filter_apply(self, f, stream=None):
+        ptrs = _ptrs(None, (f, self.ns, "float64", "f"))
+        self._check(_LIB.fnpf_prism_filter_apply(self._h, *ptrs, _stream(stream)))
+
     def rk4_step(self, h, eta, phis, dt, opts=None, stream=None):
-        """One RK4 step of (eta, phis) in place; returns the four stages' infos."""
+        """One RK4 step of (eta, phis) in place (then the modal filter, when
+        set); returns the four stages' infos."""
         ptrs = _ptrs(None, (h, self.ns, "float64", "h"), (eta, self.ns, "float64", "eta"),
                      (phis, self.ns, "float64", "phis"))
         infos = (SolveInfo * 4)()

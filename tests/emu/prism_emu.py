@@ -67,6 +67,8 @@ class Harness:
         lib.emu_sizes.restype = None
         sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_laplace_solve": [vp] * 7,
                "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, vp]}
+        sig["emu_set_filter"] = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        sig["emu_filter_apply"] = [vp, vp]
         for nm, args in sig.items():
             getattr(lib, nm).argtypes = args
             getattr(lib, nm).restype = ctypes.c_int
@@ -124,6 +126,14 @@ class EmuMesh:
         st = self.lib.emu_rhs(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(phis), _p(ke), _p(kp),
                               ctypes.byref(info))
         return st, ke, kp
+
+    def set_filter(self, alpha, order=2, cutoff=0):
+        assert self.lib.emu_set_filter(self.h, float(alpha), int(order), int(cutoff)) == 0
+
+    def filter_apply(self, f):
+        out = np.array(f, dtype=np.float64, copy=True)
+        assert self.lib.emu_filter_apply(self.h, _p(out)) == 0
+        return out
 
     def rk4_step(self, opts, h, eta, phis, dt):
         infos = (SolveInfo * 4)()

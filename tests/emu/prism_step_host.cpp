@@ -47,7 +47,7 @@ struct Emu {
   PMesh m{};
   PWork w{};
   std::vector<std::unique_ptr<double[]>> dbufs;
-  std::vector<int> tn, mcol;
+  std::vector<int> tn, mcol, interior;
   std::vector<int64_t> voff, vinc, soff, sinc, mrow;
   std::vector<double> mval, mdiag;
   HostEx ex;
@@ -186,6 +186,32 @@ int emu_rhs(void* h, const fnpf_prism_opts* o, const double* eta, const double* 
   Emu* e = static_cast<Emu*>(h);
   Stepper<HostEx> sp{e->m, e->w, e->ex};
   return sp.rhs(eta, hh, phis, ke, kp, params(o), info);
+}
+
+int emu_set_filter(void* h, double alpha, int order, int cutoff) {
+  Emu* e = static_cast<Emu*>(h);
+  if (alpha == 0) {
+    e->m.filt = nullptr;
+    e->m.interior = nullptr;
+    return FNPF_OK;
+  }
+  std::vector<double> rn, sn, wq, L, Lr, Ls, F;
+  std::vector<int> interior;
+  if (!fnpf::prism_tables(e->m.p, &rn, &sn, &wq, &L, &Lr, &Ls) ||
+      !triangle_filter(e->m.p, rn.data(), sn.data(), alpha, order, cutoff, &F, &interior))
+    return FNPF_EINVAL;
+  e->dbufs.emplace_back(new double[F.size()]);
+  memcpy(e->dbufs.back().get(), F.data(), sizeof(double) * F.size());
+  e->m.filt = e->dbufs.back().get();
+  e->interior = interior;
+  e->m.interior = e->interior.data();
+  return FNPF_OK;
+}
+
+int emu_filter_apply(void* h, double* f) {
+  Emu* e = static_cast<Emu*>(h);
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  return sp.filter(f);
 }
 
 int emu_rk4_step(void* h, const fnpf_prism_opts* o, const double* hh, double* eta, double* phis, double dt,

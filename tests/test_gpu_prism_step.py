@@ -115,3 +115,36 @@ def test_rk4_steps_match_oracle(fnpf, p, linear):
         assert all(i["status"] == 0 for i in infos) and max(i["iters"] for i in infos) > 0
         eo, po = P.rk4_step(pm, h, eo, po, dt, C.G, linear=linear)
     assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10
+
+
+@pytest.mark.parametrize("p, alpha, order, cutoff", [(3, 2.0, 2, 0), (4, 36.0, 4, 1), (6, 1.0, 8, 3)])
+def test_modal_filter_matches_oracle(fnpf, p, alpha, order, cutoff):
+    v, t, pm = C.mesh(p, 1)
+    gm = fnpf.PrismMesh(v, t, p, 1)
+    f = np.random.default_rng(p).standard_normal(pm.ns)
+    gm.set_filter(alpha, order, cutoff)
+    fd = T(f)
+    gm.filter_apply(fd)
+    ref = P.apply_filter(pm.tm, f, alpha, order, cutoff)
+    assert np.max(np.abs(fd.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(f))
+    gm.set_filter(0.0)
+    with pytest.raises(fnpf.FnpfError) as e:
+        gm.filter_apply(fd)
+    assert e.value.status == fnpf.FNPF_EINVAL
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_filtered_rk4_steps_match_oracle(fnpf, p):
+    nz = 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, _ = C.standing_wave(pm)
+    phis = C.fields(pm)[2]
+    gm.set_filter(4.0, 2, 1)
+    e1, p1, hd = T(eta), T(phis), T(h)
+    eo, po = eta.copy(), phis.copy()
+    for _ in range(2):
+        gm.rk4_step(hd, e1, p1, 0.02, opts(fnpf))
+        eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
+        eo, po = P.apply_filter(pm.tm, eo, 4.0, 2, 1), P.apply_filter(pm.tm, po, 4.0, 2, 1)
+    assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10

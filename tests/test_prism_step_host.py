@@ -118,6 +118,38 @@ def test_rk4_steps_match_oracle(harness, p, linear):
     assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
 
 
+@pytest.mark.parametrize("p, alpha, order, cutoff", [(3, 2.0, 2, 0), (4, 36.0, 4, 1), (5, 8.0, 2, 2), (6, 1.0, 8, 3)])
+def test_modal_filter_matches_oracle(harness, p, alpha, order, cutoff):
+    v, t, pm = C.mesh(p, 1)
+    em = harness.mesh(v, t, p, 1)
+    f = np.random.default_rng(p).standard_normal(pm.ns)
+    em.set_filter(alpha, order, cutoff)
+    ref = P.apply_filter(pm.tm, f, alpha, order, cutoff)
+    out = em.filter_apply(f)
+    assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(f))
+    assert not np.array_equal(out, f)
+    em.set_filter(0.0)
+    with pytest.raises(AssertionError):
+        em.filter_apply(f)   # no filter set: EINVAL
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_filtered_rk4_steps_match_oracle(harness, p):
+    nz = 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, _ = C.standing_wave(pm)
+    phis = C.fields(pm)[2]
+    em.set_filter(4.0, 2, 1)
+    e1, p1 = eta.copy(), phis.copy()
+    eo, po = eta.copy(), phis.copy()
+    for _ in range(2):
+        assert em.rk4_step(opts(), h, e1, p1, 0.02)[0] == 0
+        eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
+        eo, po = P.apply_filter(pm.tm, eo, 4.0, 2, 1), P.apply_filter(pm.tm, po, 4.0, 2, 1)
+    assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -138,6 +170,10 @@ for p, nz, nx, ny in [(1, 1, 2, 2), (3, 2, 3, 2), (5, 3, 2, 3)]:
     assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
     o.model = 1
     assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
+    if p >= 3:
+        em.set_filter(2.0, 2, 1)
+        em.filter_apply(eta)
+        assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
 print("asan run ok")
 """
 
