@@ -21,7 +21,7 @@ def T(a):
 
 
 def opts(fnpf, rtol=1e-13, max_iter=20000, linear=False):
-    return fnpf.PrismMesh.default_opts(rtol=rtol, max_iter=max_iter, mass_rtol=1e-14, g=C.G,
+    return fnpf.PrismMesh.default_opts(rtol=rtol, max_iter=max_iter, mass_rtol=1e-13, g=C.G,
                                        model=fnpf.FNPF_LINEAR if linear else fnpf.FNPF_NONLINEAR)
 
 
