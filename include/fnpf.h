@@ -517,7 +517,16 @@ const char* fnpf_prism_last_error(const fnpf_prism* mesh);
  *     mass, M k = int f l_i dA (Eq. free_surface_weak; the mass solve by
  *     Jacobi-PCG to mass_rtol on the matrix assembled at the first call);
  *   RK4: the classical four stages and combination, (eta, phis) updated in
- *     place only when all four stages succeed.
+ *     place only when all four stages succeed;
+ *   FNPF_PMG: the CG preconditioner is one p-multigrid V-cycle over the orders
+ *     p, p/2, ..., 1 of the same prisms (rediscretised on the geometry of eta
+ *     and h interpolated to each order; the spaces are nested, so prolongation
+ *     is exact interpolation and restriction its transpose), first-kind
+ *     Chebyshev acceleration of Jacobi on [lmax / cheb_range, lmax] of every
+ *     level as smoother (Saad, Iterative Methods, Alg. 12.1; lmax = 1.1 x the
+ *     largest Ritz value of 12 Jacobi-PCG steps, per solve), Chebyshev of
+ *     degree coarse_iters on the coarsest level: a fixed symmetric positive
+ *     definite preconditioner, so plain PCG converges to the same solution.
  * Arrays are DEVICE pointers owned by the caller: eta, h, phis, w, k_eta,
  * k_phis [Ns]; phi, diag, x, y [N] (layout of fnpf_prism_apply: plane-major,
  * surface plane last).  fnpf_prism_laplace_solve reads phi's interior entries
@@ -525,7 +534,9 @@ const char* fnpf_prism_last_error(const fnpf_prism* mesh);
  * plane).  fnpf_prism_dtn, _rhs and _rk4_step solve into the mesh's own
  * potential, which warm-starts the next solve.  fnpf_prism_diagonal writes the
  * diagonal of A(eta, h) (the Jacobi preconditioner), fnpf_prism_apply_stored
- * y = A(eta, h) x through the stored metric.  opts may be NULL (defaults).
+ * y = A(eta, h) x through the stored metric, fnpf_prism_precond_apply z [N] =
+ * the preconditioner of opts (Jacobi or one V-cycle) applied to the interior
+ * entries of r [N] (z zero on the surface plane).  opts may be NULL (defaults).
  * info: NULL, one struct, or 4 (fnpf_prism_rk4_step, one per stage): iters =
  * Laplace CG iterations, rel_res = ||r|| / ||b||, status; outer_iters = 0 and
  * ms = 0.  The first call on a mesh allocates its workspace (about
@@ -543,11 +554,17 @@ typedef struct {
   int mass_max_iter;       /* its cap (default 5000)                              */
   double g;                /* gravitational acceleration (default 9.81)           */
   int model;               /* FNPF_NONLINEAR (default) or FNPF_LINEAR             */
+  int precond;             /* FNPF_JACOBI (default) or FNPF_PMG                   */
+  int cheb_degree;         /* FNPF_PMG: Chebyshev degree of pre/post smoothing (3) */
+  int coarse_iters;        /* FNPF_PMG: Chebyshev degree on the coarsest level (6) */
+  double cheb_range;       /* FNPF_PMG: smoothers act on [lmax / range, lmax] (40) */
 } fnpf_prism_opts;
 void fnpf_prism_default_opts(fnpf_prism_opts* opts);
 fnpf_status fnpf_prism_diagonal(fnpf_prism* mesh, const double* eta, const double* h, double* diag, void* stream);
 fnpf_status fnpf_prism_apply_stored(fnpf_prism* mesh, const double* eta, const double* h, const double* x, double* y,
                                     void* stream);
+fnpf_status fnpf_prism_precond_apply(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta,
+                                     const double* h, const double* r, double* z, void* stream);
 fnpf_status fnpf_prism_laplace_solve(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta,
                                      const double* h, const double* phis, double* phi, fnpf_solve_info* info,
                                      void* stream);

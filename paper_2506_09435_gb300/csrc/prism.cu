@@ -398,6 +398,8 @@ fnpf_status fnpf_prism_create(const double* verts, int nverts, const int* tris, 
   m->n = p + 1;
   m->nz = nz;
   m->ntri = ntris;
+  m->verts.assign(verts, verts + 2 * (size_t)nverts);
+  m->tris.assign(tris, tris + 3 * (size_t)ntris);
   if (!fnpf::prism_numbering(verts, nverts, tris, ntris, p, &m->tnodes, &m->xs, &m->ys)) {
     g_prism_error = "bad triangle (vertex out of range or repeated)";
     delete m;

@@ -17,6 +17,8 @@ struct fnpf_prism {
   int64_t N = 0;
   std::vector<int> tnodes;   // host copy [ntri][nt]
   std::vector<double> xs, ys;
+  std::vector<double> verts;  // host copy [nverts][2] (the coarser orders of the p-multigrid)
+  std::vector<int> tris;      // host copy [ntri][3]
   int* d_tnodes = nullptr;
   double* d_tab = nullptr;   // geo [ntri][4], L, Lr, Ls [nq][nt], wq [nq], xi, wv [n], D [n][n]
   double* d_ye = nullptr;    // element results [ntri * nz][nt * n]

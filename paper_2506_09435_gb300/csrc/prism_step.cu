@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fnpf_internal.cuh"
@@ -17,9 +18,6 @@
 #include "prism_step.h"
 
 namespace fnpf {
-
-bool prism_tables(int p, std::vector<double>* rn, std::vector<double>* sn, std::vector<double>* wq,
-                  std::vector<double>* L, std::vector<double>* Lr, std::vector<double>* Ls);   // prism.cu
 
 constexpr int kItemThreads = 256;
 
@@ -60,6 +58,9 @@ struct PrismStepState {
   double* d_mdiag = nullptr;
   double* d_filt = nullptr;    // [nt][nt] the modal filter (at the first fnpf_prism_set_filter)
   int* d_interior = nullptr;   // [nt]
+  pstep::PMG pmg{};            // the p-multigrid hierarchy (at the first FNPF_PMG call)
+  bool pmg_ready = false;
+  std::vector<void*> pmg_bufs;
 };
 
 void prism_step_free(fnpf_prism* m) {
@@ -74,6 +75,7 @@ void prism_step_free(fnpf_prism* m) {
   cudaFree(st->d_mdiag);
   cudaFree(st->d_filt);
   cudaFree(st->d_interior);
+  for (void* b : st->pmg_bufs) cudaFree(b);
   delete st;
   m->step = nullptr;
 }
@@ -154,16 +156,60 @@ fnpf_status ensure_step(fnpf_prism* m) {
   return FNPF_OK;
 }
 
+// The p-multigrid hierarchy of m on the device (built at the first FNPF_PMG call).
+fnpf_status ensure_pmg(fnpf_prism* m) {
+  PrismStepState* st = m->step;
+  if (st->pmg_ready) return FNPF_OK;
+  bool ok = true;
+  auto up = [&](const auto& v) {
+    using T = typename std::decay_t<decltype(v)>::value_type;
+    T* d = nullptr;
+    if (cudaMalloc(&d, sizeof(T) * std::max<size_t>(1, v.size())) != cudaSuccess) {
+      ok = false;
+      return (const T*)nullptr;
+    }
+    st->pmg_bufs.push_back(d);
+    if (!v.empty() && cudaMemcpy(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+    return (const T*)d;
+  };
+  auto take = [&](double** p, int64_t cnt) {
+    *p = nullptr;
+    double* d = nullptr;
+    if (cudaMalloc(&d, sizeof(double) * std::max<int64_t>(1, cnt)) != cudaSuccess ||
+        cudaMemset(d, 0, sizeof(double) * std::max<int64_t>(1, cnt)) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    st->pmg_bufs.push_back(d);
+    *p = d;
+  };
+  const int nverts = (int)(m->verts.size() / 2);
+  const bool built = pstep::build_pmg(st->pm, st->w, m->verts.data(), nverts, m->tris.data(), m->nz, &st->pmg, up, take);
+  if (ok && built && cudaDeviceSynchronize() == cudaSuccess) {
+    st->pmg_ready = true;
+    return FNPF_OK;
+  }
+  for (void* b : st->pmg_bufs) cudaFree(b);
+  st->pmg_bufs.clear();
+  st->pmg = pstep::PMG{};
+  m->err = ok ? "prism p-multigrid set-up failed" : "prism p-multigrid: device allocation failed";
+  return ok ? FNPF_EINVAL : FNPF_ENOMEM;
+}
+
 fnpf_status check_opts(const fnpf_prism_opts* o, pstep::Params* p, std::string* why) {
   fnpf_prism_opts d;
   fnpf_prism_default_opts(&d);
   if (!o) o = &d;
   if (!(o->rtol > 0) || !(o->mass_rtol > 0) || o->max_iter < 0 || o->mass_max_iter < 0 || !isfinite(o->g) ||
-      (o->model != FNPF_NONLINEAR && o->model != FNPF_LINEAR)) {
-    *why = "bad options (rtol, mass_rtol > 0; iteration caps >= 0; finite g; model NONLINEAR or LINEAR)";
+      (o->model != FNPF_NONLINEAR && o->model != FNPF_LINEAR) ||
+      (o->precond != FNPF_JACOBI && o->precond != FNPF_PMG) || o->cheb_degree < 1 || o->coarse_iters < 1 ||
+      !(o->cheb_range > 1) || !isfinite(o->cheb_range)) {
+    *why = "bad options (rtol, mass_rtol > 0; iteration caps >= 0; finite g; model NONLINEAR or LINEAR; precond "
+           "JACOBI or PMG; Chebyshev degrees >= 1; cheb_range > 1)";
     return FNPF_EINVAL;
   }
-  *p = pstep::Params{o->rtol, o->max_iter, o->mass_rtol, o->mass_max_iter, o->g, o->model == FNPF_LINEAR};
+  *p = pstep::Params{o->rtol,         o->max_iter, o->mass_rtol,   o->mass_max_iter, o->g, o->model == FNPF_LINEAR,
+                     o->precond == FNPF_PMG, o->cheb_degree, o->coarse_iters, o->cheb_range};
   return FNPF_OK;
 }
 
@@ -178,8 +224,9 @@ fnpf_status with_stepper(fnpf_prism* m, const fnpf_prism_opts* opts, void* strea
     return st;
   }
   if ((st = ensure_step(m)) != FNPF_OK) return st;
+  if (prm.pmg && (st = ensure_pmg(m)) != FNPF_OK) return st;
   DeviceEx ex{(cudaStream_t)stream};
-  pstep::Stepper<DeviceEx> sp{m->step->pm, m->step->w, ex};
+  pstep::Stepper<DeviceEx> sp{m->step->pm, m->step->w, ex, prm.pmg ? &m->step->pmg : nullptr};
   st = f(sp, prm);
   if (st == FNPF_ECUDA) {
     m->err = std::string(what) + ": " + cudaGetErrorString(cudaGetLastError());
@@ -202,6 +249,10 @@ void fnpf_prism_default_opts(fnpf_prism_opts* o) {
   o->mass_max_iter = 5000;
   o->g = 9.81;
   o->model = FNPF_NONLINEAR;
+  o->precond = FNPF_JACOBI;
+  o->cheb_degree = 3;
+  o->coarse_iters = 6;
+  o->cheb_range = 40.0;
 }
 
 fnpf_status fnpf_prism_diagonal(fnpf_prism* m, const double* eta, const double* h, double* diag, void* stream) {
@@ -220,6 +271,14 @@ fnpf_status fnpf_prism_apply_stored(fnpf_prism* m, const double* eta, const doub
     fnpf_status st = sp.geometry(eta, h);
     if (st == FNPF_OK) st = sp.apply(x, y);
     return st;
+  });
+}
+
+fnpf_status fnpf_prism_precond_apply(fnpf_prism* m, const fnpf_prism_opts* opts, const double* eta, const double* h,
+                                     const double* r, double* z, void* stream) {
+  if (!m || !eta || !h || !r || !z) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, opts, stream, "prism preconditioner", [&](auto& sp, const fnpf::pstep::Params& p) {
+    return sp.precond_apply(eta, h, r, z, p);
   });
 }
 

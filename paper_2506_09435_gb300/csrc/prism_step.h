@@ -280,6 +280,159 @@ inline bool triangle_filter(int p, const double* rn, const double* sn, double al
 }
 
 // ---------------------------------------------------------------------------
+// The p-multigrid hierarchy (host set-up).  Levels p = q_0 > q_1 > ... > 1,
+// q_(l+1) = floor(q_l / 2): the same prisms at lower order, their operators
+// rediscretised on the eta-following geometry (eta and h interpolated to each
+// level).  The order-q spaces are nested (degree-q polynomials on the triangle
+// times degree-q polynomials in the vertical), so prolongation is exact
+// interpolation and restriction its transpose.
+
+}  // namespace pstep
+
+// Host functions of the library (prism.cu, mesh.cu).
+void gll_tables(int p, double* xi, double* w, double* D);
+bool prism_tables(int p, std::vector<double>* rn, std::vector<double>* sn, std::vector<double>* wq,
+                  std::vector<double>* L, std::vector<double>* Lr, std::vector<double>* Ls);
+bool prism_numbering(const double* verts, int nverts, const int* tris, int ntri, int p, std::vector<int>* tnodes,
+                     std::vector<double>* xs, std::vector<double>* ys);
+
+namespace pstep {
+
+constexpr int kMaxLevels = 4;   // p <= 8: 8, 4, 2, 1
+
+// Volume node g -> its element results (elem nt n + m nt + c), in (element,
+// local node) order.
+inline void volume_incidence(const int* tn, int ntri, int nt, int nz, int p, int64_t ns, std::vector<int64_t>* off,
+                             std::vector<int64_t>* inc) {
+  const int n = p + 1;
+  const int64_t N = ((int64_t)nz * p + 1) * ns;
+  off->assign(N + 1, 0);
+  for (int t = 0; t < ntri; ++t)
+    for (int l = 0; l < nz; ++l)
+      for (int mm = 0; mm < n; ++mm)
+        for (int q = 0; q < nt; ++q) ++(*off)[(int64_t)(l * p + mm) * ns + tn[(size_t)t * nt + q] + 1];
+  for (int64_t g = 0; g < N; ++g) (*off)[g + 1] += (*off)[g];
+  inc->assign((*off)[N], 0);
+  std::vector<int64_t> fill(off->begin(), off->end() - 1);
+  for (int t = 0; t < ntri; ++t)
+    for (int l = 0; l < nz; ++l)
+      for (int mm = 0; mm < n; ++mm)
+        for (int q = 0; q < nt; ++q) {
+          const int64_t g = (int64_t)(l * p + mm) * ns + tn[(size_t)t * nt + q];
+          (*inc)[fill[g]++] = ((int64_t)t * nz + l) * nt * n + (int64_t)mm * nt + q;
+        }
+}
+
+// Host data of one level: numbering, packed tables (the layout of bind_tables),
+// volume and surface incidences, triangle node coordinates.
+struct LevelHost {
+  int q = 0, nt = 0, nq = 0;
+  int64_t ns = 0;
+  std::vector<int> tn;
+  std::vector<double> tab, rn, sn;
+  std::vector<int64_t> voff, vinc, soff, sinc;
+};
+
+inline bool build_level(const double* verts, int nverts, const int* tris, int ntri, int q, int nz, LevelHost* L) {
+  std::vector<double> xs, ys, wq, Lq, Lr, Ls;
+  if (!prism_numbering(verts, nverts, tris, ntri, q, &L->tn, &xs, &ys)) return false;
+  if (!prism_tables(q, &L->rn, &L->sn, &wq, &Lq, &Lr, &Ls)) return false;
+  L->q = q;
+  L->nt = (int)L->rn.size();
+  L->nq = (int)wq.size();
+  L->ns = (int64_t)xs.size();
+  const int n = q + 1;
+  std::vector<double> xi(n), wv(n), D(n * n);
+  gll_tables(q, xi.data(), wv.data(), D.data());
+  L->tab.clear();
+  for (int t = 0; t < ntri; ++t) {
+    const int A = tris[3 * t], B = tris[3 * t + 1], C = tris[3 * t + 2];
+    L->tab.push_back(0.5 * (verts[2 * B] - verts[2 * A]));
+    L->tab.push_back(0.5 * (verts[2 * C] - verts[2 * A]));
+    L->tab.push_back(0.5 * (verts[2 * B + 1] - verts[2 * A + 1]));
+    L->tab.push_back(0.5 * (verts[2 * C + 1] - verts[2 * A + 1]));
+  }
+  for (const std::vector<double>* v : {&Lq, &Lr, &Ls, &wq, &xi, &wv, &D}) L->tab.insert(L->tab.end(), v->begin(), v->end());
+  volume_incidence(L->tn.data(), ntri, L->nt, nz, q, L->ns, &L->voff, &L->vinc);
+  surface_incidence(L->tn.data(), ntri, L->nt, L->ns, &L->soff, &L->sinc);
+  return true;
+}
+
+// Values [npts][nt] of the order-q nodal basis (nodes rn, sn) at the points
+// (r, s): the Dubiner basis at the points times the inverse of its values at
+// the nodes (both span the degree-q polynomials).
+inline bool nodal_basis_at(int q, const std::vector<double>& rn, const std::vector<double>& sn, int npts,
+                           const double* r, const double* s, std::vector<double>* out) {
+  std::vector<std::pair<int, int>> idx;
+  for (int j = 0; j <= q; ++j)
+    for (int i = 0; i + j <= q; ++i) idx.emplace_back(i, j);
+  const int nt = (int)idx.size();
+  std::vector<long double> A((size_t)nt * nt), Vi((size_t)nt * nt, 0.0L);
+  for (int a = 0; a < nt; ++a)
+    for (int k = 0; k < nt; ++k) A[(size_t)a * nt + k] = dubiner(idx[k].first, idx[k].second, rn[a], sn[a]);
+  for (int i = 0; i < nt; ++i) Vi[(size_t)i * nt + i] = 1;
+  for (int c = 0; c < nt; ++c) {   // Gauss-Jordan with partial pivoting
+    int piv = c;
+    for (int r2 = c + 1; r2 < nt; ++r2)
+      if (fabsl(A[(size_t)r2 * nt + c]) > fabsl(A[(size_t)piv * nt + c])) piv = r2;
+    if (fabsl(A[(size_t)piv * nt + c]) < 1e-300L) return false;
+    for (int k = 0; k < nt; ++k) {
+      std::swap(A[(size_t)c * nt + k], A[(size_t)piv * nt + k]);
+      std::swap(Vi[(size_t)c * nt + k], Vi[(size_t)piv * nt + k]);
+    }
+    const long double d = A[(size_t)c * nt + c];
+    for (int k = 0; k < nt; ++k) {
+      A[(size_t)c * nt + k] /= d;
+      Vi[(size_t)c * nt + k] /= d;
+    }
+    for (int r2 = 0; r2 < nt; ++r2) {
+      if (r2 == c) continue;
+      const long double f = A[(size_t)r2 * nt + c];
+      if (f == 0) continue;
+      for (int k = 0; k < nt; ++k) {
+        A[(size_t)r2 * nt + k] -= f * A[(size_t)c * nt + k];
+        Vi[(size_t)r2 * nt + k] -= f * Vi[(size_t)c * nt + k];
+      }
+    }
+  }
+  // A psi-values matrix V[a][k] = psi_k(node a); l_c(x) = sum_k psi_k(x) (V^-1)[k][c]
+  out->assign((size_t)npts * nt, 0.0);
+  std::vector<long double> ps(nt);
+  for (int i = 0; i < npts; ++i) {
+    for (int k = 0; k < nt; ++k) ps[k] = dubiner(idx[k].first, idx[k].second, r[i], s[i]);
+    for (int c = 0; c < nt; ++c) {
+      long double v = 0;
+      for (int k = 0; k < nt; ++k) v += ps[k] * Vi[(size_t)k * nt + c];
+      (*out)[(size_t)i * nt + c] = (double)v;
+    }
+  }
+  return true;
+}
+
+// Transfer tables between a fine level f and the next coarser level c:
+// Ptri [nt_f][nt_c] (coarse nodal basis at the fine triangle nodes), Pv
+// [n_f][n_c] (coarse GLL Lagrange basis at the fine GLL nodes), Etri
+// [nt_c][nt_f] (fine nodal basis at the coarse triangle nodes).
+inline bool transfer_tables(const LevelHost& f, const LevelHost& c, std::vector<double>* Ptri, std::vector<double>* Pv,
+                            std::vector<double>* Etri) {
+  if (!nodal_basis_at(c.q, c.rn, c.sn, f.nt, f.rn.data(), f.sn.data(), Ptri)) return false;
+  if (!nodal_basis_at(f.q, f.rn, f.sn, c.nt, c.rn.data(), c.sn.data(), Etri)) return false;
+  const int nf = f.q + 1, nc = c.q + 1;
+  std::vector<double> xf(nf), xc(nc), w(std::max(nf, nc)), D((size_t)std::max(nf, nc) * std::max(nf, nc));
+  gll_tables(f.q, xf.data(), w.data(), D.data());
+  gll_tables(c.q, xc.data(), w.data(), D.data());
+  Pv->assign((size_t)nf * nc, 0.0);
+  for (int i = 0; i < nf; ++i)
+    for (int j = 0; j < nc; ++j) {
+      long double v = 1;
+      for (int k = 0; k < nc; ++k)
+        if (k != j) v *= ((long double)xf[i] - xc[k]) / ((long double)xc[j] - xc[k]);
+      (*Pv)[(size_t)i * nc + j] = (double)v;
+    }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // Items.
 
 // Prism point (elem, k, q) of item i over nelem n nq; elem = triangle nz + layer.
@@ -728,6 +881,234 @@ struct FilterWriteItem {
   }
 };
 
+// The p-multigrid items.  A level's mesh view is a PMesh of its own order.
+
+struct PXfer {
+  const double *Ptri, *Pv, *Etri;   // transfer_tables, fine level -> next coarser level
+};
+
+// x_f[g] += (P x_c)[g] at every interior fine node g: the coarse element
+// polynomial of the node's first element evaluated at the node.
+struct ProlongItem {
+  struct Args {
+    PMesh f, c;
+    PXfer t;
+    const double* xc;
+    double* xf;
+  };
+  FNPF_HD static void at(int64_t g, const Args& a) {
+    if (g >= a.f.NI) return;
+    const int64_t slot = a.f.vinc[a.f.voff[g]];
+    const int64_t per = (int64_t)a.f.nt * a.f.n;
+    const int64_t elem = slot / per;
+    const int idx = (int)(slot - elem * per);
+    const int cf = idx % a.f.nt, mf = idx / a.f.nt;
+    const int e = (int)(elem / a.f.nz), l = (int)(elem - (int64_t)e * a.f.nz);
+    const int* tnc = a.c.tn + (int64_t)e * a.c.nt;
+    const double* Pt = a.t.Ptri + (int64_t)cf * a.c.nt;
+    const double* Pv = a.t.Pv + (int64_t)mf * a.c.n;
+    double s = 0;
+    for (int mc = 0; mc < a.c.n; ++mc) {
+      const double* xp = a.xc + ((int64_t)l * a.c.p + mc) * a.c.ns;
+      double sc = 0;
+      for (int k = 0; k < a.c.nt; ++k) sc += Pt[k] * xp[tnc[k]];
+      s += Pv[mc] * sc;
+    }
+    a.xf[g] += s;
+  }
+};
+
+// Element result of coarse local node (c', m') of coarse element elem: the
+// transposed interpolation of the fine residual, each fine node's value
+// divided by the number of fine elements that share it (so that the gather
+// over the coarse elements gives P^T r exactly).
+struct RestrictItem {
+  struct Args {
+    PMesh f, c;
+    PXfer t;
+    const double* rf;
+    double* yec;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const int64_t per = (int64_t)a.c.nt * a.c.n;
+    const int64_t elem = i / per;
+    const int idx = (int)(i - elem * per);
+    const int cc = idx % a.c.nt, mc = idx / a.c.nt;
+    const int e = (int)(elem / a.c.nz), l = (int)(elem - (int64_t)e * a.c.nz);
+    const int* tnf = a.f.tn + (int64_t)e * a.f.nt;
+    double s = 0;
+    for (int mf = 0; mf < a.f.n; ++mf) {
+      const double pv = a.t.Pv[(int64_t)mf * a.c.n + mc];
+      const int64_t plane = ((int64_t)l * a.f.p + mf) * a.f.ns;
+      double sf = 0;
+      for (int k = 0; k < a.f.nt; ++k) {
+        const int64_t g = plane + tnf[k];
+        const double mult = (double)(a.f.voff[g + 1] - a.f.voff[g]);
+        sf += a.t.Ptri[(int64_t)k * a.c.nt + cc] * a.rf[g] / mult;
+      }
+      s += pv * sf;
+    }
+    a.yec[i] = s;
+  }
+};
+
+// eta and h at coarse surface node J: the fine triangle polynomial of J's
+// first triangle evaluated at J.
+struct CoarseGeoItem {
+  struct Args {
+    PMesh f, c;
+    PXfer t;
+    const double *etaf, *hf;
+    double *etac, *hc;
+  };
+  FNPF_HD static void at(int64_t J, const Args& a) {
+    const int64_t slot = a.c.sinc[a.c.soff[J]];
+    const int tri = (int)(slot / a.c.nt), cc = (int)(slot - (int64_t)tri * a.c.nt);
+    const int* tnf = a.f.tn + (int64_t)tri * a.f.nt;
+    const double* Et = a.t.Etri + (int64_t)cc * a.f.nt;
+    double se = 0, sh = 0;
+    for (int k = 0; k < a.f.nt; ++k) {
+      se += Et[k] * a.etaf[tnf[k]];
+      sh += Et[k] * a.hf[tnf[k]];
+    }
+    a.etac[J] = se;
+    a.hc[J] = sh;
+  }
+};
+
+// One Chebyshev step: d = s d + c D^-1 r, x += d.
+struct ChebItem {
+  struct Args {
+    double s, c;
+    const double *r, *diag;
+    double *d, *x;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const double d = a.s * a.d[i] + a.c * a.r[i] / a.diag[i];
+    a.d[i] = d;
+    a.x[i] += d;
+  }
+};
+
+// A fixed pseudo-random vector in [-1, 1) on the interior (splitmix64 of the
+// index), zero on the surface plane: the start of the eigenvalue estimate.
+struct HashItem {
+  struct Args {
+    int64_t NI;
+    double* x;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    if (i >= a.NI) {
+      a.x[i] = 0.0;
+      return;
+    }
+    uint64_t z = (uint64_t)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    a.x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+};
+
+// A level of the hierarchy: its mesh view and workspace (level 0: the mesh's own).
+struct PLevel {
+  PMesh m;
+  double *G, *F, *ye, *diag;   // metric, fluxes, element results, Jacobi diagonal
+  double *eta, *h;             // [ns] geometry (level 0: the caller's arrays)
+  double *x, *b, *r, *d, *q;   // [N] smoother and V-cycle vectors
+  double lo, hi;               // Chebyshev interval of D^-1 A
+};
+
+struct PMG {
+  int nlev = 0;
+  PLevel lev[kMaxLevels];
+  PXfer xf[kMaxLevels];        // xf[l]: level l -> l + 1
+};
+
+// The orders of the hierarchy for order p: p, p/2, ..., 1.
+inline int pmg_orders(int p, int* q) {
+  int n = 0;
+  for (int o = p; n < kMaxLevels; o /= 2) {
+    q[n++] = o;
+    if (o == 1) break;
+  }
+  return n;
+}
+
+// Workspace of level l >= 1 (take(&ptr, count) as carve), and of level 0's vectors.
+template <class Take>
+void carve_level(const PMesh& m, bool own_operator, PLevel* L, Take take) {
+  const int64_t pts = m.nelem * m.n * m.nq;
+  if (own_operator) {
+    take(&L->G, pts * 6);
+    take(&L->F, pts * 3);
+    take(&L->ye, m.nelem * m.nt * m.n);
+    take(&L->diag, m.N);
+    take(&L->eta, m.ns);
+    take(&L->h, m.ns);
+  }
+  double** v[] = {&L->x, &L->b, &L->r, &L->d, &L->q};
+  for (double** p : v) take(p, m.N);
+}
+
+// The hierarchy of a mesh of order p over the triangles (verts, tris), level 0
+// being the mesh's own view m0 and workspace w0.  up(vector) returns a copy of
+// a host vector in the memory the items read (null on failure), take(&ptr,
+// count) a zeroed buffer of count doubles.  False on a failure of either or of
+// the host set-up.
+template <class Up, class Take>
+bool build_pmg(const PMesh& m0, const PWork& w0, const double* verts, int nverts, const int* tris, int nz, PMG* pmg,
+               Up up, Take take) {
+  int q[kMaxLevels];
+  const int nl = pmg_orders(m0.p, q);
+  std::vector<LevelHost> H(nl);
+  for (int l = 0; l < nl; ++l)
+    if (!build_level(verts, nverts, tris, m0.ntri, q[l], nz, &H[l])) return false;
+  pmg->nlev = nl;
+  PLevel& L0 = pmg->lev[0];
+  L0 = PLevel{};
+  L0.m = m0;
+  L0.G = w0.G;
+  L0.F = w0.F;
+  L0.ye = w0.ye;
+  L0.diag = w0.diag;
+  carve_level(m0, false, &L0, take);
+  for (int l = 1; l < nl; ++l) {
+    PMesh pm{};
+    pm.p = q[l];
+    pm.n = q[l] + 1;
+    pm.nz = nz;
+    pm.nt = H[l].nt;
+    pm.nq = H[l].nq;
+    pm.ntri = m0.ntri;
+    pm.ns = H[l].ns;
+    pm.nv = (int64_t)nz * q[l] + 1;
+    pm.N = pm.nv * pm.ns;
+    pm.NI = pm.N - pm.ns;
+    pm.nelem = m0.nelem;
+    pm.tn = up(H[l].tn);
+    const double* tab = up(H[l].tab);
+    if (!pm.tn || !tab) return false;
+    bind_tables(&pm, tab);
+    pm.voff = up(H[l].voff);
+    pm.vinc = up(H[l].vinc);
+    pm.soff = up(H[l].soff);
+    pm.sinc = up(H[l].sinc);
+    if (!pm.voff || !pm.vinc || !pm.soff || !pm.sinc) return false;
+    PLevel& L = pmg->lev[l];
+    L = PLevel{};
+    L.m = pm;
+    carve_level(pm, true, &L, take);
+  }
+  for (int l = 0; l + 1 < nl; ++l) {
+    std::vector<double> Pt, Pv, Et;
+    if (!transfer_tables(H[l], H[l + 1], &Pt, &Pv, &Et)) return false;
+    pmg->xf[l] = PXfer{up(Pt), up(Pv), up(Et)};
+    if (!pmg->xf[l].Ptri || !pmg->xf[l].Pv || !pmg->xf[l].Etri) return false;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Orchestration.
 
@@ -738,6 +1119,10 @@ struct Params {
   int mass_max_iter;
   double g;
   int linear;
+  int pmg;            // 1: p-multigrid V-cycle preconditioner, 0: Jacobi
+  int cheb_degree;    // Chebyshev degree of the pre- and post-smoothing
+  int coarse_degree;  // Chebyshev degree on the coarsest level
+  double cheb_range;  // the smoothers act on [lmax / cheb_range, lmax]
 };
 
 #define FNPF_PS_TRY(x)                   \
@@ -751,6 +1136,7 @@ struct Stepper {
   const PMesh& m;
   const PWork& w;
   Ex& ex;
+  PMG* pmg = nullptr;   // the hierarchy (needed when Params::pmg is set)
 
   template <class It>
   fnpf_status go(int64_t n, const typename It::Args& a) {
@@ -784,13 +1170,157 @@ struct Stepper {
     return go<GatherItem>(m.N, {m.voff, m.vinc, w.ye, y});
   }
 
+  // ---- p-multigrid
+
+  fnpf_status geometry_level(PLevel& L, const double* eta, const double* h) {
+    FNPF_PS_TRY(go<GeomItem>(L.m.nelem * L.m.n * L.m.nq, {L.m, eta, h, L.G}));
+    FNPF_PS_TRY(go<DiagItem>(L.m.nelem * L.m.nt * L.m.n, {L.m, L.G, L.ye}));
+    return go<GatherItem>(L.m.N, {L.m.voff, L.m.vinc, L.ye, L.diag});
+  }
+
+  fnpf_status apply_level(PLevel& L, const double* x, double* y) {
+    FNPF_PS_TRY(go<FluxItem>(L.m.nelem * L.m.n * L.m.nq, {L.m, L.G, x, L.F}));
+    FNPF_PS_TRY(go<NodeItem>(L.m.nelem * L.m.nt * L.m.n, {L.m, L.F, L.ye}));
+    return go<GatherItem>(L.m.N, {L.m.voff, L.m.vinc, L.ye, y});
+  }
+
+  // Largest eigenvalue of D^-1 A_II on a level: the Lanczos tridiagonal matrix of
+  // k Jacobi-PCG steps from a fixed pseudo-random right-hand side (its largest
+  // eigenvalue by bisection on the Sturm sequence).
+  fnpf_status lmax_level(PLevel& L, double* out) {
+    const int64_t N = L.m.N, NI = L.m.NI;
+    const int k_max = 12;
+    double al[k_max], be[k_max];
+    FNPF_PS_TRY(go<HashItem>(N, {NI, L.r}));
+    FNPF_PS_TRY(go<DivItem>(NI, {L.r, L.diag, L.x}));
+    FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, L.x, L.d}));
+    double rz = 0;
+    FNPF_PS_TRY(dot(L.r, L.x, NI, &rz));
+    int k = 0;
+    for (; k < k_max && rz > 0; ++k) {
+      FNPF_PS_TRY(apply_level(L, L.d, L.q));
+      double pq = 0;
+      FNPF_PS_TRY(dot(L.d, L.q, NI, &pq));
+      if (!(pq > 0)) break;
+      al[k] = rz / pq;
+      FNPF_PS_TRY(go<AxpyItem>(NI, {-al[k], L.q, L.r}));
+      FNPF_PS_TRY(go<DivItem>(NI, {L.r, L.diag, L.x}));
+      double rzn = 0;
+      FNPF_PS_TRY(dot(L.r, L.x, NI, &rzn));
+      be[k] = rzn / rz;
+      rz = rzn;
+      FNPF_PS_TRY(go<XpbyItem>(NI, {L.x, be[k], L.d}));
+    }
+    if (k == 0) return FNPF_EBREAKDOWN;
+    // T[j][j] = 1/al_j + be_(j-1)/al_(j-1), T[j][j-1] = sqrt(be_(j-1))/al_(j-1)
+    double dg[k_max], off[k_max];
+    for (int j = 0; j < k; ++j) {
+      dg[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+      off[j] = j > 0 ? sqrt(be[j - 1]) / al[j - 1] : 0.0;
+    }
+    double hi = 0;
+    for (int j = 0; j < k; ++j) hi = std::max(hi, dg[j] + fabs(off[j]) + (j + 1 < k ? fabs(off[j + 1]) : 0.0));
+    double lo = 0;
+    for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {   // count of eigenvalues above mid
+      const double mid = 0.5 * (lo + hi);
+      int below = 0;   // negative pivots of T - mid I count the eigenvalues below mid
+      double q = 1;
+      for (int j = 0; j < k; ++j) {
+        q = (dg[j] - mid) - (j > 0 ? off[j] * off[j] / q : 0.0);
+        if (q == 0) q = -1e-300;
+        if (q < 0) ++below;
+      }
+      if (below < k) lo = mid;   // an eigenvalue lies above mid
+      else hi = mid;
+    }
+    *out = hi;
+    return FNPF_OK;
+  }
+
+  // Geometry, diagonals and Chebyshev intervals of every level for (eta, h);
+  // level 0's geometry is current.
+  fnpf_status setup_pmg(const double* eta, const double* h, const Params& o) {
+    pmg->lev[0].eta = const_cast<double*>(eta);
+    pmg->lev[0].h = const_cast<double*>(h);
+    for (int l = 0; l < pmg->nlev; ++l) {
+      PLevel& L = pmg->lev[l];
+      if (l > 0) {
+        PLevel& F = pmg->lev[l - 1];
+        FNPF_PS_TRY(go<CoarseGeoItem>(L.m.ns, {F.m, L.m, pmg->xf[l - 1], F.eta, F.h, L.eta, L.h}));
+        FNPF_PS_TRY(geometry_level(L, L.eta, L.h));
+      }
+      double lmax = 0;
+      FNPF_PS_TRY(lmax_level(L, &lmax));
+      L.hi = 1.1 * lmax;
+      L.lo = L.hi / o.cheb_range;
+    }
+    return FNPF_OK;
+  }
+
+  // deg Chebyshev steps on level L: x and r = b - A x (both in, both out; r
+  // updated at the end only if need_r).
+  fnpf_status cheb(PLevel& L, double* x, double* r, int deg, bool need_r) {
+    const int64_t N = L.m.N, NI = L.m.NI;
+    const double theta = 0.5 * (L.hi + L.lo), delta = 0.5 * (L.hi - L.lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    FNPF_PS_TRY(go<FillItem>(N, {0.0, L.d}));
+    FNPF_PS_TRY(go<ChebItem>(NI, {0.0, 1.0 / theta, r, L.diag, L.d, x}));
+    for (int k = 1; k < deg; ++k) {
+      FNPF_PS_TRY(apply_level(L, L.d, L.q));
+      FNPF_PS_TRY(go<AxpyItem>(NI, {-1.0, L.q, r}));
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      FNPF_PS_TRY(go<ChebItem>(NI, {rn * rho, 2.0 * rn / delta, r, L.diag, L.d, x}));
+      rho = rn;
+    }
+    if (!need_r) return FNPF_OK;
+    FNPF_PS_TRY(apply_level(L, L.d, L.q));
+    return go<AxpyItem>(NI, {-1.0, L.q, r});
+  }
+
+  // x = M_l^-1 b: one V-cycle from x = 0 (b and x: interior values, surface plane zero).
+  fnpf_status vcycle(int l, const double* b, double* x, const Params& o) {
+    PLevel& L = pmg->lev[l];
+    const int64_t N = L.m.N, NI = L.m.NI;
+    FNPF_PS_TRY(go<FillItem>(N, {0.0, x}));
+    FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, b, L.r}));
+    if (l == pmg->nlev - 1) return cheb(L, x, L.r, o.coarse_degree, false);
+    FNPF_PS_TRY(cheb(L, x, L.r, o.cheb_degree, true));
+    PLevel& C = pmg->lev[l + 1];
+    FNPF_PS_TRY(go<RestrictItem>(C.m.nelem * C.m.nt * C.m.n, {L.m, C.m, pmg->xf[l], L.r, C.ye}));
+    FNPF_PS_TRY(go<GatherItem>(C.m.N, {C.m.voff, C.m.vinc, C.ye, C.q}));
+    FNPF_PS_TRY(go<InteriorItem>(C.m.N, {C.m.NI, 1.0, C.q, C.b}));
+    FNPF_PS_TRY(vcycle(l + 1, C.b, C.x, o));
+    FNPF_PS_TRY(go<ProlongItem>(N, {L.m, C.m, pmg->xf[l], C.x, x}));
+    FNPF_PS_TRY(apply_level(L, x, L.q));
+    FNPF_PS_TRY(go<LinItem>(NI, {b, -1.0, L.q, L.r}));
+    return cheb(L, x, L.r, o.cheb_degree, false);
+  }
+
+  // z = M^-1 r: Jacobi or one V-cycle.
+  fnpf_status precond(const double* r, double* z, const Params& o) {
+    if (!o.pmg) return go<DivItem>(m.NI, {r, w.diag, z});
+    return vcycle(0, r, z, o);
+  }
+
+  // z = M^-1 r for the geometry of (eta, h) (r, z [N]; r's surface plane is ignored).
+  fnpf_status precond_apply(const double* eta, const double* h, const double* r, double* z, const Params& o) {
+    if (o.pmg && !pmg) return FNPF_EINVAL;
+    FNPF_PS_TRY(geometry(eta, h));
+    if (o.pmg) FNPF_PS_TRY(setup_pmg(eta, h, o));
+    FNPF_PS_TRY(go<InteriorItem>(m.N, {m.NI, 1.0, r, w.r}));
+    FNPF_PS_TRY(go<FillItem>(m.N, {0.0, z}));
+    return precond(w.r, z, o);
+  }
+
   // phi = the solution of A_II phi_I = -A_IS phis (in: the interior guess),
   // phi = phis on the surface plane; Jacobi-PCG to ||r|| <= rtol ||b||.
   fnpf_status solve(const double* eta, const double* h, const double* phis, double* phi, const Params& o,
                     fnpf_solve_info* info) {
     const int64_t N = m.N, NI = m.NI;
     if (info) *info = fnpf_solve_info{0, 0, 0.0, FNPF_OK, 0.0f};
+    if (o.pmg && !pmg) return FNPF_EINVAL;
     FNPF_PS_TRY(geometry(eta, h));
+    if (o.pmg) FNPF_PS_TRY(setup_pmg(eta, h, o));
     FNPF_PS_TRY(go<SurfaceOnlyItem>(N, {NI, phis, w.xs}));
     FNPF_PS_TRY(apply(w.xs, w.q));
     FNPF_PS_TRY(go<InteriorItem>(N, {NI, -1.0, w.q, w.r}));   // r = b = -A_IS phis
@@ -809,7 +1339,7 @@ struct Stepper {
       FNPF_PS_TRY(go<AxpyItem>(NI, {-1.0, w.q, w.r}));          // r = b - A_II x0
       FNPF_PS_TRY(dot(w.r, w.r, NI, &rr));
       if (sqrt(rr) > stop) {
-        FNPF_PS_TRY(go<DivItem>(NI, {w.r, w.diag, w.z}));
+        FNPF_PS_TRY(precond(w.r, w.z, o));
         FNPF_PS_TRY(go<CopyItem>(NI, {w.z, w.pd}));
         double rz = 0;
         FNPF_PS_TRY(dot(w.r, w.z, NI, &rz));
@@ -835,7 +1365,7 @@ struct Stepper {
             st = FNPF_OK;
             break;
           }
-          FNPF_PS_TRY(go<DivItem>(NI, {w.r, w.diag, w.z}));
+          FNPF_PS_TRY(precond(w.r, w.z, o));
           double rzn = 0;
           FNPF_PS_TRY(dot(w.r, w.z, NI, &rzn));
           const double beta = rzn / rz;

@@ -45,7 +45,9 @@ class Opts(ctypes.Structure):
 
 class PrismOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mass_rtol", ctypes.c_double),
-                ("mass_max_iter", ctypes.c_int), ("g", ctypes.c_double), ("model", ctypes.c_int)]
+                ("mass_max_iter", ctypes.c_int), ("g", ctypes.c_double), ("model", ctypes.c_int),
+                ("precond", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int),
+                ("cheb_range", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -115,6 +117,7 @@ def load():
         "fnpf_prism_filter_apply": [vp, vp, vp],
         "fnpf_prism_apply_stored": [vp, vp, vp, vp, vp, vp],
         "fnpf_prism_laplace_solve": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
+        "fnpf_prism_precond_apply": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp],
         "fnpf_prism_dtn": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_rhs": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_rk4_step": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, ctypes.c_double,
@@ -629,6 +632,15 @@ class PrismMesh:
         ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
                      (x, self.N, "float64", "x"), (y, self.N, "float64", "y"))
         self._check(_LIB.fnpf_prism_apply_stored(self._h, *ptrs, _stream(stream)))
+
+    def precond_apply(self, eta, h, r, z, opts=None, stream=None):
+        """z [N] = the preconditioner of opts (Jacobi or one V-cycle) applied to
+        the interior entries of r [N]."""
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (r, self.N, "float64", "r"), (z, self.N, "float64", "z"))
+        st = _LIB.fnpf_prism_precond_apply(self._h, None if opts is None else ctypes.byref(opts), *ptrs,
+                                           _stream(stream))
+        self._check(st)
 
     def laplace_solve(self, eta, h, phis, phi, opts=None, stream=None):
         """phi [N] (in: interior guess) = the potential with phi = phis on the

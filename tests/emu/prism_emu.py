@@ -42,7 +42,15 @@ def build(out_dir, asan=False):
 
 class PrismOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mass_rtol", ctypes.c_double),
-                ("mass_max_iter", ctypes.c_int), ("g", ctypes.c_double), ("model", ctypes.c_int)]
+                ("mass_max_iter", ctypes.c_int), ("g", ctypes.c_double), ("model", ctypes.c_int),
+                ("precond", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int),
+                ("cheb_range", ctypes.c_double)]
+
+
+def opts(rtol=1e-10, max_iter=20000, mass_rtol=1e-13, g=9.81, linear=False, pmg=False, cheb_degree=3,
+         coarse_iters=6, cheb_range=40.0):
+    return PrismOpts(rtol, max_iter, mass_rtol, 5000, g, int(linear), int(pmg), cheb_degree, coarse_iters,
+                     cheb_range)
 
 
 class SolveInfo(ctypes.Structure):
@@ -65,7 +73,7 @@ class Harness:
         lib.emu_destroy.restype = None
         lib.emu_sizes.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int64)] * 3
         lib.emu_sizes.restype = None
-        sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_laplace_solve": [vp] * 7,
+        sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_laplace_solve": [vp] * 7, "emu_precond_apply": [vp] * 6,
                "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, vp]}
         sig["emu_set_filter"] = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         sig["emu_filter_apply"] = [vp, vp]
@@ -115,6 +123,12 @@ class EmuMesh:
         st = self.lib.emu_laplace_solve(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(phis), _p(phi),
                                         ctypes.byref(info))
         return st, info
+
+    def precond_apply(self, opts, eta, h, r):
+        z = np.zeros(self.N)
+        st = self.lib.emu_precond_apply(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(r), _p(z))
+        assert st == 0, st
+        return z
 
     def dtn(self, opts, eta, h, phis):
         w, info = np.zeros(self.ns), SolveInfo()

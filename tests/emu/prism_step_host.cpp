@@ -11,19 +11,13 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <memory>
+#include <type_traits>
 #include <vector>
 
 #include "fnpf.h"
 #include "prism_step.h"
-
-namespace fnpf {
-void gll_tables(int p, double* xi, double* w, double* D);
-bool prism_tables(int p, std::vector<double>* rn, std::vector<double>* sn, std::vector<double>* wq,
-                  std::vector<double>* L, std::vector<double>* Lr, std::vector<double>* Ls);
-bool prism_numbering(const double* verts, int nverts, const int* tris, int ntri, int p, std::vector<int>* tnodes,
-                     std::vector<double>* xs, std::vector<double>* ys);
-}  // namespace fnpf
 
 namespace {
 
@@ -50,7 +44,30 @@ struct Emu {
   std::vector<int> tn, mcol, interior;
   std::vector<int64_t> voff, vinc, soff, sinc, mrow;
   std::vector<double> mval, mdiag;
+  std::vector<double> verts;
+  std::vector<int> tris;
+  int nz = 0;
+  PMG pmg{};
+  bool pmg_ready = false;
+  std::vector<std::shared_ptr<void>> pbufs;   // hierarchy tables, each its own allocation
   HostEx ex;
+
+  bool ensure_pmg() {
+    if (pmg_ready) return true;
+    auto up = [this](const auto& v) {
+      using T = typename std::decay_t<decltype(v)>::value_type;
+      std::shared_ptr<T> b(new T[std::max<size_t>(1, v.size())](), std::default_delete<T[]>());
+      std::copy(v.begin(), v.end(), b.get());
+      pbufs.push_back(b);
+      return (const T*)b.get();
+    };
+    auto take = [this](double** p, int64_t cnt) {
+      dbufs.emplace_back(new double[cnt > 0 ? cnt : 1]());
+      *p = dbufs.back().get();
+    };
+    pmg_ready = build_pmg(m, w, verts.data(), (int)(verts.size() / 2), tris.data(), nz, &pmg, up, take);
+    return pmg_ready;
+  }
 
   const double* table(const std::vector<double>& v, size_t off, size_t count) {
     dbufs.emplace_back(new double[count]);
@@ -65,6 +82,9 @@ extern "C" {
 
 void* emu_create(const double* verts, int nverts, const int* tris, int ntris, int p, int nz) {
   std::unique_ptr<Emu> e(new Emu());
+  e->verts.assign(verts, verts + 2 * (size_t)nverts);
+  e->tris.assign(tris, tris + 3 * (size_t)ntris);
+  e->nz = nz;
   std::vector<double> xs, ys;
   if (!fnpf::prism_numbering(verts, nverts, tris, ntris, p, &e->tn, &xs, &ys)) return nullptr;
   std::vector<double> rn, sn, wq, L, Lr, Ls;
@@ -102,21 +122,7 @@ void* emu_create(const double* verts, int nverts, const int* tris, int ntris, in
   m.wv = e->table(wv, 0, wv.size());
   m.D = e->table(D, 0, D.size());
   // volume incidence in (element, local node) order, as fnpf_prism_create
-  e->voff.assign(m.N + 1, 0);
-  for (int t = 0; t < ntris; ++t)
-    for (int l = 0; l < nz; ++l)
-      for (int mm = 0; mm < n; ++mm)
-        for (int q = 0; q < nt; ++q) ++e->voff[(int64_t)(l * p + mm) * m.ns + e->tn[(size_t)t * nt + q] + 1];
-  for (int64_t g = 0; g < m.N; ++g) e->voff[g + 1] += e->voff[g];
-  e->vinc.assign(e->voff[m.N], 0);
-  std::vector<int64_t> fill(e->voff.begin(), e->voff.end() - 1);
-  for (int t = 0; t < ntris; ++t)
-    for (int l = 0; l < nz; ++l)
-      for (int mm = 0; mm < n; ++mm)
-        for (int q = 0; q < nt; ++q) {
-          const int64_t g = (int64_t)(l * p + mm) * m.ns + e->tn[(size_t)t * nt + q];
-          e->vinc[fill[g]++] = ((int64_t)t * nz + l) * nt * n + (int64_t)mm * nt + q;
-        }
+  volume_incidence(e->tn.data(), ntris, nt, nz, p, m.ns, &e->voff, &e->vinc);
   m.voff = e->voff.data();
   m.vinc = e->vinc.data();
   surface_incidence(e->tn.data(), ntris, nt, m.ns, &e->soff, &e->sinc);
@@ -148,7 +154,15 @@ static Params params(const fnpf_prism_opts* o) {
   fnpf_prism_opts d;
   fnpf_prism_default_opts(&d);
   if (!o) o = &d;
-  return Params{o->rtol, o->max_iter, o->mass_rtol, o->mass_max_iter, o->g, o->model == FNPF_LINEAR};
+  return Params{o->rtol,         o->max_iter,    o->mass_rtol,    o->mass_max_iter, o->g, o->model == FNPF_LINEAR,
+                o->precond == FNPF_PMG, o->cheb_degree, o->coarse_iters, o->cheb_range};
+}
+
+// A stepper over the harness's memory (with the hierarchy when the options ask for it).
+static Stepper<HostEx> stepper(Emu* e, const Params& prm) {
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  if (prm.pmg && e->ensure_pmg()) sp.pmg = &e->pmg;
+  return sp;
 }
 
 int emu_diagonal(void* h, const double* eta, const double* hh, double* diag) {
@@ -170,22 +184,33 @@ int emu_apply_stored(void* h, const double* eta, const double* hh, const double*
 int emu_laplace_solve(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis,
                       double* phi, fnpf_solve_info* info) {
   Emu* e = static_cast<Emu*>(h);
-  Stepper<HostEx> sp{e->m, e->w, e->ex};
-  return sp.solve(eta, hh, phis, phi, params(o), info);
+  const Params prm = params(o);
+  Stepper<HostEx> sp = stepper(e, prm);
+  return sp.solve(eta, hh, phis, phi, prm, info);
+}
+
+int emu_precond_apply(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* r,
+                      double* z) {
+  Emu* e = static_cast<Emu*>(h);
+  const Params prm = params(o);
+  Stepper<HostEx> sp = stepper(e, prm);
+  return sp.precond_apply(eta, hh, r, z, prm);
 }
 
 int emu_dtn(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis, double* w,
             fnpf_solve_info* info) {
   Emu* e = static_cast<Emu*>(h);
-  Stepper<HostEx> sp{e->m, e->w, e->ex};
-  return sp.dtn(eta, hh, phis, w, params(o), info);
+  const Params prm = params(o);
+  Stepper<HostEx> sp = stepper(e, prm);
+  return sp.dtn(eta, hh, phis, w, prm, info);
 }
 
 int emu_rhs(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis, double* ke,
             double* kp, fnpf_solve_info* info) {
   Emu* e = static_cast<Emu*>(h);
-  Stepper<HostEx> sp{e->m, e->w, e->ex};
-  return sp.rhs(eta, hh, phis, ke, kp, params(o), info);
+  const Params prm = params(o);
+  Stepper<HostEx> sp = stepper(e, prm);
+  return sp.rhs(eta, hh, phis, ke, kp, prm, info);
 }
 
 int emu_set_filter(void* h, double alpha, int order, int cutoff) {
@@ -217,8 +242,9 @@ int emu_filter_apply(void* h, double* f) {
 int emu_rk4_step(void* h, const fnpf_prism_opts* o, const double* hh, double* eta, double* phis, double dt,
                  fnpf_solve_info* info) {
   Emu* e = static_cast<Emu*>(h);
-  Stepper<HostEx> sp{e->m, e->w, e->ex};
-  return sp.rk4(hh, eta, phis, dt, params(o), info);
+  const Params prm = params(o);
+  Stepper<HostEx> sp = stepper(e, prm);
+  return sp.rk4(hh, eta, phis, dt, prm, info);
 }
 
 }  // extern "C"

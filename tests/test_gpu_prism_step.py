@@ -20,9 +20,10 @@ def T(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
 
 
-def opts(fnpf, rtol=1e-13, max_iter=20000, linear=False):
+def opts(fnpf, rtol=1e-13, max_iter=20000, linear=False, pmg=False):
     return fnpf.PrismMesh.default_opts(rtol=rtol, max_iter=max_iter, mass_rtol=1e-13, g=C.G,
-                                       model=fnpf.FNPF_LINEAR if linear else fnpf.FNPF_NONLINEAR)
+                                       model=fnpf.FNPF_LINEAR if linear else fnpf.FNPF_NONLINEAR,
+                                       precond=fnpf.FNPF_PMG if pmg else fnpf.FNPF_JACOBI)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
@@ -147,4 +148,50 @@ def test_filtered_rk4_steps_match_oracle(fnpf, p):
         gm.rk4_step(hd, e1, p1, 0.02, opts(fnpf))
         eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
         eo, po = P.apply_filter(pm.tm, eo, 4.0, 2, 1), P.apply_filter(pm.tm, po, 4.0, 2, 1)
+    assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10
+
+
+@pytest.mark.parametrize("p, nz, nx, ny", [(2, 2, 3, 2), (4, 2, 6, 4), (5, 3, 4, 3)])
+def test_pmg_solve_matches_oracle_in_fewer_iterations(fnpf, p, nz, nx, ny):
+    v, t, pm = C.mesh(p, nz, nx=nx, ny=ny)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi_j = torch.zeros(pm.N, dtype=torch.float64, device=DEV)
+    phi_m = torch.zeros(pm.N, dtype=torch.float64, device=DEV)
+    info_j = gm.laplace_solve(T(eta), T(h), T(phis), phi_j, opts(fnpf))
+    info_m = gm.laplace_solve(T(eta), T(h), T(phis), phi_m, opts(fnpf, pmg=True))
+    assert info_m["status"] == 0 and info_m["rel_res"] <= 1e-13
+    assert C.rel(phi_m.cpu().numpy(), P.laplace_solve(pm, eta, h, phis)) <= 1e-10
+    assert info_m["iters"] * 3 <= info_j["iters"]
+
+
+def test_vcycle_is_symmetric_positive_definite(fnpf):
+    p, nz = 4, 2
+    v, t, pm = C.mesh(p, nz, nx=3, ny=2)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, _ = C.fields(pm)
+    NI = pm.N - pm.ns
+    rng = np.random.default_rng(5)
+    u, w = rng.standard_normal(pm.N), rng.standard_normal(pm.N)
+    u[NI:] = 0
+    w[NI:] = 0
+    Mu, Mw = (torch.zeros(pm.N, dtype=torch.float64, device=DEV) for _ in range(2))
+    gm.precond_apply(T(eta), T(h), T(u), Mu, opts(fnpf, pmg=True))
+    gm.precond_apply(T(eta), T(h), T(w), Mw, opts(fnpf, pmg=True))
+    Mu, Mw = Mu.cpu().numpy(), Mw.cpu().numpy()
+    assert not Mu[NI:].any()
+    assert abs(w @ Mu - u @ Mw) <= 1e-12 * np.linalg.norm(u) * np.linalg.norm(Mw)
+    assert u @ Mu > 0 and w @ Mw > 0
+
+
+def test_pmg_rk4_steps_match_oracle(fnpf):
+    p, nz = 4, 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.standing_wave(pm)
+    e1, p1, hd = T(eta), T(phis), T(h)
+    eo, po = eta.copy(), phis.copy()
+    for _ in range(3):
+        gm.rk4_step(hd, e1, p1, 0.02, opts(fnpf, pmg=True))
+        eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
     assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10

@@ -26,8 +26,8 @@ def harness(tmp_path_factory):
     return E.Harness(E.build(str(tmp_path_factory.mktemp("prism_emu"))))
 
 
-def opts(rtol=1e-13, max_iter=20000, mass_rtol=1e-14, linear=False):
-    return E.PrismOpts(rtol, max_iter, mass_rtol, 5000, C.G, int(linear))
+def opts(rtol=1e-13, max_iter=20000, mass_rtol=1e-14, linear=False, pmg=False):
+    return E.opts(rtol, max_iter, mass_rtol, C.G, linear, pmg)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
@@ -150,6 +150,52 @@ def test_filtered_rk4_steps_match_oracle(harness, p):
     assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
 
 
+@pytest.mark.parametrize("p, nz, nx, ny", [(2, 2, 3, 2), (3, 2, 4, 3), (4, 2, 6, 4), (6, 2, 4, 3), (5, 3, 4, 3)])
+def test_pmg_solve_matches_oracle_in_fewer_iterations(harness, p, nz, nx, ny):
+    v, t, pm = C.mesh(p, nz, nx=nx, ny=ny)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi_j, phi_m = np.zeros(pm.N), np.zeros(pm.N)
+    st, info_j = em.laplace_solve(opts(), eta, h, phis, phi_j)
+    assert st == 0
+    st, info_m = em.laplace_solve(opts(pmg=True), eta, h, phis, phi_m)
+    assert st == 0 and info_m.rel_res <= 1e-13
+    ref = P.laplace_solve(pm, eta, h, phis)
+    assert C.rel(phi_m, ref) <= 1e-10
+    assert info_m.iters * 3 <= info_j.iters
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_vcycle_is_symmetric_positive_definite(harness, p):
+    nz = 2
+    v, t, pm = C.mesh(p, nz, nx=2, ny=2)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, _ = C.fields(pm)
+    NI = pm.N - pm.ns
+    M = np.zeros((NI, NI))
+    for j in range(NI):
+        r = np.zeros(pm.N)
+        r[j] = 1.0
+        z = em.precond_apply(opts(pmg=True), eta, h, r)
+        assert not z[NI:].any()
+        M[:, j] = z[:NI]
+    assert np.max(np.abs(M - M.T)) <= 1e-12 * np.max(np.abs(M))
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_pmg_rk4_steps_match_oracle(harness):
+    p, nz = 4, 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.standing_wave(pm)
+    e1, p1 = eta.copy(), phis.copy()
+    eo, po = eta.copy(), phis.copy()
+    for _ in range(3):
+        assert em.rk4_step(opts(pmg=True), h, e1, p1, 0.02)[0] == 0
+        eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
+    assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -163,7 +209,8 @@ for p, nz, nx, ny in [(1, 1, 2, 2), (3, 2, 3, 2), (5, 3, 2, 3)]:
     eta, h, phis = C.fields(pm)
     em.diagonal(eta, h)
     em.apply_stored(eta, h, np.ones(pm.N))
-    o = E.PrismOpts(1e-10, 20000, 1e-13, 5000, C.G, 0)
+    em.precond_apply(E.opts(g=C.G, pmg=True), eta, h, np.ones(pm.N))
+    o = E.opts(g=C.G, pmg=(p > 1))
     assert em.laplace_solve(o, eta, h, phis, np.zeros(pm.N))[0] == 0
     assert em.dtn(o, eta, h, phis)[0] == 0
     assert em.rhs(o, eta, h, phis)[0] == 0
