@@ -573,7 +573,18 @@ fnpf_status fnpf_prism_dtn(fnpf_prism* mesh, const fnpf_prism_opts* opts, const 
 fnpf_status fnpf_prism_rhs(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta, const double* h,
                            const double* phis, double* k_eta, double* k_phis, fnpf_solve_info* info, void* stream);
 fnpf_status fnpf_prism_rk4_step(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* h, double* eta,
-                                double* phis, double dt, fnpf_solve_info* info, void* stream);
+                                double* phis, double t, double dt, fnpf_solve_info* info, void* stream);
+
+/* Relaxation zones on the prism mesh (Sec. 3.3; Step 4.7): after every
+ * fnpf_prism_rk4_step from t to t + dt, f <- (1 - C_r) f + C_r f_true at every
+ * surface node, the targets of fnpf_set_relaxation (the linear incident wave
+ * with the ramp in generation nodes, zero in absorption nodes) at t + dt with
+ * the node's depth h; then the modal filter, when set.  cr and gen are HOST
+ * arrays [Ns] in the numbering of fnpf_prism_numbering, copied (synchronous);
+ * a NULL relax or cr removes the zones.  Errors: EINVAL (cr outside [0, 1],
+ * a non-finite gen, ramp_time <= 0, non-finite wave parameters, omega <= 0
+ * with generation nodes), ENOMEM, ECUDA. */
+fnpf_status fnpf_prism_set_relaxation(fnpf_prism* mesh, const fnpf_relaxation* relax);
 
 /* Modal filter on the prism mesh's triangular surface elements (Sec. 3.2,
  * modal filtering; applied in Step 4.7).  On every triangle the nodal values

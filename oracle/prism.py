@@ -311,6 +311,24 @@ def rk4_step(pm, h, eta, phis, dt, g, linear=False):
             phis + dt / 6.0 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]))
 
 
+def relaxation_step(pm, h, eta, phis, t, dt, g, cr, gen, wave, linear=False, filt=None):
+    """One RK4 step, then the relaxation-zone blend f <- (1 - C_r) f + C_r f_true
+    toward the linear incident wave where gen = 1 and toward zero where gen = 0,
+    with the targets at t + dt (Sec. 3.3, Step 4.7), at the surface nodes of the
+    triangle mesh; then the modal filter of eta and phi_eta when
+    filt = (alpha, order, cutoff) (after the relaxation, as on the quadrilateral
+    surfaces)."""
+    from . import surface as S
+    eta, phis = rk4_step(pm, h, eta, phis, dt, g, linear)
+    te, tp = S.incident_wave(pm.tm.xs, pm.tm.ys, h, t + dt, g=g, **wave)
+    te = np.where(gen != 0, te, 0.0)
+    tp = np.where(gen != 0, tp, 0.0)
+    eta, phis = S.relax(eta, te, cr), S.relax(phis, tp, cr)
+    if filt is not None:
+        eta, phis = apply_filter(pm.tm, eta, *filt), apply_filter(pm.tm, phis, *filt)
+    return eta, phis
+
+
 # ----------------------------------------------------------------------------- modal filter
 # The paper's modal filter on its triangular surface elements (Sec. 3.2): the
 # nodal values of an element are mapped to a modal basis on the reference

@@ -58,6 +58,7 @@ struct PrismStepState {
   double* d_mdiag = nullptr;
   double* d_filt = nullptr;    // [nt][nt] the modal filter (at the first fnpf_prism_set_filter)
   int* d_interior = nullptr;   // [nt]
+  double* d_relax = nullptr;   // [4][ns] C_r, gen, x, y (at the first fnpf_prism_set_relaxation)
   pstep::PMG pmg{};            // the p-multigrid hierarchy (at the first FNPF_PMG call)
   bool pmg_ready = false;
   std::vector<void*> pmg_bufs;
@@ -75,6 +76,7 @@ void prism_step_free(fnpf_prism* m) {
   cudaFree(st->d_mdiag);
   cudaFree(st->d_filt);
   cudaFree(st->d_interior);
+  cudaFree(st->d_relax);
   for (void* b : st->pmg_bufs) cudaFree(b);
   delete st;
   m->step = nullptr;
@@ -352,11 +354,61 @@ fnpf_status fnpf_prism_filter_apply(fnpf_prism* m, double* f, void* stream) {
                             [&](auto& sp, const fnpf::pstep::Params&) { return sp.filter(f); });
 }
 
+fnpf_status fnpf_prism_set_relaxation(fnpf_prism* m, const fnpf_relaxation* r) {
+  if (!m) return FNPF_EINVAL;
+  fnpf_status st = fnpf::ensure_step(m);
+  if (st != FNPF_OK) return st;
+  fnpf::pstep::PMesh& pm = m->step->pm;
+  if (!r || !r->cr) {
+    pm.rcr = pm.rgen = pm.xs = pm.ys = nullptr;
+    return FNPF_OK;
+  }
+  bool gen = false;
+  for (int c = 0; c < m->ns; ++c) {
+    if (!(r->cr[c] >= 0 && r->cr[c] <= 1) || !r->gen || !isfinite(r->gen[c])) {
+      m->err = "prism relaxation: cr in [0, 1] and a finite gen flag at every node";
+      return FNPF_EINVAL;
+    }
+    gen = gen || (r->gen[c] != 0 && r->cr[c] > 0);
+  }
+  if (!(r->ramp_time > 0) || !isfinite(r->amp) || !isfinite(r->kx) || !isfinite(r->ky) || !isfinite(r->phase) ||
+      (gen && !(r->omega > 0))) {
+    m->err = "prism relaxation: ramp_time > 0, finite wave parameters, omega > 0 with generation nodes";
+    return FNPF_EINVAL;
+  }
+  std::vector<double> host(4 * (size_t)m->ns);
+  for (int c = 0; c < m->ns; ++c) {
+    host[c] = r->cr[c];
+    host[m->ns + c] = r->gen[c];
+    host[2 * (size_t)m->ns + c] = m->xs[c];
+    host[3 * (size_t)m->ns + c] = m->ys[c];
+  }
+  fnpf::PrismStepState* ps = m->step;
+  cudaError_t e = cudaSuccess;
+  if (!ps->d_relax) e = cudaMalloc(&ps->d_relax, sizeof(double) * host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(ps->d_relax, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    m->err = std::string("prism relaxation: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? FNPF_ENOMEM : FNPF_ECUDA;
+  }
+  pm.rcr = ps->d_relax;
+  pm.rgen = ps->d_relax + m->ns;
+  pm.xs = ps->d_relax + 2 * (size_t)m->ns;
+  pm.ys = ps->d_relax + 3 * (size_t)m->ns;
+  pm.ramp = r->ramp_time;
+  pm.amp = r->amp;
+  pm.kx = r->kx;
+  pm.ky = r->ky;
+  pm.omega = r->omega;
+  pm.phase = r->phase;
+  return FNPF_OK;
+}
+
 fnpf_status fnpf_prism_rk4_step(fnpf_prism* m, const fnpf_prism_opts* opts, const double* h, double* eta,
-                                double* phis, double dt, fnpf_solve_info* info, void* stream) {
-  if (!m || !h || !eta || !phis || !isfinite(dt)) return FNPF_EINVAL;
+                                double* phis, double t, double dt, fnpf_solve_info* info, void* stream) {
+  if (!m || !h || !eta || !phis || !isfinite(dt) || !isfinite(t)) return FNPF_EINVAL;
   return fnpf::with_stepper(m, opts, stream, "prism RK4 step", [&](auto& sp, const fnpf::pstep::Params& p) {
-    return sp.rk4(h, eta, phis, dt, p, info);
+    return sp.rk4(h, eta, phis, t, dt, p, info);
   });
 }
 

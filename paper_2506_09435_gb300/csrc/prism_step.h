@@ -66,6 +66,9 @@ struct PMesh {
   const double* mdiag;                  // [ns] its diagonal
   const double* filt;                   // [nt][nt] modal filter V F V^-1 on the triangle nodes (null: none)
   const int* interior;                  // [nt] 1 for the triangle-interior local nodes
+  const double *rcr, *rgen;             // [ns] relaxation weight C_r and generation flag (null: no zones)
+  const double *xs, *ys;                // [ns] surface node coordinates (the incident wave's phase)
+  double ramp, amp, kx, ky, omega, phase;   // incident wave of the generation zones
 };
 
 // Points the table pointers of m into the packed tables of fnpf_prism_create:
@@ -1109,6 +1112,35 @@ bool build_pmg(const PMesh& m0, const PWork& w0, const double* verts, int nverts
   return true;
 }
 
+// Relaxation zones at surface node c after the step to t1 (Sec. 3.3, Step
+// 4.7): f <- (1 - C_r) f + C_r f_true, the target the linear incident wave
+//   eta_I = r a cos(theta), phi_I = r (g a / omega) cosh(k (eta_I + h)) / cosh(k h) sin(theta),
+// theta = kx x + ky y - omega t1 + phase, r = min(1, t1 / ramp), in generation
+// nodes and zero in absorption nodes.
+struct RelaxItem {
+  struct Args {
+    PMesh m;
+    const double* h;
+    double t1, g;
+    double *eta, *phis;
+  };
+  FNPF_HD static void at(int64_t c, const Args& a) {
+    const PMesh& m = a.m;
+    const double cr = m.rcr[c];
+    if (cr == 0.0) return;
+    double te = 0.0, tp = 0.0;
+    if (m.rgen[c] != 0.0) {
+      const double r = a.t1 / m.ramp < 1.0 ? a.t1 / m.ramp : 1.0;
+      const double th = m.kx * m.xs[c] + m.ky * m.ys[c] - m.omega * a.t1 + m.phase;
+      const double k = sqrt(m.kx * m.kx + m.ky * m.ky);
+      te = r * m.amp * cos(th);
+      tp = r * (a.g * m.amp / m.omega) * cosh(k * (te + a.h[c])) / cosh(k * a.h[c]) * sin(th);
+    }
+    a.eta[c] = (1.0 - cr) * a.eta[c] + cr * te;
+    a.phis[c] = (1.0 - cr) * a.phis[c] + cr * tp;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Orchestration.
 
@@ -1446,9 +1478,10 @@ struct Stepper {
     return go<FilterWriteItem>(slots, {m, w.ft, f});
   }
 
-  // One classical RK4 step of (eta, phis) in place, then the modal filter of
-  // both (when one is set); info: NULL or [4].
-  fnpf_status rk4(const double* h, double* eta, double* phis, double dt, const Params& o, fnpf_solve_info* info) {
+  // One classical RK4 step of (eta, phis) from t to t + dt in place, then the
+  // relaxation zones and the modal filter (when set); info: NULL or [4].
+  fnpf_status rk4(const double* h, double* eta, double* phis, double t, double dt, const Params& o,
+                  fnpf_solve_info* info) {
     const int64_t ns = m.ns;
     for (int s = 0; s < 4; ++s) {
       const double* E = eta;
@@ -1472,6 +1505,7 @@ struct Stepper {
     }
     FNPF_PS_TRY(go<AxpyItem>(ns, {dt / 6.0, w.ae, eta}));
     FNPF_PS_TRY(go<AxpyItem>(ns, {dt / 6.0, w.ap, phis}));
+    if (m.rcr) FNPF_PS_TRY(go<RelaxItem>(ns, {m, h, t + dt, o.g, eta, phis}));
     if (!m.filt) return FNPF_OK;
     FNPF_PS_TRY(filter(eta));
     return filter(phis);

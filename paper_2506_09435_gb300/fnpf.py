@@ -120,8 +120,9 @@ def load():
         "fnpf_prism_precond_apply": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp],
         "fnpf_prism_dtn": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_rhs": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
-        "fnpf_prism_rk4_step": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, ctypes.c_double,
+        "fnpf_prism_rk4_step": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(SolveInfo), vp],
+        "fnpf_prism_set_relaxation": [vp, ctypes.POINTER(Relaxation)],
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
@@ -679,12 +680,25 @@ class PrismMesh:
         ptrs = _ptrs(None, (f, self.ns, "float64", "f"))
         self._check(_LIB.fnpf_prism_filter_apply(self._h, *ptrs, _stream(stream)))
 
-    def rk4_step(self, h, eta, phis, dt, opts=None, stream=None):
-        """One RK4 step of (eta, phis) in place (then the modal filter, when
-        set); returns the four stages' infos."""
+    def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
+        """Relaxation zones (host arrays cr, gen [Ns]); cr None removes them."""
+        if cr is None:
+            self._check(_LIB.fnpf_prism_set_relaxation(self._h, None))
+            return
+        c = np.ascontiguousarray(cr, dtype=np.float64)
+        g = np.ascontiguousarray(gen, dtype=np.float64)
+        if c.shape != (self.ns,) or g.shape != (self.ns,):
+            raise ValueError("cr and gen must have Ns = %d entries" % self.ns)
+        r = Relaxation(c.ctypes.data_as(_dp), g.ctypes.data_as(_dp), amp, kx, ky, omega, phase, ramp_time)
+        self._check(_LIB.fnpf_prism_set_relaxation(self._h, ctypes.byref(r)))
+
+    def rk4_step(self, h, eta, phis, dt, opts=None, stream=None, t=0.0):
+        """One RK4 step of (eta, phis) from t to t + dt in place (then the
+        relaxation zones and the modal filter, when set); returns the four
+        stages' infos."""
         ptrs = _ptrs(None, (h, self.ns, "float64", "h"), (eta, self.ns, "float64", "eta"),
                      (phis, self.ns, "float64", "phis"))
         infos = (SolveInfo * 4)()
-        st = _LIB.fnpf_prism_rk4_step(self._h, None if opts is None else ctypes.byref(opts), *ptrs, float(dt),
-                                      infos, _stream(stream))
+        st = _LIB.fnpf_prism_rk4_step(self._h, None if opts is None else ctypes.byref(opts), *ptrs, float(t),
+                                      float(dt), infos, _stream(stream))
         return self._check(st, [infos[i].as_dict() for i in range(4)])

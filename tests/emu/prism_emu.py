@@ -74,7 +74,8 @@ class Harness:
         lib.emu_sizes.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int64)] * 3
         lib.emu_sizes.restype = None
         sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_laplace_solve": [vp] * 7, "emu_precond_apply": [vp] * 6,
-               "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, vp]}
+               "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, ctypes.c_double, vp],
+               "emu_set_relaxation": [vp] * 3 + [ctypes.c_double] * 6}
         sig["emu_set_filter"] = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         sig["emu_filter_apply"] = [vp, vp]
         for nm, args in sig.items():
@@ -149,7 +150,13 @@ class EmuMesh:
         assert self.lib.emu_filter_apply(self.h, _p(out)) == 0
         return out
 
-    def rk4_step(self, opts, h, eta, phis, dt):
+    def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
+        self._cr, self._gen = np.ascontiguousarray(cr, dtype=np.float64), np.ascontiguousarray(gen, dtype=np.float64)
+        assert self.lib.emu_set_relaxation(self.h, _p(self._cr), _p(self._gen), amp, kx, ky, omega, phase,
+                                           ramp_time) == 0
+
+    def rk4_step(self, opts, h, eta, phis, dt, t=0.0):
         infos = (SolveInfo * 4)()
-        st = self.lib.emu_rk4_step(self.h, ctypes.byref(opts), _p(h), _p(eta), _p(phis), float(dt), infos)
+        st = self.lib.emu_rk4_step(self.h, ctypes.byref(opts), _p(h), _p(eta), _p(phis), float(t), float(dt),
+                                   infos)
         return st, [infos[i].iters for i in range(4)]

@@ -44,7 +44,7 @@ struct Emu {
   std::vector<int> tn, mcol, interior;
   std::vector<int64_t> voff, vinc, soff, sinc, mrow;
   std::vector<double> mval, mdiag;
-  std::vector<double> verts;
+  std::vector<double> verts, xs, ys;
   std::vector<int> tris;
   int nz = 0;
   PMG pmg{};
@@ -85,7 +85,8 @@ void* emu_create(const double* verts, int nverts, const int* tris, int ntris, in
   e->verts.assign(verts, verts + 2 * (size_t)nverts);
   e->tris.assign(tris, tris + 3 * (size_t)ntris);
   e->nz = nz;
-  std::vector<double> xs, ys;
+  std::vector<double>& xs = e->xs;
+  std::vector<double>& ys = e->ys;
   if (!fnpf::prism_numbering(verts, nverts, tris, ntris, p, &e->tn, &xs, &ys)) return nullptr;
   std::vector<double> rn, sn, wq, L, Lr, Ls;
   if (!fnpf::prism_tables(p, &rn, &sn, &wq, &L, &Lr, &Ls)) return nullptr;
@@ -239,12 +240,34 @@ int emu_filter_apply(void* h, double* f) {
   return sp.filter(f);
 }
 
-int emu_rk4_step(void* h, const fnpf_prism_opts* o, const double* hh, double* eta, double* phis, double dt,
+int emu_set_relaxation(void* h, const double* cr, const double* gen, double amp, double kx, double ky, double omega,
+                       double phase, double ramp) {
+  Emu* e = static_cast<Emu*>(h);
+  PMesh& m = e->m;
+  if (!cr) {
+    m.rcr = m.rgen = m.xs = m.ys = nullptr;
+    return FNPF_OK;
+  }
+  const std::vector<double> vc(cr, cr + m.ns), vg(gen, gen + m.ns);
+  m.rcr = e->table(vc, 0, vc.size());
+  m.rgen = e->table(vg, 0, vg.size());
+  m.xs = e->table(e->xs, 0, e->xs.size());
+  m.ys = e->table(e->ys, 0, e->ys.size());
+  m.ramp = ramp;
+  m.amp = amp;
+  m.kx = kx;
+  m.ky = ky;
+  m.omega = omega;
+  m.phase = phase;
+  return FNPF_OK;
+}
+
+int emu_rk4_step(void* h, const fnpf_prism_opts* o, const double* hh, double* eta, double* phis, double t, double dt,
                  fnpf_solve_info* info) {
   Emu* e = static_cast<Emu*>(h);
   const Params prm = params(o);
   Stepper<HostEx> sp = stepper(e, prm);
-  return sp.rk4(hh, eta, phis, dt, prm, info);
+  return sp.rk4(hh, eta, phis, t, dt, prm, info);
 }
 
 }  // extern "C"

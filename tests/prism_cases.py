@@ -37,3 +37,15 @@ def standing_wave(pm, Lx=1.3, amp=0.01):
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def flume(p, nz, nx=8, ny=2, Lx=4.0, Ly=0.5, h0=0.4, T=1.0, amp=0.005, seed=3):
+    """A triangulated walled flume of depth h0 with a generation zone over
+    [0, 1] and an absorption zone over [Lx - 1, Lx] (the relaxation weight and
+    the linear incident wave of the structured flume workloads)."""
+    v, t = W.triangulated_box(nx, ny, Lx, Ly, seed=seed)
+    pm = P.PrismMesh(P.TriMesh(v, t, p), nz)
+    omega = 2.0 * np.pi / T
+    desc = dict(zone=1.0, Lx=Lx, amp=amp, k=W.wavenumber(omega, h0, G), omega=omega, T=T)
+    cr, gen = W.flume_zones(desc, pm.tm.xs)
+    return v, t, pm, np.full(pm.ns, h0), cr, gen, W.flume_wave(desc)

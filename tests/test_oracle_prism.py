@@ -338,3 +338,28 @@ def test_triangle_filter(p):
     # a mode of degree d <= p is scaled by sigma_d
     mid = P.dubiner(p, rn, sn)[:, P.tri_index(p).index((1, 1))]
     assert np.max(np.abs(Fm @ mid - np.exp(-2.0 * (2 / p) ** 2) * mid)) < 1e-12
+
+
+def test_relaxation_step_limits():
+    """The prism relaxation step (Sec. 3.3, Step 4.7): C_r = 0 leaves the RK4
+    step untouched; C_r = 1 in generation nodes returns exactly the incident
+    wave at t + dt (ramped), in absorption nodes exactly zero; a node's blend
+    is (1 - C_r) f + C_r f_true with the target at its own position and depth."""
+    from oracle import surface as S
+    from tests import prism_cases as C
+    v, t, pm, h, cr, gen, wave = C.flume(2, 1, nx=4, ny=1)
+    eta, h_, phis = C.fields(pm)
+    t0, dt = 4.0, 0.02
+    e0, p0 = P.rk4_step(pm, h, eta, phis, dt, C.G)
+    zero, one = np.zeros(pm.ns), np.ones(pm.ns)
+    e1, p1 = P.relaxation_step(pm, h, eta, phis, t0, dt, C.G, zero, one, wave)
+    assert np.array_equal(e1, e0) and np.array_equal(p1, p0)
+    te, tp = S.incident_wave(pm.tm.xs, pm.tm.ys, h, t0 + dt, g=C.G, **wave)
+    e2, p2 = P.relaxation_step(pm, h, eta, phis, t0, dt, C.G, one, one, wave)
+    assert np.max(np.abs(e2 - te)) < 1e-15 and np.max(np.abs(p2 - tp)) < 1e-15
+    assert abs(np.max(np.abs(te)) - 0.8 * wave["amp"]) < 0.05 * wave["amp"]   # ramp (t + dt) / 5T = 0.804
+    e3, p3 = P.relaxation_step(pm, h, eta, phis, t0, dt, C.G, one, zero, wave)
+    assert not e3.any() and not p3.any()
+    e4, p4 = P.relaxation_step(pm, h, eta, phis, t0, dt, C.G, cr, gen, wave)
+    ref_e = np.where(gen != 0, (1 - cr) * e0 + cr * te, (1 - cr) * e0)
+    assert np.max(np.abs(e4 - ref_e)) < 1e-15 and np.any((cr > 0) & (cr < 1))

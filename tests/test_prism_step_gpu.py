@@ -195,3 +195,21 @@ def test_pmg_rk4_steps_match_oracle(fnpf):
         gm.rk4_step(hd, e1, p1, 0.02, opts(fnpf, pmg=True))
         eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
     assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10
+
+
+@pytest.mark.parametrize("p, filt", [(2, None), (3, (4.0, 2, 1))])
+def test_relaxation_zones_match_oracle(fnpf, p, filt):
+    nz = 2
+    v, t, pm, h, cr, gen, wave = C.flume(p, nz)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    gm.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+    if filt:
+        gm.set_filter(*filt)
+    e1, p1, hd = T(np.zeros(pm.ns)), T(np.zeros(pm.ns)), T(h)
+    eo, po = np.zeros(pm.ns), np.zeros(pm.ns)
+    t0, dt = 4.0, 0.025
+    for k in range(3):
+        gm.rk4_step(hd, e1, p1, dt, opts(fnpf), t=t0 + k * dt)
+        eo, po = P.relaxation_step(pm, h, eo, po, t0 + k * dt, dt, C.G, cr, gen, wave, filt=filt)
+    assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10
+    gm.set_relaxation(None, None, 0, 0, 0, 0, 0, 0)

@@ -196,6 +196,24 @@ def test_pmg_rk4_steps_match_oracle(harness):
     assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
 
 
+@pytest.mark.parametrize("p, filt", [(2, None), (3, (4.0, 2, 1))])
+def test_relaxation_zones_match_oracle(harness, p, filt):
+    nz = 2
+    v, t, pm, h, cr, gen, wave = C.flume(p, nz)
+    em = harness.mesh(v, t, p, nz)
+    em.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+    if filt:
+        em.set_filter(*filt)
+    e1, p1 = np.zeros(pm.ns), np.zeros(pm.ns)
+    eo, po = e1.copy(), p1.copy()
+    t0, dt = 4.0, 0.025
+    for k in range(3):
+        assert em.rk4_step(opts(), h, e1, p1, dt, t=t0 + k * dt)[0] == 0
+        eo, po = P.relaxation_step(pm, h, eo, po, t0 + k * dt, dt, C.G, cr, gen, wave, filt=filt)
+    assert np.max(np.abs(eo)) > 1e-3 * wave["amp"]
+    assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -221,6 +239,10 @@ for p, nz, nx, ny in [(1, 1, 2, 2), (3, 2, 3, 2), (5, 3, 2, 3)]:
         em.set_filter(2.0, 2, 1)
         em.filter_apply(eta)
         assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
+v, t, pm, h, cr, gen, wave = C.flume(3, 2, nx=4, ny=1)
+em = hs.mesh(v, t, 3, 2)
+em.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+assert em.rk4_step(E.opts(g=C.G), h, np.zeros(pm.ns), np.zeros(pm.ns), 0.02, t=4.0)[0] == 0
 print("asan run ok")
 """
 
