@@ -311,6 +311,21 @@ def rk4_step(pm, h, eta, phis, dt, g, linear=False):
             phis + dt / 6.0 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]))
 
 
+def mass(pm, eta):
+    """M = int eta dA over the surface (the consistent surface mass, 1^T M eta)."""
+    return float(np.ones(pm.ns) @ (surface_mass(pm) @ eta))
+
+
+def energy(pm, h, eta, phis, g, linear=False):
+    """E = 1/2 phi^T A phi + 1/2 g eta^T M eta (unit density), phi the Laplace
+    solution with phi = phis on the surface and A the stiffness matrix of the
+    model's geometry (still water when linear)."""
+    geo = np.zeros_like(eta) if linear else eta
+    phi = laplace_solve(pm, geo, h, phis)
+    A = pm.assemble(geo, h)
+    return 0.5 * float(phi @ (A @ phi)) + 0.5 * g * float(eta @ (surface_mass(pm) @ eta))
+
+
 def relaxation_step(pm, h, eta, phis, t, dt, g, cr, gen, wave, linear=False, filt=None):
     """One RK4 step, then the relaxation-zone blend f <- (1 - C_r) f + C_r f_true
     toward the linear incident wave where gen = 1 and toward zero where gen = 0,

@@ -363,3 +363,33 @@ def test_relaxation_step_limits():
     e4, p4 = P.relaxation_step(pm, h, eta, phis, t0, dt, C.G, cr, gen, wave)
     ref_e = np.where(gen != 0, (1 - cr) * e0 + cr * te, (1 - cr) * e0)
     assert np.max(np.abs(e4 - ref_e)) < 1e-15 and np.any((cr > 0) & (cr < 1))
+
+
+def test_mass_and_energy():
+    """Mass and energy of a state on the prism mesh: the mass of eta = c is c
+    times the area and that of eta = x its first moment (both exact: the
+    fields lie in the space); the energy of a constant elevation at rest is
+    g c^2 area / 2; the kinetic energy of the wall mode phi =
+    cosh(kap (z + h)) cos(kx x) cos(ky y) on still water (harmonic, zero normal
+    derivative on the walls and the bottom) equals, by Green's identity,
+    1/2 int phi phi_z dA = kap sinh(kap h) cosh(kap h) Lx Ly / 8, and the
+    discrete energy converges to it exponentially in p."""
+    import math
+    Lx, Ly, h0, g = 1.3, 1.0, 0.5, 9.81
+    v, t = W.triangulated_box(3, 2, Lx, Ly)
+    kx, ky = math.pi / Lx, math.pi / Ly
+    kap = math.hypot(kx, ky)
+    exact = kap * math.sinh(kap * h0) * math.cosh(kap * h0) * Lx * Ly / 8
+    errs = []
+    for p in (2, 3, 4, 5):
+        pm = P.PrismMesh(P.TriMesh(v, t, p), 2)
+        x, y = pm.tm.xs, pm.tm.ys
+        h = np.full(pm.ns, h0)
+        assert abs(P.mass(pm, np.full(pm.ns, 0.3)) - 0.3 * Lx * Ly) < 1e-13
+        assert abs(P.mass(pm, x) - 0.5 * Lx * Lx * Ly) < 1e-13
+        assert abs(P.energy(pm, h, np.full(pm.ns, 0.01), np.zeros(pm.ns), g) - 0.5 * g * 1e-4 * Lx * Ly) < 1e-15
+        phis = math.cosh(kap * h0) * np.cos(kx * x) * np.cos(ky * y)
+        errs.append(abs(P.energy(pm, h, np.zeros(pm.ns), phis, g) - exact) / exact)
+    # measured 5.4e-3, 2.3e-3, 1.1e-4, 5.5e-6 for p = 2..5
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1)), errs
+    assert errs[-1] < 1e-5 and errs[-1] < 1e-2 * errs[0], errs
