@@ -575,6 +575,17 @@ fnpf_status fnpf_prism_rhs(fnpf_prism* mesh, const fnpf_prism_opts* opts, const 
 fnpf_status fnpf_prism_rk4_step(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* h, double* eta,
                                 double* phis, double t, double dt, fnpf_solve_info* info, void* stream);
 
+/* Mass and energy of a prism state (eta, phis) [Ns] (device): M = int eta dA
+ * = 1^T M_s eta with the consistent surface mass M_s, and E = 1/2 phi^T A phi
+ * + 1/2 g eta^T M_s eta (unit density), phi the Laplace solution with
+ * phi = phis on the surface (into the mesh's potential) and A the stiffness
+ * matrix of the model's geometry (eta, or still water for FNPF_LINEAR).
+ * Writes the HOST doubles *mass and *energy; waits for the stream.  Errors:
+ * EINVAL (NULL, bad options), ENOMEM, ECUDA, the solve's statuses. */
+fnpf_status fnpf_prism_invariants(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta, const double* h,
+                                  const double* phis, double* mass, double* energy, fnpf_solve_info* info,
+                                  void* stream);
+
 /* Relaxation zones on the prism mesh (Sec. 3.3; Step 4.7): after every
  * fnpf_prism_rk4_step from t to t + dt, f <- (1 - C_r) f + C_r f_true at every
  * surface node, the targets of fnpf_set_relaxation (the linear incident wave

@@ -354,6 +354,15 @@ fnpf_status fnpf_prism_filter_apply(fnpf_prism* m, double* f, void* stream) {
                             [&](auto& sp, const fnpf::pstep::Params&) { return sp.filter(f); });
 }
 
+fnpf_status fnpf_prism_invariants(fnpf_prism* m, const fnpf_prism_opts* opts, const double* eta, const double* h,
+                                  const double* phis, double* mass, double* energy, fnpf_solve_info* info,
+                                  void* stream) {
+  if (!m || !eta || !h || !phis || !mass || !energy) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, opts, stream, "prism invariants", [&](auto& sp, const fnpf::pstep::Params& p) {
+    return sp.invariants(eta, h, phis, p, mass, energy, info);
+  });
+}
+
 fnpf_status fnpf_prism_set_relaxation(fnpf_prism* m, const fnpf_relaxation* r) {
   if (!m) return FNPF_EINVAL;
   fnpf_status st = fnpf::ensure_step(m);

@@ -1415,6 +1415,25 @@ struct Stepper {
     return st;
   }
 
+  // Mass M = 1^T M_s eta and energy E = 1/2 phi^T A phi + 1/2 g eta^T M_s eta of
+  // (eta, phis) (host doubles): the solve into the mesh's potential and one
+  // application of the stored operator (the model's geometry).
+  fnpf_status invariants(const double* eta, const double* h, const double* phis, const Params& o, double* mass,
+                         double* energy, fnpf_solve_info* info) {
+    const double* geo = o.linear ? w.zero : eta;
+    FNPF_PS_TRY(solve(geo, h, phis, w.phi, o, info));
+    FNPF_PS_TRY(apply(w.phi, w.q));
+    double kin = 0, pot = 0, tot = 0;
+    FNPF_PS_TRY(dot(w.phi, w.q, m.N, &kin));
+    FNPF_PS_TRY(go<CsrItem>(m.ns, {m.mrow, m.mcol, m.mval, eta, w.mq}));
+    FNPF_PS_TRY(dot(eta, w.mq, m.ns, &pot));
+    FNPF_PS_TRY(go<FillItem>(m.ns, {1.0, w.mr}));
+    FNPF_PS_TRY(dot(w.mr, w.mq, m.ns, &tot));
+    *mass = tot;
+    *energy = 0.5 * kin + 0.5 * o.g * pot;
+    return FNPF_OK;
+  }
+
   // x = M^-1 b on the surface (Jacobi-PCG on the consistent mass from x = 0).
   fnpf_status mass_solve(const double* b, double* x, const Params& o) {
     const int64_t ns = m.ns;

@@ -123,6 +123,8 @@ def load():
         "fnpf_prism_rk4_step": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_set_relaxation": [vp, ctypes.POINTER(Relaxation)],
+        "fnpf_prism_invariants": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_ensemble_rk4_step": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveInfo), vp],
         "fnpf_autotune": [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp],
@@ -679,6 +681,16 @@ class PrismMesh:
     def filter_apply(self, f, stream=None):
         ptrs = _ptrs(None, (f, self.ns, "float64", "f"))
         self._check(_LIB.fnpf_prism_filter_apply(self._h, *ptrs, _stream(stream)))
+
+    def invariants(self, eta, h, phis, opts=None, stream=None):
+        """(mass, energy) of the state (eta, phis) [Ns] (waits for the stream)."""
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (phis, self.ns, "float64", "phis"))
+        M, En, info = ctypes.c_double(), ctypes.c_double(), SolveInfo()
+        st = _LIB.fnpf_prism_invariants(self._h, None if opts is None else ctypes.byref(opts), *ptrs,
+                                        ctypes.byref(M), ctypes.byref(En), ctypes.byref(info), _stream(stream))
+        self._check(st)
+        return M.value, En.value
 
     def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
         """Relaxation zones (host arrays cr, gen [Ns]); cr None removes them."""

@@ -75,7 +75,7 @@ class Harness:
         lib.emu_sizes.restype = None
         sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_laplace_solve": [vp] * 7, "emu_precond_apply": [vp] * 6,
                "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, ctypes.c_double, vp],
-               "emu_set_relaxation": [vp] * 3 + [ctypes.c_double] * 6}
+               "emu_set_relaxation": [vp] * 3 + [ctypes.c_double] * 6, "emu_invariants": [vp] * 7}
         sig["emu_set_filter"] = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         sig["emu_filter_apply"] = [vp, vp]
         for nm, args in sig.items():
@@ -149,6 +149,12 @@ class EmuMesh:
         out = np.array(f, dtype=np.float64, copy=True)
         assert self.lib.emu_filter_apply(self.h, _p(out)) == 0
         return out
+
+    def invariants(self, opts, eta, h, phis):
+        M, En = ctypes.c_double(), ctypes.c_double()
+        assert self.lib.emu_invariants(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(phis), ctypes.byref(M),
+                                       ctypes.byref(En)) == 0
+        return M.value, En.value
 
     def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
         self._cr, self._gen = np.ascontiguousarray(cr, dtype=np.float64), np.ascontiguousarray(gen, dtype=np.float64)

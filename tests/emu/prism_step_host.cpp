@@ -240,6 +240,14 @@ int emu_filter_apply(void* h, double* f) {
   return sp.filter(f);
 }
 
+int emu_invariants(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis,
+                   double* mass, double* energy) {
+  Emu* e = static_cast<Emu*>(h);
+  const Params prm = params(o);
+  Stepper<HostEx> sp = stepper(e, prm);
+  return sp.invariants(eta, hh, phis, prm, mass, energy, nullptr);
+}
+
 int emu_set_relaxation(void* h, const double* cr, const double* gen, double amp, double kx, double ky, double omega,
                        double phase, double ramp) {
   Emu* e = static_cast<Emu*>(h);

@@ -213,3 +213,14 @@ def test_relaxation_zones_match_oracle(fnpf, p, filt):
         eo, po = P.relaxation_step(pm, h, eo, po, t0 + k * dt, dt, C.G, cr, gen, wave, filt=filt)
     assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10
     gm.set_relaxation(None, None, 0, 0, 0, 0, 0, 0)
+
+
+@pytest.mark.parametrize("linear", [False, True])
+def test_invariants_match_oracle(fnpf, linear):
+    p, nz = 3, 2
+    v, t, pm = C.mesh(p, nz)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    M, En = gm.invariants(T(eta), T(h), T(phis), opts(fnpf, linear=linear))
+    assert abs(M - P.mass(pm, eta)) <= 1e-13 * np.sum(np.abs(eta))
+    assert abs(En - P.energy(pm, h, eta, phis, C.G, linear=linear)) <= 1e-10 * abs(En)

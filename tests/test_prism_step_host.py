@@ -214,6 +214,17 @@ def test_relaxation_zones_match_oracle(harness, p, filt):
     assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
 
 
+@pytest.mark.parametrize("linear", [False, True])
+def test_invariants_match_oracle(harness, linear):
+    p, nz = 3, 2
+    v, t, pm = C.mesh(p, nz)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    M, En = em.invariants(opts(linear=linear), eta, h, phis)
+    assert abs(M - P.mass(pm, eta)) <= 1e-13 * np.sum(np.abs(eta))
+    assert abs(En - P.energy(pm, h, eta, phis, C.G, linear=linear)) <= 1e-10 * abs(En)
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -233,6 +244,7 @@ for p, nz, nx, ny in [(1, 1, 2, 2), (3, 2, 3, 2), (5, 3, 2, 3)]:
     assert em.dtn(o, eta, h, phis)[0] == 0
     assert em.rhs(o, eta, h, phis)[0] == 0
     assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
+    em.invariants(o, eta, h, phis)
     o.model = 1
     assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
     if p >= 3:
