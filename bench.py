@@ -85,17 +85,19 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-prism", action="store_true", help="skip the prism-mesh leg of the step benchmark")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "pc32"],
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
     ap.add_argument("--mode", default="step",
-                    choices=["step", "apply", "ensemble", "convergence", "bar", "cylinder", "peaks"],
+                    choices=["step", "apply", "ensemble", "convergence", "bar", "cylinder", "peaks", "prism"],
                     help="step: RK4 steps (the benchmark); apply: operator applications only; "
                          "ensemble: 64 seeded tanks in one launch per step vs one tank at a time; "
                          "convergence: error of a stream-function wave after one period vs p and h; "
                          "bar: the submerged-bar flume in FP64 and both mixed-precision forms; "
                          "cylinder: adjoint cost on the O-grid around a cylinder; "
-                         "peaks: measured FP64 / FP32 FMA throughput")
+                         "peaks: measured FP64 / FP32 FMA throughput; "
+                         "prism: the prism-mesh leg (triangulated flume) alone")
     ap.add_argument("--tanks", type=int, default=64)
     ap.add_argument("--bar-steps", type=int, default=150, help="RK4 steps of the bar-flume accuracy run")
     ap.add_argument("--p", type=int, default=6)
@@ -136,6 +138,28 @@ print(json.dumps(dict(N=m.N, times=times)))
 """
 
 ONE_THREAD = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+PRISM_ORACLE_SAMPLE = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import prism as P
+from paper_2506_09435_gb300 import workloads as W
+v, t, d = W.prism_flume(nx={nx}, ny={ny}, p={p}, nz={nz})
+pm = P.PrismMesh(P.TriMesh(v, t, d['p']), d['nz'])
+cr, gen = W.flume_zones(d, pm.tm.xs)
+wave = W.flume_wave(d)
+h = np.full(pm.ns, d['h0'])
+eta, phis = np.zeros(pm.ns), np.zeros(pm.ns)
+t0, dt = {t0}, d['T'] / 40
+times = []
+for k in range({steps}):
+    s = time.perf_counter()
+    eta, phis = P.relaxation_step(pm, h, eta, phis, t0 + k * dt, dt, d['g'], cr, gen, wave)
+    times.append(time.perf_counter() - s)
+np.savez({out!r}, eta=eta, phis=phis)
+print(json.dumps(dict(N=pm.N, times=times)))
+"""
 
 
 def run_oracle_sample(nxy, steps, warm, out=""):
@@ -657,6 +681,13 @@ def main_gb300(args):
         if args.model != "fnpf":
             vs_oracle = None      # the oracle sample is the nonlinear model
 
+    prism = None
+    if rank == 0 and world == 1 and not args.no_prism:
+        try:   # runs last: nothing measured above depends on it
+            prism = prism_leg(dev, args, flush)
+        except Exception as e:   # reported in the line instead of ending the run
+            prism = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -686,9 +717,104 @@ def main_gb300(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
+            "prism": prism,
         }
         print(json.dumps(line))
     ranks.close()
+    return 0
+
+
+PRISM_T0 = 4.0   # the flume runs from rest at t = 4 s: the generation ramp (5 T) is at 80 %
+
+
+def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None):
+    """The prism path (operator, solve, w, projected conditions, RK4,
+    relaxation zones) on the triangulated flume W.prism_flume from rest at
+    t = 4 s: `warm` untimed steps, then `steps` steps timed with CUDA events on
+    the current stream (L2 flushed before each when `flush` is given).
+    Returns (state, ms per timed step, mean CG iterations per solve, mesh)."""
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    from paper_2506_09435_gb300 import workloads as W
+    v, t, d = W.prism_flume(nx=nx, ny=ny, p=p, nz=nz)
+    _, x, _ = fnpf.prism_numbering(v, t, d["p"])
+    gm = fnpf.PrismMesh(v, t, d["p"], d["nz"])
+    cr, gen = W.flume_zones(d, x)
+    wv = W.flume_wave(d)
+    gm.set_relaxation(cr, gen, wv["amp"], wv["kx"], wv["ky"], wv["omega"], wv["phase"], wv["ramp_time"])
+    o = fnpf.PrismMesh.default_opts(rtol=rtol, g=d["g"], precond=precond)
+    h = torch.full((gm.ns,), d["h0"], dtype=torch.float64, device=dev)
+    eta = torch.zeros(gm.ns, dtype=torch.float64, device=dev)
+    phis = torch.zeros(gm.ns, dtype=torch.float64, device=dev)
+    dt = d["T"] / 40
+    stream = torch.cuda.current_stream()
+    iters, ms = [], 0.0
+    for k in range(warm + steps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        infos = gm.rk4_step(h, eta, phis, dt, o, t=PRISM_T0 + k * dt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k >= warm:
+            ms += a.elapsed_time(b)
+            iters += [i["iters"] for i in infos]
+    return (eta, phis), ms / max(1, steps), statistics.mean(iters) if iters else 0.0, gm
+
+
+def prism_leg(dev, args, flush, size=(64, 16, 4, 2), sample=(6, 2, 3, 2, 2)):
+    """Sub-object of the benchmark line: the prism path on the triangulated
+    flume of `size` = (cells in x, cells in y, p, Nz) (throughput, CG
+    iterations with the p-multigrid and with Jacobi), and its error against the
+    oracle on the flume of `sample` = (cells in x, in y, p, Nz, RK4 steps)."""
+    import numpy as np
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    (nx, ny, p, nz), steps = size, max(1, min(args.steps, 5))
+    (eta, _), ms, it_pmg, gm = prism_flume_run(dev, nx, ny, p, nz, steps, 2, args.rtol, fnpf.FNPF_PMG, flush)
+    out = {"workload": "prisms (Sec. 3.1.2) over a jittered triangulation of a walled 4 x 1 m flume, %d x %d cells "
+                       "(%d triangles), Nz=%d, p=%d, h=0.4 m, generation and absorption zones, T = 1 s, dt = T/40, "
+                       "from rest at t = 4 s" % (nx, ny, 2 * nx * ny, nz, p),
+           "dof": gm.N, "surface_dof": gm.ns, "precond": "pmg", "rtol": args.rtol, "steps": steps,
+           "ms_per_step": ms, "value": gm.N / (ms * 1e-3), "unit": UNIT,
+           "cg_iters_per_solve_mean": it_pmg, "finite": bool(torch.isfinite(eta).all())}
+    del gm
+    _, ms_j, it_j, gm = prism_flume_run(dev, nx, ny, p, nz, 1, 2, args.rtol, fnpf.FNPF_JACOBI, flush)
+    out["jacobi"] = {"ms_per_step": ms_j, "cg_iters_per_solve_mean": it_j}
+    del gm
+    if not args.no_cpu_baseline:
+        sx, sy, sp, snz, ssteps = sample
+        path = os.path.join(tempfile.gettempdir(), "fnpf_prism_oracle_%d.npz" % os.getpid())
+        code = PRISM_ORACLE_SAMPLE.format(root=ROOT, nx=sx, ny=sy, p=sp, nz=snz, t0=PRISM_T0, steps=ssteps, out=path)
+        res = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, **ONE_THREAD), capture_output=True,
+                             text=True, check=True)
+        rec = json.loads(res.stdout.strip().splitlines()[-1])
+        ref = np.load(path)
+        os.remove(path)
+        (ge, gp), _, _, gm = prism_flume_run(dev, sx, sy, sp, snz, ssteps, 0, 1e-13, fnpf.FNPF_PMG)
+        ge, gp = ge.cpu().numpy(), gp.cpu().numpy()
+        out["cpu_baseline"] = {"value": rec["N"] * len(rec["times"]) / sum(rec["times"]), "unit": UNIT, "cores": 1,
+                               "kind": "oracle",
+                               "sample": "the same flume on %d x %d cells, p=%d, Nz=%d (N=%d), %d RK4 steps"
+                                         % (sx, sy, sp, snz, rec["N"], ssteps)}
+        out["rel_l2_vs_oracle"] = {"sample": out["cpu_baseline"]["sample"] + "; GPU rtol 1e-13, oracle direct solves",
+                                   "eta": float(np.linalg.norm(ge - ref["eta"]) / np.linalg.norm(ref["eta"])),
+                                   "phis": float(np.linalg.norm(gp - ref["phis"]) / np.linalg.norm(ref["phis"]))}
+        del gm
+    return out
+
+
+def main_prism(args):
+    """--mode prism: the prism leg of the step benchmark on its own."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    with ClockSampler(dev.index) as clk:
+        out = prism_leg(dev, args, None)
+    out["clocks"] = clk.summary()
+    print(json.dumps({"mode": "prism", **out}))
     return 0
 
 
@@ -1148,6 +1274,8 @@ def main():
         return main_cylinder(args)
     if args.mode == "ensemble":
         return main_ensemble(args)
+    if args.mode == "prism":
+        return main_prism(args)
     if args.impl == "reference":
         return main_reference(args)
     if args.mode == "apply":

@@ -264,6 +264,20 @@ def triangulated_box(nx, ny, Lx=1.0, Ly=1.0, jitter=0.2, seed=7):
     return verts, np.array(tris, dtype=np.int64)
 
 
+def prism_flume(nx=64, ny=16, Lx=4.0, Ly=1.0, h0=0.4, T=1.0, amp=0.005, p=4, nz=2, seed=3, g=G_DEFAULT):
+    """A walled flume on an unstructured triangulation (the paper's prism mesh
+    type, Sec. 3.1.2): the jittered triangulation of triangulated_box, depth h0,
+    a generation zone over [0, 1] m and an absorption zone over [Lx - 1, Lx]
+    (relaxation_weight profiles) for a linear incident wave of period T and
+    amplitude amp.  Returns (verts, tris, desc); flume_zones(desc, x) and
+    flume_wave(desc) give the zones and the wave."""
+    v, t = triangulated_box(nx, ny, Lx, Ly, seed=seed)
+    om = 2.0 * math.pi / T
+    desc = dict(p=p, nz=nz, h0=h0, g=g, zone=1.0, Lx=Lx, Ly=Ly, nx=nx, ny=ny, amp=amp,
+                k=wavenumber(om, h0, g), omega=om, T=T)
+    return v, t, desc
+
+
 def manufactured_potential(x, y, z, h, kx, ky):
     """Harmonic phi = cosh(kappa (z + h)) cos(kx x) cos(ky y) and its d/dz."""
     kap = math.hypot(kx, ky)

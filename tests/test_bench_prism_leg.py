@@ -1,0 +1,69 @@
+"""The prism leg of the step benchmark (bench.prism_leg) end to end on the
+CPU: the library binding is replaced by the host harness of the prism step
+(tests/emu, the kernels' own bodies run item by item) and CUDA events by a
+stand-in, so that the leg's own logic -- mesh and zones, the timed steps, the
+Jacobi comparison, the oracle child process and the error against it -- runs
+as on the GPU, on a small flume."""
+import sys
+import types
+
+import numpy as np
+import pytest
+import torch
+
+import bench
+from paper_2506_09435_gb300 import fnpf as F
+from tests.emu import prism_emu as E
+
+
+class _Event:
+    def __init__(self, enable_timing=False):
+        pass
+
+    def record(self, stream=None):
+        pass
+
+    def elapsed_time(self, other):
+        return 1.0
+
+
+@pytest.fixture
+def fake_binding(monkeypatch, tmp_path):
+    hs = E.Harness(E.build(str(tmp_path)))
+
+    class PrismMesh:
+        def __init__(self, verts, tris, p, nz):
+            self.em = hs.mesh(verts, tris, p, nz)
+            self.N, self.ns = self.em.N, self.em.ns
+
+        @staticmethod
+        def default_opts(rtol=1e-10, g=9.81, precond=F.FNPF_JACOBI):
+            return E.opts(rtol=rtol, g=g, pmg=precond == F.FNPF_PMG)
+
+        def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
+            self.em.set_relaxation(cr, gen, amp, kx, ky, omega, phase, ramp_time)
+
+        def rk4_step(self, h, eta, phis, dt, opts, t=0.0):
+            st, iters = self.em.rk4_step(opts, h.numpy(), eta.numpy(), phis.numpy(), dt, t=t)
+            assert st == 0
+            return [{"iters": i} for i in iters]
+
+    fake = types.SimpleNamespace(PrismMesh=PrismMesh, prism_numbering=F.prism_numbering,
+                                 FNPF_PMG=F.FNPF_PMG, FNPF_JACOBI=F.FNPF_JACOBI)
+    import paper_2506_09435_gb300 as pkg
+    monkeypatch.setattr(pkg, "fnpf", fake)
+    monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: None)
+    yield
+    monkeypatch.setattr(pkg, "fnpf", F)
+
+
+def test_prism_leg_reports_throughput_iterations_and_oracle_error(fake_binding):
+    args = types.SimpleNamespace(steps=2, rtol=1e-10, no_cpu_baseline=False)
+    out = bench.prism_leg(torch.device("cpu"), args, None, size=(6, 2, 3, 2), sample=(4, 1, 2, 1, 2))
+    assert out["finite"] and out["steps"] == 2 and out["dof"] > 0 and out["value"] > 0
+    assert 0 < out["cg_iters_per_solve_mean"] < out["jacobi"]["cg_iters_per_solve_mean"]
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 1
+    err = out["rel_l2_vs_oracle"]
+    assert err["eta"] <= 1e-10 and err["phis"] <= 1e-10, err
