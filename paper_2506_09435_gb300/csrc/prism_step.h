@@ -993,6 +993,49 @@ struct ChebItem {
   }
 };
 
+// The end of one Chebyshev step at interior node g: q = the gathered element
+// results of A d (d the previous direction), r -= q, d = s d + c D^-1 r, x += d
+// (the gather, the residual update and the smoother update of one step in one
+// pass; only node g's own entries are written).
+struct GatherChebItem {
+  struct Args {
+    const int64_t *off, *inc;
+    const double* ye;
+    int64_t NI;
+    double s, c;
+    const double* diag;
+    double *r, *d, *x;
+  };
+  FNPF_HD static void at(int64_t g, const Args& a) {
+    if (g >= a.NI) return;
+    double q = 0;
+    for (int64_t j = a.off[g]; j < a.off[g + 1]; ++j) q += a.ye[a.inc[j]];
+    const double r = a.r[g] - q;
+    const double d = a.s * a.d[g] + a.c * r / a.diag[g];
+    a.r[g] = r;
+    a.d[g] = d;
+    a.x[g] += d;
+  }
+};
+
+// r = b - (gathered element results) at interior node g (r's surface plane
+// untouched): the residual after an operator application.
+struct GatherResidualItem {
+  struct Args {
+    const int64_t *off, *inc;
+    const double* ye;
+    int64_t NI;
+    const double* b;
+    double* r;
+  };
+  FNPF_HD static void at(int64_t g, const Args& a) {
+    if (g >= a.NI) return;
+    double q = 0;
+    for (int64_t j = a.off[g]; j < a.off[g + 1]; ++j) q += a.ye[a.inc[j]];
+    a.r[g] = a.b[g] - q;
+  }
+};
+
 // A fixed pseudo-random vector in [-1, 1) on the interior (splitmix64 of the
 // index), zero on the surface plane: the start of the eigenvalue estimate.
 struct HashItem {
@@ -1289,8 +1332,15 @@ struct Stepper {
     return FNPF_OK;
   }
 
+  // The element results of A x on level L (the operator without its gather).
+  fnpf_status element_level(PLevel& L, const double* x) {
+    FNPF_PS_TRY(go<FluxItem>(L.m.nelem * L.m.n * L.m.nq, {L.m, L.G, x, L.F}));
+    return go<NodeItem>(L.m.nelem * L.m.nt * L.m.n, {L.m, L.F, L.ye});
+  }
+
   // deg Chebyshev steps on level L: x and r = b - A x (both in, both out; r
-  // updated at the end only if need_r).
+  // updated at the end only if need_r).  Step k > 0 is the element results of
+  // A d_(k-1) followed by one fused gather-and-update pass.
   fnpf_status cheb(PLevel& L, double* x, double* r, int deg, bool need_r) {
     const int64_t N = L.m.N, NI = L.m.NI;
     const double theta = 0.5 * (L.hi + L.lo), delta = 0.5 * (L.hi - L.lo), sigma = theta / delta;
@@ -1298,15 +1348,14 @@ struct Stepper {
     FNPF_PS_TRY(go<FillItem>(N, {0.0, L.d}));
     FNPF_PS_TRY(go<ChebItem>(NI, {0.0, 1.0 / theta, r, L.diag, L.d, x}));
     for (int k = 1; k < deg; ++k) {
-      FNPF_PS_TRY(apply_level(L, L.d, L.q));
-      FNPF_PS_TRY(go<AxpyItem>(NI, {-1.0, L.q, r}));
+      FNPF_PS_TRY(element_level(L, L.d));
       const double rn = 1.0 / (2.0 * sigma - rho);
-      FNPF_PS_TRY(go<ChebItem>(NI, {rn * rho, 2.0 * rn / delta, r, L.diag, L.d, x}));
+      FNPF_PS_TRY(go<GatherChebItem>(N, {L.m.voff, L.m.vinc, L.ye, NI, rn * rho, 2.0 * rn / delta, L.diag, r, L.d, x}));
       rho = rn;
     }
     if (!need_r) return FNPF_OK;
-    FNPF_PS_TRY(apply_level(L, L.d, L.q));
-    return go<AxpyItem>(NI, {-1.0, L.q, r});
+    FNPF_PS_TRY(element_level(L, L.d));
+    return go<GatherResidualItem>(N, {L.m.voff, L.m.vinc, L.ye, NI, r, r});
   }
 
   // x = M_l^-1 b: one V-cycle from x = 0 (b and x: interior values, surface plane zero).
@@ -1323,8 +1372,8 @@ struct Stepper {
     FNPF_PS_TRY(go<InteriorItem>(C.m.N, {C.m.NI, 1.0, C.q, C.b}));
     FNPF_PS_TRY(vcycle(l + 1, C.b, C.x, o));
     FNPF_PS_TRY(go<ProlongItem>(N, {L.m, C.m, pmg->xf[l], C.x, x}));
-    FNPF_PS_TRY(apply_level(L, x, L.q));
-    FNPF_PS_TRY(go<LinItem>(NI, {b, -1.0, L.q, L.r}));
+    FNPF_PS_TRY(element_level(L, x));
+    FNPF_PS_TRY(go<GatherResidualItem>(N, {L.m.voff, L.m.vinc, L.ye, NI, b, L.r}));
     return cheb(L, x, L.r, o.cheb_degree, false);
   }
 
