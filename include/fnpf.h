@@ -503,8 +503,9 @@ const char* fnpf_prism_last_error(const fnpf_prism* mesh);
  *     operator of fnpf_prism_apply, Eq. Laplace_weak, with that stored metric);
  *   solve: A_II phi_I = -A_IS phis (Eq. Laplace_strong: phi = phis on the
  *     surface plane, zero normal derivative on the bottom and the walls) by
- *     Jacobi-preconditioned CG to ||r|| <= rtol ||b||, the host reading one
- *     scalar per dot product;
+ *     preconditioned CG to ||r|| <= rtol ||b|| with its scalars on the
+ *     device, the host reading the convergence state every iteration
+ *     (FNPF_PMG) or every 8 iterations (Jacobi, and the surface-mass solves);
  *   w = d phi / dz at the surface nodes: phi_t / z_t on the top layer's
  *     vertical GLL line (the extrusion is vertical, so every prism sharing the
  *     line gives the same value);

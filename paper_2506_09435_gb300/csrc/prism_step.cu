@@ -2,8 +2,8 @@
 // triangular surface mesh (fnpf_prism_laplace_solve, fnpf_prism_dtn,
 // fnpf_prism_rhs, fnpf_prism_rk4_step; Sec. 3.1.2, Sec. 3.4 Steps 4.1-4.6,
 // Sec. 3.2): the items of prism_step.h launched one thread per item on the
-// caller's stream, the CG loops driven from the host (one read of a scalar per
-// dot product).  The workspace and the surface tables (the incidence of the
+// caller's stream; the CG loops keep their scalars on the device and the host
+// reads their state every iteration (p-multigrid) or every 8 (Jacobi).  The workspace and the surface tables (the incidence of the
 // triangle slots and the consistent surface mass in CSR form) are built at a
 // mesh's first call.
 #include <limits.h>

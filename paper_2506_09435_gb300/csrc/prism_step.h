@@ -9,7 +9,8 @@
 // so the same bodies run as CUDA kernels (prism_step.cu: one thread per item)
 // and, compiled as plain C++, one item after another.  Stepper<Ex> orders the
 // launches; Ex supplies run<Item>(n, args) and get(host, src, count), the
-// device-to-host read of the scalars the host-driven CG loops test.
+// device-to-host read of the CG loops' state (their scalars stay on the
+// device; the host tests the stop flag).
 //
 // Per RK4 stage (Sec. 3.4, Steps 4.1-4.6; ERK4, Sec. 3.2):
 //   geometry  G = w_q w_k |det J| J^-1 J^-T at every quadrature point of every
@@ -89,6 +90,7 @@ struct PWork {
   double *G, *F, *ye, *diag;            // [nelem n nq 6], [nelem n nq 3], [nelem nt n], [N]
   double *xs, *r, *z, *pd, *q;          // Laplace PCG [N]
   double *part, *scal;                  // dot-product partials, scalars
+  double* cg;                           // CG state on the device (kCgSlots) and Lanczos coefficients
   double *phi, *w;                      // the mesh's potential [N] (warm start), w [ns]
   double *fq, *se, *be, *bp;            // [ntri nq 2], [ntri nt 2], [ns], [ns]
   double *mr, *mz, *mp, *mq;            // surface-mass CG [ns]
@@ -115,6 +117,7 @@ void carve(const PMesh& m, PWork* w, Take take) {
   take(&w->q, m.N);
   take(&w->part, dot_partials(std::max<int64_t>(m.N, m.ns)));
   take(&w->scal, 4);
+  take(&w->cg, 64);
   take(&w->phi, m.N);
   take(&w->w, m.ns);
   take(&w->fq, (int64_t)m.ntri * m.nq * 2);
@@ -124,6 +127,12 @@ void carve(const PMesh& m, PWork* w, Take take) {
   for (double** s : surf) take(s, m.ns);
   take(&w->ft, (int64_t)m.ntri * m.nt);
 }
+
+// CG state slots (device doubles): r.z, p.q, r.r, alpha, beta, the new r.z,
+// the stop flag (0 running, 1 converged, 2 breakdown, 3 diverged) and the
+// number of completed iterations; the Lanczos coefficients follow.
+enum { kRZ = 0, kPQ, kRR, kAL, kBE, kRZN, kDONE, kITERS, kCgSlots };
+constexpr int kMaxLanczos = 12;   // steps of the eigenvalue estimate (coefficients at cg + kCgSlots)
 
 // ---------------------------------------------------------------------------
 // Host set-up: the surface incidence and the consistent surface mass.
@@ -741,6 +750,93 @@ struct CsrItem {
   }
 };
 
+// Device-side CG scalars.  Every CG item returns at once once the stop flag
+// cg[kDONE] is set, so iterations launched after convergence change nothing
+// and the host may read the flag only every few iterations.  hist (or null)
+// receives alpha_j at 2 j and beta_j at 2 j + 1 (the Lanczos coefficients).
+struct CgResetItem {
+  struct Args {
+    double* cg;
+  };
+  FNPF_HD static void at(int64_t, const Args& a) {
+    a.cg[kDONE] = 0.0;
+    a.cg[kITERS] = 0.0;
+  }
+};
+
+struct CgAlphaItem {   // alpha = r.z / p.q (p.q <= 0 or not finite: breakdown or divergence)
+  struct Args {
+    double *cg, *hist;
+  };
+  FNPF_HD static void at(int64_t, const Args& a) {
+    double* cg = a.cg;
+    if (cg[kDONE] != 0.0) return;
+    const double pq = cg[kPQ];
+    if (!(pq > 0.0)) {
+      cg[kDONE] = pq - pq == 0.0 ? 2.0 : 3.0;
+      return;
+    }
+    const double al = cg[kRZ] / pq;
+    cg[kAL] = al;
+    if (a.hist) a.hist[2 * (int64_t)cg[kITERS]] = al;
+  }
+};
+
+struct CgUpdateItem {   // x += alpha p (x may be null), r -= alpha q
+  struct Args {
+    const double* cg;
+    const double *p, *q;
+    double *x, *r;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    if (a.cg[kDONE] != 0.0) return;
+    const double al = a.cg[kAL];
+    if (a.x) a.x[i] += al * a.p[i];
+    a.r[i] -= al * a.q[i];
+  }
+};
+
+struct CgCheckItem {   // one more completed iteration; converged when ||r|| <= stop
+  struct Args {
+    double* cg;
+    double stop;
+  };
+  FNPF_HD static void at(int64_t, const Args& a) {
+    double* cg = a.cg;
+    if (cg[kDONE] != 0.0) return;
+    cg[kITERS] += 1.0;
+    const double rr = cg[kRR];
+    if (!(rr - rr == 0.0)) cg[kDONE] = 3.0;
+    else if (sqrt(rr) <= a.stop) cg[kDONE] = 1.0;
+  }
+};
+
+struct CgBetaItem {   // beta = r.z_new / r.z, r.z = r.z_new
+  struct Args {
+    double *cg, *hist;
+  };
+  FNPF_HD static void at(int64_t, const Args& a) {
+    double* cg = a.cg;
+    if (cg[kDONE] != 0.0) return;
+    const double be = cg[kRZN] / cg[kRZ];
+    cg[kBE] = be;
+    cg[kRZ] = cg[kRZN];
+    if (a.hist) a.hist[2 * ((int64_t)cg[kITERS] - 1) + 1] = be;
+  }
+};
+
+struct CgDirItem {   // p = z + beta p
+  struct Args {
+    const double* cg;
+    const double* z;
+    double* p;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    if (a.cg[kDONE] != 0.0) return;
+    a.p[i] = a.z[i] + a.cg[kBE] * a.p[i];
+  }
+};
+
 // w = d phi / dz at surface node c: (sum_j D[p][j] phi(plane N_v - 1 - p + j)) 2 N_z / (eta + h).
 struct WItem {
   struct Args {
@@ -1245,6 +1341,58 @@ struct Stepper {
     return go<GatherItem>(m.N, {m.voff, m.vinc, w.ye, y});
   }
 
+  // *out (device) = x . y over n entries, without reading it back.
+  fnpf_status dot_dev(const double* x, const double* y, int64_t n, double* out) {
+    const int64_t np = dot_partials(n);
+    FNPF_PS_TRY(go<DotPartItem>(np, {x, y, n, w.part}));
+    return go<SumItem>(1, {w.part, np, out});
+  }
+
+  // Preconditioned CG over n entries with its scalars on the device: on entry
+  // r = b - A x; op(p, q) sets q = A p, pre(r, z) sets z = M^-1 r (p's and q's
+  // entries beyond n, if any, are the caller's).  The host reads the state
+  // after the convergence test of every iteration when check == 1 (the
+  // preconditioner of a converged iteration is then never applied), else at
+  // the end of every check-th iteration; the iterates, iteration count and
+  // residual equal those of reading every scalar at once.  x may be null
+  // (only the coefficients are wanted: hist).  *iters and *rr: completed
+  // iterations and the last r.r (unchanged when no iteration completed).
+  template <class Op, class Pre>
+  fnpf_status cg_run(int64_t n, double* x, double* r, double* z, double* p, double* q, double stop, int max_iter,
+                     int check, double* hist, Op op, Pre pre, int* iters, double* rr) {
+    double* cg = w.cg;
+    FNPF_PS_TRY(pre(r, z));
+    FNPF_PS_TRY(go<CopyItem>(n, {z, p}));
+    FNPF_PS_TRY(dot_dev(r, z, n, cg + kRZ));
+    FNPF_PS_TRY(go<CgResetItem>(1, {cg}));
+    double st[kCgSlots] = {0};
+    for (int it = 0; it < max_iter; ++it) {
+      FNPF_PS_TRY(op(p, q));
+      FNPF_PS_TRY(dot_dev(p, q, n, cg + kPQ));
+      FNPF_PS_TRY(go<CgAlphaItem>(1, {cg, hist}));
+      FNPF_PS_TRY(go<CgUpdateItem>(n, {cg, p, q, x, r}));
+      FNPF_PS_TRY(dot_dev(r, r, n, cg + kRR));
+      FNPF_PS_TRY(go<CgCheckItem>(1, {cg, stop}));
+      if (check == 1) {
+        if (ex.get(st, cg, kCgSlots)) return FNPF_ECUDA;
+        if (st[kDONE] != 0.0) break;
+      }
+      FNPF_PS_TRY(pre(r, z));
+      FNPF_PS_TRY(dot_dev(r, z, n, cg + kRZN));
+      FNPF_PS_TRY(go<CgBetaItem>(1, {cg, hist}));
+      FNPF_PS_TRY(go<CgDirItem>(n, {cg, z, p}));
+      if (check > 1 && (it + 1) % check == 0) {
+        if (ex.get(st, cg, kCgSlots)) return FNPF_ECUDA;
+        if (st[kDONE] != 0.0) break;
+      }
+    }
+    if (ex.get(st, cg, kCgSlots)) return FNPF_ECUDA;
+    *iters = (int)st[kITERS];
+    if (*iters > 0) *rr = st[kRR];   // else the caller's initial r.r stands
+    const int done = (int)st[kDONE];
+    return done == 1 ? FNPF_OK : done == 2 ? FNPF_EBREAKDOWN : done == 3 ? FNPF_EDIVERGED : FNPF_ENOCONV;
+  }
+
   // ---- p-multigrid
 
   fnpf_status geometry_level(PLevel& L, const double* eta, const double* h) {
@@ -1264,29 +1412,23 @@ struct Stepper {
   // eigenvalue by bisection on the Sturm sequence).
   fnpf_status lmax_level(PLevel& L, double* out) {
     const int64_t N = L.m.N, NI = L.m.NI;
-    const int k_max = 12;
-    double al[k_max], be[k_max];
+    const int k_max = kMaxLanczos;
+    double al[k_max], be[k_max], hist[2 * k_max];
     FNPF_PS_TRY(go<HashItem>(N, {NI, L.r}));
-    FNPF_PS_TRY(go<DivItem>(NI, {L.r, L.diag, L.x}));
-    FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, L.x, L.d}));
-    double rz = 0;
-    FNPF_PS_TRY(dot(L.r, L.x, NI, &rz));
+    FNPF_PS_TRY(go<FillItem>(N, {0.0, L.d}));   // the direction's surface plane stays zero
     int k = 0;
-    for (; k < k_max && rz > 0; ++k) {
-      FNPF_PS_TRY(apply_level(L, L.d, L.q));
-      double pq = 0;
-      FNPF_PS_TRY(dot(L.d, L.q, NI, &pq));
-      if (!(pq > 0)) break;
-      al[k] = rz / pq;
-      FNPF_PS_TRY(go<AxpyItem>(NI, {-al[k], L.q, L.r}));
-      FNPF_PS_TRY(go<DivItem>(NI, {L.r, L.diag, L.x}));
-      double rzn = 0;
-      FNPF_PS_TRY(dot(L.r, L.x, NI, &rzn));
-      be[k] = rzn / rz;
-      rz = rzn;
-      FNPF_PS_TRY(go<XpbyItem>(NI, {L.x, be[k], L.d}));
-    }
+    double rr = 0;
+    const fnpf_status cs =
+        cg_run(NI, nullptr, L.r, L.x, L.d, L.q, 0.0, k_max, k_max, w.cg + kCgSlots,
+               [&](const double* pv, double* qv) { return apply_level(L, pv, qv); },
+               [&](const double* rv, double* zv) { return go<DivItem>(NI, {rv, L.diag, zv}); }, &k, &rr);
+    if (cs == FNPF_ECUDA) return cs;
     if (k == 0) return FNPF_EBREAKDOWN;
+    if (ex.get(hist, w.cg + kCgSlots, 2 * k)) return FNPF_ECUDA;
+    for (int j = 0; j < k; ++j) {
+      al[j] = hist[2 * j];
+      be[j] = hist[2 * j + 1];
+    }
     // T[j][j] = 1/al_j + be_(j-1)/al_(j-1), T[j][j-1] = sqrt(be_(j-1))/al_(j-1)
     double dg[k_max], off[k_max];
     for (int j = 0; j < k; ++j) {
@@ -1420,39 +1562,11 @@ struct Stepper {
       FNPF_PS_TRY(go<AxpyItem>(NI, {-1.0, w.q, w.r}));          // r = b - A_II x0
       FNPF_PS_TRY(dot(w.r, w.r, NI, &rr));
       if (sqrt(rr) > stop) {
-        FNPF_PS_TRY(precond(w.r, w.z, o));
-        FNPF_PS_TRY(go<CopyItem>(NI, {w.z, w.pd}));
-        double rz = 0;
-        FNPF_PS_TRY(dot(w.r, w.z, NI, &rz));
-        st = FNPF_ENOCONV;
-        while (it < o.max_iter) {
-          FNPF_PS_TRY(apply(w.pd, w.q));
-          double pq = 0;
-          FNPF_PS_TRY(dot(w.pd, w.q, NI, &pq));
-          if (!(pq > 0)) {
-            st = isfinite(pq) ? FNPF_EBREAKDOWN : FNPF_EDIVERGED;
-            break;
-          }
-          const double alpha = rz / pq;
-          FNPF_PS_TRY(go<AxpyItem>(NI, {alpha, w.pd, phi}));
-          FNPF_PS_TRY(go<AxpyItem>(NI, {-alpha, w.q, w.r}));
-          ++it;
-          FNPF_PS_TRY(dot(w.r, w.r, NI, &rr));
-          if (!isfinite(rr)) {
-            st = FNPF_EDIVERGED;
-            break;
-          }
-          if (sqrt(rr) <= stop) {
-            st = FNPF_OK;
-            break;
-          }
-          FNPF_PS_TRY(precond(w.r, w.z, o));
-          double rzn = 0;
-          FNPF_PS_TRY(dot(w.r, w.z, NI, &rzn));
-          const double beta = rzn / rz;
-          rz = rzn;
-          FNPF_PS_TRY(go<XpbyItem>(NI, {w.z, beta, w.pd}));
-        }
+        // w.pd's surface plane is zero (above); the loop writes its first NI entries only
+        st = cg_run(NI, phi, w.r, w.z, w.pd, w.q, stop, o.max_iter, o.pmg ? 1 : 8, nullptr,
+                    [&](const double* pv, double* qv) { return apply(pv, qv); },
+                    [&](const double* rv, double* zv) { return precond(rv, zv, o); }, &it, &rr);
+        if (st == FNPF_ECUDA) return st;
       }
     }
     FNPF_PS_TRY(go<CopyItem>(m.ns, {phis, phi + NI}));
@@ -1492,30 +1606,11 @@ struct Stepper {
     if (!(bb > 0)) return bb == 0 ? FNPF_OK : FNPF_EDIVERGED;
     const double stop = o.mass_rtol * sqrt(bb);
     FNPF_PS_TRY(go<CopyItem>(ns, {b, w.mr}));
-    FNPF_PS_TRY(go<DivItem>(ns, {w.mr, m.mdiag, w.mz}));
-    FNPF_PS_TRY(go<CopyItem>(ns, {w.mz, w.mp}));
-    double rz = 0;
-    FNPF_PS_TRY(dot(w.mr, w.mz, ns, &rz));
-    for (int it = 0; it < o.mass_max_iter; ++it) {
-      FNPF_PS_TRY(go<CsrItem>(ns, {m.mrow, m.mcol, m.mval, w.mp, w.mq}));
-      double pq = 0;
-      FNPF_PS_TRY(dot(w.mp, w.mq, ns, &pq));
-      if (!(pq > 0)) return isfinite(pq) ? FNPF_EBREAKDOWN : FNPF_EDIVERGED;
-      const double alpha = rz / pq;
-      FNPF_PS_TRY(go<AxpyItem>(ns, {alpha, w.mp, x}));
-      FNPF_PS_TRY(go<AxpyItem>(ns, {-alpha, w.mq, w.mr}));
-      double rr = 0;
-      FNPF_PS_TRY(dot(w.mr, w.mr, ns, &rr));
-      if (!isfinite(rr)) return FNPF_EDIVERGED;
-      if (sqrt(rr) <= stop) return FNPF_OK;
-      FNPF_PS_TRY(go<DivItem>(ns, {w.mr, m.mdiag, w.mz}));
-      double rzn = 0;
-      FNPF_PS_TRY(dot(w.mr, w.mz, ns, &rzn));
-      const double beta = rzn / rz;
-      rz = rzn;
-      FNPF_PS_TRY(go<XpbyItem>(ns, {w.mz, beta, w.mp}));
-    }
-    return FNPF_ENOCONV;
+    int it = 0;
+    double rr = bb;
+    return cg_run(ns, x, w.mr, w.mz, w.mp, w.mq, stop, o.mass_max_iter, 8, nullptr,
+                  [&](const double* pv, double* qv) { return go<CsrItem>(ns, {m.mrow, m.mcol, m.mval, pv, qv}); },
+                  [&](const double* rv, double* zv) { return go<DivItem>(ns, {rv, m.mdiag, zv}); }, &it, &rr);
   }
 
   // w [ns] at (eta, phis): the solve (warm-started from the mesh's potential) and w.
