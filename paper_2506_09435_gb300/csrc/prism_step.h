@@ -88,6 +88,7 @@ inline void bind_tables(PMesh* m, const double* tab) {
 // Workspace of the path.
 struct PWork {
   double *G, *F, *ye, *diag;            // [nelem n nq 6], [nelem n nq 3], [nelem nt n], [N]
+  double* vt;                           // [nelem n nt] vertical derivatives, then vertical sums
   double *xs, *r, *z, *pd, *q;          // Laplace PCG [N]
   double *part, *scal;                  // dot-product partials, scalars
   double* cg;                           // CG state on the device (kCgSlots) and Lanczos coefficients
@@ -109,6 +110,7 @@ void carve(const PMesh& m, PWork* w, Take take) {
   take(&w->G, pts * 6);
   take(&w->F, pts * 3);
   take(&w->ye, m.nelem * m.nt * m.n);
+  take(&w->vt, m.nelem * m.nt * m.n);
   take(&w->diag, m.N);
   take(&w->xs, m.N);
   take(&w->r, m.N);
@@ -512,12 +514,38 @@ struct GeomItem {
   }
 };
 
-// Flux G grad_ref u at every point (u the volume field x).
+// d u / d t at element node (elem, k, c) of item i over nelem n nt (slot
+// k nt + c): the vertical GLL derivative along the node's line.
+struct DtItem {
+  struct Args {
+    PMesh m;
+    const double* x;
+    double* ut;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int64_t per = (int64_t)m.nt * m.n;
+    const int64_t elem = i / per;
+    const int idx = (int)(i - elem * per);
+    const int c = idx % m.nt, k = idx / m.nt;
+    const int e = (int)(elem / m.nz), l = (int)(elem - (int64_t)e * m.nz);
+    const int64_t col = m.tn[(int64_t)e * m.nt + c];
+    const double* Dk = m.D + (int64_t)k * m.n;
+    const int64_t plane0 = (int64_t)l * m.p;
+    double s = 0;
+    for (int mm = 0; mm < m.n; ++mm) s += Dk[mm] * a.x[(plane0 + mm) * m.ns + col];
+    a.ut[i] = s;
+  }
+};
+
+// Flux G grad_ref u at every point (u the volume field x, ut its vertical
+// derivatives at the element nodes from DtItem).
 struct FluxItem {
   struct Args {
     PMesh m;
     const double* G;
     const double* x;
+    const double* ut;
     double* F;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
@@ -528,17 +556,14 @@ struct FluxItem {
     const double* Lq = m.L + (int64_t)pi.q * nt;
     const double* Lrq = m.Lr + (int64_t)pi.q * nt;
     const double* Lsq = m.Ls + (int64_t)pi.q * nt;
-    const double* Dk = m.D + (int64_t)pi.k * n;
-    const int64_t plane0 = (int64_t)pi.l * m.p;
+    const double* xk = a.x + ((int64_t)pi.l * m.p + pi.k) * m.ns;
+    const double* utk = a.ut + (pi.elem * n + pi.k) * nt;
     double ur = 0, us = 0, ut = 0;
     for (int c = 0; c < nt; ++c) {
-      const int64_t col = tn[c];
-      const double u = a.x[(plane0 + pi.k) * m.ns + col];
+      const double u = xk[tn[c]];
       ur += Lrq[c] * u;
       us += Lsq[c] * u;
-      double uc = 0;
-      for (int mm = 0; mm < n; ++mm) uc += Dk[mm] * a.x[(plane0 + mm) * m.ns + col];
-      ut += Lq[c] * uc;
+      ut += Lq[c] * utk[c];
     }
     const double* G = a.G + 6 * i;
     double* F = a.F + 3 * i;
@@ -571,6 +596,7 @@ struct NodeItem {
   struct Args {
     PMesh m;
     const double* F;
+    const double* vs;   // [nelem n nt] from TSumItem
     double* ye;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
@@ -580,13 +606,31 @@ struct NodeItem {
     const double* Fm = a.F + 3 * (ni.base + (int64_t)ni.mm * nq);
     double y = 0;
     for (int q = 0; q < nq; ++q) y += m.Lr[(int64_t)q * nt + ni.c] * Fm[3 * q] + m.Ls[(int64_t)q * nt + ni.c] * Fm[3 * q + 1];
-    for (int k = 0; k < n; ++k) {
-      const double* Fk = a.F + 3 * (ni.base + (int64_t)k * nq);
-      double s = 0;
-      for (int q = 0; q < nq; ++q) s += m.L[(int64_t)q * nt + ni.c] * Fk[3 * q + 2];
-      y += m.D[(int64_t)k * n + ni.mm] * s;
-    }
+    const double* vs = a.vs + ni.elem * n * nt + ni.c;
+    for (int k = 0; k < n; ++k) y += m.D[(int64_t)k * n + ni.mm] * vs[(int64_t)k * nt];
     a.ye[i] = y;
+  }
+};
+
+// The vertical flux contracted over the triangle points, at (elem, k, c) of
+// item i over nelem n nt (slot k nt + c): sum over q of L[q][c] F_t(k, q) (the
+// part of NodeItem's transposed contraction shared by the n nodes of a line).
+struct TSumItem {
+  struct Args {
+    PMesh m;
+    const double* F;
+    double* vs;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int64_t per = (int64_t)m.nt * m.n;
+    const int64_t elem = i / per;
+    const int idx = (int)(i - elem * per);
+    const int c = idx % m.nt, k = idx / m.nt;
+    const double* Fk = a.F + 3 * (elem * m.n * m.nq + (int64_t)k * m.nq);
+    double s = 0;
+    for (int q = 0; q < m.nq; ++q) s += m.L[(int64_t)q * m.nt + c] * Fk[3 * q + 2];
+    a.vs[i] = s;
   }
 };
 
@@ -1156,6 +1200,7 @@ struct HashItem {
 struct PLevel {
   PMesh m;
   double *G, *F, *ye, *diag;   // metric, fluxes, element results, Jacobi diagonal
+  double* vt;                  // vertical derivatives and sums of the operator
   double *eta, *h;             // [ns] geometry (level 0: the caller's arrays)
   double *x, *b, *r, *d, *q;   // [N] smoother and V-cycle vectors
   double lo, hi;               // Chebyshev interval of D^-1 A
@@ -1185,6 +1230,7 @@ void carve_level(const PMesh& m, bool own_operator, PLevel* L, Take take) {
     take(&L->G, pts * 6);
     take(&L->F, pts * 3);
     take(&L->ye, m.nelem * m.nt * m.n);
+    take(&L->vt, m.nelem * m.nt * m.n);
     take(&L->diag, m.N);
     take(&L->eta, m.ns);
     take(&L->h, m.ns);
@@ -1213,6 +1259,7 @@ bool build_pmg(const PMesh& m0, const PWork& w0, const double* verts, int nverts
   L0.G = w0.G;
   L0.F = w0.F;
   L0.ye = w0.ye;
+  L0.vt = w0.vt;
   L0.diag = w0.diag;
   carve_level(m0, false, &L0, take);
   for (int l = 1; l < nl; ++l) {
@@ -1315,6 +1362,16 @@ struct Stepper {
     return ex.template run<It>(n, a) ? FNPF_ECUDA : FNPF_OK;
   }
 
+  // The element results ye of A x on the mesh view mv with its metric G (the
+  // vertical derivatives, the fluxes, the vertical sums, the node contractions).
+  fnpf_status elements(const PMesh& mv, const double* G, double* F, double* ye, double* vt, const double* x) {
+    const int64_t nodes = mv.nelem * mv.nt * mv.n;
+    FNPF_PS_TRY(go<DtItem>(nodes, {mv, x, vt}));
+    FNPF_PS_TRY(go<FluxItem>(mv.nelem * mv.n * mv.nq, {mv, G, x, vt, F}));
+    FNPF_PS_TRY(go<TSumItem>(nodes, {mv, F, vt}));
+    return go<NodeItem>(nodes, {mv, F, vt, ye});
+  }
+
   // *out = x . y over n entries (two launches and a read of the scalar).
   fnpf_status dot(const double* x, const double* y, int64_t n, double* out) {
     if (n <= 0) {
@@ -1336,8 +1393,7 @@ struct Stepper {
 
   // y = A x with the stored G (the full operator, surface rows included).
   fnpf_status apply(const double* x, double* y) {
-    FNPF_PS_TRY(go<FluxItem>(m.nelem * m.n * m.nq, {m, w.G, x, w.F}));
-    FNPF_PS_TRY(go<NodeItem>(m.nelem * m.nt * m.n, {m, w.F, w.ye}));
+    FNPF_PS_TRY(elements(m, w.G, w.F, w.ye, w.vt, x));
     return go<GatherItem>(m.N, {m.voff, m.vinc, w.ye, y});
   }
 
@@ -1402,8 +1458,7 @@ struct Stepper {
   }
 
   fnpf_status apply_level(PLevel& L, const double* x, double* y) {
-    FNPF_PS_TRY(go<FluxItem>(L.m.nelem * L.m.n * L.m.nq, {L.m, L.G, x, L.F}));
-    FNPF_PS_TRY(go<NodeItem>(L.m.nelem * L.m.nt * L.m.n, {L.m, L.F, L.ye}));
+    FNPF_PS_TRY(elements(L.m, L.G, L.F, L.ye, L.vt, x));
     return go<GatherItem>(L.m.N, {L.m.voff, L.m.vinc, L.ye, y});
   }
 
@@ -1476,8 +1531,7 @@ struct Stepper {
 
   // The element results of A x on level L (the operator without its gather).
   fnpf_status element_level(PLevel& L, const double* x) {
-    FNPF_PS_TRY(go<FluxItem>(L.m.nelem * L.m.n * L.m.nq, {L.m, L.G, x, L.F}));
-    return go<NodeItem>(L.m.nelem * L.m.nt * L.m.n, {L.m, L.F, L.ye});
+    return elements(L.m, L.G, L.F, L.ye, L.vt, x);
   }
 
   // deg Chebyshev steps on level L: x and r = b - A x (both in, both out; r
