@@ -559,6 +559,9 @@ typedef struct {
   int cheb_degree;         /* FNPF_PMG: Chebyshev degree of pre/post smoothing (3) */
   int coarse_iters;        /* FNPF_PMG: Chebyshev degree on the coarsest level (6) */
   double cheb_range;       /* FNPF_PMG: smoothers act on [lmax / range, lmax] (40) */
+  int precision;           /* FNPF_FP64 (default) or FNPF_FP64_PC32: FP64 PCG with
+                              the V-cycle in FP32 (FP32 tables, metric, vectors;
+                              FNPF_PMG only, FNPF_FP64 with Jacobi)             */
 } fnpf_prism_opts;
 void fnpf_prism_default_opts(fnpf_prism_opts* opts);
 fnpf_status fnpf_prism_diagonal(fnpf_prism* mesh, const double* eta, const double* h, double* diag, void* stream);

@@ -70,7 +70,16 @@ struct PMesh {
   const double *rcr, *rgen;             // [ns] relaxation weight C_r and generation flag (null: no zones)
   const double *xs, *ys;                // [ns] surface node coordinates (the incident wave's phase)
   double ramp, amp, kx, ky, omega, phase;   // incident wave of the generation zones
+  const float *Lf, *Lrf, *Lsf, *Df;     // FP32 copies of L, Lr, Ls, D (levels of an FP32 V-cycle)
 };
+
+// The operator tables of a mesh view in the value type T of a computation.
+template <class T>
+struct Tabs {
+  const T *L, *Lr, *Ls, *D;
+};
+FNPF_HD inline Tabs<double> tabs_of(const PMesh& m, const double*) { return {m.L, m.Lr, m.Ls, m.D}; }
+FNPF_HD inline Tabs<float> tabs_of(const PMesh& m, const float*) { return {m.Lf, m.Lrf, m.Lsf, m.Df}; }
 
 // Points the table pointers of m into the packed tables of fnpf_prism_create:
 // geo [4 ntri], L, Lr, Ls [nq nt], wq [nq], xi [n], wv [n], D [n n].
@@ -516,62 +525,68 @@ struct GeomItem {
 
 // d u / d t at element node (elem, k, c) of item i over nelem n nt (slot
 // k nt + c): the vertical GLL derivative along the node's line.
-struct DtItem {
+template <class T>
+struct DtItemT {
   struct Args {
     PMesh m;
-    const double* x;
-    double* ut;
+    const T* x;
+    T* ut;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
     const PMesh& m = a.m;
+    const Tabs<T> tb = tabs_of(m, (const T*)nullptr);
     const int64_t per = (int64_t)m.nt * m.n;
     const int64_t elem = i / per;
     const int idx = (int)(i - elem * per);
     const int c = idx % m.nt, k = idx / m.nt;
     const int e = (int)(elem / m.nz), l = (int)(elem - (int64_t)e * m.nz);
     const int64_t col = m.tn[(int64_t)e * m.nt + c];
-    const double* Dk = m.D + (int64_t)k * m.n;
+    const T* Dk = tb.D + (int64_t)k * m.n;
     const int64_t plane0 = (int64_t)l * m.p;
-    double s = 0;
+    T s = 0;
     for (int mm = 0; mm < m.n; ++mm) s += Dk[mm] * a.x[(plane0 + mm) * m.ns + col];
     a.ut[i] = s;
   }
 };
+using DtItem = DtItemT<double>;
 
 // Flux G grad_ref u at every point (u the volume field x, ut its vertical
 // derivatives at the element nodes from DtItem).
-struct FluxItem {
+template <class T>
+struct FluxItemT {
   struct Args {
     PMesh m;
-    const double* G;
-    const double* x;
-    const double* ut;
-    double* F;
+    const T* G;
+    const T* x;
+    const T* ut;
+    T* F;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
     const PMesh& m = a.m;
+    const Tabs<T> tb = tabs_of(m, (const T*)nullptr);
     const PointIdx pi = point_of(m, i);
     const int nt = m.nt, n = m.n;
     const int* tn = m.tn + (int64_t)pi.e * nt;
-    const double* Lq = m.L + (int64_t)pi.q * nt;
-    const double* Lrq = m.Lr + (int64_t)pi.q * nt;
-    const double* Lsq = m.Ls + (int64_t)pi.q * nt;
-    const double* xk = a.x + ((int64_t)pi.l * m.p + pi.k) * m.ns;
-    const double* utk = a.ut + (pi.elem * n + pi.k) * nt;
-    double ur = 0, us = 0, ut = 0;
+    const T* Lq = tb.L + (int64_t)pi.q * nt;
+    const T* Lrq = tb.Lr + (int64_t)pi.q * nt;
+    const T* Lsq = tb.Ls + (int64_t)pi.q * nt;
+    const T* xk = a.x + ((int64_t)pi.l * m.p + pi.k) * m.ns;
+    const T* utk = a.ut + (pi.elem * n + pi.k) * nt;
+    T ur = 0, us = 0, ut = 0;
     for (int c = 0; c < nt; ++c) {
-      const double u = xk[tn[c]];
+      const T u = xk[tn[c]];
       ur += Lrq[c] * u;
       us += Lsq[c] * u;
       ut += Lq[c] * utk[c];
     }
-    const double* G = a.G + 6 * i;
-    double* F = a.F + 3 * i;
+    const T* G = a.G + 6 * i;
+    T* F = a.F + 3 * i;
     F[0] = G[0] * ur + G[1] * us + G[2] * ut;
     F[1] = G[1] * ur + G[3] * us + G[4] * ut;
     F[2] = G[2] * ur + G[4] * us + G[5] * ut;
   }
 };
+using FluxItem = FluxItemT<double>;
 
 // Local node (elem, mm, c) of item i over nelem nt n; slot = mm nt + c.
 struct NodeIdx {
@@ -592,47 +607,53 @@ FNPF_HD inline NodeIdx node_of(const PMesh& m, int64_t i) {
 // Element result at local node (c, mm): the transposed contractions of the
 // fluxes with the basis gradients, sum over the points (q, k) of
 // (delta_k,mm L_r[q][c], delta_k,mm L_s[q][c], L[q][c] D[k][mm]) . F(q, k).
-struct NodeItem {
+template <class T>
+struct NodeItemT {
   struct Args {
     PMesh m;
-    const double* F;
-    const double* vs;   // [nelem n nt] from TSumItem
-    double* ye;
+    const T* F;
+    const T* vs;   // [nelem n nt] from TSumItem
+    T* ye;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
     const PMesh& m = a.m;
+    const Tabs<T> tb = tabs_of(m, (const T*)nullptr);
     const NodeIdx ni = node_of(m, i);
     const int nt = m.nt, nq = m.nq, n = m.n;
-    const double* Fm = a.F + 3 * (ni.base + (int64_t)ni.mm * nq);
-    double y = 0;
-    for (int q = 0; q < nq; ++q) y += m.Lr[(int64_t)q * nt + ni.c] * Fm[3 * q] + m.Ls[(int64_t)q * nt + ni.c] * Fm[3 * q + 1];
-    const double* vs = a.vs + ni.elem * n * nt + ni.c;
-    for (int k = 0; k < n; ++k) y += m.D[(int64_t)k * n + ni.mm] * vs[(int64_t)k * nt];
+    const T* Fm = a.F + 3 * (ni.base + (int64_t)ni.mm * nq);
+    T y = 0;
+    for (int q = 0; q < nq; ++q) y += tb.Lr[(int64_t)q * nt + ni.c] * Fm[3 * q] + tb.Ls[(int64_t)q * nt + ni.c] * Fm[3 * q + 1];
+    const T* vs = a.vs + ni.elem * n * nt + ni.c;
+    for (int k = 0; k < n; ++k) y += tb.D[(int64_t)k * n + ni.mm] * vs[(int64_t)k * nt];
     a.ye[i] = y;
   }
 };
+using NodeItem = NodeItemT<double>;
 
 // The vertical flux contracted over the triangle points, at (elem, k, c) of
 // item i over nelem n nt (slot k nt + c): sum over q of L[q][c] F_t(k, q) (the
 // part of NodeItem's transposed contraction shared by the n nodes of a line).
-struct TSumItem {
+template <class T>
+struct TSumItemT {
   struct Args {
     PMesh m;
-    const double* F;
-    double* vs;
+    const T* F;
+    T* vs;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
     const PMesh& m = a.m;
+    const Tabs<T> tb = tabs_of(m, (const T*)nullptr);
     const int64_t per = (int64_t)m.nt * m.n;
     const int64_t elem = i / per;
     const int idx = (int)(i - elem * per);
     const int c = idx % m.nt, k = idx / m.nt;
-    const double* Fk = a.F + 3 * (elem * m.n * m.nq + (int64_t)k * m.nq);
-    double s = 0;
-    for (int q = 0; q < m.nq; ++q) s += m.L[(int64_t)q * m.nt + c] * Fk[3 * q + 2];
+    const T* Fk = a.F + 3 * (elem * m.n * m.nq + (int64_t)k * m.nq);
+    T s = 0;
+    for (int q = 0; q < m.nq; ++q) s += tb.L[(int64_t)q * m.nt + c] * Fk[3 * q + 2];
     a.vs[i] = s;
   }
 };
+using TSumItem = TSumItemT<double>;
 
 // Element diagonal at local node (c, mm): sum over the points of g^T G g with g
 // the reference gradient of that node's basis function.
@@ -663,18 +684,20 @@ struct DiagItem {
 };
 
 // y_g = sum of the element results of node g, in incidence order.
-struct GatherItem {
+template <class T>
+struct GatherItemT {
   struct Args {
     const int64_t *off, *inc;
-    const double* ye;
-    double* y;
+    const T* ye;
+    T* y;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
-    double s = 0;
+    T s = 0;
     for (int64_t j = a.off[i]; j < a.off[i + 1]; ++j) s += a.ye[a.inc[j]];
     a.y[i] = s;
   }
 };
+using GatherItem = GatherItemT<double>;
 
 // x = [0 (interior); phis (surface plane)] over N.
 struct SurfaceOnlyItem {
@@ -687,15 +710,17 @@ struct SurfaceOnlyItem {
 };
 
 // out = [s src (interior); 0 (surface plane)] over N.
-struct InteriorItem {
+template <class T>
+struct InteriorItemT {
   struct Args {
     int64_t NI;
     double s;
-    const double* src;
-    double* out;
+    const T* src;
+    T* out;
   };
-  FNPF_HD static void at(int64_t i, const Args& a) { a.out[i] = i < a.NI ? a.s * a.src[i] : 0.0; }
+  FNPF_HD static void at(int64_t i, const Args& a) { a.out[i] = i < a.NI ? (T)a.s * a.src[i] : (T)0; }
 };
+using InteriorItem = InteriorItemT<double>;
 
 struct AxpyItem {   // y += s x
   struct Args {
@@ -741,12 +766,24 @@ struct CopyItem {
   FNPF_HD static void at(int64_t i, const Args& a) { a.dst[i] = a.src[i]; }
 };
 
-struct FillItem {
+template <class T>
+struct FillItemT {
   struct Args {
     double v;
-    double* dst;
+    T* dst;
   };
-  FNPF_HD static void at(int64_t i, const Args& a) { a.dst[i] = a.v; }
+  FNPF_HD static void at(int64_t i, const Args& a) { a.dst[i] = (T)a.v; }
+};
+using FillItem = FillItemT<double>;
+
+// out = (To) in: the precision changes at the FP32 V-cycle's entry and exit.
+template <class To, class From>
+struct CastItem {
+  struct Args {
+    const From* in;
+    To* out;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.out[i] = (To)a.in[i]; }
 };
 
 // part[i] = sum of x_j y_j over the i-th chunk of kChunk entries (fixed order).
@@ -1028,16 +1065,22 @@ struct FilterWriteItem {
 
 struct PXfer {
   const double *Ptri, *Pv, *Etri;   // transfer_tables, fine level -> next coarser level
+  const float *Ptri_f, *Pv_f;       // FP32 copies of Ptri and Pv
 };
+FNPF_HD inline const double* ptri_of(const PXfer& t, const double*) { return t.Ptri; }
+FNPF_HD inline const float* ptri_of(const PXfer& t, const float*) { return t.Ptri_f; }
+FNPF_HD inline const double* pv_of(const PXfer& t, const double*) { return t.Pv; }
+FNPF_HD inline const float* pv_of(const PXfer& t, const float*) { return t.Pv_f; }
 
 // x_f[g] += (P x_c)[g] at every interior fine node g: the coarse element
 // polynomial of the node's first element evaluated at the node.
-struct ProlongItem {
+template <class T>
+struct ProlongItemT {
   struct Args {
     PMesh f, c;
     PXfer t;
-    const double* xc;
-    double* xf;
+    const T* xc;
+    T* xf;
   };
   FNPF_HD static void at(int64_t g, const Args& a) {
     if (g >= a.f.NI) return;
@@ -1048,29 +1091,31 @@ struct ProlongItem {
     const int cf = idx % a.f.nt, mf = idx / a.f.nt;
     const int e = (int)(elem / a.f.nz), l = (int)(elem - (int64_t)e * a.f.nz);
     const int* tnc = a.c.tn + (int64_t)e * a.c.nt;
-    const double* Pt = a.t.Ptri + (int64_t)cf * a.c.nt;
-    const double* Pv = a.t.Pv + (int64_t)mf * a.c.n;
-    double s = 0;
+    const T* Pt = ptri_of(a.t, (const T*)nullptr) + (int64_t)cf * a.c.nt;
+    const T* Pv = pv_of(a.t, (const T*)nullptr) + (int64_t)mf * a.c.n;
+    T s = 0;
     for (int mc = 0; mc < a.c.n; ++mc) {
-      const double* xp = a.xc + ((int64_t)l * a.c.p + mc) * a.c.ns;
-      double sc = 0;
+      const T* xp = a.xc + ((int64_t)l * a.c.p + mc) * a.c.ns;
+      T sc = 0;
       for (int k = 0; k < a.c.nt; ++k) sc += Pt[k] * xp[tnc[k]];
       s += Pv[mc] * sc;
     }
     a.xf[g] += s;
   }
 };
+using ProlongItem = ProlongItemT<double>;
 
 // Element result of coarse local node (c', m') of coarse element elem: the
 // transposed interpolation of the fine residual, each fine node's value
 // divided by the number of fine elements that share it (so that the gather
 // over the coarse elements gives P^T r exactly).
-struct RestrictItem {
+template <class T>
+struct RestrictItemT {
   struct Args {
     PMesh f, c;
     PXfer t;
-    const double* rf;
-    double* yec;
+    const T* rf;
+    T* yec;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
     const int64_t per = (int64_t)a.c.nt * a.c.n;
@@ -1079,21 +1124,24 @@ struct RestrictItem {
     const int cc = idx % a.c.nt, mc = idx / a.c.nt;
     const int e = (int)(elem / a.c.nz), l = (int)(elem - (int64_t)e * a.c.nz);
     const int* tnf = a.f.tn + (int64_t)e * a.f.nt;
-    double s = 0;
+    const T* Ptri = ptri_of(a.t, (const T*)nullptr);
+    const T* Pvt = pv_of(a.t, (const T*)nullptr);
+    T s = 0;
     for (int mf = 0; mf < a.f.n; ++mf) {
-      const double pv = a.t.Pv[(int64_t)mf * a.c.n + mc];
+      const T pv = Pvt[(int64_t)mf * a.c.n + mc];
       const int64_t plane = ((int64_t)l * a.f.p + mf) * a.f.ns;
-      double sf = 0;
+      T sf = 0;
       for (int k = 0; k < a.f.nt; ++k) {
         const int64_t g = plane + tnf[k];
-        const double mult = (double)(a.f.voff[g + 1] - a.f.voff[g]);
-        sf += a.t.Ptri[(int64_t)k * a.c.nt + cc] * a.rf[g] / mult;
+        const T mult = (T)(a.f.voff[g + 1] - a.f.voff[g]);
+        sf += Ptri[(int64_t)k * a.c.nt + cc] * a.rf[g] / mult;
       }
       s += pv * sf;
     }
     a.yec[i] = s;
   }
 };
+using RestrictItem = RestrictItemT<double>;
 
 // eta and h at coarse surface node J: the fine triangle polynomial of J's
 // first triangle evaluated at J.
@@ -1120,61 +1168,67 @@ struct CoarseGeoItem {
 };
 
 // One Chebyshev step: d = s d + c D^-1 r, x += d.
-struct ChebItem {
+template <class T>
+struct ChebItemT {
   struct Args {
     double s, c;
-    const double *r, *diag;
-    double *d, *x;
+    const T *r, *diag;
+    T *d, *x;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
-    const double d = a.s * a.d[i] + a.c * a.r[i] / a.diag[i];
+    const T d = (T)a.s * a.d[i] + (T)a.c * a.r[i] / a.diag[i];
     a.d[i] = d;
     a.x[i] += d;
   }
 };
+using ChebItem = ChebItemT<double>;
 
 // The end of one Chebyshev step at interior node g: q = the gathered element
 // results of A d (d the previous direction), r -= q, d = s d + c D^-1 r, x += d
 // (the gather, the residual update and the smoother update of one step in one
 // pass; only node g's own entries are written).
-struct GatherChebItem {
+template <class T>
+struct GatherChebItemT {
   struct Args {
     const int64_t *off, *inc;
-    const double* ye;
+    const T* ye;
     int64_t NI;
     double s, c;
-    const double* diag;
-    double *r, *d, *x;
+    const T* diag;
+    T *r, *d, *x;
   };
   FNPF_HD static void at(int64_t g, const Args& a) {
     if (g >= a.NI) return;
-    double q = 0;
+    T q = 0;
     for (int64_t j = a.off[g]; j < a.off[g + 1]; ++j) q += a.ye[a.inc[j]];
-    const double r = a.r[g] - q;
-    const double d = a.s * a.d[g] + a.c * r / a.diag[g];
+    const T r = a.r[g] - q;
+    const T d = (T)a.s * a.d[g] + (T)a.c * r / a.diag[g];
     a.r[g] = r;
     a.d[g] = d;
     a.x[g] += d;
   }
 };
+using GatherChebItem = GatherChebItemT<double>;
 
 // r = b - (gathered element results) at interior node g (r's surface plane
 // untouched): the residual after an operator application.
-struct GatherResidualItem {
+template <class T>
+struct GatherResidualItemT {
   struct Args {
     const int64_t *off, *inc;
-    const double* ye;
+    const T* ye;
     int64_t NI;
-    const double* b;
-    double* r;
+    const T* b;
+    T* r;
   };
   FNPF_HD static void at(int64_t g, const Args& a) {
     if (g >= a.NI) return;
-    double q = 0;
+    T q = 0;
     for (int64_t j = a.off[g]; j < a.off[g + 1]; ++j) q += a.ye[a.inc[j]];
     a.r[g] = a.b[g] - q;
   }
 };
+using GatherResidualItem = GatherResidualItemT<double>;
 
 // A fixed pseudo-random vector in [-1, 1) on the interior (splitmix64 of the
 // index), zero on the surface plane: the start of the eigenvalue estimate.
@@ -1204,7 +1258,20 @@ struct PLevel {
   double *eta, *h;             // [ns] geometry (level 0: the caller's arrays)
   double *x, *b, *r, *d, *q;   // [N] smoother and V-cycle vectors
   double lo, hi;               // Chebyshev interval of D^-1 A
+  // FP32 copies for an FP32 V-cycle: metric, fluxes, element results, vertical
+  // terms, diagonal and vectors
+  float *G32, *F32, *ye32, *vt32, *diag32, *x32, *b32, *r32, *d32, *q32;
 };
+
+// A level's buffers in the value type T of a V-cycle.
+template <class T>
+struct LView {
+  T *G, *F, *ye, *vt, *diag, *x, *b, *r, *d, *q;
+};
+inline LView<double> view_of(PLevel& L, const double*) { return {L.G, L.F, L.ye, L.vt, L.diag, L.x, L.b, L.r, L.d, L.q}; }
+inline LView<float> view_of(PLevel& L, const float*) {
+  return {L.G32, L.F32, L.ye32, L.vt32, L.diag32, L.x32, L.b32, L.r32, L.d32, L.q32};
+}
 
 struct PMG {
   int nlev = 0;
@@ -1237,6 +1304,34 @@ void carve_level(const PMesh& m, bool own_operator, PLevel* L, Take take) {
   }
   double** v[] = {&L->x, &L->b, &L->r, &L->d, &L->q};
   for (double** p : v) take(p, m.N);
+  // FP32 buffers (a float buffer of c entries takes (c + 1) / 2 doubles)
+  auto takef = [&](float** p, int64_t c) {
+    double* d = nullptr;
+    take(&d, (c + 1) / 2);
+    *p = reinterpret_cast<float*>(d);
+  };
+  takef(&L->G32, pts * 6);
+  takef(&L->F32, pts * 3);
+  takef(&L->ye32, m.nelem * m.nt * m.n);
+  takef(&L->vt32, m.nelem * m.nt * m.n);
+  takef(&L->diag32, m.N);
+  float** vf[] = {&L->x32, &L->b32, &L->r32, &L->d32, &L->q32};
+  for (float** p : vf) takef(p, m.N);
+}
+
+// FP32 copies of a level's operator tables, from the host copy of its packed
+// FP64 tables (the layout of bind_tables).
+template <class Up>
+bool float_tables(PMesh* pm, const double* host_tab, Up up) {
+  PMesh hv = *pm;
+  bind_tables(&hv, host_tab);
+  auto cvt = [](const double* a, int64_t n) { return std::vector<float>(a, a + n); };
+  const int64_t qt = (int64_t)pm->nq * pm->nt;
+  pm->Lf = up(cvt(hv.L, qt));
+  pm->Lrf = up(cvt(hv.Lr, qt));
+  pm->Lsf = up(cvt(hv.Ls, qt));
+  pm->Df = up(cvt(hv.D, (int64_t)pm->n * pm->n));
+  return pm->Lf && pm->Lrf && pm->Lsf && pm->Df;
 }
 
 // The hierarchy of a mesh of order p over the triangles (verts, tris), level 0
@@ -1261,6 +1356,7 @@ bool build_pmg(const PMesh& m0, const PWork& w0, const double* verts, int nverts
   L0.ye = w0.ye;
   L0.vt = w0.vt;
   L0.diag = w0.diag;
+  if (!float_tables(&L0.m, H[0].tab.data(), up)) return false;
   carve_level(m0, false, &L0, take);
   for (int l = 1; l < nl; ++l) {
     PMesh pm{};
@@ -1279,6 +1375,7 @@ bool build_pmg(const PMesh& m0, const PWork& w0, const double* verts, int nverts
     const double* tab = up(H[l].tab);
     if (!pm.tn || !tab) return false;
     bind_tables(&pm, tab);
+    if (!float_tables(&pm, H[l].tab.data(), up)) return false;
     pm.voff = up(H[l].voff);
     pm.vinc = up(H[l].vinc);
     pm.soff = up(H[l].soff);
@@ -1292,8 +1389,9 @@ bool build_pmg(const PMesh& m0, const PWork& w0, const double* verts, int nverts
   for (int l = 0; l + 1 < nl; ++l) {
     std::vector<double> Pt, Pv, Et;
     if (!transfer_tables(H[l], H[l + 1], &Pt, &Pv, &Et)) return false;
-    pmg->xf[l] = PXfer{up(Pt), up(Pv), up(Et)};
-    if (!pmg->xf[l].Ptri || !pmg->xf[l].Pv || !pmg->xf[l].Etri) return false;
+    pmg->xf[l] = PXfer{up(Pt), up(Pv), up(Et), up(std::vector<float>(Pt.begin(), Pt.end())),
+                        up(std::vector<float>(Pv.begin(), Pv.end()))};
+    if (!pmg->xf[l].Ptri || !pmg->xf[l].Pv || !pmg->xf[l].Etri || !pmg->xf[l].Ptri_f || !pmg->xf[l].Pv_f) return false;
   }
   return true;
 }
@@ -1341,11 +1439,12 @@ struct Params {
   int cheb_degree;    // Chebyshev degree of the pre- and post-smoothing
   int coarse_degree;  // Chebyshev degree on the coarsest level
   double cheb_range;  // the smoothers act on [lmax / cheb_range, lmax]
+  int pc32;           // 1: the V-cycle in FP32 (FP64 PCG around it)
 };
 
-#define FNPF_PS_TRY(x)                   \
+#define FNPF_PS_TRY(...)                 \
   do {                                   \
-    const fnpf_status st_ = (x);         \
+    const fnpf_status st_ = (__VA_ARGS__); \
     if (st_ != FNPF_OK) return st_;      \
   } while (0)
 
@@ -1364,12 +1463,13 @@ struct Stepper {
 
   // The element results ye of A x on the mesh view mv with its metric G (the
   // vertical derivatives, the fluxes, the vertical sums, the node contractions).
-  fnpf_status elements(const PMesh& mv, const double* G, double* F, double* ye, double* vt, const double* x) {
+  template <class T>
+  fnpf_status elements(const PMesh& mv, const T* G, T* F, T* ye, T* vt, const T* x) {
     const int64_t nodes = mv.nelem * mv.nt * mv.n;
-    FNPF_PS_TRY(go<DtItem>(nodes, {mv, x, vt}));
-    FNPF_PS_TRY(go<FluxItem>(mv.nelem * mv.n * mv.nq, {mv, G, x, vt, F}));
-    FNPF_PS_TRY(go<TSumItem>(nodes, {mv, F, vt}));
-    return go<NodeItem>(nodes, {mv, F, vt, ye});
+    FNPF_PS_TRY(go<DtItemT<T>>(nodes, {mv, x, vt}));
+    FNPF_PS_TRY(go<FluxItemT<T>>(mv.nelem * mv.n * mv.nq, {mv, G, x, vt, F}));
+    FNPF_PS_TRY(go<TSumItemT<T>>(nodes, {mv, F, vt}));
+    return go<NodeItemT<T>>(nodes, {mv, F, vt, ye});
   }
 
   // *out = x . y over n entries (two launches and a read of the scalar).
@@ -1525,58 +1625,68 @@ struct Stepper {
       FNPF_PS_TRY(lmax_level(L, &lmax));
       L.hi = 1.1 * lmax;
       L.lo = L.hi / o.cheb_range;
+      if (o.pc32) {   // the FP32 V-cycle's metric and diagonal: the FP64 ones rounded
+        FNPF_PS_TRY(go<CastItem<float, double>>(L.m.nelem * L.m.n * L.m.nq * 6, {L.G, L.G32}));
+        FNPF_PS_TRY(go<CastItem<float, double>>(L.m.N, {L.diag, L.diag32}));
+      }
     }
     return FNPF_OK;
   }
 
-  // The element results of A x on level L (the operator without its gather).
-  fnpf_status element_level(PLevel& L, const double* x) {
-    return elements(L.m, L.G, L.F, L.ye, L.vt, x);
-  }
-
-  // deg Chebyshev steps on level L: x and r = b - A x (both in, both out; r
-  // updated at the end only if need_r).  Step k > 0 is the element results of
-  // A d_(k-1) followed by one fused gather-and-update pass.
-  fnpf_status cheb(PLevel& L, double* x, double* r, int deg, bool need_r) {
+  // deg Chebyshev steps on level L in the value type T (its buffers v): x and
+  // r = b - A x (both in, both out; r updated at the end only if need_r).  Step
+  // k > 0 is the element results of A d_(k-1) followed by one fused
+  // gather-and-update pass.
+  template <class T>
+  fnpf_status cheb(PLevel& L, const LView<T>& v, T* x, T* r, int deg, bool need_r) {
     const int64_t N = L.m.N, NI = L.m.NI;
     const double theta = 0.5 * (L.hi + L.lo), delta = 0.5 * (L.hi - L.lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
-    FNPF_PS_TRY(go<FillItem>(N, {0.0, L.d}));
-    FNPF_PS_TRY(go<ChebItem>(NI, {0.0, 1.0 / theta, r, L.diag, L.d, x}));
+    FNPF_PS_TRY(go<FillItemT<T>>(N, {0.0, v.d}));
+    FNPF_PS_TRY(go<ChebItemT<T>>(NI, {0.0, 1.0 / theta, r, v.diag, v.d, x}));
     for (int k = 1; k < deg; ++k) {
-      FNPF_PS_TRY(element_level(L, L.d));
+      FNPF_PS_TRY(elements<T>(L.m, v.G, v.F, v.ye, v.vt, v.d));
       const double rn = 1.0 / (2.0 * sigma - rho);
-      FNPF_PS_TRY(go<GatherChebItem>(N, {L.m.voff, L.m.vinc, L.ye, NI, rn * rho, 2.0 * rn / delta, L.diag, r, L.d, x}));
+      FNPF_PS_TRY(go<GatherChebItemT<T>>(N, {L.m.voff, L.m.vinc, v.ye, NI, rn * rho, 2.0 * rn / delta, v.diag, r, v.d, x}));
       rho = rn;
     }
     if (!need_r) return FNPF_OK;
-    FNPF_PS_TRY(element_level(L, L.d));
-    return go<GatherResidualItem>(N, {L.m.voff, L.m.vinc, L.ye, NI, r, r});
+    FNPF_PS_TRY(elements<T>(L.m, v.G, v.F, v.ye, v.vt, v.d));
+    return go<GatherResidualItemT<T>>(N, {L.m.voff, L.m.vinc, v.ye, NI, r, r});
   }
 
-  // x = M_l^-1 b: one V-cycle from x = 0 (b and x: interior values, surface plane zero).
-  fnpf_status vcycle(int l, const double* b, double* x, const Params& o) {
+  // x = M_l^-1 b: one V-cycle from x = 0 in the value type T (b and x: interior
+  // values, surface plane zero).
+  template <class T>
+  fnpf_status vcycle(int l, const T* b, T* x, const Params& o) {
     PLevel& L = pmg->lev[l];
+    const LView<T> v = view_of(L, (const T*)nullptr);
     const int64_t N = L.m.N, NI = L.m.NI;
-    FNPF_PS_TRY(go<FillItem>(N, {0.0, x}));
-    FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, b, L.r}));
-    if (l == pmg->nlev - 1) return cheb(L, x, L.r, o.coarse_degree, false);
-    FNPF_PS_TRY(cheb(L, x, L.r, o.cheb_degree, true));
+    FNPF_PS_TRY(go<FillItemT<T>>(N, {0.0, x}));
+    FNPF_PS_TRY(go<InteriorItemT<T>>(N, {NI, 1.0, b, v.r}));
+    if (l == pmg->nlev - 1) return cheb<T>(L, v, x, v.r, o.coarse_degree, false);
+    FNPF_PS_TRY(cheb<T>(L, v, x, v.r, o.cheb_degree, true));
     PLevel& C = pmg->lev[l + 1];
-    FNPF_PS_TRY(go<RestrictItem>(C.m.nelem * C.m.nt * C.m.n, {L.m, C.m, pmg->xf[l], L.r, C.ye}));
-    FNPF_PS_TRY(go<GatherItem>(C.m.N, {C.m.voff, C.m.vinc, C.ye, C.q}));
-    FNPF_PS_TRY(go<InteriorItem>(C.m.N, {C.m.NI, 1.0, C.q, C.b}));
-    FNPF_PS_TRY(vcycle(l + 1, C.b, C.x, o));
-    FNPF_PS_TRY(go<ProlongItem>(N, {L.m, C.m, pmg->xf[l], C.x, x}));
-    FNPF_PS_TRY(element_level(L, x));
-    FNPF_PS_TRY(go<GatherResidualItem>(N, {L.m.voff, L.m.vinc, L.ye, NI, b, L.r}));
-    return cheb(L, x, L.r, o.cheb_degree, false);
+    const LView<T> c = view_of(C, (const T*)nullptr);
+    FNPF_PS_TRY(go<RestrictItemT<T>>(C.m.nelem * C.m.nt * C.m.n, {L.m, C.m, pmg->xf[l], v.r, c.ye}));
+    FNPF_PS_TRY(go<GatherItemT<T>>(C.m.N, {C.m.voff, C.m.vinc, c.ye, c.q}));
+    FNPF_PS_TRY(go<InteriorItemT<T>>(C.m.N, {C.m.NI, 1.0, c.q, c.b}));
+    FNPF_PS_TRY(vcycle<T>(l + 1, c.b, c.x, o));
+    FNPF_PS_TRY(go<ProlongItemT<T>>(N, {L.m, C.m, pmg->xf[l], c.x, x}));
+    FNPF_PS_TRY(elements<T>(L.m, v.G, v.F, v.ye, v.vt, x));
+    FNPF_PS_TRY(go<GatherResidualItemT<T>>(N, {L.m.voff, L.m.vinc, v.ye, NI, b, v.r}));
+    return cheb<T>(L, v, x, v.r, o.cheb_degree, false);
   }
 
-  // z = M^-1 r: Jacobi or one V-cycle.
+  // z = M^-1 r: Jacobi, one FP64 V-cycle, or one FP32 V-cycle on the rounded
+  // residual (pc32) whose result is widened back.
   fnpf_status precond(const double* r, double* z, const Params& o) {
     if (!o.pmg) return go<DivItem>(m.NI, {r, w.diag, z});
-    return vcycle(0, r, z, o);
+    if (!o.pc32) return vcycle<double>(0, r, z, o);
+    PLevel& L0 = pmg->lev[0];
+    FNPF_PS_TRY(go<CastItem<float, double>>(m.N, {r, L0.b32}));
+    FNPF_PS_TRY(vcycle<float>(0, L0.b32, L0.x32, o));
+    return go<CastItem<double, float>>(m.N, {L0.x32, z});
   }
 
   // z = M^-1 r for the geometry of (eta, h) (r, z [N]; r's surface plane is ignored).

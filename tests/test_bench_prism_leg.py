@@ -37,8 +37,8 @@ def fake_binding(monkeypatch, tmp_path):
             self.N, self.ns = self.em.N, self.em.ns
 
         @staticmethod
-        def default_opts(rtol=1e-10, g=9.81, precond=F.FNPF_JACOBI):
-            return E.opts(rtol=rtol, g=g, pmg=precond == F.FNPF_PMG)
+        def default_opts(rtol=1e-10, g=9.81, precond=F.FNPF_JACOBI, precision=F.FNPF_FP64):
+            return E.opts(rtol=rtol, g=g, pmg=precond == F.FNPF_PMG, pc32=precision == F.FNPF_FP64_PC32)
 
         def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
             self.em.set_relaxation(cr, gen, amp, kx, ky, omega, phase, ramp_time)
@@ -49,7 +49,8 @@ def fake_binding(monkeypatch, tmp_path):
             return [{"iters": i} for i in iters]
 
     fake = types.SimpleNamespace(PrismMesh=PrismMesh, prism_numbering=F.prism_numbering,
-                                 FNPF_PMG=F.FNPF_PMG, FNPF_JACOBI=F.FNPF_JACOBI)
+                                 FNPF_PMG=F.FNPF_PMG, FNPF_JACOBI=F.FNPF_JACOBI, FNPF_FP64=F.FNPF_FP64,
+                                 FNPF_FP64_PC32=F.FNPF_FP64_PC32)
     import paper_2506_09435_gb300 as pkg
     monkeypatch.setattr(pkg, "fnpf", fake)
     monkeypatch.setattr(torch.cuda, "Event", _Event)
@@ -64,6 +65,8 @@ def test_prism_leg_reports_throughput_iterations_and_oracle_error(fake_binding):
     out = bench.prism_leg(torch.device("cpu"), args, None, size=(6, 2, 3, 2), sample=(4, 1, 2, 1, 2))
     assert out["finite"] and out["steps"] == 2 and out["dof"] > 0 and out["value"] > 0
     assert 0 < out["cg_iters_per_solve_mean"] < out["jacobi"]["cg_iters_per_solve_mean"]
+    pc = out["fp64_pc32"]
+    assert pc["rel_l2_vs_fp64"]["eta"] <= 1e-8 and pc["rel_l2_vs_fp64"]["phis"] <= 1e-8, pc
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 1
     err = out["rel_l2_vs_oracle"]
     assert err["eta"] <= 1e-10 and err["phis"] <= 1e-10, err

@@ -20,10 +20,11 @@ def T(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
 
 
-def opts(fnpf, rtol=1e-13, max_iter=20000, linear=False, pmg=False):
+def opts(fnpf, rtol=1e-13, max_iter=20000, linear=False, pmg=False, pc32=False):
     return fnpf.PrismMesh.default_opts(rtol=rtol, max_iter=max_iter, mass_rtol=1e-13, g=C.G,
                                        model=fnpf.FNPF_LINEAR if linear else fnpf.FNPF_NONLINEAR,
-                                       precond=fnpf.FNPF_PMG if pmg else fnpf.FNPF_JACOBI)
+                                       precond=fnpf.FNPF_PMG if (pmg or pc32) else fnpf.FNPF_JACOBI,
+                                       precision=fnpf.FNPF_FP64_PC32 if pc32 else fnpf.FNPF_FP64)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
@@ -224,3 +225,30 @@ def test_invariants_match_oracle(fnpf, linear):
     M, En = gm.invariants(T(eta), T(h), T(phis), opts(fnpf, linear=linear))
     assert abs(M - P.mass(pm, eta)) <= 1e-13 * np.sum(np.abs(eta))
     assert abs(En - P.energy(pm, h, eta, phis, C.G, linear=linear)) <= 1e-10 * abs(En)
+
+
+@pytest.mark.parametrize("p, nz, nx, ny", [(2, 2, 3, 2), (4, 2, 6, 4)])
+def test_fp32_vcycle_solve_matches_oracle(fnpf, p, nz, nx, ny):
+    v, t, pm = C.mesh(p, nz, nx=nx, ny=ny)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi64 = torch.zeros(pm.N, dtype=torch.float64, device=DEV)
+    phi32 = torch.zeros(pm.N, dtype=torch.float64, device=DEV)
+    i64 = gm.laplace_solve(T(eta), T(h), T(phis), phi64, opts(fnpf, pmg=True))
+    i32 = gm.laplace_solve(T(eta), T(h), T(phis), phi32, opts(fnpf, pc32=True))
+    assert i32["status"] == 0 and i32["rel_res"] <= 1e-13
+    assert C.rel(phi32.cpu().numpy(), P.laplace_solve(pm, eta, h, phis)) <= 1e-10
+    assert i32["iters"] <= i64["iters"] + 2
+
+
+def test_fp32_vcycle_rk4_steps_match_oracle(fnpf):
+    p, nz = 4, 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.standing_wave(pm)
+    e1, p1, hd = T(eta), T(phis), T(h)
+    eo, po = eta.copy(), phis.copy()
+    for _ in range(3):
+        gm.rk4_step(hd, e1, p1, 0.02, opts(fnpf, pc32=True))
+        eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
+    assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10

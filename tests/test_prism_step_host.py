@@ -26,8 +26,8 @@ def harness(tmp_path_factory):
     return E.Harness(E.build(str(tmp_path_factory.mktemp("prism_emu"))))
 
 
-def opts(rtol=1e-13, max_iter=20000, mass_rtol=1e-14, linear=False, pmg=False):
-    return E.opts(rtol, max_iter, mass_rtol, C.G, linear, pmg)
+def opts(rtol=1e-13, max_iter=20000, mass_rtol=1e-14, linear=False, pmg=False, pc32=False):
+    return E.opts(rtol, max_iter, mass_rtol, C.G, linear, pmg or pc32, pc32=pc32)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
@@ -225,6 +225,36 @@ def test_invariants_match_oracle(harness, linear):
     assert abs(En - P.energy(pm, h, eta, phis, C.G, linear=linear)) <= 1e-10 * abs(En)
 
 
+@pytest.mark.parametrize("p, nz, nx, ny", [(2, 2, 3, 2), (4, 2, 6, 4), (6, 2, 4, 3)])
+def test_fp32_vcycle_solve_matches_oracle(harness, p, nz, nx, ny):
+    """FP64 PCG with the V-cycle in FP32 (FP32 tables, metric and vectors): the
+    same solution as the oracle's direct solve, in about as many iterations as
+    the FP64 V-cycle."""
+    v, t, pm = C.mesh(p, nz, nx=nx, ny=ny)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi64, phi32 = np.zeros(pm.N), np.zeros(pm.N)
+    st, i64 = em.laplace_solve(opts(pmg=True), eta, h, phis, phi64)
+    assert st == 0
+    st, i32 = em.laplace_solve(opts(pc32=True), eta, h, phis, phi32)
+    assert st == 0 and i32.rel_res <= 1e-13
+    assert C.rel(phi32, P.laplace_solve(pm, eta, h, phis)) <= 1e-10
+    assert i32.iters <= i64.iters + 2
+
+
+def test_fp32_vcycle_rk4_steps_match_oracle(harness):
+    p, nz = 4, 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.standing_wave(pm)
+    e1, p1 = eta.copy(), phis.copy()
+    eo, po = eta.copy(), phis.copy()
+    for _ in range(3):
+        assert em.rk4_step(opts(pc32=True), h, e1, p1, 0.02)[0] == 0
+        eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
+    assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -239,6 +269,8 @@ for p, nz, nx, ny in [(1, 1, 2, 2), (3, 2, 3, 2), (5, 3, 2, 3)]:
     em.diagonal(eta, h)
     em.apply_stored(eta, h, np.ones(pm.N))
     em.precond_apply(E.opts(g=C.G, pmg=True), eta, h, np.ones(pm.N))
+    em.precond_apply(E.opts(g=C.G, pmg=True, pc32=True), eta, h, np.ones(pm.N))
+    assert em.laplace_solve(E.opts(g=C.G, pmg=True, pc32=True), eta, h, phis, np.zeros(pm.N))[0] == 0
     o = E.opts(g=C.G, pmg=(p > 1))
     assert em.laplace_solve(o, eta, h, phis, np.zeros(pm.N))[0] == 0
     assert em.dtn(o, eta, h, phis)[0] == 0
