@@ -283,6 +283,20 @@ for p, nz, nx, ny in [(1, 1, 2, 2), (3, 2, 3, 2), (5, 3, 2, 3)]:
         em.set_filter(2.0, 2, 1)
         em.filter_apply(eta)
         assert em.rk4_step(o, h, eta, phis, 0.01)[0] == 0
+# the edges of the valid range: one level (p = 1), four levels (p = 8), one layer; every option at once
+for p, nz in [(1, 1), (8, 1), (7, 2)]:
+    v, t, pm = C.mesh(p, nz, nx=2, ny=1)
+    em = hs.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    for o in (E.opts(g=C.G, pmg=True), E.opts(g=C.G, pmg=True, pc32=True), E.opts(g=C.G, pmg=True, linear=True)):
+        assert em.laplace_solve(o, eta, h, phis, np.zeros(pm.N))[0] == 0
+        assert em.rk4_step(o, h, eta.copy(), phis.copy(), 0.01)[0] == 0
+    em.invariants(E.opts(g=C.G, pmg=True, pc32=True), eta, h, phis)
+v, t, pm, h, cr, gen, wave = C.flume(4, 2, nx=4, ny=1)
+em = hs.mesh(v, t, 4, 2)
+em.set_filter(4.0, 2, 1)
+em.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+assert em.rk4_step(E.opts(g=C.G, pmg=True, pc32=True), h, np.zeros(pm.ns), np.zeros(pm.ns), 0.02, t=4.0)[0] == 0
 v, t, pm, h, cr, gen, wave = C.flume(3, 2, nx=4, ny=1)
 em = hs.mesh(v, t, 3, 2)
 em.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
