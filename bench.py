@@ -727,7 +727,7 @@ def main_gb300(args):
 PRISM_T0 = 4.0   # the flume runs from rest at t = 4 s: the generation ramp (5 T) is at 80 %
 
 
-def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None, precision=0):
+def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None, precision=0, projection=0):
     """The prism path (operator, solve, w, projected conditions, RK4,
     relaxation zones) on the triangulated flume W.prism_flume from rest at
     t = 4 s: `warm` untimed steps, then `steps` steps timed with CUDA events on
@@ -743,7 +743,7 @@ def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None, 
     cr, gen = W.flume_zones(d, x)
     wv = W.flume_wave(d)
     gm.set_relaxation(cr, gen, wv["amp"], wv["kx"], wv["ky"], wv["omega"], wv["phase"], wv["ramp_time"])
-    o = fnpf.PrismMesh.default_opts(rtol=rtol, g=d["g"], precond=precond, precision=precision)
+    o = fnpf.PrismMesh.default_opts(rtol=rtol, g=d["g"], precond=precond, precision=precision, projection=projection)
     h = torch.full((gm.ns,), d["h0"], dtype=torch.float64, device=dev)
     eta = torch.zeros(gm.ns, dtype=torch.float64, device=dev)
     phis = torch.zeros(gm.ns, dtype=torch.float64, device=dev)
@@ -774,17 +774,18 @@ def prism_leg(dev, args, flush, size=(64, 16, 4, 2), sample=(6, 2, 3, 2, 2)):
 
     from paper_2506_09435_gb300 import fnpf
     (nx, ny, p, nz), steps = size, max(1, min(args.steps, 5))
-    (eta, phis), ms, it_pmg, gm = prism_flume_run(dev, nx, ny, p, nz, steps, 2, args.rtol, fnpf.FNPF_PMG, flush)
+    (eta, phis), ms, it_pmg, gm = prism_flume_run(dev, nx, ny, p, nz, steps, 2, args.rtol, fnpf.FNPF_PMG, flush,
+                                                  projection=8)
     out = {"workload": "prisms (Sec. 3.1.2) over a jittered triangulation of a walled 4 x 1 m flume, %d x %d cells "
                        "(%d triangles), Nz=%d, p=%d, h=0.4 m, generation and absorption zones, T = 1 s, dt = T/40, "
                        "from rest at t = 4 s" % (nx, ny, 2 * nx * ny, nz, p),
-           "dof": gm.N, "surface_dof": gm.ns, "precond": "pmg", "rtol": args.rtol, "steps": steps,
+           "dof": gm.N, "surface_dof": gm.ns, "precond": "pmg", "projection": 8, "rtol": args.rtol, "steps": steps,
            "ms_per_step": ms, "value": gm.N / (ms * 1e-3), "unit": UNIT,
            "cg_iters_per_solve_mean": it_pmg, "finite": bool(torch.isfinite(eta).all())}
     del gm
     try:   # the V-cycle in FP32 inside the FP64 PCG, from the same state for the same steps
         (e32, p32), ms32, it32, gm = prism_flume_run(dev, nx, ny, p, nz, steps, 2, args.rtol, fnpf.FNPF_PMG, flush,
-                                                     precision=fnpf.FNPF_FP64_PC32)
+                                                     precision=fnpf.FNPF_FP64_PC32, projection=8)
         out["fp64_pc32"] = {"ms_per_step": ms32, "value": gm.N / (ms32 * 1e-3), "cg_iters_per_solve_mean": it32,
                             "rel_l2_vs_fp64": {"eta": float(torch.linalg.norm(e32 - eta) / torch.linalg.norm(eta)),
                                                "phis": float(torch.linalg.norm(p32 - phis) / torch.linalg.norm(phis))}}

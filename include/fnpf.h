@@ -562,6 +562,13 @@ typedef struct {
   int precision;           /* FNPF_FP64 (default) or FNPF_FP64_PC32: FP64 PCG with
                               the V-cycle in FP32 (FP32 tables, metric, vectors;
                               FNPF_PMG only, FNPF_FP64 with Jacobi)             */
+  int projection;          /* 0..8: initial guess of a solve = the A-orthogonal
+                              projection of the solution onto the span of the
+                              last `projection` solutions of this mesh and the
+                              caller's guess (Fischer's projection for
+                              successive right-hand sides; `projection`
+                              operator applications more per solve); 0 (the
+                              default) starts from the caller's guess     */
 } fnpf_prism_opts;
 void fnpf_prism_default_opts(fnpf_prism_opts* opts);
 fnpf_status fnpf_prism_diagonal(fnpf_prism* mesh, const double* eta, const double* h, double* diag, void* stream);

@@ -49,6 +49,7 @@ namespace fnpf {
 namespace pstep {
 
 constexpr int kChunk = 256;   // entries per partial sum of a dot product
+constexpr int kMaxProj = 8;   // previous solutions in the projected initial guess (one more slot: the caller's guess)
 
 // The mesh as the items read it (device pointers on the GPU).
 struct PMesh {
@@ -107,6 +108,9 @@ struct PWork {
   double *ke, *kp, *es, *ps, *ae, *ap;  // RK4 stage right-hand side, stage state, accumulator [ns]
   double* zero;                         // [ns] zeros (still-water geometry of the linear model)
   double* ft;                           // [ntri nt] filtered interior values
+  double *H, *AH;                       // [kMaxProj + 1][N] projection basis and its images under A
+  double* gram;                         // [(kMaxProj + 1) (kMaxProj + 2)] Gram matrix and right-hand side
+  int hist_n = 0, hist_next = 0;        // stored solutions, next slot (host state)
 };
 
 inline int64_t dot_partials(int64_t n) { return (n + kChunk - 1) / kChunk; }
@@ -137,6 +141,9 @@ void carve(const PMesh& m, PWork* w, Take take) {
                      &w->kp, &w->es, &w->ps, &w->ae, &w->ap, &w->zero};
   for (double** s : surf) take(s, m.ns);
   take(&w->ft, (int64_t)m.ntri * m.nt);
+  take(&w->H, (int64_t)(kMaxProj + 1) * m.N);
+  take(&w->AH, (int64_t)(kMaxProj + 1) * m.N);
+  take(&w->gram, (kMaxProj + 1) * (kMaxProj + 2));
 }
 
 // CG state slots (device doubles): r.z, p.q, r.r, alpha, beta, the new r.z,
@@ -1230,6 +1237,28 @@ struct GatherResidualItemT {
 };
 using GatherResidualItem = GatherResidualItemT<double>;
 
+// Projected initial guess (Fischer's projection for successive right-hand
+// sides): x0 = sum_j c_j H_j and r0 = b - sum_j c_j (A H_j) at interior node i
+// (the basis vectors at stride N; coefficients in the launch's parameters).
+struct ProjCombItem {
+  struct Args {
+    int nb;
+    double c[kMaxProj + 1];
+    const double* H[kMaxProj + 1];
+    const double* AH[kMaxProj + 1];
+    double *x, *r;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    double x = 0, q = 0;
+    for (int j = 0; j < a.nb; ++j) {
+      x += a.c[j] * a.H[j][i];
+      q += a.c[j] * a.AH[j][i];
+    }
+    a.x[i] = x;
+    a.r[i] -= q;
+  }
+};
+
 // A fixed pseudo-random vector in [-1, 1) on the interior (splitmix64 of the
 // index), zero on the surface plane: the start of the eigenvalue estimate.
 struct HashItem {
@@ -1440,6 +1469,7 @@ struct Params {
   int coarse_degree;  // Chebyshev degree on the coarsest level
   double cheb_range;  // the smoothers act on [lmax / cheb_range, lmax]
   int pc32;           // 1: the V-cycle in FP32 (FP64 PCG around it)
+  int projection;     // 0..kMaxProj: previous solutions in the projected initial guess (0: the caller's guess)
 };
 
 #define FNPF_PS_TRY(...)                 \
@@ -1451,7 +1481,7 @@ struct Params {
 template <class Ex>
 struct Stepper {
   const PMesh& m;
-  const PWork& w;
+  PWork& w;
   Ex& ex;
   PMG* pmg = nullptr;   // the hierarchy (needed when Params::pmg is set)
 
@@ -1699,6 +1729,78 @@ struct Stepper {
     return precond(w.r, z, o);
   }
 
+  // The projected initial guess: phi (interior) = the A-orthogonal projection
+  // of the solution onto the span of the last o.projection solutions and the
+  // caller's guess (Fischer, Comput. Methods Appl. Mech. Engrg. 163, 1998), and
+  // w.r = b - A phi (w.r = b on entry).  The Gram system is formed on the
+  // device and read once; a vector whose Cholesky pivot falls below 1e-14 of its
+  // diagonal (nearly dependent, zero, non-finite) is dropped.
+  fnpf_status project(double* phi, const Params& o) {
+    const int64_t N = m.N, NI = m.NI;
+    const int nh = std::min(w.hist_n, o.projection);
+    double* H[kMaxProj + 1];
+    double* AH[kMaxProj + 1];
+    int nb = 0;
+    for (int j = 0; j < nh; ++j) {   // the most recent first
+      const int slot = (w.hist_next - 1 - j + 2 * kMaxProj) % kMaxProj;
+      H[nb] = w.H + (int64_t)slot * N;
+      AH[nb++] = w.AH + (int64_t)slot * N;
+    }
+    H[nb] = w.H + (int64_t)kMaxProj * N;   // the caller's guess, surface plane zero
+    AH[nb++] = w.AH + (int64_t)kMaxProj * N;
+    FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, phi, H[nb - 1]}));
+    for (int j = 0; j < nb; ++j) FNPF_PS_TRY(apply(H[j], AH[j]));
+    int k = 0;
+    for (int i = 0; i < nb; ++i)
+      for (int j = i; j < nb; ++j) FNPF_PS_TRY(dot_dev(H[i], AH[j], NI, w.gram + k++));
+    for (int i = 0; i < nb; ++i) FNPF_PS_TRY(dot_dev(H[i], w.r, NI, w.gram + k++));
+    double g[(kMaxProj + 1) * (kMaxProj + 2)];
+    if (ex.get(g, w.gram, k)) return FNPF_ECUDA;
+    double G[kMaxProj + 1][kMaxProj + 1], rhs[kMaxProj + 1];
+    k = 0;
+    for (int i = 0; i < nb; ++i)
+      for (int j = i; j < nb; ++j) G[i][j] = G[j][i] = g[k++];
+    for (int i = 0; i < nb; ++i) rhs[i] = g[k++];
+    // Cholesky of the kept vectors, in order, dropping dependent ones
+    double Lc[kMaxProj + 1][kMaxProj + 1];
+    int kept[kMaxProj + 1], nk = 0;
+    for (int j = 0; j < nb; ++j) {
+      double l[kMaxProj + 1];
+      double d = G[j][j];
+      for (int a = 0; a < nk; ++a) {
+        double v = G[j][kept[a]];
+        for (int b = 0; b < a; ++b) v -= l[b] * Lc[a][b];
+        l[a] = v / Lc[a][a];
+        d -= l[a] * l[a];
+      }
+      if (!(d > 1e-14 * G[j][j]) || !isfinite(d)) continue;
+      for (int a = 0; a < nk; ++a) Lc[nk][a] = l[a];
+      Lc[nk][nk] = sqrt(d);
+      kept[nk++] = j;
+    }
+    ProjCombItem::Args a{};
+    a.nb = nb;
+    for (int j = 0; j < nb; ++j) {
+      a.c[j] = 0.0;
+      a.H[j] = H[j];
+      a.AH[j] = AH[j];
+    }
+    double y[kMaxProj + 1];
+    for (int i = 0; i < nk; ++i) {   // L y = rhs, L^T c = y
+      double v = rhs[kept[i]];
+      for (int b = 0; b < i; ++b) v -= Lc[i][b] * y[b];
+      y[i] = v / Lc[i][i];
+    }
+    for (int i = nk - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int b = i + 1; b < nk; ++b) v -= Lc[b][i] * a.c[kept[b]];
+      a.c[kept[i]] = v / Lc[i][i];
+    }
+    a.x = phi;
+    a.r = w.r;
+    return go<ProjCombItem>(NI, a);
+  }
+
   // phi = the solution of A_II phi_I = -A_IS phis (in: the interior guess),
   // phi = phis on the surface plane; Jacobi-PCG to ||r|| <= rtol ||b||.
   fnpf_status solve(const double* eta, const double* h, const double* phis, double* phi, const Params& o,
@@ -1721,9 +1823,14 @@ struct Stepper {
       FNPF_PS_TRY(go<FillItem>(NI, {0.0, phi}));
     } else {
       const double stop = o.rtol * sqrt(bb);
-      FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, phi, w.pd}));   // the guess, surface plane zero
-      FNPF_PS_TRY(apply(w.pd, w.q));
-      FNPF_PS_TRY(go<AxpyItem>(NI, {-1.0, w.q, w.r}));          // r = b - A_II x0
+      if (o.projection > 0) {
+        FNPF_PS_TRY(project(phi, o));                              // phi = x0, r = b - A_II x0
+        FNPF_PS_TRY(go<FillItem>(N, {0.0, w.pd}));                 // the direction's surface plane zero
+      } else {
+        FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, phi, w.pd}));   // the guess, surface plane zero
+        FNPF_PS_TRY(apply(w.pd, w.q));
+        FNPF_PS_TRY(go<AxpyItem>(NI, {-1.0, w.q, w.r}));          // r = b - A_II x0
+      }
       FNPF_PS_TRY(dot(w.r, w.r, NI, &rr));
       if (sqrt(rr) > stop) {
         // w.pd's surface plane is zero (above); the loop writes its first NI entries only
@@ -1732,6 +1839,11 @@ struct Stepper {
                     [&](const double* rv, double* zv) { return precond(rv, zv, o); }, &it, &rr);
         if (st == FNPF_ECUDA) return st;
       }
+    }
+    if (o.projection > 0 && st == FNPF_OK && bb > 0) {   // the solution joins the projection basis
+      FNPF_PS_TRY(go<CopyItem>(NI, {phi, w.H + (int64_t)w.hist_next * N}));
+      w.hist_next = (w.hist_next + 1) % kMaxProj;
+      w.hist_n = std::min(w.hist_n + 1, kMaxProj);
     }
     FNPF_PS_TRY(go<CopyItem>(m.ns, {phis, phi + NI}));
     if (info) {

@@ -37,8 +37,9 @@ def fake_binding(monkeypatch, tmp_path):
             self.N, self.ns = self.em.N, self.em.ns
 
         @staticmethod
-        def default_opts(rtol=1e-10, g=9.81, precond=F.FNPF_JACOBI, precision=F.FNPF_FP64):
-            return E.opts(rtol=rtol, g=g, pmg=precond == F.FNPF_PMG, pc32=precision == F.FNPF_FP64_PC32)
+        def default_opts(rtol=1e-10, g=9.81, precond=F.FNPF_JACOBI, precision=F.FNPF_FP64, projection=0):
+            return E.opts(rtol=rtol, g=g, pmg=precond == F.FNPF_PMG, pc32=precision == F.FNPF_FP64_PC32,
+                          projection=projection)
 
         def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
             self.em.set_relaxation(cr, gen, amp, kx, ky, omega, phase, ramp_time)

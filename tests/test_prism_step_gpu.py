@@ -252,3 +252,21 @@ def test_fp32_vcycle_rk4_steps_match_oracle(fnpf):
         gm.rk4_step(hd, e1, p1, 0.02, opts(fnpf, pc32=True))
         eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
     assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10
+
+
+def test_projected_guess_same_states_fewer_iterations(fnpf):
+    p, nz = 4, 2
+    v, t, pm, h, cr, gen, wave = C.flume(p, nz, nx=8, ny=2)
+    out = {}
+    for proj in (0, 8):
+        gm = fnpf.PrismMesh(v, t, p, nz)
+        gm.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+        e, ph, hd = T(np.zeros(pm.ns)), T(np.zeros(pm.ns)), T(h)
+        o = fnpf.PrismMesh.default_opts(rtol=1e-12, g=C.G, precond=fnpf.FNPF_PMG, projection=proj)
+        total = 0
+        for k in range(6):
+            total += sum(i["iters"] for i in gm.rk4_step(hd, e, ph, 0.025, o, t=4.0 + 0.025 * k))
+        out[proj] = (e.cpu().numpy(), ph.cpu().numpy(), total)
+    (e0, p0, n0), (e8, p8, n8) = out[0], out[8]
+    assert C.rel(e8, e0) <= 1e-9 and C.rel(p8, p0) <= 1e-9
+    assert n8 < 0.9 * n0, (n8, n0)

@@ -255,6 +255,34 @@ def test_fp32_vcycle_rk4_steps_match_oracle(harness):
     assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
 
 
+@pytest.mark.parametrize("pmg", [False, True])
+def test_projected_guess_same_states_fewer_iterations(harness, pmg):
+    """The projected initial guess (the last 8 solutions and the caller's guess)
+    changes where CG starts, not where it stops: six steps of the flume equal
+    the unprojected run to the tolerance, in fewer iterations; an exact guess
+    is kept (no iteration)."""
+    p, nz = 4, 2
+    v, t, pm, h, cr, gen, wave = C.flume(p, nz, nx=8, ny=2)
+    out = {}
+    for proj in (0, 8):
+        em = harness.mesh(v, t, p, nz)
+        em.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+        e, ph = np.zeros(pm.ns), np.zeros(pm.ns)
+        total = 0
+        for k in range(6):
+            st, it = em.rk4_step(E.opts(rtol=1e-12, g=C.G, pmg=pmg, projection=proj), h, e, ph, 0.025, t=4.0 + 0.025 * k)
+            assert st == 0
+            total += sum(it)
+        out[proj] = (e, ph, total, em)
+    (e0, p0, n0, _), (e8, p8, n8, em) = out[0], out[8]
+    assert C.rel(e8, e0) <= 1e-9 and C.rel(p8, p0) <= 1e-9
+    assert n8 < 0.9 * n0, (n8, n0)
+    eta, hh, phis = C.fields(pm)
+    ref = P.laplace_solve(pm, eta, hh, phis)
+    st, info = em.laplace_solve(E.opts(rtol=1e-10, g=C.G, pmg=pmg, projection=8), eta, hh, phis, ref.copy())
+    assert st == 0 and info.iters == 0
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -292,6 +320,8 @@ for p, nz in [(1, 1), (8, 1), (7, 2)]:
         assert em.laplace_solve(o, eta, h, phis, np.zeros(pm.N))[0] == 0
         assert em.rk4_step(o, h, eta.copy(), phis.copy(), 0.01)[0] == 0
     em.invariants(E.opts(g=C.G, pmg=True, pc32=True), eta, h, phis)
+    for k in range(3):
+        assert em.rk4_step(E.opts(g=C.G, pmg=True, projection=8), h, eta.copy(), phis.copy(), 0.01)[0] == 0
 v, t, pm, h, cr, gen, wave = C.flume(4, 2, nx=4, ny=1)
 em = hs.mesh(v, t, 4, 2)
 em.set_filter(4.0, 2, 1)
