@@ -764,6 +764,56 @@ def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None, 
     return (eta, phis), ms / max(1, steps), statistics.mean(iters) if iters else 0.0, gm
 
 
+def prism_operator_timing(dev, nx, ny, p, nz, reps=20):
+    """The prism operator on the flume mesh: y = A(eta, h) x with the stored
+    metric (the items of the solve: vertical derivatives, fluxes, vertical sums,
+    node contractions, gather) and with the metric rebuilt per application
+    (fnpf_prism_apply), each timed over `reps` applications with CUDA events;
+    executed FP64 flops per prism 12 n nq nt + 18 n nq + 4 n^2 nt for the stored
+    form (n = p + 1, nq = (p + 2)^2, nt = (p + 1)(p + 2) / 2)."""
+    import torch
+
+    from paper_2506_09435_gb300 import fnpf
+    from paper_2506_09435_gb300 import workloads as W
+    v, t, d = W.prism_flume(nx=nx, ny=ny, p=p, nz=nz)
+    _, x_, y_ = fnpf.prism_numbering(v, t, p)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    xs = torch.tensor(x_, dtype=torch.float64, device=dev)
+    eta = 0.01 * torch.cos(6.0 * xs)
+    h = torch.full((gm.ns,), d["h0"], dtype=torch.float64, device=dev)
+    x = torch.sin(torch.arange(gm.N, dtype=torch.float64, device=dev))
+    y = torch.zeros(gm.N, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    n, nq, nt = p + 1, (p + 2) ** 2, (p + 1) * (p + 2) // 2
+    prisms = 2 * nx * ny * nz
+    out = {"prisms": prisms, "dof": gm.N, "reps": reps}
+
+    def timed(fn):
+        fn()   # first call: set-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return 1e3 * a.elapsed_time(b) / reps
+
+    # fnpf_prism_apply_stored rebuilds the metric and the diagonal before applying the operator;
+    # fnpf_prism_diagonal is that rebuild alone, so the difference is the operator with the stored metric
+    t_full = timed(lambda: gm.apply_stored(eta, h, x, y))
+    t_geo = timed(lambda: gm.diagonal(eta, h, y))
+    us = max(t_full - t_geo, 1e-3)
+    flops = prisms * (12 * n * nq * nt + 18 * n * nq + 4 * n * n * nt)
+    out["stored_metric"] = {"us_per_application": us, "us_metric_and_diagonal": t_geo,
+                            "us_apply_stored_call": t_full, "flops_executed": flops, "gflops": flops / (us * 1e3),
+                            "frac_of_fp64_peak": flops / (us * 1e-6) / (FP64_PEAK_TFLOPS * 1e12),
+                            "applications_per_s": 1e6 / us}
+    out["metric_per_application"] = {"us_per_application": timed(lambda: gm.apply(eta, h, x, y))}
+    del gm
+    return out
+
+
 def prism_leg(dev, args, flush, size=(64, 16, 4, 2), sample=(6, 2, 3, 2, 2)):
     """Sub-object of the benchmark line: the prism path on the triangulated
     flume of `size` = (cells in x, cells in y, p, Nz) (throughput, CG
@@ -783,6 +833,10 @@ def prism_leg(dev, args, flush, size=(64, 16, 4, 2), sample=(6, 2, 3, 2, 2)):
            "ms_per_step": ms, "value": gm.N / (ms * 1e-3), "unit": UNIT,
            "cg_iters_per_solve_mean": it_pmg, "finite": bool(torch.isfinite(eta).all())}
     del gm
+    try:
+        out["operator"] = prism_operator_timing(dev, nx, ny, p, nz)
+    except Exception as e:
+        out["operator"] = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
     try:   # the V-cycle in FP32 inside the FP64 PCG, from the same state for the same steps
         (e32, p32), ms32, it32, gm = prism_flume_run(dev, nx, ny, p, nz, steps, 2, args.rtol, fnpf.FNPF_PMG, flush,
                                                      precision=fnpf.FNPF_FP64_PC32, projection=8)

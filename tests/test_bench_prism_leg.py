@@ -44,6 +44,15 @@ def fake_binding(monkeypatch, tmp_path):
         def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
             self.em.set_relaxation(cr, gen, amp, kx, ky, omega, phase, ramp_time)
 
+        def apply_stored(self, eta, h, x, y):
+            y.copy_(torch.from_numpy(self.em.apply_stored(eta.numpy(), h.numpy(), x.numpy())))
+
+        def apply(self, eta, h, x, y):
+            self.apply_stored(eta, h, x, y)
+
+        def diagonal(self, eta, h, d):
+            d.copy_(torch.from_numpy(self.em.diagonal(eta.numpy(), h.numpy())))
+
         def rk4_step(self, h, eta, phis, dt, opts, t=0.0):
             st, iters = self.em.rk4_step(opts, h.numpy(), eta.numpy(), phis.numpy(), dt, t=t)
             assert st == 0
@@ -66,6 +75,8 @@ def test_prism_leg_reports_throughput_iterations_and_oracle_error(fake_binding):
     out = bench.prism_leg(torch.device("cpu"), args, None, size=(6, 2, 3, 2), sample=(4, 1, 2, 1, 2))
     assert out["finite"] and out["steps"] == 2 and out["dof"] > 0 and out["value"] > 0
     assert 0 < out["cg_iters_per_solve_mean"] < out["jacobi"]["cg_iters_per_solve_mean"]
+    op = out["operator"]
+    assert op["stored_metric"]["flops_executed"] > 0 and "us_per_application" in op["metric_per_application"], op
     pc = out["fp64_pc32"]
     assert pc["rel_l2_vs_fp64"]["eta"] <= 1e-8 and pc["rel_l2_vs_fp64"]["phis"] <= 1e-8, pc
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 1
