@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -180,12 +181,12 @@ bool prism_numbering(const double* verts, int nverts, const int* tris, int ntri,
                      std::vector<double>* xs, std::vector<double>* ys) {
   const auto idx = tri_index(p);
   const int nt = (int)idx.size();
-  std::vector<std::pair<std::pair<int, int>, int>> edges;   // (min, max) -> first node
+  // (min, max) vertex pair -> first node of the edge, edges numbered in order of first appearance
+  std::map<std::pair<int, int>, int> edge_first;
+  int nedges = 0;
   auto find_edge = [&](int u, int w) {
-    const std::pair<int, int> key(std::min(u, w), std::max(u, w));
-    for (auto& e : edges)
-      if (e.first == key) return e.second;
-    return -1;
+    const auto it = edge_first.find(std::pair<int, int>(std::min(u, w), std::max(u, w)));
+    return it == edge_first.end() ? -1 : it->second;
   };
   for (int t = 0; t < ntri; ++t) {
     const int A = tris[3 * t], B = tris[3 * t + 1], C = tris[3 * t + 2];
@@ -194,9 +195,9 @@ bool prism_numbering(const double* verts, int nverts, const int* tris, int ntri,
     const int pairs[3][2] = {{A, B}, {B, C}, {A, C}};
     for (auto& pr : pairs)
       if (find_edge(pr[0], pr[1]) < 0)
-        edges.push_back({{std::min(pr[0], pr[1]), std::max(pr[0], pr[1])}, nverts + (int)edges.size() * (p - 1)});
+        edge_first[{std::min(pr[0], pr[1]), std::max(pr[0], pr[1])}] = nverts + (nedges++) * (p - 1);
   }
-  int n = nverts + (int)edges.size() * (p - 1);
+  int n = nverts + nedges * (p - 1);
   tnodes->assign((size_t)ntri * nt, 0);
   auto edge_node = [&](int u, int w, int m) {
     const int base = find_edge(u, w);
