@@ -814,7 +814,7 @@ def prism_operator_timing(dev, nx, ny, p, nz, reps=20):
     return out
 
 
-def prism_leg(dev, args, flush, size=(64, 16, 4, 2), sample=(6, 2, 3, 2, 2)):
+def prism_leg(dev, args, flush, size=(128, 32, 4, 2), sample=(6, 2, 3, 2, 2)):
     """Sub-object of the benchmark line: the prism path on the triangulated
     flume of `size` = (cells in x, cells in y, p, Nz) (throughput, CG
     iterations with the p-multigrid and with Jacobi), and its error against the
