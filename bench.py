@@ -837,6 +837,16 @@ def prism_leg(dev, args, flush, size=(128, 32, 4, 2), sample=(6, 2, 3, 2, 2)):
         out["operator"] = prism_operator_timing(dev, nx, ny, p, nz)
     except Exception as e:
         out["operator"] = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
+    try:   # FP64 defect correction around the FP32 PCG, from the same state for the same steps
+        (em_, pm_), msm, itm, gm = prism_flume_run(dev, nx, ny, p, nz, steps, 2, args.rtol, fnpf.FNPF_PMG, flush,
+                                                   precision=fnpf.FNPF_MIXED, projection=8)
+        out["mixed"] = {"ms_per_step": msm, "value": gm.N / (msm * 1e-3), "inner_iters_per_solve_mean": itm,
+                        "inner_rtol": 1e-5,
+                        "rel_l2_vs_fp64": {"eta": float(torch.linalg.norm(em_ - eta) / torch.linalg.norm(eta)),
+                                           "phis": float(torch.linalg.norm(pm_ - phis) / torch.linalg.norm(phis))}}
+        del gm
+    except Exception as e:
+        out["mixed"] = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
     try:   # the V-cycle in FP32 inside the FP64 PCG, from the same state for the same steps
         (e32, p32), ms32, it32, gm = prism_flume_run(dev, nx, ny, p, nz, steps, 2, args.rtol, fnpf.FNPF_PMG, flush,
                                                      precision=fnpf.FNPF_FP64_PC32, projection=8)

@@ -539,8 +539,9 @@ const char* fnpf_prism_last_error(const fnpf_prism* mesh);
  * the preconditioner of opts (Jacobi or one V-cycle) applied to the interior
  * entries of r [N] (z zero on the surface plane).  opts may be NULL (defaults).
  * info: NULL, one struct, or 4 (fnpf_prism_rk4_step, one per stage): iters =
- * Laplace CG iterations, rel_res = ||r|| / ||b||, status; outer_iters = 0 and
- * ms = 0.  The first call on a mesh allocates its workspace (about
+ * Laplace CG iterations (FNPF_MIXED: inner iterations), outer_iters = defect-
+ * correction steps (0 unless FNPF_MIXED), rel_res = ||r|| / ||b|| (FP64),
+ * status; ms = 0.  The first call on a mesh allocates its workspace (about
  * 9 N + 72 nprisms (p + 1) (p + 2)^2 doubles, synchronising the device) and
  * builds the surface tables; later calls allocate nothing.  Calls on one mesh
  * must not overlap; each returns after its stream has finished its work (the
@@ -559,9 +560,13 @@ typedef struct {
   int cheb_degree;         /* FNPF_PMG: Chebyshev degree of pre/post smoothing (3) */
   int coarse_iters;        /* FNPF_PMG: Chebyshev degree on the coarsest level (6) */
   double cheb_range;       /* FNPF_PMG: smoothers act on [lmax / range, lmax] (40) */
-  int precision;           /* FNPF_FP64 (default) or FNPF_FP64_PC32: FP64 PCG with
-                              the V-cycle in FP32 (FP32 tables, metric, vectors;
-                              FNPF_PMG only, FNPF_FP64 with Jacobi)             */
+  int precision;           /* FNPF_FP64 (default); FNPF_FP64_PC32: FP64 PCG with
+                              the V-cycle in FP32 (FP32 tables, metric, vectors);
+                              FNPF_MIXED: FP64 defect correction around an FP32
+                              PCG (FP32 operator and V-cycle, dot products
+                              accumulated in FP64) solved to inner_rtol times
+                              the current FP64 residual; both FNPF_PMG only
+                              (FNPF_FP64 with Jacobi)                         */
   int projection;          /* 0..8: initial guess of a solve = the A-orthogonal
                               projection of the solution onto the span of the
                               last `projection` solutions of this mesh and the
@@ -569,6 +574,8 @@ typedef struct {
                               successive right-hand sides; `projection`
                               operator applications more per solve); 0 (the
                               default) starts from the caller's guess     */
+  double inner_rtol;       /* FNPF_MIXED: inner tolerance (default 1e-5)          */
+  int max_outer;           /* FNPF_MIXED: defect-correction steps (default 20)    */
 } fnpf_prism_opts;
 void fnpf_prism_default_opts(fnpf_prism_opts* opts);
 fnpf_status fnpf_prism_diagonal(fnpf_prism* mesh, const double* eta, const double* h, double* diag, void* stream);

@@ -206,15 +206,17 @@ fnpf_status check_opts(const fnpf_prism_opts* o, pstep::Params* p, std::string* 
       (o->model != FNPF_NONLINEAR && o->model != FNPF_LINEAR) ||
       (o->precond != FNPF_JACOBI && o->precond != FNPF_PMG) || o->cheb_degree < 1 || o->coarse_iters < 1 ||
       !(o->cheb_range > 1) || !isfinite(o->cheb_range) ||
-      (o->precision != FNPF_FP64 && o->precision != FNPF_FP64_PC32) || o->projection < 0 ||
-      o->projection > pstep::kMaxProj) {
+      (o->precision != FNPF_FP64 && o->precision != FNPF_FP64_PC32 && o->precision != FNPF_MIXED) ||
+      o->projection < 0 || o->projection > pstep::kMaxProj || !(o->inner_rtol > 0 && o->inner_rtol < 1) ||
+      o->max_outer < 1) {
     *why = "bad options (rtol, mass_rtol > 0; iteration caps >= 0; finite g; model NONLINEAR or LINEAR; precond "
-           "JACOBI or PMG; Chebyshev degrees >= 1; cheb_range > 1; precision FP64 or FP64_PC32; projection 0..8)";
+           "JACOBI or PMG; Chebyshev degrees >= 1; cheb_range > 1; precision FP64, FP64_PC32 or MIXED; projection 0..8; inner_rtol in (0, 1); max_outer >= 1)";
     return FNPF_EINVAL;
   }
   *p = pstep::Params{o->rtol,         o->max_iter, o->mass_rtol,   o->mass_max_iter, o->g, o->model == FNPF_LINEAR,
                      o->precond == FNPF_PMG, o->cheb_degree, o->coarse_iters, o->cheb_range,
-                     o->precond == FNPF_PMG && o->precision == FNPF_FP64_PC32, o->projection};
+                     o->precond == FNPF_PMG && o->precision == FNPF_FP64_PC32, o->projection,
+                     o->precond == FNPF_PMG && o->precision == FNPF_MIXED, o->inner_rtol, o->max_outer};
   return FNPF_OK;
 }
 
@@ -260,6 +262,8 @@ void fnpf_prism_default_opts(fnpf_prism_opts* o) {
   o->cheb_range = 40.0;
   o->precision = FNPF_FP64;
   o->projection = 0;
+  o->inner_rtol = 1e-5;
+  o->max_outer = 20;
 }
 
 fnpf_status fnpf_prism_diagonal(fnpf_prism* m, const double* eta, const double* h, double* diag, void* stream) {

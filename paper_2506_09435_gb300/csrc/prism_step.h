@@ -111,6 +111,7 @@ struct PWork {
   double *H, *AH;                       // [kMaxProj + 1][N] projection basis and its images under A
   double* gram;                         // [(kMaxProj + 1) (kMaxProj + 2)] Gram matrix and right-hand side
   int hist_n = 0, hist_next = 0;        // stored solutions, next slot (host state)
+  float *ie, *ir, *iz, *ip, *iq;        // [N] the FP32 inner solve of the defect correction
 };
 
 inline int64_t dot_partials(int64_t n) { return (n + kChunk - 1) / kChunk; }
@@ -144,6 +145,12 @@ void carve(const PMesh& m, PWork* w, Take take) {
   take(&w->H, (int64_t)(kMaxProj + 1) * m.N);
   take(&w->AH, (int64_t)(kMaxProj + 1) * m.N);
   take(&w->gram, (kMaxProj + 1) * (kMaxProj + 2));
+  float** inner[] = {&w->ie, &w->ir, &w->iz, &w->ip, &w->iq};
+  for (float** f : inner) {   // a float buffer of N entries takes (N + 1) / 2 doubles
+    double* d = nullptr;
+    take(&d, (m.N + 1) / 2);
+    *f = reinterpret_cast<float*>(d);
+  }
 }
 
 // CG state slots (device doubles): r.z, p.q, r.r, alpha, beta, the new r.z,
@@ -765,13 +772,15 @@ struct DivItem {   // out = x / d (the Jacobi preconditioner)
   FNPF_HD static void at(int64_t i, const Args& a) { a.out[i] = a.x[i] / a.d[i]; }
 };
 
-struct CopyItem {
+template <class T>
+struct CopyItemT {
   struct Args {
-    const double* src;
-    double* dst;
+    const T* src;
+    T* dst;
   };
   FNPF_HD static void at(int64_t i, const Args& a) { a.dst[i] = a.src[i]; }
 };
+using CopyItem = CopyItemT<double>;
 
 template <class T>
 struct FillItemT {
@@ -794,19 +803,21 @@ struct CastItem {
 };
 
 // part[i] = sum of x_j y_j over the i-th chunk of kChunk entries (fixed order).
-struct DotPartItem {
+template <class T>
+struct DotPartItemT {
   struct Args {
-    const double *x, *y;
+    const T *x, *y;
     int64_t n;
     double* part;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
     const int64_t lo = i * kChunk, hi = lo + kChunk < a.n ? lo + kChunk : a.n;
-    double s = 0;
-    for (int64_t j = lo; j < hi; ++j) s += a.x[j] * a.y[j];
+    double s = 0;   // FP64 accumulation for every vector type
+    for (int64_t j = lo; j < hi; ++j) s += (double)a.x[j] * (double)a.y[j];
     a.part[i] = s;
   }
 };
+using DotPartItem = DotPartItemT<double>;
 
 // out[0] = sum of the partials (one item).
 struct SumItem {
@@ -870,19 +881,21 @@ struct CgAlphaItem {   // alpha = r.z / p.q (p.q <= 0 or not finite: breakdown o
   }
 };
 
-struct CgUpdateItem {   // x += alpha p (x may be null), r -= alpha q
+template <class T>
+struct CgUpdateItemT {
   struct Args {
     const double* cg;
-    const double *p, *q;
-    double *x, *r;
+    const T *p, *q;
+    T *x, *r;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
     if (a.cg[kDONE] != 0.0) return;
-    const double al = a.cg[kAL];
+    const T al = (T)a.cg[kAL];
     if (a.x) a.x[i] += al * a.p[i];
     a.r[i] -= al * a.q[i];
   }
 };
+using CgUpdateItem = CgUpdateItemT<double>;
 
 struct CgCheckItem {   // one more completed iteration; converged when ||r|| <= stop
   struct Args {
@@ -913,17 +926,19 @@ struct CgBetaItem {   // beta = r.z_new / r.z, r.z = r.z_new
   }
 };
 
-struct CgDirItem {   // p = z + beta p
+template <class T>
+struct CgDirItemT {
   struct Args {
     const double* cg;
-    const double* z;
-    double* p;
+    const T* z;
+    T* p;
   };
   FNPF_HD static void at(int64_t i, const Args& a) {
     if (a.cg[kDONE] != 0.0) return;
-    a.p[i] = a.z[i] + a.cg[kBE] * a.p[i];
+    a.p[i] = a.z[i] + (T)a.cg[kBE] * a.p[i];
   }
 };
+using CgDirItem = CgDirItemT<double>;
 
 // w = d phi / dz at surface node c: (sum_j D[p][j] phi(plane N_v - 1 - p + j)) 2 N_z / (eta + h).
 struct WItem {
@@ -1259,6 +1274,15 @@ struct ProjCombItem {
   }
 };
 
+// x += (double) e: a correction of the FP32 inner solve added to the FP64 iterate.
+struct AddCastItem {
+  struct Args {
+    const float* e;
+    double* x;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.x[i] += (double)a.e[i]; }
+};
+
 // A fixed pseudo-random vector in [-1, 1) on the interior (splitmix64 of the
 // index), zero on the surface plane: the start of the eigenvalue estimate.
 struct HashItem {
@@ -1470,6 +1494,9 @@ struct Params {
   double cheb_range;  // the smoothers act on [lmax / cheb_range, lmax]
   int pc32;           // 1: the V-cycle in FP32 (FP64 PCG around it)
   int projection;     // 0..kMaxProj: previous solutions in the projected initial guess (0: the caller's guess)
+  int mixed;          // 1: FP64 defect correction around an FP32 PCG with the FP32 V-cycle
+  double inner_rtol;  // the FP32 solve's tolerance relative to the current FP64 residual
+  int max_outer;      // defect-correction steps at most
 };
 
 #define FNPF_PS_TRY(...)                 \
@@ -1528,9 +1555,10 @@ struct Stepper {
   }
 
   // *out (device) = x . y over n entries, without reading it back.
-  fnpf_status dot_dev(const double* x, const double* y, int64_t n, double* out) {
+  template <class T>
+  fnpf_status dot_dev(const T* x, const T* y, int64_t n, double* out) {
     const int64_t np = dot_partials(n);
-    FNPF_PS_TRY(go<DotPartItem>(np, {x, y, n, w.part}));
+    FNPF_PS_TRY(go<DotPartItemT<T>>(np, {x, y, n, w.part}));
     return go<SumItem>(1, {w.part, np, out});
   }
 
@@ -1543,12 +1571,12 @@ struct Stepper {
   // residual equal those of reading every scalar at once.  x may be null
   // (only the coefficients are wanted: hist).  *iters and *rr: completed
   // iterations and the last r.r (unchanged when no iteration completed).
-  template <class Op, class Pre>
-  fnpf_status cg_run(int64_t n, double* x, double* r, double* z, double* p, double* q, double stop, int max_iter,
-                     int check, double* hist, Op op, Pre pre, int* iters, double* rr) {
+  template <class T, class Op, class Pre>
+  fnpf_status cg_run(int64_t n, T* x, T* r, T* z, T* p, T* q, double stop, int max_iter, int check, double* hist,
+                     Op op, Pre pre, int* iters, double* rr) {
     double* cg = w.cg;
     FNPF_PS_TRY(pre(r, z));
-    FNPF_PS_TRY(go<CopyItem>(n, {z, p}));
+    FNPF_PS_TRY(go<CopyItemT<T>>(n, {z, p}));
     FNPF_PS_TRY(dot_dev(r, z, n, cg + kRZ));
     FNPF_PS_TRY(go<CgResetItem>(1, {cg}));
     double st[kCgSlots] = {0};
@@ -1556,7 +1584,7 @@ struct Stepper {
       FNPF_PS_TRY(op(p, q));
       FNPF_PS_TRY(dot_dev(p, q, n, cg + kPQ));
       FNPF_PS_TRY(go<CgAlphaItem>(1, {cg, hist}));
-      FNPF_PS_TRY(go<CgUpdateItem>(n, {cg, p, q, x, r}));
+      FNPF_PS_TRY(go<CgUpdateItemT<T>>(n, {cg, p, q, x, r}));
       FNPF_PS_TRY(dot_dev(r, r, n, cg + kRR));
       FNPF_PS_TRY(go<CgCheckItem>(1, {cg, stop}));
       if (check == 1) {
@@ -1566,7 +1594,7 @@ struct Stepper {
       FNPF_PS_TRY(pre(r, z));
       FNPF_PS_TRY(dot_dev(r, z, n, cg + kRZN));
       FNPF_PS_TRY(go<CgBetaItem>(1, {cg, hist}));
-      FNPF_PS_TRY(go<CgDirItem>(n, {cg, z, p}));
+      FNPF_PS_TRY(go<CgDirItemT<T>>(n, {cg, z, p}));
       if (check > 1 && (it + 1) % check == 0) {
         if (ex.get(st, cg, kCgSlots)) return FNPF_ECUDA;
         if (st[kDONE] != 0.0) break;
@@ -1604,7 +1632,7 @@ struct Stepper {
     int k = 0;
     double rr = 0;
     const fnpf_status cs =
-        cg_run(NI, nullptr, L.r, L.x, L.d, L.q, 0.0, k_max, k_max, w.cg + kCgSlots,
+        cg_run(NI, static_cast<double*>(nullptr), L.r, L.x, L.d, L.q, 0.0, k_max, k_max, w.cg + kCgSlots,
                [&](const double* pv, double* qv) { return apply_level(L, pv, qv); },
                [&](const double* rv, double* zv) { return go<DivItem>(NI, {rv, L.diag, zv}); }, &k, &rr);
     if (cs == FNPF_ECUDA) return cs;
@@ -1655,7 +1683,7 @@ struct Stepper {
       FNPF_PS_TRY(lmax_level(L, &lmax));
       L.hi = 1.1 * lmax;
       L.lo = L.hi / o.cheb_range;
-      if (o.pc32) {   // the FP32 V-cycle's metric and diagonal: the FP64 ones rounded
+      if (o.pc32 || o.mixed) {   // the FP32 V-cycle's metric and diagonal: the FP64 ones rounded
         FNPF_PS_TRY(go<CastItem<float, double>>(L.m.nelem * L.m.n * L.m.nq * 6, {L.G, L.G32}));
         FNPF_PS_TRY(go<CastItem<float, double>>(L.m.N, {L.diag, L.diag32}));
       }
@@ -1801,6 +1829,49 @@ struct Stepper {
     return go<ProjCombItem>(NI, a);
   }
 
+  // FP64 defect correction around an FP32 PCG (the mixed form): with w.r =
+  // b - A phi (FP64) and b in w.z on entry, repeat until ||r|| <= stop: e = the
+  // FP32 solution of A e = r to inner_rtol ||r|| (FP32 operator with the rounded
+  // metric and tables, the FP32 V-cycle as preconditioner, CG scalars and dot
+  // products accumulated in FP64), phi += e, r = b - A phi in FP64.
+  fnpf_status defect_correction(double* phi, double stop, const Params& o, int* iters, int* outer, double* rr) {
+    const int64_t N = m.N, NI = m.NI;
+    PLevel& L0 = pmg->lev[0];
+    int inner = 0, k = 0;
+    fnpf_status st = FNPF_ENOCONV;
+    for (;;) {
+      if (sqrt(*rr) <= stop) {
+        st = FNPF_OK;
+        break;
+      }
+      if (k >= o.max_outer) break;
+      ++k;
+      FNPF_PS_TRY(go<CastItem<float, double>>(N, {w.r, w.ir}));   // r's surface plane is zero
+      FNPF_PS_TRY(go<FillItemT<float>>(N, {0.0, w.ie}));
+      FNPF_PS_TRY(go<FillItemT<float>>(N, {0.0, w.ip}));
+      int it_in = 0;
+      double rr_in = *rr;
+      const fnpf_status si = cg_run(
+          NI, w.ie, w.ir, w.iz, w.ip, w.iq, o.inner_rtol * sqrt(*rr), o.max_iter, 1, nullptr,
+          [&](const float* pv, float* qv) {
+            FNPF_PS_TRY(elements<float>(L0.m, L0.G32, L0.F32, L0.ye32, L0.vt32, pv));
+            return go<GatherItemT<float>>(N, {L0.m.voff, L0.m.vinc, L0.ye32, qv});
+          },
+          [&](const float* rv, float* zv) { return vcycle<float>(0, rv, zv, o); }, &it_in, &rr_in);
+      if (si != FNPF_OK && si != FNPF_ENOCONV) return si;
+      inner += it_in;
+      FNPF_PS_TRY(go<AddCastItem>(NI, {w.ie, phi}));
+      FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, phi, w.pd}));
+      FNPF_PS_TRY(apply(w.pd, w.q));
+      FNPF_PS_TRY(go<LinItem>(NI, {w.z, -1.0, w.q, w.r}));   // r = b - A phi
+      FNPF_PS_TRY(dot(w.r, w.r, NI, rr));
+      if (!isfinite(*rr)) return FNPF_EDIVERGED;
+    }
+    *iters = inner;
+    *outer = k;
+    return st;
+  }
+
   // phi = the solution of A_II phi_I = -A_IS phis (in: the interior guess),
   // phi = phis on the surface plane; Jacobi-PCG to ||r|| <= rtol ||b||.
   fnpf_status solve(const double* eta, const double* h, const double* phis, double* phi, const Params& o,
@@ -1815,8 +1886,9 @@ struct Stepper {
     FNPF_PS_TRY(go<InteriorItem>(N, {NI, -1.0, w.q, w.r}));   // r = b = -A_IS phis
     double bb = 0;
     FNPF_PS_TRY(dot(w.r, w.r, NI, &bb));
+    if (o.mixed) FNPF_PS_TRY(go<CopyItem>(NI, {w.r, w.z}));   // b, for the outer residuals
     fnpf_status st = FNPF_OK;
-    int it = 0;
+    int it = 0, outer = 0;
     double rr = 0;
     if (!(bb > 0)) {   // b = 0: the solution is zero
       if (!(bb == 0)) st = FNPF_EDIVERGED;
@@ -1832,7 +1904,10 @@ struct Stepper {
         FNPF_PS_TRY(go<AxpyItem>(NI, {-1.0, w.q, w.r}));          // r = b - A_II x0
       }
       FNPF_PS_TRY(dot(w.r, w.r, NI, &rr));
-      if (sqrt(rr) > stop) {
+      if (o.mixed) {
+        st = defect_correction(phi, stop, o, &it, &outer, &rr);
+        if (st == FNPF_ECUDA) return st;
+      } else if (sqrt(rr) > stop) {
         // w.pd's surface plane is zero (above); the loop writes its first NI entries only
         st = cg_run(NI, phi, w.r, w.z, w.pd, w.q, stop, o.max_iter, o.pmg ? 1 : 8, nullptr,
                     [&](const double* pv, double* qv) { return apply(pv, qv); },
@@ -1848,6 +1923,7 @@ struct Stepper {
     FNPF_PS_TRY(go<CopyItem>(m.ns, {phis, phi + NI}));
     if (info) {
       info->iters = it;
+      info->outer_iters = outer;
       info->rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
       info->status = st;
     }

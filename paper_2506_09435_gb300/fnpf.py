@@ -47,7 +47,8 @@ class PrismOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mass_rtol", ctypes.c_double),
                 ("mass_max_iter", ctypes.c_int), ("g", ctypes.c_double), ("model", ctypes.c_int),
                 ("precond", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int),
-                ("cheb_range", ctypes.c_double), ("precision", ctypes.c_int), ("projection", ctypes.c_int)]
+                ("cheb_range", ctypes.c_double), ("precision", ctypes.c_int), ("projection", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

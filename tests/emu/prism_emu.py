@@ -44,13 +44,14 @@ class PrismOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mass_rtol", ctypes.c_double),
                 ("mass_max_iter", ctypes.c_int), ("g", ctypes.c_double), ("model", ctypes.c_int),
                 ("precond", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("coarse_iters", ctypes.c_int),
-                ("cheb_range", ctypes.c_double), ("precision", ctypes.c_int), ("projection", ctypes.c_int)]
+                ("cheb_range", ctypes.c_double), ("precision", ctypes.c_int), ("projection", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int)]
 
 
 def opts(rtol=1e-10, max_iter=20000, mass_rtol=1e-13, g=9.81, linear=False, pmg=False, cheb_degree=3,
-         coarse_iters=6, cheb_range=40.0, pc32=False, projection=0):
+         coarse_iters=6, cheb_range=40.0, pc32=False, projection=0, mixed=False, inner_rtol=1e-5, max_outer=20):
     return PrismOpts(rtol, max_iter, mass_rtol, 5000, g, int(linear), int(pmg), cheb_degree, coarse_iters,
-                     cheb_range, 2 if pc32 else 0, projection)
+                     cheb_range, 1 if mixed else (2 if pc32 else 0), projection, inner_rtol, max_outer)
 
 
 class SolveInfo(ctypes.Structure):

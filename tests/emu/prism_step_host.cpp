@@ -157,7 +157,8 @@ static Params params(const fnpf_prism_opts* o) {
   if (!o) o = &d;
   return Params{o->rtol,         o->max_iter,    o->mass_rtol,    o->mass_max_iter, o->g, o->model == FNPF_LINEAR,
                 o->precond == FNPF_PMG, o->cheb_degree, o->coarse_iters, o->cheb_range,
-                o->precond == FNPF_PMG && o->precision == FNPF_FP64_PC32, o->projection};
+                o->precond == FNPF_PMG && o->precision == FNPF_FP64_PC32, o->projection,
+                o->precond == FNPF_PMG && o->precision == FNPF_MIXED, o->inner_rtol, o->max_outer};
 }
 
 // A stepper over the harness's memory (with the hierarchy when the options ask for it).

@@ -39,7 +39,7 @@ def fake_binding(monkeypatch, tmp_path):
         @staticmethod
         def default_opts(rtol=1e-10, g=9.81, precond=F.FNPF_JACOBI, precision=F.FNPF_FP64, projection=0):
             return E.opts(rtol=rtol, g=g, pmg=precond == F.FNPF_PMG, pc32=precision == F.FNPF_FP64_PC32,
-                          projection=projection)
+                          mixed=precision == F.FNPF_MIXED, projection=projection)
 
         def set_relaxation(self, cr, gen, amp, kx, ky, omega, phase, ramp_time):
             self.em.set_relaxation(cr, gen, amp, kx, ky, omega, phase, ramp_time)
@@ -60,7 +60,7 @@ def fake_binding(monkeypatch, tmp_path):
 
     fake = types.SimpleNamespace(PrismMesh=PrismMesh, prism_numbering=F.prism_numbering,
                                  FNPF_PMG=F.FNPF_PMG, FNPF_JACOBI=F.FNPF_JACOBI, FNPF_FP64=F.FNPF_FP64,
-                                 FNPF_FP64_PC32=F.FNPF_FP64_PC32)
+                                 FNPF_FP64_PC32=F.FNPF_FP64_PC32, FNPF_MIXED=F.FNPF_MIXED)
     import paper_2506_09435_gb300 as pkg
     monkeypatch.setattr(pkg, "fnpf", fake)
     monkeypatch.setattr(torch.cuda, "Event", _Event)
@@ -77,6 +77,8 @@ def test_prism_leg_reports_throughput_iterations_and_oracle_error(fake_binding):
     assert 0 < out["cg_iters_per_solve_mean"] < out["jacobi"]["cg_iters_per_solve_mean"]
     op = out["operator"]
     assert op["stored_metric"]["flops_executed"] > 0 and "us_per_application" in op["metric_per_application"], op
+    mx = out["mixed"]
+    assert mx["rel_l2_vs_fp64"]["eta"] <= 1e-8 and mx["rel_l2_vs_fp64"]["phis"] <= 1e-8, mx
     pc = out["fp64_pc32"]
     assert pc["rel_l2_vs_fp64"]["eta"] <= 1e-8 and pc["rel_l2_vs_fp64"]["phis"] <= 1e-8, pc
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 1

@@ -270,3 +270,31 @@ def test_projected_guess_same_states_fewer_iterations(fnpf):
     (e0, p0, n0), (e8, p8, n8) = out[0], out[8]
     assert C.rel(e8, e0) <= 1e-9 and C.rel(p8, p0) <= 1e-9
     assert n8 < 0.9 * n0, (n8, n0)
+
+
+@pytest.mark.parametrize("p, nz, nx, ny", [(2, 2, 3, 2), (4, 2, 6, 4)])
+def test_defect_correction_solve_matches_oracle(fnpf, p, nz, nx, ny):
+    v, t, pm = C.mesh(p, nz, nx=nx, ny=ny)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi = torch.zeros(pm.N, dtype=torch.float64, device=DEV)
+    o = fnpf.PrismMesh.default_opts(rtol=1e-13, g=C.G, precond=fnpf.FNPF_PMG, precision=fnpf.FNPF_MIXED,
+                                    inner_rtol=1e-4, mass_rtol=1e-13)
+    info = gm.laplace_solve(T(eta), T(h), T(phis), phi, o)
+    assert info["status"] == 0 and info["rel_res"] <= 1e-13 and 1 <= info["outer_iters"] <= 6
+    assert C.rel(phi.cpu().numpy(), P.laplace_solve(pm, eta, h, phis)) <= 1e-10
+
+
+def test_defect_correction_rk4_steps_match_oracle(fnpf):
+    p, nz = 4, 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.standing_wave(pm)
+    e1, p1, hd = T(eta), T(phis), T(h)
+    eo, po = eta.copy(), phis.copy()
+    o = fnpf.PrismMesh.default_opts(rtol=1e-13, g=C.G, precond=fnpf.FNPF_PMG, precision=fnpf.FNPF_MIXED,
+                                    mass_rtol=1e-13)
+    for _ in range(3):
+        gm.rk4_step(hd, e1, p1, 0.02, o)
+        eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
+    assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10

@@ -283,6 +283,32 @@ def test_projected_guess_same_states_fewer_iterations(harness, pmg):
     assert st == 0 and info.iters == 0
 
 
+@pytest.mark.parametrize("p, nz, nx, ny", [(2, 2, 3, 2), (4, 2, 6, 4), (6, 2, 4, 3)])
+def test_defect_correction_solve_matches_oracle(harness, p, nz, nx, ny):
+    """FP64 defect correction around an FP32 PCG with the FP32 V-cycle: the
+    oracle's solution to the FP64 tolerance, in a few outer steps."""
+    v, t, pm = C.mesh(p, nz, nx=nx, ny=ny)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi = np.zeros(pm.N)
+    st, info = em.laplace_solve(E.opts(rtol=1e-13, g=C.G, pmg=True, mixed=True, inner_rtol=1e-4), eta, h, phis, phi)
+    assert st == 0 and info.rel_res <= 1e-13 and 1 <= info.outer_iters <= 6 and info.iters > 0
+    assert C.rel(phi, P.laplace_solve(pm, eta, h, phis)) <= 1e-10
+
+
+def test_defect_correction_rk4_steps_match_oracle(harness):
+    p, nz = 4, 2
+    v, t, pm = C.mesh(p, nz, nx=4, ny=3, seed=11)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.standing_wave(pm)
+    e1, p1 = eta.copy(), phis.copy()
+    eo, po = eta.copy(), phis.copy()
+    for _ in range(3):
+        assert em.rk4_step(E.opts(rtol=1e-13, g=C.G, pmg=True, mixed=True), h, e1, p1, 0.02)[0] == 0
+        eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
+    assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -316,7 +342,8 @@ for p, nz in [(1, 1), (8, 1), (7, 2)]:
     v, t, pm = C.mesh(p, nz, nx=2, ny=1)
     em = hs.mesh(v, t, p, nz)
     eta, h, phis = C.fields(pm)
-    for o in (E.opts(g=C.G, pmg=True), E.opts(g=C.G, pmg=True, pc32=True), E.opts(g=C.G, pmg=True, linear=True)):
+    for o in (E.opts(g=C.G, pmg=True), E.opts(g=C.G, pmg=True, pc32=True), E.opts(g=C.G, pmg=True, linear=True),
+              E.opts(g=C.G, pmg=True, mixed=True, projection=8)):
         assert em.laplace_solve(o, eta, h, phis, np.zeros(pm.N))[0] == 0
         assert em.rk4_step(o, h, eta.copy(), phis.copy(), 0.01)[0] == 0
     em.invariants(E.opts(g=C.G, pmg=True, pc32=True), eta, h, phis)
