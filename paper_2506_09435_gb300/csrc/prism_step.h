@@ -17,15 +17,20 @@
 //             prism, from eta and h (z = -h + sigma (eta + h)), stored for the
 //             solve, and the Jacobi diagonal from it;
 //   lift      b = -A_IS phi_eta (the operator applied to the surface values);
-//   PCG       A_II phi_I = b with the Jacobi preconditioner (Eq. Laplace_weak:
-//             element fluxes G grad u at the points, transposed contractions to
-//             the local nodes, element results summed per node in a fixed order);
+//   PCG       A_II phi_I = b (Eq. Laplace_weak: element fluxes G grad u at the
+//             points, transposed contractions to the local nodes, element
+//             results summed per node in a fixed order), preconditioned by
+//             Jacobi or a p-multigrid V-cycle (Chebyshev-Jacobi smoothing) in
+//             FP64 or FP32, or as FP64 defect correction around an FP32 PCG;
+//             optionally from the projection of the solution onto the previous
+//             solutions;
 //   w         d phi / dz = phi_t / z_t on the top layer's vertical GLL lines;
 //   conditions the kinematic and dynamic conditions (Sec. 2) at the triangle
 //             quadrature points, projected onto the nodal surface space with the
 //             consistent mass, M k = int f l_i dA (Eq. free_surface_weak; the
 //             mass solve by Jacobi-PCG on the assembled CSR matrix);
-//   RK4       the classical stage states and combination.
+//   RK4       the classical stage states and combination, then the relaxation
+//             zones and the modal filter (Sec. 3.3, Sec. 3.2) when set.
 // Node and quadrature conventions are those of prism.cu (fnpf_prism_*).
 #pragma once
 
@@ -743,15 +748,6 @@ struct AxpyItem {   // y += s x
     double* y;
   };
   FNPF_HD static void at(int64_t i, const Args& a) { a.y[i] += a.s * a.x[i]; }
-};
-
-struct XpbyItem {   // y = x + s y
-  struct Args {
-    const double* x;
-    double s;
-    double* y;
-  };
-  FNPF_HD static void at(int64_t i, const Args& a) { a.y[i] = a.x[i] + a.s * a.y[i]; }
 };
 
 struct LinItem {   // out = x + s y
