@@ -27,10 +27,28 @@ __global__ void __launch_bounds__(kItemThreads) pstep_kernel(int64_t n, typename
   if (i < n) It::at(i, a);
 }
 
+// A block kernel: K's phases in order, a barrier after each, the block's
+// shared memory given to every phase.
+template <class K>
+__global__ void __launch_bounds__(K::kThreads) pstep_block_kernel(typename K::Args a) {
+  extern __shared__ __align__(16) unsigned char pstep_smem[];
+  auto* sm = reinterpret_cast<typename K::value_type*>(pstep_smem);
+  for (int ph = 0; ph < K::kPhases; ++ph) {
+    K::phase(ph, (int64_t)blockIdx.x, (int)threadIdx.x, (int)blockDim.x, sm, a);
+    __syncthreads();
+  }
+}
+
 namespace {
 
 struct DeviceEx {
   cudaStream_t s;
+  template <class K>
+  int run_block(int64_t blocks, size_t smem, const typename K::Args& a) {
+    if (blocks < 1 || blocks > INT_MAX || smem > 48 * 1024) return 1;   // p <= 8: at most 31 KB
+    pstep_block_kernel<K><<<(unsigned)blocks, K::kThreads, smem, s>>>(a);
+    return cudaPeekAtLastError() != cudaSuccess;
+  }
   template <class It>
   int run(int64_t n, const typename It::Args& a) {
     const int64_t blocks = (n + kItemThreads - 1) / kItemThreads;

@@ -8,7 +8,8 @@
 // synchronisation inside a launch, every output written by exactly one item),
 // so the same bodies run as CUDA kernels (prism_step.cu: one thread per item)
 // and, compiled as plain C++, one item after another.  Stepper<Ex> orders the
-// launches; Ex supplies run<Item>(n, args) and get(host, src, count), the
+// launches; Ex supplies run<Item>(n, args), run_block<Block>(blocks, smem
+// bytes, args) for the block kernels and get(host, src, count), the
 // device-to-host read of the CG loops' state (their scalars stay on the
 // device; the host tests the stop flag).
 //
@@ -673,6 +674,91 @@ struct TSumItemT {
   }
 };
 using TSumItem = TSumItemT<double>;
+
+// The element results of A x for one prism per block, staged in shared memory:
+// the block's phases run in order with a barrier after each (a phase writes
+// only shared or output entries that no other thread of the same phase reads
+// or writes), every thread of the block taking the entries tid, tid + threads,
+// ... of each phase.  Phase 0 loads the element's values u [n][nt], 1 forms
+// the vertical derivatives ut [n][nt], 2 the fluxes F [n nq][3] at the points
+// (the metric read from G), 3 the vertical sums vs [n][nt], 4 the node results
+// ye -- the arithmetic of DtItem, FluxItem, TSumItem and NodeItem in the same
+// order, with each value loaded from global memory once per element.  Shared
+// memory: smem_entries(m) values of T.
+template <class T>
+struct ElementBlock {
+  using value_type = T;
+  static constexpr int kThreads = 128;
+  static constexpr int kPhases = 5;
+  struct Args {
+    PMesh m;
+    const T* G;
+    const T* x;
+    T* ye;
+  };
+  FNPF_HD static int64_t smem_entries(const PMesh& m) { return 3 * (int64_t)m.nt * m.n + 3 * (int64_t)m.n * m.nq; }
+  FNPF_HD static void phase(int ph, int64_t elem, int tid, int nthr, T* sm, const Args& a) {
+    const PMesh& m = a.m;
+    const Tabs<T> tb = tabs_of(m, (const T*)nullptr);
+    const int nt = m.nt, n = m.n, nq = m.nq, ntn = nt * n, npt = n * nq;
+    T* u = sm;
+    T* ut = u + ntn;
+    T* vs = ut + ntn;
+    T* F = vs + ntn;
+    const int e = (int)(elem / m.nz), l = (int)(elem - (int64_t)e * m.nz);
+    const int* tn = m.tn + (int64_t)e * nt;
+    if (ph == 0) {
+      for (int idx = tid; idx < ntn; idx += nthr) {
+        const int c = idx % nt, mm = idx / nt;
+        u[idx] = a.x[((int64_t)l * m.p + mm) * m.ns + tn[c]];
+      }
+    } else if (ph == 1) {
+      for (int idx = tid; idx < ntn; idx += nthr) {
+        const int c = idx % nt, k = idx / nt;
+        const T* Dk = tb.D + (int64_t)k * n;
+        T s = 0;
+        for (int mm = 0; mm < n; ++mm) s += Dk[mm] * u[mm * nt + c];
+        ut[idx] = s;
+      }
+    } else if (ph == 2) {
+      for (int pt = tid; pt < npt; pt += nthr) {
+        const int k = pt / nq, q = pt - k * nq;
+        const T* Lq = tb.L + (int64_t)q * nt;
+        const T* Lrq = tb.Lr + (int64_t)q * nt;
+        const T* Lsq = tb.Ls + (int64_t)q * nt;
+        const T* uk = u + k * nt;
+        const T* utk = ut + k * nt;
+        T ur = 0, us = 0, uz = 0;
+        for (int c = 0; c < nt; ++c) {
+          ur += Lrq[c] * uk[c];
+          us += Lsq[c] * uk[c];
+          uz += Lq[c] * utk[c];
+        }
+        const T* G = a.G + 6 * (elem * npt + pt);
+        F[3 * pt] = G[0] * ur + G[1] * us + G[2] * uz;
+        F[3 * pt + 1] = G[1] * ur + G[3] * us + G[4] * uz;
+        F[3 * pt + 2] = G[2] * ur + G[4] * us + G[5] * uz;
+      }
+    } else if (ph == 3) {
+      for (int idx = tid; idx < ntn; idx += nthr) {
+        const int c = idx % nt, k = idx / nt;
+        const T* Fk = F + 3 * (k * nq);
+        T s = 0;
+        for (int q = 0; q < nq; ++q) s += tb.L[(int64_t)q * nt + c] * Fk[3 * q + 2];
+        vs[idx] = s;
+      }
+    } else {
+      for (int idx = tid; idx < ntn; idx += nthr) {
+        const int c = idx % nt, mm = idx / nt;
+        const T* Fm = F + 3 * (mm * nq);
+        T y = 0;
+        for (int q = 0; q < nq; ++q) y += tb.Lr[(int64_t)q * nt + c] * Fm[3 * q] + tb.Ls[(int64_t)q * nt + c] * Fm[3 * q + 1];
+        for (int k = 0; k < n; ++k) y += tb.D[(int64_t)k * n + mm] * vs[k * nt + c];
+        a.ye[elem * ntn + idx] = y;
+      }
+    }
+  }
+};
 
 // Element diagonal at local node (c, mm): sum over the points of g^T G g with g
 // the reference gradient of that node's basis function.
@@ -1516,8 +1602,20 @@ struct Stepper {
 
   // The element results ye of A x on the mesh view mv with its metric G (the
   // vertical derivatives, the fluxes, the vertical sums, the node contractions).
+  // The element results ye of A x: one block per prism, staged in shared memory.
   template <class T>
   fnpf_status elements(const PMesh& mv, const T* G, T* F, T* ye, T* vt, const T* x) {
+    (void)F;
+    (void)vt;
+    if (mv.nelem <= 0) return FNPF_OK;
+    const size_t smem = sizeof(T) * (size_t)ElementBlock<T>::smem_entries(mv);
+    return ex.template run_block<ElementBlock<T>>(mv.nelem, smem, {mv, G, x, ye}) ? FNPF_ECUDA : FNPF_OK;
+  }
+
+  // The same element results from the one-thread-per-item kernels (the
+  // reference of the block form: the same arithmetic in the same order).
+  template <class T>
+  fnpf_status elements_items(const PMesh& mv, const T* G, T* F, T* ye, T* vt, const T* x) {
     const int64_t nodes = mv.nelem * mv.nt * mv.n;
     FNPF_PS_TRY(go<DtItemT<T>>(nodes, {mv, x, vt}));
     FNPF_PS_TRY(go<FluxItemT<T>>(mv.nelem * mv.n * mv.nq, {mv, G, x, vt, F}));

@@ -74,7 +74,7 @@ class Harness:
         lib.emu_destroy.restype = None
         lib.emu_sizes.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int64)] * 3
         lib.emu_sizes.restype = None
-        sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_laplace_solve": [vp] * 7, "emu_precond_apply": [vp] * 6,
+        sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_apply_items": [vp] * 5, "emu_laplace_solve": [vp] * 7, "emu_precond_apply": [vp] * 6,
                "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, ctypes.c_double, vp],
                "emu_set_relaxation": [vp] * 3 + [ctypes.c_double] * 6, "emu_invariants": [vp] * 7}
         sig["emu_set_filter"] = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
@@ -118,6 +118,11 @@ class EmuMesh:
     def apply_stored(self, eta, h, x):
         y = np.zeros(self.N)
         assert self.lib.emu_apply_stored(self.h, _p(eta), _p(h), _p(x), _p(y)) == 0
+        return y
+
+    def apply_items(self, eta, h, x):
+        y = np.zeros(self.N)
+        assert self.lib.emu_apply_items(self.h, _p(eta), _p(h), _p(x), _p(y)) == 0
         return y
 
     def laplace_solve(self, opts, eta, h, phis, phi):

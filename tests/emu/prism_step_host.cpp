@@ -31,6 +31,19 @@ struct HostEx {
     for (int64_t i = 0; i < n; ++i) It::at(i, a);
     return 0;
   }
+  // A block kernel: for every block, each phase for every thread of the block
+  // before the next phase (the barrier), on a shared array of exactly the
+  // requested size.
+  template <class K>
+  int run_block(int64_t blocks, size_t smem, const typename K::Args& a) {
+    ++launches;
+    using T = typename K::value_type;
+    std::unique_ptr<T[]> sm(new T[smem / sizeof(T)]);
+    for (int64_t b = 0; b < blocks; ++b)
+      for (int ph = 0; ph < K::kPhases; ++ph)
+        for (int tid = 0; tid < K::kThreads; ++tid) K::phase(ph, b, tid, K::kThreads, sm.get(), a);
+    return 0;
+  }
   int get(double* dst, const double* src, int count) {
     memcpy(dst, src, sizeof(double) * count);
     return 0;
@@ -181,6 +194,17 @@ int emu_apply_stored(void* h, const double* eta, const double* hh, const double*
   Stepper<HostEx> sp{e->m, e->w, e->ex};
   fnpf_status st = sp.geometry(eta, hh);
   if (st == FNPF_OK) st = sp.apply(x, y);
+  return st;
+}
+
+// y = A x through the one-thread-per-item operator kernels (the reference of
+// the block kernel used by every other entry point).
+int emu_apply_items(void* h, const double* eta, const double* hh, const double* x, double* y) {
+  Emu* e = static_cast<Emu*>(h);
+  Stepper<HostEx> sp{e->m, e->w, e->ex};
+  fnpf_status st = sp.geometry(eta, hh);
+  if (st == FNPF_OK) st = sp.elements_items(e->m, (const double*)e->w.G, e->w.F, e->w.ye, e->w.vt, x);
+  if (st == FNPF_OK) st = sp.go<GatherItem>(e->m.N, {e->m.voff, e->m.vinc, e->w.ye, y});
   return st;
 }
 

@@ -45,6 +45,19 @@ def test_stored_operator_and_diagonal_match_oracle(harness, p, nz):
     assert np.max(np.abs(em.diagonal(eta, h) - d)) <= 1e-13 * np.max(np.abs(d))
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("nz", [1, 3])
+def test_block_operator_equals_item_operator_bitwise(harness, p, nz):
+    """The shared-memory block kernel of the operator (one prism per block, five
+    phases with a barrier after each) against the one-thread-per-item kernels
+    it replaces: the same arithmetic in the same order, so the same bits."""
+    v, t, pm = C.mesh(p, nz, nx=2, ny=2)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, _ = C.fields(pm)
+    x = np.random.default_rng(p).standard_normal(pm.N)
+    assert np.array_equal(em.apply_stored(eta, h, x), em.apply_items(eta, h, x))
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_laplace_solve_matches_oracle(harness, p):
     nz = 2
