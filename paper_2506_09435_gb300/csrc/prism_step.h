@@ -1593,6 +1593,7 @@ struct Stepper {
   PWork& w;
   Ex& ex;
   PMG* pmg = nullptr;   // the hierarchy (needed when Params::pmg is set)
+  bool reuse_lmax = false;   // keep the levels' Chebyshev intervals (stages 2-4 of an RK4 step)
 
   template <class It>
   fnpf_status go(int64_t n, const typename It::Args& a) {
@@ -1761,8 +1762,10 @@ struct Stepper {
     return FNPF_OK;
   }
 
-  // Geometry, diagonals and Chebyshev intervals of every level for (eta, h);
-  // level 0's geometry is current.
+  // Geometry, diagonals and Chebyshev intervals of every level for (eta, h)
+  // (the intervals kept when reuse_lmax: within one RK4 step the geometry moves
+  // by O(dt), well inside the 10 % margin on lambda_max); level 0's geometry is
+  // current.
   fnpf_status setup_pmg(const double* eta, const double* h, const Params& o) {
     pmg->lev[0].eta = const_cast<double*>(eta);
     pmg->lev[0].h = const_cast<double*>(h);
@@ -1773,10 +1776,12 @@ struct Stepper {
         FNPF_PS_TRY(go<CoarseGeoItem>(L.m.ns, {F.m, L.m, pmg->xf[l - 1], F.eta, F.h, L.eta, L.h}));
         FNPF_PS_TRY(geometry_level(L, L.eta, L.h));
       }
-      double lmax = 0;
-      FNPF_PS_TRY(lmax_level(L, &lmax));
-      L.hi = 1.1 * lmax;
-      L.lo = L.hi / o.cheb_range;
+      if (!(reuse_lmax && L.hi > 0)) {
+        double lmax = 0;
+        FNPF_PS_TRY(lmax_level(L, &lmax));
+        L.hi = 1.1 * lmax;
+        L.lo = L.hi / o.cheb_range;
+      }
       if (o.pc32 || o.mixed) {   // the FP32 V-cycle's metric and diagonal: the FP64 ones rounded
         FNPF_PS_TRY(go<CastItem<float, double>>(L.m.nelem * L.m.n * L.m.nq * 6, {L.G, L.G32}));
         FNPF_PS_TRY(go<CastItem<float, double>>(L.m.N, {L.diag, L.diag32}));
@@ -2102,7 +2107,10 @@ struct Stepper {
         E = w.es;
         P = w.ps;
       }
-      FNPF_PS_TRY(rhs(E, h, P, w.ke, w.kp, o, info ? info + s : nullptr));
+      reuse_lmax = s > 0;   // the Chebyshev intervals of the step's first stage serve all four
+      const fnpf_status sr = rhs(E, h, P, w.ke, w.kp, o, info ? info + s : nullptr);
+      reuse_lmax = false;
+      FNPF_PS_TRY(sr);
       if (s == 0) {
         FNPF_PS_TRY(go<CopyItem>(ns, {w.ke, w.ae}));
         FNPF_PS_TRY(go<CopyItem>(ns, {w.kp, w.ap}));
