@@ -525,7 +525,8 @@ const char* fnpf_prism_last_error(const fnpf_prism* mesh);
  *     is exact interpolation and restriction its transpose), first-kind
  *     Chebyshev acceleration of Jacobi on [lmax / cheb_range, lmax] of every
  *     level as smoother (Saad, Iterative Methods, Alg. 12.1; lmax = 1.1 x the
- *     largest Ritz value of 12 Jacobi-PCG steps, per solve), Chebyshev of
+ *     largest Ritz value of 12 Jacobi-PCG steps, per solve and once per
+ *     RK4 step), Chebyshev of
  *     degree coarse_iters on the coarsest level: a fixed symmetric positive
  *     definite preconditioner, so plain PCG converges to the same solution.
  * Arrays are DEVICE pointers owned by the caller: eta, h, phis, w, k_eta,
