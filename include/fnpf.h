@@ -543,10 +543,12 @@ const char* fnpf_prism_last_error(const fnpf_prism* mesh);
  * Laplace CG iterations (FNPF_MIXED: inner iterations), outer_iters = defect-
  * correction steps (0 unless FNPF_MIXED), rel_res = ||r|| / ||b|| (FP64),
  * status; ms = 0.  The first call on a mesh allocates its workspace (about
- * 9 N + 72 nprisms (p + 1) (p + 2)^2 doubles, synchronising the device) and
- * builds the surface tables; later calls allocate nothing.  Calls on one mesh
- * must not overlap; each returns after its stream has finished its work (the
- * CG loops wait for every dot product).  eta + h > 0 is assumed (not checked).
+ * 28 N + 9 nprisms (p + 1) (p + 2)^2 doubles, the projection basis included;
+ * synchronising the device) and builds the surface tables, the first FNPF_PMG
+ * call the hierarchy (per level about the same in FP64 and half of it in
+ * FP32); later calls allocate nothing.  Calls on one mesh must not overlap;
+ * each returns after its stream has finished its work (the CG loops read
+ * their state from the device every few iterations).  eta + h > 0 is assumed (not checked).
  * Errors: EINVAL (NULL, non-finite dt, bad options), ENOMEM, ECUDA, ENOCONV
  * (an iteration cap reached), EBREAKDOWN (p.Ap <= 0), EDIVERGED (non-finite
  * residual); the message from fnpf_prism_last_error(mesh). */
