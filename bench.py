@@ -86,6 +86,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-prism", action="store_true", help="skip the prism-mesh leg of the step benchmark")
+    ap.add_argument("--no-bar", action="store_true", help="skip the shortened bar-flume leg of the step benchmark")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "pc32"],
                     help="precision of the headline path (the configuration's plain method is fp64)")
     ap.add_argument("--nx", type=int, default=32)
@@ -681,6 +682,13 @@ def main_gb300(args):
         if args.model != "fnpf":
             vs_oracle = None      # the oracle sample is the nonlinear model
 
+    bar = None
+    if rank == 0 and world == 1 and not args.no_bar:
+        try:   # the mixed form's own configuration, shortened: 30 steps from rest, 5 timed after 3
+            bar = bar_flume_run(args, 30, 5, 3)
+        except Exception as e:   # reported in the line instead of ending the run
+            bar = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
+
     prism = None
     if rank == 0 and world == 1 and not args.no_prism:
         try:   # runs last: nothing measured above depends on it
@@ -717,6 +725,7 @@ def main_gb300(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
+            "bar": bar,
             "prism": prism,
         }
         print(json.dumps(line))
@@ -1155,14 +1164,21 @@ def main_convergence(args):
 
 
 def main_bar(args):
+    """--mode bar: bar_flume_run for `--bar-steps` steps, `--steps` timed after `--warmup`."""
+    out = bar_flume_run(args, args.bar_steps, args.steps, args.warmup)
+    print(json.dumps({"mode": "bar", **out}))
+    return 0
+
+
+def bar_flume_run(args, bar_steps, steps, warmup):
     """The submerged-bar flume (256 x 16 x 3 elements, p = 5, 1,660,176 DOF,
     walls, variable depth; incident T = 2.02 s, H = 0.02 m through a
     generation zone, absorption zone at the outlet), run from rest for
-    `--bar-steps` RK4 steps of dt = T/100 in FP64, in the defect-correction
+    `bar_steps` RK4 steps of dt = T/100 in FP64, in the defect-correction
     mixed form and in FP64 PCG with the FP32 p-multigrid preconditioner.
-    Throughput from `--steps` timed steps after `--warmup`; accuracy of each
+    Throughput from `steps` timed steps after `warmup`; accuracy of each
     mixed form against the FP64 run at 8 probes spread over x = 8 ... 30 m at
-    y = 0.5 m (the nearest surface node)."""
+    y = 0.5 m (the nearest surface node) and over the whole surface."""
     import numpy as np
     import torch
 
@@ -1194,11 +1210,11 @@ def main_bar(args):
         eta = torch.zeros(gm.ns, dtype=torch.float64, device=dev)
         phis = torch.zeros_like(eta)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(steps)]
         iters = []
-        for n in range(max(args.bar_steps, args.warmup + args.steps)):
-            k = n - args.warmup
-            timed = 0 <= k < args.steps
+        for n in range(max(bar_steps, warmup + steps)):
+            k = n - warmup
+            timed = 0 <= k < steps
             if timed:
                 flush.zero_()
                 ev[k][0].record(stream)
@@ -1207,7 +1223,7 @@ def main_bar(args):
                 ev[k][1].record(stream)
                 iters += [i["iters"] for i in inf]
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
         e = eta.cpu().numpy()
         row = {"precision": name, "value": gm.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                "cg_iters_per_solve_mean": statistics.mean(iters)}
@@ -1219,11 +1235,10 @@ def main_bar(args):
             row["field_rel_l2_vs_fp64"] = float(np.linalg.norm(e - ref) / np.linalg.norm(ref))
         rows.append(row)
         del gm
-    print(json.dumps({"mode": "bar", "workload": "submerged-bar flume 256x16x3, p=5, walls, relaxation zones",
-                      "dof": ncx * ncy * (d["p"] * d["nz"] + 1),
-                      "steps_run": max(args.bar_steps, args.warmup + args.steps), "dt": dt, "probes_x": px.tolist(),
-                      "rows": rows, "data": "synthetic"}))
-    return 0
+    return {"workload": "submerged-bar flume 256x16x3, p=5, walls, relaxation zones",
+            "dof": ncx * ncy * (d["p"] * d["nz"] + 1), "steps_run": max(bar_steps, warmup + steps),
+            "timed_steps": steps, "warmup": warmup, "dt": dt, "probes_x": px.tolist(), "rows": rows,
+            "data": "synthetic"}
 
 
 def main_cylinder(args):
