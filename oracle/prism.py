@@ -174,7 +174,7 @@ class PrismMesh:
         e_q, er, es = self.L @ E, self.Lr @ E, self.Ls @ E
         h_q, hr, hs = self.L @ H, self.Lr @ H, self.Ls @ H
         xi, wv, D = self.rule.xi, self.rule.w, self.rule.D
-        K = np.zeros((nt * (p + 1), nt * (p + 1)))
+        K = np.zeros((nt * (p + 1), nt * (p + 1)), dtype=np.result_type(eta, h, float))
         for k in range(p + 1):
             sig = (lay + 0.5 * (1.0 + xi[k])) / nz
             for q in range(len(self.wq)):
@@ -193,7 +193,9 @@ class PrismMesh:
                         gref[1, sl] = self.Ls[q]
                     gref[2, sl] = self.L[q] * D[k, m]
                 g = Jinv.T @ gref
-                K += self.wq[q] * wv[k] * abs(det) * (g.T @ g)
+                # |det J| written as det J sign(Re det J): the same value for real
+                # input, and analytic, so that a complex step differentiates it
+                K += self.wq[q] * wv[k] * (det * np.sign(det.real)) * (g.T @ g)
         return K
 
     def local_to_global(self, e, lay):
@@ -219,7 +221,7 @@ def laplace_solve(pm, eta, h, phis):
     (homogeneous Neumann on the bottom and the lateral walls)."""
     A = pm.assemble(eta, h)
     NI = pm.N - pm.ns
-    phi = np.zeros(pm.N)
+    phi = np.zeros(pm.N, dtype=np.result_type(eta, h, phis, float))
     phi[NI:] = phis
     rhs = -(A[:NI, NI:] @ phis)
     phi[:NI] = spla.spsolve(A[:NI, :NI].tocsc(), rhs)

@@ -393,3 +393,24 @@ def test_mass_and_energy():
     # measured 5.4e-3, 2.3e-3, 1.1e-4, 5.5e-6 for p = 2..5
     assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1)), errs
     assert errs[-1] < 1e-5 and errs[-1] < 1e-2 * errs[0], errs
+
+
+def test_complex_step_derivative_of_the_solve():
+    """The prism solve differentiated by a complex step in eta and in h (the
+    oracle's arithmetic is analytic: |det J| is written det J sign(Re det J))
+    equals central finite differences; real input gives the real solve."""
+    from tests import prism_cases as C
+    v, t, pm = C.mesh(2, 2, nx=2, ny=1)
+    eta, h, phis = C.fields(pm)
+    rng = np.random.default_rng(4)
+    de, dh = rng.standard_normal(pm.ns), rng.standard_normal(pm.ns)
+    eps, fd = 1e-30, 1e-6
+    for d_eta, d_h in ((de, 0 * dh), (0 * de, dh)):
+        cs = P.laplace_solve(pm, eta + 1j * eps * d_eta, h + 1j * eps * d_h, phis.astype(complex)).imag / eps
+        cd = (P.laplace_solve(pm, eta + fd * d_eta, h + fd * d_h, phis)
+              - P.laplace_solve(pm, eta - fd * d_eta, h - fd * d_h, phis)) / (2 * fd)
+        assert np.linalg.norm(cs - cd) <= 1e-7 * np.linalg.norm(cd)
+    real = P.laplace_solve(pm, eta, h, phis)
+    zero = P.laplace_solve(pm, eta + 0j, h + 0j, phis)
+    assert real.dtype == np.float64 and np.max(np.abs(real - zero.real)) <= 1e-14 * np.max(np.abs(real))
+    assert not zero.imag.any()
