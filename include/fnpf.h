@@ -589,6 +589,20 @@ fnpf_status fnpf_prism_precond_apply(fnpf_prism* mesh, const fnpf_prism_opts* op
 fnpf_status fnpf_prism_laplace_solve(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta,
                                      const double* h, const double* phis, double* phi, fnpf_solve_info* info,
                                      void* stream);
+/* Vector-Jacobian product of the prism Laplace solve (the differentiation form
+ * around Steps 4.1-4.3 of Sec. 3.4): for phi [N] = fnpf_prism_laplace_solve
+ * (eta, h, phis) and a cotangent lam_phi = dJ/dphi [N], writes dJ/deta,
+ * dJ/dphis and (lam_h non-NULL) dJ/dh [Ns]: one adjoint solve A_II psi =
+ * lam_phi,I with the solver of opts (A is symmetric; no projection), then
+ * dJ/dphis = lam_phi,S - (A psi)_S and dJ/d(eta, h) = -d(psi^T A(eta, h) phi)
+ * /d(eta, h), the metric's derivative at every quadrature point from
+ * d J^-1 = -J^-1 dJ J^-1 and d|det J| = |det J| tr(J^-1 dJ) through the
+ * vertical row (z_r, z_s, z_t) of J, chained to the nodal eta and h.  phi
+ * must be the solution for these eta, h (surface plane = phis).  Device
+ * arrays; errors as fnpf_prism_laplace_solve. */
+fnpf_status fnpf_prism_laplace_solve_vjp(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta,
+                                         const double* h, const double* phi, const double* lam_phi, double* lam_eta,
+                                         double* lam_phis, double* lam_h, fnpf_solve_info* info, void* stream);
 fnpf_status fnpf_prism_dtn(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta, const double* h,
                            const double* phis, double* w, fnpf_solve_info* info, void* stream);
 fnpf_status fnpf_prism_rhs(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta, const double* h,

@@ -319,6 +319,15 @@ fnpf_status fnpf_prism_laplace_solve(fnpf_prism* m, const fnpf_prism_opts* opts,
   });
 }
 
+fnpf_status fnpf_prism_laplace_solve_vjp(fnpf_prism* m, const fnpf_prism_opts* opts, const double* eta,
+                                         const double* h, const double* phi, const double* lam_phi, double* lam_eta,
+                                         double* lam_phis, double* lam_h, fnpf_solve_info* info, void* stream) {
+  if (!m || !eta || !h || !phi || !lam_phi || !lam_eta || !lam_phis) return FNPF_EINVAL;
+  return fnpf::with_stepper(m, opts, stream, "prism solve VJP", [&](auto& sp, const fnpf::pstep::Params& p) {
+    return sp.solve_vjp(eta, h, phi, lam_phi, lam_eta, lam_phis, lam_h, p, info);
+  });
+}
+
 fnpf_status fnpf_prism_dtn(fnpf_prism* m, const fnpf_prism_opts* opts, const double* eta, const double* h,
                            const double* phis, double* w, fnpf_solve_info* info, void* stream) {
   if (!m || !eta || !h || !phis || !w) return FNPF_EINVAL;

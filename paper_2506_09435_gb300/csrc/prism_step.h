@@ -760,6 +760,119 @@ struct ElementBlock {
   }
 };
 
+// The derivatives of B = grad_ref psi^T G grad_ref phi (G = w |det J| J^-1 J^-T)
+// with respect to the vertical row (z_r, z_s, z_t) of J at point (elem, k, q):
+// with M = J^-1, u = M^T grad_ref psi, v = M^T grad_ref phi and
+// d M = -M dJ M, d|det J| = |det J| tr(M dJ),
+//   dB / dz_j = w |det J| (M[j][2] u.v - u_z (M v)_j - v_z (M u)_j)
+// (the adjoint's geometric term, d(psi^T A(eta, h) phi) = sum of these times
+// the variations of z_r, z_s, z_t).  psi and phi are volume fields.
+struct GeomVjpItem {
+  struct Args {
+    PMesh m;
+    const double *eta, *h, *psi, *phi;
+    double* P;   // [points][3]
+  };
+  FNPF_HD static void ref_grad(const PMesh& m, const PointIdx& pi, const double* x, double* g) {
+    const int nt = m.nt, n = m.n;
+    const int* tn = m.tn + (int64_t)pi.e * nt;
+    const double* Lq = m.L + (int64_t)pi.q * nt;
+    const double* Lrq = m.Lr + (int64_t)pi.q * nt;
+    const double* Lsq = m.Ls + (int64_t)pi.q * nt;
+    const double* Dk = m.D + (int64_t)pi.k * n;
+    const int64_t plane0 = (int64_t)pi.l * m.p;
+    double gr = 0, gs = 0, gt = 0;
+    for (int c = 0; c < nt; ++c) {
+      const int64_t col = tn[c];
+      const double u = x[(plane0 + pi.k) * m.ns + col];
+      gr += Lrq[c] * u;
+      gs += Lsq[c] * u;
+      double uc = 0;
+      for (int mm = 0; mm < n; ++mm) uc += Dk[mm] * x[(plane0 + mm) * m.ns + col];
+      gt += Lq[c] * uc;
+    }
+    g[0] = gr;
+    g[1] = gs;
+    g[2] = gt;
+  }
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const PointIdx pi = point_of(m, i);
+    const int nt = m.nt;
+    const int* tn = m.tn + (int64_t)pi.e * nt;
+    const double* Lq = m.L + (int64_t)pi.q * nt;
+    const double* Lrq = m.Lr + (int64_t)pi.q * nt;
+    const double* Lsq = m.Ls + (int64_t)pi.q * nt;
+    double ev = 0, er = 0, es = 0, hv = 0, hr = 0, hs = 0;
+    for (int c = 0; c < nt; ++c) {
+      const double E = a.eta[tn[c]], H = a.h[tn[c]];
+      ev += Lq[c] * E;
+      er += Lrq[c] * E;
+      es += Lsq[c] * E;
+      hv += Lq[c] * H;
+      hr += Lrq[c] * H;
+      hs += Lsq[c] * H;
+    }
+    const double* gt = m.geo + 4 * (int64_t)pi.e;
+    const double xr = gt[0], xs = gt[1], yr = gt[2], ys = gt[3];
+    const double det2 = xr * ys - xs * yr;
+    const double sig = (pi.l + 0.5 * (1.0 + m.xi[pi.k])) / m.nz;
+    const double zr = -hr + sig * (er + hr), zs = -hs + sig * (es + hs), zt = (ev + hv) / (2.0 * m.nz);
+    const double det = det2 * zt;
+    // M = J^-1 (its third column is (0, 0, det2 / det))
+    const double M00 = ys * zt / det, M01 = -xs * zt / det;
+    const double M10 = -yr * zt / det, M11 = xr * zt / det;
+    const double M20 = (yr * zs - ys * zr) / det, M21 = (xs * zr - xr * zs) / det, M22 = det2 / det;
+    double ga[3], gb[3];
+    ref_grad(m, pi, a.psi, ga);
+    ref_grad(m, pi, a.phi, gb);
+    const double ux = M00 * ga[0] + M10 * ga[1] + M20 * ga[2], uy = M01 * ga[0] + M11 * ga[1] + M21 * ga[2],
+                 uz = M22 * ga[2];
+    const double vx = M00 * gb[0] + M10 * gb[1] + M20 * gb[2], vy = M01 * gb[0] + M11 * gb[1] + M21 * gb[2],
+                 vz = M22 * gb[2];
+    const double Mu0 = M00 * ux + M01 * uy, Mu1 = M10 * ux + M11 * uy, Mu2 = M20 * ux + M21 * uy + M22 * uz;
+    const double Mv0 = M00 * vx + M01 * vy, Mv1 = M10 * vx + M11 * vy, Mv2 = M20 * vx + M21 * vy + M22 * vz;
+    const double uv = ux * vx + uy * vy + uz * vz;
+    const double wd = m.wq[pi.q] * m.wv[pi.k] * fabs(det);
+    double* P = a.P + 3 * i;
+    P[0] = wd * (-uz * Mv0 - vz * Mu0);             // M[0][2] = 0
+    P[1] = wd * (-uz * Mv1 - vz * Mu1);             // M[1][2] = 0
+    P[2] = wd * (M22 * uv - uz * Mv2 - vz * Mu2);
+  }
+};
+
+// The geometric term at triangle slot (t, c): the point derivatives chained to
+// eta and h at the triangle's node c, summed over the prisms of its column:
+//   d / d eta_c: dz_r = sigma L_r[q][c], dz_s = sigma L_s[q][c], dz_t = L[q][c] / (2 N_z),
+//   d / d h_c:   dz_r = (sigma - 1) L_r[q][c], dz_s = (sigma - 1) L_s[q][c], dz_t = L[q][c] / (2 N_z).
+struct VjpTriItem {
+  struct Args {
+    PMesh m;
+    const double* P;
+    double* se;   // [ntri nt][2]: (eta, h)
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int t = (int)(i / m.nt), c = (int)(i - (int64_t)t * m.nt);
+    double ge = 0, gh = 0;
+    for (int l = 0; l < m.nz; ++l) {
+      const int64_t elem = (int64_t)t * m.nz + l;
+      for (int k = 0; k < m.n; ++k) {
+        const double sig = (l + 0.5 * (1.0 + m.xi[k])) / m.nz;
+        const double* P = a.P + 3 * (elem * m.n * m.nq + (int64_t)k * m.nq);
+        for (int q = 0; q < m.nq; ++q) {
+          const double rs = P[3 * q] * m.Lr[(int64_t)q * m.nt + c] + P[3 * q + 1] * m.Ls[(int64_t)q * m.nt + c];
+          const double tz = P[3 * q + 2] * m.L[(int64_t)q * m.nt + c] / (2.0 * m.nz);
+          ge += sig * rs + tz;
+          gh += (sig - 1.0) * rs + tz;
+        }
+      }
+    }
+    a.se[2 * i] = ge;
+    a.se[2 * i + 1] = gh;
+  }
+};
+
 // Element diagonal at local node (c, mm): sum over the points of g^T G g with g
 // the reference gradient of that node's basis function.
 struct DiagItem {
@@ -2027,6 +2140,60 @@ struct Stepper {
       info->status = st;
     }
     return st;
+  }
+
+  // Vector-Jacobian product of the solve phi = S(eta, h, phis) (phi the forward
+  // solution, full N): for dJ/dphi = lam [N], the adjoint solve A_II psi =
+  // lam_I (the same operator and preconditioner: A is symmetric), then
+  //   dJ/dphis = lam_S - (A psi)_S,  dJ/d(eta, h) = -d(psi^T A(eta, h) phi)/d(eta, h)
+  // (psi zero on the surface plane).  lam_h may be null.
+  fnpf_status solve_vjp(const double* eta, const double* h, const double* phi, const double* lam, double* lam_eta,
+                        double* lam_phis, double* lam_h, const Params& o, fnpf_solve_info* info) {
+    const int64_t N = m.N, NI = m.NI;
+    if (info) *info = fnpf_solve_info{0, 0, 0.0, FNPF_OK, 0.0f};
+    if (o.pmg && !pmg) return FNPF_EINVAL;
+    Params oa = o;
+    oa.projection = 0;   // the adjoint solves do not share the forward solutions' basis
+    FNPF_PS_TRY(geometry(eta, h));
+    if (oa.pmg) FNPF_PS_TRY(setup_pmg(eta, h, oa));
+    double* psi = w.xs;
+    FNPF_PS_TRY(go<FillItem>(N, {0.0, psi}));
+    FNPF_PS_TRY(go<InteriorItem>(N, {NI, 1.0, lam, w.r}));
+    double bb = 0;
+    FNPF_PS_TRY(dot(w.r, w.r, NI, &bb));
+    fnpf_status st = FNPF_OK;
+    int it = 0, outer = 0;
+    double rr = bb;
+    if (bb > 0) {
+      const double stop = oa.rtol * sqrt(bb);
+      FNPF_PS_TRY(go<FillItem>(N, {0.0, w.pd}));
+      if (oa.mixed) {
+        FNPF_PS_TRY(go<CopyItem>(NI, {w.r, w.z}));
+        st = defect_correction(psi, stop, oa, &it, &outer, &rr);
+      } else {
+        st = cg_run(NI, psi, w.r, w.z, w.pd, w.q, stop, oa.max_iter, oa.pmg ? 1 : 8, nullptr,
+                    [&](const double* pv, double* qv) { return apply(pv, qv); },
+                    [&](const double* rv, double* zv) { return precond(rv, zv, oa); }, &it, &rr);
+      }
+      if (st == FNPF_ECUDA) return st;
+    } else if (!(bb == 0)) {
+      st = FNPF_EDIVERGED;
+    }
+    if (info) {
+      info->iters = it;
+      info->outer_iters = outer;
+      info->rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
+      info->status = st;
+    }
+    if (st != FNPF_OK) return st;
+    FNPF_PS_TRY(apply(psi, w.q));
+    FNPF_PS_TRY(go<LinItem>(m.ns, {lam + NI, -1.0, w.q + NI, lam_phis}));
+    FNPF_PS_TRY(go<GeomVjpItem>(m.nelem * m.n * m.nq, {m, eta, h, psi, phi, w.F}));
+    FNPF_PS_TRY(go<VjpTriItem>((int64_t)m.ntri * m.nt, {m, w.F, w.se}));
+    FNPF_PS_TRY(go<SurfGatherItem>(m.ns, {m.soff, m.sinc, w.se, w.be, w.bp}));
+    FNPF_PS_TRY(go<InteriorItem>(m.ns, {m.ns, -1.0, w.be, lam_eta}));
+    if (lam_h) FNPF_PS_TRY(go<InteriorItem>(m.ns, {m.ns, -1.0, w.bp, lam_h}));
+    return FNPF_OK;
   }
 
   // Mass M = 1^T M_s eta and energy E = 1/2 phi^T A phi + 1/2 g eta^T M_s eta of

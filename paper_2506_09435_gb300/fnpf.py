@@ -119,6 +119,8 @@ def load():
         "fnpf_prism_apply_stored": [vp, vp, vp, vp, vp, vp],
         "fnpf_prism_laplace_solve": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_precond_apply": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp],
+        "fnpf_prism_laplace_solve_vjp": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp, vp, vp,
+                                         ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_dtn": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_rhs": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_rk4_step": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, ctypes.c_double, ctypes.c_double,
@@ -654,6 +656,18 @@ class PrismMesh:
         info = SolveInfo()
         st = _LIB.fnpf_prism_laplace_solve(self._h, None if opts is None else ctypes.byref(opts), *ptrs,
                                            ctypes.byref(info), _stream(stream))
+        return self._check(st, info.as_dict())
+
+    def laplace_solve_vjp(self, eta, h, phi, lam_phi, lam_eta, lam_phis, lam_h=None, opts=None, stream=None):
+        """dJ/deta, dJ/dphis (and dJ/dh) [Ns] of the solve phi [N] for the
+        cotangent lam_phi = dJ/dphi [N]; returns the adjoint solve's info."""
+        ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),
+                     (phi, self.N, "float64", "phi"), (lam_phi, self.N, "float64", "lam_phi"),
+                     (lam_eta, self.ns, "float64", "lam_eta"), (lam_phis, self.ns, "float64", "lam_phis"),
+                     (lam_h, self.ns, "float64", "lam_h"))
+        info = SolveInfo()
+        st = _LIB.fnpf_prism_laplace_solve_vjp(self._h, None if opts is None else ctypes.byref(opts), *ptrs,
+                                               ctypes.byref(info), _stream(stream))
         return self._check(st, info.as_dict())
 
     def dtn(self, eta, h, phis, w, opts=None, stream=None):

@@ -75,6 +75,7 @@ class Harness:
         lib.emu_sizes.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int64)] * 3
         lib.emu_sizes.restype = None
         sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_apply_items": [vp] * 5, "emu_laplace_solve": [vp] * 7, "emu_precond_apply": [vp] * 6,
+               "emu_laplace_solve_vjp": [vp] * 9,
                "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, ctypes.c_double, vp],
                "emu_set_relaxation": [vp] * 3 + [ctypes.c_double] * 6, "emu_invariants": [vp] * 7}
         sig["emu_set_filter"] = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
@@ -136,6 +137,13 @@ class EmuMesh:
         st = self.lib.emu_precond_apply(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(r), _p(z))
         assert st == 0, st
         return z
+
+    def laplace_solve_vjp(self, opts, eta, h, phi, lam):
+        le, lp, lh = np.zeros(self.ns), np.zeros(self.ns), np.zeros(self.ns)
+        st = self.lib.emu_laplace_solve_vjp(self.h, ctypes.byref(opts), _p(eta), _p(h), _p(phi), _p(lam), _p(le),
+                                            _p(lp), _p(lh))
+        assert st == 0, st
+        return le, lp, lh
 
     def dtn(self, opts, eta, h, phis):
         w, info = np.zeros(self.ns), SolveInfo()

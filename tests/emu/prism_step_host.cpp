@@ -224,6 +224,14 @@ int emu_precond_apply(void* h, const fnpf_prism_opts* o, const double* eta, cons
   return sp.precond_apply(eta, hh, r, z, prm);
 }
 
+int emu_laplace_solve_vjp(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phi,
+                          const double* lam, double* lam_eta, double* lam_phis, double* lam_h) {
+  Emu* e = static_cast<Emu*>(h);
+  const Params prm = params(o);
+  Stepper<HostEx> sp = stepper(e, prm);
+  return sp.solve_vjp(eta, hh, phi, lam, lam_eta, lam_phis, lam_h, prm, nullptr);
+}
+
 int emu_dtn(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis, double* w,
             fnpf_solve_info* info) {
   Emu* e = static_cast<Emu*>(h);

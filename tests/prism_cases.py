@@ -35,6 +35,19 @@ def standing_wave(pm, Lx=1.3, amp=0.01):
     return eta, h, np.zeros_like(eta)
 
 
+def complex_step_vjp(pm, eta, h, phis, lam, eps=1e-30):
+    """(dJ/deta, dJ/dphis, dJ/dh) of J = lam . phi(eta, h, phis) for the
+    oracle's solve, one complex step per surface node and argument."""
+    ge, gp, gh = np.zeros(pm.ns), np.zeros(pm.ns), np.zeros(pm.ns)
+    for c in range(pm.ns):
+        e = np.zeros(pm.ns)
+        e[c] = 1.0
+        ge[c] = lam @ P.laplace_solve(pm, eta + 1j * eps * e, h + 0j, phis + 0j).imag / eps
+        gh[c] = lam @ P.laplace_solve(pm, eta + 0j, h + 1j * eps * e, phis + 0j).imag / eps
+        gp[c] = lam @ P.laplace_solve(pm, eta + 0j, h + 0j, phis + 1j * eps * e).imag / eps
+    return ge, gp, gh
+
+
 def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 

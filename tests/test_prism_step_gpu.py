@@ -298,3 +298,17 @@ def test_defect_correction_rk4_steps_match_oracle(fnpf):
         gm.rk4_step(hd, e1, p1, 0.02, o)
         eo, po = P.rk4_step(pm, h, eo, po, 0.02, C.G)
     assert C.rel(e1.cpu().numpy(), eo) <= 1e-10 and C.rel(p1.cpu().numpy(), po) <= 1e-10
+
+
+@pytest.mark.parametrize("p, nz, pmg", [(2, 2, False), (3, 1, True)])
+def test_solve_vjp_matches_oracle_complex_step(fnpf, p, nz, pmg):
+    v, t, pm = C.mesh(p, nz, nx=2, ny=1)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi = P.laplace_solve(pm, eta, h, phis)
+    lam = np.random.default_rng(7).standard_normal(pm.N)
+    le, lp, lh = (torch.zeros(pm.ns, dtype=torch.float64, device=DEV) for _ in range(3))
+    gm.laplace_solve_vjp(T(eta), T(h), T(phi), T(lam), le, lp, lh, opts(fnpf, pmg=pmg))
+    ge, gp, gh = C.complex_step_vjp(pm, eta, h, phis, lam)
+    for dev_out, ref in ((le, ge), (lp, gp), (lh, gh)):
+        assert C.rel(dev_out.cpu().numpy(), ref) <= 1e-10

@@ -322,6 +322,21 @@ def test_defect_correction_rk4_steps_match_oracle(harness):
     assert C.rel(e1, eo) <= 1e-10 and C.rel(p1, po) <= 1e-10
 
 
+@pytest.mark.parametrize("p, nz, pmg", [(2, 2, False), (3, 1, True), (2, 3, True)])
+def test_solve_vjp_matches_oracle_complex_step(harness, p, nz, pmg):
+    """The vector-Jacobian product of the prism solve (adjoint solve, surface
+    rows, the metric's derivative through the vertical row of J) against the
+    oracle's complex-step derivatives in every eta, phis and h entry."""
+    v, t, pm = C.mesh(p, nz, nx=2, ny=1)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    phi = P.laplace_solve(pm, eta, h, phis)
+    lam = np.random.default_rng(7).standard_normal(pm.N)
+    le, lp, lh = em.laplace_solve_vjp(opts(pmg=pmg), eta, h, phi, lam)
+    ge, gp, gh = C.complex_step_vjp(pm, eta, h, phis, lam)
+    assert C.rel(le, ge) <= 1e-10 and C.rel(lp, gp) <= 1e-10 and C.rel(lh, gh) <= 1e-10
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -360,6 +375,7 @@ for p, nz in [(1, 1), (8, 1), (7, 2)]:
         assert em.laplace_solve(o, eta, h, phis, np.zeros(pm.N))[0] == 0
         assert em.rk4_step(o, h, eta.copy(), phis.copy(), 0.01)[0] == 0
     em.invariants(E.opts(g=C.G, pmg=True, pc32=True), eta, h, phis)
+    em.laplace_solve_vjp(E.opts(g=C.G, pmg=True), eta, h, np.ones(pm.N), np.ones(pm.N))
     for k in range(3):
         assert em.rk4_step(E.opts(g=C.G, pmg=True, projection=8), h, eta.copy(), phis.copy(), 0.01)[0] == 0
 v, t, pm, h, cr, gen, wave = C.flume(4, 2, nx=4, ny=1)
