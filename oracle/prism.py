@@ -268,8 +268,9 @@ def project_rhs(pm, eta, phis, w, g, linear=False):
         f_phi = -g eta - 1/2 |grad phi_eta|^2 + 1/2 w^2 (1 + |grad eta|^2)
     (linear: f_eta = w, f_phi = -g eta)."""
     tm = pm.tm
-    b_eta = np.zeros(pm.ns)
-    b_phi = np.zeros(pm.ns)
+    dt_ = np.result_type(eta, phis, w, float)   # complex for a complex step
+    b_eta = np.zeros(pm.ns, dtype=dt_)
+    b_phi = np.zeros(pm.ns, dtype=dt_)
     for e, (A, B, C) in enumerate(tm.tris):
         va, vb, vc = tm.verts[A], tm.verts[B], tm.verts[C]
         J2 = np.array([[vb[0] - va[0], vc[0] - va[0]], [vb[1] - va[1], vc[1] - va[1]]]) / 2.0

@@ -414,3 +414,20 @@ def test_complex_step_derivative_of_the_solve():
     zero = P.laplace_solve(pm, eta + 0j, h + 0j, phis)
     assert real.dtype == np.float64 and np.max(np.abs(real - zero.real)) <= 1e-14 * np.max(np.abs(real))
     assert not zero.imag.any()
+
+
+def test_complex_step_derivative_of_the_rk4_step():
+    """One prism RK4 step differentiated by a complex step in (eta, phis) and
+    in h equals central finite differences (the whole step's arithmetic is
+    analytic: solves, w, projected conditions)."""
+    from tests import prism_cases as C
+    v, t, pm = C.mesh(2, 2, nx=2, ny=1)
+    eta, h, phis = C.fields(pm)
+    rng = np.random.default_rng(5)
+    de, dp, dh = (rng.standard_normal(pm.ns) for _ in range(3))
+    dt, eps, fd = 0.02, 1e-30, 1e-6
+    ce, cp = P.rk4_step(pm, h + 1j * eps * dh, eta + 1j * eps * de, phis + 1j * eps * dp, dt, C.G)
+    pe, pp = P.rk4_step(pm, h + fd * dh, eta + fd * de, phis + fd * dp, dt, C.G)
+    me, mp = P.rk4_step(pm, h - fd * dh, eta - fd * de, phis - fd * dp, dt, C.G)
+    for cs, cd in ((ce.imag / eps, (pe - me) / (2 * fd)), (cp.imag / eps, (pp - mp) / (2 * fd))):
+        assert np.linalg.norm(cs - cd) <= 1e-6 * np.linalg.norm(cd)
