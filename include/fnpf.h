@@ -603,6 +603,22 @@ fnpf_status fnpf_prism_laplace_solve(fnpf_prism* mesh, const fnpf_prism_opts* op
 fnpf_status fnpf_prism_laplace_solve_vjp(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta,
                                          const double* h, const double* phi, const double* lam_phi, double* lam_eta,
                                          double* lam_phis, double* lam_h, fnpf_solve_info* info, void* stream);
+/* Adjoint of one prism RK4 step (the differentiation form around Sec. 3.2's
+ * ERK4 step, Sec. 3.4 Steps 4.1-4.6): for the step from (eta_n, phis_n) [Ns]
+ * and the cotangents (lam_eta, lam_phis) = dJ/d(eta, phis)_(n+1), writes
+ * dJ/d(eta, phis)_n into (lam_eta_out, lam_phis_out) and, if lam_h is not
+ * NULL, dJ/dh [Ns].  The forward stages are recomputed with opts (their
+ * states, potentials and w kept in the mesh's workspace), then each stage in
+ * reverse: two surface-mass solves for the cotangents of the projected
+ * conditions (M is symmetric), the conditions' and w's products at the
+ * triangle points and nodes, and fnpf_prism_laplace_solve_vjp's adjoint solve
+ * and geometric term.  EUNSUPPORTED while relaxation zones or a modal filter
+ * are set; other errors as fnpf_prism_rk4_step.  Device arrays; the outputs
+ * may not alias the inputs. */
+fnpf_status fnpf_prism_step_adjoint(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* h,
+                                    const double* eta_n, const double* phis_n, const double* lam_eta,
+                                    const double* lam_phis, double* lam_eta_out, double* lam_phis_out, double* lam_h,
+                                    double t, double dt, void* stream);
 fnpf_status fnpf_prism_dtn(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta, const double* h,
                            const double* phis, double* w, fnpf_solve_info* info, void* stream);
 fnpf_status fnpf_prism_rhs(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* eta, const double* h,

@@ -328,6 +328,18 @@ fnpf_status fnpf_prism_laplace_solve_vjp(fnpf_prism* m, const fnpf_prism_opts* o
   });
 }
 
+fnpf_status fnpf_prism_step_adjoint(fnpf_prism* m, const fnpf_prism_opts* opts, const double* h, const double* eta_n,
+                                    const double* phis_n, const double* lam_eta, const double* lam_phis,
+                                    double* lam_eta_out, double* lam_phis_out, double* lam_h, double t, double dt,
+                                    void* stream) {
+  if (!m || !h || !eta_n || !phis_n || !lam_eta || !lam_phis || !lam_eta_out || !lam_phis_out || !isfinite(dt) ||
+      !isfinite(t))
+    return FNPF_EINVAL;
+  return fnpf::with_stepper(m, opts, stream, "prism step adjoint", [&](auto& sp, const fnpf::pstep::Params& p) {
+    return sp.rk4_adjoint(h, eta_n, phis_n, t, dt, lam_eta, lam_phis, lam_eta_out, lam_phis_out, lam_h, p);
+  });
+}
+
 fnpf_status fnpf_prism_dtn(fnpf_prism* m, const fnpf_prism_opts* opts, const double* eta, const double* h,
                            const double* phis, double* w, fnpf_solve_info* info, void* stream) {
   if (!m || !eta || !h || !phis || !w) return FNPF_EINVAL;

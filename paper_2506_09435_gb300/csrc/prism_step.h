@@ -118,6 +118,7 @@ struct PWork {
   double* gram;                         // [(kMaxProj + 1) (kMaxProj + 2)] Gram matrix and right-hand side
   int hist_n = 0, hist_next = 0;        // stored solutions, next slot (host state)
   float *ie, *ir, *iz, *ip, *iq;        // [N] the FP32 inner solve of the defect correction
+  double *aN, *aS, *aq, *se3;           // adjoint: [5][N], [32][ns], [ntri nq 6], [ntri nt 3]
 };
 
 inline int64_t dot_partials(int64_t n) { return (n + kChunk - 1) / kChunk; }
@@ -151,6 +152,10 @@ void carve(const PMesh& m, PWork* w, Take take) {
   take(&w->H, (int64_t)(kMaxProj + 1) * m.N);
   take(&w->AH, (int64_t)(kMaxProj + 1) * m.N);
   take(&w->gram, (kMaxProj + 1) * (kMaxProj + 2));
+  take(&w->aN, 5 * m.N);
+  take(&w->aS, 32 * m.ns);
+  take(&w->aq, (int64_t)m.ntri * m.nq * 6);
+  take(&w->se3, (int64_t)m.ntri * m.nt * 3);
   float** inner[] = {&w->ie, &w->ir, &w->iz, &w->ip, &w->iq};
   for (float** f : inner) {   // a float buffer of N entries takes (N + 1) / 2 doubles
     double* d = nullptr;
@@ -1204,6 +1209,145 @@ struct SurfQItem {
   }
 };
 
+// The vector-Jacobian product of the weighted conditions at point (t, q): with
+// the cotangents nu_eta, nu_phi of the projected right-hand sides (nodal, the
+// mass solves' solutions) interpolated to the point, the coefficients of the
+// variations of (grad eta, grad phis, w, eta) there, times the rule's weight:
+// A = wt (nu_eta d f_eta + nu_phi d f_phi), 6 entries (d grad eta [2],
+// d grad phis [2], d w, d eta).
+struct SurfQVjpItem {
+  struct Args {
+    PMesh m;
+    const double *eta, *phis, *w, *ne, *np;
+    double g;
+    int linear;
+    double* A;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int nt = m.nt;
+    const int t = (int)(i / m.nq), q = (int)(i - (int64_t)t * m.nq);
+    const int* tn = m.tn + (int64_t)t * nt;
+    const double* Lq = m.L + (int64_t)q * nt;
+    const double* Lrq = m.Lr + (int64_t)q * nt;
+    const double* Lsq = m.Ls + (int64_t)q * nt;
+    double er = 0, es = 0, pr = 0, ps = 0, wv = 0, ne = 0, np = 0;
+    for (int c = 0; c < nt; ++c) {
+      const int64_t g = tn[c];
+      er += Lrq[c] * a.eta[g];
+      es += Lsq[c] * a.eta[g];
+      pr += Lrq[c] * a.phis[g];
+      ps += Lsq[c] * a.phis[g];
+      wv += Lq[c] * a.w[g];
+      ne += Lq[c] * a.ne[g];
+      np += Lq[c] * a.np[g];
+    }
+    const double* gt = m.geo + 4 * (int64_t)t;
+    const double xr = gt[0], xs = gt[1], yr = gt[2], ys = gt[3];
+    const double det = xr * ys - xs * yr;
+    const double wt = m.wq[q] * fabs(det);
+    double* A = a.A + 6 * i;
+    if (a.linear) {   // f_eta = w, f_phi = -g eta
+      A[0] = A[1] = A[2] = A[3] = 0.0;
+      A[4] = wt * ne;
+      A[5] = wt * np * -a.g;
+      return;
+    }
+    const double ex = (ys * er - yr * es) / det, ey = (xr * es - xs * er) / det;
+    const double px = (ys * pr - yr * ps) / det, py = (xr * ps - xs * pr) / det;
+    const double q2 = 1.0 + ex * ex + ey * ey;
+    A[0] = wt * (ne * (-px + 2.0 * wv * ex) + np * wv * wv * ex);
+    A[1] = wt * (ne * (-py + 2.0 * wv * ey) + np * wv * wv * ey);
+    A[2] = wt * (ne * -ex + np * -px);
+    A[3] = wt * (ne * -ey + np * -py);
+    A[4] = wt * (ne * q2 + np * wv * q2);
+    A[5] = wt * np * -a.g;
+  }
+};
+
+// The point coefficients of SurfQVjpItem chained to triangle node c (grad =
+// J_2^-T grad_ref): slots [ntri nt][3] = (d eta, d phis, d w).
+struct SurfNodeVjpItem {
+  struct Args {
+    PMesh m;
+    const double* A;
+    double* se;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int t = (int)(i / m.nt), c = (int)(i - (int64_t)t * m.nt);
+    const double* gt = m.geo + 4 * (int64_t)t;
+    const double xr = gt[0], xs = gt[1], yr = gt[2], ys = gt[3];
+    const double det = xr * ys - xs * yr;
+    double se = 0, sp = 0, sw = 0;
+    for (int q = 0; q < m.nq; ++q) {
+      const double l = m.L[(int64_t)q * m.nt + c], lr = m.Lr[(int64_t)q * m.nt + c], ls = m.Ls[(int64_t)q * m.nt + c];
+      const double gx = (ys * lr - yr * ls) / det, gy = (xr * ls - xs * lr) / det;
+      const double* A = a.A + 6 * ((int64_t)t * m.nq + q);
+      se += A[0] * gx + A[1] * gy + A[5] * l;
+      sp += A[2] * gx + A[3] * gy;
+      sw += A[4] * l;
+    }
+    a.se[3 * i] = se;
+    a.se[3 * i + 1] = sp;
+    a.se[3 * i + 2] = sw;
+  }
+};
+
+// Surface node c: its slots' three components summed in incidence order.
+struct SurfGather3Item {
+  struct Args {
+    const int64_t *off, *inc;
+    const double* se;
+    double *o0, *o1, *o2;
+  };
+  FNPF_HD static void at(int64_t c, const Args& a) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int64_t j = a.off[c]; j < a.off[c + 1]; ++j) {
+      s0 += a.se[3 * a.inc[j]];
+      s1 += a.se[3 * a.inc[j] + 1];
+      s2 += a.se[3 * a.inc[j] + 2];
+    }
+    a.o0[c] = s0;
+    a.o1[c] = s1;
+    a.o2[c] = s2;
+  }
+};
+
+// The vector-Jacobian product of w = s sum_j D[p][j] phi(top + j), s = 2 N_z /
+// (geo + h) at surface node c for the cotangent lw: lphi(top + j, c) =
+// lw s D[p][j] (lphi [N], zero elsewhere), and -lw w / (geo + h) added to
+// le (when le is not null: the geometry is eta) and to lh.
+struct WVjpItem {
+  struct Args {
+    PMesh m;
+    const double *geo, *h, *w, *lw;
+    double *lphi, *le, *lh;
+  };
+  FNPF_HD static void at(int64_t c, const Args& a) {
+    const PMesh& m = a.m;
+    const double d = a.geo[c] + a.h[c];
+    const double s = 2.0 * m.nz / d;
+    const double* Dp = m.D + (int64_t)m.p * m.n;
+    const int64_t top = m.nv - 1 - m.p;
+    for (int j = 0; j < m.n; ++j) a.lphi[(top + j) * m.ns + c] = a.lw[c] * s * Dp[j];
+    const double gw = -a.lw[c] * a.w[c] / d;
+    if (a.le) a.le[c] += gw;
+    a.lh[c] += gw;
+  }
+};
+
+struct Lin2Item {   // out = a x + b y
+  struct Args {
+    double a;
+    const double* x;
+    double b;
+    const double* y;
+    double* out;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) { a.out[i] = a.a * a.x[i] + a.b * a.y[i]; }
+};
+
 // Triangle slot (t, c): sum over the points of L[q][c] times the weighted conditions.
 struct SurfNodeItem {
   struct Args {
@@ -2193,6 +2337,90 @@ struct Stepper {
     FNPF_PS_TRY(go<SurfGatherItem>(m.ns, {m.soff, m.sinc, w.se, w.be, w.bp}));
     FNPF_PS_TRY(go<InteriorItem>(m.ns, {m.ns, -1.0, w.be, lam_eta}));
     if (lam_h) FNPF_PS_TRY(go<InteriorItem>(m.ns, {m.ns, -1.0, w.bp, lam_h}));
+    return FNPF_OK;
+  }
+
+  // The cotangents (gE, gP, gh) of a stage's input (E, P) and of h from those
+  // (mu_e, mu_p) of its right-hand side, with the stage's solution phi_s and
+  // w_s: nu = M^-1 mu (M symmetric), the conditions' products, w's product and
+  // the solve's (geometry E, or still water when linear).
+  fnpf_status rhs_vjp(const double* E, const double* h, const double* P, const double* phi_s, const double* w_s,
+                      const double* mu_e, const double* mu_p, double* gE, double* gP, double* gh, const Params& o) {
+    const int64_t ns = m.ns;
+    double* S = w.aS;
+    double *ne = S, *np = S + ns, *tw = S + 2 * ns, *le = S + 3 * ns, *lp = S + 4 * ns, *lh = S + 5 * ns;
+    double* lphi = w.aN;
+    FNPF_PS_TRY(mass_solve(mu_e, ne, o));
+    FNPF_PS_TRY(mass_solve(mu_p, np, o));
+    FNPF_PS_TRY(go<SurfQVjpItem>((int64_t)m.ntri * m.nq, {m, E, P, w_s, ne, np, o.g, o.linear, w.aq}));
+    FNPF_PS_TRY(go<SurfNodeVjpItem>((int64_t)m.ntri * m.nt, {m, w.aq, w.se3}));
+    FNPF_PS_TRY(go<SurfGather3Item>(ns, {m.soff, m.sinc, w.se3, gE, gP, tw}));
+    FNPF_PS_TRY(go<FillItem>(ns, {0.0, gh}));
+    const double* geo = o.linear ? w.zero : E;
+    FNPF_PS_TRY(go<FillItem>(m.N, {0.0, lphi}));
+    FNPF_PS_TRY(go<WVjpItem>(ns, {m, geo, h, w_s, tw, lphi, o.linear ? nullptr : gE, gh}));
+    FNPF_PS_TRY(solve_vjp(geo, h, phi_s, lphi, le, lp, lh, o, nullptr));
+    if (!o.linear) FNPF_PS_TRY(go<AxpyItem>(ns, {1.0, le, gE}));
+    FNPF_PS_TRY(go<AxpyItem>(ns, {1.0, lp, gP}));
+    return go<AxpyItem>(ns, {1.0, lh, gh});
+  }
+
+  // The adjoint of one RK4 step from (eta, phis) (the step-n state): for the
+  // cotangents (lam_e, lam_p) of the step's result, the cotangents of its
+  // input (out_e, out_p) and of h (out_h, may be null).  The forward stages
+  // are recomputed (their states, solutions and w kept), then swept in
+  // reverse: lam_k3 = dt/6 lam, lam_k2 = dt/3 lam + dt g3, lam_k1 = dt/3 lam +
+  // dt/2 g2, lam_k0 = dt/6 lam + dt/2 g1 with g_s the stage-input cotangents,
+  // out = lam + sum_s g_s.  Relaxation zones and the modal filter: EUNSUPPORTED.
+  fnpf_status rk4_adjoint(const double* h, const double* eta, const double* phis, double t, double dt,
+                          const double* lam_e, const double* lam_p, double* out_e, double* out_p, double* out_h,
+                          const Params& o) {
+    (void)t;
+    if (m.filt || m.rcr) return FNPF_EUNSUPPORTED;
+    const int64_t ns = m.ns, N = m.N;
+    double* S = w.aS;
+    auto st_e = [&](int s) { return S + (6 + 2 * s) * ns; };
+    auto st_p = [&](int s) { return S + (7 + 2 * s) * ns; };
+    auto ws = [&](int s) { return S + (14 + s) * ns; };
+    auto phs = [&](int s) { return w.aN + (1 + s) * N; };
+    double *lk_e = S + 18 * ns, *lk_p = S + 19 * ns, *acc_e = S + 20 * ns, *acc_p = S + 21 * ns;
+    double *acc_h = S + 22 * ns, *gE = S + 23 * ns, *gP = S + 24 * ns, *gh = S + 25 * ns;
+    // forward recompute of the stages
+    for (int s = 0; s < 4; ++s) {
+      if (s == 0) {
+        FNPF_PS_TRY(go<CopyItem>(ns, {eta, st_e(0)}));
+        FNPF_PS_TRY(go<CopyItem>(ns, {phis, st_p(0)}));
+      } else {
+        const double c = (s == 3 ? 1.0 : 0.5) * dt;
+        FNPF_PS_TRY(go<LinItem>(ns, {eta, c, w.ke, st_e(s)}));
+        FNPF_PS_TRY(go<LinItem>(ns, {phis, c, w.kp, st_p(s)}));
+      }
+      FNPF_PS_TRY(rhs(st_e(s), h, st_p(s), w.ke, w.kp, o, nullptr));
+      FNPF_PS_TRY(go<CopyItem>(N, {w.phi, phs(s)}));
+      FNPF_PS_TRY(go<CopyItem>(ns, {w.w, ws(s)}));
+    }
+    // reverse sweep
+    FNPF_PS_TRY(go<FillItem>(ns, {0.0, acc_e}));
+    FNPF_PS_TRY(go<FillItem>(ns, {0.0, acc_p}));
+    FNPF_PS_TRY(go<FillItem>(ns, {0.0, acc_h}));
+    for (int s = 3; s >= 0; --s) {
+      const double b = (s == 0 || s == 3 ? 1.0 : 2.0) * dt / 6.0;
+      if (s == 3) {
+        FNPF_PS_TRY(go<Lin2Item>(ns, {b, lam_e, 0.0, lam_e, lk_e}));
+        FNPF_PS_TRY(go<Lin2Item>(ns, {b, lam_p, 0.0, lam_p, lk_p}));
+      } else {
+        const double c = (s + 1 == 3 ? 1.0 : 0.5) * dt;   // stage s + 1 reads k_s with this weight
+        FNPF_PS_TRY(go<Lin2Item>(ns, {b, lam_e, c, gE, lk_e}));
+        FNPF_PS_TRY(go<Lin2Item>(ns, {b, lam_p, c, gP, lk_p}));
+      }
+      FNPF_PS_TRY(rhs_vjp(st_e(s), h, st_p(s), phs(s), ws(s), lk_e, lk_p, gE, gP, gh, o));
+      FNPF_PS_TRY(go<AxpyItem>(ns, {1.0, gE, acc_e}));
+      FNPF_PS_TRY(go<AxpyItem>(ns, {1.0, gP, acc_p}));
+      FNPF_PS_TRY(go<AxpyItem>(ns, {1.0, gh, acc_h}));
+    }
+    FNPF_PS_TRY(go<LinItem>(ns, {lam_e, 1.0, acc_e, out_e}));
+    FNPF_PS_TRY(go<LinItem>(ns, {lam_p, 1.0, acc_p, out_p}));
+    if (out_h) FNPF_PS_TRY(go<CopyItem>(ns, {acc_h, out_h}));
     return FNPF_OK;
   }
 

@@ -121,6 +121,8 @@ def load():
         "fnpf_prism_precond_apply": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp],
         "fnpf_prism_laplace_solve_vjp": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp, vp, vp,
                                          ctypes.POINTER(SolveInfo), vp],
+        "fnpf_prism_step_adjoint": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_double,
+                                    ctypes.c_double, vp],
         "fnpf_prism_dtn": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_rhs": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, vp, vp, ctypes.POINTER(SolveInfo), vp],
         "fnpf_prism_rk4_step": [vp, ctypes.POINTER(PrismOpts), vp, vp, vp, ctypes.c_double, ctypes.c_double,
@@ -669,6 +671,18 @@ class PrismMesh:
         st = _LIB.fnpf_prism_laplace_solve_vjp(self._h, None if opts is None else ctypes.byref(opts), *ptrs,
                                                ctypes.byref(info), _stream(stream))
         return self._check(st, info.as_dict())
+
+    def step_adjoint(self, h, eta_n, phis_n, lam_eta, lam_phis, lam_eta_out, lam_phis_out, dt, lam_h=None,
+                     opts=None, stream=None, t=0.0):
+        """dJ/d(eta, phis)_n (and dJ/dh) of one RK4 step from (eta_n, phis_n) for
+        the cotangents (lam_eta, lam_phis) of its result [Ns each]."""
+        ptrs = _ptrs(None, (h, self.ns, "float64", "h"), (eta_n, self.ns, "float64", "eta_n"),
+                     (phis_n, self.ns, "float64", "phis_n"), (lam_eta, self.ns, "float64", "lam_eta"),
+                     (lam_phis, self.ns, "float64", "lam_phis"), (lam_eta_out, self.ns, "float64", "lam_eta_out"),
+                     (lam_phis_out, self.ns, "float64", "lam_phis_out"), (lam_h, self.ns, "float64", "lam_h"))
+        st = _LIB.fnpf_prism_step_adjoint(self._h, None if opts is None else ctypes.byref(opts), *ptrs, float(t),
+                                          float(dt), _stream(stream))
+        self._check(st)
 
     def dtn(self, eta, h, phis, w, opts=None, stream=None):
         ptrs = _ptrs(None, (eta, self.ns, "float64", "eta"), (h, self.ns, "float64", "h"),

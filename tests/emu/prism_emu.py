@@ -76,6 +76,7 @@ class Harness:
         lib.emu_sizes.restype = None
         sig = {"emu_diagonal": [vp] * 4, "emu_apply_stored": [vp] * 5, "emu_apply_items": [vp] * 5, "emu_laplace_solve": [vp] * 7, "emu_precond_apply": [vp] * 6,
                "emu_laplace_solve_vjp": [vp] * 9,
+               "emu_step_adjoint": [vp] * 10 + [ctypes.c_double, ctypes.c_double],
                "emu_dtn": [vp] * 7, "emu_rhs": [vp] * 8, "emu_rk4_step": [vp] * 5 + [ctypes.c_double, ctypes.c_double, vp],
                "emu_set_relaxation": [vp] * 3 + [ctypes.c_double] * 6, "emu_invariants": [vp] * 7}
         sig["emu_set_filter"] = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
@@ -144,6 +145,12 @@ class EmuMesh:
                                             _p(lp), _p(lh))
         assert st == 0, st
         return le, lp, lh
+
+    def step_adjoint(self, opts, h, eta, phis, lam_e, lam_p, dt, t=0.0):
+        oe, op, oh = np.zeros(self.ns), np.zeros(self.ns), np.zeros(self.ns)
+        st = self.lib.emu_step_adjoint(self.h, ctypes.byref(opts), _p(h), _p(eta), _p(phis), _p(lam_e), _p(lam_p),
+                                       _p(oe), _p(op), _p(oh), float(t), float(dt))
+        return st, oe, op, oh
 
     def dtn(self, opts, eta, h, phis):
         w, info = np.zeros(self.ns), SolveInfo()

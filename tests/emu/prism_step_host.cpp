@@ -232,6 +232,14 @@ int emu_laplace_solve_vjp(void* h, const fnpf_prism_opts* o, const double* eta, 
   return sp.solve_vjp(eta, hh, phi, lam, lam_eta, lam_phis, lam_h, prm, nullptr);
 }
 
+int emu_step_adjoint(void* h, const fnpf_prism_opts* o, const double* hh, const double* eta, const double* phis,
+                     const double* le, const double* lp, double* oe, double* op, double* oh, double t, double dt) {
+  Emu* e = static_cast<Emu*>(h);
+  const Params prm = params(o);
+  Stepper<HostEx> sp = stepper(e, prm);
+  return sp.rk4_adjoint(hh, eta, phis, t, dt, le, lp, oe, op, oh, prm);
+}
+
 int emu_dtn(void* h, const fnpf_prism_opts* o, const double* eta, const double* hh, const double* phis, double* w,
             fnpf_solve_info* info) {
   Emu* e = static_cast<Emu*>(h);

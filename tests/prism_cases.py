@@ -48,6 +48,22 @@ def complex_step_vjp(pm, eta, h, phis, lam, eps=1e-30):
     return ge, gp, gh
 
 
+def complex_step_step_vjp(pm, h, eta, phis, lam_e, lam_p, dt, linear=False, eps=1e-30):
+    """J^T lam of one oracle RK4 step, entry by entry: one complex step per
+    unit direction in eta, phis and h."""
+    out = []
+    for which in range(3):
+        g = np.zeros(pm.ns)
+        for c in range(pm.ns):
+            d = [np.zeros(pm.ns) for _ in range(3)]
+            d[which][c] = 1.0
+            ce, cp = P.rk4_step(pm, h + 1j * eps * d[2], eta + 1j * eps * d[0], phis + 1j * eps * d[1], dt, G,
+                                linear=linear)
+            g[c] = lam_e @ (ce.imag / eps) + lam_p @ (cp.imag / eps)
+        out.append(g)
+    return out
+
+
 def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 

@@ -312,3 +312,21 @@ def test_solve_vjp_matches_oracle_complex_step(fnpf, p, nz, pmg):
     ge, gp, gh = C.complex_step_vjp(pm, eta, h, phis, lam)
     for dev_out, ref in ((le, ge), (lp, gp), (lh, gh)):
         assert C.rel(dev_out.cpu().numpy(), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("p, nz, pmg, linear", [(2, 2, False, False), (3, 1, True, False), (2, 2, True, True)])
+def test_step_adjoint_matches_oracle(fnpf, p, nz, pmg, linear):
+    v, t, pm = C.mesh(p, nz, nx=2, ny=1)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    rng = np.random.default_rng(3)
+    le, lp = rng.standard_normal(pm.ns), rng.standard_normal(pm.ns)
+    dt = 0.02
+    oe, op, oh = (torch.zeros(pm.ns, dtype=torch.float64, device=DEV) for _ in range(3))
+    o = fnpf.PrismMesh.default_opts(rtol=1e-13, mass_rtol=1e-13, g=C.G,
+                                    precond=fnpf.FNPF_PMG if pmg else fnpf.FNPF_JACOBI,
+                                    model=fnpf.FNPF_LINEAR if linear else fnpf.FNPF_NONLINEAR)
+    gm.step_adjoint(T(h), T(eta), T(phis), T(le), T(lp), oe, op, dt, lam_h=oh, opts=o)
+    ge, gp, gh = C.complex_step_step_vjp(pm, h, eta, phis, le, lp, dt, linear=linear)
+    for dev_out, ref in ((oe, ge), (op, gp), (oh, gh)):
+        assert C.rel(dev_out.cpu().numpy(), ref) <= 1e-9

@@ -337,6 +337,38 @@ def test_solve_vjp_matches_oracle_complex_step(harness, p, nz, pmg):
     assert C.rel(le, ge) <= 1e-10 and C.rel(lp, gp) <= 1e-10 and C.rel(lh, gh) <= 1e-10
 
 
+@pytest.mark.parametrize("p, nz, pmg, linear", [(2, 2, False, False), (3, 1, True, False), (2, 2, True, True)])
+def test_step_adjoint_matches_oracle(harness, p, nz, pmg, linear):
+    """The adjoint of one RK4 step (forward recompute, the projected
+    conditions' and w's products, the solve's VJP, the reverse RK4 sweep)
+    against the oracle's complex-step tangent: the dot-product identity
+    <lam, J d> = <J^T lam, d> for a random direction in (eta, phis, h), and
+    J^T lam entry by entry."""
+    v, t, pm = C.mesh(p, nz, nx=2, ny=1)
+    em = harness.mesh(v, t, p, nz)
+    eta, h, phis = C.fields(pm)
+    rng = np.random.default_rng(3)
+    le, lp = rng.standard_normal(pm.ns), rng.standard_normal(pm.ns)
+    dt = 0.02
+    st, oe, op, oh = em.step_adjoint(E.opts(rtol=1e-13, mass_rtol=1e-14, g=C.G, pmg=pmg, linear=linear), h, eta, phis,
+                                     le, lp, dt)
+    assert st == 0
+    de, dp, dh = (rng.standard_normal(pm.ns) for _ in range(3))
+    ce, cp = P.rk4_step(pm, h + 1e-30j * dh, eta + 1e-30j * de, phis + 1e-30j * dp, dt, C.G, linear=linear)
+    lhs = le @ (ce.imag / 1e-30) + lp @ (cp.imag / 1e-30)
+    assert abs(lhs - (oe @ de + op @ dp + oh @ dh)) <= 1e-10 * abs(lhs)
+    ge, gp, gh = C.complex_step_step_vjp(pm, h, eta, phis, le, lp, dt, linear=linear)
+    assert C.rel(oe, ge) <= 1e-9 and C.rel(op, gp) <= 1e-9 and C.rel(oh, gh) <= 1e-9
+
+
+def test_step_adjoint_unsupported_with_relaxation(harness):
+    v, t, pm, h, cr, gen, wave = C.flume(2, 1, nx=4, ny=1)
+    em = harness.mesh(v, t, 2, 1)
+    em.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+    z = np.zeros(pm.ns)
+    assert em.step_adjoint(opts(), h, z, z, z, z, 0.02)[0] == 7   # FNPF_EUNSUPPORTED
+
+
 ASAN_DRIVER = r"""
 import sys
 import numpy as np
@@ -376,6 +408,7 @@ for p, nz in [(1, 1), (8, 1), (7, 2)]:
         assert em.rk4_step(o, h, eta.copy(), phis.copy(), 0.01)[0] == 0
     em.invariants(E.opts(g=C.G, pmg=True, pc32=True), eta, h, phis)
     em.laplace_solve_vjp(E.opts(g=C.G, pmg=True), eta, h, np.ones(pm.N), np.ones(pm.N))
+    assert em.step_adjoint(E.opts(g=C.G, pmg=True), h, eta, phis, np.ones(pm.ns), np.ones(pm.ns), 0.01)[0] == 0
     for k in range(3):
         assert em.rk4_step(E.opts(g=C.G, pmg=True, projection=8), h, eta.copy(), phis.copy(), 0.01)[0] == 0
 v, t, pm, h, cr, gen, wave = C.flume(4, 2, nx=4, ny=1)
