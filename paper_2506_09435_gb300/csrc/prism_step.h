@@ -1817,6 +1817,38 @@ struct RelaxItem {
   }
 };
 
+// The relaxation zones' vector-Jacobian product at surface node c (the blend
+// f <- (1 - C_r) f + C_r f_true after the step to t1): the cotangents of the
+// blended state scaled by 1 - C_r into (le, lp), and C_r lam_phi d phi_I / dh
+// (the target potential's dependence on the depth, generation nodes) into dh.
+struct RelaxVjpItem {
+  struct Args {
+    PMesh m;
+    const double* h;
+    double t1, g;
+    const double *lam_e, *lam_p;
+    double *le, *lp, *dh;
+  };
+  FNPF_HD static void at(int64_t c, const Args& a) {
+    const PMesh& m = a.m;
+    const double cr = m.rcr[c];
+    a.le[c] = (1.0 - cr) * a.lam_e[c];
+    a.lp[c] = (1.0 - cr) * a.lam_p[c];
+    double d = 0.0;
+    if (cr != 0.0 && m.rgen[c] != 0.0) {
+      const double r = a.t1 / m.ramp < 1.0 ? a.t1 / m.ramp : 1.0;
+      const double th = m.kx * m.xs[c] + m.ky * m.ys[c] - m.omega * a.t1 + m.phase;
+      const double k = sqrt(m.kx * m.kx + m.ky * m.ky);
+      const double te = r * m.amp * cos(th), hc = a.h[c];
+      const double ch = cosh(k * hc);
+      // d/dh [cosh(k (te + h)) / cosh(k h)]
+      const double dq = k * (sinh(k * (te + hc)) * ch - cosh(k * (te + hc)) * sinh(k * hc)) / (ch * ch);
+      d = cr * a.lam_p[c] * r * (a.g * m.amp / m.omega) * sin(th) * dq;
+    }
+    a.dh[c] = d;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Orchestration.
 
@@ -2371,12 +2403,12 @@ struct Stepper {
   // are recomputed (their states, solutions and w kept), then swept in
   // reverse: lam_k3 = dt/6 lam, lam_k2 = dt/3 lam + dt g3, lam_k1 = dt/3 lam +
   // dt/2 g2, lam_k0 = dt/6 lam + dt/2 g1 with g_s the stage-input cotangents,
-  // out = lam + sum_s g_s.  Relaxation zones and the modal filter: EUNSUPPORTED.
+  // out = lam + sum_s g_s; with relaxation zones lam is first the cotangent of
+  // the blended state (RelaxVjpItem).  The modal filter: EUNSUPPORTED.
   fnpf_status rk4_adjoint(const double* h, const double* eta, const double* phis, double t, double dt,
-                          const double* lam_e, const double* lam_p, double* out_e, double* out_p, double* out_h,
-                          const Params& o) {
-    (void)t;
-    if (m.filt || m.rcr) return FNPF_EUNSUPPORTED;
+                          const double* lam_e_in, const double* lam_p_in, double* out_e, double* out_p,
+                          double* out_h, const Params& o) {
+    if (m.filt) return FNPF_EUNSUPPORTED;
     const int64_t ns = m.ns, N = m.N;
     double* S = w.aS;
     auto st_e = [&](int s) { return S + (6 + 2 * s) * ns; };
@@ -2385,6 +2417,14 @@ struct Stepper {
     auto phs = [&](int s) { return w.aN + (1 + s) * N; };
     double *lk_e = S + 18 * ns, *lk_p = S + 19 * ns, *acc_e = S + 20 * ns, *acc_p = S + 21 * ns;
     double *acc_h = S + 22 * ns, *gE = S + 23 * ns, *gP = S + 24 * ns, *gh = S + 25 * ns;
+    double *rl_e = S + 26 * ns, *rl_p = S + 27 * ns, *rl_h = S + 28 * ns;
+    const double* lam_e = lam_e_in;
+    const double* lam_p = lam_p_in;
+    if (m.rcr) {   // the cotangents of the state before the blend
+      FNPF_PS_TRY(go<RelaxVjpItem>(ns, {m, h, t + dt, o.g, lam_e_in, lam_p_in, rl_e, rl_p, rl_h}));
+      lam_e = rl_e;
+      lam_p = rl_p;
+    }
     // forward recompute of the stages
     for (int s = 0; s < 4; ++s) {
       if (s == 0) {
@@ -2402,7 +2442,8 @@ struct Stepper {
     // reverse sweep
     FNPF_PS_TRY(go<FillItem>(ns, {0.0, acc_e}));
     FNPF_PS_TRY(go<FillItem>(ns, {0.0, acc_p}));
-    FNPF_PS_TRY(go<FillItem>(ns, {0.0, acc_h}));
+    if (m.rcr) FNPF_PS_TRY(go<CopyItem>(ns, {rl_h, acc_h}));
+    else FNPF_PS_TRY(go<FillItem>(ns, {0.0, acc_h}));
     for (int s = 3; s >= 0; --s) {
       const double b = (s == 0 || s == 3 ? 1.0 : 2.0) * dt / 6.0;
       if (s == 3) {
