@@ -133,3 +133,55 @@ def rk4_trajectory(mesh, eta0, phis0, h, t0, dt, nsteps, keep_from=0, every=16):
         raise ValueError("need 0 <= keep_from <= nsteps")
     _check_depth(mesh, h)
     return RK4Trajectory.apply(eta0, phis0, h, mesh, t0, dt, nsteps, keep_from, every)
+
+class PrismRK4Run(torch.autograd.Function):
+    """The RK4 loop on a prism mesh (fnpf_prism_rk4_step forward,
+    fnpf_prism_step_adjoint backward) with checkpoints every `every` steps:
+    the backward recomputes each segment's step-start states from its
+    checkpoint, newest segment first, and runs the step adjoints over them in
+    reverse, accumulating dJ/dh (the depth enters every call, so it is
+    differentiated directly)."""
+
+    @staticmethod
+    def forward(ctx, eta0, phis0, h, mesh, t0, dt, nsteps, every, opts):
+        work_e = eta0.detach().clone().contiguous()
+        work_p = phis0.detach().clone().contiguous()
+        hd = h.detach().contiguous()
+        ckpts = []
+        for n in range(nsteps):
+            if n % every == 0:
+                ckpts.append((n, work_e.clone(), work_p.clone()))
+            mesh.rk4_step(hd, work_e, work_p, dt, opts, t=t0 + n * dt)
+        ctx.mesh, ctx.t0, ctx.dt, ctx.nsteps, ctx.every, ctx.opts = mesh, t0, dt, nsteps, every, opts
+        ctx.ckpts, ctx.hd = ckpts, hd
+        return work_e.clone(), work_p.clone()
+
+    @staticmethod
+    def backward(ctx, g_eta, g_phis):
+        mesh, t0, dt, nsteps, every, opts, hd = ctx.mesh, ctx.t0, ctx.dt, ctx.nsteps, ctx.every, ctx.opts, ctx.hd
+        ref = ctx.ckpts[0][1]
+        lam_e = (g_eta if g_eta is not None else torch.zeros_like(ref)).detach().clone().contiguous()
+        lam_p = (g_phis if g_phis is not None else torch.zeros_like(ref)).detach().clone().contiguous()
+        out_e, out_p = torch.empty_like(lam_e), torch.empty_like(lam_p)
+        lam_h = torch.zeros_like(hd)
+        step_h = torch.empty_like(hd)
+        for n0, e0, p0 in reversed(ctx.ckpts):
+            n1 = min(n0 + every, nsteps)
+            states = [(e0.clone(), p0.clone())]
+            for n in range(n0, n1 - 1):
+                e, p = states[-1][0].clone(), states[-1][1].clone()
+                mesh.rk4_step(hd, e, p, dt, opts, t=t0 + n * dt)
+                states.append((e, p))
+            for n in reversed(range(n0, n1)):
+                e, p = states[n - n0]
+                mesh.step_adjoint(hd, e, p, lam_e, lam_p, out_e, out_p, dt, lam_h=step_h, opts=opts, t=t0 + n * dt)
+                lam_e, out_e = out_e, lam_e
+                lam_p, out_p = out_p, lam_p
+                lam_h += step_h
+        return lam_e, lam_p, lam_h, None, None, None, None, None, None
+
+
+def prism_rk4_run(mesh, eta0, phis0, h, t0, dt, nsteps, every=16, opts=None):
+    """(eta_N, phi_N) after nsteps RK4 steps on a prism mesh (PrismMesh);
+    differentiable in eta0, phis0 and the depth h [Ns]."""
+    return PrismRK4Run.apply(eta0, phis0, h, mesh, t0, dt, nsteps, every, opts)

@@ -349,3 +349,33 @@ def test_step_adjoint_with_relaxation_matches_oracle(fnpf):
     lhs = le @ (ce.imag / 1e-30) + lp @ (cp.imag / 1e-30)
     rhs = oe.cpu().numpy() @ de + op.cpu().numpy() @ dp + oh.cpu().numpy() @ dh
     assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+def test_checkpointed_prism_gradients_match_oracle_complex_step(fnpf):
+    from paper_2506_09435_gb300 import autograd as AG
+    p, nz = 2, 1
+    v, t, pm = C.mesh(p, nz, nx=2, ny=1)
+    eta0, h0, phis0 = C.fields(pm)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    o = fnpf.PrismMesh.default_opts(rtol=1e-13, mass_rtol=1e-13, g=C.G)
+    dt, nsteps = 0.02, 3
+    e = T(eta0).requires_grad_(True)
+    ph = T(phis0).requires_grad_(True)
+    hh = T(h0).requires_grad_(True)
+    eN, pN = AG.prism_rk4_run(gm, e, ph, hh, 0.0, dt, nsteps, every=2, opts=o)
+    (eN.pow(2).sum() + pN.sum()).backward()
+
+    def J(de, dp, dh):
+        x, y = eta0 + de, phis0 + dp
+        for _ in range(nsteps):
+            x, y = P.rk4_step(pm, h0 + dh, x, y, dt, C.G)
+        return (x * x).sum() + y.sum()
+
+    eps, z = 1e-30, np.zeros(pm.ns, dtype=complex)
+    for grad, which in ((e.grad, 0), (ph.grad, 1), (hh.grad, 2)):
+        ref = np.zeros(pm.ns)
+        for c in range(pm.ns):
+            d = [z.copy(), z.copy(), z.copy()]
+            d[which][c] = 1j * eps
+            ref[c] = J(*d).imag / eps
+        assert C.rel(grad.cpu().numpy(), ref) <= 1e-9
