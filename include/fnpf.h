@@ -614,8 +614,8 @@ fnpf_status fnpf_prism_laplace_solve_vjp(fnpf_prism* mesh, const fnpf_prism_opts
  * triangle points and nodes, and fnpf_prism_laplace_solve_vjp's adjoint solve
  * and geometric term; with relaxation zones the blend's product comes first
  * (the cotangents scaled by 1 - C_r, and the target potential's dependence
- * on h into dJ/dh; t is the step's start time).  EUNSUPPORTED while a modal
- * filter is set; other errors as fnpf_prism_rk4_step.  Device arrays; the outputs
+ * on h into dJ/dh; t is the step's start time), and with a modal filter its
+ * transpose before that; errors as fnpf_prism_rk4_step.  Device arrays; the outputs
  * may not alias the inputs. */
 fnpf_status fnpf_prism_step_adjoint(fnpf_prism* mesh, const fnpf_prism_opts* opts, const double* h,
                                     const double* eta_n, const double* phis_n, const double* lam_eta,

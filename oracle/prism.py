@@ -400,7 +400,7 @@ def apply_filter(tm, f, alpha, order=2, cutoff=0):
     Fm = filter_matrix(p, alpha, order, cutoff)
     idx = tri_index(p)
     interior = np.array([i > 0 and j > 0 and i + j < p for i, j in idx])
-    out = np.array(f, dtype=np.float64, copy=True)
+    out = np.array(f, dtype=np.result_type(f, float), copy=True)   # complex for a complex step
     for e in range(len(tm.tris)):
         g = tm.nodes[e]
         out[g[interior]] = (Fm @ f[g])[interior]

@@ -1849,6 +1849,43 @@ struct RelaxVjpItem {
   }
 };
 
+// The transpose of the modal filter (the map f -> f with the triangle-interior
+// values replaced by F applied to the triangle's values): slot (t, c) gets
+// sum over the interior local nodes i of F[i][c] lam(tn[i]).
+struct FilterTSlotItem {
+  struct Args {
+    PMesh m;
+    const double* lam;
+    double* ft;
+  };
+  FNPF_HD static void at(int64_t i, const Args& a) {
+    const PMesh& m = a.m;
+    const int t = (int)(i / m.nt), c = (int)(i - (int64_t)t * m.nt);
+    const int* tn = m.tn + (int64_t)t * m.nt;
+    double s = 0;
+    for (int k = 0; k < m.nt; ++k)
+      if (m.interior[k]) s += m.filt[(int64_t)k * m.nt + c] * a.lam[tn[k]];
+    a.ft[i] = s;
+  }
+};
+
+// Node g: its own cotangent unless it is a triangle-interior node (replaced by
+// the filter), plus its slots' FilterTSlotItem sums.
+struct FilterTGatherItem {
+  struct Args {
+    PMesh m;
+    const double *lam, *ft;
+    double* out;
+  };
+  FNPF_HD static void at(int64_t g, const Args& a) {
+    const PMesh& m = a.m;
+    const int64_t j0 = m.soff[g];
+    double s = m.interior[m.sinc[j0] % m.nt] ? 0.0 : a.lam[g];
+    for (int64_t j = j0; j < m.soff[g + 1]; ++j) s += a.ft[m.sinc[j]];
+    a.out[g] = s;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Orchestration.
 
@@ -2403,12 +2440,12 @@ struct Stepper {
   // are recomputed (their states, solutions and w kept), then swept in
   // reverse: lam_k3 = dt/6 lam, lam_k2 = dt/3 lam + dt g3, lam_k1 = dt/3 lam +
   // dt/2 g2, lam_k0 = dt/6 lam + dt/2 g1 with g_s the stage-input cotangents,
-  // out = lam + sum_s g_s; with relaxation zones lam is first the cotangent of
-  // the blended state (RelaxVjpItem).  The modal filter: EUNSUPPORTED.
+  // out = lam + sum_s g_s; lam is first taken through the transposes of the
+  // modal filter (FilterTSlotItem, FilterTGatherItem) and of the relaxation
+  // blend (RelaxVjpItem) when these are set, in the reverse of their order.
   fnpf_status rk4_adjoint(const double* h, const double* eta, const double* phis, double t, double dt,
                           const double* lam_e_in, const double* lam_p_in, double* out_e, double* out_p,
                           double* out_h, const Params& o) {
-    if (m.filt) return FNPF_EUNSUPPORTED;
     const int64_t ns = m.ns, N = m.N;
     double* S = w.aS;
     auto st_e = [&](int s) { return S + (6 + 2 * s) * ns; };
@@ -2417,11 +2454,20 @@ struct Stepper {
     auto phs = [&](int s) { return w.aN + (1 + s) * N; };
     double *lk_e = S + 18 * ns, *lk_p = S + 19 * ns, *acc_e = S + 20 * ns, *acc_p = S + 21 * ns;
     double *acc_h = S + 22 * ns, *gE = S + 23 * ns, *gP = S + 24 * ns, *gh = S + 25 * ns;
-    double *rl_e = S + 26 * ns, *rl_p = S + 27 * ns, *rl_h = S + 28 * ns;
+    double *rl_e = S + 26 * ns, *rl_p = S + 27 * ns, *rl_h = S + 28 * ns, *fl_e = S + 29 * ns, *fl_p = S + 30 * ns;
     const double* lam_e = lam_e_in;
     const double* lam_p = lam_p_in;
+    if (m.filt) {   // the cotangents of the state before the filter
+      const int64_t slots = (int64_t)m.ntri * m.nt;
+      FNPF_PS_TRY(go<FilterTSlotItem>(slots, {m, lam_e_in, w.ft}));
+      FNPF_PS_TRY(go<FilterTGatherItem>(ns, {m, lam_e_in, w.ft, fl_e}));
+      FNPF_PS_TRY(go<FilterTSlotItem>(slots, {m, lam_p_in, w.ft}));
+      FNPF_PS_TRY(go<FilterTGatherItem>(ns, {m, lam_p_in, w.ft, fl_p}));
+      lam_e = fl_e;
+      lam_p = fl_p;
+    }
     if (m.rcr) {   // the cotangents of the state before the blend
-      FNPF_PS_TRY(go<RelaxVjpItem>(ns, {m, h, t + dt, o.g, lam_e_in, lam_p_in, rl_e, rl_p, rl_h}));
+      FNPF_PS_TRY(go<RelaxVjpItem>(ns, {m, h, t + dt, o.g, lam_e, lam_p, rl_e, rl_p, rl_h}));
       lam_e = rl_e;
       lam_p = rl_p;
     }

@@ -379,3 +379,24 @@ def test_checkpointed_prism_gradients_match_oracle_complex_step(fnpf):
             d[which][c] = 1j * eps
             ref[c] = J(*d).imag / eps
         assert C.rel(grad.cpu().numpy(), ref) <= 1e-9
+
+
+def test_step_adjoint_with_relaxation_and_filter_matches_oracle(fnpf):
+    p, nz = 3, 1
+    v, t, pm, h, cr, gen, wave = C.flume(p, nz, nx=4, ny=1)
+    gm = fnpf.PrismMesh(v, t, p, nz)
+    gm.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+    gm.set_filter(4.0, 2, 1)
+    rng = np.random.default_rng(11)
+    x = pm.tm.xs
+    eta, phis = 0.003 * np.cos(2.0 * x), 0.001 * np.sin(1.5 * x)
+    le, lp = rng.standard_normal(pm.ns), rng.standard_normal(pm.ns)
+    t0, dt = 4.0, 0.025
+    oe, op, oh = (torch.zeros(pm.ns, dtype=torch.float64, device=DEV) for _ in range(3))
+    gm.step_adjoint(T(h), T(eta), T(phis), T(le), T(lp), oe, op, dt, lam_h=oh, opts=opts(fnpf), t=t0)
+    de, dp, dh = (rng.standard_normal(pm.ns) for _ in range(3))
+    ce, cp = P.relaxation_step(pm, h + 1e-30j * dh, eta + 1e-30j * de, phis + 1e-30j * dp, t0, dt, C.G, cr, gen, wave,
+                               filt=(4.0, 2, 1))
+    lhs = le @ (ce.imag / 1e-30) + lp @ (cp.imag / 1e-30)
+    rhs = oe.cpu().numpy() @ de + op.cpu().numpy() @ dp + oh.cpu().numpy() @ dh
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)

@@ -381,9 +381,30 @@ def test_step_adjoint_with_relaxation_matches_oracle(harness):
     ce, cp = P.relaxation_step(pm, h + 1e-30j * dh, eta + 1e-30j * de, phis + 1e-30j * dp, t0, dt, C.G, cr, gen, wave)
     lhs = le @ (ce.imag / 1e-30) + lp @ (cp.imag / 1e-30)
     assert abs(lhs - (oe @ de + op @ dp + oh @ dh)) <= 1e-10 * abs(lhs)
-    em.set_filter(2.0, 2, 0)
-    z = np.zeros(pm.ns)
-    assert em.step_adjoint(opts(), h, z, z, z, z, dt)[0] == 7   # FNPF_EUNSUPPORTED
+
+
+
+def test_step_adjoint_with_relaxation_and_filter_matches_oracle(harness):
+    """Zones and the modal filter together (p = 3: triangles with interior
+    nodes): the dot-product identity against the oracle's filtered relaxation
+    step."""
+    p, nz = 3, 1
+    v, t, pm, h, cr, gen, wave = C.flume(p, nz, nx=4, ny=1)
+    em = harness.mesh(v, t, p, nz)
+    em.set_relaxation(cr, gen, wave["amp"], wave["kx"], wave["ky"], wave["omega"], wave["phase"], wave["ramp_time"])
+    em.set_filter(4.0, 2, 1)
+    rng = np.random.default_rng(11)
+    x = pm.tm.xs
+    eta, phis = 0.003 * np.cos(2.0 * x), 0.001 * np.sin(1.5 * x)
+    le, lp = rng.standard_normal(pm.ns), rng.standard_normal(pm.ns)
+    t0, dt = 4.0, 0.025
+    st, oe, op, oh = em.step_adjoint(opts(), h, eta, phis, le, lp, dt, t=t0)
+    assert st == 0
+    de, dp, dh = (rng.standard_normal(pm.ns) for _ in range(3))
+    ce, cp = P.relaxation_step(pm, h + 1e-30j * dh, eta + 1e-30j * de, phis + 1e-30j * dp, t0, dt, C.G, cr, gen, wave,
+                               filt=(4.0, 2, 1))
+    lhs = le @ (ce.imag / 1e-30) + lp @ (cp.imag / 1e-30)
+    assert abs(lhs - (oe @ de + op @ dp + oh @ dh)) <= 1e-10 * abs(lhs)
 
 
 ASAN_DRIVER = r"""
