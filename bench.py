@@ -736,12 +736,15 @@ def main_gb300(args):
 PRISM_T0 = 4.0   # the flume runs from rest at t = 4 s: the generation ramp (5 T) is at 80 %
 
 
-def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None, precision=0, projection=0):
+def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None, precision=0, projection=0,
+                    adjoint=False):
     """The prism path (operator, solve, w, projected conditions, RK4,
     relaxation zones) on the triangulated flume W.prism_flume from rest at
     t = 4 s: `warm` untimed steps, then `steps` steps timed with CUDA events on
     the current stream (L2 flushed before each when `flush` is given).
-    Returns (state, ms per timed step, mean CG iterations per solve, mesh)."""
+    Returns (state, ms per timed step, mean CG iterations per solve, mesh);
+    with `adjoint`, also the mean time of fnpf_prism_step_adjoint over the
+    same timed steps (the cotangent of sum(eta) at each step's start state)."""
     import torch
 
     from paper_2506_09435_gb300 import fnpf
@@ -758,10 +761,22 @@ def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None, 
     phis = torch.zeros(gm.ns, dtype=torch.float64, device=dev)
     dt = d["T"] / 40
     stream = torch.cuda.current_stream()
-    iters, ms = [], 0.0
+    iters, ms, ms_adj = [], 0.0, 0.0
+    if adjoint:
+        le, lz = torch.ones_like(eta), torch.zeros_like(eta)
+        oe, op, oh = torch.empty_like(eta), torch.empty_like(eta), torch.empty_like(eta)
     for k in range(warm + steps):
         if flush is not None:
             flush.zero_()
+        if adjoint and k >= warm:   # the adjoint of the step about to run, from the same start state
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gm.step_adjoint(h, eta, phis, le, lz, oe, op, dt, lam_h=oh, opts=o, t=PRISM_T0 + k * dt)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms_adj += a.elapsed_time(b)
+            if flush is not None:
+                flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         infos = gm.rk4_step(h, eta, phis, dt, o, t=PRISM_T0 + k * dt)
@@ -770,7 +785,8 @@ def prism_flume_run(dev, nx, ny, p, nz, steps, warm, rtol, precond, flush=None, 
         if k >= warm:
             ms += a.elapsed_time(b)
             iters += [i["iters"] for i in infos]
-    return (eta, phis), ms / max(1, steps), statistics.mean(iters) if iters else 0.0, gm
+    out = ((eta, phis), ms / max(1, steps), statistics.mean(iters) if iters else 0.0, gm)
+    return out + (ms_adj / max(1, steps),) if adjoint else out
 
 
 def prism_operator_timing(dev, nx, ny, p, nz, reps=20):
@@ -846,6 +862,14 @@ def prism_leg(dev, args, flush, size=(128, 32, 4, 2), sample=(6, 2, 3, 2, 2)):
         out["operator"] = prism_operator_timing(dev, nx, ny, p, nz)
     except Exception as e:
         out["operator"] = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
+    try:   # the step adjoint against the forward step (a fresh mesh: the same start states, 2 timed steps)
+        _, ms_f, _, gm, ms_a = prism_flume_run(dev, nx, ny, p, nz, 2, 2, args.rtol, fnpf.FNPF_PMG, flush,
+                                               projection=8, adjoint=True)
+        out["adjoint"] = {"ms_per_step": ms_a, "forward_ms_per_step": ms_f, "ratio": ms_a / ms_f,
+                          "note": "fnpf_prism_step_adjoint (forward stages recomputed) over fnpf_prism_rk4_step"}
+        del gm
+    except Exception as e:
+        out["adjoint"] = {"error": "%s: %s" % (type(e).__name__, str(e).splitlines()[0] if str(e) else "")}
     try:   # FP64 defect correction around the FP32 PCG, from the same state for the same steps
         (em_, pm_), msm, itm, gm = prism_flume_run(dev, nx, ny, p, nz, steps, 2, args.rtol, fnpf.FNPF_PMG, flush,
                                                    precision=fnpf.FNPF_MIXED, projection=8)

@@ -53,6 +53,13 @@ def fake_binding(monkeypatch, tmp_path):
         def diagonal(self, eta, h, d):
             d.copy_(torch.from_numpy(self.em.diagonal(eta.numpy(), h.numpy())))
 
+        def step_adjoint(self, h, e, p, le, lp, oe, op, dt, lam_h=None, opts=None, t=0.0):
+            st, a, b, c = self.em.step_adjoint(opts, h.numpy(), e.numpy(), p.numpy(), le.numpy(), lp.numpy(), dt, t=t)
+            assert st == 0
+            oe.copy_(torch.from_numpy(a))
+            op.copy_(torch.from_numpy(b))
+            lam_h.copy_(torch.from_numpy(c))
+
         def rk4_step(self, h, eta, phis, dt, opts, t=0.0):
             st, iters = self.em.rk4_step(opts, h.numpy(), eta.numpy(), phis.numpy(), dt, t=t)
             assert st == 0
@@ -77,6 +84,7 @@ def test_prism_leg_reports_throughput_iterations_and_oracle_error(fake_binding):
     assert 0 < out["cg_iters_per_solve_mean"] < out["jacobi"]["cg_iters_per_solve_mean"]
     op = out["operator"]
     assert op["stored_metric"]["flops_executed"] > 0 and "us_per_application" in op["metric_per_application"], op
+    assert out["adjoint"]["ratio"] > 0, out["adjoint"]
     mx = out["mixed"]
     assert mx["rel_l2_vs_fp64"]["eta"] <= 1e-8 and mx["rel_l2_vs_fp64"]["phis"] <= 1e-8, mx
     pc = out["fp64_pc32"]
